@@ -1,0 +1,254 @@
+"""Plain FP64 CPU oracle of the vectorial LBM for MHD.
+
+TEST INFRASTRUCTURE, NOT PART OF THE PRODUCT.  Only ``tests/``,
+``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may
+import this package.  It shares no code with the CUDA path; the product
+library never loads it.
+
+Two independent statements of the method live here:
+
+* ``vlbm_oracle.c`` -- plain C, two population arrays, push streaming,
+  compiled with ``-ffp-contract=off`` (the oracle proper);
+* ``numpy_ref.py`` -- a NumPy restatement for tiny grids, used to
+  brute-force check the C code.
+
+Equation numbers follow the order in which the paper displays them
+(Eq. 2 update, Eq. 3 equilibrium, Eq. 4 moments, Eq. 9 EOS, Eq. 12 ideal
+MHD flux); see the header of ``vlbm_oracle.c``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "vlbm_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+NVAR_IDEAL = 8
+NVAR_RESISTIVE = 7
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle with gcc (plain -O2, no FMA contraction, OpenMP)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+        return _LIB
+    tmp = _LIB + ".%d.tmp" % os.getpid()
+    cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC",
+           "-shared", "-std=c99", _SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _configure(L):
+    d, i, p = ctypes.c_double, ctypes.c_int, ctypes.c_void_p
+    L.orc_ideal_flux.argtypes = [d, p, p]
+    L.orc_ideal_flux.restype = None
+    L.orc_ideal_pressure.argtypes = [d, p]
+    L.orc_ideal_pressure.restype = d
+    L.orc_lattice_info.argtypes = [i, p, p, p, p]
+    L.orc_ideal_collide_cell.argtypes = [i, d, p, p, p, p]
+    L.orc_ideal_init.argtypes = [i, i, i, i, d, p, p]
+    L.orc_ideal_step.argtypes = [i, i, i, i, d, p, p, p, p, i]
+    L.orc_ideal_moments.argtypes = [i, i, i, i, p, p]
+    L.orc_ideal_run.argtypes = [i, i, i, i, d, p, p, p, i, p, i]
+    L.orc_resistive_init.argtypes = [i, i, i, p, p, p, p]
+    L.orc_resistive_step.argtypes = [i, i, i, d, d, p, p, i, p, p, p, p, i]
+    L.orc_resistive_moments.argtypes = [i, i, i, p, p, i, p, p, p]
+    L.orc_resistive_run.argtypes = [i, i, i, d, d, p, p, i, p, i, p, i]
+    return L
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            _lib = _configure(ctypes.CDLL(build()))
+    return _lib
+
+
+class use_library:
+    """Context manager: route every oracle call through another build of the
+    oracle source (used by the mutation test, which plants mistakes in a copy
+    of ``vlbm_oracle.c`` to show that the pins catch them)."""
+
+    def __init__(self, path: str):
+        self._new = _configure(ctypes.CDLL(path))
+
+    def __enter__(self):
+        global _lib
+        lib()
+        self._old = _lib
+        _lib = self._new
+        return self
+
+    def __exit__(self, *exc):
+        global _lib
+        _lib = self._old
+        return False
+
+
+def compile_variant(src_text: str, out_path: str) -> str:
+    """Compile an edited copy of the oracle source with the oracle's flags."""
+    c_path = out_path + ".c"
+    with open(c_path, "w") as fh:
+        fh.write(src_text)
+    subprocess.run(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC",
+                    "-shared", "-std=c99", c_path, "-o", out_path, "-lm"], check=True)
+    return out_path
+
+
+def source_text() -> str:
+    with open(_SRC) as fh:
+        return fh.read()
+
+
+def _ptr(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise ValueError("oracle %s failed (rc=%d)" % (what, rc))
+
+
+def lattice(q: int):
+    """(c[q,3] int, w[q], cs2, opp[q]) of D2Q5 / D3Q7 / D3Q19."""
+    c = np.zeros(3 * q, dtype=np.int32)
+    w = np.zeros(q)
+    opp = np.zeros(q, dtype=np.int32)
+    cs2 = ctypes.c_double(0.0)
+    _check(lib().orc_lattice_info(q, c.ctypes.data_as(ctypes.c_void_p), _ptr(w),
+                                  ctypes.byref(cs2), opp.ctypes.data_as(ctypes.c_void_p)),
+           "lattice_info")
+    return c.reshape(q, 3), w, cs2.value, opp
+
+
+def ideal_flux(gamma: float, Q) -> np.ndarray:
+    """Flux tensor phi[k, a] of ideal MHD (Eq. 12) at one state Q[8]."""
+    Q = _f64(Q)
+    phi = np.zeros(24)
+    lib().orc_ideal_flux(gamma, _ptr(Q), _ptr(phi))
+    return phi.reshape(8, 3)
+
+
+def ideal_pressure(gamma: float, Q) -> float:
+    return lib().orc_ideal_pressure(gamma, _ptr(_f64(Q)))
+
+
+def _dims(shape):
+    if len(shape) == 2:
+        ny, nx = shape
+        return 2, nx, ny, 1
+    nz, ny, nx = shape
+    return 3, nx, ny, nz
+
+
+def ideal_init(Q0: np.ndarray, gamma: float) -> np.ndarray:
+    """Populations f[8, q, *shape] = f_eq(Q0); Q0 has shape [8, (nz,) ny, nx]."""
+    Q0 = _f64(Q0)
+    dim, nx, ny, nz = _dims(Q0.shape[1:])
+    q = 5 if dim == 2 else 7
+    f = np.zeros((8, q) + Q0.shape[1:])
+    _check(lib().orc_ideal_init(dim, nx, ny, nz, gamma, _ptr(Q0), _ptr(f)), "init")
+    return f
+
+
+def ideal_step(f: np.ndarray, gamma: float, tau, src=None, nthreads: int = 1) -> np.ndarray:
+    f = _f64(f)
+    dim, nx, ny, nz = _dims(f.shape[2:])
+    out = np.empty_like(f)
+    tau = _f64(np.broadcast_to(np.asarray(tau, dtype=np.float64), (8,)))
+    s = _f64(src) if src is not None else None
+    _check(lib().orc_ideal_step(dim, nx, ny, nz, gamma, _ptr(tau),
+                                _ptr(s) if s is not None else None, _ptr(f), _ptr(out),
+                                nthreads), "step")
+    return out
+
+
+def ideal_moments(f: np.ndarray) -> np.ndarray:
+    f = _f64(f)
+    dim, nx, ny, nz = _dims(f.shape[2:])
+    Q = np.zeros((8,) + f.shape[2:])
+    _check(lib().orc_ideal_moments(dim, nx, ny, nz, _ptr(f), _ptr(Q)), "moments")
+    return Q
+
+
+def ideal_collide_cell(dim: int, gamma: float, tau, fin, src=None) -> np.ndarray:
+    """Post-collision populations [8, q] of one cell from its pre-collision ones."""
+    fin = _f64(fin)
+    out = np.zeros_like(fin)
+    tau = _f64(np.broadcast_to(np.asarray(tau, dtype=np.float64), (8,)))
+    s = _f64(src) if src is not None else None
+    _check(lib().orc_ideal_collide_cell(dim, gamma, _ptr(tau), _ptr(s) if s is not None else None,
+                                        _ptr(fin), _ptr(out)), "collide_cell")
+    return out
+
+
+def ideal_run(Q0: np.ndarray, gamma: float, tau, nsteps: int, src=None,
+              nthreads: int = 1) -> np.ndarray:
+    """Moments after nsteps steps of the ideal-MHD VLBM started from f_eq(Q0)."""
+    Q0 = _f64(Q0)
+    dim, nx, ny, nz = _dims(Q0.shape[1:])
+    out = np.zeros_like(Q0)
+    tau = _f64(np.broadcast_to(np.asarray(tau, dtype=np.float64), (8,)))
+    s = _f64(src) if src is not None else None
+    _check(lib().orc_ideal_run(dim, nx, ny, nz, gamma, _ptr(tau),
+                               _ptr(s) if s is not None else None, _ptr(Q0), nsteps,
+                               _ptr(out), nthreads), "run")
+    return out
+
+
+def resistive_init(Q0: np.ndarray, force):
+    Q0 = _f64(Q0)
+    nz, ny, nx = Q0.shape[1:]
+    f = np.zeros((19,) + Q0.shape[1:])
+    g = np.zeros((3, 7) + Q0.shape[1:])
+    _check(lib().orc_resistive_init(nx, ny, nz, _ptr(Q0), _ptr(_f64(force)), _ptr(f), _ptr(g)),
+           "resistive_init")
+    return f, g
+
+
+def resistive_step(f, g, tau_f, tau_m, force, b_wall, walls_y, nthreads: int = 1):
+    f, g = _f64(f), _f64(g)
+    nz, ny, nx = f.shape[1:]
+    fo, go = f.copy(), g.copy()
+    _check(lib().orc_resistive_step(nx, ny, nz, tau_f, tau_m, _ptr(_f64(force)),
+                                    _ptr(_f64(b_wall)), int(walls_y), _ptr(f), _ptr(g),
+                                    _ptr(fo), _ptr(go), nthreads), "resistive_step")
+    return fo, go
+
+
+def resistive_moments(f, g, force, b_wall, walls_y):
+    f, g = _f64(f), _f64(g)
+    nz, ny, nx = f.shape[1:]
+    Q = np.zeros((7,) + f.shape[1:])
+    _check(lib().orc_resistive_moments(nx, ny, nz, _ptr(_f64(force)), _ptr(_f64(b_wall)),
+                                       int(walls_y), _ptr(f), _ptr(g), _ptr(Q)),
+           "resistive_moments")
+    return Q
+
+
+def resistive_run(Q0, tau_f, tau_m, force, b_wall, walls_y, nsteps, nthreads: int = 1):
+    Q0 = _f64(Q0)
+    nz, ny, nx = Q0.shape[1:]
+    out = np.zeros_like(Q0)
+    _check(lib().orc_resistive_run(nx, ny, nz, tau_f, tau_m, _ptr(_f64(force)),
+                                   _ptr(_f64(b_wall)), int(walls_y), _ptr(Q0), nsteps,
+                                   _ptr(out), nthreads), "resistive_run")
+    return out

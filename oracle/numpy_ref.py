@@ -1,0 +1,213 @@
+"""Independent NumPy restatement of the VLBM step for tiny grids.
+
+TEST INFRASTRUCTURE (see ``oracle/__init__.py``).  It restates the same
+paper passages as ``vlbm_oracle.c`` in a different style (whole-array
+algebra, ``np.roll`` streaming, primitive variables first) so that a coding
+slip in either statement shows up as a disagreement on small grids:
+
+* Eq. 2  -- BGK collision, direct source injection, streaming x -> x + c_i;
+* Eq. 3  -- f_eq = w_i (Q_k + c_i . Phi_k / cs^2);
+* Eq. 4  -- Q_k = sum_i f_ki;
+* Eq. 9  -- p = (gamma - 1)(e_tot - rho|u|^2/2 - |B|^2/2);
+* Eq. 12 -- ideal MHD flux.
+
+The resistive model (D3Q19 + three D3Q7 magnetic lattices, Guo force,
+halfway bounce-back, equilibrium magnetic walls) follows the same reading
+as the C oracle.  Arrays use the layout [field, direction, (z,) y, x].
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def _axis_dirs(dim: int):
+    dirs = [(0, 0, 0)]
+    for a in range(dim):
+        e = [0, 0, 0]
+        e[a] = 1
+        dirs.append(tuple(e))
+        dirs.append(tuple(-v for v in e))
+    return np.array(dirs, dtype=int)
+
+
+def vset(name: str):
+    """Velocities, weights and cs^2 written out from the quadrature conditions."""
+    if name == "D2Q5":
+        c = _axis_dirs(2)
+        w = np.array([1 / 3] + [1 / 6] * 4)
+        return c, w, 1 / 3
+    if name == "D3Q7":
+        c = _axis_dirs(3)
+        w = np.array([1 / 4] + [1 / 8] * 6)
+        return c, w, 1 / 4
+    if name == "D3Q19":
+        c = list(_axis_dirs(3))
+        for (a, b) in ((0, 1), (0, 2), (1, 2)):
+            for (sa, sb) in ((1, 1), (-1, -1), (1, -1), (-1, 1)):
+                e = [0, 0, 0]
+                e[a], e[b] = sa, sb
+                c.append(np.array(e))
+        w = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
+        return np.array(c, dtype=int), w, 1 / 3
+    raise ValueError(name)
+
+
+def _shift(a: np.ndarray, c, dim: int) -> np.ndarray:
+    """Value at x moves to x + c (periodic).  Array axes are (z,) y, x."""
+    out = a
+    for ax in range(dim):
+        if c[ax]:
+            out = np.roll(out, c[ax], axis=a.ndim - 1 - ax)
+    return out
+
+
+def primitives(Q: np.ndarray, gamma: float):
+    rho = Q[0]
+    u = Q[1:4] / rho
+    e = Q[4]
+    B = Q[5:8]
+    p = (gamma - 1.0) * (e - 0.5 * rho * (u * u).sum(0) - 0.5 * (B * B).sum(0))
+    return rho, u, e, B, p
+
+
+def ideal_flux(Q: np.ndarray, gamma: float) -> np.ndarray:
+    """Phi[k, a, ...]: Eq. 12 assembled from primitive variables."""
+    rho, u, e, B, p = primitives(Q, gamma)
+    pt = p + 0.5 * (B * B).sum(0)
+    phi = np.zeros((8, 3) + Q.shape[1:])
+    phi[0] = rho * u
+    for b in range(3):
+        for a in range(3):
+            phi[1 + b, a] = rho * u[a] * u[b] - B[a] * B[b] + (pt if a == b else 0.0)
+            phi[5 + b, a] = u[a] * B[b] - B[a] * u[b]
+    phi[4] = (e + pt) * u - B * (u * B).sum(0)
+    return phi
+
+
+def ideal_feq(Q: np.ndarray, gamma: float, dim: int) -> np.ndarray:
+    c, w, cs2 = vset("D2Q5" if dim == 2 else "D3Q7")
+    phi = ideal_flux(Q, gamma)
+    feq = np.zeros((8, len(w)) + Q.shape[1:])
+    for i in range(len(w)):
+        cphi = sum(c[i, a] * phi[:, a] for a in range(3))
+        feq[:, i] = w[i] * (Q + cphi / cs2)
+    return feq
+
+
+def ideal_step(f: np.ndarray, gamma: float, tau, dim: int, src=None) -> np.ndarray:
+    c, w, _ = vset("D2Q5" if dim == 2 else "D3Q7")
+    Q = f.sum(axis=1)
+    feq = ideal_feq(Q, gamma, dim)
+    tau = np.broadcast_to(np.asarray(tau, dtype=float), (8,))
+    post = f + (feq - f) / tau[:, None].reshape((8, 1) + (1,) * (f.ndim - 2))
+    if src is not None:
+        s = np.asarray(src, dtype=float)
+        post = post + w[None, :].reshape((1, len(w)) + (1,) * (f.ndim - 2)) * \
+            s.reshape((8, 1) + (1,) * (f.ndim - 2))
+    out = np.empty_like(f)
+    for i in range(len(w)):
+        out[:, i] = _shift(post[:, i], c[i], dim)
+    return out
+
+
+def ideal_run(Q0: np.ndarray, gamma: float, tau, nsteps: int, src=None) -> np.ndarray:
+    dim = Q0.ndim - 1
+    f = ideal_feq(Q0, gamma, dim)
+    for _ in range(nsteps):
+        f = ideal_step(f, gamma, tau, dim, src)
+    return f.sum(axis=1)
+
+
+# ----------------------------------------------------------------------------
+# resistive incompressible reading: D3Q19 flow + three D3Q7 B lattices
+# ----------------------------------------------------------------------------
+
+def _flow_feq(rho, j, B):
+    c, w, cs2 = vset("D3Q19")
+    u = j / rho
+    B2 = (B * B).sum(0)
+    feq = np.zeros((19,) + rho.shape)
+    for i in range(19):
+        cu = sum(c[i, a] * u[a] for a in range(3))
+        cB = sum(c[i, a] * B[a] for a in range(3))
+        c2 = float((c[i] * c[i]).sum())
+        uu = (u * u).sum(0)
+        # (c c - cs2 I) : (rho u u + B^2/2 I - B B)
+        second = rho * (cu * cu - cs2 * uu) + 0.5 * B2 * (c2 - 3 * cs2) - (cB * cB - cs2 * B2)
+        feq[i] = w[i] * (rho + rho * cu / cs2 + second / (2 * cs2 * cs2))
+    return feq
+
+
+def _mag_feq(u, B):
+    c, w, cs2 = vset("D3Q7")
+    geq = np.zeros((3, 7) + B.shape[1:])
+    for b in range(3):
+        for i in range(7):
+            cphi = sum(c[i, a] * (u[a] * B[b] - B[a] * u[b]) for a in range(3))
+            geq[b, i] = w[i] * (B[b] + cphi / cs2)
+    return geq
+
+
+def resistive_init(Q0, force):
+    rho = Q0[0]
+    m = Q0[1:4]
+    B = Q0[4:7]
+    F = np.asarray(force, dtype=float).reshape(3, 1, 1, 1)
+    f = _flow_feq(rho, m - 0.5 * F, B)
+    g = _mag_feq(m / rho, B)
+    return f, g
+
+
+def resistive_step(f, g, tau_f, tau_m, force, b_wall, walls_y):
+    c19, w19, cs2 = vset("D3Q19")
+    c7, w7, _ = vset("D3Q7")
+    F = np.asarray(force, dtype=float).reshape(3, 1, 1, 1)
+    ny = f.shape[2]
+    wall = np.zeros(f.shape[1:], dtype=bool)
+    if walls_y:
+        wall[:, 0, :] = True
+        wall[:, ny - 1, :] = True
+    rho = f.sum(0)
+    j = np.stack([sum(c19[i, a] * f[i] for i in range(19)) for a in range(3)])
+    m = j + 0.5 * F
+    u = m / rho
+    B = g.sum(1)
+    feq = _flow_feq(rho, m, B)
+    geq = _mag_feq(u, B)
+    fo = f.copy()
+    go = g.copy()
+    for i in range(19):
+        cu = sum(c19[i, a] * u[a] for a in range(3))
+        cF = sum(c19[i, a] * F[a] for a in range(3))
+        uF = (u * F).sum(0)
+        guo = (1 - 0.5 / tau_f) * w19[i] * ((cF - uF) / cs2 + cu * cF / cs2 ** 2)
+        post = f[i] - (f[i] - feq[i]) / tau_f + guo
+        # a population whose destination is a wall returns in the opposite direction
+        dest_wall = _shift(wall, -c19[i], 3)  # dest_wall[x] = wall[x + c_i]
+        opp = [k for k in range(19) if (c19[k] == -c19[i]).all()][0]
+        moved = _shift(np.where(wall | dest_wall, np.nan, post), c19[i], 3)
+        keep = ~np.isnan(moved)
+        fo[i] = np.where(keep, moved, fo[i])
+        fo[opp] = np.where(dest_wall & ~wall, post, fo[opp])
+    for b in range(3):
+        for i in range(7):
+            post = np.where(wall, w7[i] * b_wall[b], g[b, i] - (g[b, i] - geq[b, i]) / tau_m)
+            go[b, i] = _shift(post, c7[i], 3)
+    return fo, go
+
+
+def resistive_moments(f, g, force, b_wall, walls_y):
+    c19, _, _ = vset("D3Q19")
+    F = np.asarray(force, dtype=float).reshape(3, 1, 1, 1)
+    rho = f.sum(0)
+    m = np.stack([sum(c19[i, a] * f[i] for i in range(19)) for a in range(3)]) + 0.5 * F
+    B = g.sum(1)
+    Q = np.concatenate([rho[None], m, B])
+    if walls_y:
+        ny = f.shape[2]
+        for y in (0, ny - 1):
+            Q[0, :, y, :] = 1.0
+            Q[1:4, :, y, :] = 0.0
+            for b in range(3):
+                Q[4 + b, :, y, :] = b_wall[b]
+    return Q

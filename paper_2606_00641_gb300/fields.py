@@ -1,0 +1,244 @@
+"""Seeded synthetic initial fields, in lattice units, for the VLBM workloads.
+
+This module only builds inputs.  It contains none of the update arithmetic
+(no equilibrium, no flux, no collision, no streaming); both the CUDA library
+and the CPU oracle receive the arrays it returns.
+
+Recipe (the same for every workload, parameters per workload):
+
+* random-phase scalar modes: ``s(x) = sum_m cos(2 pi k_m . x / n + phi_m)``
+  with integer wave vectors ``1 <= |k_m|_inf <= kmax`` and phases drawn from
+  one ``numpy.random.default_rng(seed)`` stream in a fixed order;
+* density ``rho = rho0 (1 + drho * s / max|s|)``;
+* velocity: each component its own random-phase sum, scaled so that
+  ``max |u| = mach * c_s0`` with ``c_s0 = sqrt(gamma p0 / mean(rho))``;
+* magnetic field ``B = delta x A``, the discrete centred curl of a
+  random-phase vector potential (2-D: ``A = A_z``, plus an independent
+  ``B_z``), so that the centred divergence of B vanishes to round-off;
+  scaled so that ``max |B|^2 = 2 p0 / beta``;
+* uniform gas pressure ``p0``; total energy from the ideal-gas relation of
+  the paper's EOS (sec. 2.3) solved for e_tot;
+* lattice scaling (sec. 2.2, "Unit conversion"): with the CFL reading
+  ``CFL = (max|u| + max c_f) dt / dx`` -- it reproduces the rotor's
+  ``dt ~ 1.3e-6`` at N = 2000, CFL = 0.01 (sec. 3.2) -- the velocity scale is
+  ``lam = (max|u| + max c_f) / CFL`` and ideal MHD is invariant under
+  ``u -> u/lam, B -> B/lam, p -> p/lam^2, e_tot -> e_tot/lam^2`` (mu_0 = 1).
+
+Field order of the conserved state (ideal MHD, 8 fields):
+``rho, rho u_x, rho u_y, rho u_z, e_tot, B_x, B_y, B_z``.
+Resistive incompressible state (7 fields): ``rho, m_x, m_y, m_z, B_x, B_y, B_z``.
+Arrays are C-ordered ``[field, (z,) y, x]`` (x fastest), float64.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field as dc_field
+
+import numpy as np
+
+IDEAL_FIELDS = ("rho", "mx", "my", "mz", "E", "Bx", "By", "Bz")
+RESISTIVE_FIELDS = ("rho", "mx", "my", "mz", "Bx", "By", "Bz")
+
+
+def _wavevectors(rng, dim: int, kmax: int, count: int):
+    ks = []
+    while len(ks) < count:
+        k = rng.integers(-kmax, kmax + 1, size=dim)
+        if np.abs(k).max() >= 1:
+            ks.append(k)
+    return ks
+
+
+def random_phase(rng, shape, kmax: int, count: int) -> np.ndarray:
+    """Sum of ``count`` unit cosines with random integer wave vectors and phases."""
+    dim = len(shape)
+    grids = np.meshgrid(*[np.arange(n, dtype=np.float64) / n for n in shape], indexing="ij")
+    # grids are ordered like the array axes: (z,) y, x; wave vectors are (x, y, z)
+    coords = list(reversed(grids))
+    out = np.zeros(shape)
+    for k in _wavevectors(rng, dim, kmax, count):
+        phase = rng.uniform(0.0, 2.0 * math.pi)
+        arg = sum(2.0 * math.pi * float(k[a]) * coords[a] for a in range(dim)) + phase
+        out += np.cos(arg)
+    return out
+
+
+def _cdiff(a: np.ndarray, axis_xyz: int) -> np.ndarray:
+    """Centred periodic difference along x (0), y (1) or z (2)."""
+    ax = a.ndim - 1 - axis_xyz
+    return 0.5 * (np.roll(a, -1, axis=ax) - np.roll(a, 1, axis=ax))
+
+
+def centred_divergence(Bx, By, Bz=None) -> np.ndarray:
+    div = _cdiff(Bx, 0) + _cdiff(By, 1)
+    if Bz is not None and Bx.ndim == 3:
+        div = div + _cdiff(Bz, 2)
+    return div
+
+
+def signal_speed(rho, u, p, B, gamma) -> float:
+    """max|u| + max c_f over the grid, with c_f^2 = (gamma p + |B|^2)/rho.
+
+    This is the velocity in the CFL reading ``CFL = (max|u| + max c_f) dt/dx``
+    (``u`` and ``B`` have a leading component axis of length 3).
+    """
+    u = np.asarray(u, dtype=float)
+    B = np.asarray(B, dtype=float)
+    cf = np.sqrt((gamma * np.asarray(p, dtype=float) + (B * B).sum(0)) / np.asarray(rho, dtype=float))
+    return float(np.sqrt((u * u).sum(0)).max() + cf.max())
+
+
+@dataclass
+class IdealFields:
+    Q: np.ndarray            # [8, (nz,) ny, nx] float64, lattice units
+    gamma: float
+    lam: float               # physical velocity per lattice velocity
+    mach: float
+    beta: float
+    cfl: float
+    seed: int
+    meta: dict = dc_field(default_factory=dict)
+
+
+def ideal_fields(shape, seed: int, *, gamma: float = 5.0 / 3.0, mach: float = 1.0,
+                 beta: float = 10.0 / 3.0, p0: float = 0.6, rho0: float = 1.0,
+                 drho: float = 0.1, cfl: float = 0.1, k_rho: int = 3, k_u: int = 2,
+                 k_b: int = 2) -> IdealFields:
+    """Smooth random-phase ideal-MHD state, scaled to lattice units.
+
+    2-D ``shape = (ny, nx)``, 3-D ``shape = (nz, ny, nx)``.  The defaults are
+    the 128^2 workload (peak Mach 1, beta 10/3, CFL 0.1, gamma 5/3).
+    """
+    shape = tuple(int(n) for n in shape)
+    dim = len(shape)
+    rng = np.random.default_rng(seed)
+    s = random_phase(rng, shape, k_rho, 4)
+    rho = rho0 * (1.0 + drho * s / np.abs(s).max())
+    u = [random_phase(rng, shape, k_u, 2) for _ in range(3)]
+    if dim == 2:
+        Az = random_phase(rng, shape, k_b, 3)
+        Bx = _cdiff(Az, 1)
+        By = -_cdiff(Az, 0)
+        Bz = random_phase(rng, shape, k_b, 2)
+    else:
+        A = [random_phase(rng, shape, k_b, 3) for _ in range(3)]
+        Bx = _cdiff(A[2], 1) - _cdiff(A[1], 2)
+        By = _cdiff(A[0], 2) - _cdiff(A[2], 0)
+        Bz = _cdiff(A[1], 0) - _cdiff(A[0], 1)
+    B = np.stack([Bx, By, Bz])
+    cs0 = math.sqrt(gamma * p0 / rho.mean())
+    umag = np.sqrt(sum(c * c for c in u))
+    u = np.stack(u) * (mach * cs0 / umag.max())
+    if beta > 0:
+        bmag2 = (B * B).sum(0)
+        B = B * math.sqrt((2.0 * p0 / beta) / bmag2.max())
+    else:
+        B = np.zeros_like(B)
+    p = np.full(shape, p0)
+    # lattice scaling from the CFL reading (max |u| + max fast speed)
+    vmax = signal_speed(rho, u, p, B, gamma)
+    lam = vmax / cfl
+    u = u / lam
+    B = B / lam
+    p = p / lam ** 2
+    e = p / (gamma - 1.0) + 0.5 * rho * (u * u).sum(0) + 0.5 * (B * B).sum(0)
+    Q = np.concatenate([rho[None], rho[None] * u, e[None], B]).astype(np.float64)
+    return IdealFields(Q=np.ascontiguousarray(Q), gamma=gamma, lam=lam, mach=mach, beta=beta,
+                       cfl=cfl, seed=seed,
+                       meta={"p0_lattice": p0 / lam ** 2, "vmax_phys": vmax})
+
+
+def uniform_ideal_state(shape, rho=1.0, u=(0.0, 0.0, 0.0), p=0.01, B=(0.0, 0.0, 0.0),
+                        gamma=5.0 / 3.0) -> np.ndarray:
+    """Spatially constant conserved state in lattice units."""
+    u = np.asarray(u, dtype=float)
+    B = np.asarray(B, dtype=float)
+    e = p / (gamma - 1.0) + 0.5 * rho * float(u @ u) + 0.5 * float(B @ B)
+    vals = [rho, rho * u[0], rho * u[1], rho * u[2], e, B[0], B[1], B[2]]
+    return np.stack([np.full(tuple(shape), v, dtype=np.float64) for v in vals])
+
+
+# ----------------------------------------------------------------------------
+# resistive incompressible channel (Hartmann set-up)
+# ----------------------------------------------------------------------------
+
+@dataclass
+class HartmannSetup:
+    Q: np.ndarray            # [7, nz, ny, nx]
+    tau_f: float
+    tau_m: float
+    nu: float
+    eta: float
+    force: tuple
+    b_wall: tuple
+    B0: float
+    Ha: float
+    a: float
+    U_c: float
+
+
+def hartmann_profile(y, a, F, rho, nu, eta, B0):
+    """Closed-form steady Hartmann flow with insulating walls at y = +-a.
+
+    Returns (u_x(y), b_x(y)) with y measured from the channel centre.  From
+    rho nu u'' + B0 b' + F = 0 and B0 u' + eta b'' = 0 with u(+-a) = b(+-a) = 0.
+    """
+    y = np.asarray(y, dtype=float)
+    if B0 == 0.0:
+        return F / (2.0 * rho * nu) * (a * a - y * y), np.zeros_like(y)
+    Ha = B0 * a / math.sqrt(rho * nu * eta)
+    u = F * a * a / (rho * nu * Ha * math.tanh(Ha)) * (1.0 - np.cosh(Ha * y / a) / math.cosh(Ha))
+    K = F * a * a / (rho * nu * Ha * math.sinh(Ha))
+    b = B0 * K * a / (eta * Ha) * (np.sinh(Ha * y / a) - (y / a) * math.sinh(Ha))
+    return u, b
+
+
+def hartmann_setup(shape, seed: int, *, Ha: float = 10.0, U_c: float = 0.05, Re: float = 100.0,
+                   Pm: float = 1.0, noise: float = 0.01, rho0: float = 1.0) -> HartmannSetup:
+    """Channel ``shape = (nz, ny, nx)`` with solid rows y = 0 and ny - 1.
+
+    Half-width a = (ny - 2)/2 (halfway walls), nu = U_c a / Re, eta = nu / Pm,
+    tau_f = 1/2 + 3 nu (D3Q19), tau_m = 1/2 + 4 eta (D3Q7),
+    B0 = Ha sqrt(rho nu eta) / a along y, body force F_x chosen so that the
+    closed-form centreline speed is U_c.  Initial velocity: uniform noise of
+    relative size ``noise`` (times U_c) per component in the fluid rows.
+    """
+    nz, ny, nx = (int(n) for n in shape)
+    a = (ny - 2) / 2.0
+    nu = U_c * a / Re
+    eta = nu / Pm
+    tau_f = 0.5 + 3.0 * nu
+    tau_m = 0.5 + 4.0 * eta
+    B0 = Ha * math.sqrt(rho0 * nu * eta) / a
+    if Ha > 0:
+        F = U_c * rho0 * nu * Ha * math.tanh(Ha) / (a * a * (1.0 - 1.0 / math.cosh(Ha)))
+    else:
+        F = U_c * 2.0 * rho0 * nu / (a * a)
+    rng = np.random.default_rng(seed)
+    Q = np.zeros((7, nz, ny, nx))
+    Q[0] = rho0
+    Q[1:4] = rho0 * noise * U_c * rng.uniform(-1.0, 1.0, size=(3, nz, ny, nx))
+    Q[5] = B0
+    Q[1:4, :, 0, :] = 0.0
+    Q[1:4, :, ny - 1, :] = 0.0
+    return HartmannSetup(Q=np.ascontiguousarray(Q), tau_f=tau_f, tau_m=tau_m, nu=nu, eta=eta,
+                         force=(F, 0.0, 0.0), b_wall=(0.0, B0, 0.0), B0=B0, Ha=Ha, a=a, U_c=U_c)
+
+
+# ----------------------------------------------------------------------------
+# batch of independent 2-D domains
+# ----------------------------------------------------------------------------
+
+BATCH_SIDES = (64, 128, 256, 512, 1024)
+
+
+def batch_specs(count: int = 64, seed: int = 4004, sides=BATCH_SIDES):
+    """Per-domain (side, gamma, mach, seed) drawn from one seeded stream."""
+    rng = np.random.default_rng(seed)
+    specs = []
+    for d in range(count):
+        side = int(rng.choice(np.asarray(sides)))
+        gamma = float(rng.uniform(1.4, 5.0 / 3.0))
+        mach = float(rng.uniform(0.5, 3.0))
+        specs.append({"side": side, "gamma": gamma, "mach": mach, "seed": seed + d})
+    return specs

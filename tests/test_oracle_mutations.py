@@ -1,0 +1,82 @@
+"""The oracle's pins are sensitive: each plausible mistake, planted in a copy
+of the oracle source and compiled on the CPU, makes at least one pin fail.
+
+The mutants never touch the real oracle build; they are compiled into a
+temporary directory and swapped in only for the duration of one check.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import test_oracle_pins as P
+import test_oracle_resistive as R
+
+IDEAL_PINS = [
+    lambda o: P.test_lattice_quadrature(o, 5),
+    lambda o: P.test_lattice_quadrature(o, 7),
+    lambda o: P.test_flux_jacobian_eigenvalues_are_mhd_wave_speeds(o, 1),
+    lambda o: P.test_flux_jacobian_eigenvalues_are_mhd_wave_speeds(o, 2),
+    lambda o: P.test_equilibrium_moments_return_state_and_flux(o, 2),
+    lambda o: P.test_equilibrium_moments_return_state_and_flux(o, 3),
+    lambda o: P.test_exact_conservation_periodic(o, 2, 0.9),
+    lambda o: P.test_centred_divB_stays_zero_with_tau_B_one(o, 3),
+    lambda o: P.test_linear_wave_speed_and_decay(o, "sound"),
+    lambda o: P.test_linear_wave_speed_and_decay(o, "oblique"),
+    lambda o: P.test_direct_source_injection_adds_S_per_cell_per_step(o),
+]
+RES_PINS = [
+    lambda o: R.test_mass_exact_and_force_adds_F_per_cell(o),
+    lambda o: R.test_shear_wave_decay_gives_viscosity(o),
+    lambda o: R.test_magnetic_diffusion_gives_eta(o),
+    lambda o: R.test_poiseuille_profile(o),
+    lambda o: R.test_hartmann_profile(o, 5.0),
+]
+
+# (name, original text, planted mistake, which pin family must catch it)
+MUTANTS = [
+    ("induction flux transposed", "phi[3 * (5 + b) + a] = u[a] * B[b] - B[a] * u[b];",
+     "phi[3 * (5 + b) + a] = u[b] * B[a] - B[b] * u[a];", IDEAL_PINS),
+    ("energy flux misses B(u.B)", "phi[3 * 4 + a] = (e + ptot) * u[a] - B[a] * uB;",
+     "phi[3 * 4 + a] = (e + ptot) * u[a];", IDEAL_PINS),
+    ("total pressure misses B^2/2", "double ptot = p + 0.5 * B2;", "double ptot = p;",
+     IDEAL_PINS),
+    ("EOS misses magnetic energy", "(e - 0.5 * rho * u2 - 0.5 * B2); /* Eq. 9 */",
+     "(e - 0.5 * rho * u2); /* Eq. 9 */", IDEAL_PINS),
+    ("Maxwell stress sign", "+ ptot * delta - B[a] * B[b];", "+ ptot * delta + B[a] * B[b];",
+     IDEAL_PINS),
+    ("D2Q5 rest weight", "set_dir(L, 0, 0, 0, 0, 1.0 / 3.0);\n        set_dir(L, 1, 1, 0, 0, 1.0 / 6.0);",
+     "set_dir(L, 0, 0, 0, 0, 0.3);\n        set_dir(L, 1, 1, 0, 0, 1.0 / 6.0);", IDEAL_PINS),
+    ("equilibrium drops 1/cs^2", "feq[k][i] = L->w[i] * (Q[k] + cphi / L->cs2);",
+     "feq[k][i] = L->w[i] * (Q[k] + cphi);", IDEAL_PINS),
+    ("BGK relaxes the wrong way", "double out = f + (feq[k][i] - f) / tau[k];",
+     "double out = f + (f - feq[k][i]) / tau[k];", IDEAL_PINS),
+    ("streams against c_i", "long dst = neighbour(x, y, z, L.c[i], nx, ny, nz);\n            for (int k = 0;",
+     "long dst = neighbour(x, y, z, L.c[L.opp[i]], nx, ny, nz);\n            for (int k = 0;",
+     IDEAL_PINS),
+    ("source injected without weight", "if (src) out += L->w[i] * src[k];",
+     "if (src) out += src[k];", IDEAL_PINS),
+    ("bounce-back keeps direction", "fout[(long)L19.opp[i] * N + cell] = fs;",
+     "fout[(long)i * N + cell] = fs;", RES_PINS),
+    ("Guo force half-step factor", "double guo = (1.0 - 0.5 / tau_f) * L19.w[i] *",
+     "double guo = L19.w[i] *", RES_PINS),
+    ("magnetic flux transposed", "for (int a = 0; a < 3; ++a) phi[a] = u[a] * B[b] - B[a] * u[b];",
+     "for (int a = 0; a < 3; ++a) phi[a] = u[b] * B[a] - B[b] * u[a];", RES_PINS),
+    ("Maxwell stress missing in flow", "(a == b ? 0.5 * B2 : 0.0) - B[a] * B[b];",
+     "(a == b ? 0.5 * B2 : 0.0);", RES_PINS),
+]
+
+
+@pytest.mark.parametrize("name,orig,planted,pins", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_pins_catch_planted_mistake(tmp_path, name, orig, planted, pins):
+    src = oracle.source_text()
+    assert src.count(orig) == 1, "mutation anchor not unique: " + name
+    so = oracle.compile_variant(src.replace(orig, planted), str(tmp_path / "mutant.so"))
+    caught = []
+    with oracle.use_library(so):
+        for pin in pins:
+            try:
+                with np.errstate(all="ignore"):
+                    pin(oracle)
+            except Exception as exc:  # an assertion or a numerical failure
+                caught.append(type(exc).__name__)
+    assert caught, "no pin caught the planted mistake: " + name
