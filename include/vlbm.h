@@ -1,0 +1,201 @@
+/*
+ * vlbm.h -- C ABI of the GB300-native vectorial lattice Boltzmann library
+ * (fused collide-and-stream update of the MHD conserved variables, each on
+ * its own small velocity set with a flux-carrying equilibrium).
+ *
+ * Paper passages implemented behind this interface (equations numbered in
+ * the order the paper displays them):
+ *   Eq. 2  fully local VLBM update: BGK collision, source injection, stream
+ *   Eq. 3  first-order equilibrium f_eq_ki = w_i (Q_k + c_i . Phi_k / cs^2)
+ *   Eq. 4  moments Q_k = sum_i f_ki
+ *   Eq. 9  EOS p = (gamma - 1)(e_tot - rho|u|^2/2 - |B|^2/2)
+ *   Eq. 12 ideal MHD state (rho, rho u, e_tot, B) and flux
+ *   sec. 2.3 "Incompressible resistive MHD" with sec. 2.4 "Static
+ *   boundaries" for the resistive channel model (D3Q19 flow lattice with a
+ *   second-order equilibrium carrying the Maxwell stress, three D3Q7
+ *   magnetic lattices with the Eq. 3 equilibrium, Guo body force, halfway
+ *   bounce-back walls at y = 0 and ny-1, magnetic walls held at the
+ *   equilibrium of the applied field).
+ *
+ * Conventions for every call
+ *   - Lattice units: dx = dt = 1.  Fields are double precision, structure of
+ *     arrays: Q[v * N + cell], cell = x + nx * (y + ny * z), x fastest,
+ *     N = nx * ny * nz.  Ideal MHD has nvar = 8 fields (rho, rho u_x,
+ *     rho u_y, rho u_z, e_tot, B_x, B_y, B_z); the resistive model has
+ *     nvar = 7 (rho, m_x, m_y, m_z, B_x, B_y, B_z), where m includes the
+ *     half-force shift of the Guo scheme.
+ *   - Velocity sets and direction order: D2Q5 (w0 = 1/3, w = 1/6,
+ *     cs^2 = 1/3), D3Q7 (w0 = 1/4, w = 1/8, cs^2 = 1/4), D3Q19 (1/3, 1/18,
+ *     1/36, cs^2 = 1/3).  Direction 0 is rest; 1 +x, 2 -x, 3 +y, 4 -y,
+ *     5 +z, 6 -z; D3Q19 continues 7 (+1,+1,0) 8 (-1,-1,0) 9 (+1,-1,0)
+ *     10 (-1,+1,0) 11 (+1,0,+1) 12 (-1,0,-1) 13 (+1,0,-1) 14 (-1,0,+1)
+ *     15 (0,+1,+1) 16 (0,-1,-1) 17 (0,+1,-1) 18 (0,-1,+1).
+ *   - Ownership: the caller owns every host and device array it passes and
+ *     keeps it alive for the duration of the call; the library copies.
+ *     The context owns all device memory it allocates (through the
+ *     optional allocator hooks) and releases it in vlbm_destroy.
+ *   - Streams: all device work of a context is enqueued on its stream
+ *     (params.stream, or a stream the library creates when it is NULL).
+ *     Calls that return host data synchronise that stream.
+ *   - Errors: every call returns a vlbm_status; vlbm_last_error() gives a
+ *     one-line reason.  After VLBM_ERR_NONPHYSICAL or VLBM_ERR_TIMEOUT the
+ *     context is sticky-failed (vlbm_step returns the error) until
+ *     vlbm_init_fields or vlbm_load succeeds.  A NULL context or a
+ *     non-positive size is VLBM_ERR_ARG.  No call aborts the process.
+ */
+#ifndef VLBM_H
+#define VLBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct vlbm_ctx vlbm_ctx;
+
+typedef enum {
+    VLBM_OK = 0,
+    VLBM_ERR_ARG = 1,          /* invalid argument or size */
+    VLBM_ERR_UNSTABLE = 2,     /* tau <= 1/2, or max(|u| + c_f) >= cs at init */
+    VLBM_ERR_OOM = 3,          /* device allocation failed */
+    VLBM_ERR_CUDA = 4,         /* a CUDA runtime call failed */
+    VLBM_ERR_NONPHYSICAL = 5,  /* NaN, rho <= 0 or p <= 0 seen by a kernel */
+    VLBM_ERR_TIMEOUT = 6,      /* a bounded device wait expired */
+    VLBM_ERR_STATE = 7,        /* call not valid in the context's state */
+    VLBM_ERR_UNSUPPORTED = 8   /* combination of options not built */
+} vlbm_status;
+
+typedef enum { VLBM_IDEAL = 0, VLBM_RESISTIVE = 1 } vlbm_model;
+
+/* Population storage.  F64: double storage and arithmetic.  F32: float
+ * storage and arithmetic.  F16_DEV / BF16_DEV: populations stored as
+ * half / bfloat16 shifted deviations (f_ki - w_i q_ref_k) / q_scale_k,
+ * decoded to float for the arithmetic. */
+typedef enum { VLBM_F64 = 0, VLBM_F32 = 1, VLBM_F16_DEV = 2, VLBM_BF16_DEV = 3 } vlbm_storage;
+
+typedef void *(*vlbm_alloc_fn)(size_t bytes, void *stream, void *user);
+typedef void (*vlbm_free_fn)(void *ptr, size_t bytes, void *stream, void *user);
+
+typedef struct {
+    int model;            /* vlbm_model */
+    int dim;              /* 2 (D2Q5 lattices) or 3 (D3Q7); resistive: 3 */
+    int nx, ny, nz;       /* cells per axis, nz = 1 when dim = 2 */
+    int storage;          /* vlbm_storage */
+    double gamma;         /* ideal: adiabatic index of the EOS (Eq. 9) */
+    double tau[8];        /* BGK relaxation time per lattice (Eq. 2), > 1/2.
+                             ideal: one per conserved field; resistive:
+                             tau[0] flow lattice, tau[1..3] magnetic lattices */
+    double source[8];     /* ideal: uniform direct-injection source S_k
+                             (f* += w_i S_k); zero for the Eq. 12 system */
+    double force[3];      /* resistive: body force per cell (Guo scheme) */
+    double b_wall[3];     /* resistive: field held by the magnetic walls */
+    int walls_y;          /* resistive: 1 = solid rows y = 0 and ny - 1 */
+    int check_every;      /* read the device health flag back every this many
+                             steps (0: only at vlbm_sync / vlbm_moments) */
+    double q_ref[8];      /* deviation storage: reference state per lattice */
+    double q_scale[8];    /* deviation storage: scale per lattice (0 -> 1) */
+    void *stream;         /* cudaStream_t to enqueue on, or NULL */
+    vlbm_alloc_fn alloc;  /* device allocator hook, or NULL for cudaMalloc */
+    vlbm_free_fn dealloc; /* matching release hook */
+    void *alloc_user;     /* passed back to the hooks */
+} vlbm_params;
+
+/* Fill *p with defaults: ideal MHD, dim 3, 64^3 cells, F32 storage,
+ * gamma = 5/3, tau = 0.51 on every lattice (the paper's showcase value,
+ * sec. 5 table), no source, no walls, check_every = 0, NULL hooks. */
+void vlbm_default_params(vlbm_params *p);
+
+/* Create a context for one domain: validates p (dims > 0, dim 2 => nz = 1,
+ * tau > 1/2, gamma > 1, storage/model combination built), allocates the
+ * single in-place population buffer (nvar lattices x q directions x N
+ * cells in the storage type) and a few words of status memory. */
+vlbm_status vlbm_create(const vlbm_params *p, vlbm_ctx **out);
+
+/* Create one context holding `count` independent periodic 2-D ideal-MHD
+ * domains (p[d] describes domain d; each may have its own size, gamma and
+ * tau).  All domains advance together: one vlbm_step launch covers every
+ * domain through a tile table.  Only F32 storage, dim 2, ideal model. */
+vlbm_status vlbm_create_batch(const vlbm_params *p, int count, vlbm_ctx **out);
+
+/* Set domain `domain` to f = f_eq(Q) (Eq. 3) from host fields Q
+ * (nvar x N doubles, lattice units) and reset its step count to 0.
+ * Returns VLBM_ERR_UNSTABLE when max(|u| + c_f) >= cs on some cell
+ * (c_f^2 = (gamma p + |B|^2)/rho; the scheme's diffusion
+ * (tau - 1/2)(cs^2 - a^2) would be negative), VLBM_ERR_NONPHYSICAL when
+ * rho <= 0 or p <= 0 somewhere.  Synchronises the stream. */
+vlbm_status vlbm_init_fields(vlbm_ctx *ctx, int domain, const double *Q_host);
+
+/* As vlbm_init_fields, Q_dev a device pointer (nvar x N doubles). */
+vlbm_status vlbm_init_fields_device(vlbm_ctx *ctx, int domain, const double *Q_dev);
+
+/* Enqueue n >= 0 time steps of Eq. 2 on every domain: one fused
+ * collide-and-stream kernel per step (in-place AA pattern), asynchronous.
+ * Returns the sticky status from the last health flag read back (a NaN,
+ * rho <= 0 or p <= 0 seen by a step kernel gives VLBM_ERR_NONPHYSICAL). */
+vlbm_status vlbm_step(vlbm_ctx *ctx, int n);
+
+/* Wait for the context's stream and return the health status. */
+vlbm_status vlbm_sync(vlbm_ctx *ctx);
+
+/* Zeroth moments Q_k = sum_i f_ki (Eq. 4) of domain `domain` at the
+ * current step, nvar x N doubles into host memory (synchronises). */
+vlbm_status vlbm_moments(vlbm_ctx *ctx, int domain, double *Q_host);
+
+/* As vlbm_moments into a device buffer, enqueued on the stream only. */
+vlbm_status vlbm_moments_device(vlbm_ctx *ctx, int domain, double *Q_dev);
+
+/* Pre-collision populations f_ki(x) at the current step (after streaming)
+ * for `ncells` cells listed in `cells` (linear indices, 0 <= cell < N),
+ * into f_host[c * nvar_q + j] with j running over the context's lattices
+ * in field order and directions in the order above (ideal: j = k*q + i;
+ * resistive: 19 flow directions then 3 x 7 magnetic ones).  Decoded to
+ * double.  Synchronises. */
+vlbm_status vlbm_gather_populations(vlbm_ctx *ctx, int domain, const int64_t *cells,
+                                    int ncells, double *f_host);
+
+/* Domain sums of the conserved fields, sum_x Q_k(x), accumulated in
+ * double precision from the stored populations (fixed reduction order:
+ * repeated calls on the same state return identical values), into
+ * sums[nvar] on the host.  Also refreshes the health status.  Synchronises. */
+vlbm_status vlbm_conservation(vlbm_ctx *ctx, int domain, double *sums);
+
+/* Checkpoint: raw populations, step count and parameters of every domain.
+ * With buf == NULL, *bytes receives the size needed.  vlbm_load restores a
+ * context created with identical parameters bit-exactly. */
+vlbm_status vlbm_save(vlbm_ctx *ctx, void *buf, size_t *bytes);
+vlbm_status vlbm_load(vlbm_ctx *ctx, const void *buf, size_t bytes);
+
+/* Batched contexts: time each built tile configuration for `steps` steps on
+ * the current state (state is restored afterwards) and keep the fastest;
+ * *choice receives its index.  Single-domain contexts return VLBM_OK with
+ * *choice = 0. */
+vlbm_status vlbm_autotune(vlbm_ctx *ctx, int steps, int *choice);
+
+/* Batched contexts: number of built tile shapes, and explicit selection of
+ * one (0 <= shape < vlbm_tile_shapes; VLBM_ERR_ARG otherwise).  Single-domain
+ * contexts have 0 shapes. */
+int vlbm_tile_shapes(const vlbm_ctx *ctx);
+vlbm_status vlbm_set_tile_shape(vlbm_ctx *ctx, int shape);
+
+/* Small queries. */
+int vlbm_nvar(const vlbm_ctx *ctx);                  /* 8 ideal, 7 resistive */
+int vlbm_slots_per_cell(const vlbm_ctx *ctx);        /* populations per cell: 40, 56 or 40 (D3Q19 + 3 x D3Q7) */
+int vlbm_num_domains(const vlbm_ctx *ctx);
+int64_t vlbm_num_cells(const vlbm_ctx *ctx, int domain);
+int64_t vlbm_step_count(const vlbm_ctx *ctx);
+int64_t vlbm_launch_count(const vlbm_ctx *ctx);      /* kernels this ctx launched */
+size_t vlbm_population_bytes(const vlbm_ctx *ctx);   /* device bytes of populations */
+void *vlbm_stream(const vlbm_ctx *ctx);              /* the cudaStream_t in use */
+const char *vlbm_last_error(const vlbm_ctx *ctx);
+const char *vlbm_status_string(int status);
+
+/* Release every device resource of the context (NULL is a no-op). */
+void vlbm_destroy(vlbm_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VLBM_H */

@@ -1,0 +1,73 @@
+// ideal_cell.cuh -- per-cell arithmetic of the ideal-MHD VLBM step (device).
+//
+// Given the 8 x q pre-collision populations of one cell, computes
+//   moments          Q_k = sum_i f_ki                                (Eq. 4)
+//   EOS              p = (gamma - 1)(e_tot - rho|u|^2/2 - |B|^2/2)    (Eq. 9)
+//   fluxes           Phi_k of ideal MHD along the lattice axes       (Eq. 12)
+//   BGK + source     f*_ki = f_ki + omega_k (f_eq_ki - f_ki) + w_i S_k
+//                    with f_eq_ki = w_i (Q_k + c_i . Phi_k / cs^2)  (Eq. 2, 3)
+// in place.  Directions: 0 rest, 2a+1 = +e_a, 2a+2 = -e_a; w_moving/cs^2 = 1/2.
+#pragma once
+
+#include "vlbm_internal.cuh"
+
+namespace vlbm {
+
+template <int D, class C>
+__device__ __forceinline__ void ideal_collide(C (&f)[8][AxisSet<D>::Q], const C gm1, const C *omega,
+                                              const C *src0, const C *src1, unsigned *flags)
+{
+    constexpr int Q = AxisSet<D>::Q;
+    C q[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        C s = f[k][0];
+#pragma unroll
+        for (int i = 1; i < Q; ++i) s += f[k][i];
+        q[k] = s;
+    }
+    const C rho = q[0];
+    const C ir = C(1) / rho;
+    const C m[3] = {q[1], q[2], q[3]};
+    const C u[3] = {m[0] * ir, m[1] * ir, m[2] * ir};
+    const C E = q[4];
+    const C B[3] = {q[5], q[6], q[7]};
+    const C B2 = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
+    const C mu = m[0] * u[0] + m[1] * u[1] + m[2] * u[2];
+    const C uB = u[0] * B[0] + u[1] * B[1] + u[2] * B[2];
+    const C p = gm1 * (E - C(0.5) * mu - C(0.5) * B2);
+    const C pt = p + C(0.5) * B2;
+    if (!(rho > C(0)) || !(p > C(0))) atomicOr(flags, kFlagNonPhysical);
+    const C Ept = E + pt;
+
+    C phi[8][D];
+#pragma unroll
+    for (int ax = 0; ax < D; ++ax) {
+        phi[0][ax] = m[ax];
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            phi[1 + b][ax] = m[ax] * u[b] - B[ax] * B[b] + (ax == b ? pt : C(0));
+            phi[5 + b][ax] = (ax == b) ? C(0) : u[ax] * B[b] - B[ax] * u[b];
+        }
+        phi[4][ax] = Ept * u[ax] - B[ax] * uB;
+    }
+
+    constexpr C w0 = C(AxisSet<D>::w0), w1 = C(AxisSet<D>::w1);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const C om = omega[k];
+        const C omc = C(1) - om;
+        const C A0 = om * w0 * q[k] + src0[k];
+        const C A1 = om * w1 * q[k] + src1[k];
+        const C hom = C(0.5) * om;  // omega * w_moving / cs^2
+        f[k][0] = omc * f[k][0] + A0;
+#pragma unroll
+        for (int ax = 0; ax < D; ++ax) {
+            const C bv = hom * phi[k][ax];
+            f[k][2 * ax + 1] = omc * f[k][2 * ax + 1] + A1 + bv;
+            f[k][2 * ax + 2] = omc * f[k][2 * ax + 2] + A1 - bv;
+        }
+    }
+}
+
+}  // namespace vlbm

@@ -1,0 +1,487 @@
+// k_ideal.cu -- ideal compressible MHD on D2Q5 / D3Q7 lattices (sm_103a).
+//
+// One fused kernel per time step performs Eq. 2 of the paper for every cell:
+// it loads the cell's 8 x q populations (AA in-place pattern, see
+// vlbm_internal.cuh), forms the moments Q_k (Eq. 4), the primitive state and
+// gas pressure from the EOS (Eq. 9), the ideal MHD fluxes (Eq. 12), relaxes
+// every population towards the first-order equilibrium of Eq. 3 (BGK), adds
+// the direct-injection source w_i S_k, and stores the results so that the
+// next step finds them streamed.
+//
+// The step is HBM-bound (8 q populations read and written once per cell;
+// a few hundred flops per cell against 448 B at FP32/D3Q7), so the design
+// goal is plain bandwidth: one cell per thread, coalesced x-contiguous slot
+// planes, every load issued before any arithmetic, no shared memory, grid
+// (ceil(nx/128), ny, nz).
+#include "ideal_cell.cuh"
+
+namespace vlbm {
+namespace {
+
+template <class C> struct IdealArgs {
+    void *pop;
+    int nx, ny, nz;
+    int64_t stride;
+    C gm1;
+    C omega[kMaxLat];
+    C src0[kMaxLat];
+    C src1[kMaxLat];
+    C ref0[kMaxLat];
+    C ref1[kMaxLat];
+    C scale[kMaxLat];
+    C inv_scale[kMaxLat];
+    unsigned *flags;
+};
+
+// Linear indices of the cell's neighbours x + c_i (periodic), i in set order.
+template <int D>
+__device__ __forceinline__ void neighbours(int x, int y, int z, int nx, int ny, int nz, int64_t cell,
+                                           int64_t *nb)
+{
+    const int64_t row = nx;
+    const int64_t plane = (int64_t)nx * ny;
+    nb[0] = cell;
+    nb[1] = (x + 1 < nx) ? cell + 1 : cell + 1 - nx;
+    nb[2] = (x > 0) ? cell - 1 : cell - 1 + nx;
+    nb[3] = (y + 1 < ny) ? cell + row : cell + row - plane;
+    nb[4] = (y > 0) ? cell - row : cell - row + plane;
+    if (D == 3) {
+        const int64_t vol = plane * nz;
+        nb[5] = (z + 1 < nz) ? cell + plane : cell + plane - vol;
+        nb[6] = (z > 0) ? cell - plane : cell - plane + vol;
+    }
+}
+
+template <int D, class S, class C>
+__device__ __forceinline__ C decode(const IdealArgs<C> &a, const S *p, int k, int i)
+{
+    C v = Codec<S>::load(p);
+    if constexpr (Codec<S>::kDev) v = v * a.scale[k] + (i == 0 ? a.ref0[k] : a.ref1[k]);
+    return v;
+}
+
+template <int D, class S, class C>
+__device__ __forceinline__ void encode(const IdealArgs<C> &a, S *p, int k, int i, C v)
+{
+    if constexpr (Codec<S>::kDev) v = (v - (i == 0 ? a.ref0[k] : a.ref1[k])) * a.inv_scale[k];
+    Codec<S>::store(p, v);
+}
+
+// The fused collide-and-stream step.  ODD selects the AA parity.
+template <int D, class S, class C, bool ODD>
+__global__ void __launch_bounds__(kBlockX) k_ideal_step(const IdealArgs<C> a)
+{
+    constexpr int Q = AxisSet<D>::Q;
+    const int x = blockIdx.x * kBlockX + threadIdx.x;
+    if (x >= a.nx) return;
+    const int y = blockIdx.y, z = blockIdx.z;
+    const int64_t cell = x + (int64_t)a.nx * (y + (int64_t)a.ny * z);
+    int64_t nb[Q];
+    neighbours<D>(x, y, z, a.nx, a.ny, a.nz, cell, nb);
+    S *pop = static_cast<S *>(a.pop);
+
+    // load: even parity reads slot (i, x); odd parity reads slot (opp i, x - c_i)
+    C f[8][Q];
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const int j = ODD ? opp_axis(i) : i;
+            const int64_t at = ODD ? nb[opp_axis(i)] : cell;
+            f[k][i] = decode<D, S, C>(a, pop + (int64_t)(k * Q + j) * a.stride + at, k, i);
+        }
+
+    ideal_collide<D, C>(f, a.gm1, a.omega, a.src0, a.src1, a.flags);
+
+    // store: even parity sends direction i to slot (opp i, x);
+    //        odd parity sends direction i to slot (i, x + c_i)
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const int j = ODD ? i : opp_axis(i);
+            const int64_t at = ODD ? nb[i] : cell;
+            encode<D, S, C>(a, pop + (int64_t)(k * Q + j) * a.stride + at, k, i, f[k][i]);
+        }
+}
+
+// f = f_eq(Q) at parity 0, computed in double; also checks positivity and the
+// sub-characteristic condition max(|u| + c_f) < cs of the scheme.
+template <int D, class S> struct InitArgs {
+    void *pop;
+    int64_t stride;
+    int64_t c0, count, qstride;
+    double gamma;
+    double ref[kMaxLat], scale[kMaxLat];
+    unsigned *flags;
+};
+
+template <int D, class S>
+__global__ void k_ideal_init(const InitArgs<D, S> a, const double *__restrict__ Qin)
+{
+    constexpr int Q = AxisSet<D>::Q;
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= a.count) return;
+    const int64_t cell = a.c0 + t;
+    double q[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) q[k] = Qin[k * a.qstride + t];
+    const double rho = q[0];
+    const double u[3] = {q[1] / rho, q[2] / rho, q[3] / rho};
+    const double B[3] = {q[5], q[6], q[7]};
+    const double B2 = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
+    const double u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    const double uB = u[0] * B[0] + u[1] * B[1] + u[2] * B[2];
+    const double p = (a.gamma - 1.0) * (q[4] - 0.5 * rho * u2 - 0.5 * B2);
+    const double pt = p + 0.5 * B2;
+    if (!(rho > 0.0) || !(p > 0.0)) atomicOr(a.flags, kFlagNonPhysical);
+    const double vsig = sqrt(u2) + sqrt(fmax((a.gamma * p + B2) / rho, 0.0));
+    if (!(vsig < sqrt(AxisSet<D>::cs2))) atomicOr(a.flags, kFlagUnstable);
+    S *pop = static_cast<S *>(a.pop);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        double phi[D];
+#pragma unroll
+        for (int ax = 0; ax < D; ++ax) {
+            if (k == 0) phi[ax] = q[1 + ax];
+            else if (k <= 3) phi[ax] = rho * u[ax] * u[k - 1] - B[ax] * B[k - 1] + (ax == k - 1 ? pt : 0.0);
+            else if (k == 4) phi[ax] = (q[4] + pt) * u[ax] - B[ax] * uB;
+            else phi[ax] = (ax == k - 5) ? 0.0 : u[ax] * B[k - 5] - B[ax] * u[k - 5];
+        }
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const double w = i == 0 ? AxisSet<D>::w0 : AxisSet<D>::w1;
+            double cphi = 0.0;
+            if (i > 0) cphi = ((i & 1) ? 1.0 : -1.0) * phi[(i - 1) / 2];
+            double feq = w * (q[k] + cphi / AxisSet<D>::cs2);
+            double v = feq;
+            if (Codec<S>::kDev) v = (feq - w * a.ref[k]) / a.scale[k];
+            Codec<S>::store(pop + (int64_t)(k * Q + i) * a.stride + cell, (decltype(Codec<S>::load(pop)))v);
+        }
+    }
+}
+
+// Logical populations of one cell (parity-aware) decoded to double.
+template <int D, class S> struct ReadArgs {
+    const void *pop;
+    int nx, ny, nz;
+    int64_t stride;
+    int parity;
+    double ref[kMaxLat], scale[kMaxLat];
+};
+
+template <int D, class S>
+__device__ __forceinline__ double logical(const ReadArgs<D, S> &a, int64_t cell, const int64_t *nb, int k,
+                                          int i)
+{
+    constexpr int Q = AxisSet<D>::Q;
+    const S *pop = static_cast<const S *>(a.pop);
+    const int j = a.parity ? opp_axis(i) : i;
+    const int64_t at = a.parity ? nb[opp_axis(i)] : cell;
+    double v = (double)Codec<S>::load(pop + (int64_t)(k * Q + j) * a.stride + at);
+    if (Codec<S>::kDev) v = v * a.scale[k] + (i == 0 ? AxisSet<D>::w0 : AxisSet<D>::w1) * a.ref[k];
+    return v;
+}
+
+template <int D>
+__device__ __forceinline__ void cell_xyz(int64_t cell, int nx, int ny, int &x, int &y, int &z)
+{
+    x = (int)(cell % nx);
+    const int64_t r = cell / nx;
+    y = (int)(r % ny);
+    z = (int)(r / ny);
+}
+
+template <int D, class S>
+__global__ void k_ideal_moments(const ReadArgs<D, S> a, int64_t c0, int64_t count, int64_t ostride,
+                                double *__restrict__ out)
+{
+    constexpr int Q = AxisSet<D>::Q;
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= count) return;
+    const int64_t cell = c0 + t;
+    int x, y, z;
+    cell_xyz<D>(cell, a.nx, a.ny, x, y, z);
+    int64_t nb[Q];
+    neighbours<D>(x, y, z, a.nx, a.ny, a.nz, cell, nb);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        double s = 0.0;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) s += logical<D, S>(a, cell, nb, k, i);
+        out[k * ostride + t] = s;
+    }
+}
+
+template <int D, class S>
+__global__ void k_ideal_gather(const ReadArgs<D, S> a, const int64_t *__restrict__ cells, int n,
+                               double *__restrict__ out)
+{
+    constexpr int Q = AxisSet<D>::Q;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const int64_t cell = cells[t];
+    int x, y, z;
+    cell_xyz<D>(cell, a.nx, a.ny, x, y, z);
+    int64_t nb[Q];
+    neighbours<D>(x, y, z, a.nx, a.ny, a.nz, cell, nb);
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+#pragma unroll
+        for (int i = 0; i < Q; ++i) out[(int64_t)t * 8 * Q + k * Q + i] = logical<D, S>(a, cell, nb, k, i);
+}
+
+// Domain sums of Q_k: each thread accumulates its cells in double, warps and
+// the CTA reduce with shuffles and shared memory, one partial per CTA goes to
+// the scratch array; k_finish_sums adds the partials in a fixed order.
+template <int D, class S>
+__global__ void __launch_bounds__(kReduceThreads) k_ideal_partials(const ReadArgs<D, S> a, int64_t ncell,
+                                                                   double *__restrict__ partials)
+{
+    constexpr int Q = AxisSet<D>::Q;
+    double acc[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) acc[k] = 0.0;
+    for (int64_t cell = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; cell < ncell;
+         cell += (int64_t)gridDim.x * blockDim.x) {
+        int x, y, z;
+        cell_xyz<D>(cell, a.nx, a.ny, x, y, z);
+        int64_t nb[Q];
+        neighbours<D>(x, y, z, a.nx, a.ny, a.nz, cell, nb);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            double s = 0.0;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) s += logical<D, S>(a, cell, nb, k, i);
+            acc[k] += s;
+        }
+    }
+    __shared__ double red[kReduceThreads / 32][8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        double v = acc[k];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+        if (lane == 0) red[warp][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 8) {
+        double v = 0.0;
+        for (int w = 0; w < kReduceThreads / 32; ++w) v += red[w][threadIdx.x];
+        partials[(int64_t)blockIdx.x * 8 + threadIdx.x] = v;
+    }
+}
+
+__global__ void k_finish_sums(const double *__restrict__ partials, int nblocks, int nvar,
+                              double *__restrict__ sums)
+{
+    __shared__ double red[256];
+    for (int k = 0; k < nvar; ++k) {
+        double v = 0.0;
+        for (int b = threadIdx.x; b < nblocks; b += blockDim.x) v += partials[(int64_t)b * 8 + k];
+        red[threadIdx.x] = v;
+        __syncthreads();
+        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+            if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) sums[k] = red[0];
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+
+template <class C> IdealArgs<C> make_step_args(vlbm_ctx *c)
+{
+    const Domain &d = c->dom[0];
+    IdealArgs<C> a{};
+    a.pop = c->pop;
+    a.nx = d.nx;
+    a.ny = d.ny;
+    a.nz = d.nz;
+    a.stride = d.stride;
+    a.gm1 = C(d.gamma - 1.0);
+    const double w0 = c->dim == 2 ? AxisSet<2>::w0 : AxisSet<3>::w0;
+    const double w1 = c->dim == 2 ? AxisSet<2>::w1 : AxisSet<3>::w1;
+    for (int k = 0; k < kMaxLat; ++k) {
+        a.omega[k] = C(1.0 / d.tau[k]);
+        a.src0[k] = C(w0 * d.source[k]);
+        a.src1[k] = C(w1 * d.source[k]);
+        a.ref0[k] = C(w0 * d.q_ref[k]);
+        a.ref1[k] = C(w1 * d.q_ref[k]);
+        a.scale[k] = C(d.q_scale[k]);
+        a.inv_scale[k] = C(1.0 / d.q_scale[k]);
+    }
+    a.flags = c->d_flags;
+    return a;
+}
+
+template <int D, class S> ReadArgs<D, S> make_read_args(vlbm_ctx *c, int di)
+{
+    const Domain &d = c->dom[di];
+    ReadArgs<D, S> a{};
+    a.pop = static_cast<const char *>(c->pop) + d.offset * c->elem;
+    a.nx = d.nx;
+    a.ny = d.ny;
+    a.nz = d.nz;
+    a.stride = d.stride;
+    a.parity = (int)(c->step & 1);
+    for (int k = 0; k < kMaxLat; ++k) {
+        a.ref[k] = d.q_ref[k];
+        a.scale[k] = d.q_scale[k];
+    }
+    return a;
+}
+
+template <int D, class S, class C> vlbm_status step_t(vlbm_ctx *c, int parity)
+{
+    const Domain &d = c->dom[0];
+    const IdealArgs<C> a = make_step_args<C>(c);
+    const dim3 grid((unsigned)((d.nx + kBlockX - 1) / kBlockX), (unsigned)d.ny, (unsigned)d.nz);
+    if (parity)
+        k_ideal_step<D, S, C, true><<<grid, kBlockX, 0, c->stream>>>(a);
+    else
+        k_ideal_step<D, S, C, false><<<grid, kBlockX, 0, c->stream>>>(a);
+    c->launches++;
+    return cuda_check(c, cudaGetLastError(), "ideal step launch");
+}
+
+template <int D, class S> vlbm_status init_t(vlbm_ctx *c, int di, const double *Q, int64_t c0, int64_t count,
+                                             int64_t qstride)
+{
+    const Domain &d = c->dom[di];
+    InitArgs<D, S> a{};
+    a.pop = static_cast<char *>(c->pop) + d.offset * c->elem;
+    a.stride = d.stride;
+    a.c0 = c0;
+    a.count = count;
+    a.qstride = qstride;
+    a.gamma = d.gamma;
+    for (int k = 0; k < kMaxLat; ++k) {
+        a.ref[k] = d.q_ref[k];
+        a.scale[k] = d.q_scale[k];
+    }
+    a.flags = c->d_flags;
+    const int threads = 256;
+    k_ideal_init<D, S><<<(unsigned)((count + threads - 1) / threads), threads, 0, c->stream>>>(a, Q);
+    c->launches++;
+    return cuda_check(c, cudaGetLastError(), "ideal init launch");
+}
+
+template <int D, class S> vlbm_status moments_t(vlbm_ctx *c, int di, double *out, int64_t c0, int64_t count,
+                                                int64_t ostride)
+{
+    const int threads = 256;
+    k_ideal_moments<D, S><<<(unsigned)((count + threads - 1) / threads), threads, 0, c->stream>>>(
+        make_read_args<D, S>(c, di), c0, count, ostride, out);
+    c->launches++;
+    return cuda_check(c, cudaGetLastError(), "ideal moments launch");
+}
+
+template <int D, class S> vlbm_status gather_t(vlbm_ctx *c, int di, const int64_t *cells, int n, double *out)
+{
+    const int threads = 128;
+    k_ideal_gather<D, S><<<(unsigned)((n + threads - 1) / threads), threads, 0, c->stream>>>(
+        make_read_args<D, S>(c, di), cells, n, out);
+    c->launches++;
+    return cuda_check(c, cudaGetLastError(), "ideal gather launch");
+}
+
+template <int D, class S> vlbm_status sums_t(vlbm_ctx *c, int di, double *sums)
+{
+    k_ideal_partials<D, S><<<kReduceBlocks, kReduceThreads, 0, c->stream>>>(make_read_args<D, S>(c, di),
+                                                                             c->dom[di].ncell, c->d_partials);
+    c->launches++;
+    vlbm_status s = cuda_check(c, cudaGetLastError(), "ideal partial sums launch");
+    if (s != VLBM_OK) return s;
+    return finish_sums(c, 8, sums);
+}
+
+// dispatch on (dim, storage)
+template <template <int, class> class F, class... A> vlbm_status dispatch(vlbm_ctx *c, A... args)
+{
+    const int D = c->dim;
+    switch (c->storage) {
+    case VLBM_F64: return D == 2 ? F<2, double>::run(c, args...) : F<3, double>::run(c, args...);
+    case VLBM_F32: return D == 2 ? F<2, float>::run(c, args...) : F<3, float>::run(c, args...);
+    case VLBM_F16_DEV: return D == 2 ? F<2, __half>::run(c, args...) : F<3, __half>::run(c, args...);
+    case VLBM_BF16_DEV:
+        return D == 2 ? F<2, __nv_bfloat16>::run(c, args...) : F<3, __nv_bfloat16>::run(c, args...);
+    }
+    return fail(c, VLBM_ERR_UNSUPPORTED, "unknown storage");
+}
+
+template <int D, class S> struct StepF {
+    static vlbm_status run(vlbm_ctx *c, int parity)
+    {
+        if constexpr (std::is_same<S, double>::value) return step_t<D, S, double>(c, parity);
+        else return step_t<D, S, float>(c, parity);
+    }
+};
+template <int D, class S> struct InitF {
+    static vlbm_status run(vlbm_ctx *c, int di, const double *Q, int64_t c0, int64_t n, int64_t qs)
+    {
+        return init_t<D, S>(c, di, Q, c0, n, qs);
+    }
+};
+template <int D, class S> struct MomF {
+    static vlbm_status run(vlbm_ctx *c, int di, double *out, int64_t c0, int64_t n, int64_t os)
+    {
+        return moments_t<D, S>(c, di, out, c0, n, os);
+    }
+};
+template <int D, class S> struct GatherF {
+    static vlbm_status run(vlbm_ctx *c, int di, const int64_t *cells, int n, double *out)
+    {
+        return gather_t<D, S>(c, di, cells, n, out);
+    }
+};
+template <int D, class S> struct SumsF {
+    static vlbm_status run(vlbm_ctx *c, int di, double *sums) { return sums_t<D, S>(c, di, sums); }
+};
+
+}  // namespace
+
+vlbm_status finish_sums(vlbm_ctx *c, int nvar, double *sums_dev)
+{
+    k_finish_sums<<<1, 256, 0, c->stream>>>(c->d_partials, kReduceBlocks, nvar, sums_dev);
+    c->launches++;
+    return cuda_check(c, cudaGetLastError(), "finish sums launch");
+}
+
+vlbm_status ideal_step(vlbm_ctx *c, int parity) { return dispatch<StepF>(c, parity); }
+
+vlbm_status ideal_init_range(vlbm_ctx *c, int d, const double *Q, int64_t c0, int64_t n, int64_t qstride)
+{
+    return dispatch<InitF>(c, d, Q, c0, n, qstride);
+}
+
+vlbm_status ideal_moments_range(vlbm_ctx *c, int d, double *out, int64_t c0, int64_t n, int64_t ostride)
+{
+    return dispatch<MomF>(c, d, out, c0, n, ostride);
+}
+
+vlbm_status ideal_init(vlbm_ctx *c, int d, const double *Q_dev)
+{
+    const int64_t N = c->dom[d].ncell;
+    return ideal_init_range(c, d, Q_dev, 0, N, N);
+}
+
+vlbm_status ideal_moments(vlbm_ctx *c, int d, double *Q_dev)
+{
+    const int64_t N = c->dom[d].ncell;
+    return ideal_moments_range(c, d, Q_dev, 0, N, N);
+}
+
+vlbm_status ideal_gather(vlbm_ctx *c, int d, const int64_t *cells_dev, int n, double *out_dev)
+{
+    return dispatch<GatherF>(c, d, cells_dev, n, out_dev);
+}
+
+vlbm_status ideal_sums(vlbm_ctx *c, int d, double *sums_dev) { return dispatch<SumsF>(c, d, sums_dev); }
+
+}  // namespace vlbm

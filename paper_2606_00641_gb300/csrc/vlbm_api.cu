@@ -1,0 +1,677 @@
+// vlbm_api.cu -- the C ABI declared in include/vlbm.h.
+//
+// Host responsibilities only: validation, device memory, the stream, the
+// step loop (kernels captured once into CUDA graphs of kGraphLen steps per
+// AA parity and replayed), health-flag read-back, staging of host fields in
+// bounded chunks, checkpoints.  Every arithmetic step of the method runs in
+// the kernels of k_ideal.cu, k_resistive.cu and k_batch.cu.
+#include <algorithm>
+#include <cstring>
+
+#include "vlbm_internal.cuh"
+
+using namespace vlbm;
+
+namespace {
+
+constexpr int kGraphLen = 32;                  // steps per captured graph
+constexpr int64_t kStageCells = int64_t(1) << 22;  // cells per host-staging chunk
+thread_local std::string g_err;                // errors raised before a ctx exists
+
+size_t elem_size(int storage)
+{
+    switch (storage) {
+    case VLBM_F64: return 8;
+    case VLBM_F32: return 4;
+    case VLBM_F16_DEV:
+    case VLBM_BF16_DEV: return 2;
+    }
+    return 0;
+}
+
+int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+void *dev_alloc(vlbm_ctx *c, size_t bytes)
+{
+    void *p = nullptr;
+    if (bytes == 0) bytes = 256;
+    if (c->params.alloc) {
+        p = c->params.alloc(bytes, (void *)c->stream, c->params.alloc_user);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (p) c->owned.emplace_back(p, bytes);
+    return p;
+}
+
+void dev_free_all(vlbm_ctx *c)
+{
+    for (auto &pr : c->owned) {
+        if (c->params.dealloc)
+            c->params.dealloc(pr.first, pr.second, (void *)c->stream, c->params.alloc_user);
+        else if (!c->params.alloc)
+            cudaFree(pr.first);
+    }
+    c->owned.clear();
+}
+
+vlbm_status validate(const vlbm_params *p, bool batch_member)
+{
+    if (!p) return VLBM_ERR_ARG;
+    if (p->model != VLBM_IDEAL && p->model != VLBM_RESISTIVE) {
+        g_err = "model must be VLBM_IDEAL or VLBM_RESISTIVE";
+        return VLBM_ERR_ARG;
+    }
+    if (p->dim != 2 && p->dim != 3) {
+        g_err = "dim must be 2 or 3";
+        return VLBM_ERR_ARG;
+    }
+    if (p->nx < 1 || p->ny < 1 || p->nz < 1 || (p->dim == 2 && p->nz != 1) || p->ny > 65535 ||
+        p->nz > 65535) {
+        g_err = "bad grid size (nx, ny, nz >= 1; ny, nz <= 65535; nz = 1 in 2-D)";
+        return VLBM_ERR_ARG;
+    }
+    if (elem_size(p->storage) == 0) {
+        g_err = "unknown storage";
+        return VLBM_ERR_ARG;
+    }
+    const int nt = p->model == VLBM_IDEAL ? 8 : 4;
+    for (int k = 0; k < nt; ++k)
+        if (!(p->tau[k] > 0.5) || !(p->tau[k] < 1e6)) {
+            g_err = "tau must be > 1/2 on every lattice";
+            return VLBM_ERR_UNSTABLE;
+        }
+    if (p->model == VLBM_IDEAL) {
+        if (!(p->gamma > 1.0)) {
+            g_err = "gamma must be > 1";
+            return VLBM_ERR_ARG;
+        }
+        if (p->storage == VLBM_F16_DEV || p->storage == VLBM_BF16_DEV)
+            for (int k = 0; k < 8; ++k)
+                if (p->q_scale[k] < 0.0 || !(p->q_scale[k] < 1e300)) {
+                    g_err = "q_scale must be >= 0 and finite";
+                    return VLBM_ERR_ARG;
+                }
+    } else {
+        if (p->dim != 3) {
+            g_err = "the resistive model is 3-D";
+            return VLBM_ERR_ARG;
+        }
+        if (p->storage != VLBM_F32) {
+            g_err = "the resistive model is built for F32 storage";
+            return VLBM_ERR_UNSUPPORTED;
+        }
+        if (p->walls_y && p->ny < 3) {
+            g_err = "walls need ny >= 3";
+            return VLBM_ERR_ARG;
+        }
+    }
+    if (batch_member && (p->model != VLBM_IDEAL || p->dim != 2 || p->storage != VLBM_F32)) {
+        g_err = "batched domains are 2-D ideal MHD with F32 storage";
+        return VLBM_ERR_UNSUPPORTED;
+    }
+    return VLBM_OK;
+}
+
+Domain make_domain(const vlbm_params *p)
+{
+    Domain d{};
+    d.nx = p->nx;
+    d.ny = p->ny;
+    d.nz = p->nz;
+    d.ncell = (int64_t)p->nx * p->ny * p->nz;
+    d.stride = round_up(d.ncell, 64);
+    d.gamma = p->gamma;
+    for (int k = 0; k < kMaxLat; ++k) {
+        d.tau[k] = p->tau[k] > 0.5 ? p->tau[k] : 1.0;
+        d.source[k] = p->source[k];
+        d.q_ref[k] = p->q_ref[k];
+        d.q_scale[k] = p->q_scale[k] > 0.0 ? p->q_scale[k] : 1.0;
+    }
+    for (int a = 0; a < 3; ++a) {
+        d.force[a] = p->force[a];
+        d.b_wall[a] = p->b_wall[a];
+    }
+    d.walls_y = p->walls_y;
+    return d;
+}
+
+vlbm_status apply_flags(vlbm_ctx *c, unsigned flags)
+{
+    if (flags & kFlagTimeout) {
+        c->sticky = VLBM_ERR_TIMEOUT;
+        c->err = "a bounded device wait expired";
+    } else if (flags & kFlagNonPhysical) {
+        c->sticky = VLBM_ERR_NONPHYSICAL;
+        c->err = "a kernel saw NaN, rho <= 0 or p <= 0";
+    }
+    return c->sticky;
+}
+
+vlbm_status read_flags_sync(vlbm_ctx *c, unsigned *out)
+{
+    vlbm_status s = cuda_check(c, cudaMemcpyAsync(c->h_flags, c->d_flags, sizeof(unsigned),
+                                                  cudaMemcpyDeviceToHost, c->stream),
+                               "flag read-back");
+    if (s != VLBM_OK) return s;
+    s = cuda_check(c, cudaStreamSynchronize(c->stream), "stream synchronise");
+    if (s != VLBM_OK) return s;
+    *out = *c->h_flags;
+    c->flag_pending = false;
+    return VLBM_OK;
+}
+
+void poll_flags(vlbm_ctx *c)
+{
+    if (c->flag_pending && cudaEventQuery(c->flag_event) == cudaSuccess) {
+        c->flag_pending = false;
+        apply_flags(c, *c->h_flags);
+    }
+    cudaGetLastError();  // cudaErrorNotReady from the query is not an error
+}
+
+vlbm_status launch_step(vlbm_ctx *c, int parity)
+{
+    if (c->batched) return batch_step(c, parity, c->tune_choice);
+    if (c->model == VLBM_RESISTIVE) return resistive_step(c, parity);
+    return ideal_step(c, parity);
+}
+
+vlbm_status init_range(vlbm_ctx *c, int d, const double *Q, int64_t c0, int64_t n, int64_t qs)
+{
+    if (c->model == VLBM_RESISTIVE) return resistive_init_range(c, d, Q, c0, n, qs);
+    return ideal_init_range(c, d, Q, c0, n, qs);
+}
+
+vlbm_status moments_range(vlbm_ctx *c, int d, double *out, int64_t c0, int64_t n, int64_t os)
+{
+    if (c->model == VLBM_RESISTIVE) return resistive_moments_range(c, d, out, c0, n, os);
+    return ideal_moments_range(c, d, out, c0, n, os);
+}
+
+vlbm_status ensure_stage(vlbm_ctx *c, size_t bytes)
+{
+    if (c->d_q_bytes >= bytes) return VLBM_OK;
+    // staging grows monotonically; the old block stays owned until destroy
+    void *p = dev_alloc(c, bytes);
+    if (!p) return fail(c, VLBM_ERR_OOM, "staging allocation failed");
+    c->d_q = static_cast<double *>(p);
+    c->d_q_bytes = bytes;
+    return VLBM_OK;
+}
+
+void drop_graphs(vlbm_ctx *c)
+{
+    for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second);
+    c->graphs.clear();
+}
+
+cudaGraphExec_t get_graph(vlbm_ctx *c, int parity, int len)
+{
+    const int key = parity * 1024 + len;
+    auto it = c->graphs.find(key);
+    if (it != c->graphs.end()) return it->second;
+    if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    const int64_t before = c->launches;
+    bool ok = true;
+    for (int s = 0; s < len && ok; ++s) ok = launch_step(c, (parity + s) & 1) == VLBM_OK;
+    c->launches = before;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    if (!ok || e != cudaSuccess || !g) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return nullptr;
+    }
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    c->graphs[key] = exec;
+    return exec;
+}
+
+vlbm_status create_common(const vlbm_params *p, int count, vlbm_ctx **out)
+{
+    if (!out || !p || count < 1) return VLBM_ERR_ARG;
+    *out = nullptr;
+    for (int d = 0; d < count; ++d) {
+        vlbm_status s = validate(&p[d], count > 1);
+        if (s != VLBM_OK) return s;
+    }
+    vlbm_ctx *c = new vlbm_ctx();
+    c->params = p[0];
+    c->model = p[0].model;
+    c->dim = p[0].dim;
+    c->storage = p[0].storage;
+    c->elem = elem_size(c->storage);
+    c->batched = count > 1;
+    if (c->model == VLBM_IDEAL) {
+        c->q = c->dim == 2 ? 5 : 7;
+        c->nlat = 8;
+        c->nvar = 8;
+        c->nslot = 8 * c->q;
+    } else {
+        c->q = 19;
+        c->nlat = 4;
+        c->nvar = 7;
+        c->nslot = 19 + 3 * 7;
+    }
+    int64_t total = 0;
+    for (int d = 0; d < count; ++d) {
+        Domain dm = make_domain(&p[d]);
+        dm.offset = total;
+        total += (int64_t)c->nslot * dm.stride;
+        c->dom.push_back(dm);
+    }
+    vlbm_status s = VLBM_OK;
+    if (p[0].stream) {
+        c->stream = static_cast<cudaStream_t>(p[0].stream);
+    } else {
+        s = cuda_check(c, cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking), "stream create");
+        c->own_stream = s == VLBM_OK;
+    }
+    if (s == VLBM_OK) s = cuda_check(c, cudaEventCreateWithFlags(&c->flag_event, cudaEventDisableTiming),
+                                     "event create");
+    if (s == VLBM_OK) s = cuda_check(c, cudaMallocHost(&c->h_flags, 64), "pinned flag word");
+    if (s == VLBM_OK) {
+        c->pop_bytes = (size_t)total * c->elem;
+        c->pop = dev_alloc(c, c->pop_bytes);
+        void *status = dev_alloc(c, 256 + (size_t)kReduceBlocks * 8 * sizeof(double) + 8 * sizeof(double));
+        if (!c->pop || !status) {
+            s = fail(c, VLBM_ERR_OOM, "device allocation failed");
+        } else {
+            c->d_flags = static_cast<unsigned *>(status);
+            c->d_sums = reinterpret_cast<double *>(static_cast<char *>(status) + 128);
+            c->d_partials = reinterpret_cast<double *>(static_cast<char *>(status) + 256);
+            s = cuda_check(c, cudaMemsetAsync(c->d_flags, 0, 128, c->stream), "flag clear");
+        }
+    }
+    if (s == VLBM_OK && c->batched) s = batch_prepare(c);
+    if (s == VLBM_OK) s = cuda_check(c, cudaStreamSynchronize(c->stream), "create synchronise");
+    if (s != VLBM_OK) {
+        g_err = c->err;
+        vlbm_destroy(c);
+        return s;
+    }
+    *out = c;
+    return VLBM_OK;
+}
+
+}  // namespace
+
+namespace vlbm {
+
+vlbm_status fail(vlbm_ctx *c, vlbm_status s, const std::string &msg)
+{
+    if (c) c->err = msg;
+    else g_err = msg;
+    return s;
+}
+
+vlbm_status cuda_check(vlbm_ctx *c, cudaError_t e, const char *what)
+{
+    if (e == cudaSuccess) return VLBM_OK;
+    return fail(c, e == cudaErrorMemoryAllocation ? VLBM_ERR_OOM : VLBM_ERR_CUDA,
+                std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+}  // namespace vlbm
+
+extern "C" {
+
+void vlbm_default_params(vlbm_params *p)
+{
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->model = VLBM_IDEAL;
+    p->dim = 3;
+    p->nx = p->ny = p->nz = 64;
+    p->storage = VLBM_F32;
+    p->gamma = 5.0 / 3.0;
+    for (int k = 0; k < 8; ++k) {
+        p->tau[k] = 0.51;
+        p->q_scale[k] = 1.0;
+    }
+}
+
+vlbm_status vlbm_create(const vlbm_params *p, vlbm_ctx **out) { return create_common(p, 1, out); }
+
+vlbm_status vlbm_create_batch(const vlbm_params *p, int count, vlbm_ctx **out)
+{
+    if (count < 1) return VLBM_ERR_ARG;
+    return create_common(p, count, out);
+}
+
+static vlbm_status finish_init(vlbm_ctx *c)
+{
+    unsigned flags = 0;
+    vlbm_status s = read_flags_sync(c, &flags);
+    if (s != VLBM_OK) return s;
+    if (flags & kFlagUnstable) {
+        cudaMemsetAsync(c->d_flags, 0, sizeof(unsigned), c->stream);
+        return fail(c, VLBM_ERR_UNSTABLE, "max(|u| + c_f) >= cs: the scheme's diffusion would be negative");
+    }
+    if (flags & kFlagNonPhysical) {
+        cudaMemsetAsync(c->d_flags, 0, sizeof(unsigned), c->stream);
+        return fail(c, VLBM_ERR_NONPHYSICAL, "initial fields have rho <= 0 or p <= 0");
+    }
+    c->sticky = VLBM_OK;
+    return VLBM_OK;
+}
+
+static vlbm_status begin_init(vlbm_ctx *c, int domain)
+{
+    if (domain < 0 || domain >= (int)c->dom.size()) return fail(c, VLBM_ERR_ARG, "bad domain index");
+    if (c->batched && (c->step & 1)) return fail(c, VLBM_ERR_STATE, "batched init needs an even step count");
+    if (c->flag_pending) cudaEventSynchronize(c->flag_event);
+    c->flag_pending = false;
+    c->step = 0;
+    c->steps_since_check = 0;
+    return cuda_check(c, cudaMemsetAsync(c->d_flags, 0, sizeof(unsigned), c->stream), "flag clear");
+}
+
+vlbm_status vlbm_init_fields(vlbm_ctx *c, int domain, const double *Q_host)
+{
+    if (!c || !Q_host) return VLBM_ERR_ARG;
+    vlbm_status s = begin_init(c, domain);
+    if (s != VLBM_OK) return s;
+    const int64_t N = c->dom[domain].ncell;
+    const int64_t chunk = std::min<int64_t>(N, kStageCells);
+    s = ensure_stage(c, (size_t)c->nvar * chunk * sizeof(double));
+    for (int64_t c0 = 0; s == VLBM_OK && c0 < N; c0 += chunk) {
+        const int64_t n = std::min<int64_t>(chunk, N - c0);
+        for (int v = 0; v < c->nvar && s == VLBM_OK; ++v)
+            s = cuda_check(c, cudaMemcpyAsync(c->d_q + v * chunk, Q_host + v * N + c0, n * sizeof(double),
+                                              cudaMemcpyHostToDevice, c->stream),
+                           "field upload");
+        if (s == VLBM_OK) s = init_range(c, domain, c->d_q, c0, n, chunk);
+    }
+    if (s != VLBM_OK) return s;
+    return finish_init(c);
+}
+
+vlbm_status vlbm_init_fields_device(vlbm_ctx *c, int domain, const double *Q_dev)
+{
+    if (!c || !Q_dev) return VLBM_ERR_ARG;
+    vlbm_status s = begin_init(c, domain);
+    if (s != VLBM_OK) return s;
+    const int64_t N = c->dom[domain].ncell;
+    s = init_range(c, domain, Q_dev, 0, N, N);
+    if (s != VLBM_OK) return s;
+    return finish_init(c);
+}
+
+vlbm_status vlbm_step(vlbm_ctx *c, int n)
+{
+    if (!c || n < 0) return VLBM_ERR_ARG;
+    poll_flags(c);
+    if (c->sticky != VLBM_OK) return c->sticky;
+    const bool graphs = c->stream != nullptr && c->stream != cudaStreamLegacy &&
+                        c->stream != cudaStreamPerThread;
+    int left = n;
+    while (left > 0) {
+        if (graphs && left >= kGraphLen) {
+            cudaGraphExec_t g = get_graph(c, (int)(c->step & 1), kGraphLen);
+            if (g) {
+                vlbm_status s = cuda_check(c, cudaGraphLaunch(g, c->stream), "graph launch");
+                if (s != VLBM_OK) return s;
+                c->step += kGraphLen;
+                c->launches += kGraphLen;
+                left -= kGraphLen;
+                continue;
+            }
+        }
+        vlbm_status s = launch_step(c, (int)(c->step & 1));
+        if (s != VLBM_OK) return s;
+        c->step += 1;
+        left -= 1;
+    }
+    c->steps_since_check += n;
+    const int every = c->params.check_every;
+    if (every > 0 && c->steps_since_check >= every && !c->flag_pending) {
+        c->steps_since_check = 0;
+        if (cudaMemcpyAsync(c->h_flags, c->d_flags, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream) ==
+                cudaSuccess &&
+            cudaEventRecord(c->flag_event, c->stream) == cudaSuccess)
+            c->flag_pending = true;
+        cudaGetLastError();
+    }
+    return c->sticky;
+}
+
+vlbm_status vlbm_sync(vlbm_ctx *c)
+{
+    if (!c) return VLBM_ERR_ARG;
+    unsigned flags = 0;
+    vlbm_status s = read_flags_sync(c, &flags);
+    if (s != VLBM_OK) return s;
+    return apply_flags(c, flags);
+}
+
+vlbm_status vlbm_moments(vlbm_ctx *c, int domain, double *Q_host)
+{
+    if (!c || !Q_host) return VLBM_ERR_ARG;
+    if (domain < 0 || domain >= (int)c->dom.size()) return fail(c, VLBM_ERR_ARG, "bad domain index");
+    const int64_t N = c->dom[domain].ncell;
+    const int64_t chunk = std::min<int64_t>(N, kStageCells);
+    vlbm_status s = ensure_stage(c, (size_t)c->nvar * chunk * sizeof(double));
+    for (int64_t c0 = 0; s == VLBM_OK && c0 < N; c0 += chunk) {
+        const int64_t n = std::min<int64_t>(chunk, N - c0);
+        s = moments_range(c, domain, c->d_q, c0, n, chunk);
+        for (int v = 0; v < c->nvar && s == VLBM_OK; ++v)
+            s = cuda_check(c, cudaMemcpyAsync(Q_host + v * N + c0, c->d_q + v * chunk, n * sizeof(double),
+                                              cudaMemcpyDeviceToHost, c->stream),
+                           "field download");
+    }
+    if (s != VLBM_OK) return s;
+    return cuda_check(c, cudaStreamSynchronize(c->stream), "moments synchronise");
+}
+
+vlbm_status vlbm_moments_device(vlbm_ctx *c, int domain, double *Q_dev)
+{
+    if (!c || !Q_dev) return VLBM_ERR_ARG;
+    if (domain < 0 || domain >= (int)c->dom.size()) return fail(c, VLBM_ERR_ARG, "bad domain index");
+    const int64_t N = c->dom[domain].ncell;
+    return moments_range(c, domain, Q_dev, 0, N, N);
+}
+
+vlbm_status vlbm_gather_populations(vlbm_ctx *c, int domain, const int64_t *cells, int ncells, double *f_host)
+{
+    if (!c || !cells || !f_host || ncells < 1) return VLBM_ERR_ARG;
+    if (domain < 0 || domain >= (int)c->dom.size()) return fail(c, VLBM_ERR_ARG, "bad domain index");
+    const int64_t N = c->dom[domain].ncell;
+    for (int t = 0; t < ncells; ++t)
+        if (cells[t] < 0 || cells[t] >= N) return fail(c, VLBM_ERR_ARG, "cell index out of range");
+    const size_t need = (size_t)ncells * (1 + c->nslot) * sizeof(double);
+    vlbm_status s = ensure_stage(c, need);
+    if (s != VLBM_OK) return s;
+    int64_t *d_cells = reinterpret_cast<int64_t *>(c->d_q);
+    double *d_out = c->d_q + ncells;
+    s = cuda_check(c, cudaMemcpyAsync(d_cells, cells, ncells * sizeof(int64_t), cudaMemcpyHostToDevice, c->stream),
+                   "cell upload");
+    if (s == VLBM_OK)
+        s = c->model == VLBM_RESISTIVE ? resistive_gather(c, domain, d_cells, ncells, d_out)
+                                       : ideal_gather(c, domain, d_cells, ncells, d_out);
+    if (s == VLBM_OK)
+        s = cuda_check(c, cudaMemcpyAsync(f_host, d_out, (size_t)ncells * c->nslot * sizeof(double),
+                                          cudaMemcpyDeviceToHost, c->stream),
+                       "population download");
+    if (s != VLBM_OK) return s;
+    return cuda_check(c, cudaStreamSynchronize(c->stream), "gather synchronise");
+}
+
+vlbm_status vlbm_conservation(vlbm_ctx *c, int domain, double *sums)
+{
+    if (!c || !sums) return VLBM_ERR_ARG;
+    if (domain < 0 || domain >= (int)c->dom.size()) return fail(c, VLBM_ERR_ARG, "bad domain index");
+    vlbm_status s = c->model == VLBM_RESISTIVE ? resistive_sums(c, domain, c->d_sums)
+                                               : ideal_sums(c, domain, c->d_sums);
+    if (s == VLBM_OK)
+        s = cuda_check(c, cudaMemcpyAsync(sums, c->d_sums, c->nvar * sizeof(double), cudaMemcpyDeviceToHost,
+                                          c->stream),
+                       "sums download");
+    if (s != VLBM_OK) return s;
+    unsigned flags = 0;
+    s = read_flags_sync(c, &flags);
+    if (s != VLBM_OK) return s;
+    apply_flags(c, flags);
+    return VLBM_OK;
+}
+
+struct SaveHeader {
+    uint64_t magic;
+    int32_t model, dim, storage, ndomains;
+    int64_t step;
+    uint64_t pop_bytes;
+};
+static const uint64_t kMagic = 0x564c424d53415645ull;  // "VLBMSAVE"
+
+vlbm_status vlbm_save(vlbm_ctx *c, void *buf, size_t *bytes)
+{
+    if (!c || !bytes) return VLBM_ERR_ARG;
+    const size_t need = sizeof(SaveHeader) + c->pop_bytes;
+    if (!buf) {
+        *bytes = need;
+        return VLBM_OK;
+    }
+    if (*bytes < need) return fail(c, VLBM_ERR_ARG, "checkpoint buffer too small");
+    SaveHeader h{kMagic, c->model, c->dim, c->storage, (int32_t)c->dom.size(), c->step, c->pop_bytes};
+    std::memcpy(buf, &h, sizeof(h));
+    vlbm_status s = cuda_check(c, cudaMemcpyAsync(static_cast<char *>(buf) + sizeof(h), c->pop, c->pop_bytes,
+                                                  cudaMemcpyDeviceToHost, c->stream),
+                               "checkpoint download");
+    if (s != VLBM_OK) return s;
+    *bytes = need;
+    return cuda_check(c, cudaStreamSynchronize(c->stream), "checkpoint synchronise");
+}
+
+vlbm_status vlbm_load(vlbm_ctx *c, const void *buf, size_t bytes)
+{
+    if (!c || !buf || bytes < sizeof(SaveHeader)) return VLBM_ERR_ARG;
+    SaveHeader h;
+    std::memcpy(&h, buf, sizeof(h));
+    if (h.magic != kMagic || h.model != c->model || h.dim != c->dim || h.storage != c->storage ||
+        h.ndomains != (int32_t)c->dom.size() || h.pop_bytes != c->pop_bytes ||
+        bytes < sizeof(h) + c->pop_bytes)
+        return fail(c, VLBM_ERR_ARG, "checkpoint does not match this context");
+    vlbm_status s = cuda_check(c, cudaMemcpyAsync(c->pop, static_cast<const char *>(buf) + sizeof(h),
+                                                  c->pop_bytes, cudaMemcpyHostToDevice, c->stream),
+                               "checkpoint upload");
+    if (s == VLBM_OK) s = cuda_check(c, cudaMemsetAsync(c->d_flags, 0, sizeof(unsigned), c->stream), "flag clear");
+    if (s == VLBM_OK) s = cuda_check(c, cudaStreamSynchronize(c->stream), "load synchronise");
+    if (s != VLBM_OK) return s;
+    c->step = h.step;
+    c->sticky = VLBM_OK;
+    c->flag_pending = false;
+    return VLBM_OK;
+}
+
+vlbm_status vlbm_autotune(vlbm_ctx *c, int steps, int *choice)
+{
+    if (!c || !choice || steps < 0) return VLBM_ERR_ARG;
+    *choice = 0;
+    if (!c->batched) return VLBM_OK;
+    // save state, time every choice, restore
+    size_t bytes = c->pop_bytes;
+    std::vector<char> keep(bytes);
+    vlbm_status s = cuda_check(c, cudaMemcpyAsync(keep.data(), c->pop, bytes, cudaMemcpyDeviceToHost, c->stream),
+                               "autotune save");
+    if (s == VLBM_OK) s = cuda_check(c, cudaStreamSynchronize(c->stream), "autotune synchronise");
+    if (s != VLBM_OK) return s;
+    const int64_t step0 = c->step;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    int best_choice = 0;
+    const int nchoice = batch_num_choices();
+    for (int ch = 0; ch < nchoice && s == VLBM_OK; ++ch) {
+        for (int w = 0; w < 2 && s == VLBM_OK; ++w) s = batch_step(c, (int)((step0 + w) & 1), ch);
+        cudaEventRecord(e0, c->stream);
+        for (int t = 0; t < steps && s == VLBM_OK; ++t) s = batch_step(c, (int)((step0 + 2 + t) & 1), ch);
+        cudaEventRecord(e1, c->stream);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+            best = ms;
+            best_choice = ch;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s == VLBM_OK)
+        s = cuda_check(c, cudaMemcpyAsync(c->pop, keep.data(), bytes, cudaMemcpyHostToDevice, c->stream),
+                       "autotune restore");
+    if (s == VLBM_OK) s = cuda_check(c, cudaStreamSynchronize(c->stream), "autotune synchronise");
+    if (s != VLBM_OK) return s;
+    c->step = step0;
+    if (best_choice != c->tune_choice) drop_graphs(c);
+    c->tune_choice = best_choice;
+    *choice = best_choice;
+    return VLBM_OK;
+}
+
+int vlbm_tile_shapes(const vlbm_ctx *c) { return (c && c->batched) ? batch_num_choices() : 0; }
+
+vlbm_status vlbm_set_tile_shape(vlbm_ctx *c, int shape)
+{
+    if (!c) return VLBM_ERR_ARG;
+    if (!c->batched || shape < 0 || shape >= batch_num_choices())
+        return fail(c, VLBM_ERR_ARG, "no such tile shape");
+    if (shape != c->tune_choice) drop_graphs(c);
+    c->tune_choice = shape;
+    return VLBM_OK;
+}
+
+int vlbm_nvar(const vlbm_ctx *c) { return c ? c->nvar : 0; }
+int vlbm_slots_per_cell(const vlbm_ctx *c) { return c ? c->nslot : 0; }
+int vlbm_num_domains(const vlbm_ctx *c) { return c ? (int)c->dom.size() : 0; }
+int64_t vlbm_num_cells(const vlbm_ctx *c, int d)
+{
+    return (c && d >= 0 && d < (int)c->dom.size()) ? c->dom[d].ncell : 0;
+}
+int64_t vlbm_step_count(const vlbm_ctx *c) { return c ? c->step : 0; }
+int64_t vlbm_launch_count(const vlbm_ctx *c) { return c ? c->launches : 0; }
+size_t vlbm_population_bytes(const vlbm_ctx *c) { return c ? c->pop_bytes : 0; }
+void *vlbm_stream(const vlbm_ctx *c) { return c ? (void *)c->stream : nullptr; }
+const char *vlbm_last_error(const vlbm_ctx *c) { return c ? c->err.c_str() : g_err.c_str(); }
+
+const char *vlbm_status_string(int s)
+{
+    switch (s) {
+    case VLBM_OK: return "VLBM_OK";
+    case VLBM_ERR_ARG: return "VLBM_ERR_ARG";
+    case VLBM_ERR_UNSTABLE: return "VLBM_ERR_UNSTABLE";
+    case VLBM_ERR_OOM: return "VLBM_ERR_OOM";
+    case VLBM_ERR_CUDA: return "VLBM_ERR_CUDA";
+    case VLBM_ERR_NONPHYSICAL: return "VLBM_ERR_NONPHYSICAL";
+    case VLBM_ERR_TIMEOUT: return "VLBM_ERR_TIMEOUT";
+    case VLBM_ERR_STATE: return "VLBM_ERR_STATE";
+    case VLBM_ERR_UNSUPPORTED: return "VLBM_ERR_UNSUPPORTED";
+    }
+    return "unknown status";
+}
+
+void vlbm_destroy(vlbm_ctx *c)
+{
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    drop_graphs(c);
+    dev_free_all(c);
+    if (c->h_flags) cudaFreeHost(c->h_flags);
+    if (c->flag_event) cudaEventDestroy(c->flag_event);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    cudaGetLastError();
+    delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,176 @@
+// vlbm_internal.cuh -- internal types of the GB300 VLBM library (not ABI).
+//
+// Population storage: one in-place buffer per context, structure of arrays.
+// Slot (j, cell) of a domain lives at  base + j * stride + cell, where j runs
+// over lattice-major (lattice k, direction i) pairs and stride is the cell
+// count rounded up to a multiple of 64 elements, so that every slot plane
+// starts on a 128-byte boundary for every storage type.
+//
+// AA in-place streaming (two kernels that alternate):
+//   parity 0 ("even") step at cell x:  read slot (i, x), write the
+//       post-collision value of direction i to slot (opp(i), x);
+//   parity 1 ("odd") step at cell x:   read slot (opp(i), x - c_i), write
+//       the post-collision value of direction i to slot (i, x + c_i).
+// The set of slots a cell reads equals the set it writes, so one buffer
+// suffices and no two threads touch the same slot.  The logical
+// (pre-collision) population of the state is slot (i, x) at parity 0 and
+// slot (opp(i), x - c_i) at parity 1.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <map>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "../../include/vlbm.h"
+
+namespace vlbm {
+
+constexpr int kMaxLat = 8;
+constexpr int kBlockX = 128;     // threads per CTA along x for the step kernels
+constexpr int kReduceBlocks = 1216;  // 8 CTAs per SM on 152 SMs
+constexpr int kReduceThreads = 256;
+
+// Status bits written by kernels into the context's device flag word.
+constexpr unsigned kFlagNonPhysical = 1u;  // NaN, rho <= 0 or p <= 0
+constexpr unsigned kFlagUnstable = 2u;     // max(|u| + c_f) >= cs at init
+constexpr unsigned kFlagTimeout = 4u;      // a bounded device wait gave up
+
+// Direction i of the axis-aligned sets: 0 rest, 2a+1 = +e_a, 2a+2 = -e_a.
+__host__ __device__ constexpr int opp_axis(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+
+// Weights of the axis sets: D2Q5 (1/3, 1/6; cs^2 = 1/3), D3Q7 (1/4, 1/8;
+// cs^2 = 1/4).  In both, w_moving / cs^2 = 1/2.
+template <int D> struct AxisSet;
+template <> struct AxisSet<2> {
+    static constexpr int Q = 5;
+    static constexpr double w0 = 1.0 / 3.0, w1 = 1.0 / 6.0, cs2 = 1.0 / 3.0;
+};
+template <> struct AxisSet<3> {
+    static constexpr int Q = 7;
+    static constexpr double w0 = 1.0 / 4.0, w1 = 1.0 / 8.0, cs2 = 1.0 / 4.0;
+};
+
+// Storage codecs: deviation forms store (f - w_i ref_k) / scale_k.
+template <class S> struct Codec;
+template <> struct Codec<double> {
+    static constexpr bool kDev = false;
+    __device__ static __forceinline__ double load(const double *p) { return *p; }
+    __device__ static __forceinline__ void store(double *p, double v) { *p = v; }
+};
+template <> struct Codec<float> {
+    static constexpr bool kDev = false;
+    __device__ static __forceinline__ float load(const float *p) { return *p; }
+    __device__ static __forceinline__ void store(float *p, float v) { *p = v; }
+};
+template <> struct Codec<__half> {
+    static constexpr bool kDev = true;
+    __device__ static __forceinline__ float load(const __half *p) { return __half2float(*p); }
+    __device__ static __forceinline__ void store(__half *p, float v) { *p = __float2half_rn(v); }
+};
+template <> struct Codec<__nv_bfloat16> {
+    static constexpr bool kDev = true;
+    __device__ static __forceinline__ float load(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
+    __device__ static __forceinline__ void store(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
+};
+
+// Per-domain description (host and device copies).
+struct Domain {
+    int nx, ny, nz;
+    int64_t ncell;
+    int64_t stride;        // elements between slot planes
+    int64_t offset;        // element offset of the domain's block in the buffer
+    double gamma;
+    double tau[kMaxLat];
+    double source[kMaxLat];
+    double q_ref[kMaxLat];
+    double q_scale[kMaxLat];
+    double force[3];
+    double b_wall[3];
+    int walls_y;
+};
+
+}  // namespace vlbm
+
+struct vlbm_ctx {
+    vlbm_params params;                 // parameters of domain 0 (copied)
+    int model = 0, dim = 3, q = 7, nlat = 8, nvar = 8;
+    int storage = VLBM_F32;
+    size_t elem = 4;                    // bytes per stored population
+    int nslot = 56;                     // slots per cell (lattices x directions)
+    std::vector<vlbm::Domain> dom;
+    bool batched = false;
+
+    void *pop = nullptr;                // population buffer
+    size_t pop_bytes = 0;
+    unsigned *d_flags = nullptr;        // device status word
+    unsigned *h_flags = nullptr;        // pinned host mirror
+    double *d_partials = nullptr;       // reduction scratch [kReduceBlocks x 8]
+    double *d_sums = nullptr;           // reduction result [8]
+    double *d_q = nullptr;              // staging for host fields (lazily sized)
+    size_t d_q_bytes = 0;
+    double *h_stage = nullptr;          // pinned host staging
+    size_t h_stage_bytes = 0;
+
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaEvent_t flag_event = nullptr;
+    bool flag_pending = false;
+    int64_t steps_since_check = 0;
+
+    int64_t step = 0;                   // completed (enqueued) steps
+    int64_t launches = 0;               // kernels launched by this context
+    vlbm_status sticky = VLBM_OK;
+    std::string err;
+
+    std::map<int, cudaGraphExec_t> graphs;  // key: parity*1024 + length
+
+    // batched form
+    std::vector<void *> tile_tables;    // per tile shape: device (domain, first cell) pairs
+    std::vector<int> tile_counts;       // tiles per table
+    std::vector<int> tile_grid;         // CTAs launched per table
+    int tune_choice = 0;
+    void *d_dom = nullptr;              // device copy of the domain table
+
+    // allocator
+    std::vector<std::pair<void *, size_t>> owned;
+};
+
+namespace vlbm {
+
+// host helpers (vlbm_api.cu)
+vlbm_status fail(vlbm_ctx *c, vlbm_status s, const std::string &msg);
+vlbm_status cuda_check(vlbm_ctx *c, cudaError_t e, const char *what);
+
+// launchers (k_ideal.cu)
+vlbm_status ideal_init(vlbm_ctx *c, int d, const double *Q_dev);
+vlbm_status ideal_init_range(vlbm_ctx *c, int d, const double *Q, int64_t c0, int64_t n, int64_t qstride);
+vlbm_status ideal_moments_range(vlbm_ctx *c, int d, double *out, int64_t c0, int64_t n, int64_t ostride);
+vlbm_status ideal_step(vlbm_ctx *c, int parity);
+vlbm_status ideal_moments(vlbm_ctx *c, int d, double *Q_dev);
+vlbm_status ideal_gather(vlbm_ctx *c, int d, const int64_t *cells_dev, int n, double *out_dev);
+vlbm_status ideal_sums(vlbm_ctx *c, int d, double *sums_dev);
+
+// launchers (k_resistive.cu)
+vlbm_status resistive_init(vlbm_ctx *c, int d, const double *Q_dev);
+vlbm_status resistive_init_range(vlbm_ctx *c, int d, const double *Q, int64_t c0, int64_t n, int64_t qstride);
+vlbm_status resistive_moments_range(vlbm_ctx *c, int d, double *out, int64_t c0, int64_t n, int64_t ostride);
+vlbm_status resistive_step(vlbm_ctx *c, int parity);
+vlbm_status resistive_moments(vlbm_ctx *c, int d, double *Q_dev);
+vlbm_status resistive_gather(vlbm_ctx *c, int d, const int64_t *cells_dev, int n, double *out_dev);
+vlbm_status resistive_sums(vlbm_ctx *c, int d, double *sums_dev);
+
+// launchers (k_batch.cu)
+vlbm_status batch_prepare(vlbm_ctx *c);
+vlbm_status batch_step(vlbm_ctx *c, int parity, int choice);
+int batch_num_choices();
+
+// reduction of per-block partials into sums (k_ideal.cu)
+vlbm_status finish_sums(vlbm_ctx *c, int nvar, double *sums_dev);
+
+}  // namespace vlbm

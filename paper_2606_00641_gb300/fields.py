@@ -49,24 +49,81 @@ def _wavevectors(rng, dim: int, kmax: int, count: int):
     return ks
 
 
-def random_phase(rng, shape, kmax: int, count: int) -> np.ndarray:
+class _Backend:
+    """Array operations for NumPy (host) or torch (device) field building."""
+
+    def __init__(self, device=None):
+        self.device = device
+        if device is None:
+            self.t = None
+        else:
+            import torch
+            self.t = torch
+
+    def coords(self, shape):
+        """1-D coordinate vectors x/n, shaped to broadcast, ordered (x, y, z)."""
+        dim = len(shape)
+        out = []
+        for a in range(dim):
+            n = shape[dim - 1 - a]
+            if self.t is None:
+                v = np.arange(n, dtype=np.float64) / n
+            else:
+                v = self.t.arange(n, dtype=self.t.float64, device=self.device) / n
+            view = [1] * dim
+            view[dim - 1 - a] = n
+            out.append(v.reshape(view))
+        return out
+
+    def zeros(self, shape):
+        if self.t is None:
+            return np.zeros(shape)
+        return self.t.zeros(shape, dtype=self.t.float64, device=self.device)
+
+    def cos(self, a):
+        return np.cos(a) if self.t is None else self.t.cos(a)
+
+    def sqrt(self, a):
+        return np.sqrt(a) if self.t is None else self.t.sqrt(a)
+
+    def roll(self, a, shift, axis):
+        return np.roll(a, shift, axis=axis) if self.t is None else self.t.roll(a, shift, dims=axis)
+
+    def amax(self, a) -> float:
+        return float(np.abs(a).max()) if self.t is None else float(a.abs().max())
+
+    def mean(self, a) -> float:
+        return float(a.mean())
+
+    def stack(self, xs):
+        return np.stack(xs) if self.t is None else self.t.stack(xs)
+
+    def full(self, shape, v):
+        if self.t is None:
+            return np.full(shape, v, dtype=np.float64)
+        return self.t.full(shape, v, dtype=self.t.float64, device=self.device)
+
+
+def random_phase(rng, shape, kmax: int, count: int, backend: _Backend = None):
     """Sum of ``count`` unit cosines with random integer wave vectors and phases."""
+    be = backend or _Backend()
     dim = len(shape)
-    grids = np.meshgrid(*[np.arange(n, dtype=np.float64) / n for n in shape], indexing="ij")
-    # grids are ordered like the array axes: (z,) y, x; wave vectors are (x, y, z)
-    coords = list(reversed(grids))
-    out = np.zeros(shape)
+    coords = be.coords(shape)
+    out = be.zeros(shape)
     for k in _wavevectors(rng, dim, kmax, count):
         phase = rng.uniform(0.0, 2.0 * math.pi)
-        arg = sum(2.0 * math.pi * float(k[a]) * coords[a] for a in range(dim)) + phase
-        out += np.cos(arg)
+        arg = phase
+        for a in range(dim):
+            arg = arg + (2.0 * math.pi * float(k[a])) * coords[a]
+        out = out + be.cos(arg)
     return out
 
 
-def _cdiff(a: np.ndarray, axis_xyz: int) -> np.ndarray:
+def _cdiff(a, axis_xyz: int, backend: _Backend = None):
     """Centred periodic difference along x (0), y (1) or z (2)."""
+    be = backend or _Backend()
     ax = a.ndim - 1 - axis_xyz
-    return 0.5 * (np.roll(a, -1, axis=ax) - np.roll(a, 1, axis=ax))
+    return 0.5 * (be.roll(a, -1, ax) - be.roll(a, 1, ax))
 
 
 def centred_divergence(Bx, By, Bz=None) -> np.ndarray:
@@ -90,7 +147,7 @@ def signal_speed(rho, u, p, B, gamma) -> float:
 
 @dataclass
 class IdealFields:
-    Q: np.ndarray            # [8, (nz,) ny, nx] float64, lattice units
+    Q: object                # [8, (nz,) ny, nx] float64 (numpy, or torch on `device`), lattice units
     gamma: float
     lam: float               # physical velocity per lattice velocity
     mach: float
@@ -103,49 +160,62 @@ class IdealFields:
 def ideal_fields(shape, seed: int, *, gamma: float = 5.0 / 3.0, mach: float = 1.0,
                  beta: float = 10.0 / 3.0, p0: float = 0.6, rho0: float = 1.0,
                  drho: float = 0.1, cfl: float = 0.1, k_rho: int = 3, k_u: int = 2,
-                 k_b: int = 2) -> IdealFields:
+                 k_b: int = 2, device=None) -> IdealFields:
     """Smooth random-phase ideal-MHD state, scaled to lattice units.
 
     2-D ``shape = (ny, nx)``, 3-D ``shape = (nz, ny, nx)``.  The defaults are
-    the 128^2 workload (peak Mach 1, beta 10/3, CFL 0.1, gamma 5/3).
+    the 128^2 workload (peak Mach 1, beta 10/3, CFL 0.1, gamma 5/3).  With
+    ``device`` (a torch device) the same recipe runs on that device and
+    ``Q`` is a torch float64 tensor; the seeded wave vectors and phases are
+    identical, values agree with the host build to rounding.
     """
+    be = _Backend(device)
     shape = tuple(int(n) for n in shape)
     dim = len(shape)
     rng = np.random.default_rng(seed)
-    s = random_phase(rng, shape, k_rho, 4)
-    rho = rho0 * (1.0 + drho * s / np.abs(s).max())
-    u = [random_phase(rng, shape, k_u, 2) for _ in range(3)]
+    s = random_phase(rng, shape, k_rho, 4, be)
+    rho = rho0 * (1.0 + drho * s / be.amax(s))
+    del s
+    u = [random_phase(rng, shape, k_u, 2, be) for _ in range(3)]
     if dim == 2:
-        Az = random_phase(rng, shape, k_b, 3)
-        Bx = _cdiff(Az, 1)
-        By = -_cdiff(Az, 0)
-        Bz = random_phase(rng, shape, k_b, 2)
+        Az = random_phase(rng, shape, k_b, 3, be)
+        B = [_cdiff(Az, 1, be), -_cdiff(Az, 0, be), random_phase(rng, shape, k_b, 2, be)]
+        del Az
     else:
-        A = [random_phase(rng, shape, k_b, 3) for _ in range(3)]
-        Bx = _cdiff(A[2], 1) - _cdiff(A[1], 2)
-        By = _cdiff(A[0], 2) - _cdiff(A[2], 0)
-        Bz = _cdiff(A[1], 0) - _cdiff(A[0], 1)
-    B = np.stack([Bx, By, Bz])
-    cs0 = math.sqrt(gamma * p0 / rho.mean())
-    umag = np.sqrt(sum(c * c for c in u))
-    u = np.stack(u) * (mach * cs0 / umag.max())
+        A = [random_phase(rng, shape, k_b, 3, be) for _ in range(3)]
+        B = [_cdiff(A[2], 1, be) - _cdiff(A[1], 2, be),
+             _cdiff(A[0], 2, be) - _cdiff(A[2], 0, be),
+             _cdiff(A[1], 0, be) - _cdiff(A[0], 1, be)]
+        del A
+    cs0 = math.sqrt(gamma * p0 / be.mean(rho))
+    umag = be.sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2])
+    su = mach * cs0 / be.amax(umag)
+    del umag
+    u = [c * su for c in u]
     if beta > 0:
-        bmag2 = (B * B).sum(0)
-        B = B * math.sqrt((2.0 * p0 / beta) / bmag2.max())
+        bmag2 = B[0] * B[0] + B[1] * B[1] + B[2] * B[2]
+        sb = math.sqrt((2.0 * p0 / beta) / be.amax(bmag2))
+        del bmag2
+        B = [c * sb for c in B]
     else:
-        B = np.zeros_like(B)
-    p = np.full(shape, p0)
-    # lattice scaling from the CFL reading (max |u| + max fast speed)
-    vmax = signal_speed(rho, u, p, B, gamma)
+        B = [c * 0.0 for c in B]
+    # lattice scaling from the CFL reading (max |u| + max fast speed), p uniform
+    u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2]
+    B2 = B[0] * B[0] + B[1] * B[1] + B[2] * B[2]
+    vmax = be.amax(be.sqrt(u2)) + be.amax(be.sqrt((gamma * p0 + B2) / rho))
     lam = vmax / cfl
-    u = u / lam
-    B = B / lam
-    p = p / lam ** 2
-    e = p / (gamma - 1.0) + 0.5 * rho * (u * u).sum(0) + 0.5 * (B * B).sum(0)
-    Q = np.concatenate([rho[None], rho[None] * u, e[None], B]).astype(np.float64)
-    return IdealFields(Q=np.ascontiguousarray(Q), gamma=gamma, lam=lam, mach=mach, beta=beta,
-                       cfl=cfl, seed=seed,
-                       meta={"p0_lattice": p0 / lam ** 2, "vmax_phys": vmax})
+    u = [c / lam for c in u]
+    B = [c / lam for c in B]
+    p = p0 / lam ** 2
+    e = p / (gamma - 1.0) + 0.5 * rho * (u2 / lam ** 2) + 0.5 * (B2 / lam ** 2)
+    del u2, B2
+    Q = be.stack([rho, rho * u[0], rho * u[1], rho * u[2], e, B[0], B[1], B[2]])
+    if be.t is None:
+        Q = np.ascontiguousarray(Q, dtype=np.float64)
+    else:
+        Q = Q.contiguous()
+    return IdealFields(Q=Q, gamma=gamma, lam=lam, mach=mach, beta=beta, cfl=cfl, seed=seed,
+                       meta={"p0_lattice": p, "vmax_phys": vmax})
 
 
 def uniform_ideal_state(shape, rho=1.0, u=(0.0, 0.0, 0.0), p=0.01, B=(0.0, 0.0, 0.0),

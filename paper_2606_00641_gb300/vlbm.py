@@ -1,0 +1,431 @@
+"""Thin ctypes binding of the C ABI in ``include/vlbm.h`` (``libvlbm.so``).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  The functions keep the C names (``vlbm_create``,
+``vlbm_init_fields``, ``vlbm_step``, ``vlbm_moments``, ``vlbm_destroy`` ...);
+``Context`` wraps one ``vlbm_ctx*`` for convenience.
+
+PyTorch is used only as plumbing: ``torch_hooks()`` routes the library's
+device allocations through torch's caching allocator, and a torch stream can
+be passed as the context's stream.  There is no CPU fallback: importing this
+module fails loudly when the compiled library is missing or cannot load.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import _build
+
+VLBM_OK = 0
+VLBM_ERR_ARG = 1
+VLBM_ERR_UNSTABLE = 2
+VLBM_ERR_OOM = 3
+VLBM_ERR_CUDA = 4
+VLBM_ERR_NONPHYSICAL = 5
+VLBM_ERR_TIMEOUT = 6
+VLBM_ERR_STATE = 7
+VLBM_ERR_UNSUPPORTED = 8
+
+VLBM_IDEAL = 0
+VLBM_RESISTIVE = 1
+
+VLBM_F64 = 0
+VLBM_F32 = 1
+VLBM_F16_DEV = 2
+VLBM_BF16_DEV = 3
+
+STORAGE_NAMES = {"f64": VLBM_F64, "f32": VLBM_F32, "f16dev": VLBM_F16_DEV, "bf16dev": VLBM_BF16_DEV}
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class vlbm_params(ctypes.Structure):
+    _fields_ = [
+        ("model", ctypes.c_int),
+        ("dim", ctypes.c_int),
+        ("nx", ctypes.c_int),
+        ("ny", ctypes.c_int),
+        ("nz", ctypes.c_int),
+        ("storage", ctypes.c_int),
+        ("gamma", ctypes.c_double),
+        ("tau", ctypes.c_double * 8),
+        ("source", ctypes.c_double * 8),
+        ("force", ctypes.c_double * 3),
+        ("b_wall", ctypes.c_double * 3),
+        ("walls_y", ctypes.c_int),
+        ("check_every", ctypes.c_int),
+        ("q_ref", ctypes.c_double * 8),
+        ("q_scale", ctypes.c_double * 8),
+        ("stream", ctypes.c_void_p),
+        ("alloc", ALLOC_FN),
+        ("dealloc", FREE_FN),
+        ("alloc_user", ctypes.c_void_p),
+    ]
+
+
+class VlbmError(RuntimeError):
+    def __init__(self, status: int, what: str, detail: str = ""):
+        self.status = status
+        super().__init__("%s: %s%s" % (what, status_string(status), (" (" + detail + ")") if detail else ""))
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build: bool = True):
+    """Load libvlbm.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build() if build else _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError("libvlbm.so is missing: build it with __graft_entry__.build()")
+    L = ctypes.CDLL(path)
+    P, i, d, s = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+    pp = ctypes.POINTER(vlbm_params)
+    sig = {
+        "vlbm_default_params": (None, [pp]),
+        "vlbm_create": (i, [pp, ctypes.POINTER(P)]),
+        "vlbm_create_batch": (i, [pp, i, ctypes.POINTER(P)]),
+        "vlbm_init_fields": (i, [P, i, P]),
+        "vlbm_init_fields_device": (i, [P, i, P]),
+        "vlbm_step": (i, [P, i]),
+        "vlbm_sync": (i, [P]),
+        "vlbm_moments": (i, [P, i, P]),
+        "vlbm_moments_device": (i, [P, i, P]),
+        "vlbm_gather_populations": (i, [P, i, P, i, P]),
+        "vlbm_conservation": (i, [P, i, P]),
+        "vlbm_save": (i, [P, P, ctypes.POINTER(s)]),
+        "vlbm_load": (i, [P, P, s]),
+        "vlbm_autotune": (i, [P, i, ctypes.POINTER(i)]),
+        "vlbm_tile_shapes": (i, [P]),
+        "vlbm_set_tile_shape": (i, [P, i]),
+        "vlbm_nvar": (i, [P]),
+        "vlbm_slots_per_cell": (i, [P]),
+        "vlbm_num_domains": (i, [P]),
+        "vlbm_num_cells": (ctypes.c_int64, [P, i]),
+        "vlbm_step_count": (ctypes.c_int64, [P]),
+        "vlbm_launch_count": (ctypes.c_int64, [P]),
+        "vlbm_population_bytes": (s, [P]),
+        "vlbm_stream": (P, [P]),
+        "vlbm_last_error": (ctypes.c_char_p, [P]),
+        "vlbm_status_string": (ctypes.c_char_p, [i]),
+        "vlbm_destroy": (None, [P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def status_string(status: int) -> str:
+    return load().vlbm_status_string(int(status)).decode()
+
+
+def last_error(ctx=None) -> str:
+    msg = load().vlbm_last_error(ctx)
+    return msg.decode() if msg else ""
+
+
+def _check(status: int, what: str, ctx=None):
+    if status != VLBM_OK:
+        raise VlbmError(status, what, last_error(ctx))
+
+
+def vlbm_default_params() -> vlbm_params:
+    p = vlbm_params()
+    load().vlbm_default_params(ctypes.byref(p))
+    return p
+
+
+def make_params(model: int = VLBM_IDEAL, shape=(64, 64, 64), storage="f32", gamma=5.0 / 3.0,
+                tau=0.51, source=None, force=(0.0, 0.0, 0.0), b_wall=(0.0, 0.0, 0.0),
+                walls_y: bool = False, check_every: int = 0, q_ref=None, q_scale=None,
+                stream: Optional[int] = None, hooks=None) -> vlbm_params:
+    """Parameters for one domain; ``shape`` is (ny, nx) in 2-D, (nz, ny, nx) in 3-D."""
+    p = vlbm_default_params()
+    p.model = int(model)
+    shape = tuple(int(n) for n in shape)
+    if len(shape) == 2:
+        p.dim, p.nz, p.ny, p.nx = 2, 1, shape[0], shape[1]
+    else:
+        p.dim, p.nz, p.ny, p.nx = 3, shape[0], shape[1], shape[2]
+    p.storage = STORAGE_NAMES[storage] if isinstance(storage, str) else int(storage)
+    p.gamma = float(gamma)
+    tau = np.broadcast_to(np.asarray(tau, dtype=float), (8,)) if np.ndim(tau) == 0 else \
+        np.concatenate([np.asarray(tau, dtype=float), np.ones(8 - len(tau))])
+    for k in range(8):
+        p.tau[k] = float(tau[k])
+        p.source[k] = float(source[k]) if source is not None else 0.0
+        p.q_ref[k] = float(q_ref[k]) if q_ref is not None else 0.0
+        p.q_scale[k] = float(q_scale[k]) if q_scale is not None else 1.0
+    for a in range(3):
+        p.force[a] = float(force[a])
+        p.b_wall[a] = float(b_wall[a])
+    p.walls_y = int(bool(walls_y))
+    p.check_every = int(check_every)
+    p.stream = stream if stream else None
+    if hooks is not None:
+        p.alloc, p.dealloc, p.alloc_user = hooks.alloc, hooks.dealloc, None
+    return p
+
+
+class TorchHooks:
+    """Device allocator hooks backed by torch's caching allocator."""
+
+    def __init__(self, device: int = 0):
+        import torch
+        self._torch = torch
+        self.device = device
+
+        def _alloc(nbytes, stream, user):
+            try:
+                return int(torch.cuda.caching_allocator_alloc(int(nbytes), self.device, stream))
+            except Exception:
+                return None
+
+        def _free(ptr, nbytes, stream, user):
+            torch.cuda.caching_allocator_delete(int(ptr))
+
+        self.alloc = ALLOC_FN(_alloc)
+        self.dealloc = FREE_FN(_free)
+
+
+def torch_hooks(device: int = 0) -> TorchHooks:
+    return TorchHooks(device)
+
+
+def vlbm_create(params: vlbm_params) -> int:
+    ctx = ctypes.c_void_p()
+    _check(load().vlbm_create(ctypes.byref(params), ctypes.byref(ctx)), "vlbm_create")
+    return ctx.value
+
+
+def vlbm_create_batch(params: Sequence[vlbm_params]) -> int:
+    arr = (vlbm_params * len(params))(*params)
+    ctx = ctypes.c_void_p()
+    _check(load().vlbm_create_batch(arr, len(params), ctypes.byref(ctx)), "vlbm_create_batch")
+    return ctx.value
+
+
+def _host_f64(a: np.ndarray) -> np.ndarray:
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a
+
+
+def vlbm_init_fields(ctx: int, domain: int, Q: np.ndarray) -> int:
+    """Host fields Q [nvar, (nz,) ny, nx] float64; returns the status (raises on CUDA errors)."""
+    Q = _host_f64(Q)
+    st = load().vlbm_init_fields(ctx, domain, Q.ctypes.data_as(ctypes.c_void_p))
+    if st not in (VLBM_OK, VLBM_ERR_UNSTABLE, VLBM_ERR_NONPHYSICAL):
+        _check(st, "vlbm_init_fields", ctx)
+    return st
+
+
+def vlbm_init_fields_ptr(ctx: int, domain: int, host_ptr: int) -> int:
+    """Host fields from a raw host address (for pinned buffers)."""
+    return load().vlbm_init_fields(ctx, domain, ctypes.c_void_p(host_ptr))
+
+
+def vlbm_init_fields_device(ctx: int, domain: int, dev_ptr: int) -> int:
+    st = load().vlbm_init_fields_device(ctx, domain, ctypes.c_void_p(dev_ptr))
+    if st not in (VLBM_OK, VLBM_ERR_UNSTABLE, VLBM_ERR_NONPHYSICAL):
+        _check(st, "vlbm_init_fields_device", ctx)
+    return st
+
+
+def vlbm_step(ctx: int, n: int) -> int:
+    st = load().vlbm_step(ctx, int(n))
+    if st not in (VLBM_OK, VLBM_ERR_NONPHYSICAL, VLBM_ERR_TIMEOUT):
+        _check(st, "vlbm_step", ctx)
+    return st
+
+
+def vlbm_sync(ctx: int) -> int:
+    st = load().vlbm_sync(ctx)
+    if st not in (VLBM_OK, VLBM_ERR_NONPHYSICAL, VLBM_ERR_TIMEOUT):
+        _check(st, "vlbm_sync", ctx)
+    return st
+
+
+def vlbm_nvar(ctx: int) -> int:
+    return load().vlbm_nvar(ctx)
+
+
+def vlbm_num_cells(ctx: int, domain: int = 0) -> int:
+    return int(load().vlbm_num_cells(ctx, domain))
+
+
+def vlbm_moments(ctx: int, domain: int, shape) -> np.ndarray:
+    out = np.empty((vlbm_nvar(ctx),) + tuple(shape), dtype=np.float64)
+    _check(load().vlbm_moments(ctx, domain, out.ctypes.data_as(ctypes.c_void_p)), "vlbm_moments", ctx)
+    return out
+
+
+def vlbm_moments_ptr(ctx: int, domain: int, host_ptr: int):
+    _check(load().vlbm_moments(ctx, domain, ctypes.c_void_p(host_ptr)), "vlbm_moments", ctx)
+
+
+def vlbm_moments_device(ctx: int, domain: int, dev_ptr: int):
+    _check(load().vlbm_moments_device(ctx, domain, ctypes.c_void_p(dev_ptr)), "vlbm_moments_device", ctx)
+
+
+def vlbm_slots_per_cell(ctx: int) -> int:
+    return load().vlbm_slots_per_cell(ctx)
+
+
+def vlbm_gather_populations(ctx: int, domain: int, cells) -> np.ndarray:
+    """Pre-collision populations [ncell, slots] at the listed linear cell indices."""
+    cells = np.ascontiguousarray(np.asarray(cells, dtype=np.int64))
+    out = np.empty((len(cells), vlbm_slots_per_cell(ctx)), dtype=np.float64)
+    _check(load().vlbm_gather_populations(ctx, domain, cells.ctypes.data_as(ctypes.c_void_p), len(cells),
+                                          out.ctypes.data_as(ctypes.c_void_p)), "vlbm_gather_populations", ctx)
+    return out
+
+
+def vlbm_conservation(ctx: int, domain: int = 0) -> np.ndarray:
+    out = np.zeros(vlbm_nvar(ctx), dtype=np.float64)
+    _check(load().vlbm_conservation(ctx, domain, out.ctypes.data_as(ctypes.c_void_p)), "vlbm_conservation", ctx)
+    return out
+
+
+def vlbm_save(ctx: int) -> bytes:
+    L = load()
+    n = ctypes.c_size_t(0)
+    _check(L.vlbm_save(ctx, None, ctypes.byref(n)), "vlbm_save", ctx)
+    buf = ctypes.create_string_buffer(n.value)
+    _check(L.vlbm_save(ctx, buf, ctypes.byref(n)), "vlbm_save", ctx)
+    return buf.raw[:n.value]
+
+
+def vlbm_load(ctx: int, data: bytes):
+    _check(load().vlbm_load(ctx, data, len(data)), "vlbm_load", ctx)
+
+
+def vlbm_autotune(ctx: int, steps: int = 10) -> int:
+    ch = ctypes.c_int(0)
+    _check(load().vlbm_autotune(ctx, int(steps), ctypes.byref(ch)), "vlbm_autotune", ctx)
+    return ch.value
+
+
+def vlbm_tile_shapes(ctx: int) -> int:
+    return load().vlbm_tile_shapes(ctx)
+
+
+def vlbm_set_tile_shape(ctx: int, shape: int):
+    _check(load().vlbm_set_tile_shape(ctx, int(shape)), "vlbm_set_tile_shape", ctx)
+
+
+def vlbm_step_count(ctx: int) -> int:
+    return int(load().vlbm_step_count(ctx))
+
+
+def vlbm_launch_count(ctx: int) -> int:
+    return int(load().vlbm_launch_count(ctx))
+
+
+def vlbm_population_bytes(ctx: int) -> int:
+    return int(load().vlbm_population_bytes(ctx))
+
+
+def vlbm_stream(ctx: int) -> int:
+    return load().vlbm_stream(ctx) or 0
+
+
+def vlbm_destroy(ctx: int):
+    if ctx:
+        load().vlbm_destroy(ctx)
+
+
+class Context:
+    """One library context (a single domain, or a batch of 2-D domains)."""
+
+    def __init__(self, params, batch: bool = False, hooks: Optional[TorchHooks] = None):
+        self._hooks = hooks  # keep the callbacks alive as long as the context
+        if batch:
+            self.params = list(params)
+            self.ptr = vlbm_create_batch(self.params)
+            first = self.params[0]
+        else:
+            self.params = [params]
+            self.ptr = vlbm_create(params)
+            first = params
+        self.nvar = vlbm_nvar(self.ptr)
+        self.nslot = vlbm_slots_per_cell(self.ptr)
+
+    def shape(self, domain: int = 0):
+        p = self.params[domain]
+        return (p.ny, p.nx) if p.dim == 2 else (p.nz, p.ny, p.nx)
+
+    def init_fields(self, Q, domain: int = 0) -> int:
+        return vlbm_init_fields(self.ptr, domain, Q)
+
+    def step(self, n: int) -> int:
+        return vlbm_step(self.ptr, n)
+
+    def sync(self) -> int:
+        return vlbm_sync(self.ptr)
+
+    def moments(self, domain: int = 0) -> np.ndarray:
+        return vlbm_moments(self.ptr, domain, self.shape(domain))
+
+    def populations(self, cells, domain: int = 0) -> np.ndarray:
+        return vlbm_gather_populations(self.ptr, domain, cells)
+
+    def conservation(self, domain: int = 0) -> np.ndarray:
+        return vlbm_conservation(self.ptr, domain)
+
+    def save(self) -> bytes:
+        return vlbm_save(self.ptr)
+
+    def load(self, data: bytes):
+        vlbm_load(self.ptr, data)
+
+    def autotune(self, steps: int = 10) -> int:
+        return vlbm_autotune(self.ptr, steps)
+
+    def tile_shapes(self) -> int:
+        return vlbm_tile_shapes(self.ptr)
+
+    def set_tile_shape(self, shape: int):
+        vlbm_set_tile_shape(self.ptr, shape)
+
+    @property
+    def step_count(self) -> int:
+        return vlbm_step_count(self.ptr)
+
+    @property
+    def launches(self) -> int:
+        return vlbm_launch_count(self.ptr)
+
+    @property
+    def stream(self) -> int:
+        return vlbm_stream(self.ptr)
+
+    def close(self):
+        if self.ptr:
+            vlbm_destroy(self.ptr)
+            self.ptr = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
