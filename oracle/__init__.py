@@ -66,6 +66,7 @@ def _configure(L):
     L.orc_resistive_step.argtypes = [i, i, i, d, d, p, p, i, p, p, p, p, i]
     L.orc_resistive_moments.argtypes = [i, i, i, p, p, i, p, p, p]
     L.orc_resistive_run.argtypes = [i, i, i, d, d, p, p, i, p, i, p, i]
+    L.orc_resistive_collide_cell.argtypes = [d, d, p, p, p]
     return L
 
 
@@ -242,6 +243,15 @@ def resistive_moments(f, g, force, b_wall, walls_y):
                                        int(walls_y), _ptr(f), _ptr(g), _ptr(Q)),
            "resistive_moments")
     return Q
+
+
+def resistive_collide_cell(tau_f, tau_m, force, fin) -> np.ndarray:
+    """Post-collision populations [40] (19 flow, then 3 x 7 magnetic) of one fluid cell."""
+    fin = _f64(fin)
+    out = np.zeros(40)
+    _check(lib().orc_resistive_collide_cell(tau_f, tau_m, _ptr(_f64(force)), _ptr(fin), _ptr(out)),
+           "resistive_collide_cell")
+    return out
 
 
 def resistive_run(Q0, tau_f, tau_m, force, b_wall, walls_y, nsteps, nthreads: int = 1):

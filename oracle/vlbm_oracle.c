@@ -404,6 +404,58 @@ static void res_mag_feq(const orc_lattice *L7, const double *u, const double *B,
     }
 }
 
+/* Collision of one fluid cell of the resistive model (see the model block
+ * above): moments, equilibria, BGK and the Guo force term. */
+static void res_collide(const orc_lattice *L19, const orc_lattice *L7, double tau_f, double tau_m,
+                        const double *force, const double *fl, double gl[3][7], double *fs,
+                        double gs[3][7])
+{
+    double rho = 0.0, m[3] = {0, 0, 0}, B[3] = {0, 0, 0}, u[3];
+    for (int i = 0; i < 19; ++i) {
+        rho += fl[i];
+        for (int a = 0; a < 3; ++a) m[a] += fl[i] * L19->c[i][a];
+    }
+    for (int a = 0; a < 3; ++a) {
+        m[a] += 0.5 * force[a];
+        u[a] = m[a] / rho;
+    }
+    for (int b = 0; b < 3; ++b)
+        for (int i = 0; i < 7; ++i) B[b] += gl[b][i];
+    double feq[ORC_QMAX], geq[3][7];
+    res_flow_feq(L19, rho, m, B, feq);
+    res_mag_feq(L7, u, B, geq);
+    for (int i = 0; i < 19; ++i) {
+        double cu = 0.0, cF = 0.0, cuF = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            cu += L19->c[i][a] * u[a];
+            cF += L19->c[i][a] * force[a];
+            cuF += u[a] * force[a];
+        }
+        double guo = (1.0 - 0.5 / tau_f) * L19->w[i] *
+                     ((cF - cuF) / L19->cs2 + cu * cF / (L19->cs2 * L19->cs2));
+        fs[i] = fl[i] - (fl[i] - feq[i]) / tau_f + guo;
+    }
+    for (int b = 0; b < 3; ++b)
+        for (int i = 0; i < 7; ++i) gs[b][i] = gl[b][i] - (gl[b][i] - geq[b][i]) / tau_m;
+}
+
+/* Single fluid-cell collision, exported for sampled parity checks:
+ * fin = 19 flow then 21 magnetic populations, fout likewise. */
+int orc_resistive_collide_cell(double tau_f, double tau_m, const double *force, const double *fin,
+                               double *fout)
+{
+    orc_lattice L19, L7;
+    build_lattice(19, &L19);
+    build_lattice(7, &L7);
+    double gl[3][7], gs[3][7];
+    for (int b = 0; b < 3; ++b)
+        for (int i = 0; i < 7; ++i) gl[b][i] = fin[19 + 7 * b + i];
+    res_collide(&L19, &L7, tau_f, tau_m, force, fin, gl, fout, gs);
+    for (int b = 0; b < 3; ++b)
+        for (int i = 0; i < 7; ++i) fout[19 + 7 * b + i] = gs[b][i];
+    return 0;
+}
+
 /* Initial populations from the state: flow f = f_eq(rho, m - F/2, B), so
  * that the momentum moment (sum f c + F/2) returns m; B lattices g = g_eq. */
 int orc_resistive_init(int nx, int ny, int nz, const double *Qr, const double *force,
@@ -457,47 +509,22 @@ int orc_resistive_step(int nx, int ny, int nz, double tau_f, double tau_m, const
             }
             continue;
         }
-        double fl[ORC_QMAX], gl[3][7];
+        double fl[ORC_QMAX], gl[3][7], fs[ORC_QMAX], gs[3][7];
         for (int i = 0; i < 19; ++i) fl[i] = fin[(long)i * N + cell];
         for (int b = 0; b < 3; ++b)
             for (int i = 0; i < 7; ++i) gl[b][i] = gin[(long)(b * 7 + i) * N + cell];
-        double rho = 0.0, m[3] = {0, 0, 0}, B[3] = {0, 0, 0}, u[3];
+        res_collide(&L19, &L7, tau_f, tau_m, force, fl, gl, fs, gs);
         for (int i = 0; i < 19; ++i) {
-            rho += fl[i];
-            for (int a = 0; a < 3; ++a) m[a] += fl[i] * L19.c[i][a];
-        }
-        for (int a = 0; a < 3; ++a) {
-            m[a] += 0.5 * force[a];
-            u[a] = m[a] / rho;
-        }
-        for (int b = 0; b < 3; ++b)
-            for (int i = 0; i < 7; ++i) B[b] += gl[b][i];
-        double feq[ORC_QMAX], geq[3][7];
-        res_flow_feq(&L19, rho, m, B, feq);
-        res_mag_feq(&L7, u, B, geq);
-        for (int i = 0; i < 19; ++i) {
-            double cu = 0.0, cF = 0.0, cuF = 0.0;
-            for (int a = 0; a < 3; ++a) {
-                cu += L19.c[i][a] * u[a];
-                cF += L19.c[i][a] * force[a];
-                cuF += u[a] * force[a];
-            }
-            double guo = (1.0 - 0.5 / tau_f) * L19.w[i] *
-                         ((cF - cuF) / L19.cs2 + cu * cF / (L19.cs2 * L19.cs2));
-            double fs = fl[i] - (fl[i] - feq[i]) / tau_f + guo;
             long dst = neighbour(x, y, z, L19.c[i], nx, ny, nz);
             int dy = (y + L19.c[i][1] + ny) % ny;
             if (is_wall(dy, ny, walls_y))
-                fout[(long)L19.opp[i] * N + cell] = fs; /* halfway bounce-back */
+                fout[(long)L19.opp[i] * N + cell] = fs[i]; /* halfway bounce-back */
             else
-                fout[(long)i * N + dst] = fs;
+                fout[(long)i * N + dst] = fs[i];
         }
         for (int i = 0; i < 7; ++i) {
             long dst = neighbour(x, y, z, L7.c[i], nx, ny, nz);
-            for (int b = 0; b < 3; ++b) {
-                double gs = gl[b][i] - (gl[b][i] - geq[b][i]) / tau_m;
-                gout[(long)(b * 7 + i) * N + dst] = gs;
-            }
+            for (int b = 0; b < 3; ++b) gout[(long)(b * 7 + i) * N + dst] = gs[b][i];
         }
     }
     return 0;

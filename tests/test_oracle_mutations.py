@@ -55,10 +55,10 @@ MUTANTS = [
      IDEAL_PINS),
     ("source injected without weight", "if (src) out += L->w[i] * src[k];",
      "if (src) out += src[k];", IDEAL_PINS),
-    ("bounce-back keeps direction", "fout[(long)L19.opp[i] * N + cell] = fs;",
-     "fout[(long)i * N + cell] = fs;", RES_PINS),
-    ("Guo force half-step factor", "double guo = (1.0 - 0.5 / tau_f) * L19.w[i] *",
-     "double guo = L19.w[i] *", RES_PINS),
+    ("bounce-back keeps direction", "fout[(long)L19.opp[i] * N + cell] = fs[i];",
+     "fout[(long)i * N + cell] = fs[i];", RES_PINS),
+    ("Guo force half-step factor", "double guo = (1.0 - 0.5 / tau_f) * L19->w[i] *",
+     "double guo = L19->w[i] *", RES_PINS),
     ("magnetic flux transposed", "for (int a = 0; a < 3; ++a) phi[a] = u[a] * B[b] - B[a] * u[b];",
      "for (int a = 0; a < 3; ++a) phi[a] = u[b] * B[a] - B[b] * u[a];", RES_PINS),
     ("Maxwell stress missing in flow", "(a == b ? 0.5 * B2 : 0.0) - B[a] * B[b];",
