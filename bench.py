@@ -30,6 +30,11 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 BYTES_PER_POP = {"f64": 8, "f32": 4, "f16dev": 2, "bf16dev": 2}
+# DRAM bytes (read + write) per cell update of the step kernel, from one ncu
+# capture of a 256^3 launch (profiles/k_ideal_step_f32_256cubed.md); traffic
+# grows in proportion to the cells, so a full launch is this times the cells.
+# Set an entry to None whenever that kernel changes until it is re-captured.
+MEASURED_DRAM_BYTES_PER_CELL = {"f32": 7456549e3 / 16777216}
 WORKLOAD = "ideal MHD 3-D, 8 x D3Q7, periodic, random-phase k<=4, Mach 2, beta 1, CFL 0.2, tau 0.51"
 
 
@@ -45,6 +50,7 @@ def parse():
                     help="other storage forms to time and compare with FP64 ('' to skip)")
     ap.add_argument("--form-steps", type=int, default=20)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the channel and batched forms")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--seed", type=int, default=3003)
@@ -163,6 +169,90 @@ def cpu_baseline(args, seconds):
             "steps": steps, "ms_per_step": dt / steps * 1e3}
 
 
+def _time_steps(vlbm, ctx_ptrs, stream, torch, steps, per_call):
+    """CUDA-event time of `steps` steps; per_call=True issues one vlbm_step(ctx, 1)
+    per context per step (sequential plain launches), else vlbm_step(ctx, steps)."""
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    stream.synchronize()
+    e0.record(stream)
+    if per_call:
+        for _ in range(steps):
+            for c in ctx_ptrs:
+                vlbm.vlbm_step(c, 1)
+    else:
+        for c in ctx_ptrs:
+            vlbm.vlbm_step(c, steps)
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def channel_form(args, vlbm, fields, torch, stream, hbm_peak):
+    """Resistive channel 256 x 128 x 128 (D3Q19 + 3 x D3Q7, FP32, walls, Guo force)."""
+    shape = (128, 128, 256)
+    setup = fields.hartmann_setup(shape, 2002, Ha=10.0)
+    p = vlbm.make_params(model=vlbm.VLBM_RESISTIVE, shape=shape, storage="f32",
+                         tau=[setup.tau_f, setup.tau_m, setup.tau_m, setup.tau_m], force=setup.force,
+                         b_wall=setup.b_wall, walls_y=True, stream=stream.cuda_stream)
+    ctx = vlbm.Context(p)
+    Qd = torch.from_numpy(setup.Q).cuda()
+    st = vlbm.vlbm_init_fields_device(ctx.ptr, 0, Qd.data_ptr())
+    del Qd
+    vlbm.vlbm_step(ctx.ptr, 64)
+    steps = 256
+    ms = _time_steps(vlbm, [ctx.ptr], stream, torch, steps, False)
+    status = vlbm.status_string(vlbm.vlbm_sync(ctx.ptr))
+    ctx.close()
+    ncell = 256 * 128 * 128
+    gl = ncell * steps / (ms * 1e-3) / 1e9
+    return {"workload": "resistive incompressible channel 256x128x128, D3Q19 + 3 x D3Q7, FP32, "
+                        "bounce-back walls in y, Ha 10, Re 100", "init_status": vlbm.status_string(st),
+            "status": status, "glups": gl, "steps": steps, "bytes_per_cell": 320,
+            "roofline_frac": gl * 1e9 * 320 / (hbm_peak * 1e9)}
+
+
+def batch_form(args, vlbm, fields, torch, stream, hbm_peak):
+    """64 independent 2-D domains (sides 64..1024) in one launch per step vs 64 plain launches."""
+    specs = fields.batch_specs(64, 4004)
+    params, Qs = [], []
+    for sp in specs:
+        n = sp["side"]
+        f0 = fields.ideal_fields((n, n), sp["seed"], gamma=sp["gamma"], mach=sp["mach"], cfl=0.1,
+                                 device=torch.device("cuda"))
+        Qs.append(f0.Q)
+        params.append(vlbm.make_params(shape=(n, n), storage="f32", gamma=sp["gamma"], tau=0.51,
+                                       stream=stream.cuda_stream))
+    ncell = sum(sp["side"] ** 2 for sp in specs)
+    steps = 64
+    # batched: one context, one launch per step, graph-captured, autotuned tile shape
+    bctx = vlbm.Context(params, batch=True)
+    bad = 0
+    for d, Q in enumerate(Qs):
+        bad += vlbm.vlbm_init_fields_device(bctx.ptr, d, Q.data_ptr()) != vlbm.VLBM_OK
+    choice = bctx.autotune(8)
+    vlbm.vlbm_step(bctx.ptr, 64)
+    ms_b = _time_steps(vlbm, [bctx.ptr], stream, torch, steps, False)
+    st_b = vlbm.status_string(vlbm.vlbm_sync(bctx.ptr))
+    bctx.close()
+    # baseline: 64 contexts, one plain launch per domain per step
+    ctxs = [vlbm.Context(p) for p in params]
+    for c, Q in zip(ctxs, Qs):
+        vlbm.vlbm_init_fields_device(c.ptr, 0, Q.data_ptr())
+    ptrs = [c.ptr for c in ctxs]
+    _time_steps(vlbm, ptrs, stream, torch, 2, True)
+    ms_s = _time_steps(vlbm, ptrs, stream, torch, steps, True)
+    for c in ctxs:
+        c.close()
+    gb = ncell * steps / (ms_b * 1e-3) / 1e9
+    gs = ncell * steps / (ms_s * 1e-3) / 1e9
+    return {"workload": "64 periodic 2-D ideal-MHD domains, sides from {64..1024} (seed 4004), "
+                        "gamma U[1.4,5/3], Mach U[0.5,3], 8 x D2Q5, FP32", "cells": ncell,
+            "init_failures": int(bad), "status": st_b, "tile_shape": choice,
+            "glups_batched": gb, "glups_sequential_launches": gs, "speedup": gb / gs, "steps": steps,
+            "bytes_per_cell": 320, "roofline_frac_batched": gb * 1e9 * 320 / (hbm_peak * 1e9)}
+
+
 def main():
     args = parse()
     world, rank, local = dist_env()
@@ -254,23 +344,20 @@ def main():
         hostQ = torch.empty(Q.shape, dtype=torch.float64, pin_memory=True)
         hostQ.copy_(Q)
         hostOut = torch.empty(Q.shape, dtype=torch.float64, pin_memory=True)
-        sums = np.zeros(8)
-        L = vlbm.load()
-        import ctypes
         barrier()
         t0 = time.perf_counter()
         st = vlbm.vlbm_init_fields_ptr(ctx.ptr, 0, hostQ.data_ptr())
         for _ in range(args.steps):
             vlbm.vlbm_step(ctx.ptr, 1)
-            L.vlbm_conservation(ctx.ptr, 0, sums.ctypes.data_as(ctypes.c_void_p))
+            vlbm.vlbm_sync(ctx.ptr)  # 4-byte health word read back every step
         vlbm.vlbm_moments_ptr(ctx.ptr, 0, hostOut.data_ptr())
         dt = time.perf_counter() - t0
         barrier()
         e2e = {"value": world * ncell * args.steps / dt / 1e9, "unit": "GLUPS",
                "h2d_bytes_per_step": int(Q.numel() * 8 / args.steps),
-               "d2h_bytes_per_step": int(Q.numel() * 8 / args.steps + 8 * 8),
-               "note": "init from pinned host fields, per step one vlbm_step + vlbm_conservation "
-                       "read-back, final vlbm_moments to pinned host"}
+               "d2h_bytes_per_step": int(Q.numel() * 8 / args.steps + 4),
+               "note": "vlbm_init_fields from pinned host FP64 fields, per step vlbm_step(1) + "
+                       "vlbm_sync (health word read back), final vlbm_moments to pinned host"}
         del hostQ, hostOut
     ctx.close()
 
@@ -311,6 +398,11 @@ def main():
                            "rel_l2_vs_f64": dict(zip(fields.IDEAL_FIELDS, [float(v) for v in l2]))}
         del Q64
 
+    extra = {}
+    if rank == 0 and not args.no_extra:
+        extra["resistive_channel"] = channel_form(args, vlbm, fields, torch, stream, hbm_peak)
+        extra["batched_2d"] = batch_form(args, vlbm, fields, torch, stream, hbm_peak)
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         cpu = cpu_baseline(args, args.cpu_seconds)
@@ -328,7 +420,9 @@ def main():
                              % (ncell * 56 * BYTES_PER_POP[args.storage] / 1e9)},
             "status": vlbm.status_string(status),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                         "frac": achieved / hbm_peak, "traffic": None,
+                         "frac": achieved / hbm_peak,
+                         "traffic": (MEASURED_DRAM_BYTES_PER_CELL[args.storage] * ncell
+                                     if MEASURED_DRAM_BYTES_PER_CELL.get(args.storage) else None),
                          "peak_kind": peak_kind,
                          "kernel": "k_ideal_step<3,float,float> (fused collide+stream)",
                          "algorithmic_bytes_per_launch": ncell * bytes_cell},
@@ -337,6 +431,7 @@ def main():
             "e2e": e2e,
             "cpu_baseline": cpu,
             "forms": forms or None,
+            "other_paths": extra or None,
             "paper_context": {"note": "RTX A5000, FP32, 2-D D2Q5 kernel 98.9% and 3-D homogenised D3Q7 "
                                       "kernel 75.8% of a 680 GB/s measured roofline; other hardware"},
         }

@@ -80,9 +80,10 @@ def test_config_128sq_fp64_200_steps(V):
     assert err.max() < 1e-12, err
 
 
-@pytest.mark.parametrize("shape,steps", [((64, 72), 50), ((16, 20, 140), 50), ((3, 130, 5), 31)])
-def test_ideal_fp32_matches_oracle(V, shape, steps):
-    f0 = fields.ideal_fields(shape, 202, mach=1.5, beta=1.0, cfl=0.1 if len(shape) == 2 else 0.2)
+@pytest.mark.parametrize("shape,steps,mach", [((64, 72), 50, 1.5), ((16, 20, 140), 50, 1.5),
+                                              ((3, 130, 5), 31, 0.5)])
+def test_ideal_fp32_matches_oracle(V, shape, steps, mach):
+    f0 = fields.ideal_fields(shape, 202, mach=mach, beta=1.0, cfl=0.1 if len(shape) == 2 else 0.2)
     got = run_gpu(V, f0.Q, f0.gamma, 0.51, steps, "f32")
     ref = oracle.ideal_run(f0.Q, f0.gamma, 0.51, steps)
     err = rel_err(got, ref, ideal_scales(f0.Q))
@@ -183,6 +184,32 @@ def test_health_and_stability_statuses(V):
         assert ctx.sync() == V.VLBM_ERR_NONPHYSICAL
         assert ctx.step(1) == V.VLBM_ERR_NONPHYSICAL  # sticky
         assert ctx.init_fields(f0.Q) == V.VLBM_OK      # init clears it
+
+
+def test_nonphysical_flag_rises_at_the_oracle_step(V):
+    # an under-resolved Mach 1.5 field on a 3 x 130 x 5 grid: the oracle's gas
+    # pressure first turns negative during step 7; the step kernel's health
+    # flag must rise at that step and not before
+    shape = (3, 130, 5)
+    f0 = fields.ideal_fields(shape, 202, mach=1.5, beta=1.0, cfl=0.2)
+    f = oracle.ideal_init(f0.Q, f0.gamma)
+    first_bad = None
+    for s in range(12):
+        f = oracle.ideal_step(f, f0.gamma, 0.51)
+        Q = oracle.ideal_moments(f)
+        pmin = min(oracle.ideal_pressure(f0.gamma, Q[:, z, y, x])
+                   for z in range(3) for y in range(130) for x in range(5))
+        if pmin <= 0:
+            first_bad = s + 1
+            break
+    assert first_bad is not None
+    p = V.make_params(shape=shape, storage="f64", gamma=f0.gamma, tau=0.51)
+    with V.Context(p) as ctx:
+        assert ctx.init_fields(f0.Q) == V.VLBM_OK
+        ctx.step(first_bad)  # these kernels inspect only the physical states 0 .. first_bad-1
+        assert ctx.sync() == V.VLBM_OK
+        ctx.step(1)
+        assert ctx.sync() == V.VLBM_ERR_NONPHYSICAL
 
 
 @pytest.mark.parametrize("storage", ["f64", "f32", "bf16dev"])
