@@ -124,7 +124,9 @@ vlbm_status vlbm_create_batch(const vlbm_params *p, int count, vlbm_ctx **out);
  * Returns VLBM_ERR_UNSTABLE when max(|u| + c_f) >= cs on some cell
  * (c_f^2 = (gamma p + |B|^2)/rho; the scheme's diffusion
  * (tau - 1/2)(cs^2 - a^2) would be negative), VLBM_ERR_NONPHYSICAL when
- * rho <= 0 or p <= 0 somewhere.  Synchronises the stream. */
+ * some cell has NaN, rho <= 0 or p <= 0 (this takes precedence).  Either
+ * error leaves the populations written but the status word clear.
+ * Synchronises the stream. */
 vlbm_status vlbm_init_fields(vlbm_ctx *ctx, int domain, const double *Q_host);
 
 /* As vlbm_init_fields, Q_dev a device pointer (nvar x N doubles). */

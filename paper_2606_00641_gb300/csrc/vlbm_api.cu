@@ -355,13 +355,15 @@ static vlbm_status finish_init(vlbm_ctx *c)
     unsigned flags = 0;
     vlbm_status s = read_flags_sync(c, &flags);
     if (s != VLBM_OK) return s;
+    // a NaN or non-positive state is reported as such even though it also
+    // fails the signal-speed test
+    if (flags & kFlagNonPhysical) {
+        cudaMemsetAsync(c->d_flags, 0, sizeof(unsigned), c->stream);
+        return fail(c, VLBM_ERR_NONPHYSICAL, "initial fields have NaN, rho <= 0 or p <= 0");
+    }
     if (flags & kFlagUnstable) {
         cudaMemsetAsync(c->d_flags, 0, sizeof(unsigned), c->stream);
         return fail(c, VLBM_ERR_UNSTABLE, "max(|u| + c_f) >= cs: the scheme's diffusion would be negative");
-    }
-    if (flags & kFlagNonPhysical) {
-        cudaMemsetAsync(c->d_flags, 0, sizeof(unsigned), c->stream);
-        return fail(c, VLBM_ERR_NONPHYSICAL, "initial fields have rho <= 0 or p <= 0");
     }
     c->sticky = VLBM_OK;
     return VLBM_OK;

@@ -170,7 +170,13 @@ def test_health_and_stability_statuses(V):
         bad[0, 3, 4] = np.nan
         assert ctx.init_fields(bad) == V.VLBM_ERR_NONPHYSICAL
         bad = f0.Q.copy()
-        bad[1] *= 40.0  # |u| far above the lattice sound speed
+        bad[1, 5, 6] = 0.0  # rho u set, energy kept: a cell with p <= 0 somewhere is nonphysical
+        bad[4, 5, 6] = -1.0
+        assert ctx.init_fields(bad) == V.VLBM_ERR_NONPHYSICAL
+        bad = f0.Q.copy()
+        ke = 0.5 * (bad[1] ** 2) / bad[0]
+        bad[1] *= 40.0  # |u| far above the lattice sound speed, gas pressure unchanged
+        bad[4] += 0.5 * (bad[1] ** 2) / bad[0] - ke
         assert ctx.init_fields(bad) == V.VLBM_ERR_UNSTABLE
         assert ctx.init_fields(f0.Q) == V.VLBM_OK
         assert ctx.step(4) == V.VLBM_OK and ctx.sync() == V.VLBM_OK
