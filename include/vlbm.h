@@ -163,6 +163,40 @@ vlbm_status vlbm_gather_populations(vlbm_ctx *ctx, int domain, const int64_t *ce
  * sums[nvar] on the host.  Also refreshes the health status.  Synchronises. */
 vlbm_status vlbm_conservation(vlbm_ctx *ctx, int domain, double *sums);
 
+/* Domain sums of the eight ideal-MHD fields, like vlbm_conservation, for a
+ * caller that owns the population buffer and may not allocate device memory
+ * at all -- for example code embedded in a host application whose memory
+ * manager owns every device allocation, or a latency-bound loop that must not
+ * pay for (or synchronise on) cudaMalloc.  The paper has no counterpart: this
+ * is a library-service entry point.
+ *
+ * Inputs: pop_dev, a device buffer in the library's population layout
+ * (slot j = k * q + i of cell x at pop_dev + (j * stride + x) elements of the
+ * storage type, q = 5 in 2-D and 7 in 3-D, x = x + nx * (y + ny * z),
+ * periodic), holding the state after a number of steps whose parity is
+ * `parity` (the AA in-place pattern: at parity 0 slot (i, x) is f_i(x), at
+ * parity 1 slot (opp i, x - c_i) is); storage as in vlbm_storage, with the
+ * per-lattice q_ref and q_scale (8 host doubles each) required for the
+ * deviation forms and ignored otherwise.  Output: sums_dev, 8 device doubles.
+ * Work is enqueued on `stream` (a cudaStream_t, NULL for the default stream);
+ * the call returns without synchronising.
+ *
+ * It allocates nothing: the per-CTA partial sums go to a fixed 256 KiB array
+ * in the library's device image (present on every GPU that loads the library
+ * until the process exits).  That bounds the domain to at most 2^28 =
+ * 268,435,456 cells; larger domains are rejected with VLBM_ERR_ARG before any
+ * device work.  The first call on each device looks up the array's device
+ * address with that device current, so make that first call before capturing
+ * any stream.  All calls share the one array; nothing in it has to start at
+ * zero (every partial is written before it is read), but two calls whose work
+ * overlaps on the GPU race on it -- serialise them (one stream, or events).
+ * Errors: VLBM_ERR_ARG for NULL buffers, bad sizes or parity, missing
+ * q_ref/q_scale; VLBM_ERR_CUDA if the look-up or a launch fails; the reason is
+ * in vlbm_last_error(NULL). */
+vlbm_status vlbm_conservation_noalloc(const void *pop_dev, int storage, int dim, int nx, int ny, int nz,
+                                      int64_t stride, int parity, const double *q_ref, const double *q_scale,
+                                      double *sums_dev, void *stream);
+
 /* Checkpoint: raw populations, step count and parameters of every domain.
  * With buf == NULL, *bytes receives the size needed.  vlbm_load restores a
  * context created with identical parameters bit-exactly. */
