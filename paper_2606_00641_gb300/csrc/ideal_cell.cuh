@@ -13,18 +13,28 @@
 
 namespace vlbm {
 
-template <int D, class C>
+//
+// Deviation storage (DEV): the values in f are the stored deviations
+// g_ki = (f_ki - w_i r_k) / s_k.  Because sum_i w_i = 1 the moment is
+// Q_k = r_k + s_k sum_i g_ki, and the BGK update is affine in f, so it runs on
+// g directly: g*_ki = (1 - omega) g_ki + omega w_i G_k + w_i S_k / s_k
+// +- omega Phi_k,a / (2 s_k) with G_k = sum_i g_ki -- no per-population decode
+// or encode.  The caller passes src0/src1 already divided by s_k.
+template <int D, class C, bool DEV = false>
 __device__ __forceinline__ void ideal_collide(C (&f)[8][AxisSet<D>::Q], const C gm1, const C *omega,
-                                              const C *src0, const C *src1, unsigned *flags)
+                                              const C *src0, const C *src1, unsigned *flags,
+                                              const C *ref = nullptr, const C *scale = nullptr,
+                                              const C *inv_scale = nullptr)
 {
     constexpr int Q = AxisSet<D>::Q;
-    C q[8];
+    C G[8], q[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
         C s = f[k][0];
 #pragma unroll
         for (int i = 1; i < Q; ++i) s += f[k][i];
-        q[k] = s;
+        G[k] = s;
+        q[k] = DEV ? ref[k] + scale[k] * s : s;
     }
     const C rho = q[0];
     const C ir = C(1) / rho;
@@ -57,9 +67,9 @@ __device__ __forceinline__ void ideal_collide(C (&f)[8][AxisSet<D>::Q], const C 
     for (int k = 0; k < 8; ++k) {
         const C om = omega[k];
         const C omc = C(1) - om;
-        const C A0 = om * w0 * q[k] + src0[k];
-        const C A1 = om * w1 * q[k] + src1[k];
-        const C hom = C(0.5) * om;  // omega * w_moving / cs^2
+        const C A0 = om * w0 * G[k] + src0[k];
+        const C A1 = om * w1 * G[k] + src1[k];
+        const C hom = DEV ? C(0.5) * om * inv_scale[k] : C(0.5) * om;  // omega * w_moving / cs^2 (/ s_k)
         f[k][0] = omc * f[k][0] + A0;
 #pragma unroll
         for (int ax = 0; ax < D; ++ax) {

@@ -24,12 +24,11 @@ template <class C> struct IdealArgs {
     int64_t stride;
     C gm1;
     C omega[kMaxLat];
-    C src0[kMaxLat];
-    C src1[kMaxLat];
-    C ref0[kMaxLat];
-    C ref1[kMaxLat];
-    C scale[kMaxLat];
-    C inv_scale[kMaxLat];
+    C src0[kMaxLat];      // w_0 S_k       (deviation storage: / s_k)
+    C src1[kMaxLat];      // w_moving S_k  (deviation storage: / s_k)
+    C ref[kMaxLat];       // deviation storage: r_k
+    C scale[kMaxLat];     //                    s_k
+    C inv_scale[kMaxLat]; //                    1 / s_k
     unsigned *flags;
 };
 
@@ -52,20 +51,6 @@ __device__ __forceinline__ void neighbours(int x, int y, int z, int nx, int ny, 
     }
 }
 
-template <int D, class S, class C>
-__device__ __forceinline__ C decode(const IdealArgs<C> &a, const S *p, int k, int i)
-{
-    C v = Codec<S>::load(p);
-    if constexpr (Codec<S>::kDev) v = v * a.scale[k] + (i == 0 ? a.ref0[k] : a.ref1[k]);
-    return v;
-}
-
-template <int D, class S, class C>
-__device__ __forceinline__ void encode(const IdealArgs<C> &a, S *p, int k, int i, C v)
-{
-    if constexpr (Codec<S>::kDev) v = (v - (i == 0 ? a.ref0[k] : a.ref1[k])) * a.inv_scale[k];
-    Codec<S>::store(p, v);
-}
 
 // The fused collide-and-stream step.  ODD selects the AA parity.
 template <int D, class S, class C, bool ODD>
@@ -88,10 +73,12 @@ __global__ void __launch_bounds__(kBlockX) k_ideal_step(const IdealArgs<C> a)
         for (int i = 0; i < Q; ++i) {
             const int j = ODD ? opp_axis(i) : i;
             const int64_t at = ODD ? nb[opp_axis(i)] : cell;
-            f[k][i] = decode<D, S, C>(a, pop + (int64_t)(k * Q + j) * a.stride + at, k, i);
+            f[k][i] = Codec<S>::load(pop + (int64_t)(k * Q + j) * a.stride + at);
         }
 
-    ideal_collide<D, C>(f, a.gm1, a.omega, a.src0, a.src1, a.flags);
+    // deviation storage collides on the stored deviations directly (ideal_cell.cuh)
+    ideal_collide<D, C, Codec<S>::kDev>(f, a.gm1, a.omega, a.src0, a.src1, a.flags, a.ref, a.scale,
+                                        a.inv_scale);
 
     // store: even parity sends direction i to slot (opp i, x);
     //        odd parity sends direction i to slot (i, x + c_i)
@@ -101,7 +88,7 @@ __global__ void __launch_bounds__(kBlockX) k_ideal_step(const IdealArgs<C> a)
         for (int i = 0; i < Q; ++i) {
             const int j = ODD ? i : opp_axis(i);
             const int64_t at = ODD ? nb[i] : cell;
-            encode<D, S, C>(a, pop + (int64_t)(k * Q + j) * a.stride + at, k, i, f[k][i]);
+            Codec<S>::store(pop + (int64_t)(k * Q + j) * a.stride + at, f[k][i]);
         }
 }
 
@@ -307,14 +294,15 @@ template <class C> IdealArgs<C> make_step_args(vlbm_ctx *c)
     a.gm1 = C(d.gamma - 1.0);
     const double w0 = c->dim == 2 ? AxisSet<2>::w0 : AxisSet<3>::w0;
     const double w1 = c->dim == 2 ? AxisSet<2>::w1 : AxisSet<3>::w1;
+    const bool dev = c->storage == VLBM_F16_DEV || c->storage == VLBM_BF16_DEV;
     for (int k = 0; k < kMaxLat; ++k) {
+        const double s = dev ? d.q_scale[k] : 1.0;
         a.omega[k] = C(1.0 / d.tau[k]);
-        a.src0[k] = C(w0 * d.source[k]);
-        a.src1[k] = C(w1 * d.source[k]);
-        a.ref0[k] = C(w0 * d.q_ref[k]);
-        a.ref1[k] = C(w1 * d.q_ref[k]);
-        a.scale[k] = C(d.q_scale[k]);
-        a.inv_scale[k] = C(1.0 / d.q_scale[k]);
+        a.src0[k] = C(w0 * d.source[k] / s);
+        a.src1[k] = C(w1 * d.source[k] / s);
+        a.ref[k] = C(dev ? d.q_ref[k] : 0.0);
+        a.scale[k] = C(s);
+        a.inv_scale[k] = C(1.0 / s);
     }
     a.flags = c->d_flags;
     return a;
