@@ -50,7 +50,10 @@ def parse():
                     help="other storage forms to time and compare with FP64 ('' to skip)")
     ap.add_argument("--form-steps", type=int, default=20)
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-extra", action="store_true", help="skip the channel and batched forms")
+    ap.add_argument("--no-extra", action="store_true", help="skip the channel, batched and closure forms")
+    ap.add_argument("--extras", default="channel,batch,closure",
+                    help="which other workloads to run (comma list of channel, batch, closure)")
+    ap.add_argument("--closure-fine", type=int, default=512, help="fine grid side of the closure workload")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--seed", type=int, default=3003)
@@ -253,6 +256,39 @@ def batch_form(args, vlbm, fields, torch, stream, hbm_peak):
             "bytes_per_cell": 320, "roofline_frac_batched": gb * 1e9 * 320 / (hbm_peak * 1e9)}
 
 
+def closure_form(args, vlbm, torch, stream):
+    """Learned flux closure: coarse (fine/4)^3 + closure vs plain coarse and plain fine."""
+    from paper_2606_00641_gb300 import closure
+    nf = args.closure_fine
+    r = closure.run_experiment(fine_shape=(nf, nf, nf), train_seeds=tuple(range(5000, 5008)),
+                               val_seed=5100, test_seeds=(5101,), episodes=120)
+    cl = r["closure"]
+    t = r["tests"][0]
+    # tensor-core cost of the network per coarse step
+    N = (nf // 4) ** 3
+    flop = 2.0 * N * 27 * (8 * 32 + 32 * 32 + 32 * 24)
+    net_ms = (t["coarse_closure_ms"] - t["coarse_plain_ms"]) / r["n_eval"]
+    cl.close()
+    bf16_peak = None
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            bf16_peak = float(json.load(fh)["bf16_tflops"])
+    except (OSError, KeyError, ValueError):
+        pass
+    tflops = flop / (net_ms * 1e-3) / 1e12 if net_ms > 0 else None
+    return {"workload": "ideal MHD 3-D, fine %d^3 restricted 4x to %d^3, 8 training seeds x 32 coarse "
+                        % (nf, nf // 4) +
+                        "steps, early stopping on seed 5100, test seed 5101, Mach 1.5, tau 0.51; "
+                        "network 3 x conv3x3x3 (8->32->32->24), BF16 tensor cores",
+            "coarse_steps": r["n_eval"], "test": t, "best_validation_rel_l2": r["best_val"],
+            "train_s": r["t_train_s"], "data_s": r["t_data_s"],
+            "time_to_solution_ms": {"fine": t["fine_ms"], "coarse_plain": t["coarse_plain_ms"],
+                                    "coarse_closure": t["coarse_closure_ms"]},
+            "network_ms_per_coarse_step": net_ms, "network_gflop_per_step": flop / 1e9,
+            "network_tflops": tflops, "bf16_peak_tflops": bf16_peak,
+            "tensor_frac": (tflops / bf16_peak) if (tflops and bf16_peak) else None}
+
+
 def main():
     args = parse()
     world, rank, local = dist_env()
@@ -400,8 +436,13 @@ def main():
 
     extra = {}
     if rank == 0 and not args.no_extra:
-        extra["resistive_channel"] = channel_form(args, vlbm, fields, torch, stream, hbm_peak)
-        extra["batched_2d"] = batch_form(args, vlbm, fields, torch, stream, hbm_peak)
+        which = set(x for x in args.extras.split(",") if x)
+        if "channel" in which:
+            extra["resistive_channel"] = channel_form(args, vlbm, fields, torch, stream, hbm_peak)
+        if "batch" in which:
+            extra["batched_2d"] = batch_form(args, vlbm, fields, torch, stream, hbm_peak)
+        if "closure" in which:
+            extra["learned_closure"] = closure_form(args, vlbm, torch, stream)
 
     cpu = None
     if rank == 0 and not args.no_cpu:

@@ -36,7 +36,12 @@
  *     optional allocator hooks) and releases it in vlbm_destroy.
  *   - Streams: all device work of a context is enqueued on its stream
  *     (params.stream, or a stream the library creates when it is NULL).
- *     Calls that return host data synchronise that stream.
+ *     Calls that return host data synchronise that stream.  Device inputs
+ *     must be complete before a call enqueues work that reads them, and
+ *     device outputs are ready only after the context's stream reaches the
+ *     call's work: order other streams against the context's stream (events
+ *     or synchronisation) -- a stream created with cudaStreamNonBlocking does
+ *     not wait for the legacy default stream.
  *   - Errors: every call returns a vlbm_status; vlbm_last_error() gives a
  *     one-line reason.  After VLBM_ERR_NONPHYSICAL or VLBM_ERR_TIMEOUT the
  *     context is sticky-failed (vlbm_step returns the error) until
@@ -208,6 +213,82 @@ vlbm_status vlbm_load(vlbm_ctx *ctx, const void *buf, size_t bytes);
  * *choice receives its index.  Single-domain contexts return VLBM_OK with
  * *choice = 0. */
 vlbm_status vlbm_autotune(vlbm_ctx *ctx, int steps, int *choice);
+
+/* ------------------------------------------------------------------------
+ * Learned flux closure for coarse 3-D ideal-MHD runs (no counterpart in the
+ * paper; the paper's fluxes are exact and local, this corrects the coarse
+ * grid's discretisation error as learned from restricted fine runs).
+ *
+ * Network, per cell (3 x 3 x 3 periodic convolutions, BF16 weights and
+ * activations, FP32 accumulation on the tensor cores):
+ *   x = (Q - mu) / sigma (8 channels) -> tanh(conv 8 -> H) -> tanh(conv H -> H)
+ *   -> conv H -> 24 = y;  dPhi[k][a] = out_scale[k] * y[3k + a],  H = 32.
+ * The correction is added to the post-collision populations of the D3Q7
+ * lattices: f*_{k,+a} += dPhi/2, f*_{k,-a} -= dPhi/2 (w_moving / cs^2 = 1/2),
+ * leaving every zeroth moment unchanged: it adds dPhi to the flux carried by
+ * the populations, so every domain sum is conserved exactly.
+ * Flat parameter order: W1[H][8][27], b1[H], W2[H][H][27], b2[H], W3[24][H][27],
+ * b3[24]; tap t = 9 (dz+1) + 3 (dy+1) + (dx+1), conv(x)[o] = b[o] +
+ * sum_{c,t} W[o][c][t] x[c](p + e_t).
+ * ------------------------------------------------------------------------ */
+typedef struct vlbm_closure vlbm_closure;
+
+typedef struct {
+    int nx, ny, nz;           /* coarse grid the closure trains on (3-D, periodic) */
+    double gamma;             /* EOS of the coarse solver used in training steps */
+    double tau;               /* BGK relaxation time of the coarse solver */
+    double mu[8], sigma[8];   /* feature normalisation per conserved field */
+    double out_scale[8];      /* dPhi_k = out_scale_k * network output */
+    double lr, beta1, beta2, eps;  /* Adam */
+    void *stream;             /* cudaStream_t or NULL */
+} vlbm_closure_params;
+
+/* Allocate the network (FP32 master weights, Adam state, packed BF16
+ * fragments, activation buffers for nx*ny*nz cells) and an internal coarse
+ * context used by vlbm_closure_train_step.  Weights start at zero.
+ * nx must be a multiple of 16 and nx*ny*nz at most 2^25 (VLBM_ERR_ARG). */
+vlbm_status vlbm_closure_create(const vlbm_closure_params *p, vlbm_closure **out);
+size_t vlbm_closure_num_params(const vlbm_closure *cl);
+/* Copy count = vlbm_closure_num_params floats in the flat order above. */
+vlbm_status vlbm_closure_set_weights(vlbm_closure *cl, const float *host, size_t count);
+vlbm_status vlbm_closure_get_weights(vlbm_closure *cl, float *host, size_t count);
+
+/* Network forward on device fields Q_dev (8 x N doubles, N = nx*ny*nz):
+ * dphi_dev receives N x 24 floats (cell-major, dPhi[k][a] at 3k + a). */
+vlbm_status vlbm_closure_forward(vlbm_closure *cl, const double *Q_dev, float *dphi_dev);
+
+/* Gradient of sum(gy * y) over all cells with respect to every parameter, for
+ * the network evaluated on Q_dev; gy_dev is N x 24 floats (dL/dy, before
+ * out_scale).  grads_host receives vlbm_closure_num_params floats. */
+vlbm_status vlbm_closure_backward(vlbm_closure *cl, const double *Q_dev, const float *gy_dev,
+                                  float *grads_host);
+
+/* One Adam step on the one-coarse-step loss
+ *   L = sum_{k,x} ((Q1_k - Qt_k) / sigma_k)^2 / N,
+ * Q1 = moments after one corrected lattice Boltzmann step from f_eq(Q0_dev).
+ * Q0_dev, Qt_dev: 8 x N device doubles.  *loss receives L before the update. */
+vlbm_status vlbm_closure_train_step(vlbm_closure *cl, const double *Q0_dev, const double *Qt_dev,
+                                    double *loss);
+
+/* One Adam step on the same loss along a coarse run: the network is applied
+ * to the current state of `ctx` (a 3-D F32 ideal context on the closure's
+ * grid, with its non-equilibrium populations), `ctx` advances one corrected
+ * step, and Q1 is its new moments; Qt_dev is the target at that time.
+ * Enqueued on the context's stream; synchronises it. */
+vlbm_status vlbm_closure_train_step_ctx(vlbm_closure *cl, vlbm_ctx *ctx, const double *Qt_dev, double *loss);
+
+/* Attach (cl) or detach (NULL) a closure to a 3-D ideal-MHD context with F32
+ * storage and the closure's grid: every following vlbm_step evaluates the
+ * network on the current state and applies the correction in the fused
+ * step kernel. */
+vlbm_status vlbm_set_closure(vlbm_ctx *ctx, vlbm_closure *cl);
+void vlbm_closure_destroy(vlbm_closure *cl);
+
+/* Conservative restriction: Qc[v][X] = mean of the factor^3 fine cells of
+ * coarse cell X (fine grid nx x ny x nz, each divisible by factor), 8 fields
+ * of device doubles, enqueued on `stream`. */
+vlbm_status vlbm_restrict(const double *Qf_dev, int nx, int ny, int nz, int factor, double *Qc_dev,
+                          void *stream);
 
 /* Batched contexts: number of built tile shapes, and explicit selection of
  * one (0 <= shape < vlbm_tile_shapes; VLBM_ERR_ARG otherwise).  Single-domain

@@ -1,0 +1,253 @@
+"""Training and evaluation of the learned flux closure (coarse 3-D ideal MHD).
+
+Everything numerical runs in the library's kernels (fine and coarse steps,
+restriction, network forward/backward, Adam); this module only orders the
+calls and keeps device buffers (torch tensors) alive.
+
+Set-up (acoustic scaling): a coarse cell is factor^3 fine cells and one coarse
+step spans `factor` fine steps, so the lattice-unit fields of the restricted
+fine run are valid coarse-lattice fields at the same tau.  Training pairs are
+(R Q_fine(n factor), R Q_fine((n+1) factor)) with R the conservative block
+average; the loss is the one-coarse-step error of the corrected coarse step.
+"""
+from __future__ import annotations
+
+import time
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import fields, vlbm
+
+
+@dataclass
+class ClosureRun:
+    rel_l2_plain: float
+    rel_l2_closure: float
+    fine_ms: float
+    coarse_plain_ms: float
+    coarse_closure_ms: float
+    steps_coarse: int
+
+
+def _field_kwargs(mach):
+    return dict(mach=mach, beta=1.0, cfl=0.2, k_rho=2, k_u=2, k_b=2)
+
+
+def fine_trajectory(fine_shape, factor, seed, mach, n_pairs, tau, torch, stream, warm=0):
+    """Restricted states R Q(n factor), n = 0..n_pairs, of one fine run (device tensors)."""
+    f0 = fields.ideal_fields(fine_shape, seed, device="cuda", **_field_kwargs(mach))
+    p = vlbm.make_params(shape=fine_shape, storage="f32", gamma=f0.gamma, tau=tau, stream=stream.cuda_stream)
+    coarse_shape = tuple(n // factor for n in fine_shape)
+    out = []
+    with vlbm.Context(p) as ctx:
+        st = vlbm.vlbm_init_fields_device(ctx.ptr, 0, f0.Q.data_ptr())
+        if st != vlbm.VLBM_OK:
+            raise RuntimeError("fine init: " + vlbm.status_string(st))
+        del f0
+        if warm:
+            ctx.step(warm)
+        Qf = torch.empty((8,) + tuple(fine_shape), dtype=torch.float64, device="cuda")
+        for n in range(n_pairs + 1):
+            if n:
+                ctx.step(factor)
+            vlbm.vlbm_moments_device(ctx.ptr, 0, Qf.data_ptr())
+            Qc = torch.empty((8,) + coarse_shape, dtype=torch.float64, device="cuda")
+            vlbm.vlbm_restrict(Qf.data_ptr(), fine_shape, factor, Qc.data_ptr(), stream.cuda_stream)
+            out.append(Qc)
+        stream.synchronize()
+        if ctx.sync() != vlbm.VLBM_OK:
+            raise RuntimeError("fine run became nonphysical")
+    return out
+
+
+def normalisation(states):
+    """Per-field mean, spread and output scale from training states."""
+    import torch
+    allq = torch.stack(states).transpose(0, 1).reshape(8, -1)
+    mu = allq.mean(1).cpu().numpy()
+    sigma = allq.std(1).cpu().numpy()
+    amp = allq.abs().amax(1).cpu().numpy()
+    sigma = np.maximum(sigma, 1e-3 * amp + 1e-30)
+    return mu, sigma
+
+
+def train(closure, trajectories, steps, rng, log_every=0):
+    """Adam steps on random (state, next state) pairs drawn from the trajectories,
+    each coarse step started from the equilibrium of the restricted state."""
+    losses = []
+    for it in range(steps):
+        tr = trajectories[rng.integers(len(trajectories))]
+        n = int(rng.integers(len(tr) - 1))
+        losses.append(closure.train_step(tr[n].data_ptr(), tr[n + 1].data_ptr()))
+        if log_every and it % log_every == 0:
+            print("closure train step %d loss %.4e" % (it, losses[-1]), flush=True)
+    return losses
+
+
+def train_in_the_loop(closure, trajectories, episodes, gamma, tau, stream, rng, rollout=None, log_every=0):
+    """Solver-in-the-loop training: each episode restarts a coarse run from the
+    restricted fine state at a random time and advances it with the current
+    closure, one Adam step per coarse step against the restricted fine state
+    of the same time (gradient through the last step only)."""
+    losses = []
+    shape = tuple(trajectories[0][0].shape[1:])
+    p = vlbm.make_params(shape=shape, storage="f32", gamma=gamma, tau=tau, stream=stream.cuda_stream)
+    with vlbm.Context(p) as ctx:
+        for ep in range(episodes):
+            tr = trajectories[rng.integers(len(trajectories))]
+            n_roll = rollout or (len(tr) - 1)
+            start = int(rng.integers(len(tr) - n_roll)) if n_roll < len(tr) - 1 else 0
+            st = vlbm.vlbm_init_fields_device(ctx.ptr, 0, tr[start].data_ptr())
+            if st != vlbm.VLBM_OK:
+                raise RuntimeError("coarse init: " + vlbm.status_string(st))
+            for n in range(start + 1, start + n_roll + 1):
+                losses.append(closure.train_step_ctx(ctx.ptr, tr[n].data_ptr()))
+            if ctx.sync() != vlbm.VLBM_OK:
+                losses.append(float("nan"))
+            if log_every and ep % log_every == 0:
+                print("closure episode %d loss %.4e" % (ep, losses[-1]), flush=True)
+    return losses
+
+
+def train_with_validation(closure, trajectories, episodes, gamma, tau, stream, rng, validate, val_every=10,
+                          rollout=4, log=None):
+    """In-the-loop training with early stopping: every `val_every` episodes
+    `validate()` returns the held-out error of the corrected coarse run; the
+    weights with the lowest validation error (the zero-output start included)
+    are restored at the end.  Returns (best error, history)."""
+    best_w = closure.get_weights()
+    best = validate()
+    history = [(0, best)]
+    done = 0
+    while done < episodes:
+        n = min(val_every, episodes - done)
+        train_in_the_loop(closure, trajectories, n, gamma, tau, stream, rng, rollout=rollout)
+        done += n
+        err = validate()
+        history.append((done, err))
+        if log:
+            log("episode %d validation error %.4e (best %.4e)" % (done, err, best))
+        if np.isfinite(err) and err < best:
+            best, best_w = err, closure.get_weights()
+    closure.set_weights(best_w)
+    return best, history
+
+
+@dataclass
+class FineReference:
+    Qc0: object          # restricted initial state (device, 8 x coarse cells)
+    Qref: object         # restricted fine state after n_coarse * factor fine steps
+    fine_ms: float       # device time of the fine steps
+    gamma: float
+    n_coarse: int
+
+
+def fine_reference(fine_shape, factor, seed, mach, n_coarse, tau, torch, stream):
+    """Run the fine solver once and keep the restricted start and end states."""
+    coarse_shape = tuple(n // factor for n in fine_shape)
+    f0 = fields.ideal_fields(fine_shape, seed, device="cuda", **_field_kwargs(mach))
+    gamma = f0.gamma
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p = vlbm.make_params(shape=fine_shape, storage="f32", gamma=gamma, tau=tau, stream=stream.cuda_stream)
+    Qc0 = torch.empty((8,) + coarse_shape, dtype=torch.float64, device="cuda")
+    Qref = torch.empty_like(Qc0)
+    with vlbm.Context(p) as ctx:
+        vlbm.vlbm_init_fields_device(ctx.ptr, 0, f0.Q.data_ptr())
+        del f0
+        Qf = torch.empty((8,) + tuple(fine_shape), dtype=torch.float64, device="cuda")
+        vlbm.vlbm_moments_device(ctx.ptr, 0, Qf.data_ptr())
+        vlbm.vlbm_restrict(Qf.data_ptr(), fine_shape, factor, Qc0.data_ptr(), stream.cuda_stream)
+        stream.synchronize()
+        ev0.record(stream)
+        ctx.step(n_coarse * factor)
+        ev1.record(stream)
+        ev1.synchronize()
+        fine_ms = ev0.elapsed_time(ev1)
+        vlbm.vlbm_moments_device(ctx.ptr, 0, Qf.data_ptr())
+        vlbm.vlbm_restrict(Qf.data_ptr(), fine_shape, factor, Qref.data_ptr(), stream.cuda_stream)
+        stream.synchronize()
+        if ctx.sync() != vlbm.VLBM_OK:
+            raise RuntimeError("fine reference run became nonphysical")
+    return FineReference(Qc0=Qc0, Qref=Qref, fine_ms=fine_ms, gamma=gamma, n_coarse=n_coarse)
+
+
+def coarse_error(ref, closure, tau, torch, stream):
+    """Relative L2 error (normalised per field by the reference spread) of the
+    coarse run from ref.Qc0 after ref.n_coarse steps, with `closure` (or None),
+    its device time and final status."""
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    shape = tuple(ref.Qc0.shape[1:])
+    pc = vlbm.make_params(shape=shape, storage="f32", gamma=ref.gamma, tau=tau, stream=stream.cuda_stream)
+    with vlbm.Context(pc) as c:
+        vlbm.vlbm_init_fields_device(c.ptr, 0, ref.Qc0.data_ptr())
+        if closure is not None:
+            vlbm.vlbm_set_closure(c.ptr, closure)
+        stream.synchronize()
+        ev0.record(stream)
+        c.step(ref.n_coarse)
+        ev1.record(stream)
+        ev1.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        out = torch.empty_like(ref.Qc0)
+        vlbm.vlbm_moments_device(c.ptr, 0, out.data_ptr())
+        stream.synchronize()
+        vlbm.vlbm_set_closure(c.ptr, None)
+        st = c.sync()
+    scale = ref.Qref.reshape(8, -1).std(1) + 1e-30
+    d = (out - ref.Qref).reshape(8, -1) / scale[:, None]
+    return float(d.pow(2).mean().sqrt()), ms, st
+
+
+def evaluate(closure, fine_shape, factor, seed, mach, n_coarse, tau, torch, stream, ref=None):
+    """Plain and closure-corrected coarse runs against the restricted fine run."""
+    if ref is None:
+        ref = fine_reference(fine_shape, factor, seed, mach, n_coarse, tau, torch, stream)
+    e_p, ms_p, st_p = coarse_error(ref, None, tau, torch, stream)
+    e_c, ms_c, st_c = coarse_error(ref, closure, tau, torch, stream)
+    return ClosureRun(rel_l2_plain=e_p, rel_l2_closure=e_c, fine_ms=ref.fine_ms, coarse_plain_ms=ms_p,
+                      coarse_closure_ms=ms_c, steps_coarse=n_coarse), (st_p, st_c)
+
+
+def init_weights(rng, hidden=32, last_scale=0.1):
+    """He-style random weights in the library's flat order (last layer scaled)."""
+    parts = []
+    for o, c, s in ((hidden, 8, 1.0), (hidden, hidden, 1.0), (24, hidden, last_scale)):
+        parts.append(rng.normal(0.0, s * np.sqrt(2.0 / (27 * c)), size=o * c * 27))
+        parts.append(np.zeros(o))
+    return np.concatenate(parts).astype(np.float32)
+
+
+def run_experiment(fine_shape=(512, 512, 512), factor=4, train_seeds=tuple(range(5000, 5008)), val_seed=5100,
+                   test_seeds=(5101, 5102, 5103), mach=1.5, tau=0.51, n_pairs=32, n_eval=32, episodes=150,
+                   val_every=10, rollout=4, lr=1e-5, out_scale_rel=0.005, seed=0, log=None):
+    """Train in the loop on restricted fine runs of `train_seeds` with early
+    stopping on `val_seed`; report plain and corrected coarse errors and
+    times on the held-out `test_seeds`."""
+    import torch
+    stream = torch.cuda.Stream()
+    t0 = time.perf_counter()
+    trajs = [fine_trajectory(fine_shape, factor, s, mach, n_pairs, tau, torch, stream) for s in train_seeds]
+    t_data = time.perf_counter() - t0
+    mu, sigma = normalisation([q for tr in trajs for q in tr])
+    coarse_shape = tuple(n // factor for n in fine_shape)
+    gamma = 5.0 / 3.0
+    cl = vlbm.Closure(coarse_shape, gamma, tau, mu, sigma, out_scale_rel * sigma, lr=lr,
+                      stream=stream.cuda_stream)
+    rng = np.random.default_rng(seed)
+    cl.set_weights(init_weights(rng, last_scale=0.0))
+    vref = fine_reference(fine_shape, factor, val_seed, mach, n_eval, tau, torch, stream)
+    t0 = time.perf_counter()
+    best, hist = train_with_validation(cl, trajs, episodes, gamma, tau, stream, rng,
+                                       lambda: coarse_error(vref, cl, tau, torch, stream)[0],
+                                       val_every=val_every, rollout=rollout, log=log)
+    t_train = time.perf_counter() - t0
+    del trajs
+    tests = []
+    for s in test_seeds:
+        res, st = evaluate(cl, fine_shape, factor, s, mach, n_eval, tau, torch, stream)
+        tests.append({"seed": s, "rel_l2_plain_coarse": res.rel_l2_plain, "rel_l2_closure_coarse": res.rel_l2_closure,
+                      "fine_ms": res.fine_ms, "coarse_plain_ms": res.coarse_plain_ms,
+                      "coarse_closure_ms": res.coarse_closure_ms, "status": [int(v) for v in st]})
+    return {"closure": cl, "best_val": best, "history": hist, "tests": tests, "t_data_s": t_data,
+            "t_train_s": t_train, "fine_shape": fine_shape, "coarse_shape": coarse_shape, "n_eval": n_eval}

@@ -1,0 +1,845 @@
+// k_closure.cu -- learned flux closure: BF16 tensor-core 3x3x3 convolutions
+// (forward, backward-data, backward-weight), training step and application.
+//
+// The closure corrects the fluxes of a coarse ideal-MHD run (8 x D3Q7, FP32):
+// a 3-layer periodic conv net maps the normalised conserved fields to
+// dPhi[k][a], which the fused step kernel adds to the post-collision
+// populations (f*_{k,+-a} +-= dPhi/2; see include/vlbm.h).
+//
+// Convolutions are implicit GEMMs on mma.sync.m16n8k16 (BF16 in, FP32
+// accumulate): M = cells (each warp owns 16 consecutive cells of one x-row),
+// N = output channels (8 per n-tile), K = 27 taps x input channels, walked
+// in chunks of 16 (Cin = 8: two taps per chunk; Cin = 32: half a tap).
+// Activations are channels-last BF16 ([cell][8] or [cell][32]); weights are
+// re-packed after every update into the per-lane B-fragment order, so a
+// lane's operand is one 8-byte load.  The backward-data pass is the same
+// kernel on the transposed, tap-mirrored weights; the weight gradient is a
+// second mma kernel with K = cells, one CTA per (cell block, tap).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "vlbm_internal.cuh"
+
+namespace vlbm {
+namespace {
+
+constexpr int kH = 32;          // hidden channels
+constexpr int kOut = 24;        // 8 fields x 3 axes
+constexpr int kConvThreads = 128;
+constexpr int kWgradCells = 2048;  // cells per weight-gradient CTA
+
+typedef __nv_bfloat16 bf16;
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                         uint32_t b0, uint32_t b1)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(bf16 lo, bf16 hi)
+{
+    return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
+
+// Periodic offsets of the 3 x 3 x 3 neighbourhood of a cell (x, y, z):
+// neighbour(dx, dy, dz) = cell + ox[dx+1] + oy[dy+1] + oz[dz+1].
+struct Nbr {
+    int ox[3], oy[3], oz[3];
+};
+
+__device__ __forceinline__ Nbr nbr_of(int x, int y, int z, int nx, int ny, int nz)
+{
+    Nbr n;
+    const int plane = nx * ny, vol = plane * nz;
+    n.ox[0] = x > 0 ? -1 : nx - 1;
+    n.ox[1] = 0;
+    n.ox[2] = x + 1 < nx ? 1 : 1 - nx;
+    n.oy[0] = y > 0 ? -nx : plane - nx;
+    n.oy[1] = 0;
+    n.oy[2] = y + 1 < ny ? nx : nx - plane;
+    n.oz[0] = z > 0 ? -plane : vol - plane;
+    n.oz[1] = 0;
+    n.oz[2] = z + 1 < nz ? plane : plane - vol;
+    return n;
+}
+
+__device__ __forceinline__ int tap_nbr(const Nbr &n, int cell, int t)
+{
+    return cell + n.ox[t % 3] + n.oy[(t / 3) % 3] + n.oz[t / 9];
+}
+
+__device__ __forceinline__ Nbr nbr_cell(int cell, int nx, int ny, int nz)
+{
+    const int x = cell % nx;
+    const int r = cell / nx;
+    return nbr_of(x, r % ny, r / ny, nx, ny, nz);
+}
+
+// ---------------------------------------------------------------------------
+// implicit-GEMM convolution (forward and backward-data)
+// ---------------------------------------------------------------------------
+
+struct ConvEpilogue {
+    const float *bias;     // per output channel, or null
+    int tanh_act;          // apply tanh
+    const bf16 *deriv;     // multiply by (1 - d^2), d = deriv[cell*32 + col], or null
+    const float *scale;    // per output channel, or null
+    bf16 *out_bf;          // BF16 output with stride os, or null
+    float *out_f;          // FP32 output with stride os, or null
+    int os;
+};
+
+template <int CS, int NT>
+__global__ void __launch_bounds__(kConvThreads) k_conv(const bf16 *__restrict__ act, int nx, int ny, int nz,
+                                                       const uint2 *__restrict__ frag, const ConvEpilogue e)
+{
+    constexpr int NCHUNK = CS == 8 ? 14 : 54;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane >> 2, tg = lane & 3;
+    const int N = nx * ny * nz;
+    const int cell0 = (blockIdx.x * (kConvThreads / 32) + warp) * 16;
+    if (cell0 >= N) return;  // nx % 16 == 0: a warp's 16 cells are one x-row segment
+    const int cA = cell0 + g, cB = cell0 + g + 8;
+    const Nbr nA = nbr_cell(cA, nx, ny, nz), nB = nbr_cell(cB, nx, ny, nz);
+    const uint32_t *act32 = reinterpret_cast<const uint32_t *>(act);
+    float acc[NT][4];
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
+
+#pragma unroll 2
+    for (int j = 0; j < NCHUNK; ++j) {
+        uint32_t a0, a1, a2, a3;
+        if (CS == 32) {
+            const int t = j >> 1, h = j & 1;
+            const uint32_t *pA = act32 + (size_t)tap_nbr(nA, cA, t) * 16 + h * 8;
+            const uint32_t *pB = act32 + (size_t)tap_nbr(nB, cB, t) * 16 + h * 8;
+            a0 = pA[tg];
+            a2 = pA[4 + tg];
+            a1 = pB[tg];
+            a3 = pB[4 + tg];
+        } else {
+            const int t0 = 2 * j, t1 = 2 * j + 1;
+            a0 = act32[(size_t)tap_nbr(nA, cA, t0) * 4 + tg];
+            a1 = act32[(size_t)tap_nbr(nB, cB, t0) * 4 + tg];
+            if (t1 < 27) {
+                a2 = act32[(size_t)tap_nbr(nA, cA, t1) * 4 + tg];
+                a3 = act32[(size_t)tap_nbr(nB, cB, t1) * 4 + tg];
+            } else {
+                a2 = a3 = 0u;
+            }
+        }
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) {
+            const uint2 b = __ldg(frag + ((size_t)j * NT + nt) * 32 + lane);
+            mma_bf16(acc[nt], a0, a1, a2, a3, b.x, b.y);
+        }
+    }
+
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt) {
+        const int col = nt * 8 + 2 * tg;
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            const int cell = half ? cB : cA;
+            float v0 = acc[nt][2 * half], v1 = acc[nt][2 * half + 1];
+            if (e.bias) {
+                v0 += e.bias[col];
+                v1 += e.bias[col + 1];
+            }
+            if (e.tanh_act) {
+                v0 = tanhf(v0);
+                v1 = tanhf(v1);
+            }
+            if (e.deriv) {
+                const float d0 = __bfloat162float(e.deriv[(size_t)cell * 32 + col]);
+                const float d1 = __bfloat162float(e.deriv[(size_t)cell * 32 + col + 1]);
+                v0 *= 1.f - d0 * d0;
+                v1 *= 1.f - d1 * d1;
+            }
+            if (e.scale) {
+                v0 *= e.scale[col];
+                v1 *= e.scale[col + 1];
+            }
+            if (e.out_bf) {
+                __nv_bfloat162 o;
+                o.x = __float2bfloat16_rn(v0);
+                o.y = __float2bfloat16_rn(v1);
+                *reinterpret_cast<__nv_bfloat162 *>(e.out_bf + (size_t)cell * e.os + col) = o;
+            } else {
+                *reinterpret_cast<float2 *>(e.out_f + (size_t)cell * e.os + col) = make_float2(v0, v1);
+            }
+        }
+    }
+}
+
+// B-fragment packing.  Chunk j, n-tile nt, lane l (g = l/4, tg = l%4) holds
+// b0 = B[2tg..2tg+1][n], b1 = B[2tg+8..2tg+9][n] with n = 8 nt + g, where
+// B[k][n] is the weight of K-index k of chunk j for output channel n.
+// Forward:   B[(t,c)][n] = W[n][c][t].
+// Transpose (backward-data): B[(t,c)][n] = W[c][n][26 - t]  (input c = a
+// forward output channel, output n = a forward input channel).
+__global__ void k_pack(const float *__restrict__ W, int cout, int cin, int CS, int NT, int transpose,
+                       uint2 *__restrict__ frag)
+{
+    const int nchunk = CS == 8 ? 14 : 54;
+    const int total = nchunk * NT * 32;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= total) return;
+    const int lane = idx & 31, nt = (idx >> 5) % NT, j = (idx >> 5) / NT;
+    const int g = lane >> 2, tg = lane & 3;
+    const int n = nt * 8 + g;
+    float v[4];
+    const int ks[4] = {2 * tg, 2 * tg + 1, 2 * tg + 8, 2 * tg + 9};
+    for (int q = 0; q < 4; ++q) {
+        const int k = ks[q];
+        int t, c;
+        if (CS == 32) {
+            t = j >> 1;
+            c = (j & 1) * 16 + k;
+        } else {
+            t = 2 * j + (k >= 8 ? 1 : 0);
+            c = k & 7;
+        }
+        float w = 0.f;
+        if (t < 27) {
+            if (!transpose) {
+                if (n < cout && c < cin) w = W[((size_t)n * cin + c) * 27 + t];
+            } else {
+                if (n < cin && c < cout) w = W[((size_t)c * cin + n) * 27 + (26 - t)];
+            }
+        }
+        v[q] = w;
+    }
+    uint2 out;
+    out.x = pack_bf16(__float2bfloat16_rn(v[0]), __float2bfloat16_rn(v[1]));
+    out.y = pack_bf16(__float2bfloat16_rn(v[2]), __float2bfloat16_rn(v[3]));
+    frag[idx] = out;
+}
+
+// ---------------------------------------------------------------------------
+// weight gradient: gW[o][c][t] += sum_cells gz[cell][o] * a[cell + e_t][c]
+// A = gz^T (M = 32 output channels, K = cells), B = shifted inputs (K = cells,
+// N = input channels).  One CTA per (block of kWgradCells cells, tap t).
+// ---------------------------------------------------------------------------
+template <int CSIN>
+__global__ void __launch_bounds__(kConvThreads) k_wgrad(const bf16 *__restrict__ gz, const bf16 *__restrict__ a,
+                                                        int nx, int ny, int nz, int cout, int cin,
+                                                        float *__restrict__ gW)
+{
+    constexpr int NTW = CSIN / 8;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane >> 2, tg = lane & 3;
+    const int t = blockIdx.y;
+    const int N = nx * ny * nz;
+    const unsigned short *gz16 = reinterpret_cast<const unsigned short *>(gz);
+    const unsigned short *a16 = reinterpret_cast<const unsigned short *>(a);
+    float acc[2][NTW][4];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < NTW; ++nt) acc[mt][nt][0] = acc[mt][nt][1] = acc[mt][nt][2] = acc[mt][nt][3] = 0.f;
+
+    const int per_warp = kWgradCells / (kConvThreads / 32);
+    const int begin = blockIdx.x * kWgradCells + warp * per_warp;
+    for (int c0 = begin; c0 < begin + per_warp && c0 < N; c0 += 16) {
+        // this lane's four cells of the k-step and their tap neighbours
+        int cells[4] = {c0 + 2 * tg, c0 + 2 * tg + 1, c0 + 2 * tg + 8, c0 + 2 * tg + 9};
+        int nbs[4];
+        bool ok[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            ok[q] = cells[q] < N;
+            const int cc = ok[q] ? cells[q] : 0;
+            nbs[q] = tap_nbr(nbr_cell(cc, nx, ny, nz), cc, t);
+        }
+        auto gzv = [&](int q, int o) -> uint32_t {
+            return ok[q] ? (uint32_t)gz16[(size_t)cells[q] * 32 + o] : 0u;
+        };
+        auto av = [&](int q, int c) -> uint32_t { return ok[q] ? (uint32_t)a16[(size_t)nbs[q] * CSIN + c] : 0u; };
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+            const int olo = mt * 16 + g, ohi = olo + 8;
+            const uint32_t a0 = gzv(0, olo) | (gzv(1, olo) << 16);
+            const uint32_t a1 = gzv(0, ohi) | (gzv(1, ohi) << 16);
+            const uint32_t a2 = gzv(2, olo) | (gzv(3, olo) << 16);
+            const uint32_t a3 = gzv(2, ohi) | (gzv(3, ohi) << 16);
+#pragma unroll
+            for (int nt = 0; nt < NTW; ++nt) {
+                const int c = nt * 8 + g;
+                const uint32_t b0 = av(0, c) | (av(1, c) << 16);
+                const uint32_t b1 = av(2, c) | (av(3, c) << 16);
+                mma_bf16(acc[mt][nt], a0, a1, a2, a3, b0, b1);
+            }
+        }
+    }
+    // reduce the four warps in shared memory, then one atomic add per weight
+    __shared__ float red[kConvThreads / 32][32][CSIN];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < NTW; ++nt) {
+            const int o = mt * 16 + g, c = nt * 8 + 2 * tg;
+            red[warp][o][c] = acc[mt][nt][0];
+            red[warp][o][c + 1] = acc[mt][nt][1];
+            red[warp][o + 8][c] = acc[mt][nt][2];
+            red[warp][o + 8][c + 1] = acc[mt][nt][3];
+        }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < 32 * CSIN; idx += blockDim.x) {
+        const int o = idx / CSIN, c = idx % CSIN;
+        if (o >= cout || c >= cin) continue;
+        float s = 0.f;
+        for (int w = 0; w < kConvThreads / 32; ++w) s += red[w][o][c];
+        atomicAdd(gW + ((size_t)o * cin + c) * 27 + t, s);
+    }
+}
+
+// bias gradient: gb[o] += sum_cells gz[cell][o]
+__global__ void __launch_bounds__(256) k_bgrad(const bf16 *__restrict__ gz, int N, int cout, float *__restrict__ gb)
+{
+    __shared__ float red[256];
+    const int o = blockIdx.y;
+    float s = 0.f;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x)
+        s += __bfloat162float(gz[(size_t)c * 32 + o]);
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+        if ((int)threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && o < cout) atomicAdd(gb + o, red[0]);
+}
+
+// ---------------------------------------------------------------------------
+// elementwise pieces
+// ---------------------------------------------------------------------------
+
+struct Norm {
+    float mu[8], inv_sigma[8];
+};
+
+__global__ void k_features(const double *__restrict__ Q, int N, const Norm n, bf16 *__restrict__ x)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    __align__(16) bf16 v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = __float2bfloat16_rn(((float)Q[(size_t)k * N + c] - n.mu[k]) * n.inv_sigma[k]);
+    *reinterpret_cast<uint4 *>(x + (size_t)c * 8) = *reinterpret_cast<const uint4 *>(v);
+}
+
+struct LossArgs {
+    float inv_sigma[8];
+    float coef;  // 2 / N
+};
+
+// r = (Q1 - Qt)/sigma, loss += sum r^2 / N, gq = 2 r / (sigma N)
+__global__ void __launch_bounds__(256) k_loss(const double *__restrict__ q1, const double *__restrict__ qt, int N,
+                                              const LossArgs la, float *__restrict__ gq, double *__restrict__ loss)
+{
+    __shared__ double red[256];
+    double s = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 8 * N; i += gridDim.x * blockDim.x) {
+        const int k = i / N;
+        const double r = (q1[i] - qt[i]) * la.inv_sigma[k];
+        s += r * r;
+        gq[i] = (float)(la.coef * r * la.inv_sigma[k]);
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+        if ((int)threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicAdd(loss, red[0] * 0.5 * la.coef);
+}
+
+// dL/dy[cell][3k+a] = out_scale_k * (gq_k(x + e_a) - gq_k(x - e_a)) / 2, zero for 24..31
+__global__ void k_grad_out(const float *__restrict__ gq, int nx, int ny, int nz, const float *__restrict__ col_scale,
+                           bf16 *__restrict__ gy)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int N = nx * ny * nz;
+    if (c >= N) return;
+    const Nbr n = nbr_cell(c, nx, ny, nz);
+    const int plus[3] = {c + n.ox[2], c + n.oy[2], c + n.oz[2]};
+    const int minus[3] = {c + n.ox[0], c + n.oy[0], c + n.oz[0]};
+    __align__(16) bf16 v[32];
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            v[3 * k + a] = __float2bfloat16_rn(col_scale[3 * k + a] * 0.5f *
+                                               (gq[(size_t)k * N + plus[a]] - gq[(size_t)k * N + minus[a]]));
+#pragma unroll
+    for (int j = kOut; j < 32; ++j) v[j] = __float2bfloat16_rn(0.f);
+    uint4 *dst = reinterpret_cast<uint4 *>(gy + (size_t)c * 32);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) dst[q] = reinterpret_cast<const uint4 *>(v)[q];
+}
+
+// dL/dy given as [N][24] floats -> BF16 [N][32] with zero padding
+__global__ void k_gy_from_f32(const float *__restrict__ src, int N, bf16 *__restrict__ gy)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N * 32) return;
+    const int c = i / 32, j = i % 32;
+    gy[i] = __float2bfloat16_rn(j < kOut ? src[(size_t)c * kOut + j] : 0.f);
+}
+
+struct AdamArgs {
+    float lr, b1, b2, eps, c1, c2;  // c1 = 1/(1 - b1^t), c2 = 1/(1 - b2^t)
+};
+
+__global__ void k_adam(float *__restrict__ th, float *__restrict__ m, float *__restrict__ v,
+                       const float *__restrict__ g, int n, const AdamArgs a)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = a.b1 * m[i] + (1.f - a.b1) * gi;
+    const float vi = a.b2 * v[i] + (1.f - a.b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    th[i] -= a.lr * (mi * a.c1) / (sqrtf(vi * a.c2) + a.eps);
+}
+
+__global__ void k_restrict(const double *__restrict__ qf, int nx, int ny, int nz, int f, double *__restrict__ qc)
+{
+    const int cx = nx / f, cy = ny / f, cz = nz / f;
+    const int Nc = cx * cy * cz;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 8 * Nc) return;
+    const int k = i / Nc, C = i % Nc;
+    const int X = C % cx, Y = (C / cx) % cy, Z = C / (cx * cy);
+    const int64_t Nf = (int64_t)nx * ny * nz;
+    double s = 0.0;
+    for (int dz = 0; dz < f; ++dz)
+        for (int dy = 0; dy < f; ++dy)
+            for (int dx = 0; dx < f; ++dx)
+                s += qf[k * Nf + (X * f + dx) + (int64_t)nx * ((Y * f + dy) + (int64_t)ny * (Z * f + dz))];
+    qc[i] = s / (double)(f * f * f);
+}
+
+}  // namespace
+}  // namespace vlbm
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+
+struct vlbm_closure {
+    vlbm_closure_params p{};
+    int nx = 0, ny = 0, nz = 0, N = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    size_t nparam = 0;
+    size_t off_W[3]{}, off_b[3]{};
+    float *theta = nullptr, *mom = nullptr, *vel = nullptr, *grad = nullptr;
+    uint2 *frag_fwd[3]{}, *frag_bwd[3]{};
+    vlbm::bf16 *x = nullptr, *a1 = nullptr, *a2 = nullptr, *gy = nullptr, *gz = nullptr;
+    float *dphi = nullptr, *gq = nullptr, *col_scale = nullptr;
+    double *q = nullptr, *q1 = nullptr, *loss = nullptr;
+    int64_t adam_t = 0;
+    vlbm_ctx *inner = nullptr;
+    std::vector<void *> owned;
+};
+
+namespace vlbm {
+
+vlbm_status ideal_step_corrected(vlbm_ctx *c, int parity, const float *dphi);
+
+namespace {
+
+const int kCin[3] = {8, kH, kH};
+const int kCout[3] = {kH, kH, kOut};
+const int kCS[3] = {8, 32, 32};
+const int kNT[3] = {4, 4, 3};
+
+int nchunk(int cs) { return cs == 8 ? 14 : 54; }
+
+vlbm_status cl_check(cudaError_t e, const char *what) { return cuda_check(nullptr, e, what); }
+
+void *cl_alloc(vlbm_closure *cl, size_t bytes)
+{
+    void *p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    cl->owned.push_back(p);
+    return p;
+}
+
+vlbm_status pack_all(vlbm_closure *cl, cudaStream_t s)
+{
+    for (int l = 0; l < 3; ++l) {
+        const int total = nchunk(kCS[l]) * kNT[l] * 32;
+        k_pack<<<(total + 255) / 256, 256, 0, s>>>(cl->theta + cl->off_W[l], kCout[l], kCin[l], kCS[l], kNT[l], 0,
+                                                    cl->frag_fwd[l]);
+        if (l > 0) {  // transposed packs: input channels = forward outputs (stride 32), outputs = forward inputs
+            const int tt = nchunk(32) * 4 * 32;
+            k_pack<<<(tt + 255) / 256, 256, 0, s>>>(cl->theta + cl->off_W[l], kCout[l], kCin[l], 32, 4, 1,
+                                                     cl->frag_bwd[l]);
+        }
+    }
+    return cl_check(cudaGetLastError(), "closure weight packing");
+}
+
+vlbm_status conv(vlbm_closure *cl, int layer, const bf16 *in, bool transpose, const ConvEpilogue &e, cudaStream_t s)
+{
+    const int cells_per_cta = (kConvThreads / 32) * 16;
+    const unsigned grid = (unsigned)((cl->N + cells_per_cta - 1) / cells_per_cta);
+    if (!transpose) {
+        if (layer == 0)
+            k_conv<8, 4><<<grid, kConvThreads, 0, s>>>(in, cl->nx, cl->ny, cl->nz, cl->frag_fwd[0], e);
+        else if (layer == 1)
+            k_conv<32, 4><<<grid, kConvThreads, 0, s>>>(in, cl->nx, cl->ny, cl->nz, cl->frag_fwd[1], e);
+        else
+            k_conv<32, 3><<<grid, kConvThreads, 0, s>>>(in, cl->nx, cl->ny, cl->nz, cl->frag_fwd[2], e);
+    } else {
+        k_conv<32, 4><<<grid, kConvThreads, 0, s>>>(in, cl->nx, cl->ny, cl->nz, cl->frag_bwd[layer], e);
+    }
+    return cl_check(cudaGetLastError(), "closure convolution launch");
+}
+
+ConvEpilogue epi() { ConvEpilogue e{}; return e; }
+
+// network forward from device fields Q (8 x N doubles) to dphi (N x 24 floats)
+vlbm_status forward(vlbm_closure *cl, const double *Q, float *dphi, cudaStream_t s)
+{
+    Norm n{};
+    for (int k = 0; k < 8; ++k) {
+        n.mu[k] = (float)cl->p.mu[k];
+        n.inv_sigma[k] = (float)(1.0 / cl->p.sigma[k]);
+    }
+    k_features<<<(cl->N + 255) / 256, 256, 0, s>>>(Q, cl->N, n, cl->x);
+    vlbm_status st = cl_check(cudaGetLastError(), "closure features launch");
+    ConvEpilogue e = epi();
+    e.bias = cl->theta + cl->off_b[0];
+    e.tanh_act = 1;
+    e.out_bf = cl->a1;
+    e.os = 32;
+    if (st == VLBM_OK) st = conv(cl, 0, cl->x, false, e, s);
+    e.bias = cl->theta + cl->off_b[1];
+    e.out_bf = cl->a2;
+    if (st == VLBM_OK) st = conv(cl, 1, cl->a1, false, e, s);
+    e = epi();
+    e.bias = cl->theta + cl->off_b[2];
+    e.scale = cl->col_scale;
+    e.out_f = dphi;
+    e.os = kOut;
+    if (st == VLBM_OK) st = conv(cl, 2, cl->a2, false, e, s);
+    return st;
+}
+
+// gradients of sum(gy * y) into cl->grad, given gy (BF16 [N][32]) and the
+// activations of the last forward pass
+vlbm_status backward(vlbm_closure *cl, cudaStream_t s)
+{
+    vlbm_status st = cl_check(cudaMemsetAsync(cl->grad, 0, cl->nparam * sizeof(float), s), "closure grad clear");
+    const unsigned wgx = (unsigned)((cl->N + kWgradCells - 1) / kWgradCells);
+    auto wgrad = [&](int l, const bf16 *g, const bf16 *a) {
+        if (kCS[l] == 8)
+            k_wgrad<8><<<dim3(wgx, 27), kConvThreads, 0, s>>>(g, a, cl->nx, cl->ny, cl->nz, kCout[l], kCin[l],
+                                                              cl->grad + cl->off_W[l]);
+        else
+            k_wgrad<32><<<dim3(wgx, 27), kConvThreads, 0, s>>>(g, a, cl->nx, cl->ny, cl->nz, kCout[l], kCin[l],
+                                                               cl->grad + cl->off_W[l]);
+        k_bgrad<<<dim3(64, kCout[l]), 256, 0, s>>>(g, cl->N, kCout[l], cl->grad + cl->off_b[l]);
+        return cl_check(cudaGetLastError(), "closure weight gradient launch");
+    };
+    // layer 3: gy -> W3, b3; data gradient through tanh of layer 2 -> gz
+    if (st == VLBM_OK) st = wgrad(2, cl->gy, cl->a2);
+    ConvEpilogue e = epi();
+    e.deriv = cl->a2;
+    e.out_bf = cl->gz;
+    e.os = 32;
+    if (st == VLBM_OK) st = conv(cl, 2, cl->gy, true, e, s);
+    // layer 2: gz -> W2, b2; data gradient through tanh of layer 1 -> gy (reused)
+    if (st == VLBM_OK) st = wgrad(1, cl->gz, cl->a1);
+    e.deriv = cl->a1;
+    e.out_bf = cl->gy;
+    if (st == VLBM_OK) st = conv(cl, 1, cl->gz, true, e, s);
+    // layer 1
+    if (st == VLBM_OK) st = wgrad(0, cl->gy, cl->x);
+    return st;
+}
+
+}  // namespace
+}  // namespace vlbm
+
+using namespace vlbm;
+
+extern "C" {
+
+vlbm_status vlbm_closure_create(const vlbm_closure_params *p, vlbm_closure **out)
+{
+    if (!p || !out) return VLBM_ERR_ARG;
+    *out = nullptr;
+    if (p->nx < 16 || p->ny < 1 || p->nz < 1 || p->nx % 16 != 0)
+        return fail(nullptr, VLBM_ERR_ARG, "closure grid: nx must be a multiple of 16");
+    if ((int64_t)p->nx * p->ny * p->nz > (int64_t(1) << 25))
+        return fail(nullptr, VLBM_ERR_ARG, "closure grid too large (at most 2^25 cells)");
+    for (int k = 0; k < 8; ++k)
+        if (!(p->sigma[k] > 0.0)) return fail(nullptr, VLBM_ERR_ARG, "closure sigma must be > 0");
+    if (!(p->tau > 0.5) || !(p->gamma > 1.0)) return fail(nullptr, VLBM_ERR_ARG, "closure tau/gamma");
+    vlbm_closure *cl = new vlbm_closure();
+    cl->p = *p;
+    cl->nx = p->nx;
+    cl->ny = p->ny;
+    cl->nz = p->nz;
+    cl->N = p->nx * p->ny * p->nz;
+    size_t off = 0;
+    for (int l = 0; l < 3; ++l) {
+        cl->off_W[l] = off;
+        off += (size_t)kCout[l] * kCin[l] * 27;
+        cl->off_b[l] = off;
+        off += kCout[l];
+    }
+    cl->nparam = off;
+    vlbm_status st = VLBM_OK;
+    if (p->stream) {
+        cl->stream = static_cast<cudaStream_t>(p->stream);
+    } else {
+        st = cl_check(cudaStreamCreateWithFlags(&cl->stream, cudaStreamNonBlocking), "closure stream");
+        cl->own_stream = st == VLBM_OK;
+    }
+    const size_t N = cl->N;
+    bool ok = st == VLBM_OK;
+    auto A = [&](size_t bytes) -> void * {
+        void *q = ok ? cl_alloc(cl, bytes) : nullptr;
+        ok = ok && q;
+        return q;
+    };
+    cl->theta = (float *)A(cl->nparam * 4);
+    cl->mom = (float *)A(cl->nparam * 4);
+    cl->vel = (float *)A(cl->nparam * 4);
+    cl->grad = (float *)A(cl->nparam * 4);
+    for (int l = 0; l < 3; ++l) {
+        cl->frag_fwd[l] = (uint2 *)A((size_t)nchunk(kCS[l]) * kNT[l] * 32 * sizeof(uint2));
+        cl->frag_bwd[l] = (uint2 *)A((size_t)nchunk(32) * 4 * 32 * sizeof(uint2));
+    }
+    cl->x = (bf16 *)A(N * 8 * 2);
+    cl->a1 = (bf16 *)A(N * 32 * 2);
+    cl->a2 = (bf16 *)A(N * 32 * 2);
+    cl->gy = (bf16 *)A(N * 32 * 2);
+    cl->gz = (bf16 *)A(N * 32 * 2);
+    cl->dphi = (float *)A(N * kOut * 4);
+    cl->gq = (float *)A(N * 8 * 4);
+    cl->q = (double *)A(N * 8 * 8);
+    cl->q1 = (double *)A(N * 8 * 8);
+    cl->loss = (double *)A(64);
+    cl->col_scale = (float *)A(32 * 4);
+    if (!ok) {
+        vlbm_closure_destroy(cl);
+        return st != VLBM_OK ? st : fail(nullptr, VLBM_ERR_OOM, "closure allocation failed");
+    }
+    float cs[32] = {};
+    for (int j = 0; j < kOut; ++j) cs[j] = (float)p->out_scale[j / 3];
+    st = cl_check(cudaMemcpyAsync(cl->col_scale, cs, sizeof(cs), cudaMemcpyHostToDevice, cl->stream), "closure scale");
+    for (float *b : {cl->theta, cl->mom, cl->vel, cl->grad})
+        if (st == VLBM_OK) st = cl_check(cudaMemsetAsync(b, 0, cl->nparam * 4, cl->stream), "closure clear");
+    if (st == VLBM_OK) st = pack_all(cl, cl->stream);
+    if (st == VLBM_OK) {
+        vlbm_params ip;
+        vlbm_default_params(&ip);
+        ip.dim = 3;
+        ip.nx = p->nx;
+        ip.ny = p->ny;
+        ip.nz = p->nz;
+        ip.storage = VLBM_F32;
+        ip.gamma = p->gamma;
+        for (int k = 0; k < 8; ++k) ip.tau[k] = p->tau;
+        ip.stream = cl->stream;
+        st = vlbm_create(&ip, &cl->inner);
+    }
+    if (st == VLBM_OK) st = cl_check(cudaStreamSynchronize(cl->stream), "closure create");
+    if (st != VLBM_OK) {
+        vlbm_closure_destroy(cl);
+        return st;
+    }
+    *out = cl;
+    return VLBM_OK;
+}
+
+size_t vlbm_closure_num_params(const vlbm_closure *cl) { return cl ? cl->nparam : 0; }
+
+vlbm_status vlbm_closure_set_weights(vlbm_closure *cl, const float *host, size_t count)
+{
+    if (!cl || !host || count != cl->nparam) return VLBM_ERR_ARG;
+    vlbm_status st = cl_check(cudaMemcpyAsync(cl->theta, host, count * 4, cudaMemcpyHostToDevice, cl->stream),
+                              "closure weights upload");
+    if (st == VLBM_OK) st = pack_all(cl, cl->stream);
+    if (st == VLBM_OK) st = cl_check(cudaStreamSynchronize(cl->stream), "closure weights");
+    return st;
+}
+
+vlbm_status vlbm_closure_get_weights(vlbm_closure *cl, float *host, size_t count)
+{
+    if (!cl || !host || count != cl->nparam) return VLBM_ERR_ARG;
+    vlbm_status st = cl_check(cudaMemcpyAsync(host, cl->theta, count * 4, cudaMemcpyDeviceToHost, cl->stream),
+                              "closure weights download");
+    if (st == VLBM_OK) st = cl_check(cudaStreamSynchronize(cl->stream), "closure weights");
+    return st;
+}
+
+vlbm_status vlbm_closure_forward(vlbm_closure *cl, const double *Q_dev, float *dphi_dev)
+{
+    if (!cl || !Q_dev || !dphi_dev) return VLBM_ERR_ARG;
+    vlbm_status st = forward(cl, Q_dev, dphi_dev, cl->stream);
+    if (st == VLBM_OK) st = cl_check(cudaStreamSynchronize(cl->stream), "closure forward");
+    return st;
+}
+
+vlbm_status vlbm_closure_backward(vlbm_closure *cl, const double *Q_dev, const float *gy_dev, float *grads_host)
+{
+    if (!cl || !Q_dev || !gy_dev || !grads_host) return VLBM_ERR_ARG;
+    vlbm_status st = forward(cl, Q_dev, cl->dphi, cl->stream);
+    if (st == VLBM_OK) {
+        k_gy_from_f32<<<(cl->N * 32 + 255) / 256, 256, 0, cl->stream>>>(gy_dev, cl->N, cl->gy);
+        st = cl_check(cudaGetLastError(), "closure gradient input");
+    }
+    if (st == VLBM_OK) st = backward(cl, cl->stream);
+    if (st == VLBM_OK)
+        st = cl_check(cudaMemcpyAsync(grads_host, cl->grad, cl->nparam * 4, cudaMemcpyDeviceToHost, cl->stream),
+                      "closure gradient download");
+    if (st == VLBM_OK) st = cl_check(cudaStreamSynchronize(cl->stream), "closure backward");
+    return st;
+}
+
+}  // extern "C"
+
+namespace vlbm {
+namespace {
+
+// From Q1 (moments after a corrected step) and the target: loss, gradient
+// through the step (Q1 = Q_plain - delta . dPhi), backward pass, Adam step and
+// re-packing of the weights.
+vlbm_status loss_backward_update(vlbm_closure *cl, const double *Qt_dev, double *loss, cudaStream_t s)
+{
+    vlbm_status st = cl_check(cudaMemsetAsync(cl->loss, 0, sizeof(double), s), "closure loss clear");
+    if (st == VLBM_OK) {
+        LossArgs la{};
+        for (int k = 0; k < 8; ++k) la.inv_sigma[k] = (float)(1.0 / cl->p.sigma[k]);
+        la.coef = 2.0f / (float)cl->N;
+        k_loss<<<1216, 256, 0, s>>>(cl->q1, Qt_dev, cl->N, la, cl->gq, cl->loss);
+        k_grad_out<<<(cl->N + 255) / 256, 256, 0, s>>>(cl->gq, cl->nx, cl->ny, cl->nz, cl->col_scale, cl->gy);
+        st = cl_check(cudaGetLastError(), "closure loss launch");
+    }
+    if (st == VLBM_OK) st = backward(cl, s);
+    if (st == VLBM_OK) {
+        cl->adam_t += 1;
+        AdamArgs a{};
+        a.lr = (float)cl->p.lr;
+        a.b1 = (float)cl->p.beta1;
+        a.b2 = (float)cl->p.beta2;
+        a.eps = (float)cl->p.eps;
+        a.c1 = (float)(1.0 / (1.0 - std::pow(cl->p.beta1, (double)cl->adam_t)));
+        a.c2 = (float)(1.0 / (1.0 - std::pow(cl->p.beta2, (double)cl->adam_t)));
+        const int n = (int)cl->nparam;
+        k_adam<<<(n + 255) / 256, 256, 0, s>>>(cl->theta, cl->mom, cl->vel, cl->grad, n, a);
+        st = cl_check(cudaGetLastError(), "closure adam launch");
+    }
+    if (st == VLBM_OK) st = pack_all(cl, s);
+    double h = 0.0;
+    if (st == VLBM_OK) st = cl_check(cudaMemcpyAsync(&h, cl->loss, sizeof(double), cudaMemcpyDeviceToHost, s), "loss");
+    if (st == VLBM_OK) st = cl_check(cudaStreamSynchronize(s), "closure train step");
+    if (loss) *loss = h;
+    return st;
+}
+
+}  // namespace
+}  // namespace vlbm
+
+extern "C" {
+
+vlbm_status vlbm_closure_train_step(vlbm_closure *cl, const double *Q0_dev, const double *Qt_dev, double *loss)
+{
+    if (!cl || !Q0_dev || !Qt_dev) return VLBM_ERR_ARG;
+    cudaStream_t s = cl->stream;
+    vlbm_ctx *in = cl->inner;
+    // forward: network on Q0, then one corrected step from f_eq(Q0)
+    vlbm_status st = forward(cl, Q0_dev, cl->dphi, s);
+    in->step = 0;
+    if (st == VLBM_OK) st = ideal_init_range(in, 0, Q0_dev, 0, cl->N, cl->N);
+    if (st == VLBM_OK) st = ideal_step_corrected(in, 0, cl->dphi);
+    if (st == VLBM_OK) {
+        in->step = 1;
+        st = ideal_moments(in, 0, cl->q1);
+    }
+    if (st != VLBM_OK) return st;
+    return loss_backward_update(cl, Qt_dev, loss, s);
+}
+
+vlbm_status vlbm_closure_train_step_ctx(vlbm_closure *cl, vlbm_ctx *ctx, const double *Qt_dev, double *loss)
+{
+    if (!cl || !ctx || !Qt_dev) return VLBM_ERR_ARG;
+    if (ctx->batched || ctx->model != VLBM_IDEAL || ctx->dim != 3 || ctx->storage != VLBM_F32 ||
+        ctx->dom[0].nx != cl->nx || ctx->dom[0].ny != cl->ny || ctx->dom[0].nz != cl->nz)
+        return fail(ctx, VLBM_ERR_ARG, "closure training context must be a 3-D F32 ideal context on the closure grid");
+    cudaStream_t s = ctx->stream;
+    vlbm_status st = ideal_moments(ctx, 0, cl->q);
+    if (st == VLBM_OK) st = forward(cl, cl->q, cl->dphi, s);
+    if (st == VLBM_OK) st = ideal_step_corrected(ctx, (int)(ctx->step & 1), cl->dphi);
+    if (st == VLBM_OK) {
+        ctx->step += 1;
+        st = ideal_moments(ctx, 0, cl->q1);
+    }
+    if (st != VLBM_OK) return st;
+    return loss_backward_update(cl, Qt_dev, loss, s);
+}
+
+vlbm_status vlbm_restrict(const double *Qf_dev, int nx, int ny, int nz, int factor, double *Qc_dev, void *stream)
+{
+    if (!Qf_dev || !Qc_dev || factor < 1 || nx % factor || ny % factor || nz % factor || nx < 1 || ny < 1 || nz < 1)
+        return fail(nullptr, VLBM_ERR_ARG, "restrict: sizes must be divisible by the factor");
+    const int64_t Nc = (int64_t)(nx / factor) * (ny / factor) * (nz / factor);
+    if (8 * Nc >= (int64_t(1) << 31)) return fail(nullptr, VLBM_ERR_ARG, "restrict: coarse grid too large");
+    k_restrict<<<(unsigned)((8 * Nc + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(Qf_dev, nx, ny, nz,
+                                                                                               factor, Qc_dev);
+    return cl_check(cudaGetLastError(), "restrict launch");
+}
+
+void vlbm_closure_destroy(vlbm_closure *cl)
+{
+    if (!cl) return;
+    if (cl->stream) cudaStreamSynchronize(cl->stream);
+    if (cl->inner) vlbm_destroy(cl->inner);
+    for (void *q : cl->owned) cudaFree(q);
+    if (cl->own_stream && cl->stream) cudaStreamDestroy(cl->stream);
+    cudaGetLastError();
+    delete cl;
+}
+
+}  // extern "C"
+
+namespace vlbm {
+
+// Used by the step loop of a context with an attached closure: the network
+// runs on the context's current moments, then the corrected step kernel.
+vlbm_status closure_step(vlbm_ctx *c, int parity)
+{
+    vlbm_closure *cl = c->closure;
+    vlbm_status st = ideal_moments(c, 0, cl->q);
+    if (st == VLBM_OK) st = forward(cl, cl->q, cl->dphi, c->stream);
+    c->launches += 4;  // features and three convolutions (moments and the step count themselves)
+    if (st == VLBM_OK) st = ideal_step_corrected(c, parity, cl->dphi);
+    return st;
+}
+
+int closure_cells(const vlbm_closure *cl, int *nx, int *ny, int *nz)
+{
+    *nx = cl->nx;
+    *ny = cl->ny;
+    *nz = cl->nz;
+    return cl->N;
+}
+
+}  // namespace vlbm

@@ -30,6 +30,7 @@ template <class C> struct IdealArgs {
     C scale[kMaxLat];     //                    s_k
     C inv_scale[kMaxLat]; //                    1 / s_k
     unsigned *flags;
+    const float *dphi;    // closure: per-cell flux correction [cell][24], or null
 };
 
 // Linear indices of the cell's neighbours x + c_i (periodic), i in set order.
@@ -52,8 +53,10 @@ __device__ __forceinline__ void neighbours(int x, int y, int z, int nx, int ny, 
 }
 
 
-// The fused collide-and-stream step.  ODD selects the AA parity.
-template <int D, class S, class C, bool ODD>
+// The fused collide-and-stream step.  ODD selects the AA parity; CORR adds
+// the learned flux correction dPhi[k][a] to the post-collision populations
+// (f*_{k,+a} += dPhi/2, f*_{k,-a} -= dPhi/2: zero mass, first moment dPhi).
+template <int D, class S, class C, bool ODD, bool CORR = false>
 __global__ void __launch_bounds__(kBlockX) k_ideal_step(const IdealArgs<C> a)
 {
     constexpr int Q = AxisSet<D>::Q;
@@ -79,6 +82,17 @@ __global__ void __launch_bounds__(kBlockX) k_ideal_step(const IdealArgs<C> a)
     // deviation storage collides on the stored deviations directly (ideal_cell.cuh)
     ideal_collide<D, C, Codec<S>::kDev>(f, a.gm1, a.omega, a.src0, a.src1, a.flags, a.ref, a.scale,
                                         a.inv_scale);
+    if constexpr (CORR) {
+        const float *dp = a.dphi + cell * 24;
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+#pragma unroll
+            for (int ax = 0; ax < D; ++ax) {
+                const C v = C(0.5f * dp[3 * k + ax]);
+                f[k][2 * ax + 1] += v;
+                f[k][2 * ax + 2] -= v;
+            }
+    }
 
     // store: even parity sends direction i to slot (opp i, x);
     //        odd parity sends direction i to slot (i, x + c_i)
@@ -442,6 +456,21 @@ vlbm_status finish_sums(vlbm_ctx *c, int nvar, double *sums_dev)
 }
 
 vlbm_status ideal_step(vlbm_ctx *c, int parity) { return dispatch<StepF>(c, parity); }
+
+vlbm_status ideal_step_corrected(vlbm_ctx *c, int parity, const float *dphi)
+{
+    if (c->dim != 3 || c->storage != VLBM_F32) return fail(c, VLBM_ERR_UNSUPPORTED, "closure needs 3-D F32 storage");
+    const Domain &d = c->dom[0];
+    IdealArgs<float> a = make_step_args<float>(c);
+    a.dphi = dphi;
+    const dim3 grid((unsigned)((d.nx + kBlockX - 1) / kBlockX), (unsigned)d.ny, (unsigned)d.nz);
+    if (parity)
+        k_ideal_step<3, float, float, true, true><<<grid, kBlockX, 0, c->stream>>>(a);
+    else
+        k_ideal_step<3, float, float, false, true><<<grid, kBlockX, 0, c->stream>>>(a);
+    c->launches++;
+    return cuda_check(c, cudaGetLastError(), "corrected step launch");
+}
 
 vlbm_status ideal_init_range(vlbm_ctx *c, int d, const double *Q, int64_t c0, int64_t n, int64_t qstride)
 {

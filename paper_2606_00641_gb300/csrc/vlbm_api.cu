@@ -175,6 +175,7 @@ vlbm_status launch_step(vlbm_ctx *c, int parity)
 {
     if (c->batched) return batch_step(c, parity, c->tune_choice);
     if (c->model == VLBM_RESISTIVE) return resistive_step(c, parity);
+    if (c->closure) return closure_step(c, parity);
     return ideal_step(c, parity);
 }
 
@@ -619,6 +620,22 @@ vlbm_status vlbm_autotune(vlbm_ctx *c, int steps, int *choice)
     if (best_choice != c->tune_choice) drop_graphs(c);
     c->tune_choice = best_choice;
     *choice = best_choice;
+    return VLBM_OK;
+}
+
+vlbm_status vlbm_set_closure(vlbm_ctx *c, vlbm_closure *cl)
+{
+    if (!c) return VLBM_ERR_ARG;
+    if (cl) {
+        int nx, ny, nz;
+        closure_cells(cl, &nx, &ny, &nz);
+        if (c->batched || c->model != VLBM_IDEAL || c->dim != 3 || c->storage != VLBM_F32)
+            return fail(c, VLBM_ERR_UNSUPPORTED, "the closure applies to single 3-D ideal-MHD F32 contexts");
+        if (c->dom[0].nx != nx || c->dom[0].ny != ny || c->dom[0].nz != nz)
+            return fail(c, VLBM_ERR_ARG, "closure grid differs from the context grid");
+    }
+    drop_graphs(c);
+    c->closure = cl;
     return VLBM_OK;
 }
 

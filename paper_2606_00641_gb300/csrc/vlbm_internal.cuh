@@ -137,6 +137,9 @@ struct vlbm_ctx {
     int tune_choice = 0;
     void *d_dom = nullptr;              // device copy of the domain table
 
+    // learned flux closure applied in every step (not owned)
+    struct vlbm_closure *closure = nullptr;
+
     // allocator
     std::vector<std::pair<void *, size_t>> owned;
 };
@@ -169,6 +172,11 @@ vlbm_status resistive_sums(vlbm_ctx *c, int d, double *sums_dev);
 vlbm_status batch_prepare(vlbm_ctx *c);
 vlbm_status batch_step(vlbm_ctx *c, int parity, int choice);
 int batch_num_choices();
+
+// learned closure (k_closure.cu / k_ideal.cu)
+vlbm_status ideal_step_corrected(vlbm_ctx *c, int parity, const float *dphi);
+vlbm_status closure_step(vlbm_ctx *c, int parity);
+int closure_cells(const vlbm_closure *cl, int *nx, int *ny, int *nz);
 
 // reduction of per-block partials into sums (k_ideal.cu)
 vlbm_status finish_sums(vlbm_ctx *c, int nvar, double *sums_dev);

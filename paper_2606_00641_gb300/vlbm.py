@@ -68,6 +68,24 @@ class vlbm_params(ctypes.Structure):
     ]
 
 
+class vlbm_closure_params(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int),
+        ("ny", ctypes.c_int),
+        ("nz", ctypes.c_int),
+        ("gamma", ctypes.c_double),
+        ("tau", ctypes.c_double),
+        ("mu", ctypes.c_double * 8),
+        ("sigma", ctypes.c_double * 8),
+        ("out_scale", ctypes.c_double * 8),
+        ("lr", ctypes.c_double),
+        ("beta1", ctypes.c_double),
+        ("beta2", ctypes.c_double),
+        ("eps", ctypes.c_double),
+        ("stream", ctypes.c_void_p),
+    ]
+
+
 class VlbmError(RuntimeError):
     def __init__(self, status: int, what: str, detail: str = ""):
         self.status = status
@@ -120,6 +138,17 @@ def load(build: bool = True):
         "vlbm_last_error": (ctypes.c_char_p, [P]),
         "vlbm_status_string": (ctypes.c_char_p, [i]),
         "vlbm_destroy": (None, [P]),
+        "vlbm_closure_create": (i, [ctypes.POINTER(vlbm_closure_params), ctypes.POINTER(P)]),
+        "vlbm_closure_num_params": (s, [P]),
+        "vlbm_closure_set_weights": (i, [P, P, s]),
+        "vlbm_closure_get_weights": (i, [P, P, s]),
+        "vlbm_closure_forward": (i, [P, P, P]),
+        "vlbm_closure_backward": (i, [P, P, P, P]),
+        "vlbm_closure_train_step": (i, [P, P, P, ctypes.POINTER(d)]),
+        "vlbm_closure_train_step_ctx": (i, [P, P, P, ctypes.POINTER(d)]),
+        "vlbm_set_closure": (i, [P, P]),
+        "vlbm_closure_destroy": (None, [P]),
+        "vlbm_restrict": (i, [P, i, i, i, i, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -219,6 +248,18 @@ def vlbm_create_batch(params: Sequence[vlbm_params]) -> int:
     return ctx.value
 
 
+def _device_inputs_ready():
+    """Order torch's work before a library call that reads device memory.
+
+    Library calls run on the context's stream, which does not synchronise
+    with torch's current stream; device inputs produced by torch kernels must
+    be complete before the call enqueues its work."""
+    import sys as _sys
+    torch = _sys.modules.get("torch")
+    if torch is not None and torch.cuda.is_available() and torch.cuda.is_initialized():
+        torch.cuda.current_stream().synchronize()
+
+
 def _host_f64(a: np.ndarray) -> np.ndarray:
     a = np.ascontiguousarray(a, dtype=np.float64)
     return a
@@ -239,6 +280,7 @@ def vlbm_init_fields_ptr(ctx: int, domain: int, host_ptr: int) -> int:
 
 
 def vlbm_init_fields_device(ctx: int, domain: int, dev_ptr: int) -> int:
+    _device_inputs_ready()
     st = load().vlbm_init_fields_device(ctx, domain, ctypes.c_void_p(dev_ptr))
     if st not in (VLBM_OK, VLBM_ERR_UNSTABLE, VLBM_ERR_NONPHYSICAL):
         _check(st, "vlbm_init_fields_device", ctx)
@@ -346,6 +388,87 @@ def vlbm_stream(ctx: int) -> int:
 def vlbm_destroy(ctx: int):
     if ctx:
         load().vlbm_destroy(ctx)
+
+
+def vlbm_restrict(Qf_ptr: int, shape, factor: int, Qc_ptr: int, stream: int = 0):
+    """Conservative block average of 8 device fields (fine shape (nz, ny, nx))."""
+    nz, ny, nx = shape
+    _device_inputs_ready()
+    _check(load().vlbm_restrict(ctypes.c_void_p(Qf_ptr), nx, ny, nz, factor, ctypes.c_void_p(Qc_ptr),
+                                ctypes.c_void_p(stream) if stream else None), "vlbm_restrict")
+
+
+def vlbm_set_closure(ctx: int, closure) -> None:
+    _check(load().vlbm_set_closure(ctx, closure.ptr if closure is not None else None), "vlbm_set_closure", ctx)
+
+
+class Closure:
+    """Learned flux closure (3-layer 3x3x3 conv net on the tensor cores)."""
+
+    def __init__(self, shape, gamma: float, tau: float, mu, sigma, out_scale, lr: float = 1e-3,
+                 beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8, stream: int = 0):
+        p = vlbm_closure_params()
+        p.nz, p.ny, p.nx = (int(n) for n in shape)
+        p.gamma, p.tau = float(gamma), float(tau)
+        for k in range(8):
+            p.mu[k], p.sigma[k], p.out_scale[k] = float(mu[k]), float(sigma[k]), float(out_scale[k])
+        p.lr, p.beta1, p.beta2, p.eps = float(lr), float(beta1), float(beta2), float(eps)
+        p.stream = stream if stream else None
+        ptr = ctypes.c_void_p()
+        _check(load().vlbm_closure_create(ctypes.byref(p), ctypes.byref(ptr)), "vlbm_closure_create")
+        self.ptr = ptr.value
+        self.shape = tuple(int(n) for n in shape)
+        self.nparam = int(load().vlbm_closure_num_params(self.ptr))
+
+    def set_weights(self, flat: np.ndarray):
+        flat = np.ascontiguousarray(flat, dtype=np.float32)
+        assert flat.size == self.nparam
+        _check(load().vlbm_closure_set_weights(self.ptr, flat.ctypes.data_as(ctypes.c_void_p), flat.size),
+               "vlbm_closure_set_weights")
+
+    def get_weights(self) -> np.ndarray:
+        out = np.empty(self.nparam, dtype=np.float32)
+        _check(load().vlbm_closure_get_weights(self.ptr, out.ctypes.data_as(ctypes.c_void_p), out.size),
+               "vlbm_closure_get_weights")
+        return out
+
+    def forward(self, Q_ptr: int, dphi_ptr: int):
+        _device_inputs_ready()
+        _check(load().vlbm_closure_forward(self.ptr, ctypes.c_void_p(Q_ptr), ctypes.c_void_p(dphi_ptr)),
+               "vlbm_closure_forward")
+
+    def backward(self, Q_ptr: int, gy_ptr: int) -> np.ndarray:
+        _device_inputs_ready()
+        out = np.empty(self.nparam, dtype=np.float32)
+        _check(load().vlbm_closure_backward(self.ptr, ctypes.c_void_p(Q_ptr), ctypes.c_void_p(gy_ptr),
+                                            out.ctypes.data_as(ctypes.c_void_p)), "vlbm_closure_backward")
+        return out
+
+    def train_step(self, Q0_ptr: int, Qt_ptr: int) -> float:
+        _device_inputs_ready()
+        loss = ctypes.c_double(0.0)
+        _check(load().vlbm_closure_train_step(self.ptr, ctypes.c_void_p(Q0_ptr), ctypes.c_void_p(Qt_ptr),
+                                              ctypes.byref(loss)), "vlbm_closure_train_step")
+        return loss.value
+
+    def train_step_ctx(self, ctx_ptr: int, Qt_ptr: int) -> float:
+        """One Adam step along a coarse run: ctx advances one corrected step."""
+        _device_inputs_ready()
+        loss = ctypes.c_double(0.0)
+        _check(load().vlbm_closure_train_step_ctx(self.ptr, ctx_ptr, ctypes.c_void_p(Qt_ptr),
+                                                  ctypes.byref(loss)), "vlbm_closure_train_step_ctx", ctx_ptr)
+        return loss.value
+
+    def close(self):
+        if self.ptr:
+            load().vlbm_closure_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Context:
