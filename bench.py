@@ -298,6 +298,7 @@ def main():
     import numpy as np
     import torch
 
+    from paper_2606_00641_gb300 import dist as vdist
     from paper_2606_00641_gb300 import fields, vlbm
 
     assert torch.cuda.is_available(), "bench.py needs a CUDA device"
@@ -364,11 +365,8 @@ def main():
     ms, launches = timed(ctx, args.steps, 0)
     clk = clocks.stop()
     status = vlbm.vlbm_sync(ctx.ptr)
-    ms_t = torch.tensor([ms], device="cuda")
-    if dist is not None:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
-    glups = world * ncell * args.steps / (ms_max * 1e-3) / 1e9
+    # whole-job rate: every rank's cells over the slowest rank's time
+    glups, ms_max, _ = vdist.weak_scaling_rate(ms, ncell, args.steps, device="cuda")
     bytes_cell = 2 * 56 * BYTES_PER_POP[args.storage]
     per_launch_ms = ms / args.steps
     achieved = ncell * bytes_cell / (per_launch_ms * 1e-3) / 1e9
