@@ -27,7 +27,7 @@
 #include <type_traits>
 #include <vector>
 
-#include "../../include/vlbm.h"
+#include "vlbm.h"
 
 namespace vlbm {
 

@@ -241,9 +241,9 @@ def test_checkpoint_restart_is_bit_exact(V, storage):
 # reduced-precision storage (shifted deviations): stated error, no exact pin
 # ---------------------------------------------------------------------------
 
+@pytest.mark.parametrize("shape", [(12, 16, 40), (6, 8, 64), (3, 5, 128)])
 @pytest.mark.parametrize("storage,bound", [("f16dev", 2e-3), ("bf16dev", 2e-2)])
-def test_deviation_storage_error_bound(V, storage, bound):
-    shape = (12, 16, 40)
+def test_deviation_storage_error_bound(V, storage, bound, shape):
     f0 = fields.ideal_fields(shape, 606, mach=1.0, beta=1.0, cfl=0.2)
     qref = f0.Q.reshape(8, -1).mean(1)
     dev = np.abs(f0.Q - qref.reshape(8, 1, 1, 1)).reshape(8, -1).max(1)
@@ -252,6 +252,53 @@ def test_deviation_storage_error_bound(V, storage, bound):
     ref = oracle.ideal_run(f0.Q, f0.gamma, 0.51, 20)
     err = rel_err(got, ref, ideal_scales(f0.Q))
     assert err.max() < bound, err
+
+
+@pytest.mark.parametrize("shape", [(5, 6, 128), (9, 192)])
+@pytest.mark.parametrize("storage,ulp", [("f16dev", 2.0 ** -11), ("bf16dev", 2.0 ** -8)])
+@pytest.mark.parametrize("parity", [0, 1])
+def test_deviation_storage_one_step_sampled(V, shape, storage, ulp, parity):
+    # one step of the 16-bit deviation forms from gathered populations equals
+    # the oracle collision up to the storage rounding, at warp and row edges
+    dim = len(shape)
+    q = 5 if dim == 2 else 7
+    f0 = fields.ideal_fields(shape, 707, mach=1.0, beta=1.0, cfl=0.1 if dim == 2 else 0.2)
+    qref = f0.Q.reshape(8, -1).mean(1)
+    qscale = np.abs(f0.Q - qref.reshape((8,) + (1,) * dim)).reshape(8, -1).max(1)
+    p = V.make_params(shape=shape, storage=storage, gamma=f0.gamma, tau=0.6, q_ref=qref, q_scale=qscale)
+    N = int(np.prod(shape))
+    nx = shape[-1]
+    dirs = [(0, 0, 0), (1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)][:q]
+    full = (1,) * (3 - dim) + tuple(shape)
+
+    def upstream(cell, c):
+        nz, ny, nx_ = full
+        x, y, z = cell % nx_, (cell // nx_) % ny, cell // (nx_ * ny)
+        return (x - c[0]) % nx_ + nx_ * (((y - c[1]) % ny) + ny * ((z - c[2]) % nz))
+
+    rng = np.random.default_rng(parity)
+    # every warp-edge lane (x0 = 0, 62, 64, 126 ...) and row ends, plus random cells
+    edge_x = sorted({0, 1, 62, 63, 64, 65, 126, 127} | {nx - 2, nx - 1})
+    base = rng.choice(N // nx, size=6, replace=False) * nx
+    cells = np.unique(np.concatenate([b + np.array(edge_x) for b in base] +
+                                     [rng.choice(N, size=40, replace=False)])).astype(np.int64)
+    with V.Context(p) as ctx:
+        assert ctx.init_fields(f0.Q) == V.VLBM_OK
+        ctx.step(2 + parity)
+        src = {int(x): [upstream(int(x), c) for c in dirs] for x in cells}
+        uniq = np.array(sorted({u for v in src.values() for u in v}), dtype=np.int64)
+        pre = dict(zip(uniq.tolist(), ctx.populations(uniq)))
+        ctx.step(1)
+        post = ctx.populations(cells)
+        assert ctx.sync() == V.VLBM_OK
+    w = np.array([1 / 3 if dim == 2 else 1 / 4] + [1 / 6 if dim == 2 else 1 / 8] * (q - 1))
+    coll = {u: oracle.ideal_collide_cell(dim, f0.gamma, 0.6, pre[u].reshape(8, q)) for u in uniq.tolist()}
+    for r, x in enumerate(cells.tolist()):
+        exp = np.array([[coll[src[x][i]][k, i] for i in range(q)] for k in range(8)])
+        g_exp = (exp - w[None, :] * qref[:, None]) / qscale[:, None]
+        g_got = (post[r].reshape(8, q) - w[None, :] * qref[:, None]) / qscale[:, None]
+        tol = ulp * np.abs(g_exp) + 2e-3 * ulp * 64 * np.abs(g_exp).max()
+        assert (np.abs(g_got - g_exp) <= tol).all(), (x, np.abs(g_got - g_exp).max())
 
 
 # ---------------------------------------------------------------------------
