@@ -42,16 +42,27 @@ __global__ void __launch_bounds__(TX) k_batch_step(const int2 *__restrict__ tile
     constexpr int D = 2, Q = 5;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int2 tile = tiles[t];
-        const BatchDomain &dm = doms[tile.x];
-        const int nx = dm.nx, ny = dm.ny;
-        const int64_t stride = dm.stride;
-        float *base = pop + dm.offset;
+        const BatchDomain *dm = doms + tile.x;
+        // the domain's parameters, read once per tile into registers
+        const int nx = __ldg(&dm->nx), ny = __ldg(&dm->ny);
+        const int64_t ncell = __ldg(&dm->ncell);
+        const int64_t stride = __ldg(&dm->stride);
+        float *base = pop + __ldg(&dm->offset);
+        const float gm1 = __ldg(&dm->gm1);
+        float omega[8], src0[8], src1[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            omega[k] = __ldg(&dm->omega[k]);
+            src0[k] = __ldg(&dm->src0[k]);
+            src1[k] = __ldg(&dm->src1[k]);
+        }
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const int64_t cell = (int64_t)tile.y + r * TX + threadIdx.x;
-            if (cell >= dm.ncell) continue;
-            const int x = (int)(cell % nx);
-            const int y = (int)(cell / nx);
+            const int c32 = tile.y + r * TX + (int)threadIdx.x;  // per-domain cells < 2^31
+            if (c32 >= ncell) continue;
+            const int64_t cell = c32;
+            const int y = c32 / nx;
+            const int x = c32 - y * nx;
             const int64_t plane = (int64_t)nx * ny;
             int64_t nb[Q];
             nb[0] = cell;
@@ -68,14 +79,17 @@ __global__ void __launch_bounds__(TX) k_batch_step(const int2 *__restrict__ tile
                     const int64_t at = ODD ? nb[opp_axis(i)] : cell;
                     f[k][i] = base[(int64_t)(k * Q + j) * stride + at];
                 }
-            ideal_collide<D, float>(f, dm.gm1, dm.omega, dm.src0, dm.src1, flags);
+            ideal_collide<D, float>(f, gm1, omega, src0, src1, flags);
+            // the stride is per-domain (not a kernel parameter): recompute the
+            // store addresses rather than hold 40 offsets across the collision
+            const int64_t sst = opaque(stride);
 #pragma unroll
             for (int k = 0; k < 8; ++k)
 #pragma unroll
                 for (int i = 0; i < Q; ++i) {
                     const int j = ODD ? i : opp_axis(i);
                     const int64_t at = ODD ? nb[i] : cell;
-                    base[(int64_t)(k * Q + j) * stride + at] = f[k][i];
+                    base[(int64_t)(k * Q + j) * sst + at] = f[k][i];
                 }
         }
     }

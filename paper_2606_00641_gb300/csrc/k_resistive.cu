@@ -201,7 +201,8 @@ __global__ void __launch_bounds__(kBlockX) k_res_step(const Args a)
         }
     }
 
-    // ---- store ----
+    // ---- store ---- (addresses recomputed from an opaque stride, not held)
+    const int64_t Ss = opaque(S);
 #pragma unroll
     for (int i = 0; i < kQf; ++i) {
         int64_t at;
@@ -215,7 +216,7 @@ __global__ void __launch_bounds__(kBlockX) k_res_step(const Args a)
             j = to_wall ? opp_axis(i) : i;
             at = to_wall ? cell : nbr(o, cell, cx19(i), cy19(i), cz19(i));
         }
-        pop[(int64_t)j * S + at] = f[i];
+        pop[(int64_t)j * Ss + at] = f[i];
     }
 #pragma unroll
     for (int b = 0; b < 3; ++b)
@@ -223,7 +224,7 @@ __global__ void __launch_bounds__(kBlockX) k_res_step(const Args a)
         for (int i = 0; i < 7; ++i) {
             const int j = ODD ? i : opp_axis(i);
             const int64_t at = ODD ? nbr(o, cell, cx19(i), cy19(i), cz19(i)) : cell;
-            pop[(int64_t)(19 + 7 * b + j) * S + at] = g[b][i];
+            pop[(int64_t)(19 + 7 * b + j) * Ss + at] = g[b][i];
         }
 }
 

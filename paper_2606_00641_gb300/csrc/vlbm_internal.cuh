@@ -56,6 +56,15 @@ template <> struct AxisSet<3> {
     static constexpr double w0 = 1.0 / 4.0, w1 = 1.0 / 8.0, cs2 = 1.0 / 4.0;
 };
 
+// An opaque copy of a value: the compiler cannot reuse expressions computed
+// from the original across it, so addresses built from the copy are
+// recomputed where they are used instead of being held in registers.
+__device__ __forceinline__ int64_t opaque(int64_t v)
+{
+    asm volatile("" : "+l"(v));
+    return v;
+}
+
 // Storage codecs: deviation forms store (f - w_i ref_k) / scale_k.
 template <class S> struct Codec;
 template <> struct Codec<double> {
