@@ -177,6 +177,115 @@ __global__ void __launch_bounds__(kConvThreads) k_conv(const bf16 *__restrict__ 
     }
 }
 
+// Shared-memory variant: one CTA = 8 warps = a 16 x 8 (x, y) patch of cells
+// at one z.  The patch and its one-cell halo (18 x 10 x 3 cells) are staged
+// in shared memory with 16-byte copies; A fragments come from it by
+// ldmatrix.x4 (16 cell rows x 8 channels per 8x8 matrix).  Channel rows are
+// padded (CS = 32: 80 bytes) so the 8 rows of a matrix hit distinct banks.
+constexpr int kTx = 16, kTy = 8;
+constexpr int kHx = kTx + 2, kHy = kTy + 2, kHalo = kHx * kHy * 3;
+
+__device__ __forceinline__ void ldmatrix_x4(uint32_t addr, uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr));
+}
+
+template <int CS, int NT>
+__global__ void __launch_bounds__(kTx * kTy * 2) k_conv_smem(const bf16 *__restrict__ act, int nx, int ny, int nz,
+                                                             const uint2 *__restrict__ frag, const ConvEpilogue e)
+{
+    constexpr int NCHUNK = CS == 8 ? 14 : 54;
+    constexpr int ROW = CS == 8 ? 8 : 40;        // bf16 per staged cell (padded)
+    constexpr int VEC = CS / 8;                  // 16-byte pieces per cell
+    __shared__ __align__(16) bf16 tile[kHalo * ROW];
+    const int x0 = blockIdx.x * kTx, y0 = blockIdx.y * kTy, z = blockIdx.z;
+    const int plane = nx * ny;
+    // stage the halo box: (bx, by, bz) -> cell (x0-1+bx, y0-1+by, z-1+bz), periodic
+    for (int idx = threadIdx.x; idx < kHalo * VEC; idx += blockDim.x) {
+        const int piece = idx % VEC, c = idx / VEC;
+        const int bx = c % kHx, by = (c / kHx) % kHy, bz = c / (kHx * kHy);
+        int gx = x0 - 1 + bx, gy = y0 - 1 + by, gz = z - 1 + bz;
+        gx += gx < 0 ? nx : (gx >= nx ? -nx : 0);
+        gy += gy < 0 ? ny : (gy >= ny ? -ny : 0);
+        gz += gz < 0 ? nz : (gz >= nz ? -nz : 0);
+        const size_t cell = (size_t)gx + (size_t)nx * gy + (size_t)plane * gz;
+        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(act + cell * CS) + piece);
+        *reinterpret_cast<uint4 *>(tile + c * ROW + piece * 8) = v;
+    }
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;  // warp = row y0 + warp
+    const int g = lane >> 2, tg = lane & 3;
+    const int m = lane >> 3, rr = lane & 7;                      // ldmatrix: matrix m, row rr
+    const uint32_t tile_s = (uint32_t)__cvta_generic_to_shared(tile);
+    float acc[NT][4];
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
+
+#pragma unroll 2
+    for (int j = 0; j < NCHUNK; ++j) {
+        int t, col;
+        if (CS == 32) {
+            t = j >> 1;
+            col = (j & 1) * 16 + (m >> 1) * 8;  // matrices 2, 3 hold channels +8
+        } else {
+            t = 2 * j + (m >> 1);               // matrices 2, 3 hold the second tap
+            col = 0;
+        }
+        const int tt = t < 27 ? t : 13;         // padding tap: any valid row, zeroed below
+        const int dx = tt % 3 - 1, dy = (tt / 3) % 3 - 1, dz = tt / 9 - 1;
+        const int r = (m & 1) * 8 + rr;         // cell row of the 16 within the warp
+        const int c = (1 + dz) * (kHx * kHy) + (warp + 1 + dy) * kHx + (r + 1 + dx);
+        uint32_t a0, a1, a2, a3;
+        ldmatrix_x4(tile_s + (uint32_t)((c * ROW + col) * 2), a0, a1, a2, a3);
+        if (CS == 8 && 2 * j + 1 >= 27) a2 = a3 = 0u;
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) {
+            const uint2 b = __ldg(frag + ((size_t)j * NT + nt) * 32 + lane);
+            mma_bf16(acc[nt], a0, a1, a2, a3, b.x, b.y);
+        }
+    }
+
+    const int cA = (x0 + g) + nx * (y0 + warp) + plane * z, cB = cA + 8;
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt) {
+        const int col = nt * 8 + 2 * tg;
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            const int cell = half ? cB : cA;
+            float v0 = acc[nt][2 * half], v1 = acc[nt][2 * half + 1];
+            if (e.bias) {
+                v0 += e.bias[col];
+                v1 += e.bias[col + 1];
+            }
+            if (e.tanh_act) {
+                v0 = tanhf(v0);
+                v1 = tanhf(v1);
+            }
+            if (e.deriv) {
+                const float d0 = __bfloat162float(e.deriv[(size_t)cell * 32 + col]);
+                const float d1 = __bfloat162float(e.deriv[(size_t)cell * 32 + col + 1]);
+                v0 *= 1.f - d0 * d0;
+                v1 *= 1.f - d1 * d1;
+            }
+            if (e.scale) {
+                v0 *= e.scale[col];
+                v1 *= e.scale[col + 1];
+            }
+            if (e.out_bf) {
+                __nv_bfloat162 o;
+                o.x = __float2bfloat16_rn(v0);
+                o.y = __float2bfloat16_rn(v1);
+                *reinterpret_cast<__nv_bfloat162 *>(e.out_bf + (size_t)cell * e.os + col) = o;
+            } else {
+                *reinterpret_cast<float2 *>(e.out_f + (size_t)cell * e.os + col) = make_float2(v0, v1);
+            }
+        }
+    }
+}
+
 // B-fragment packing.  Chunk j, n-tile nt, lane l (g = l/4, tg = l%4) holds
 // b0 = B[2tg..2tg+1][n], b1 = B[2tg+8..2tg+9][n] with n = 8 nt + g, where
 // B[k][n] is the weight of K-index k of chunk j for output channel n.
@@ -494,6 +603,22 @@ vlbm_status pack_all(vlbm_closure *cl, cudaStream_t s)
 
 vlbm_status conv(vlbm_closure *cl, int layer, const bf16 *in, bool transpose, const ConvEpilogue &e, cudaStream_t s)
 {
+    if (cl->nx % kTx == 0 && cl->ny % kTy == 0) {
+        // shared-memory staged tiles (16 x 8 cells per CTA)
+        const dim3 grid((unsigned)(cl->nx / kTx), (unsigned)(cl->ny / kTy), (unsigned)cl->nz);
+        const int threads = kTx * kTy * 2;
+        if (!transpose) {
+            if (layer == 0)
+                k_conv_smem<8, 4><<<grid, threads, 0, s>>>(in, cl->nx, cl->ny, cl->nz, cl->frag_fwd[0], e);
+            else if (layer == 1)
+                k_conv_smem<32, 4><<<grid, threads, 0, s>>>(in, cl->nx, cl->ny, cl->nz, cl->frag_fwd[1], e);
+            else
+                k_conv_smem<32, 3><<<grid, threads, 0, s>>>(in, cl->nx, cl->ny, cl->nz, cl->frag_fwd[2], e);
+        } else {
+            k_conv_smem<32, 4><<<grid, threads, 0, s>>>(in, cl->nx, cl->ny, cl->nz, cl->frag_bwd[layer], e);
+        }
+        return cl_check(cudaGetLastError(), "closure convolution launch");
+    }
     const int cells_per_cta = (kConvThreads / 32) * 16;
     const unsigned grid = (unsigned)((cl->N + cells_per_cta - 1) / cells_per_cta);
     if (!transpose) {
