@@ -286,6 +286,229 @@ __global__ void __launch_bounds__(kTx * kTy * 2) k_conv_smem(const bf16 *__restr
     }
 }
 
+// ---------------------------------------------------------------------------
+// tcgen05 convolution (5th-generation tensor cores, accumulators in TMEM)
+// ---------------------------------------------------------------------------
+// Tile = 8 (x) x 16 (y) cells at one z = the M = 128 rows of one
+// tcgen05.mma.cta_group::1.kind::f16 (BF16 in, FP32 accumulate), N = 32
+// output channels (24-channel layers use zero weights for 24..31), K = 16 per
+// instruction.  The halo box (10 x 18 x 3 cells) is staged as channel-block
+// planes: plane cb holds channels 8cb..8cb+7 of every box cell (16 bytes per
+// cell), so 8 x-consecutive cells form one 128-byte core matrix and each tap
+// is only a start offset of the shared-memory descriptor: rows m = 8y + x,
+// 8-row groups 160 bytes apart (SBO), K-adjacent core matrices one plane
+// (Cin = 32) or one tap (Cin = 8) apart (LBO).  The weights of the layer sit
+// in shared memory in the same canonical K-major layout.  Persistent CTAs:
+// weights once, then one tile after another; one thread issues the MMAs,
+// tcgen05.commit arrives on an mbarrier (bounded wait), and each warp reads
+// its 32 TMEM lanes (= its 32 cells) with tcgen05.ld.
+constexpr int kTcX = 8, kTcY = 16, kTcZ = 2;  // kTcZ z-slices per tile = kTcZ M-blocks
+constexpr int kTcHx = kTcX + 2, kTcHy = kTcY + 2, kTcHz = kTcZ + 2, kTcHalo = kTcHx * kTcHy * kTcHz;
+constexpr int kTcPlane = kTcHalo * 16;  // bytes per channel-block plane
+constexpr int kTcThreads = 128;
+constexpr int kTcCols = 32 * kTcZ;      // TMEM columns: one 32-column accumulator per z-slice
+constexpr uint32_t kTcWaitLimit = 1u << 24;
+
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;  // descriptor version of the sm_100 family; no swizzle
+    return d;
+}
+
+// byte offset, inside a plane, of the first row of tap t for z-slice zz
+__device__ __forceinline__ int tc_tap_ofs(int t, int zz)
+{
+    const int dx = t % 3, dy = (t / 3) % 3, dz = t / 9;  // 0..2 = offset + 1
+    return (((dz + zz) * kTcHy + dy) * kTcHx + dx) * 16;
+}
+
+template <int CS>
+__global__ void __launch_bounds__(kTcThreads) k_conv_tc(const bf16 *__restrict__ act, int nx, int ny, int nz,
+                                                        const bf16 *__restrict__ wtc, int cout_real,
+                                                        const ConvEpilogue e, unsigned *err)
+{
+    constexpr int NCHUNK = CS == 8 ? 14 : 54;
+    constexpr int NPLANE = CS / 8;
+    constexpr int WBYTES = NCHUNK * 1024;  // 4 n-groups x 2 k-halves x 128 bytes per chunk
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char *sw = smem;                       // weights
+    unsigned char *sa = smem + WBYTES;              // halo planes
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_base;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tiles_x = nx / kTcX, tiles_y = ny / kTcY, tiles_z = nz / kTcZ;
+    const int ntiles = tiles_x * tiles_y * tiles_z;
+    const int plane = nx * ny;
+
+    for (int i = tid; i < WBYTES / 16; i += kTcThreads)
+        reinterpret_cast<uint4 *>(sw)[i] = __ldg(reinterpret_cast<const uint4 *>(wtc) + i);
+    if (warp == 0) {
+        const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&tmem_base);
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(dst), "r"(kTcCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    const uint32_t mb = (uint32_t)__cvta_generic_to_shared(&mbar);
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb));
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const uint32_t tmem = tmem_base;
+    const uint32_t sw_s = (uint32_t)__cvta_generic_to_shared(sw);
+    const uint32_t sa_s = (uint32_t)__cvta_generic_to_shared(sa);
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+    uint32_t phase = 0;
+    bool ok = true;
+
+    for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        const int tx = tile % tiles_x, ty = (tile / tiles_x) % tiles_y, tz = tile / (tiles_x * tiles_y);
+        const int x0 = tx * kTcX, y0 = ty * kTcY, z0 = tz * kTcZ;
+        // stage the halo box as channel-block planes: every 16-byte piece in flight at once
+        for (int idx = tid; idx < kTcHalo * NPLANE; idx += kTcThreads) {
+            const int cb = idx % NPLANE, c = idx / NPLANE;
+            const int bx = c % kTcHx, by = (c / kTcHx) % kTcHy, bz = c / (kTcHx * kTcHy);
+            int gx = x0 - 1 + bx, gy = y0 - 1 + by, gz = z0 - 1 + bz;
+            gx += gx < 0 ? nx : (gx >= nx ? -nx : 0);
+            gy += gy < 0 ? ny : (gy >= ny ? -ny : 0);
+            gz += gz < 0 ? nz : (gz >= nz ? -nz : 0);
+            const size_t cell = (size_t)gx + (size_t)nx * gy + (size_t)plane * gz;
+            const uint32_t dst = sa_s + (uint32_t)(cb * kTcPlane + c * 16);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(act + cell * CS + cb * 8)
+                         : "memory");
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            for (int zz = 0; zz < kTcZ; ++zz) {
+                const uint32_t dacc = tmem + (uint32_t)(32 * zz);  // accumulator columns of slice zz
+                for (int j = 0; j < NCHUNK; ++j) {
+                    uint32_t a_addr, lbo;
+                    if (CS == 32) {  // chunk j: tap j/2, planes 2(j%2) and 2(j%2)+1
+                        a_addr = sa_s + (uint32_t)((j & 1) * 2 * kTcPlane + tc_tap_ofs(j >> 1, zz));
+                        lbo = kTcPlane;
+                    } else {         // chunk j: taps 2j and 2j+1 of the single plane
+                        const int t0 = 2 * j, t1 = 2 * j + 1;
+                        a_addr = sa_s + (uint32_t)tc_tap_ofs(t0, zz);
+                        lbo = t1 < 27 ? (uint32_t)(tc_tap_ofs(t1, zz) - tc_tap_ofs(t0, zz)) : 0u;  // padding: zero weights
+                    }
+                    const uint64_t da = tc_desc(a_addr, lbo, kTcHx * 16);
+                    const uint64_t db = tc_desc(sw_s + (uint32_t)(j * 1024), 128, 256);
+                    const uint32_t acc = j > 0;
+                    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+                                 ::"r"(dacc), "l"(da), "l"(db), "r"(idesc), "r"(acc));
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mb));
+        }
+        uint32_t done = 0;
+        for (uint32_t it = 0; it < kTcWaitLimit && !done; ++it)
+            asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                         "selp.u32 %0, 1, 0, p;\n\t}\n"
+                         : "=r"(done)
+                         : "r"(mb), "r"(phase));
+        // one outcome for the whole CTA, so that no thread leaves the loop alone
+        const int all_done = __syncthreads_and((int)done);
+        phase ^= 1u;
+        if (!all_done) {
+            if (tid == 0) atomicOr(err, kFlagTimeout);
+            ok = false;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        if (all_done) {
+            const int m = warp * 32 + lane;  // TMEM lane = tile row
+            for (int zz = 0; zz < kTcZ; ++zz) {
+                uint32_t r[32];
+                const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(32 * zz);
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+                             "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+                             : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                               "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+                               "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+                               "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+                               "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+                               "=r"(r[31])
+                             : "r"(taddr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+                const size_t cell =
+                    (size_t)(x0 + (m & 7)) + (size_t)nx * (y0 + (m >> 3)) + (size_t)plane * (z0 + zz);
+                float v[32];
+#pragma unroll
+                for (int c = 0; c < 32; ++c) {
+                    float x = __uint_as_float(r[c]);
+                    if (e.bias && c < cout_real) x += e.bias[c];
+                    if (e.tanh_act) x = tanhf(x);
+                    if (e.deriv) {
+                        const float d = __bfloat162float(e.deriv[cell * 32 + c]);
+                        x *= 1.f - d * d;
+                    }
+                    if (e.scale && c < cout_real) x *= e.scale[c];
+                    v[c] = x;
+                }
+                if (e.out_bf) {
+                    __align__(16) bf16 o[32];
+#pragma unroll
+                    for (int c = 0; c < 32; ++c) o[c] = __float2bfloat16_rn(c < cout_real ? v[c] : 0.f);
+                    uint4 *dst = reinterpret_cast<uint4 *>(e.out_bf + cell * e.os);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) dst[q] = reinterpret_cast<const uint4 *>(o)[q];
+                } else {
+                    float *dst = e.out_f + cell * e.os;
+#pragma unroll
+                    for (int c = 0; c < 32; c += 4)
+                        if (c < cout_real)
+                            *reinterpret_cast<float4 *>(dst + c) = make_float4(v[c], v[c + 1], v[c + 2], v[c + 3]);
+                }
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+        __syncthreads();  // TMEM read and halo consumed before the next tile reuses them
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTcCols));
+    }
+}
+
+// Weights in the canonical K-major layout of k_conv_tc: chunk j, output
+// channel n (< 32; zero beyond cout), K-index k (< 16) at
+// j*512 + (n/8)*128 + (k/8)*64 + (n%8)*8 + k%8 (bf16 elements).
+__global__ void k_pack_tc(const float *__restrict__ W, int cout, int cin, int CS, int transpose,
+                          bf16 *__restrict__ out)
+{
+    const int nchunk = CS == 8 ? 14 : 54;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nchunk * 512) return;
+    const int j = idx / 512, rem = idx % 512;
+    const int g = rem / 128, kc = (rem / 64) % 2, r = (rem / 8) % 8, e8 = rem % 8;
+    const int n = g * 8 + r, k = kc * 8 + e8;
+    int t, c;
+    if (CS == 32) {
+        t = j >> 1;
+        c = (j & 1) * 16 + k;
+    } else {
+        t = 2 * j + (k >= 8 ? 1 : 0);
+        c = k & 7;
+    }
+    float w = 0.f;
+    if (t < 27) {
+        if (!transpose) {
+            if (n < cout && c < cin) w = W[((size_t)n * cin + c) * 27 + t];
+        } else {
+            if (n < cin && c < cout) w = W[((size_t)c * cin + n) * 27 + (26 - t)];
+        }
+    }
+    out[idx] = __float2bfloat16_rn(w);
+}
+
 // B-fragment packing.  Chunk j, n-tile nt, lane l (g = l/4, tg = l%4) holds
 // b0 = B[2tg..2tg+1][n], b1 = B[2tg+8..2tg+9][n] with n = 8 nt + g, where
 // B[k][n] is the weight of K-index k of chunk j for output channel n.
@@ -408,21 +631,229 @@ __global__ void __launch_bounds__(kConvThreads) k_wgrad(const bf16 *__restrict__
     }
 }
 
-// bias gradient: gb[o] += sum_cells gz[cell][o]
-__global__ void __launch_bounds__(256) k_bgrad(const bf16 *__restrict__ gz, int N, int cout, float *__restrict__ gb)
+// Bias gradient, coalesced: each thread reads whole 16-byte channel blocks of a
+// cell; one partial per CTA, summed by k_part_sum (fixed order).
+__global__ void __launch_bounds__(256) k_bgrad_part(const bf16 *__restrict__ gz, int N, int cout,
+                                                    float *__restrict__ part)
 {
-    __shared__ float red[256];
-    const int o = blockIdx.y;
-    float s = 0.f;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x)
-        s += __bfloat162float(gz[(size_t)c * 32 + o]);
-    red[threadIdx.x] = s;
-    __syncthreads();
-    for (int k = blockDim.x / 2; k > 0; k >>= 1) {
-        if ((int)threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
-        __syncthreads();
+    __shared__ float red[256][9];
+    const int cb = threadIdx.x & 3;
+    float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int c = blockIdx.x * 64 + (threadIdx.x >> 2); c < N; c += gridDim.x * 64) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(gz + (size_t)c * 32) + cb);
+        const bf16 *h = reinterpret_cast<const bf16 *>(&v);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) s[e] += __bfloat162float(h[e]);
     }
-    if (threadIdx.x == 0 && o < cout) atomicAdd(gb + o, red[0]);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) red[threadIdx.x][e] = s[e];
+    __syncthreads();
+    const int o = threadIdx.x;
+    if (o < cout) {
+        float t = 0.f;
+        for (int r = 0; r < 64; ++r) t += red[r * 4 + (o >> 3)][o & 7];
+        part[(size_t)blockIdx.x * cout + o] = t;
+    }
+}
+
+// out[j] += sum over blocks b of part[b * count + j], in block order
+__global__ void __launch_bounds__(256) k_part_sum(const float *__restrict__ part, int nblk, int count,
+                                                  float *__restrict__ out)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= count) return;
+    float s = 0.f;
+    for (int b = 0; b < nblk; ++b) s += part[(size_t)b * count + j];
+    out[j] += s;
+}
+
+// Weight gradient on the tcgen05 tensor cores:
+//   gW[o][c][t] = sum over cells p of gz[p][o] * a[p + e_t][c]
+// is a GEMM whose reduction runs over the cells.  Both operands are read in
+// their natural cell-major layout (channels contiguous), i.e. as MN-major
+// operands, from planes staged in shared memory:
+//   A (M = 128 rows) = 4 z-offsets x 4 slots x 8 channels.  Row z-offset h is
+//     the tap dz = h (h = 3 is computed and discarded).  With 32 input channels
+//     the slots are the 4 channel blocks and there is one accumulator per
+//     (dy, dx); with 8 input channels the slots hold copies of the halo
+//     shifted by dx = 0, 1, 2 (slot 3 discarded) and there is one accumulator
+//     per dy.  A tap (dy, dx) is an address offset into the staged planes.
+//   B (N = 32) = the output-channel gradients of the tile's cells.
+// Tiles of 8 x 16 x kWgZ cells; persistent CTAs (one per SM: the two staging
+// buffers take more than half of the shared memory) accumulate all their
+// tiles in TMEM while the next tile is staged with cp.async, then write one
+// partial gradient per CTA (summed in fixed order by k_part_sum).
+constexpr int kWgZ = 2;
+
+template <int CIN>
+struct WgLayout {
+    static constexpr int PW = CIN == 32 ? 10 : 8;  // staged row width in cells
+    static constexpr int S2D = 18 * PW * 16;       // bytes per (z plane, slot)
+    static constexpr int ABYTES = (kWgZ + 3) * 4 * S2D;
+    static constexpr int GBYTES = 4 * kWgZ * 128 * 16;
+    static constexpr int BUF = ABYTES + GBYTES;
+    static constexpr int NACC = CIN == 32 ? 9 : 3;
+    static constexpr int COLS = CIN == 32 ? 512 : 128;  // TMEM columns (power of two >= 32 * NACC)
+};
+
+template <int CIN>
+__global__ void __launch_bounds__(kTcThreads) k_wgrad_tc(const bf16 *__restrict__ gz, const bf16 *__restrict__ act,
+                                                         int nx, int ny, int nz, int cout,
+                                                         float *__restrict__ part, unsigned *err)
+{
+    using L = WgLayout<CIN>;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_base;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tiles_x = nx / 8, tiles_y = ny / 16, tiles_z = nz / kWgZ;
+    const int ntiles = tiles_x * tiles_y * tiles_z;
+    const int plane = nx * ny;
+    const uint32_t s_base = (uint32_t)__cvta_generic_to_shared(smem);
+
+    // slots that are never staged feed only discarded rows: clear them once
+    for (int i = tid; i < 2 * L::BUF / 16; i += kTcThreads) reinterpret_cast<uint4 *>(smem)[i] = make_uint4(0, 0, 0, 0);
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    if (warp == 0) {
+        const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&tmem_base);
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(dst), "r"(L::COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    const uint32_t mb = (uint32_t)__cvta_generic_to_shared(&mbar);
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb));
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const uint32_t tmem = tmem_base;
+
+    auto stage = [&](int tile, int b) {
+        const int tx = tile % tiles_x, ty = (tile / tiles_x) % tiles_y, tz = tile / (tiles_x * tiles_y);
+        const int x0 = tx * 8, y0 = ty * 16, z0 = tz * kWgZ;
+        const uint32_t abase = s_base + (uint32_t)(b * L::BUF), gbase = abase + L::ABYTES;
+        constexpr int NA = CIN == 32 ? (kWgZ + 2) * 4 * 18 * 10 : (kWgZ + 2) * 3 * 18 * 8;
+        for (int idx = tid; idx < NA; idx += kTcThreads) {
+            int slot, bx, by, h, sx;
+            if (CIN == 32) {  // slot = channel block; consecutive threads read one cell's 64 bytes
+                slot = idx & 3;
+                const int c = idx >> 2;
+                bx = c % 10;
+                by = (c / 10) % 18;
+                h = c / 180;
+                sx = bx;
+            } else {          // slot = x shift
+                bx = idx & 7;
+                const int r = idx >> 3;
+                by = r % 18;
+                slot = (r / 18) % 3;
+                h = r / 54;
+                sx = bx + slot;
+            }
+            int gx = x0 - 1 + sx, gy = y0 - 1 + by, gzz = z0 - 1 + h;
+            gx += gx < 0 ? nx : (gx >= nx ? -nx : 0);
+            gy += gy < 0 ? ny : (gy >= ny ? -ny : 0);
+            gzz += gzz < 0 ? nz : (gzz >= nz ? -nz : 0);
+            const size_t cell = (size_t)gx + (size_t)nx * gy + (size_t)plane * gzz;
+            const uint32_t dst = abase + (uint32_t)((((h * 4 + slot) * 18 + by) * L::PW + bx) * 16);
+            const bf16 *src = act + cell * CIN + (CIN == 32 ? slot * 8 : 0);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+        }
+        for (int idx = tid; idx < 4 * kWgZ * 128; idx += kTcThreads) {
+            const int cbo = idx & 3, c = idx >> 2;  // c = zz * 128 + y * 8 + x
+            const size_t cell = (size_t)(x0 + (c & 7)) + (size_t)nx * (y0 + ((c >> 3) & 15)) +
+                                (size_t)plane * (z0 + (c >> 7));
+            const uint32_t dst = gbase + (uint32_t)((cbo * kWgZ * 128 + c) * 16);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(gz + cell * 32 + cbo * 8)
+                         : "memory");
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    };
+
+    // MN-major A and B (bits 15, 16), BF16 in, FP32 accumulate, M = 128, N = 32
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) | ((32u >> 3) << 17) |
+                           ((128u >> 4) << 24);
+    uint32_t phase = 0;
+    bool ok = true, first = true;
+    int b = 0;
+    if ((int)blockIdx.x < ntiles) stage(blockIdx.x, 0);
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    __syncthreads();
+    for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            const uint32_t abase = s_base + (uint32_t)(b * L::BUF), gbase = abase + L::ABYTES;
+            for (int zz = 0; zz < kWgZ; ++zz)
+                for (int ks = 0; ks < 8; ++ks) {  // two tile rows of 8 cells per K step
+                    const uint64_t db = tc_desc(gbase + (uint32_t)(zz * 2048 + ks * 256), 128, kWgZ * 128 * 16);
+                    const uint32_t acc = !(first && zz == 0 && ks == 0);
+                    for (int j = 0; j < L::NACC; ++j) {
+                        const int dy = CIN == 32 ? j / 3 : j, dx = CIN == 32 ? j % 3 : 0;
+                        const uint32_t a_addr =
+                            abase + (uint32_t)(zz * 4 * L::S2D + ((2 * ks + dy) * L::PW + dx) * 16);
+                        const uint64_t da = tc_desc(a_addr, L::PW * 16, L::S2D);
+                        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                                     "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+                                     ::"r"(tmem + (uint32_t)(32 * j)), "l"(da), "l"(db), "r"(idesc), "r"(acc));
+                    }
+                }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mb));
+        }
+        // stage the next tile into the other buffer while the tensor cores work
+        const int next = tile + (int)gridDim.x;
+        if (next < ntiles) stage(next, b ^ 1);
+        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        uint32_t done = 0;
+        for (uint32_t it = 0; it < kTcWaitLimit && !done; ++it)
+            asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                         "selp.u32 %0, 1, 0, p;\n\t}\n"
+                         : "=r"(done)
+                         : "r"(mb), "r"(phase));
+        const int all_done = __syncthreads_and((int)done);
+        phase ^= 1u;
+        if (!all_done) {
+            if (tid == 0) atomicOr(err, kFlagTimeout);
+            ok = false;
+        }
+        first = false;
+        b ^= 1;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (ok && warp < 3) {  // warp h reads TMEM lanes of z-offset h = dz; warp 3 holds discarded rows
+        float *dst = part + (size_t)blockIdx.x * cout * CIN * 27;
+        for (int j = 0; j < L::NACC; ++j) {
+            uint32_t r[32];
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(32 * j);
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+                         "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+                         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                           "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+                           "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+                           "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+                           "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+                           "=r"(r[31])
+                         : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+            // row = (dz * 4 + slot) * 8 + e
+            const int slot = lane >> 3;
+            const int c = CIN == 32 ? lane : (lane & 7);
+            const int t = CIN == 32 ? 9 * warp + j : 9 * warp + 3 * j + slot;
+            if (CIN == 32 || slot < 3) {  // a CTA without tiles (never launched so) writes zeros
+#pragma unroll
+                for (int o = 0; o < 32; ++o)
+                    if (o < cout) dst[((size_t)o * CIN + c) * 27 + t] = first ? 0.f : __uint_as_float(r[o]);
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(L::COLS));
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -552,6 +983,12 @@ struct vlbm_closure {
     size_t off_W[3]{}, off_b[3]{};
     float *theta = nullptr, *mom = nullptr, *vel = nullptr, *grad = nullptr;
     uint2 *frag_fwd[3]{}, *frag_bwd[3]{};
+    vlbm::bf16 *wtc_fwd[3]{}, *wtc_bwd[3]{};  // weights in the tcgen05 layout
+    unsigned *errflag = nullptr;             // bounded-wait failures of closure kernels
+    unsigned *step_err = nullptr;            // where the running kernels report (errflag or a ctx flag)
+    int tc_grid = 0;                         // persistent CTAs of the tcgen05 convolution
+    int sms = 1;                             // streaming multiprocessors of the device
+    float *wpart = nullptr, *bpart = nullptr;  // per-CTA partial weight and bias gradients
     vlbm::bf16 *x = nullptr, *a1 = nullptr, *a2 = nullptr, *gy = nullptr, *gz = nullptr;
     float *dphi = nullptr, *gq = nullptr, *col_scale = nullptr;
     double *q = nullptr, *q1 = nullptr, *loss = nullptr;
@@ -575,6 +1012,17 @@ int nchunk(int cs) { return cs == 8 ? 14 : 54; }
 
 vlbm_status cl_check(cudaError_t e, const char *what) { return cuda_check(nullptr, e, what); }
 
+// After a synchronisation: a bounded device wait of a closure kernel gave up?
+vlbm_status cl_flags(vlbm_closure *cl)
+{
+    unsigned h = 0;
+    vlbm_status st = cl_check(cudaMemcpy(&h, cl->errflag, sizeof(unsigned), cudaMemcpyDeviceToHost),
+                              "closure flag read-back");
+    if (st == VLBM_OK && (h & kFlagTimeout))
+        return fail(nullptr, VLBM_ERR_TIMEOUT, "a closure kernel's bounded wait for its tensor-core work expired");
+    return st;
+}
+
 void *cl_alloc(vlbm_closure *cl, size_t bytes)
 {
     void *p = nullptr;
@@ -589,6 +1037,14 @@ void *cl_alloc(vlbm_closure *cl, size_t bytes)
 vlbm_status pack_all(vlbm_closure *cl, cudaStream_t s)
 {
     for (int l = 0; l < 3; ++l) {
+        const int ntc = nchunk(kCS[l]) * 512;
+        k_pack_tc<<<(ntc + 255) / 256, 256, 0, s>>>(cl->theta + cl->off_W[l], kCout[l], kCin[l], kCS[l], 0,
+                                                     cl->wtc_fwd[l]);
+        if (l > 0) {
+            const int nt = nchunk(32) * 512;
+            k_pack_tc<<<(nt + 255) / 256, 256, 0, s>>>(cl->theta + cl->off_W[l], kCout[l], kCin[l], 32, 1,
+                                                        cl->wtc_bwd[l]);
+        }
         const int total = nchunk(kCS[l]) * kNT[l] * 32;
         k_pack<<<(total + 255) / 256, 256, 0, s>>>(cl->theta + cl->off_W[l], kCout[l], kCin[l], kCS[l], kNT[l], 0,
                                                     cl->frag_fwd[l]);
@@ -601,8 +1057,27 @@ vlbm_status pack_all(vlbm_closure *cl, cudaStream_t s)
     return cl_check(cudaGetLastError(), "closure weight packing");
 }
 
+bool tc_grid_ok(const vlbm_closure *cl)
+{
+    return cl->nx % kTcX == 0 && cl->ny % kTcY == 0 && cl->nz % kTcZ == 0;
+}
+
 vlbm_status conv(vlbm_closure *cl, int layer, const bf16 *in, bool transpose, const ConvEpilogue &e, cudaStream_t s)
 {
+    if (tc_grid_ok(cl)) {
+        // tcgen05 / TMEM tiles of 8 x 16 cells
+        const int ntiles = (cl->nx / kTcX) * (cl->ny / kTcY) * (cl->nz / kTcZ);
+        const unsigned grid = (unsigned)std::min(ntiles, cl->tc_grid);
+        const int cout_real = transpose ? kCin[layer] : kCout[layer];
+        const bf16 *w = transpose ? cl->wtc_bwd[layer] : cl->wtc_fwd[layer];
+        const bool cs8 = !transpose && layer == 0;
+        const size_t shm = cs8 ? (size_t)14 * 1024 + kTcPlane : (size_t)54 * 1024 + 4 * kTcPlane;
+        if (cs8)
+            k_conv_tc<8><<<grid, kTcThreads, shm, s>>>(in, cl->nx, cl->ny, cl->nz, w, cout_real, e, cl->step_err);
+        else
+            k_conv_tc<32><<<grid, kTcThreads, shm, s>>>(in, cl->nx, cl->ny, cl->nz, w, cout_real, e, cl->step_err);
+        return cl_check(cudaGetLastError(), "closure tcgen05 convolution launch");
+    }
     if (cl->nx % kTx == 0 && cl->ny % kTy == 0) {
         // shared-memory staged tiles (16 x 8 cells per CTA)
         const dim3 grid((unsigned)(cl->nx / kTx), (unsigned)(cl->ny / kTy), (unsigned)cl->nz);
@@ -670,14 +1145,27 @@ vlbm_status backward(vlbm_closure *cl, cudaStream_t s)
 {
     vlbm_status st = cl_check(cudaMemsetAsync(cl->grad, 0, cl->nparam * sizeof(float), s), "closure grad clear");
     const unsigned wgx = (unsigned)((cl->N + kWgradCells - 1) / kWgradCells);
+    const bool tc = tc_grid_ok(cl);
+    const int ntiles = (cl->nx / 8) * (cl->ny / 16) * (cl->nz / kWgZ);
+    const unsigned wg_grid = (unsigned)std::min(ntiles, cl->sms), b_grid = (unsigned)(2 * cl->sms);
     auto wgrad = [&](int l, const bf16 *g, const bf16 *a) {
-        if (kCS[l] == 8)
-            k_wgrad<8><<<dim3(wgx, 27), kConvThreads, 0, s>>>(g, a, cl->nx, cl->ny, cl->nz, kCout[l], kCin[l],
-                                                              cl->grad + cl->off_W[l]);
-        else
-            k_wgrad<32><<<dim3(wgx, 27), kConvThreads, 0, s>>>(g, a, cl->nx, cl->ny, cl->nz, kCout[l], kCin[l],
-                                                               cl->grad + cl->off_W[l]);
-        k_bgrad<<<dim3(64, kCout[l]), 256, 0, s>>>(g, cl->N, kCout[l], cl->grad + cl->off_b[l]);
+        float *gW = cl->grad + cl->off_W[l];
+        if (tc) {  // tensor cores; per-CTA partials summed in a fixed order
+            const int count = kCout[l] * kCin[l] * 27;
+            if (kCS[l] == 8)
+                k_wgrad_tc<8><<<wg_grid, kTcThreads, 2 * WgLayout<8>::BUF, s>>>(g, a, cl->nx, cl->ny, cl->nz,
+                                                                                kCout[l], cl->wpart, cl->step_err);
+            else
+                k_wgrad_tc<32><<<wg_grid, kTcThreads, 2 * WgLayout<32>::BUF, s>>>(g, a, cl->nx, cl->ny, cl->nz,
+                                                                                  kCout[l], cl->wpart, cl->step_err);
+            k_part_sum<<<(count + 255) / 256, 256, 0, s>>>(cl->wpart, (int)wg_grid, count, gW);
+        } else if (kCS[l] == 8) {
+            k_wgrad<8><<<dim3(wgx, 27), kConvThreads, 0, s>>>(g, a, cl->nx, cl->ny, cl->nz, kCout[l], kCin[l], gW);
+        } else {
+            k_wgrad<32><<<dim3(wgx, 27), kConvThreads, 0, s>>>(g, a, cl->nx, cl->ny, cl->nz, kCout[l], kCin[l], gW);
+        }
+        k_bgrad_part<<<b_grid, 256, 0, s>>>(g, cl->N, kCout[l], cl->bpart);
+        k_part_sum<<<1, 256, 0, s>>>(cl->bpart, (int)b_grid, kCout[l], cl->grad + cl->off_b[l]);
         return cl_check(cudaGetLastError(), "closure weight gradient launch");
     };
     // layer 3: gy -> W3, b3; data gradient through tanh of layer 2 -> gz
@@ -750,7 +1238,11 @@ vlbm_status vlbm_closure_create(const vlbm_closure_params *p, vlbm_closure **out
     for (int l = 0; l < 3; ++l) {
         cl->frag_fwd[l] = (uint2 *)A((size_t)nchunk(kCS[l]) * kNT[l] * 32 * sizeof(uint2));
         cl->frag_bwd[l] = (uint2 *)A((size_t)nchunk(32) * 4 * 32 * sizeof(uint2));
+        cl->wtc_fwd[l] = (bf16 *)A((size_t)nchunk(kCS[l]) * 512 * sizeof(bf16));
+        cl->wtc_bwd[l] = (bf16 *)A((size_t)nchunk(32) * 512 * sizeof(bf16));
     }
+    cl->errflag = (unsigned *)A(64);
+    cl->step_err = cl->errflag;
     cl->x = (bf16 *)A(N * 8 * 2);
     cl->a1 = (bf16 *)A(N * 32 * 2);
     cl->a2 = (bf16 *)A(N * 32 * 2);
@@ -762,9 +1254,39 @@ vlbm_status vlbm_closure_create(const vlbm_closure_params *p, vlbm_closure **out
     cl->q1 = (double *)A(N * 8 * 8);
     cl->loss = (double *)A(64);
     cl->col_scale = (float *)A(32 * 4);
+    {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&cl->sms, cudaDevAttrMultiProcessorCount, dev);
+        cl->sms = std::max(cl->sms, 1);
+    }
+    cl->wpart = (float *)A((size_t)cl->sms * 32 * 32 * 27 * 4);
+    cl->bpart = (float *)A((size_t)2 * cl->sms * 32 * 4);
     if (!ok) {
         vlbm_closure_destroy(cl);
         return st != VLBM_OK ? st : fail(nullptr, VLBM_ERR_OOM, "closure allocation failed");
+    }
+    if (ok) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cl->tc_grid = 2 * std::max(sms, 1);
+        const int shm32 = 54 * 1024 + 4 * kTcPlane, shm8 = 14 * 1024 + kTcPlane;
+        st = cl_check(cudaFuncSetAttribute(k_conv_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm32),
+                      "closure tcgen05 shared memory");
+        if (st == VLBM_OK)
+            st = cl_check(cudaFuncSetAttribute(k_conv_tc<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm8),
+                          "closure tcgen05 shared memory");
+        if (st == VLBM_OK)
+            st = cl_check(cudaFuncSetAttribute(k_wgrad_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               2 * WgLayout<32>::BUF),
+                          "closure tcgen05 shared memory");
+        if (st == VLBM_OK)
+            st = cl_check(cudaFuncSetAttribute(k_wgrad_tc<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               2 * WgLayout<8>::BUF),
+                          "closure tcgen05 shared memory");
+        if (st == VLBM_OK) st = cl_check(cudaMemsetAsync(cl->errflag, 0, 64, cl->stream), "closure flag clear");
+        ok = st == VLBM_OK;
     }
     float cs[32] = {};
     for (int j = 0; j < kOut; ++j) cs[j] = (float)p->out_scale[j / 3];
@@ -820,6 +1342,7 @@ vlbm_status vlbm_closure_forward(vlbm_closure *cl, const double *Q_dev, float *d
     if (!cl || !Q_dev || !dphi_dev) return VLBM_ERR_ARG;
     vlbm_status st = forward(cl, Q_dev, dphi_dev, cl->stream);
     if (st == VLBM_OK) st = cl_check(cudaStreamSynchronize(cl->stream), "closure forward");
+    if (st == VLBM_OK) st = cl_flags(cl);
     return st;
 }
 
@@ -836,6 +1359,7 @@ vlbm_status vlbm_closure_backward(vlbm_closure *cl, const double *Q_dev, const f
         st = cl_check(cudaMemcpyAsync(grads_host, cl->grad, cl->nparam * 4, cudaMemcpyDeviceToHost, cl->stream),
                       "closure gradient download");
     if (st == VLBM_OK) st = cl_check(cudaStreamSynchronize(cl->stream), "closure backward");
+    if (st == VLBM_OK) st = cl_flags(cl);
     return st;
 }
 
@@ -876,6 +1400,7 @@ vlbm_status loss_backward_update(vlbm_closure *cl, const double *Qt_dev, double 
     double h = 0.0;
     if (st == VLBM_OK) st = cl_check(cudaMemcpyAsync(&h, cl->loss, sizeof(double), cudaMemcpyDeviceToHost, s), "loss");
     if (st == VLBM_OK) st = cl_check(cudaStreamSynchronize(s), "closure train step");
+    if (st == VLBM_OK) st = cl_flags(cl);
     if (loss) *loss = h;
     return st;
 }
@@ -953,7 +1478,9 @@ vlbm_status closure_step(vlbm_ctx *c, int parity)
 {
     vlbm_closure *cl = c->closure;
     vlbm_status st = ideal_moments(c, 0, cl->q);
+    cl->step_err = c->d_flags;  // timeouts surface through the context's health word
     if (st == VLBM_OK) st = forward(cl, cl->q, cl->dphi, c->stream);
+    cl->step_err = cl->errflag;
     c->launches += 4;  // features and three convolutions (moments and the step count themselves)
     if (st == VLBM_OK) st = ideal_step_corrected(c, parity, cl->dphi);
     return st;

@@ -63,9 +63,16 @@ def setup_closure(V, shape, seed, last_scale=1.0):
     return cl, f0, Qd, pw, mu, sigma, out_scale
 
 
-def test_closure_forward_matches_reference(V):
+# grids per convolution kernel: tcgen05/TMEM (nx % 8, ny % 16, nz % 2), shared-memory
+# mma.sync (nx % 16, ny % 8), global-load mma.sync (anything with nx % 16).
+# (10, 48, 96) has 180 tiles of 8 x 16 x 2 cells: more than one tile per
+# persistent weight-gradient CTA, so the staging pipeline runs.
+CONV_SHAPES = [(4, 16, 16), (2, 32, 48), (6, 8, 32), (4, 6, 16), (10, 48, 96)]
+
+
+@pytest.mark.parametrize("shape", CONV_SHAPES)
+def test_closure_forward_matches_reference(V, shape):
     import torch
-    shape = (6, 8, 32)
     cl, f0, Qd, pw, mu, sigma, out_scale = setup_closure(V, shape, 51)
     dphi = torch.empty((np.prod(shape), 24), dtype=torch.float32, device="cuda")
     cl.forward(Qd.data_ptr(), dphi.data_ptr())
@@ -79,9 +86,9 @@ def test_closure_forward_matches_reference(V):
     cl.close()
 
 
-def test_closure_backward_matches_reference(V):
+@pytest.mark.parametrize("shape", CONV_SHAPES)
+def test_closure_backward_matches_reference(V, shape):
     import torch
-    shape = (4, 6, 16)
     cl, f0, Qd, pw, mu, sigma, out_scale = setup_closure(V, shape, 52)
     N = int(np.prod(shape))
     rng = np.random.default_rng(9)
@@ -95,9 +102,9 @@ def test_closure_backward_matches_reference(V):
     cl.close()
 
 
-def test_corrected_step_matches_reference(V):
+@pytest.mark.parametrize("shape", [(6, 8, 32), (4, 16, 16)])
+def test_corrected_step_matches_reference(V, shape):
     import torch
-    shape = (6, 8, 32)
     cl, f0, Qd, pw, mu, sigma, out_scale = setup_closure(V, shape, 53)
     N = int(np.prod(shape))
     dphi = torch.empty((N, 24), dtype=torch.float32, device="cuda")
