@@ -94,6 +94,15 @@ struct ConvEpilogue {
     int os;
 };
 
+// tanh on the special-function unit (tanh.approx.f32, relative error below
+// 2^-10.9); the activations it feeds are stored in BF16 (2^-8).
+__device__ __forceinline__ float tanh_fast(float x)
+{
+    float y;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 template <int CS, int NT>
 __global__ void __launch_bounds__(kConvThreads) k_conv(const bf16 *__restrict__ act, int nx, int ny, int nz,
                                                        const uint2 *__restrict__ frag, const ConvEpilogue e)
@@ -152,8 +161,8 @@ __global__ void __launch_bounds__(kConvThreads) k_conv(const bf16 *__restrict__ 
                 v1 += e.bias[col + 1];
             }
             if (e.tanh_act) {
-                v0 = tanhf(v0);
-                v1 = tanhf(v1);
+                v0 = tanh_fast(v0);
+                v1 = tanh_fast(v1);
             }
             if (e.deriv) {
                 const float d0 = __bfloat162float(e.deriv[(size_t)cell * 32 + col]);
@@ -261,8 +270,8 @@ __global__ void __launch_bounds__(kTx * kTy * 2) k_conv_smem(const bf16 *__restr
                 v1 += e.bias[col + 1];
             }
             if (e.tanh_act) {
-                v0 = tanhf(v0);
-                v1 = tanhf(v1);
+                v0 = tanh_fast(v0);
+                v1 = tanh_fast(v1);
             }
             if (e.deriv) {
                 const float d0 = __bfloat162float(e.deriv[(size_t)cell * 32 + col]);
@@ -302,12 +311,18 @@ __global__ void __launch_bounds__(kTx * kTy * 2) k_conv_smem(const bf16 *__restr
 // weights once, then one tile after another; one thread issues the MMAs,
 // tcgen05.commit arrives on an mbarrier (bounded wait), and each warp reads
 // its 32 TMEM lanes (= its 32 cells) with tcgen05.ld.
-constexpr int kTcX = 8, kTcY = 16, kTcZ = 2;  // kTcZ z-slices per tile = kTcZ M-blocks
+constexpr int kTcX = 8, kTcY = 16, kTcZ = 2;  // kTcZ z-slices per tile = kTcZ M-blocks of 128 cells
 constexpr int kTcHx = kTcX + 2, kTcHy = kTcY + 2, kTcHz = kTcZ + 2, kTcHalo = kTcHx * kTcHy * kTcHz;
 constexpr int kTcPlane = kTcHalo * 16;  // bytes per channel-block plane
-constexpr int kTcThreads = 128;
-constexpr int kTcCols = 32 * kTcZ;      // TMEM columns: one 32-column accumulator per z-slice
+constexpr int kTcThreads = 288;         // warps 0-7 stage and drain, warp 8 issues the MMAs
+constexpr int kTcCols = 2 * 32 * kTcZ;  // TMEM columns: two tiles' accumulators, 32 columns per z-slice
 constexpr uint32_t kTcWaitLimit = 1u << 24;
+
+template <int CS>
+constexpr int tc_smem_bytes()
+{
+    return (CS == 8 ? 14 : 54) * 1024 + 2 * (CS / 8) * kTcPlane;
+}
 
 __device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
 {
@@ -318,6 +333,13 @@ __device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32
     return d;
 }
 
+__device__ __forceinline__ void tc_mma(uint32_t dacc, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc)
+{
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+                 ::"r"(dacc), "l"(da), "l"(db), "r"(idesc), "r"(acc));
+}
+
 // byte offset, inside a plane, of the first row of tap t for z-slice zz
 __device__ __forceinline__ int tc_tap_ofs(int t, int zz)
 {
@@ -325,6 +347,15 @@ __device__ __forceinline__ int tc_tap_ofs(int t, int zz)
     return (((dz + zz) * kTcHy + dy) * kTcHx + dx) * 16;
 }
 
+// 3x3x3 convolution on the tcgen05 tensor cores.  Tile = 8 (x) x 16 (y) x 2 (z)
+// cells; each z-slice is one M = 128 block, N = 32 output channels, K = the
+// 27 taps x CS input channels in chunks of 16.  A operand: the tile's halo,
+// staged as 16-byte channel-block planes, so that a tap is an address offset
+// (K-major, no swizzle); B operand: the weights, resident in shared memory for
+// the whole kernel.  Persistent CTAs with two halo buffers and two TMEM
+// accumulator sets: while the tensor cores work on tile i, the CTA stages
+// tile i+1 with cp.async and drains tile i-1 from TMEM (tanh derivative or
+// bias, tanh, scale; BF16 or FP32 store).  Warp 8 only issues the MMAs.
 template <int CS>
 __global__ void __launch_bounds__(kTcThreads) k_conv_tc(const bf16 *__restrict__ act, int nx, int ny, int nz,
                                                         const bf16 *__restrict__ wtc, int cout_real,
@@ -333,18 +364,24 @@ __global__ void __launch_bounds__(kTcThreads) k_conv_tc(const bf16 *__restrict__
     constexpr int NCHUNK = CS == 8 ? 14 : 54;
     constexpr int NPLANE = CS / 8;
     constexpr int WBYTES = NCHUNK * 1024;  // 4 n-groups x 2 k-halves x 128 bytes per chunk
+    constexpr int HBYTES = NPLANE * kTcPlane;
     extern __shared__ __align__(1024) unsigned char smem[];
-    unsigned char *sw = smem;                       // weights
-    unsigned char *sa = smem + WBYTES;              // halo planes
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_base;
+    __shared__ float s_bias[32], s_scale[32];
+    constexpr int kStageThreads = 256;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int tiles_x = nx / kTcX, tiles_y = ny / kTcY, tiles_z = nz / kTcZ;
     const int ntiles = tiles_x * tiles_y * tiles_z;
     const int plane = nx * ny;
+    const int n_my = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
 
     for (int i = tid; i < WBYTES / 16; i += kTcThreads)
-        reinterpret_cast<uint4 *>(sw)[i] = __ldg(reinterpret_cast<const uint4 *>(wtc) + i);
+        reinterpret_cast<uint4 *>(smem)[i] = __ldg(reinterpret_cast<const uint4 *>(wtc) + i);
+    if (tid < 32) {  // absent bias / scale: 0 / 1, exact
+        s_bias[tid] = e.bias && tid < cout_real ? e.bias[tid] : 0.f;
+        s_scale[tid] = e.scale && tid < cout_real ? e.scale[tid] : 1.f;
+    }
     if (warp == 0) {
         const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&tmem_base);
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(dst), "r"(kTcCols));
@@ -355,21 +392,27 @@ __global__ void __launch_bounds__(kTcThreads) k_conv_tc(const bf16 *__restrict__
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb));
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     const uint32_t tmem = tmem_base;
-    const uint32_t sw_s = (uint32_t)__cvta_generic_to_shared(sw);
-    const uint32_t sa_s = (uint32_t)__cvta_generic_to_shared(sa);
+    const uint32_t sw_s = (uint32_t)__cvta_generic_to_shared(smem);
+    const uint32_t sh_s = sw_s + WBYTES;
     const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
-    uint32_t phase = 0;
-    bool ok = true;
 
-    for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-        const int tx = tile % tiles_x, ty = (tile / tiles_x) % tiles_y, tz = tile / (tiles_x * tiles_y);
-        const int x0 = tx * kTcX, y0 = ty * kTcY, z0 = tz * kTcZ;
-        // stage the halo box as channel-block planes: every 16-byte piece in flight at once
-        for (int idx = tid; idx < kTcHalo * NPLANE; idx += kTcThreads) {
+    auto origin = [&](int i, int &x0, int &y0, int &z0) {
+        const int tile = (int)blockIdx.x + i * (int)gridDim.x;
+        x0 = (tile % tiles_x) * kTcX;
+        y0 = ((tile / tiles_x) % tiles_y) * kTcY;
+        z0 = (tile / (tiles_x * tiles_y)) * kTcZ;
+    };
+    // halo of tile i into buffer b, as channel-block planes; every 16-byte piece in flight at once
+    auto stage = [&](int i, int b) {
+        int x0, y0, z0;
+        origin(i, x0, y0, z0);
+        const uint32_t hb = sh_s + (uint32_t)(b * HBYTES);
+        for (int idx = tid; idx < kTcHalo * NPLANE; idx += kStageThreads) {
             const int cb = idx % NPLANE, c = idx / NPLANE;
             const int bx = c % kTcHx, by = (c / kTcHx) % kTcHy, bz = c / (kTcHx * kTcHy);
             int gx = x0 - 1 + bx, gy = y0 - 1 + by, gz = z0 - 1 + bz;
@@ -377,101 +420,133 @@ __global__ void __launch_bounds__(kTcThreads) k_conv_tc(const bf16 *__restrict__
             gy += gy < 0 ? ny : (gy >= ny ? -ny : 0);
             gz += gz < 0 ? nz : (gz >= nz ? -nz : 0);
             const size_t cell = (size_t)gx + (size_t)nx * gy + (size_t)plane * gz;
-            const uint32_t dst = sa_s + (uint32_t)(cb * kTcPlane + c * 16);
+            const uint32_t dst = hb + (uint32_t)(cb * kTcPlane + c * 16);
             asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(act + cell * CS + cb * 8)
                          : "memory");
         }
         asm volatile("cp.async.commit_group;\n" ::: "memory");
-        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        __syncthreads();
-        if (tid == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-            for (int zz = 0; zz < kTcZ; ++zz) {
-                const uint32_t dacc = tmem + (uint32_t)(32 * zz);  // accumulator columns of slice zz
+    };
+    // all MMAs of the tile in buffer b into accumulator set b (one thread)
+    auto issue = [&](int b) {
+        const uint32_t hb = sh_s + (uint32_t)(b * HBYTES);
+        const uint64_t db0 = tc_desc(sw_s, 128, 256);
+        for (int zz = 0; zz < kTcZ; ++zz) {
+            const uint32_t dacc = tmem + (uint32_t)(b * 32 * kTcZ + zz * 32);
+            if (CS == 32) {  // chunk 2t + h: tap t, channel blocks 2h and 2h + 1
+                const uint64_t da0 = tc_desc(hb, kTcPlane, kTcHx * 16);
+                int j = 0;
+                for (int dz = 0; dz < 3; ++dz)
+                    for (int dy = 0; dy < 3; ++dy)
+                        for (int dx = 0; dx < 3; ++dx) {
+                            const uint32_t ofs = (uint32_t)((((dz + zz) * kTcHy + dy) * kTcHx + dx) * 16);
+#pragma unroll
+                            for (int h = 0; h < 2; ++h, ++j)
+                                tc_mma(dacc, da0 + ((ofs + (uint32_t)(h * 2 * kTcPlane)) >> 4),
+                                       db0 + (uint64_t)(j * 64), idesc, j > 0);
+                        }
+            } else {         // chunk j: taps 2j and 2j + 1 of the single plane
                 for (int j = 0; j < NCHUNK; ++j) {
-                    uint32_t a_addr, lbo;
-                    if (CS == 32) {  // chunk j: tap j/2, planes 2(j%2) and 2(j%2)+1
-                        a_addr = sa_s + (uint32_t)((j & 1) * 2 * kTcPlane + tc_tap_ofs(j >> 1, zz));
-                        lbo = kTcPlane;
-                    } else {         // chunk j: taps 2j and 2j+1 of the single plane
-                        const int t0 = 2 * j, t1 = 2 * j + 1;
-                        a_addr = sa_s + (uint32_t)tc_tap_ofs(t0, zz);
-                        lbo = t1 < 27 ? (uint32_t)(tc_tap_ofs(t1, zz) - tc_tap_ofs(t0, zz)) : 0u;  // padding: zero weights
-                    }
-                    const uint64_t da = tc_desc(a_addr, lbo, kTcHx * 16);
-                    const uint64_t db = tc_desc(sw_s + (uint32_t)(j * 1024), 128, 256);
-                    const uint32_t acc = j > 0;
-                    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
-                                 ::"r"(dacc), "l"(da), "l"(db), "r"(idesc), "r"(acc));
+                    const int t0 = 2 * j, t1 = 2 * j + 1;
+                    const uint32_t lbo = t1 < 27 ? (uint32_t)(tc_tap_ofs(t1, zz) - tc_tap_ofs(t0, zz)) : 0u;
+                    tc_mma(dacc, tc_desc(hb + (uint32_t)tc_tap_ofs(t0, zz), lbo, kTcHx * 16),
+                           db0 + (uint64_t)(j * 64), idesc, j > 0);  // padding tap: zero weights
                 }
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mb));
         }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mb));
+    };
+    // drain tile i from accumulator set b: warp w reads TMEM lanes 32 (w % 4) .. (rows), z-slice w / 4
+    auto drain = [&](int i, int b) {
+        int x0, y0, z0;
+        origin(i, x0, y0, z0);
+        const int q = warp & 3, zz = warp >> 2;
+        const int m = q * 32 + lane;  // tile row = x + 8 y
+        uint32_t r[32];
+        const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * 32 * kTcZ + zz * 32);
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+                     "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                       "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                       "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+                       "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+                       "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                     : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+        const size_t cell = (size_t)(x0 + (m & 7)) + (size_t)nx * (y0 + (m >> 3)) + (size_t)plane * (z0 + zz);
+        float v[32];
+        if (e.deriv) {
+            const uint4 *dp = reinterpret_cast<const uint4 *>(e.deriv + cell * 32);
+#pragma unroll
+            for (int qd = 0; qd < 4; ++qd) {
+                const uint4 dv = __ldg(dp + qd);
+                const bf16 *dh = reinterpret_cast<const bf16 *>(&dv);
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    const float d = __bfloat162float(dh[c]);
+                    v[qd * 8 + c] = __uint_as_float(r[qd * 8 + c]) * (1.f - d * d);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < 32; ++c) v[c] = __uint_as_float(r[c]);
+        }
+        if (e.tanh_act) {
+#pragma unroll
+            for (int c = 0; c < 32; ++c) v[c] = tanh_fast(v[c] + s_bias[c]) * s_scale[c];
+        } else {
+#pragma unroll
+            for (int c = 0; c < 32; ++c) v[c] = (v[c] + s_bias[c]) * s_scale[c];
+        }
+        if (e.out_bf) {
+            __align__(16) bf16 o[32];
+#pragma unroll
+            for (int c = 0; c < 32; ++c) o[c] = __float2bfloat16_rn(c < cout_real ? v[c] : 0.f);
+            uint4 *dst = reinterpret_cast<uint4 *>(e.out_bf + cell * e.os);
+#pragma unroll
+            for (int qd = 0; qd < 4; ++qd) dst[qd] = reinterpret_cast<const uint4 *>(o)[qd];
+        } else {
+            float *dst = e.out_f + cell * e.os;
+#pragma unroll
+            for (int c = 0; c < 32; c += 4)
+                if (c < cout_real) *reinterpret_cast<float4 *>(dst + c) = make_float4(v[c], v[c + 1], v[c + 2], v[c + 3]);
+        }
+    };
+
+    bool ok = true;
+    if (n_my > 0 && warp < 8) stage(0, 0);
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    __syncthreads();
+    for (int i = 0; i < n_my && ok; ++i) {
+        const int b = i & 1;
+        if (warp == 8) {
+            if (lane == 0) {
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                issue(b);
+            }
+        } else {
+            if (i + 1 < n_my) stage(i + 1, b ^ 1);
+            if (i > 0) drain(i - 1, b ^ 1);
+        }
+        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         uint32_t done = 0;
         for (uint32_t it = 0; it < kTcWaitLimit && !done; ++it)
             asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
                          "selp.u32 %0, 1, 0, p;\n\t}\n"
                          : "=r"(done)
-                         : "r"(mb), "r"(phase));
+                         : "r"(mb), "r"((uint32_t)b));
+        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
         // one outcome for the whole CTA, so that no thread leaves the loop alone
-        const int all_done = __syncthreads_and((int)done);
-        phase ^= 1u;
-        if (!all_done) {
+        if (!__syncthreads_and((int)done)) {
             if (tid == 0) atomicOr(err, kFlagTimeout);
             ok = false;
         }
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-        if (all_done) {
-            const int m = warp * 32 + lane;  // TMEM lane = tile row
-            for (int zz = 0; zz < kTcZ; ++zz) {
-                uint32_t r[32];
-                const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(32 * zz);
-                asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
-                             "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
-                             : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-                               "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-                               "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
-                               "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-                               "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
-                               "=r"(r[31])
-                             : "r"(taddr));
-                asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-                const size_t cell =
-                    (size_t)(x0 + (m & 7)) + (size_t)nx * (y0 + (m >> 3)) + (size_t)plane * (z0 + zz);
-                float v[32];
-#pragma unroll
-                for (int c = 0; c < 32; ++c) {
-                    float x = __uint_as_float(r[c]);
-                    if (e.bias && c < cout_real) x += e.bias[c];
-                    if (e.tanh_act) x = tanhf(x);
-                    if (e.deriv) {
-                        const float d = __bfloat162float(e.deriv[cell * 32 + c]);
-                        x *= 1.f - d * d;
-                    }
-                    if (e.scale && c < cout_real) x *= e.scale[c];
-                    v[c] = x;
-                }
-                if (e.out_bf) {
-                    __align__(16) bf16 o[32];
-#pragma unroll
-                    for (int c = 0; c < 32; ++c) o[c] = __float2bfloat16_rn(c < cout_real ? v[c] : 0.f);
-                    uint4 *dst = reinterpret_cast<uint4 *>(e.out_bf + cell * e.os);
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) dst[q] = reinterpret_cast<const uint4 *>(o)[q];
-                } else {
-                    float *dst = e.out_f + cell * e.os;
-#pragma unroll
-                    for (int c = 0; c < 32; c += 4)
-                        if (c < cout_real)
-                            *reinterpret_cast<float4 *>(dst + c) = make_float4(v[c], v[c + 1], v[c + 2], v[c + 3]);
-                }
-            }
-        }
-        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-        __syncthreads();  // TMEM read and halo consumed before the next tile reuses them
     }
+    if (ok && n_my > 0 && warp < 8) drain(n_my - 1, (n_my - 1) & 1);
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
     if (warp == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTcCols));
@@ -656,15 +731,28 @@ __global__ void __launch_bounds__(256) k_bgrad_part(const bf16 *__restrict__ gz,
     }
 }
 
-// out[j] += sum over blocks b of part[b * count + j], in block order
+// out[j] += sum over blocks b of part[b * count + j]: a CTA takes 32 outputs,
+// warp w sums the blocks b = w mod 8, then the eight sums are added in order
+// (a fixed order, so the result does not depend on scheduling)
 __global__ void __launch_bounds__(256) k_part_sum(const float *__restrict__ part, int nblk, int count,
                                                   float *__restrict__ out)
 {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= count) return;
+    __shared__ float red[8][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int j = blockIdx.x * 32 + lane;
     float s = 0.f;
-    for (int b = 0; b < nblk; ++b) s += part[(size_t)b * count + j];
-    out[j] += s;
+    if (j < count) {
+#pragma unroll 4
+        for (int b = w; b < nblk; b += 8) s += __ldg(part + (size_t)b * count + j);
+    }
+    red[w][lane] = s;
+    __syncthreads();
+    if (w == 0 && j < count) {
+        float t = 0.f;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) t += red[q][lane];
+        out[j] += t;
+    }
 }
 
 // Weight gradient on the tcgen05 tensor cores:
@@ -681,9 +769,12 @@ __global__ void __launch_bounds__(256) k_part_sum(const float *__restrict__ part
 //   B (N = 32) = the output-channel gradients of the tile's cells.
 // Tiles of 8 x 16 x kWgZ cells; persistent CTAs (one per SM: the two staging
 // buffers take more than half of the shared memory) accumulate all their
-// tiles in TMEM while the next tile is staged with cp.async, then write one
-// partial gradient per CTA (summed in fixed order by k_part_sum).
+// tiles in TMEM while the next tile is staged with cp.async (warps 0-7; warp
+// 8 issues the MMAs), then write one partial gradient per CTA (summed in
+// fixed order by k_part_sum).
 constexpr int kWgZ = 2;
+constexpr int kWgThreads = 288;  // warps 0-7 stage, warp 8 issues the MMAs, warps 0-2 drain
+constexpr int kWgStage = 256;
 
 template <int CIN>
 struct WgLayout {
@@ -697,7 +788,7 @@ struct WgLayout {
 };
 
 template <int CIN>
-__global__ void __launch_bounds__(kTcThreads) k_wgrad_tc(const bf16 *__restrict__ gz, const bf16 *__restrict__ act,
+__global__ void __launch_bounds__(kWgThreads) k_wgrad_tc(const bf16 *__restrict__ gz, const bf16 *__restrict__ act,
                                                          int nx, int ny, int nz, int cout,
                                                          float *__restrict__ part, unsigned *err)
 {
@@ -712,7 +803,7 @@ __global__ void __launch_bounds__(kTcThreads) k_wgrad_tc(const bf16 *__restrict_
     const uint32_t s_base = (uint32_t)__cvta_generic_to_shared(smem);
 
     // slots that are never staged feed only discarded rows: clear them once
-    for (int i = tid; i < 2 * L::BUF / 16; i += kTcThreads) reinterpret_cast<uint4 *>(smem)[i] = make_uint4(0, 0, 0, 0);
+    for (int i = tid; i < 2 * L::BUF / 16; i += kWgThreads) reinterpret_cast<uint4 *>(smem)[i] = make_uint4(0, 0, 0, 0);
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     if (warp == 0) {
         const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&tmem_base);
@@ -734,7 +825,7 @@ __global__ void __launch_bounds__(kTcThreads) k_wgrad_tc(const bf16 *__restrict_
         const int x0 = tx * 8, y0 = ty * 16, z0 = tz * kWgZ;
         const uint32_t abase = s_base + (uint32_t)(b * L::BUF), gbase = abase + L::ABYTES;
         constexpr int NA = CIN == 32 ? (kWgZ + 2) * 4 * 18 * 10 : (kWgZ + 2) * 3 * 18 * 8;
-        for (int idx = tid; idx < NA; idx += kTcThreads) {
+        for (int idx = tid; idx < NA; idx += kWgStage) {
             int slot, bx, by, h, sx;
             if (CIN == 32) {  // slot = channel block; consecutive threads read one cell's 64 bytes
                 slot = idx & 3;
@@ -760,7 +851,7 @@ __global__ void __launch_bounds__(kTcThreads) k_wgrad_tc(const bf16 *__restrict_
             const bf16 *src = act + cell * CIN + (CIN == 32 ? slot * 8 : 0);
             asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
         }
-        for (int idx = tid; idx < 4 * kWgZ * 128; idx += kTcThreads) {
+        for (int idx = tid; idx < 4 * kWgZ * 128; idx += kWgStage) {
             const int cbo = idx & 3, c = idx >> 2;  // c = zz * 128 + y * 8 + x
             const size_t cell = (size_t)(x0 + (c & 7)) + (size_t)nx * (y0 + ((c >> 3) & 15)) +
                                 (size_t)plane * (z0 + (c >> 7));
@@ -777,12 +868,12 @@ __global__ void __launch_bounds__(kTcThreads) k_wgrad_tc(const bf16 *__restrict_
     uint32_t phase = 0;
     bool ok = true, first = true;
     int b = 0;
-    if ((int)blockIdx.x < ntiles) stage(blockIdx.x, 0);
+    if ((int)blockIdx.x < ntiles && warp < 8) stage(blockIdx.x, 0);
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     __syncthreads();
     for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-        if (tid == 0) {
+        if (tid == 8 * 32) {
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
             const uint32_t abase = s_base + (uint32_t)(b * L::BUF), gbase = abase + L::ABYTES;
             for (int zz = 0; zz < kWgZ; ++zz)
@@ -803,7 +894,7 @@ __global__ void __launch_bounds__(kTcThreads) k_wgrad_tc(const bf16 *__restrict_
         }
         // stage the next tile into the other buffer while the tensor cores work
         const int next = tile + (int)gridDim.x;
-        if (next < ntiles) stage(next, b ^ 1);
+        if (next < ntiles && warp < 8) stage(next, b ^ 1);
         asm volatile("cp.async.wait_group 0;\n" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         uint32_t done = 0;
@@ -986,7 +1077,6 @@ struct vlbm_closure {
     vlbm::bf16 *wtc_fwd[3]{}, *wtc_bwd[3]{};  // weights in the tcgen05 layout
     unsigned *errflag = nullptr;             // bounded-wait failures of closure kernels
     unsigned *step_err = nullptr;            // where the running kernels report (errflag or a ctx flag)
-    int tc_grid = 0;                         // persistent CTAs of the tcgen05 convolution
     int sms = 1;                             // streaming multiprocessors of the device
     float *wpart = nullptr, *bpart = nullptr;  // per-CTA partial weight and bias gradients
     vlbm::bf16 *x = nullptr, *a1 = nullptr, *a2 = nullptr, *gy = nullptr, *gz = nullptr;
@@ -1066,16 +1156,17 @@ vlbm_status conv(vlbm_closure *cl, int layer, const bf16 *in, bool transpose, co
 {
     if (tc_grid_ok(cl)) {
         // tcgen05 / TMEM tiles of 8 x 16 cells
+        // persistent CTAs: one per SM for 32 input channels (the two halo buffers and
+        // the weights fill most of the shared memory), two per SM for 8
         const int ntiles = (cl->nx / kTcX) * (cl->ny / kTcY) * (cl->nz / kTcZ);
-        const unsigned grid = (unsigned)std::min(ntiles, cl->tc_grid);
         const int cout_real = transpose ? kCin[layer] : kCout[layer];
         const bf16 *w = transpose ? cl->wtc_bwd[layer] : cl->wtc_fwd[layer];
-        const bool cs8 = !transpose && layer == 0;
-        const size_t shm = cs8 ? (size_t)14 * 1024 + kTcPlane : (size_t)54 * 1024 + 4 * kTcPlane;
-        if (cs8)
-            k_conv_tc<8><<<grid, kTcThreads, shm, s>>>(in, cl->nx, cl->ny, cl->nz, w, cout_real, e, cl->step_err);
+        if (!transpose && layer == 0)
+            k_conv_tc<8><<<(unsigned)std::min(ntiles, 2 * cl->sms), kTcThreads, tc_smem_bytes<8>(), s>>>(
+                in, cl->nx, cl->ny, cl->nz, w, cout_real, e, cl->step_err);
         else
-            k_conv_tc<32><<<grid, kTcThreads, shm, s>>>(in, cl->nx, cl->ny, cl->nz, w, cout_real, e, cl->step_err);
+            k_conv_tc<32><<<(unsigned)std::min(ntiles, cl->sms), kTcThreads, tc_smem_bytes<32>(), s>>>(
+                in, cl->nx, cl->ny, cl->nz, w, cout_real, e, cl->step_err);
         return cl_check(cudaGetLastError(), "closure tcgen05 convolution launch");
     }
     if (cl->nx % kTx == 0 && cl->ny % kTy == 0) {
@@ -1153,12 +1244,12 @@ vlbm_status backward(vlbm_closure *cl, cudaStream_t s)
         if (tc) {  // tensor cores; per-CTA partials summed in a fixed order
             const int count = kCout[l] * kCin[l] * 27;
             if (kCS[l] == 8)
-                k_wgrad_tc<8><<<wg_grid, kTcThreads, 2 * WgLayout<8>::BUF, s>>>(g, a, cl->nx, cl->ny, cl->nz,
+                k_wgrad_tc<8><<<wg_grid, kWgThreads, 2 * WgLayout<8>::BUF, s>>>(g, a, cl->nx, cl->ny, cl->nz,
                                                                                 kCout[l], cl->wpart, cl->step_err);
             else
-                k_wgrad_tc<32><<<wg_grid, kTcThreads, 2 * WgLayout<32>::BUF, s>>>(g, a, cl->nx, cl->ny, cl->nz,
+                k_wgrad_tc<32><<<wg_grid, kWgThreads, 2 * WgLayout<32>::BUF, s>>>(g, a, cl->nx, cl->ny, cl->nz,
                                                                                   kCout[l], cl->wpart, cl->step_err);
-            k_part_sum<<<(count + 255) / 256, 256, 0, s>>>(cl->wpart, (int)wg_grid, count, gW);
+            k_part_sum<<<(count + 31) / 32, 256, 0, s>>>(cl->wpart, (int)wg_grid, count, gW);
         } else if (kCS[l] == 8) {
             k_wgrad<8><<<dim3(wgx, 27), kConvThreads, 0, s>>>(g, a, cl->nx, cl->ny, cl->nz, kCout[l], kCin[l], gW);
         } else {
@@ -1267,11 +1358,7 @@ vlbm_status vlbm_closure_create(const vlbm_closure_params *p, vlbm_closure **out
         return st != VLBM_OK ? st : fail(nullptr, VLBM_ERR_OOM, "closure allocation failed");
     }
     if (ok) {
-        int dev = 0, sms = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cl->tc_grid = 2 * std::max(sms, 1);
-        const int shm32 = 54 * 1024 + 4 * kTcPlane, shm8 = 14 * 1024 + kTcPlane;
+        const int shm32 = tc_smem_bytes<32>(), shm8 = tc_smem_bytes<8>();
         st = cl_check(cudaFuncSetAttribute(k_conv_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm32),
                       "closure tcgen05 shared memory");
         if (st == VLBM_OK)
