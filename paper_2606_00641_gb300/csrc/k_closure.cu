@@ -311,17 +311,60 @@ __global__ void __launch_bounds__(kTx * kTy * 2) k_conv_smem(const bf16 *__restr
 // weights once, then one tile after another; one thread issues the MMAs,
 // tcgen05.commit arrives on an mbarrier (bounded wait), and each warp reads
 // its 32 TMEM lanes (= its 32 cells) with tcgen05.ld.
-constexpr int kTcX = 8, kTcY = 16, kTcZ = 2;  // kTcZ z-slices per tile = kTcZ M-blocks of 128 cells
+constexpr int kTcX = 8, kTcY = 16, kTcZ = 4;  // tile: kTcZ z-slices of 128 cells (one M block each)
 constexpr int kTcHx = kTcX + 2, kTcHy = kTcY + 2, kTcHz = kTcZ + 2, kTcHalo = kTcHx * kTcHy * kTcHz;
-constexpr int kTcPlane = kTcHalo * 16;  // bytes per channel-block plane
-constexpr int kTcThreads = 288;         // warps 0-7 stage and drain, warp 8 issues the MMAs
-constexpr int kTcCols = 2 * 32 * kTcZ;  // TMEM columns: two tiles' accumulators, 32 columns per z-slice
+constexpr int kTcPlane = kTcHalo * 16;    // bytes per channel-block plane
+constexpr int kTcThreads = 480;           // warps 0-7 drain, 8-13 stage, 14 issues the MMAs
+constexpr int kTcStage = 192;             // staging threads
+constexpr int kTcBufs = 2;                // halo buffers
+constexpr int kTcN = 96;                  // MMA N: 3 z-taps x 32 output channels
+constexpr int kTcSetCols = 32 * (kTcZ + 4);  // one accumulator set: slices -2 .. kTcZ + 1
+constexpr int kTcCols = 2 * kTcSetCols;   // two sets = all 512 TMEM columns
 constexpr uint32_t kTcWaitLimit = 1u << 24;
+
+// weight chunks of K = 16: (2-D tap, half of the 32 channels), or pairs of
+// 2-D taps of the 8 channels; each chunk is 96 rows (dz, output channel) x 16
+constexpr int tc_nchunk(int cs) { return cs == 8 ? 5 : 18; }
 
 template <int CS>
 constexpr int tc_smem_bytes()
 {
-    return (CS == 8 ? 14 : 54) * 1024 + 2 * (CS / 8) * kTcPlane;
+    return tc_nchunk(CS) * kTcN * 32 + kTcBufs * (CS / 8) * kTcPlane;
+}
+
+// Bounded wait for the given phase of an mbarrier.  Each try_wait may park
+// the warp for up to kTcSuspendNs (it resumes as soon as the phase completes),
+// so waiting warps take no issue slots from the working ones.  Gives up after
+// kTcWaitIters tries (about 1.3 s), or early once another role of the CTA has
+// given up (*abort set); returns false then, and a give-up sets *abort itself.
+constexpr uint32_t kTcSuspendNs = 20000;
+constexpr uint32_t kTcWaitIters = 1u << 16;
+
+__device__ __forceinline__ bool tc_wait(uint32_t mb, uint32_t phase, volatile int *abort)
+{
+    for (uint32_t it = 0; it < kTcWaitIters; ++it) {
+        uint32_t done;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}\n"
+                     : "=r"(done)
+                     : "r"(mb), "r"(phase), "r"(kTcSuspendNs)
+                     : "memory");
+        if (done) return true;
+        if (*abort) return false;
+    }
+    *abort = 1;
+    return false;
+}
+
+__device__ __forceinline__ void tc_arrive(uint32_t mb)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(mb) : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint32_t mb)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mb)
+                 : "memory");
 }
 
 __device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
@@ -340,41 +383,52 @@ __device__ __forceinline__ void tc_mma(uint32_t dacc, uint64_t da, uint64_t db, 
                  ::"r"(dacc), "l"(da), "l"(db), "r"(idesc), "r"(acc));
 }
 
-// byte offset, inside a plane, of the first row of tap t for z-slice zz
-__device__ __forceinline__ int tc_tap_ofs(int t, int zz)
-{
-    const int dx = t % 3, dy = (t / 3) % 3, dz = t / 9;  // 0..2 = offset + 1
-    return (((dz + zz) * kTcHy + dy) * kTcHx + dx) * 16;
-}
-
-// 3x3x3 convolution on the tcgen05 tensor cores.  Tile = 8 (x) x 16 (y) x 2 (z)
-// cells; each z-slice is one M = 128 block, N = 32 output channels, K = the
-// 27 taps x CS input channels in chunks of 16.  A operand: the tile's halo,
-// staged as 16-byte channel-block planes, so that a tap is an address offset
-// (K-major, no swizzle); B operand: the weights, resident in shared memory for
-// the whole kernel.  Persistent CTAs with two halo buffers and two TMEM
-// accumulator sets: while the tensor cores work on tile i, the CTA stages
-// tile i+1 with cp.async and drains tile i-1 from TMEM (tanh derivative or
-// bias, tanh, scale; BF16 or FP32 store).  Warp 8 only issues the MMAs.
+// 3x3x3 convolution on the tcgen05 tensor cores.
+// Tile = 8 (x) x 16 (y) x kTcZ (z) cells; each z-slice is one M = 128 block.
+// The three z-taps are stacked along N: halo plane h (2-D tap (dx, dy),
+// K-chunk j) times [W(dz=0) | W(dz=1) | W(dz=2)] (N = 96) contributes to the
+// output slices h, h-1 and h-2 at once.  Slice s accumulates in the TMEM
+// columns 32 (kTcZ + 1 - s) of a set, so the three 32-column blocks that one
+// MMA writes are exactly those slices; the blocks of s = -2, -1, kTcZ,
+// kTcZ + 1 collect products that belong to no slice of the tile and are
+// never read.  One M128 x N96 x K16 MMA costs about as much as an N32 one,
+// so this takes 3 (kTcZ + 2) / (3 kTcZ) of the instructions per cell of
+// one-tap-per-MMA.  Every MMA accumulates: the drain clears the blocks it
+// reads (and all of them at start).
+// A operand: the halo, staged as 16-byte channel-block planes, so that a 2-D
+// tap is an address offset (K-major, no swizzle).  B operand: the weights,
+// resident in shared memory.  One persistent CTA per SM, three roles handing
+// work over through mbarriers:
+//   warps 8-13  stage halos into two buffers with cp.async          (full[b])
+//   warp 14     issues the MMAs of a tile into one of two TMEM sets  (empty[b], tfull[s])
+//   warps 0-7   drain a finished set: warp w reads TMEM lanes 32 (w % 4)
+//               of slices w / 4 and w / 4 + 2 (tanh derivative or bias,
+//               tanh, scale; BF16 or FP32 store), then clears them    (tempty[s])
 template <int CS>
-__global__ void __launch_bounds__(kTcThreads) k_conv_tc(const bf16 *__restrict__ act, int nx, int ny, int nz,
-                                                        const bf16 *__restrict__ wtc, int cout_real,
-                                                        const ConvEpilogue e, unsigned *err)
+__global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(const bf16 *__restrict__ act, int nx, int ny, int nz,
+                                                           const bf16 *__restrict__ wtc, int cout_real,
+                                                           const ConvEpilogue e, unsigned *err)
 {
-    constexpr int NCHUNK = CS == 8 ? 14 : 54;
+    constexpr int NCHUNK = tc_nchunk(CS);
     constexpr int NPLANE = CS / 8;
-    constexpr int WBYTES = NCHUNK * 1024;  // 4 n-groups x 2 k-halves x 128 bytes per chunk
+    constexpr int WBYTES = NCHUNK * kTcN * 32;
     constexpr int HBYTES = NPLANE * kTcPlane;
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ __align__(8) uint64_t mbar;
+    __shared__ __align__(8) uint64_t bar[2 * kTcBufs + 4];  // full[2], empty[2], tfull[2], tempty[2]
     __shared__ uint32_t tmem_base;
     __shared__ float s_bias[32], s_scale[32];
-    constexpr int kStageThreads = 256;
+    __shared__ int s_abort;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int tiles_x = nx / kTcX, tiles_y = ny / kTcY, tiles_z = nz / kTcZ;
     const int ntiles = tiles_x * tiles_y * tiles_z;
     const int plane = nx * ny;
     const int n_my = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const uint32_t bar_s = (uint32_t)__cvta_generic_to_shared(bar);
+    auto full = [&](int b) { return bar_s + 8u * (uint32_t)b; };
+    auto empty = [&](int b) { return bar_s + 8u * (uint32_t)(kTcBufs + b); };
+    auto tfull = [&](int s2) { return bar_s + 8u * (uint32_t)(2 * kTcBufs + s2); };
+    auto tempty = [&](int s2) { return bar_s + 8u * (uint32_t)(2 * kTcBufs + 2 + s2); };
+    auto slice_col = [](int zz) { return (uint32_t)(32 * (kTcZ + 1 - zz)); };
 
     for (int i = tid; i < WBYTES / 16; i += kTcThreads)
         reinterpret_cast<uint4 *>(smem)[i] = __ldg(reinterpret_cast<const uint4 *>(wtc) + i);
@@ -387,9 +441,16 @@ __global__ void __launch_bounds__(kTcThreads) k_conv_tc(const bf16 *__restrict__
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(dst), "r"(kTcCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
     }
-    const uint32_t mb = (uint32_t)__cvta_generic_to_shared(&mbar);
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb));
+        s_abort = 0;
+        for (int b = 0; b < kTcBufs; ++b) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(full(b)), "r"(kTcStage));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(empty(b)));
+        }
+        for (int s2 = 0; s2 < 2; ++s2) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(tfull(s2)));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 8;\n" ::"r"(tempty(s2)));
+        }
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
@@ -399,7 +460,31 @@ __global__ void __launch_bounds__(kTcThreads) k_conv_tc(const bf16 *__restrict__
     const uint32_t tmem = tmem_base;
     const uint32_t sw_s = (uint32_t)__cvta_generic_to_shared(smem);
     const uint32_t sh_s = sw_s + WBYTES;
-    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+    volatile int *abort = &s_abort;
+    uint32_t zero[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) zero[c] = 0u;
+    auto tmem_clear = [&](uint32_t taddr) {
+        asm volatile("tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+                     "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};\n"
+                     ::"r"(taddr), "r"(zero[0]), "r"(zero[1]), "r"(zero[2]), "r"(zero[3]), "r"(zero[4]),
+                       "r"(zero[5]), "r"(zero[6]), "r"(zero[7]), "r"(zero[8]), "r"(zero[9]), "r"(zero[10]),
+                       "r"(zero[11]), "r"(zero[12]), "r"(zero[13]), "r"(zero[14]), "r"(zero[15]), "r"(zero[16]),
+                       "r"(zero[17]), "r"(zero[18]), "r"(zero[19]), "r"(zero[20]), "r"(zero[21]), "r"(zero[22]),
+                       "r"(zero[23]), "r"(zero[24]), "r"(zero[25]), "r"(zero[26]), "r"(zero[27]), "r"(zero[28]),
+                       "r"(zero[29]), "r"(zero[30]), "r"(zero[31])
+                     : "memory");
+    };
+    if (warp < 8) {  // clear the blocks this warp drains, in both sets
+        const uint32_t lanes = (uint32_t)((warp & 3) * 32) << 16;
+        for (int s2 = 0; s2 < 2; ++s2)
+            for (int p = 0; p < 2; ++p)
+                tmem_clear(tmem + lanes + (uint32_t)(s2 * kTcSetCols) + slice_col((warp >> 2) + 2 * p));
+        asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
 
     auto origin = [&](int i, int &x0, int &y0, int &z0) {
         const int tile = (int)blockIdx.x + i * (int)gridDim.x;
@@ -407,144 +492,173 @@ __global__ void __launch_bounds__(kTcThreads) k_conv_tc(const bf16 *__restrict__
         y0 = ((tile / tiles_x) % tiles_y) * kTcY;
         z0 = (tile / (tiles_x * tiles_y)) * kTcZ;
     };
-    // halo of tile i into buffer b, as channel-block planes; every 16-byte piece in flight at once
-    auto stage = [&](int i, int b) {
-        int x0, y0, z0;
-        origin(i, x0, y0, z0);
-        const uint32_t hb = sh_s + (uint32_t)(b * HBYTES);
-        for (int idx = tid; idx < kTcHalo * NPLANE; idx += kStageThreads) {
-            const int cb = idx % NPLANE, c = idx / NPLANE;
-            const int bx = c % kTcHx, by = (c / kTcHx) % kTcHy, bz = c / (kTcHx * kTcHy);
-            int gx = x0 - 1 + bx, gy = y0 - 1 + by, gz = z0 - 1 + bz;
-            gx += gx < 0 ? nx : (gx >= nx ? -nx : 0);
-            gy += gy < 0 ? ny : (gy >= ny ? -ny : 0);
-            gz += gz < 0 ? nz : (gz >= nz ? -nz : 0);
-            const size_t cell = (size_t)gx + (size_t)nx * gy + (size_t)plane * gz;
-            const uint32_t dst = hb + (uint32_t)(cb * kTcPlane + c * 16);
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(act + cell * CS + cb * 8)
-                         : "memory");
-        }
-        asm volatile("cp.async.commit_group;\n" ::: "memory");
-    };
-    // all MMAs of the tile in buffer b into accumulator set b (one thread)
-    auto issue = [&](int b) {
-        const uint32_t hb = sh_s + (uint32_t)(b * HBYTES);
-        const uint64_t db0 = tc_desc(sw_s, 128, 256);
-        for (int zz = 0; zz < kTcZ; ++zz) {
-            const uint32_t dacc = tmem + (uint32_t)(b * 32 * kTcZ + zz * 32);
-            if (CS == 32) {  // chunk 2t + h: tap t, channel blocks 2h and 2h + 1
-                const uint64_t da0 = tc_desc(hb, kTcPlane, kTcHx * 16);
-                int j = 0;
-                for (int dz = 0; dz < 3; ++dz)
-                    for (int dy = 0; dy < 3; ++dy)
-                        for (int dx = 0; dx < 3; ++dx) {
-                            const uint32_t ofs = (uint32_t)((((dz + zz) * kTcHy + dy) * kTcHx + dx) * 16);
-#pragma unroll
-                            for (int h = 0; h < 2; ++h, ++j)
-                                tc_mma(dacc, da0 + ((ofs + (uint32_t)(h * 2 * kTcPlane)) >> 4),
-                                       db0 + (uint64_t)(j * 64), idesc, j > 0);
-                        }
-            } else {         // chunk j: taps 2j and 2j + 1 of the single plane
-                for (int j = 0; j < NCHUNK; ++j) {
-                    const int t0 = 2 * j, t1 = 2 * j + 1;
-                    const uint32_t lbo = t1 < 27 ? (uint32_t)(tc_tap_ofs(t1, zz) - tc_tap_ofs(t0, zz)) : 0u;
-                    tc_mma(dacc, tc_desc(hb + (uint32_t)tc_tap_ofs(t0, zz), lbo, kTcHx * 16),
-                           db0 + (uint64_t)(j * 64), idesc, j > 0);  // padding tap: zero weights
-                }
-            }
-        }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mb));
-    };
-    // drain tile i from accumulator set b: warp w reads TMEM lanes 32 (w % 4) .. (rows), z-slice w / 4
-    auto drain = [&](int i, int b) {
-        int x0, y0, z0;
-        origin(i, x0, y0, z0);
-        const int q = warp & 3, zz = warp >> 2;
-        const int m = q * 32 + lane;  // tile row = x + 8 y
-        uint32_t r[32];
-        const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * 32 * kTcZ + zz * 32);
-        asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
-                     "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
-                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-                       "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-                       "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
-                       "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
-                       "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-                     : "r"(taddr));
-        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-        const size_t cell = (size_t)(x0 + (m & 7)) + (size_t)nx * (y0 + (m >> 3)) + (size_t)plane * (z0 + zz);
-        float v[32];
-        if (e.deriv) {
-            const uint4 *dp = reinterpret_cast<const uint4 *>(e.deriv + cell * 32);
-#pragma unroll
-            for (int qd = 0; qd < 4; ++qd) {
-                const uint4 dv = __ldg(dp + qd);
-                const bf16 *dh = reinterpret_cast<const bf16 *>(&dv);
-#pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                    const float d = __bfloat162float(dh[c]);
-                    v[qd * 8 + c] = __uint_as_float(r[qd * 8 + c]) * (1.f - d * d);
-                }
-            }
-        } else {
-#pragma unroll
-            for (int c = 0; c < 32; ++c) v[c] = __uint_as_float(r[c]);
-        }
-        if (e.tanh_act) {
-#pragma unroll
-            for (int c = 0; c < 32; ++c) v[c] = tanh_fast(v[c] + s_bias[c]) * s_scale[c];
-        } else {
-#pragma unroll
-            for (int c = 0; c < 32; ++c) v[c] = (v[c] + s_bias[c]) * s_scale[c];
-        }
-        if (e.out_bf) {
-            __align__(16) bf16 o[32];
-#pragma unroll
-            for (int c = 0; c < 32; ++c) o[c] = __float2bfloat16_rn(c < cout_real ? v[c] : 0.f);
-            uint4 *dst = reinterpret_cast<uint4 *>(e.out_bf + cell * e.os);
-#pragma unroll
-            for (int qd = 0; qd < 4; ++qd) dst[qd] = reinterpret_cast<const uint4 *>(o)[qd];
-        } else {
-            float *dst = e.out_f + cell * e.os;
-#pragma unroll
-            for (int c = 0; c < 32; c += 4)
-                if (c < cout_real) *reinterpret_cast<float4 *>(dst + c) = make_float4(v[c], v[c + 1], v[c + 2], v[c + 3]);
-        }
-    };
 
-    bool ok = true;
-    if (n_my > 0 && warp < 8) stage(0, 0);
-    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-    __syncthreads();
-    for (int i = 0; i < n_my && ok; ++i) {
-        const int b = i & 1;
-        if (warp == 8) {
-            if (lane == 0) {
-                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-                issue(b);
+    if (warp >= 8 && warp < 14) {
+        // ---- staging: halo of tile i into buffer i % kTcBufs, every 16-byte piece in flight at once.
+        // A thread owns one (channel block, halo x) column and walks the halo rows (y, z) of it.
+        constexpr int NCOL = kTcHx * NPLANE;
+        constexpr int NGRP = kTcStage / NCOL < 16 ? kTcStage / NCOL : 16;  // row stride (< kTcHy)
+        const int ptid = tid - 256;
+        const bool active = ptid < NCOL * NGRP;
+        const int cb = ptid % NPLANE, bx = (ptid % NCOL) / NPLANE, grp = ptid / NCOL;
+        bool ok = true;
+        for (int i = 0; i < n_my && ok; ++i) {
+            const int b = i % kTcBufs;
+            if (i >= kTcBufs && !tc_wait(empty(b), (uint32_t)((i / kTcBufs - 1) & 1), abort)) ok = false;
+            if (ok && active) {
+                int x0, y0, z0;
+                origin(i, x0, y0, z0);
+                int gx = x0 - 1 + bx;
+                gx += gx < 0 ? nx : (gx >= nx ? -nx : 0);
+                const bf16 *col = act + (size_t)gx * CS + cb * 8;
+                const uint32_t dst = sh_s + (uint32_t)(b * HBYTES + cb * kTcPlane + bx * 16);
+                int by = grp, bz = 0;
+                for (int r = grp; r < kTcHy * kTcHz; r += NGRP) {
+                    int gy = y0 - 1 + by, gz = z0 - 1 + bz;
+                    gy += gy < 0 ? ny : (gy >= ny ? -ny : 0);
+                    gz += gz < 0 ? nz : (gz >= nz ? -nz : 0);
+                    const size_t row = (size_t)nx * gy + (size_t)plane * gz;
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst + (uint32_t)(r * kTcHx * 16)),
+                                 "l"(col + row * CS)
+                                 : "memory");
+                    by += NGRP;
+                    if (by >= kTcHy) {
+                        by -= kTcHy;
+                        ++bz;
+                    }
+                }
             }
-        } else {
-            if (i + 1 < n_my) stage(i + 1, b ^ 1);
-            if (i > 0) drain(i - 1, b ^ 1);
+            // hand the buffer over as soon as this tile's copies have landed
+            asm volatile("cp.async.commit_group;\n" ::: "memory");
+            asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            if (ok) tc_arrive(full(b));
         }
-        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        uint32_t done = 0;
-        for (uint32_t it = 0; it < kTcWaitLimit && !done; ++it)
-            asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-                         "selp.u32 %0, 1, 0, p;\n\t}\n"
-                         : "=r"(done)
-                         : "r"(mb), "r"((uint32_t)b));
-        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-        // one outcome for the whole CTA, so that no thread leaves the loop alone
-        if (!__syncthreads_and((int)done)) {
-            if (tid == 0) atomicOr(err, kFlagTimeout);
-            ok = false;
+        if (!ok && ptid == 0) atomicOr(err, kFlagTimeout);
+    } else if (warp == 14) {
+        // ---- MMA issue (one thread)
+        if (lane == 0) {
+            const uint32_t idesc =
+                (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTcN >> 3) << 17) | ((128u >> 4) << 24);
+            const uint64_t db0 = tc_desc(sw_s, 128, 256);
+            bool ok = true;
+            for (int i = 0; i < n_my && ok; ++i) {
+                const int b = i % kTcBufs, sa = i & 1;
+                if (!tc_wait(full(b), (uint32_t)((i / kTcBufs) & 1), abort)) ok = false;
+                if (ok && i >= 2 && !tc_wait(tempty(sa), (uint32_t)(((i >> 1) - 1) & 1), abort)) ok = false;
+                if (!ok) break;
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                const uint32_t hb = sh_s + (uint32_t)(b * HBYTES);
+                for (int h = 0; h < kTcHz; ++h) {
+                    const uint32_t dacc = tmem + (uint32_t)(sa * kTcSetCols) + slice_col(h);
+                    const uint32_t pofs = (uint32_t)(h * kTcHy * kTcHx * 16);
+                    if (CS == 32) {  // chunk 2 t2 + kc: 2-D tap t2, channel blocks 2 kc and 2 kc + 1
+                        const uint64_t da0 = tc_desc(hb + pofs, kTcPlane, kTcHx * 16);
+                        int j = 0;
+                        for (int dy = 0; dy < 3; ++dy)
+                            for (int dx = 0; dx < 3; ++dx) {
+                                const uint32_t ofs = (uint32_t)((dy * kTcHx + dx) * 16);
+#pragma unroll
+                                for (int kc = 0; kc < 2; ++kc, ++j)
+                                    tc_mma(dacc, da0 + ((ofs + (uint32_t)(kc * 2 * kTcPlane)) >> 4),
+                                           db0 + (uint64_t)(j * (kTcN * 32 / 16)), idesc, 1u);
+                            }
+                    } else {         // chunk j: 2-D taps 2j and 2j + 1 of the single plane
+                        for (int j = 0; j < NCHUNK; ++j) {
+                            const int t0 = 2 * j, t1 = 2 * j + 1;
+                            const int o0 = ((t0 / 3) * kTcHx + t0 % 3) * 16;
+                            const uint32_t lbo = t1 < 9 ? (uint32_t)(((t1 / 3) * kTcHx + t1 % 3) * 16 - o0) : 0u;
+                            tc_mma(dacc, tc_desc(hb + pofs + (uint32_t)o0, lbo, kTcHx * 16),
+                                   db0 + (uint64_t)(j * (kTcN * 32 / 16)), idesc, 1u);  // tap 9: zero weights
+                        }
+                    }
+                }
+                tc_commit(empty(b));
+                tc_commit(tfull(sa));
+            }
+            if (!ok) atomicOr(err, kFlagTimeout);
         }
-        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    } else if (warp < 8) {
+        // ---- drain
+        const int q = warp & 3;
+        const int m = q * 32 + lane;  // tile row = x + 8 y
+        bool ok = true;
+        for (int i = 0; i < n_my && ok; ++i) {
+            const int sa = i & 1;
+            // tcgen05.ld is warp-collective: the whole warp takes one outcome
+            if (!__all_sync(0xffffffffu, tc_wait(tfull(sa), (uint32_t)((i >> 1) & 1), abort))) {
+                ok = false;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            int x0, y0, z0;
+            origin(i, x0, y0, z0);
+#pragma unroll 1
+            for (int p = 0; p < 2; ++p) {
+                const int zz = (warp >> 2) + 2 * p;
+                uint32_t r[32];
+                const uint32_t taddr =
+                    tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(sa * kTcSetCols) + slice_col(zz);
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+                             "%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+                             : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                               "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+                               "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+                               "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+                               "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+                               "=r"(r[31])
+                             : "r"(taddr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+                tmem_clear(taddr);
+                const size_t cell =
+                    (size_t)(x0 + (m & 7)) + (size_t)nx * (y0 + (m >> 3)) + (size_t)plane * (z0 + zz);
+                float v[32];
+                if (e.deriv) {
+                    const uint4 *dp = reinterpret_cast<const uint4 *>(e.deriv + cell * 32);
+#pragma unroll
+                    for (int qd = 0; qd < 4; ++qd) {
+                        const uint4 dv = __ldg(dp + qd);
+                        const bf16 *dh = reinterpret_cast<const bf16 *>(&dv);
+#pragma unroll
+                        for (int c = 0; c < 8; ++c) {
+                            const float d = __bfloat162float(dh[c]);
+                            v[qd * 8 + c] = __uint_as_float(r[qd * 8 + c]) * (1.f - d * d);
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 32; ++c) v[c] = __uint_as_float(r[c]);
+                }
+                if (e.tanh_act) {
+#pragma unroll
+                    for (int c = 0; c < 32; ++c) v[c] = tanh_fast(v[c] + s_bias[c]) * s_scale[c];
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 32; ++c) v[c] = (v[c] + s_bias[c]) * s_scale[c];
+                }
+                if (e.out_bf) {
+                    __align__(16) bf16 o[32];
+#pragma unroll
+                    for (int c = 0; c < 32; ++c) o[c] = __float2bfloat16_rn(c < cout_real ? v[c] : 0.f);
+                    uint4 *dst = reinterpret_cast<uint4 *>(e.out_bf + cell * e.os);
+#pragma unroll
+                    for (int qd = 0; qd < 4; ++qd) dst[qd] = reinterpret_cast<const uint4 *>(o)[qd];
+                } else {
+                    float *dst = e.out_f + cell * e.os;
+#pragma unroll
+                    for (int c = 0; c < 32; c += 4)
+                        if (c < cout_real)
+                            *reinterpret_cast<float4 *>(dst + c) = make_float4(v[c], v[c + 1], v[c + 2], v[c + 3]);
+                }
+            }
+            // both blocks read and cleared: hand the set back to the MMA warp
+            asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+            __syncwarp();
+            if (lane == 0) tc_arrive(tempty(sa));
+        }
+        if (!ok && lane == 0) atomicOr(err, kFlagTimeout);
     }
-    if (ok && n_my > 0 && warp < 8) drain(n_my - 1, (n_my - 1) & 1);
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
     if (warp == 0) {
@@ -553,32 +667,37 @@ __global__ void __launch_bounds__(kTcThreads) k_conv_tc(const bf16 *__restrict__
     }
 }
 
-// Weights in the canonical K-major layout of k_conv_tc: chunk j, output
-// channel n (< 32; zero beyond cout), K-index k (< 16) at
-// j*512 + (n/8)*128 + (k/8)*64 + (n%8)*8 + k%8 (bf16 elements).
+// Weights in the canonical K-major layout of k_conv_tc: chunk j, row
+// n = 32 dz + o (o < 32; zero beyond the output channels), K-index k (< 16)
+// at j*1536 + (n/8)*128 + (k/8)*64 + (n%8)*8 + k%8 (bf16 elements).  Chunk j
+// holds 2-D tap j/2 and channels 16 (j%2) + k (32 input channels), or 2-D tap
+// 2j + k/8 and channel k%8 (8 input channels; 2-D tap 9 is zero).  The
+// transposed pack (data gradient) swaps the channel roles and mirrors the tap.
 __global__ void k_pack_tc(const float *__restrict__ W, int cout, int cin, int CS, int transpose,
                           bf16 *__restrict__ out)
 {
-    const int nchunk = CS == 8 ? 14 : 54;
+    const int nchunk = tc_nchunk(CS);
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= nchunk * 512) return;
-    const int j = idx / 512, rem = idx % 512;
-    const int g = rem / 128, kc = (rem / 64) % 2, r = (rem / 8) % 8, e8 = rem % 8;
-    const int n = g * 8 + r, k = kc * 8 + e8;
-    int t, c;
+    if (idx >= nchunk * kTcN * 16) return;
+    const int j = idx / (kTcN * 16), rem = idx % (kTcN * 16);
+    const int g = rem / 128, kh = (rem / 64) % 2, r = (rem / 8) % 8, e8 = rem % 8;
+    const int n = g * 8 + r, k = kh * 8 + e8;
+    const int dz = n / 32, o = n % 32;
+    int t2, c;
     if (CS == 32) {
-        t = j >> 1;
+        t2 = j >> 1;
         c = (j & 1) * 16 + k;
     } else {
-        t = 2 * j + (k >= 8 ? 1 : 0);
+        t2 = 2 * j + (k >= 8 ? 1 : 0);
         c = k & 7;
     }
     float w = 0.f;
-    if (t < 27) {
+    if (t2 < 9) {
+        const int t = 9 * dz + t2;
         if (!transpose) {
-            if (n < cout && c < cin) w = W[((size_t)n * cin + c) * 27 + t];
+            if (o < cout && c < cin) w = W[((size_t)o * cin + c) * 27 + t];
         } else {
-            if (n < cin && c < cout) w = W[((size_t)c * cin + n) * 27 + (26 - t)];
+            if (o < cin && c < cout) w = W[((size_t)c * cin + o) * 27 + (26 - t)];
         }
     }
     out[idx] = __float2bfloat16_rn(w);
@@ -1127,11 +1246,11 @@ void *cl_alloc(vlbm_closure *cl, size_t bytes)
 vlbm_status pack_all(vlbm_closure *cl, cudaStream_t s)
 {
     for (int l = 0; l < 3; ++l) {
-        const int ntc = nchunk(kCS[l]) * 512;
+        const int ntc = tc_nchunk(kCS[l]) * kTcN * 16;
         k_pack_tc<<<(ntc + 255) / 256, 256, 0, s>>>(cl->theta + cl->off_W[l], kCout[l], kCin[l], kCS[l], 0,
                                                      cl->wtc_fwd[l]);
         if (l > 0) {
-            const int nt = nchunk(32) * 512;
+            const int nt = tc_nchunk(32) * kTcN * 16;
             k_pack_tc<<<(nt + 255) / 256, 256, 0, s>>>(cl->theta + cl->off_W[l], kCout[l], kCin[l], 32, 1,
                                                         cl->wtc_bwd[l]);
         }
@@ -1147,26 +1266,25 @@ vlbm_status pack_all(vlbm_closure *cl, cudaStream_t s)
     return cl_check(cudaGetLastError(), "closure weight packing");
 }
 
-bool tc_grid_ok(const vlbm_closure *cl)
-{
-    return cl->nx % kTcX == 0 && cl->ny % kTcY == 0 && cl->nz % kTcZ == 0;
-}
+// grids the tcgen05 kernels tile exactly
+bool conv_tc_ok(const vlbm_closure *cl) { return cl->nx % kTcX == 0 && cl->ny % kTcY == 0 && cl->nz % kTcZ == 0; }
+bool wgrad_tc_ok(const vlbm_closure *cl) { return cl->nx % 8 == 0 && cl->ny % 16 == 0 && cl->nz % kWgZ == 0; }
 
 vlbm_status conv(vlbm_closure *cl, int layer, const bf16 *in, bool transpose, const ConvEpilogue &e, cudaStream_t s)
 {
-    if (tc_grid_ok(cl)) {
-        // tcgen05 / TMEM tiles of 8 x 16 cells
-        // persistent CTAs: one per SM for 32 input channels (the two halo buffers and
-        // the weights fill most of the shared memory), two per SM for 8
+    if (conv_tc_ok(cl)) {
+        // tcgen05 / TMEM tiles of 8 x 16 x 4 cells
+        // persistent CTAs, one per SM (13 warps of up to 152 registers)
         const int ntiles = (cl->nx / kTcX) * (cl->ny / kTcY) * (cl->nz / kTcZ);
+        const unsigned grid = (unsigned)std::min(ntiles, cl->sms);
         const int cout_real = transpose ? kCin[layer] : kCout[layer];
         const bf16 *w = transpose ? cl->wtc_bwd[layer] : cl->wtc_fwd[layer];
         if (!transpose && layer == 0)
-            k_conv_tc<8><<<(unsigned)std::min(ntiles, 2 * cl->sms), kTcThreads, tc_smem_bytes<8>(), s>>>(
-                in, cl->nx, cl->ny, cl->nz, w, cout_real, e, cl->step_err);
+            k_conv_tc<8><<<grid, kTcThreads, tc_smem_bytes<8>(), s>>>(in, cl->nx, cl->ny, cl->nz, w, cout_real, e,
+                                                                     cl->step_err);
         else
-            k_conv_tc<32><<<(unsigned)std::min(ntiles, cl->sms), kTcThreads, tc_smem_bytes<32>(), s>>>(
-                in, cl->nx, cl->ny, cl->nz, w, cout_real, e, cl->step_err);
+            k_conv_tc<32><<<grid, kTcThreads, tc_smem_bytes<32>(), s>>>(in, cl->nx, cl->ny, cl->nz, w, cout_real, e,
+                                                                       cl->step_err);
         return cl_check(cudaGetLastError(), "closure tcgen05 convolution launch");
     }
     if (cl->nx % kTx == 0 && cl->ny % kTy == 0) {
@@ -1236,7 +1354,7 @@ vlbm_status backward(vlbm_closure *cl, cudaStream_t s)
 {
     vlbm_status st = cl_check(cudaMemsetAsync(cl->grad, 0, cl->nparam * sizeof(float), s), "closure grad clear");
     const unsigned wgx = (unsigned)((cl->N + kWgradCells - 1) / kWgradCells);
-    const bool tc = tc_grid_ok(cl);
+    const bool tc = wgrad_tc_ok(cl);
     const int ntiles = (cl->nx / 8) * (cl->ny / 16) * (cl->nz / kWgZ);
     const unsigned wg_grid = (unsigned)std::min(ntiles, cl->sms), b_grid = (unsigned)(2 * cl->sms);
     auto wgrad = [&](int l, const bf16 *g, const bf16 *a) {
@@ -1329,8 +1447,8 @@ vlbm_status vlbm_closure_create(const vlbm_closure_params *p, vlbm_closure **out
     for (int l = 0; l < 3; ++l) {
         cl->frag_fwd[l] = (uint2 *)A((size_t)nchunk(kCS[l]) * kNT[l] * 32 * sizeof(uint2));
         cl->frag_bwd[l] = (uint2 *)A((size_t)nchunk(32) * 4 * 32 * sizeof(uint2));
-        cl->wtc_fwd[l] = (bf16 *)A((size_t)nchunk(kCS[l]) * 512 * sizeof(bf16));
-        cl->wtc_bwd[l] = (bf16 *)A((size_t)nchunk(32) * 512 * sizeof(bf16));
+        cl->wtc_fwd[l] = (bf16 *)A((size_t)tc_nchunk(kCS[l]) * kTcN * 16 * sizeof(bf16));
+        cl->wtc_bwd[l] = (bf16 *)A((size_t)tc_nchunk(32) * kTcN * 16 * sizeof(bf16));
     }
     cl->errflag = (unsigned *)A(64);
     cl->step_err = cl->errflag;

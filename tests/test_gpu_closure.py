@@ -63,11 +63,12 @@ def setup_closure(V, shape, seed, last_scale=1.0):
     return cl, f0, Qd, pw, mu, sigma, out_scale
 
 
-# grids per convolution kernel: tcgen05/TMEM (nx % 8, ny % 16, nz % 2), shared-memory
-# mma.sync (nx % 16, ny % 8), global-load mma.sync (anything with nx % 16).
-# (10, 48, 96) has 180 tiles of 8 x 16 x 2 cells: more than one tile per
-# persistent weight-gradient CTA, so the staging pipeline runs.
-CONV_SHAPES = [(4, 16, 16), (2, 32, 48), (6, 8, 32), (4, 6, 16), (10, 48, 96)]
+# grids per convolution kernel: tcgen05/TMEM (nx % 8, ny % 16, nz % 4; weight
+# gradient nz % 2), shared-memory mma.sync (nx % 16, ny % 8), global-load
+# mma.sync (anything with nx % 16).  (12, 80, 96) has 180 convolution tiles
+# of 8 x 16 x 4 cells and 360 weight-gradient tiles of 8 x 16 x 2: more than
+# one tile per persistent CTA, so the staging pipelines run.
+CONV_SHAPES = [(4, 16, 16), (2, 32, 48), (6, 8, 32), (4, 6, 16), (12, 80, 96)]
 
 
 @pytest.mark.parametrize("shape", CONV_SHAPES)
