@@ -19,6 +19,10 @@
 #include <cmath>
 #include <cstring>
 
+#include <cuda.h>
+
+#include <mutex>
+
 #include "vlbm_internal.cuh"
 
 namespace vlbm {
@@ -84,13 +88,23 @@ __device__ __forceinline__ Nbr nbr_cell(int cell, int nx, int ny, int nz)
 // implicit-GEMM convolution (forward and backward-data)
 // ---------------------------------------------------------------------------
 
+// Activations and their gradients are stored channel-blocked: channel c of
+// cell p of an N-cell field at ((c / 8) N + p) 8 + c % 8, i.e. planes of
+// 16-byte cell records, one plane per block of 8 channels (a field with 8
+// channels is simply [cell][8]).  A halo row of a plane is contiguous, which
+// lets TMA load the convolution halos in long rows.
+__host__ __device__ __forceinline__ size_t blk(size_t cell, int c, size_t N)
+{
+    return ((size_t)(c >> 3) * N + cell) * 8 + (c & 7);
+}
+
 struct ConvEpilogue {
     const float *bias;     // per output channel, or null
     int tanh_act;          // apply tanh
-    const bf16 *deriv;     // multiply by (1 - d^2), d = deriv[cell*32 + col], or null
+    const bf16 *deriv;     // multiply by (1 - d^2), d = channel col of the cell (channel-blocked), or null
     const float *scale;    // per output channel, or null
-    bf16 *out_bf;          // BF16 output with stride os, or null
-    float *out_f;          // FP32 output with stride os, or null
+    bf16 *out_bf;          // BF16 output, channel-blocked, or null
+    float *out_f;          // FP32 output [cell][os], or null
     int os;
 };
 
@@ -124,13 +138,14 @@ __global__ void __launch_bounds__(kConvThreads) k_conv(const bf16 *__restrict__ 
     for (int j = 0; j < NCHUNK; ++j) {
         uint32_t a0, a1, a2, a3;
         if (CS == 32) {
+            // channels 16 h + 2 tg (+1) and 16 h + 8 + 2 tg (+1): planes 2 h and 2 h + 1
             const int t = j >> 1, h = j & 1;
-            const uint32_t *pA = act32 + (size_t)tap_nbr(nA, cA, t) * 16 + h * 8;
-            const uint32_t *pB = act32 + (size_t)tap_nbr(nB, cB, t) * 16 + h * 8;
-            a0 = pA[tg];
-            a2 = pA[4 + tg];
-            a1 = pB[tg];
-            a3 = pB[4 + tg];
+            const size_t qA = tap_nbr(nA, cA, t), qB = tap_nbr(nB, cB, t);
+            const uint32_t *p0 = act32 + (size_t)(2 * h) * N * 4, *p1 = p0 + (size_t)N * 4;
+            a0 = p0[qA * 4 + tg];
+            a2 = p1[qA * 4 + tg];
+            a1 = p0[qB * 4 + tg];
+            a3 = p1[qB * 4 + tg];
         } else {
             const int t0 = 2 * j, t1 = 2 * j + 1;
             a0 = act32[(size_t)tap_nbr(nA, cA, t0) * 4 + tg];
@@ -165,8 +180,8 @@ __global__ void __launch_bounds__(kConvThreads) k_conv(const bf16 *__restrict__ 
                 v1 = tanh_fast(v1);
             }
             if (e.deriv) {
-                const float d0 = __bfloat162float(e.deriv[(size_t)cell * 32 + col]);
-                const float d1 = __bfloat162float(e.deriv[(size_t)cell * 32 + col + 1]);
+                const float d0 = __bfloat162float(e.deriv[blk(cell, col, N)]);
+                const float d1 = __bfloat162float(e.deriv[blk(cell, col, N) + 1]);
                 v0 *= 1.f - d0 * d0;
                 v1 *= 1.f - d1 * d1;
             }
@@ -178,7 +193,7 @@ __global__ void __launch_bounds__(kConvThreads) k_conv(const bf16 *__restrict__ 
                 __nv_bfloat162 o;
                 o.x = __float2bfloat16_rn(v0);
                 o.y = __float2bfloat16_rn(v1);
-                *reinterpret_cast<__nv_bfloat162 *>(e.out_bf + (size_t)cell * e.os + col) = o;
+                *reinterpret_cast<__nv_bfloat162 *>(e.out_bf + blk(cell, col, N)) = o;
             } else {
                 *reinterpret_cast<float2 *>(e.out_f + (size_t)cell * e.os + col) = make_float2(v0, v1);
             }
@@ -211,6 +226,7 @@ __global__ void __launch_bounds__(kTx * kTy * 2) k_conv_smem(const bf16 *__restr
     __shared__ __align__(16) bf16 tile[kHalo * ROW];
     const int x0 = blockIdx.x * kTx, y0 = blockIdx.y * kTy, z = blockIdx.z;
     const int plane = nx * ny;
+    const size_t N = (size_t)plane * nz;
     // stage the halo box: (bx, by, bz) -> cell (x0-1+bx, y0-1+by, z-1+bz), periodic
     for (int idx = threadIdx.x; idx < kHalo * VEC; idx += blockDim.x) {
         const int piece = idx % VEC, c = idx / VEC;
@@ -220,7 +236,7 @@ __global__ void __launch_bounds__(kTx * kTy * 2) k_conv_smem(const bf16 *__restr
         gy += gy < 0 ? ny : (gy >= ny ? -ny : 0);
         gz += gz < 0 ? nz : (gz >= nz ? -nz : 0);
         const size_t cell = (size_t)gx + (size_t)nx * gy + (size_t)plane * gz;
-        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(act + cell * CS) + piece);
+        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(act + blk(cell, piece * 8, N)));
         *reinterpret_cast<uint4 *>(tile + c * ROW + piece * 8) = v;
     }
     __syncthreads();
@@ -274,8 +290,8 @@ __global__ void __launch_bounds__(kTx * kTy * 2) k_conv_smem(const bf16 *__restr
                 v1 = tanh_fast(v1);
             }
             if (e.deriv) {
-                const float d0 = __bfloat162float(e.deriv[(size_t)cell * 32 + col]);
-                const float d1 = __bfloat162float(e.deriv[(size_t)cell * 32 + col + 1]);
+                const float d0 = __bfloat162float(e.deriv[blk(cell, col, N)]);
+                const float d1 = __bfloat162float(e.deriv[blk(cell, col, N) + 1]);
                 v0 *= 1.f - d0 * d0;
                 v1 *= 1.f - d1 * d1;
             }
@@ -287,7 +303,7 @@ __global__ void __launch_bounds__(kTx * kTy * 2) k_conv_smem(const bf16 *__restr
                 __nv_bfloat162 o;
                 o.x = __float2bfloat16_rn(v0);
                 o.y = __float2bfloat16_rn(v1);
-                *reinterpret_cast<__nv_bfloat162 *>(e.out_bf + (size_t)cell * e.os + col) = o;
+                *reinterpret_cast<__nv_bfloat162 *>(e.out_bf + blk(cell, col, N)) = o;
             } else {
                 *reinterpret_cast<float2 *>(e.out_f + (size_t)cell * e.os + col) = make_float2(v0, v1);
             }
@@ -314,8 +330,8 @@ __global__ void __launch_bounds__(kTx * kTy * 2) k_conv_smem(const bf16 *__restr
 constexpr int kTcX = 8, kTcY = 16, kTcZ = 4;  // tile: kTcZ z-slices of 128 cells (one M block each)
 constexpr int kTcHx = kTcX + 2, kTcHy = kTcY + 2, kTcHz = kTcZ + 2, kTcHalo = kTcHx * kTcHy * kTcHz;
 constexpr int kTcPlane = kTcHalo * 16;    // bytes per channel-block plane
-constexpr int kTcThreads = 480;           // warps 0-7 drain, 8-13 stage, 14 issues the MMAs
-constexpr int kTcStage = 192;             // staging threads
+constexpr int kTcThreads = 480;           // warps 0-7 drain, 8-12 patch, 13 loads (TMA), 14 issues the MMAs
+constexpr int kTcStage = 160;             // patching threads (warps 8-12)
 constexpr int kTcBufs = 2;                // halo buffers
 constexpr int kTcN = 96;                  // MMA N: 3 z-taps x 32 output channels
 constexpr int kTcSetCols = 32 * (kTcZ + 4);  // one accumulator set: slices -2 .. kTcZ + 1
@@ -399,7 +415,8 @@ __device__ __forceinline__ void tc_mma(uint32_t dacc, uint64_t da, uint64_t db, 
 // tap is an address offset (K-major, no swizzle).  B operand: the weights,
 // resident in shared memory.  One persistent CTA per SM, three roles handing
 // work over through mbarriers:
-//   warps 8-13  stage halos into two buffers with cp.async          (full[b])
+//   warp 13     loads the halo boxes into two buffers with TMA      (tma[b])
+//   warps 8-12  patch the periodic images on the boundary (cp.async) (full[b])
 //   warp 14     issues the MMAs of a tile into one of two TMEM sets  (empty[b], tfull[s])
 //   warps 0-7   drain a finished set: warp w reads TMEM lanes 32 (w % 4)
 //               of slices w / 4 and w / 4 + 2 (tanh derivative or bias,
@@ -407,14 +424,15 @@ __device__ __forceinline__ void tc_mma(uint32_t dacc, uint64_t da, uint64_t db, 
 template <int CS>
 __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(const bf16 *__restrict__ act, int nx, int ny, int nz,
                                                            const bf16 *__restrict__ wtc, int cout_real,
-                                                           const ConvEpilogue e, unsigned *err)
+                                                           const ConvEpilogue e, unsigned *err,
+                                                           const __grid_constant__ CUtensorMap halo_map)
 {
     constexpr int NCHUNK = tc_nchunk(CS);
     constexpr int NPLANE = CS / 8;
     constexpr int WBYTES = NCHUNK * kTcN * 32;
     constexpr int HBYTES = NPLANE * kTcPlane;
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ __align__(8) uint64_t bar[2 * kTcBufs + 4];  // full[2], empty[2], tfull[2], tempty[2]
+    __shared__ __align__(8) uint64_t bar[3 * kTcBufs + 4];  // full[2], empty[2], tfull[2], tempty[2], tma[2]
     __shared__ uint32_t tmem_base;
     __shared__ float s_bias[32], s_scale[32];
     __shared__ int s_abort;
@@ -422,12 +440,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(const bf16 *__restric
     const int tiles_x = nx / kTcX, tiles_y = ny / kTcY, tiles_z = nz / kTcZ;
     const int ntiles = tiles_x * tiles_y * tiles_z;
     const int plane = nx * ny;
+    const size_t N = (size_t)plane * nz;
     const int n_my = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     const uint32_t bar_s = (uint32_t)__cvta_generic_to_shared(bar);
     auto full = [&](int b) { return bar_s + 8u * (uint32_t)b; };
     auto empty = [&](int b) { return bar_s + 8u * (uint32_t)(kTcBufs + b); };
     auto tfull = [&](int s2) { return bar_s + 8u * (uint32_t)(2 * kTcBufs + s2); };
     auto tempty = [&](int s2) { return bar_s + 8u * (uint32_t)(2 * kTcBufs + 2 + s2); };
+    auto tma_bar = [&](int b) { return bar_s + 8u * (uint32_t)(2 * kTcBufs + 4 + b); };
     auto slice_col = [](int zz) { return (uint32_t)(32 * (kTcZ + 1 - zz)); };
 
     for (int i = tid; i < WBYTES / 16; i += kTcThreads)
@@ -446,6 +466,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(const bf16 *__restric
         for (int b = 0; b < kTcBufs; ++b) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(full(b)), "r"(kTcStage));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(empty(b)));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(tma_bar(b)));
         }
         for (int s2 = 0; s2 < 2; ++s2) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(tfull(s2)));
@@ -493,46 +514,67 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(const bf16 *__restric
         z0 = (tile / (tiles_x * tiles_y)) * kTcZ;
     };
 
-    if (warp >= 8 && warp < 14) {
-        // ---- staging: halo of tile i into buffer i % kTcBufs, every 16-byte piece in flight at once.
-        // A thread owns one (channel block, halo x) column and walks the halo rows (y, z) of it.
-        constexpr int NCOL = kTcHx * NPLANE;
-        constexpr int NGRP = kTcStage / NCOL < 16 ? kTcStage / NCOL : 16;  // row stride (< kTcHy)
+    if (warp == 13) {
+        // ---- halo loads: one thread issues, a tile ahead of the MMAs as far as the buffers allow,
+        // one bulk tensor copy per channel-block plane (box of 18 x 6 rows of 10 cells x 16 bytes,
+        // contiguous in the channel-blocked field); coordinates outside the grid read as zeros
+        if (lane == 0) {
+            const uint64_t map_addr = reinterpret_cast<uint64_t>(&halo_map);
+            bool ok = true;
+            for (int i = 0; i < n_my && ok; ++i) {
+                const int b = i % kTcBufs;
+                if (i >= kTcBufs && !tc_wait(empty(b), (uint32_t)((i / kTcBufs - 1) & 1), abort)) {
+                    ok = false;
+                    break;
+                }
+                int x0, y0, z0;
+                origin(i, x0, y0, z0);
+                const uint32_t hb = sh_s + (uint32_t)(b * HBYTES);
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(tma_bar(b)),
+                             "r"((uint32_t)HBYTES)
+                             : "memory");
+                for (int cb = 0; cb < NPLANE; ++cb)
+                    asm volatile("cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                                 " [%0], [%1, {%2, %3, %4, %5}], [%6];\n" ::"r"(hb + (uint32_t)(cb * kTcPlane)),
+                                 "l"(map_addr), "r"(8 * (x0 - 1)), "r"(y0 - 1), "r"(z0 - 1), "r"(cb), "r"(tma_bar(b))
+                                 : "memory");
+            }
+            if (!ok) atomicOr(err, kFlagTimeout);
+        }
+    } else if (warp >= 8 && warp < 13) {
+        // ---- patching: once a tile's box has landed, tiles on the boundary get the periodic
+        // images of the out-of-grid halo cells with cp.async; then every patching thread
+        // hands the buffer to the MMA warp (full[b])
         const int ptid = tid - 256;
-        const bool active = ptid < NCOL * NGRP;
-        const int cb = ptid % NPLANE, bx = (ptid % NCOL) / NPLANE, grp = ptid / NCOL;
         bool ok = true;
         for (int i = 0; i < n_my && ok; ++i) {
             const int b = i % kTcBufs;
-            if (i >= kTcBufs && !tc_wait(empty(b), (uint32_t)((i / kTcBufs - 1) & 1), abort)) ok = false;
-            if (ok && active) {
-                int x0, y0, z0;
-                origin(i, x0, y0, z0);
-                int gx = x0 - 1 + bx;
-                gx += gx < 0 ? nx : (gx >= nx ? -nx : 0);
-                const bf16 *col = act + (size_t)gx * CS + cb * 8;
-                const uint32_t dst = sh_s + (uint32_t)(b * HBYTES + cb * kTcPlane + bx * 16);
-                int by = grp, bz = 0;
-                for (int r = grp; r < kTcHy * kTcHz; r += NGRP) {
-                    int gy = y0 - 1 + by, gz = z0 - 1 + bz;
+            if (!tc_wait(tma_bar(b), (uint32_t)((i / kTcBufs) & 1), abort)) {
+                ok = false;
+                break;
+            }
+            int x0, y0, z0;
+            origin(i, x0, y0, z0);
+            if (x0 == 0 || x0 + kTcX == nx || y0 == 0 || y0 + kTcY == ny || z0 == 0 || z0 + kTcZ == nz) {
+                const uint32_t hb = sh_s + (uint32_t)(b * HBYTES);
+                for (int idx = ptid; idx < kTcHalo * NPLANE; idx += kTcStage) {
+                    const int cb = idx % NPLANE, c = idx / NPLANE;
+                    const int bx = c % kTcHx, by = (c / kTcHx) % kTcHy, bz = c / (kTcHx * kTcHy);
+                    int gx = x0 - 1 + bx, gy = y0 - 1 + by, gz = z0 - 1 + bz;
+                    if (gx >= 0 && gx < nx && gy >= 0 && gy < ny && gz >= 0 && gz < nz) continue;
+                    gx += gx < 0 ? nx : (gx >= nx ? -nx : 0);
                     gy += gy < 0 ? ny : (gy >= ny ? -ny : 0);
                     gz += gz < 0 ? nz : (gz >= nz ? -nz : 0);
-                    const size_t row = (size_t)nx * gy + (size_t)plane * gz;
-                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst + (uint32_t)(r * kTcHx * 16)),
-                                 "l"(col + row * CS)
+                    const size_t cell = (size_t)gx + (size_t)nx * gy + (size_t)plane * gz;
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(hb + (uint32_t)(cb * kTcPlane + c * 16)),
+                                 "l"(act + ((size_t)cb * N + cell) * 8)
                                  : "memory");
-                    by += NGRP;
-                    if (by >= kTcHy) {
-                        by -= kTcHy;
-                        ++bz;
-                    }
                 }
+                asm volatile("cp.async.commit_group;\n" ::: "memory");
+                asm volatile("cp.async.wait_group 0;\n" ::: "memory");
             }
-            // hand the buffer over as soon as this tile's copies have landed
-            asm volatile("cp.async.commit_group;\n" ::: "memory");
-            asm volatile("cp.async.wait_group 0;\n" ::: "memory");
             asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-            if (ok) tc_arrive(full(b));
+            tc_arrive(full(b));
         }
         if (!ok && ptid == 0) atomicOr(err, kFlagTimeout);
     } else if (warp == 14) {
@@ -614,10 +656,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(const bf16 *__restric
                     (size_t)(x0 + (m & 7)) + (size_t)nx * (y0 + (m >> 3)) + (size_t)plane * (z0 + zz);
                 float v[32];
                 if (e.deriv) {
-                    const uint4 *dp = reinterpret_cast<const uint4 *>(e.deriv + cell * 32);
 #pragma unroll
                     for (int qd = 0; qd < 4; ++qd) {
-                        const uint4 dv = __ldg(dp + qd);
+                        const uint4 dv = __ldg(reinterpret_cast<const uint4 *>(e.deriv + ((size_t)qd * N + cell) * 8));
                         const bf16 *dh = reinterpret_cast<const bf16 *>(&dv);
 #pragma unroll
                         for (int c = 0; c < 8; ++c) {
@@ -640,9 +681,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(const bf16 *__restric
                     __align__(16) bf16 o[32];
 #pragma unroll
                     for (int c = 0; c < 32; ++c) o[c] = __float2bfloat16_rn(c < cout_real ? v[c] : 0.f);
-                    uint4 *dst = reinterpret_cast<uint4 *>(e.out_bf + cell * e.os);
 #pragma unroll
-                    for (int qd = 0; qd < 4; ++qd) dst[qd] = reinterpret_cast<const uint4 *>(o)[qd];
+                    for (int qd = 0; qd < 4; ++qd)
+                        *reinterpret_cast<uint4 *>(e.out_bf + ((size_t)qd * N + cell) * 8) =
+                            reinterpret_cast<const uint4 *>(o)[qd];
                 } else {
                     float *dst = e.out_f + cell * e.os;
 #pragma unroll
@@ -784,9 +826,9 @@ __global__ void __launch_bounds__(kConvThreads) k_wgrad(const bf16 *__restrict__
             nbs[q] = tap_nbr(nbr_cell(cc, nx, ny, nz), cc, t);
         }
         auto gzv = [&](int q, int o) -> uint32_t {
-            return ok[q] ? (uint32_t)gz16[(size_t)cells[q] * 32 + o] : 0u;
+            return ok[q] ? (uint32_t)gz16[blk(cells[q], o, N)] : 0u;
         };
-        auto av = [&](int q, int c) -> uint32_t { return ok[q] ? (uint32_t)a16[(size_t)nbs[q] * CSIN + c] : 0u; };
+        auto av = [&](int q, int c) -> uint32_t { return ok[q] ? (uint32_t)a16[blk(nbs[q], c, N)] : 0u; };
 #pragma unroll
         for (int mt = 0; mt < 2; ++mt) {
             const int olo = mt * 16 + g, ohi = olo + 8;
@@ -834,7 +876,7 @@ __global__ void __launch_bounds__(256) k_bgrad_part(const bf16 *__restrict__ gz,
     const int cb = threadIdx.x & 3;
     float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     for (int c = blockIdx.x * 64 + (threadIdx.x >> 2); c < N; c += gridDim.x * 64) {
-        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(gz + (size_t)c * 32) + cb);
+        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(gz + ((size_t)cb * N + c) * 8));
         const bf16 *h = reinterpret_cast<const bf16 *>(&v);
 #pragma unroll
         for (int e = 0; e < 8; ++e) s[e] += __bfloat162float(h[e]);
@@ -919,6 +961,7 @@ __global__ void __launch_bounds__(kWgThreads) k_wgrad_tc(const bf16 *__restrict_
     const int tiles_x = nx / 8, tiles_y = ny / 16, tiles_z = nz / kWgZ;
     const int ntiles = tiles_x * tiles_y * tiles_z;
     const int plane = nx * ny;
+    const size_t Ncell = (size_t)plane * nz;
     const uint32_t s_base = (uint32_t)__cvta_generic_to_shared(smem);
 
     // slots that are never staged feed only discarded rows: clear them once
@@ -967,7 +1010,7 @@ __global__ void __launch_bounds__(kWgThreads) k_wgrad_tc(const bf16 *__restrict_
             gzz += gzz < 0 ? nz : (gzz >= nz ? -nz : 0);
             const size_t cell = (size_t)gx + (size_t)nx * gy + (size_t)plane * gzz;
             const uint32_t dst = abase + (uint32_t)((((h * 4 + slot) * 18 + by) * L::PW + bx) * 16);
-            const bf16 *src = act + cell * CIN + (CIN == 32 ? slot * 8 : 0);
+            const bf16 *src = act + ((size_t)(CIN == 32 ? slot : 0) * Ncell + cell) * 8;
             asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
         }
         for (int idx = tid; idx < 4 * kWgZ * 128; idx += kWgStage) {
@@ -975,7 +1018,7 @@ __global__ void __launch_bounds__(kWgThreads) k_wgrad_tc(const bf16 *__restrict_
             const size_t cell = (size_t)(x0 + (c & 7)) + (size_t)nx * (y0 + ((c >> 3) & 15)) +
                                 (size_t)plane * (z0 + (c >> 7));
             const uint32_t dst = gbase + (uint32_t)((cbo * kWgZ * 128 + c) * 16);
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(gz + cell * 32 + cbo * 8)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(gz + ((size_t)cbo * Ncell + cell) * 8)
                          : "memory");
         }
         asm volatile("cp.async.commit_group;\n" ::: "memory");
@@ -1129,18 +1172,31 @@ __global__ void k_grad_out(const float *__restrict__ gq, int nx, int ny, int nz,
                                                (gq[(size_t)k * N + plus[a]] - gq[(size_t)k * N + minus[a]]));
 #pragma unroll
     for (int j = kOut; j < 32; ++j) v[j] = __float2bfloat16_rn(0.f);
-    uint4 *dst = reinterpret_cast<uint4 *>(gy + (size_t)c * 32);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) dst[q] = reinterpret_cast<const uint4 *>(v)[q];
+    for (int q = 0; q < 4; ++q)
+        *reinterpret_cast<uint4 *>(gy + ((size_t)q * N + c) * 8) = reinterpret_cast<const uint4 *>(v)[q];
 }
 
-// dL/dy given as [N][24] floats -> BF16 [N][32] with zero padding
+// dL/dy given as [N][24] floats -> BF16, 32 channels (zero padded), channel-blocked
 __global__ void k_gy_from_f32(const float *__restrict__ src, int N, bf16 *__restrict__ gy)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N * 32) return;
-    const int c = i / 32, j = i % 32;
-    gy[i] = __float2bfloat16_rn(j < kOut ? src[(size_t)c * kOut + j] : 0.f);
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    __align__(16) bf16 v[32];
+    const float4 *s4 = reinterpret_cast<const float4 *>(src + (size_t)c * kOut);
+#pragma unroll
+    for (int q = 0; q < kOut / 4; ++q) {
+        const float4 f = __ldg(s4 + q);
+        v[4 * q] = __float2bfloat16_rn(f.x);
+        v[4 * q + 1] = __float2bfloat16_rn(f.y);
+        v[4 * q + 2] = __float2bfloat16_rn(f.z);
+        v[4 * q + 3] = __float2bfloat16_rn(f.w);
+    }
+#pragma unroll
+    for (int j = kOut; j < 32; ++j) v[j] = __float2bfloat16_rn(0.f);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        *reinterpret_cast<uint4 *>(gy + ((size_t)q * N + c) * 8) = reinterpret_cast<const uint4 *>(v)[q];
 }
 
 struct AdamArgs {
@@ -1198,6 +1254,8 @@ struct vlbm_closure {
     unsigned *step_err = nullptr;            // where the running kernels report (errflag or a ctx flag)
     int sms = 1;                             // streaming multiprocessors of the device
     float *wpart = nullptr, *bpart = nullptr;  // per-CTA partial weight and bias gradients
+    bool tc_maps = false;                    // halo tensor maps below are encoded
+    CUtensorMap map_x{}, map_a1{}, map_a2{}, map_gy{}, map_gz{};  // TMA halo boxes of the conv inputs
     vlbm::bf16 *x = nullptr, *a1 = nullptr, *a2 = nullptr, *gy = nullptr, *gz = nullptr;
     float *dphi = nullptr, *gq = nullptr, *col_scale = nullptr;
     double *q = nullptr, *q1 = nullptr, *loss = nullptr;
@@ -1266,6 +1324,47 @@ vlbm_status pack_all(vlbm_closure *cl, cudaStream_t s)
     return cl_check(cudaGetLastError(), "closure weight packing");
 }
 
+// cuTensorMapEncodeTiled from the driver (no link against libcuda)
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled_fn()
+{
+    static std::once_flag once;
+    static EncodeTiledFn fn = nullptr;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+// Halo box of k_conv_tc over a channel-blocked BF16 field with cs channels:
+// dimensions (8 nx, ny, nz, cs/8 planes) with the 8 channels of a cell
+// innermost, box (8 * 10, 18, kTcZ + 2, 1), so that one copy fills one
+// channel-block plane with rows of 160 contiguous bytes.
+vlbm_status encode_halo_map(CUtensorMap *m, const bf16 *base, int cs, int nx, int ny, int nz)
+{
+    EncodeTiledFn fn = encode_tiled_fn();
+    if (!fn) return fail(nullptr, VLBM_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    const cuuint64_t dims[4] = {(cuuint64_t)8 * nx, (cuuint64_t)ny, (cuuint64_t)nz, (cuuint64_t)(cs / 8)};
+    const cuuint64_t strides[3] = {(cuuint64_t)nx * 16, (cuuint64_t)nx * ny * 16, (cuuint64_t)nx * ny * nz * 16};
+    const cuuint32_t box[4] = {8 * kTcHx, kTcHy, kTcHz, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16 *>(base), dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(nullptr, VLBM_ERR_CUDA, "halo tensor map encoding failed");
+    return VLBM_OK;
+}
+
 // grids the tcgen05 kernels tile exactly
 bool conv_tc_ok(const vlbm_closure *cl) { return cl->nx % kTcX == 0 && cl->ny % kTcY == 0 && cl->nz % kTcZ == 0; }
 bool wgrad_tc_ok(const vlbm_closure *cl) { return cl->nx % 8 == 0 && cl->ny % 16 == 0 && cl->nz % kWgZ == 0; }
@@ -1279,12 +1378,19 @@ vlbm_status conv(vlbm_closure *cl, int layer, const bf16 *in, bool transpose, co
         const unsigned grid = (unsigned)std::min(ntiles, cl->sms);
         const int cout_real = transpose ? kCin[layer] : kCout[layer];
         const bf16 *w = transpose ? cl->wtc_bwd[layer] : cl->wtc_fwd[layer];
+        const CUtensorMap *map = in == cl->x ? &cl->map_x
+                                 : in == cl->a1 ? &cl->map_a1
+                                 : in == cl->a2 ? &cl->map_a2
+                                 : in == cl->gy ? &cl->map_gy
+                                 : in == cl->gz ? &cl->map_gz
+                                                : nullptr;
+        if (!map || !cl->tc_maps) return fail(nullptr, VLBM_ERR_STATE, "closure convolution input has no halo map");
         if (!transpose && layer == 0)
             k_conv_tc<8><<<grid, kTcThreads, tc_smem_bytes<8>(), s>>>(in, cl->nx, cl->ny, cl->nz, w, cout_real, e,
-                                                                     cl->step_err);
+                                                                     cl->step_err, *map);
         else
             k_conv_tc<32><<<grid, kTcThreads, tc_smem_bytes<32>(), s>>>(in, cl->nx, cl->ny, cl->nz, w, cout_real, e,
-                                                                       cl->step_err);
+                                                                       cl->step_err, *map);
         return cl_check(cudaGetLastError(), "closure tcgen05 convolution launch");
     }
     if (cl->nx % kTx == 0 && cl->ny % kTy == 0) {
@@ -1490,6 +1596,14 @@ vlbm_status vlbm_closure_create(const vlbm_closure_params *p, vlbm_closure **out
             st = cl_check(cudaFuncSetAttribute(k_wgrad_tc<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                2 * WgLayout<8>::BUF),
                           "closure tcgen05 shared memory");
+        if (st == VLBM_OK && conv_tc_ok(cl)) {
+            st = encode_halo_map(&cl->map_x, cl->x, 8, cl->nx, cl->ny, cl->nz);
+            if (st == VLBM_OK) st = encode_halo_map(&cl->map_a1, cl->a1, 32, cl->nx, cl->ny, cl->nz);
+            if (st == VLBM_OK) st = encode_halo_map(&cl->map_a2, cl->a2, 32, cl->nx, cl->ny, cl->nz);
+            if (st == VLBM_OK) st = encode_halo_map(&cl->map_gy, cl->gy, 32, cl->nx, cl->ny, cl->nz);
+            if (st == VLBM_OK) st = encode_halo_map(&cl->map_gz, cl->gz, 32, cl->nx, cl->ny, cl->nz);
+            cl->tc_maps = st == VLBM_OK;
+        }
         if (st == VLBM_OK) st = cl_check(cudaMemsetAsync(cl->errflag, 0, 64, cl->stream), "closure flag clear");
         ok = st == VLBM_OK;
     }
@@ -1556,7 +1670,7 @@ vlbm_status vlbm_closure_backward(vlbm_closure *cl, const double *Q_dev, const f
     if (!cl || !Q_dev || !gy_dev || !grads_host) return VLBM_ERR_ARG;
     vlbm_status st = forward(cl, Q_dev, cl->dphi, cl->stream);
     if (st == VLBM_OK) {
-        k_gy_from_f32<<<(cl->N * 32 + 255) / 256, 256, 0, cl->stream>>>(gy_dev, cl->N, cl->gy);
+        k_gy_from_f32<<<(cl->N + 255) / 256, 256, 0, cl->stream>>>(gy_dev, cl->N, cl->gy);
         st = cl_check(cudaGetLastError(), "closure gradient input");
     }
     if (st == VLBM_OK) st = backward(cl, cl->stream);
