@@ -931,8 +931,10 @@ __global__ void __launch_bounds__(256) k_part_sum(const float *__restrict__ part
 // Tiles of 8 x 16 x kWgZ cells; persistent CTAs (one per SM: the two staging
 // buffers take more than half of the shared memory) accumulate all their
 // tiles in TMEM while the next tile is staged with cp.async (warps 0-7; warp
-// 8 issues the MMAs), then write one partial gradient per CTA (summed in
-// fixed order by k_part_sum).
+// 8 issues the MMAs).  While the MMAs run, warps 0-7 also sum the staged
+// output gradients per channel: the bias gradient.  Each CTA writes one
+// partial [cout][CIN][27] weight gradient followed by its [cout] bias
+// gradient (the parameter order), summed in fixed order by k_part_sum.
 constexpr int kWgZ = 2;
 constexpr int kWgThreads = 288;  // warps 0-7 stage, warp 8 issues the MMAs, warps 0-2 drain
 constexpr int kWgStage = 256;
@@ -1030,6 +1032,7 @@ __global__ void __launch_bounds__(kWgThreads) k_wgrad_tc(const bf16 *__restrict_
     uint32_t phase = 0;
     bool ok = true, first = true;
     int b = 0;
+    float bsum = 0.f;  // bias gradient: channel lane, cells warp, warp + 8, ... of each tile
     if ((int)blockIdx.x < ntiles && warp < 8) stage(blockIdx.x, 0);
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
@@ -1057,6 +1060,12 @@ __global__ void __launch_bounds__(kWgThreads) k_wgrad_tc(const bf16 *__restrict_
         // stage the next tile into the other buffer while the tensor cores work
         const int next = tile + (int)gridDim.x;
         if (next < ntiles && warp < 8) stage(next, b ^ 1);
+        if (warp < 8) {  // this tile's output gradients (channel lane) from the staged planes
+            const unsigned char *g = smem + b * L::BUF + L::ABYTES + (lane >> 3) * (kWgZ * 128 * 16) + (lane & 7) * 2;
+#pragma unroll 8
+            for (int c = warp; c < kWgZ * 128; c += 8)
+                bsum += __bfloat162float(*reinterpret_cast<const bf16 *>(g + c * 16));
+        }
         asm volatile("cp.async.wait_group 0;\n" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         uint32_t done = 0;
@@ -1075,8 +1084,20 @@ __global__ void __launch_bounds__(kWgThreads) k_wgrad_tc(const bf16 *__restrict_
         b ^= 1;
     }
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const size_t pstride = (size_t)cout * CIN * 27 + cout;
+    {
+        __shared__ float bred[8][32];
+        if (warp < 8) bred[warp][lane] = bsum;
+        __syncthreads();
+        if (tid < cout) {
+            float t = 0.f;
+#pragma unroll
+            for (int w = 0; w < 8; ++w) t += bred[w][tid];
+            part[(size_t)blockIdx.x * pstride + (size_t)cout * CIN * 27 + tid] = t;
+        }
+    }
     if (ok && warp < 3) {  // warp h reads TMEM lanes of z-offset h = dz; warp 3 holds discarded rows
-        float *dst = part + (size_t)blockIdx.x * cout * CIN * 27;
+        float *dst = part + (size_t)blockIdx.x * pstride;
         for (int j = 0; j < L::NACC; ++j) {
             uint32_t r[32];
             const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(32 * j);
@@ -1465,22 +1486,23 @@ vlbm_status backward(vlbm_closure *cl, cudaStream_t s)
     const unsigned wg_grid = (unsigned)std::min(ntiles, cl->sms), b_grid = (unsigned)(2 * cl->sms);
     auto wgrad = [&](int l, const bf16 *g, const bf16 *a) {
         float *gW = cl->grad + cl->off_W[l];
-        if (tc) {  // tensor cores; per-CTA partials summed in a fixed order
-            const int count = kCout[l] * kCin[l] * 27;
+        if (tc) {  // tensor cores; per-CTA partials (weights, then bias) summed in a fixed order
+            const int count = kCout[l] * kCin[l] * 27 + kCout[l];
             if (kCS[l] == 8)
                 k_wgrad_tc<8><<<wg_grid, kWgThreads, 2 * WgLayout<8>::BUF, s>>>(g, a, cl->nx, cl->ny, cl->nz,
                                                                                 kCout[l], cl->wpart, cl->step_err);
             else
                 k_wgrad_tc<32><<<wg_grid, kWgThreads, 2 * WgLayout<32>::BUF, s>>>(g, a, cl->nx, cl->ny, cl->nz,
                                                                                   kCout[l], cl->wpart, cl->step_err);
-            k_part_sum<<<(count + 31) / 32, 256, 0, s>>>(cl->wpart, (int)wg_grid, count, gW);
-        } else if (kCS[l] == 8) {
-            k_wgrad<8><<<dim3(wgx, 27), kConvThreads, 0, s>>>(g, a, cl->nx, cl->ny, cl->nz, kCout[l], kCin[l], gW);
+            k_part_sum<<<(count + 31) / 32, 256, 0, s>>>(cl->wpart, (int)wg_grid, count, gW);  // b follows W
         } else {
-            k_wgrad<32><<<dim3(wgx, 27), kConvThreads, 0, s>>>(g, a, cl->nx, cl->ny, cl->nz, kCout[l], kCin[l], gW);
+            if (kCS[l] == 8)
+                k_wgrad<8><<<dim3(wgx, 27), kConvThreads, 0, s>>>(g, a, cl->nx, cl->ny, cl->nz, kCout[l], kCin[l], gW);
+            else
+                k_wgrad<32><<<dim3(wgx, 27), kConvThreads, 0, s>>>(g, a, cl->nx, cl->ny, cl->nz, kCout[l], kCin[l], gW);
+            k_bgrad_part<<<b_grid, 256, 0, s>>>(g, cl->N, kCout[l], cl->bpart);
+            k_part_sum<<<1, 256, 0, s>>>(cl->bpart, (int)b_grid, kCout[l], cl->grad + cl->off_b[l]);
         }
-        k_bgrad_part<<<b_grid, 256, 0, s>>>(g, cl->N, kCout[l], cl->bpart);
-        k_part_sum<<<1, 256, 0, s>>>(cl->bpart, (int)b_grid, kCout[l], cl->grad + cl->off_b[l]);
         return cl_check(cudaGetLastError(), "closure weight gradient launch");
     };
     // layer 3: gy -> W3, b3; data gradient through tanh of layer 2 -> gz
@@ -1575,7 +1597,7 @@ vlbm_status vlbm_closure_create(const vlbm_closure_params *p, vlbm_closure **out
         cudaDeviceGetAttribute(&cl->sms, cudaDevAttrMultiProcessorCount, dev);
         cl->sms = std::max(cl->sms, 1);
     }
-    cl->wpart = (float *)A((size_t)cl->sms * 32 * 32 * 27 * 4);
+    cl->wpart = (float *)A((size_t)cl->sms * (32 * 32 * 27 + 32) * 4);
     cl->bpart = (float *)A((size_t)2 * cl->sms * 32 * 4);
     if (!ok) {
         vlbm_closure_destroy(cl);
