@@ -169,7 +169,9 @@ template <int D, class S> struct ReadArgs {
     int64_t stride;
     int parity;
     double ref[kMaxLat], scale[kMaxLat];
+    float ref_f[kMaxLat], scale_f[kMaxLat];  // FP32 copies for the FP32 compute path
 };
+
 
 template <int D, class S>
 __device__ __forceinline__ double logical(const ReadArgs<D, S> &a, int64_t cell, const int64_t *nb, int k,
@@ -184,9 +186,36 @@ __device__ __forceinline__ double logical(const ReadArgs<D, S> &a, int64_t cell,
     return v;
 }
 
+// Q_k of one cell in the compute precision: the sum of its populations (Eq. 3);
+// for deviation storage r_k + s_k sum_i g_ki, since the weights sum to one.
+template <int D, class S>
+__device__ __forceinline__ typename ComputeOf<S>::T cell_moment(const ReadArgs<D, S> &a, int64_t cell,
+                                                                const int64_t *nb, int k)
+{
+    using R = typename ComputeOf<S>::T;
+    constexpr int Q = AxisSet<D>::Q;
+    const S *pop = static_cast<const S *>(a.pop);
+    R s = R(0);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int j = a.parity ? opp_axis(i) : i;
+        const int64_t at = a.parity ? nb[opp_axis(i)] : cell;
+        s += (R)Codec<S>::load(pop + (int64_t)(k * Q + j) * a.stride + at);
+    }
+    if (Codec<S>::kDev) s = s * (R)a.scale_f[k] + (R)a.ref_f[k];
+    return s;
+}
+
 template <int D>
 __device__ __forceinline__ void cell_xyz(int64_t cell, int nx, int ny, int &x, int &y, int &z)
 {
+    if (cell <= 0xFFFFFFFFll) {  // 32-bit division where the index fits
+        const uint32_t c = (uint32_t)cell, r = c / (uint32_t)nx;
+        x = (int)(c - r * (uint32_t)nx);
+        y = (int)(r % (uint32_t)ny);
+        z = (int)(r / (uint32_t)ny);
+        return;
+    }
     x = (int)(cell % nx);
     const int64_t r = cell / nx;
     y = (int)(r % ny);
@@ -206,12 +235,7 @@ __global__ void k_ideal_moments(const ReadArgs<D, S> a, int64_t c0, int64_t coun
     int64_t nb[Q];
     neighbours<D>(x, y, z, a.nx, a.ny, a.nz, cell, nb);
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        double s = 0.0;
-#pragma unroll
-        for (int i = 0; i < Q; ++i) s += logical<D, S>(a, cell, nb, k, i);
-        out[k * ostride + t] = s;
-    }
+    for (int k = 0; k < 8; ++k) out[k * ostride + t] = (double)cell_moment<D, S>(a, cell, nb, k);
 }
 
 template <int D, class S>
@@ -250,12 +274,7 @@ __global__ void __launch_bounds__(kReduceThreads) k_ideal_partials(const ReadArg
         int64_t nb[Q];
         neighbours<D>(x, y, z, a.nx, a.ny, a.nz, cell, nb);
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            double s = 0.0;
-#pragma unroll
-            for (int i = 0; i < Q; ++i) s += logical<D, S>(a, cell, nb, k, i);
-            acc[k] += s;
-        }
+        for (int k = 0; k < 8; ++k) acc[k] += (double)cell_moment<D, S>(a, cell, nb, k);
     }
     __shared__ double red[kReduceThreads / 32][8];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -335,6 +354,8 @@ template <int D, class S> ReadArgs<D, S> make_read_args(vlbm_ctx *c, int di)
     for (int k = 0; k < kMaxLat; ++k) {
         a.ref[k] = d.q_ref[k];
         a.scale[k] = d.q_scale[k];
+        a.ref_f[k] = (float)d.q_ref[k];
+        a.scale_f[k] = (float)d.q_scale[k];
     }
     return a;
 }

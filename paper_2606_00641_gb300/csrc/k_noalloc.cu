@@ -33,32 +33,41 @@ template <class S> struct NaArgs {
     int64_t ncell, stride;
     int parity;
     double ref[8], scale[8];
+    float ref_f[8], scale_f[8];  // FP32 copies for the FP32 compute path
 };
 
+// Q_k of one cell, with the arithmetic of vlbm_conservation: the populations
+// summed in the compute precision of the storage (FP64 only for FP64
+// storage); deviation storage decodes once, r_k + s_k sum_i g_ki.
 template <int D, class S>
-__device__ __forceinline__ double na_logical(const NaArgs<S> &a, int64_t cell, int x, int y, int z, int k, int i)
+__device__ __forceinline__ typename ComputeOf<S>::T na_moment(const NaArgs<S> &a, int64_t cell, int x, int y, int z,
+                                                              int k)
 {
+    using R = typename ComputeOf<S>::T;
     constexpr int Q = AxisSet<D>::Q;
-    int64_t at = cell;
-    int j = i;
-    if (a.parity && i > 0) {
-        // odd parity: direction i is in slot opp(i) of the upstream cell x - c_i
-        j = opp_axis(i);
-        const int ax = (i - 1) >> 1;
-        const int sgn = (i & 1) ? -1 : 1;  // upstream offset along ax
-        if (ax == 0) at = cell + ((x + sgn + a.nx) % a.nx - x);
-        else if (ax == 1) at = cell + (int64_t)a.nx * ((y + sgn + a.ny) % a.ny - y);
-        else at = cell + (int64_t)a.nx * a.ny * ((z + sgn + a.nz) % a.nz - z);
+    R s = R(0);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        int64_t at = cell;
+        int j = i;
+        if (a.parity && i > 0) {
+            // odd parity: direction i is in slot opp(i) of the upstream cell x - c_i
+            j = opp_axis(i);
+            const int ax = (i - 1) >> 1;
+            const int sgn = (i & 1) ? -1 : 1;  // upstream offset along ax
+            if (ax == 0) at = cell + ((x + sgn + a.nx) % a.nx - x);
+            else if (ax == 1) at = cell + (int64_t)a.nx * ((y + sgn + a.ny) % a.ny - y);
+            else at = cell + (int64_t)a.nx * a.ny * ((z + sgn + a.nz) % a.nz - z);
+        }
+        s += (R)Codec<S>::load(a.pop + (int64_t)(k * Q + j) * a.stride + at);
     }
-    double v = (double)Codec<S>::load(a.pop + (int64_t)(k * Q + j) * a.stride + at);
-    if (Codec<S>::kDev) v = v * a.scale[k] + (i == 0 ? AxisSet<D>::w0 : AxisSet<D>::w1) * a.ref[k];
-    return v;
+    if (Codec<S>::kDev) s = s * (R)a.scale_f[k] + (R)a.ref_f[k];
+    return s;
 }
 
 template <int D, class S>
 __global__ void __launch_bounds__(kNaThreads) k_na_partials(const NaArgs<S> a, double *__restrict__ partials)
 {
-    constexpr int Q = AxisSet<D>::Q;
     double acc[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) acc[k] = 0.0;
@@ -71,12 +80,7 @@ __global__ void __launch_bounds__(kNaThreads) k_na_partials(const NaArgs<S> a, d
         const int y = (int)(rest % a.ny);
         const int z = (int)(rest / a.ny);
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            double s = 0.0;
-#pragma unroll
-            for (int i = 0; i < Q; ++i) s += na_logical<D, S>(a, cell, x, y, z, k, i);
-            acc[k] += s;
-        }
+        for (int k = 0; k < 8; ++k) acc[k] += (double)na_moment<D, S>(a, cell, x, y, z, k);
     }
     __shared__ double red[kNaThreads / 32][8];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -149,6 +153,8 @@ vlbm_status na_run(const void *pop, int nx, int ny, int nz, int64_t stride, int 
     for (int k = 0; k < 8; ++k) {
         a.ref[k] = q_ref ? q_ref[k] : 0.0;
         a.scale[k] = (q_scale && q_scale[k] > 0.0) ? q_scale[k] : 1.0;
+        a.ref_f[k] = (float)a.ref[k];
+        a.scale_f[k] = (float)a.scale[k];
     }
     const int nblocks = (int)((a.ncell + kNaCellsPerBlock - 1) / kNaCellsPerBlock);
     k_na_partials<D, S><<<nblocks, kNaThreads, 0, stream>>>(a, scratch);

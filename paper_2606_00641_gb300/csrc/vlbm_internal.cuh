@@ -88,6 +88,17 @@ template <> struct Codec<__nv_bfloat16> {
     __device__ static __forceinline__ void store(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
 };
 
+// Compute precision of a storage type: FP64 storage computes in FP64, the
+// others in FP32 (as the step kernel does).  GB300 runs FP64 arithmetic far
+// slower than FP32, so per-population FP64 work is kept out of the passes
+// that read every population.
+template <class S> struct ComputeOf {
+    using T = float;
+};
+template <> struct ComputeOf<double> {
+    using T = double;
+};
+
 // Per-domain description (host and device copies).
 struct Domain {
     int nx, ny, nz;
