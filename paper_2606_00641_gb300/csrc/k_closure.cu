@@ -6,15 +6,17 @@
 // dPhi[k][a], which the fused step kernel adds to the post-collision
 // populations (f*_{k,+-a} +-= dPhi/2; see include/vlbm.h).
 //
-// Convolutions are implicit GEMMs on mma.sync.m16n8k16 (BF16 in, FP32
-// accumulate): M = cells (each warp owns 16 consecutive cells of one x-row),
-// N = output channels (8 per n-tile), K = 27 taps x input channels, walked
-// in chunks of 16 (Cin = 8: two taps per chunk; Cin = 32: half a tap).
-// Activations are channels-last BF16 ([cell][8] or [cell][32]); weights are
-// re-packed after every update into the per-lane B-fragment order, so a
-// lane's operand is one 8-byte load.  The backward-data pass is the same
-// kernel on the transposed, tap-mirrored weights; the weight gradient is a
-// second mma kernel with K = cells, one CTA per (cell block, tap).
+// Convolutions are implicit GEMMs on the tcgen05 tensor cores (BF16 operands
+// in shared memory, FP32 accumulators in TMEM): k_conv_tc for the forward and
+// data-gradient passes (halo tiles loaded with TMA, the three z-taps stacked
+// along N), k_wgrad_tc for the weight and bias gradients (both operands read
+// MN-major from the staged tiles, fixed-order partial sums).  Grids the
+// tcgen05 tiles do not divide fall back to mma.sync.m16n8k16 kernels (M = 16
+// cells per warp along an x-row, N = output channels, K = 27 taps x input
+// channels in chunks of 16; weight gradient per (cell block, tap) with FP32
+// atomics).  Activations are BF16, channel-blocked (planes of 8 channels, see
+// blk()); weights are re-packed after every update into the tcgen05 and the
+// mma.sync operand layouts.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
