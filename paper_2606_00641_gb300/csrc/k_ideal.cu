@@ -106,7 +106,9 @@ __global__ void __launch_bounds__(kBlockX) k_ideal_step(const IdealArgs<C> a)
         }
 }
 
-// f = f_eq(Q) at parity 0, computed in double; also checks positivity and the
+// f = f_eq(Q) at parity 0 (Eq. 3 with the fluxes of Eq. 12), computed in the
+// compute precision of the storage (FP64 only for FP64 storage; FP64 runs far
+// slower than FP32 on GB300); also checks positivity and the
 // sub-characteristic condition max(|u| + c_f) < cs of the scheme.
 template <int D, class S> struct InitArgs {
     void *pop;
@@ -120,43 +122,48 @@ template <int D, class S> struct InitArgs {
 template <int D, class S>
 __global__ void k_ideal_init(const InitArgs<D, S> a, const double *__restrict__ Qin)
 {
+    using R = typename ComputeOf<S>::T;
     constexpr int Q = AxisSet<D>::Q;
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= a.count) return;
     const int64_t cell = a.c0 + t;
-    double q[8];
+    R q[8];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) q[k] = Qin[k * a.qstride + t];
-    const double rho = q[0];
-    const double u[3] = {q[1] / rho, q[2] / rho, q[3] / rho};
-    const double B[3] = {q[5], q[6], q[7]};
-    const double B2 = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
-    const double u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-    const double uB = u[0] * B[0] + u[1] * B[1] + u[2] * B[2];
-    const double p = (a.gamma - 1.0) * (q[4] - 0.5 * rho * u2 - 0.5 * B2);
-    const double pt = p + 0.5 * B2;
-    if (!(rho > 0.0) || !(p > 0.0)) atomicOr(a.flags, kFlagNonPhysical);
-    const double vsig = sqrt(u2) + sqrt(fmax((a.gamma * p + B2) / rho, 0.0));
-    if (!(vsig < sqrt(AxisSet<D>::cs2))) atomicOr(a.flags, kFlagUnstable);
+    for (int k = 0; k < 8; ++k) q[k] = (R)Qin[k * a.qstride + t];
+    const R rho = q[0];
+    const R inv_rho = R(1) / rho;
+    const R u[3] = {q[1] * inv_rho, q[2] * inv_rho, q[3] * inv_rho};
+    const R B[3] = {q[5], q[6], q[7]};
+    const R B2 = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
+    const R u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    const R uB = u[0] * B[0] + u[1] * B[1] + u[2] * B[2];
+    const R gamma = (R)a.gamma;
+    const R p = (gamma - R(1)) * (q[4] - R(0.5) * rho * u2 - R(0.5) * B2);
+    const R pt = p + R(0.5) * B2;
+    if (!(rho > R(0)) || !(p > R(0))) atomicOr(a.flags, kFlagNonPhysical);
+    const R vsig = sqrt(u2) + sqrt(fmax((gamma * p + B2) * inv_rho, R(0)));
+    if (!(vsig < (R)sqrt(AxisSet<D>::cs2))) atomicOr(a.flags, kFlagUnstable);
     S *pop = static_cast<S *>(a.pop);
+    constexpr double inv_cs2 = 1.0 / AxisSet<D>::cs2;
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-        double phi[D];
+        R phi[D];
 #pragma unroll
         for (int ax = 0; ax < D; ++ax) {
             if (k == 0) phi[ax] = q[1 + ax];
-            else if (k <= 3) phi[ax] = rho * u[ax] * u[k - 1] - B[ax] * B[k - 1] + (ax == k - 1 ? pt : 0.0);
+            else if (k <= 3) phi[ax] = rho * u[ax] * u[k - 1] - B[ax] * B[k - 1] + (ax == k - 1 ? pt : R(0));
             else if (k == 4) phi[ax] = (q[4] + pt) * u[ax] - B[ax] * uB;
-            else phi[ax] = (ax == k - 5) ? 0.0 : u[ax] * B[k - 5] - B[ax] * u[k - 5];
+            else phi[ax] = (ax == k - 5) ? R(0) : u[ax] * B[k - 5] - B[ax] * u[k - 5];
         }
+        const R ref = (R)a.ref[k], inv_scale = (R)(1.0 / a.scale[k]);
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            const double w = i == 0 ? AxisSet<D>::w0 : AxisSet<D>::w1;
-            double cphi = 0.0;
-            if (i > 0) cphi = ((i & 1) ? 1.0 : -1.0) * phi[(i - 1) / 2];
-            double feq = w * (q[k] + cphi / AxisSet<D>::cs2);
-            double v = feq;
-            if (Codec<S>::kDev) v = (feq - w * a.ref[k]) / a.scale[k];
+            const R w = (R)(i == 0 ? AxisSet<D>::w0 : AxisSet<D>::w1);
+            R cphi = R(0);
+            if (i > 0) cphi = ((i & 1) ? R(1) : R(-1)) * phi[(i - 1) / 2];
+            const R feq = w * (q[k] + cphi * (R)inv_cs2);
+            R v = feq;
+            if (Codec<S>::kDev) v = (feq - w * ref) * inv_scale;
             Codec<S>::store(pop + (int64_t)(k * Q + i) * a.stride + cell, (decltype(Codec<S>::load(pop)))v);
         }
     }
