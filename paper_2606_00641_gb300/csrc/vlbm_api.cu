@@ -202,6 +202,24 @@ vlbm_status ensure_stage(vlbm_ctx *c, size_t bytes)
     return VLBM_OK;
 }
 
+// Host fields move through two device chunk buffers: the copies of one chunk
+// run on an internal stream while the context's stream runs the kernel of
+// the other chunk; events order the two streams per buffer.
+static vlbm_status ensure_copy_stream(vlbm_ctx *c)
+{
+    if (c->copy_stream) return VLBM_OK;
+    cudaStream_t s = nullptr;
+    vlbm_status st = cuda_check(c, cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "copy stream");
+    for (int b = 0; b < 2 && st == VLBM_OK; ++b) {
+        st = cuda_check(c, cudaEventCreateWithFlags(&c->ev_copy[b], cudaEventDisableTiming), "copy event");
+        if (st == VLBM_OK)
+            st = cuda_check(c, cudaEventCreateWithFlags(&c->ev_kern[b], cudaEventDisableTiming), "copy event");
+    }
+    if (st == VLBM_OK) c->copy_stream = s;
+    else if (s) cudaStreamDestroy(s);
+    return st;
+}
+
 void drop_graphs(vlbm_ctx *c)
 {
     for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second);
@@ -388,14 +406,25 @@ vlbm_status vlbm_init_fields(vlbm_ctx *c, int domain, const double *Q_host)
     if (s != VLBM_OK) return s;
     const int64_t N = c->dom[domain].ncell;
     const int64_t chunk = std::min<int64_t>(N, kStageCells);
-    s = ensure_stage(c, (size_t)c->nvar * chunk * sizeof(double));
-    for (int64_t c0 = 0; s == VLBM_OK && c0 < N; c0 += chunk) {
+    const size_t half = (size_t)c->nvar * chunk;  // doubles per staging buffer
+    s = ensure_stage(c, 2 * half * sizeof(double));
+    if (s == VLBM_OK) s = ensure_copy_stream(c);
+    // both buffers free once the work already queued on the context's stream is done
+    for (int b = 0; b < 2 && s == VLBM_OK; ++b) s = cuda_check(c, cudaEventRecord(c->ev_kern[b], c->stream), "event");
+    int i = 0;
+    for (int64_t c0 = 0; s == VLBM_OK && c0 < N; c0 += chunk, ++i) {
+        const int b = i & 1;
+        double *buf = c->d_q + b * half;
         const int64_t n = std::min<int64_t>(chunk, N - c0);
+        s = cuda_check(c, cudaStreamWaitEvent(c->copy_stream, c->ev_kern[b], 0), "stream order");
         for (int v = 0; v < c->nvar && s == VLBM_OK; ++v)
-            s = cuda_check(c, cudaMemcpyAsync(c->d_q + v * chunk, Q_host + v * N + c0, n * sizeof(double),
-                                              cudaMemcpyHostToDevice, c->stream),
+            s = cuda_check(c, cudaMemcpyAsync(buf + v * chunk, Q_host + v * N + c0, n * sizeof(double),
+                                              cudaMemcpyHostToDevice, c->copy_stream),
                            "field upload");
-        if (s == VLBM_OK) s = init_range(c, domain, c->d_q, c0, n, chunk);
+        if (s == VLBM_OK) s = cuda_check(c, cudaEventRecord(c->ev_copy[b], c->copy_stream), "event");
+        if (s == VLBM_OK) s = cuda_check(c, cudaStreamWaitEvent(c->stream, c->ev_copy[b], 0), "stream order");
+        if (s == VLBM_OK) s = init_range(c, domain, buf, c0, n, chunk);
+        if (s == VLBM_OK) s = cuda_check(c, cudaEventRecord(c->ev_kern[b], c->stream), "event");
     }
     if (s != VLBM_OK) return s;
     return finish_init(c);
@@ -465,15 +494,28 @@ vlbm_status vlbm_moments(vlbm_ctx *c, int domain, double *Q_host)
     if (domain < 0 || domain >= (int)c->dom.size()) return fail(c, VLBM_ERR_ARG, "bad domain index");
     const int64_t N = c->dom[domain].ncell;
     const int64_t chunk = std::min<int64_t>(N, kStageCells);
-    vlbm_status s = ensure_stage(c, (size_t)c->nvar * chunk * sizeof(double));
-    for (int64_t c0 = 0; s == VLBM_OK && c0 < N; c0 += chunk) {
+    const size_t half = (size_t)c->nvar * chunk;  // doubles per staging buffer
+    vlbm_status s = ensure_stage(c, 2 * half * sizeof(double));
+    if (s == VLBM_OK) s = ensure_copy_stream(c);
+    for (int b = 0; b < 2 && s == VLBM_OK; ++b)  // no download pending on either buffer
+        s = cuda_check(c, cudaEventRecord(c->ev_copy[b], c->copy_stream), "event");
+    int i = 0;
+    for (int64_t c0 = 0; s == VLBM_OK && c0 < N; c0 += chunk, ++i) {
+        const int b = i & 1;
+        double *buf = c->d_q + b * half;
         const int64_t n = std::min<int64_t>(chunk, N - c0);
-        s = moments_range(c, domain, c->d_q, c0, n, chunk);
+        s = cuda_check(c, cudaStreamWaitEvent(c->stream, c->ev_copy[b], 0), "stream order");
+        if (s == VLBM_OK) s = moments_range(c, domain, buf, c0, n, chunk);
+        if (s == VLBM_OK) s = cuda_check(c, cudaEventRecord(c->ev_kern[b], c->stream), "event");
+        if (s == VLBM_OK) s = cuda_check(c, cudaStreamWaitEvent(c->copy_stream, c->ev_kern[b], 0), "stream order");
         for (int v = 0; v < c->nvar && s == VLBM_OK; ++v)
-            s = cuda_check(c, cudaMemcpyAsync(Q_host + v * N + c0, c->d_q + v * chunk, n * sizeof(double),
-                                              cudaMemcpyDeviceToHost, c->stream),
+            s = cuda_check(c, cudaMemcpyAsync(Q_host + v * N + c0, buf + v * chunk, n * sizeof(double),
+                                              cudaMemcpyDeviceToHost, c->copy_stream),
                            "field download");
+        if (s == VLBM_OK) s = cuda_check(c, cudaEventRecord(c->ev_copy[b], c->copy_stream), "event");
     }
+    if (s != VLBM_OK) return s;
+    s = cuda_check(c, cudaStreamSynchronize(c->copy_stream), "moments synchronise");
     if (s != VLBM_OK) return s;
     return cuda_check(c, cudaStreamSynchronize(c->stream), "moments synchronise");
 }
@@ -688,6 +730,14 @@ void vlbm_destroy(vlbm_ctx *c)
     dev_free_all(c);
     if (c->h_flags) cudaFreeHost(c->h_flags);
     if (c->flag_event) cudaEventDestroy(c->flag_event);
+    if (c->copy_stream) {
+        cudaStreamSynchronize(c->copy_stream);
+        cudaStreamDestroy(c->copy_stream);
+    }
+    for (int b = 0; b < 2; ++b) {
+        if (c->ev_copy[b]) cudaEventDestroy(c->ev_copy[b]);
+        if (c->ev_kern[b]) cudaEventDestroy(c->ev_kern[b]);
+    }
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     cudaGetLastError();
     delete c;

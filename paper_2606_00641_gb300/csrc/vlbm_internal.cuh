@@ -139,6 +139,8 @@ struct vlbm_ctx {
 
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    cudaStream_t copy_stream = nullptr;  // host-field staging copies (overlap the chunk kernels)
+    cudaEvent_t ev_copy[2]{}, ev_kern[2]{};  // per staging buffer: last copy / last kernel done
     cudaEvent_t flag_event = nullptr;
     bool flag_pending = false;
     int64_t steps_since_check = 0;
