@@ -13,6 +13,8 @@
 // goal is plain bandwidth: one cell per thread, coalesced x-contiguous slot
 // planes, every load issued before any arithmetic, no shared memory, grid
 // (ceil(nx/128), ny, nz).
+#include <algorithm>
+
 #include "ideal_cell.cuh"
 
 namespace vlbm {
@@ -104,6 +106,147 @@ __global__ void __launch_bounds__(kBlockX) k_ideal_step(const IdealArgs<C> a)
             const int64_t at = ODD ? nb[i] : cell;
             Codec<S>::store(pop + (int64_t)(k * Q + j) * a.stride + at, f[k][i]);
         }
+}
+
+// The same step for 16-bit storage in 3-D with the loads done by the
+// bulk-copy engine.  A tile is an x-row segment of 128 cells; the 56 slot
+// plane rows its cells read (even parity: their own row; odd parity: the row
+// of the upstream cell, one plane row over for the y and z directions and one
+// element over for x) arrive in shared memory by one cp.async.bulk each, plus
+// the single element beyond the tile edge that the x-moving slots of the odd
+// parity need.  Persistent CTAs with two buffers: the rows of the next tile
+// are in flight while the threads collide the current one from shared memory,
+// so the bytes in flight per SM no longer depend on how many warps the
+// registers allow -- the limit of the one-cell-per-thread kernel on 16-bit
+// storage, whose 2-byte loads carry half the bytes of FP32 ones.  Needs
+// nx % 8 == 0 (16-byte aligned rows).
+constexpr int kBulkPad = 8;  // elements (16 bytes) before and after each staged row
+
+template <class S, bool ODD>
+__global__ void __launch_bounds__(kBlockX) k_ideal_step_bulk(const IdealArgs<float> a)
+{
+    constexpr int Q = 7;
+    constexpr int ROW = kBlockX + 2 * kBulkPad;
+    __shared__ __align__(128) S sm[2][8 * Q][ROW];
+    __shared__ __align__(8) uint64_t bar[2];
+    const int tid = threadIdx.x;
+    const int tiles_x = (a.nx + kBlockX - 1) / kBlockX;
+    const int ntiles = tiles_x * a.ny * a.nz;
+    const int64_t plane = (int64_t)a.nx * a.ny;
+    S *pop = static_cast<S *>(a.pop);
+    const uint32_t bar_s = (uint32_t)__cvta_generic_to_shared(bar);
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar_s), "r"(8 * Q));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar_s + 8u), "r"(8 * Q));
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+
+    struct Tile {
+        int x0, y, z, tx;
+        int64_t row, c0;
+    };
+    auto tile_of = [&](int t) {
+        Tile T;
+        T.x0 = (t % tiles_x) * kBlockX;
+        const int r = t / tiles_x;
+        T.y = r % a.ny;
+        T.z = r / a.ny;
+        T.tx = min(kBlockX, a.nx - T.x0);
+        T.row = (int64_t)a.nx * T.y + plane * T.z;
+        T.c0 = T.row + T.x0;
+        return T;
+    };
+    // slot plane j = tid: arm the buffer's barrier with its bytes and copy its row segment
+    auto load_rows = [&](const Tile &T, int b) {
+        if (tid >= 8 * Q) return;
+        const int j = tid, jj = j % Q;
+        int64_t src = T.c0;
+        if (ODD) {
+            const int i = opp_axis(jj);  // the direction that reads slot jj
+            if (i == 3) src = T.y > 0 ? T.c0 - a.nx : T.c0 + (int64_t)(a.ny - 1) * a.nx;  // from y - 1
+            else if (i == 4) src = T.y + 1 < a.ny ? T.c0 + a.nx : T.c0 - (int64_t)(a.ny - 1) * a.nx;
+            else if (i == 5) src = T.z > 0 ? T.c0 - plane : T.c0 + (int64_t)(a.nz - 1) * plane;  // from z - 1
+            else if (i == 6) src = T.z + 1 < a.nz ? T.c0 + plane : T.c0 - (int64_t)(a.nz - 1) * plane;
+        }
+        const uint32_t mb = bar_s + 8u * (uint32_t)b;
+        const uint32_t bytes = (uint32_t)(T.tx * (int)sizeof(S));
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mb), "r"(bytes) : "memory");
+        const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&sm[b][j][kBulkPad]);
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
+                     ::"r"(dst), "l"(pop + (int64_t)j * a.stride + src), "r"(bytes), "r"(mb)
+                     : "memory");
+    };
+    // odd parity: +x reads slot 2 at x - 1, -x reads slot 1 at x + 1, one element beyond each tile edge
+    const bool edge_thread = ODD && tid >= 64 && tid < 80;
+    const int eq = tid - 64, ek = eq & 7;
+    const int ej = eq < 8 ? ek * Q + 2 : ek * Q + 1;
+    auto edge_load = [&](const Tile &T) -> S {
+        const int xs = eq < 8 ? (T.x0 > 0 ? T.x0 - 1 : a.nx - 1) : (T.x0 + T.tx < a.nx ? T.x0 + T.tx : 0);
+        return pop[(int64_t)ej * a.stride + T.row + xs];
+    };
+    auto edge_store = [&](const Tile &T, int b, S v) { sm[b][ej][eq < 8 ? kBulkPad - 1 : kBulkPad + T.tx] = v; };
+
+    int t = blockIdx.x;
+    Tile cur = tile_of(t);
+    if (t < ntiles) {
+        load_rows(cur, 0);
+        if (edge_thread) edge_store(cur, 0, edge_load(cur));
+    }
+    __syncthreads();
+    bool ok = true;
+    for (int i = 0; t < ntiles && ok; ++i, t += gridDim.x) {
+        const int b = i & 1;
+        const int tn = t + gridDim.x;
+        const Tile nxt = tile_of(tn);
+        S ev{};
+        if (tn < ntiles) {  // the next tile's rows travel while this one is collided
+            load_rows(nxt, b ^ 1);
+            if (edge_thread) ev = edge_load(nxt);
+        }
+        uint32_t done = 0;
+        for (uint32_t it = 0; it < (1u << 16) && !done; ++it)
+            asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+                         "selp.u32 %0, 1, 0, p;\n\t}\n"
+                         : "=r"(done)
+                         : "r"(bar_s + 8u * (uint32_t)b), "r"((uint32_t)((i >> 1) & 1)), "r"(20000u)
+                         : "memory");
+        if (!__syncthreads_and((int)done)) {  // one outcome for the whole CTA
+            if (tid == 0) atomicOr(a.flags, kFlagTimeout);
+            ok = false;
+            break;
+        }
+        if (tid < cur.tx) {
+            const int x = cur.x0 + tid;
+            const int64_t cell = cur.c0 + tid;
+            float f[8][Q];
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+#pragma unroll
+                for (int ii = 0; ii < Q; ++ii) {
+                    const int jj = ODD ? opp_axis(ii) : ii;
+                    const int sh = ODD ? (ii == 1 ? -1 : (ii == 2 ? 1 : 0)) : 0;
+                    f[k][ii] = Codec<S>::load(&sm[b][k * Q + jj][kBulkPad + tid + sh]);
+                }
+            ideal_collide<3, float, true>(f, a.gm1, a.omega, a.src0, a.src1, a.flags, a.ref, a.scale,
+                                          a.inv_scale);
+            // store: even parity sends direction i to slot (opp i, x);
+            //        odd parity sends direction i to slot (i, x + c_i)
+            int64_t nb[Q];
+            neighbours<3>(x, cur.y, cur.z, a.nx, a.ny, a.nz, cell, nb);
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+#pragma unroll
+                for (int ii = 0; ii < Q; ++ii) {
+                    const int j = ODD ? ii : opp_axis(ii);
+                    const int64_t at = ODD ? nb[ii] : cell;
+                    Codec<S>::store(pop + (int64_t)(k * Q + j) * a.stride + at, f[k][ii]);
+                }
+        }
+        if (edge_thread && tn < ntiles) edge_store(nxt, b ^ 1, ev);
+        __syncthreads();  // buffer b consumed before it is refilled; edge elements visible
+        cur = nxt;
+    }
 }
 
 // f = f_eq(Q) at parity 0 (Eq. 3 with the fluxes of Eq. 12), computed in the
@@ -372,6 +515,25 @@ template <int D, class S, class C> vlbm_status step_t(vlbm_ctx *c, int parity)
     const Domain &d = c->dom[0];
     const IdealArgs<C> a = make_step_args<C>(c);
     const dim3 grid((unsigned)((d.nx + kBlockX - 1) / kBlockX), (unsigned)d.ny, (unsigned)d.nz);
+    if constexpr (D == 3 && Codec<S>::kDev) {
+        if (d.nx % 8 == 0) {  // 16-byte aligned rows: bulk-copy loads, persistent CTAs
+            if (c->bulk_ctas == 0) {  // every SM filled to the kernel's occupancy
+                int dev = 0, sms = 1, per_sm = 1;
+                cudaGetDevice(&dev);
+                cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ideal_step_bulk<S, false>, kBlockX, 0);
+                c->bulk_ctas = std::max(1, sms) * std::max(1, per_sm);
+            }
+            const int ntiles = (int)grid.x * d.ny * d.nz;
+            const unsigned g = (unsigned)std::min(ntiles, c->bulk_ctas);
+            if (parity)
+                k_ideal_step_bulk<S, true><<<g, kBlockX, 0, c->stream>>>(a);
+            else
+                k_ideal_step_bulk<S, false><<<g, kBlockX, 0, c->stream>>>(a);
+            c->launches++;
+            return cuda_check(c, cudaGetLastError(), "ideal step launch");
+        }
+    }
     if (parity)
         k_ideal_step<D, S, C, true><<<grid, kBlockX, 0, c->stream>>>(a);
     else

@@ -140,6 +140,7 @@ struct vlbm_ctx {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     cudaStream_t copy_stream = nullptr;  // host-field staging copies (overlap the chunk kernels)
+    int bulk_ctas = 0;                   // persistent grid of the bulk-load step (0: not sized yet)
     cudaEvent_t ev_copy[2]{}, ev_kern[2]{};  // per staging buffer: last copy / last kernel done
     cudaEvent_t flag_event = nullptr;
     bool flag_pending = false;

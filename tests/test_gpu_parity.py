@@ -254,7 +254,9 @@ def test_deviation_storage_error_bound(V, storage, bound, shape):
     assert err.max() < bound, err
 
 
-@pytest.mark.parametrize("shape", [(5, 6, 128), (9, 192)])
+# 3-D rows with nx % 8 == 0 load through the bulk-copy engine: one tile (128),
+# two tiles with a partial edge tile (136); nx = 44 takes the per-thread loads
+@pytest.mark.parametrize("shape", [(5, 6, 128), (4, 6, 136), (3, 5, 44), (9, 192)])
 @pytest.mark.parametrize("storage,ulp", [("f16dev", 2.0 ** -11), ("bf16dev", 2.0 ** -8)])
 @pytest.mark.parametrize("parity", [0, 1])
 def test_deviation_storage_one_step_sampled(V, shape, storage, ulp, parity):
