@@ -35,7 +35,7 @@ constexpr Choice kChoices[] = {{128, 1, 1}, {128, 1, 0}, {256, 1, 1}, {128, 2, 1
 constexpr int kNumChoices = sizeof(kChoices) / sizeof(kChoices[0]);
 
 template <bool ODD, int TX, int R>
-__global__ void __launch_bounds__(TX) k_batch_step(const int2 *__restrict__ tiles, int ntiles,
+__global__ void __launch_bounds__(TX, 640 / TX) k_batch_step(const int2 *__restrict__ tiles, int ntiles,
                                                    const BatchDomain *__restrict__ doms, float *pop,
                                                    unsigned *flags)
 {

@@ -93,7 +93,7 @@ __device__ __forceinline__ int64_t nbr(const Offsets &o, int64_t cell, int cx, i
 __device__ __forceinline__ bool wall_row(int y, int ny, int walls) { return walls && (y == 0 || y == ny - 1); }
 
 template <bool ODD>
-__global__ void __launch_bounds__(kBlockX) k_res_step(const Args a)
+__global__ void __launch_bounds__(kBlockX, 5) k_res_step(const Args a)
 {
     const int x = blockIdx.x * kBlockX + threadIdx.x;
     if (x >= a.nx) return;
