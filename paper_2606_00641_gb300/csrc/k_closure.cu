@@ -1450,15 +1450,20 @@ vlbm_status conv(vlbm_closure *cl, int layer, const bf16 *in, bool transpose, co
 ConvEpilogue epi() { ConvEpilogue e{}; return e; }
 
 // network forward from device fields Q (8 x N doubles) to dphi (N x 24 floats)
-vlbm_status forward(vlbm_closure *cl, const double *Q, float *dphi, cudaStream_t s)
+Norm feature_norm(const vlbm_closure *cl)
 {
     Norm n{};
     for (int k = 0; k < 8; ++k) {
         n.mu[k] = (float)cl->p.mu[k];
         n.inv_sigma[k] = (float)(1.0 / cl->p.sigma[k]);
     }
-    k_features<<<(cl->N + 255) / 256, 256, 0, s>>>(Q, cl->N, n, cl->x);
-    vlbm_status st = cl_check(cudaGetLastError(), "closure features launch");
+    return n;
+}
+
+// the three convolutions from the features in cl->x to dphi
+vlbm_status forward_convs(vlbm_closure *cl, float *dphi, cudaStream_t s)
+{
+    vlbm_status st = VLBM_OK;
     ConvEpilogue e = epi();
     e.bias = cl->theta + cl->off_b[0];
     e.tanh_act = 1;
@@ -1474,6 +1479,23 @@ vlbm_status forward(vlbm_closure *cl, const double *Q, float *dphi, cudaStream_t
     e.out_f = dphi;
     e.os = kOut;
     if (st == VLBM_OK) st = conv(cl, 2, cl->a2, false, e, s);
+    return st;
+}
+
+vlbm_status forward(vlbm_closure *cl, const double *Q, float *dphi, cudaStream_t s)
+{
+    k_features<<<(cl->N + 255) / 256, 256, 0, s>>>(Q, cl->N, feature_norm(cl), cl->x);
+    vlbm_status st = cl_check(cudaGetLastError(), "closure features launch");
+    if (st == VLBM_OK) st = forward_convs(cl, dphi, s);
+    return st;
+}
+
+// forward pass on the current state of a context: features straight from its populations
+vlbm_status forward_ctx(vlbm_closure *cl, vlbm_ctx *c, float *dphi)
+{
+    const Norm n = feature_norm(cl);
+    vlbm_status st = ideal_features(c, n.mu, n.inv_sigma, cl->x);
+    if (st == VLBM_OK) st = forward_convs(cl, dphi, c->stream);
     return st;
 }
 
@@ -1778,8 +1800,7 @@ vlbm_status vlbm_closure_train_step_ctx(vlbm_closure *cl, vlbm_ctx *ctx, const d
         ctx->dom[0].nx != cl->nx || ctx->dom[0].ny != cl->ny || ctx->dom[0].nz != cl->nz)
         return fail(ctx, VLBM_ERR_ARG, "closure training context must be a 3-D F32 ideal context on the closure grid");
     cudaStream_t s = ctx->stream;
-    vlbm_status st = ideal_moments(ctx, 0, cl->q);
-    if (st == VLBM_OK) st = forward(cl, cl->q, cl->dphi, s);
+    vlbm_status st = forward_ctx(cl, ctx, cl->dphi);
     if (st == VLBM_OK) st = ideal_step_corrected(ctx, (int)(ctx->step & 1), cl->dphi);
     if (st == VLBM_OK) {
         ctx->step += 1;
@@ -1820,11 +1841,10 @@ namespace vlbm {
 vlbm_status closure_step(vlbm_ctx *c, int parity)
 {
     vlbm_closure *cl = c->closure;
-    vlbm_status st = ideal_moments(c, 0, cl->q);
     cl->step_err = c->d_flags;  // timeouts surface through the context's health word
-    if (st == VLBM_OK) st = forward(cl, cl->q, cl->dphi, c->stream);
+    vlbm_status st = forward_ctx(cl, c, cl->dphi);
     cl->step_err = cl->errflag;
-    c->launches += 4;  // features and three convolutions (moments and the step count themselves)
+    c->launches += 3;  // three convolutions (features and the step count themselves)
     if (st == VLBM_OK) st = ideal_step_corrected(c, parity, cl->dphi);
     return st;
 }

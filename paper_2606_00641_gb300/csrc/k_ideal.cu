@@ -388,6 +388,30 @@ __global__ void k_ideal_moments(const ReadArgs<D, S> a, int64_t c0, int64_t coun
     for (int k = 0; k < 8; ++k) out[k * ostride + t] = (double)cell_moment<D, S>(a, cell, nb, k);
 }
 
+// Closure input features from the populations: the FP32 moments of
+// k_ideal_moments, normalised and rounded to BF16, 16 bytes per cell.
+struct FeatureNorm {
+    float mu[8], inv_sigma[8];
+};
+
+template <int D, class S>
+__global__ void k_ideal_features(const ReadArgs<D, S> a, int64_t count, const FeatureNorm fn,
+                                 __nv_bfloat16 *__restrict__ x)
+{
+    constexpr int Q = AxisSet<D>::Q;
+    const int64_t cell = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (cell >= count) return;
+    int cx, cy, cz;
+    cell_xyz<D>(cell, a.nx, a.ny, cx, cy, cz);
+    int64_t nb[Q];
+    neighbours<D>(cx, cy, cz, a.nx, a.ny, a.nz, cell, nb);
+    __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+        v[k] = __float2bfloat16_rn(((float)cell_moment<D, S>(a, cell, nb, k) - fn.mu[k]) * fn.inv_sigma[k]);
+    *reinterpret_cast<uint4 *>(x + cell * 8) = *reinterpret_cast<const uint4 *>(v);
+}
+
 template <int D, class S>
 __global__ void k_ideal_gather(const ReadArgs<D, S> a, const int64_t *__restrict__ cells, int n,
                                double *__restrict__ out)
@@ -690,5 +714,22 @@ vlbm_status ideal_gather(vlbm_ctx *c, int d, const int64_t *cells_dev, int n, do
 }
 
 vlbm_status ideal_sums(vlbm_ctx *c, int d, double *sums_dev) { return dispatch<SumsF>(c, d, sums_dev); }
+
+vlbm_status ideal_features(vlbm_ctx *c, const float *mu, const float *inv_sigma, __nv_bfloat16 *x)
+{
+    if (c->batched || c->dim != 3 || c->storage != VLBM_F32)
+        return fail(c, VLBM_ERR_ARG, "closure features need a 3-D FP32 context");
+    FeatureNorm fn{};
+    for (int k = 0; k < 8; ++k) {
+        fn.mu[k] = mu[k];
+        fn.inv_sigma[k] = inv_sigma[k];
+    }
+    const int64_t N = c->dom[0].ncell;
+    const int threads = 256;
+    k_ideal_features<3, float><<<(unsigned)((N + threads - 1) / threads), threads, 0, c->stream>>>(
+        make_read_args<3, float>(c, 0), N, fn, x);
+    c->launches++;
+    return cuda_check(c, cudaGetLastError(), "closure features launch");
+}
 
 }  // namespace vlbm

@@ -198,6 +198,9 @@ int batch_num_choices();
 
 // learned closure (k_closure.cu / k_ideal.cu)
 vlbm_status ideal_step_corrected(vlbm_ctx *c, int parity, const float *dphi);
+// closure input features of a 3-D FP32 context straight from its populations:
+// x[cell][k] = BF16((Q_k - mu_k) * inv_sigma_k), Q_k summed in FP32 as by ideal_moments
+vlbm_status ideal_features(vlbm_ctx *c, const float *mu, const float *inv_sigma, __nv_bfloat16 *x);
 vlbm_status closure_step(vlbm_ctx *c, int parity);
 int closure_cells(const vlbm_closure *cl, int *nx, int *ny, int *nz);
 
