@@ -255,8 +255,10 @@ def test_deviation_storage_error_bound(V, storage, bound, shape):
 
 
 # 3-D rows with nx % 8 == 0 load through the bulk-copy engine: one tile (128),
-# two tiles with a partial edge tile (136); nx = 44 takes the per-thread loads
-@pytest.mark.parametrize("shape", [(5, 6, 128), (4, 6, 136), (3, 5, 44), (9, 192)])
+# two tiles with a partial edge tile (136), degenerate extents whose y / z
+# neighbours are the cell itself (1, 1, 64) and (2, 1, 16); nx = 44 takes the
+# per-thread loads
+@pytest.mark.parametrize("shape", [(5, 6, 128), (4, 6, 136), (1, 1, 64), (2, 1, 16), (3, 5, 44), (9, 192)])
 @pytest.mark.parametrize("storage,ulp", [("f16dev", 2.0 ** -11), ("bf16dev", 2.0 ** -8)])
 @pytest.mark.parametrize("parity", [0, 1])
 def test_deviation_storage_one_step_sampled(V, shape, storage, ulp, parity):
@@ -267,6 +269,7 @@ def test_deviation_storage_one_step_sampled(V, shape, storage, ulp, parity):
     f0 = fields.ideal_fields(shape, 707, mach=1.0, beta=1.0, cfl=0.1 if dim == 2 else 0.2)
     qref = f0.Q.reshape(8, -1).mean(1)
     qscale = np.abs(f0.Q - qref.reshape((8,) + (1,) * dim)).reshape(8, -1).max(1)
+    qscale = np.where(qscale > 0, qscale, 1.0)  # a uniform field (degenerate extents): unit scale
     p = V.make_params(shape=shape, storage=storage, gamma=f0.gamma, tau=0.6, q_ref=qref, q_scale=qscale)
     N = int(np.prod(shape))
     nx = shape[-1]
@@ -280,10 +283,10 @@ def test_deviation_storage_one_step_sampled(V, shape, storage, ulp, parity):
 
     rng = np.random.default_rng(parity)
     # every warp-edge lane (x0 = 0, 62, 64, 126 ...) and row ends, plus random cells
-    edge_x = sorted({0, 1, 62, 63, 64, 65, 126, 127} | {nx - 2, nx - 1})
-    base = rng.choice(N // nx, size=6, replace=False) * nx
+    edge_x = sorted(e for e in {0, 1, 62, 63, 64, 65, 126, 127, nx - 2, nx - 1} if e < nx)
+    base = rng.choice(N // nx, size=min(6, N // nx), replace=False) * nx
     cells = np.unique(np.concatenate([b + np.array(edge_x) for b in base] +
-                                     [rng.choice(N, size=40, replace=False)])).astype(np.int64)
+                                     [rng.choice(N, size=min(40, N), replace=False)])).astype(np.int64)
     with V.Context(p) as ctx:
         assert ctx.init_fields(f0.Q) == V.VLBM_OK
         ctx.step(2 + parity)
