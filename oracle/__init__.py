@@ -67,6 +67,15 @@ def _configure(L):
     L.orc_resistive_moments.argtypes = [i, i, i, p, p, i, p, p, p]
     L.orc_resistive_run.argtypes = [i, i, i, d, d, p, p, i, p, i, p, i]
     L.orc_resistive_collide_cell.argtypes = [d, d, p, p, p]
+    L.orc_powell_flux.argtypes = [d, p, p]
+    L.orc_powell_flux.restype = None
+    L.orc_powell_source.argtypes = [d, p, p]
+    L.orc_powell_source.restype = None
+    L.orc_powell_collide_cell.argtypes = [i, d, p, d, p, p, p]
+    L.orc_powell_init.argtypes = [i, i, i, i, d, p, p]
+    L.orc_powell_step.argtypes = [i, i, i, i, d, p, d, p, p, p, i]
+    L.orc_powell_moments.argtypes = [i, i, i, i, p, p]
+    L.orc_powell_run.argtypes = [i, i, i, i, d, p, d, p, p, i, p, i]
     return L
 
 
@@ -212,6 +221,79 @@ def ideal_run(Q0: np.ndarray, gamma: float, tau, nsteps: int, src=None,
     _check(lib().orc_ideal_run(dim, nx, ny, nz, gamma, _ptr(tau),
                                _ptr(s) if s is not None else None, _ptr(Q0), nsteps,
                                _ptr(out), nthreads), "run")
+    return out
+
+
+# ---- ideal MHD with the Powell correction: nine fields, the ninth D ~ tau_M div B ----
+
+def powell_flux(gamma: float, Q) -> np.ndarray:
+    """Flux phi[k, a] of the nine Powell-form fields at one state Q[9]."""
+    phi = np.zeros(27)
+    lib().orc_powell_flux(gamma, _ptr(_f64(Q)), _ptr(phi))
+    return phi.reshape(9, 3)
+
+
+def powell_source(tau_m: float, Q) -> np.ndarray:
+    """Source S[9] at one state: Powell's term with div B = D / tau_M, and -D / tau_M."""
+    S = np.zeros(9)
+    lib().orc_powell_source(tau_m, _ptr(_f64(Q)), _ptr(S))
+    return S
+
+
+def _tau9(tau):
+    return _f64(np.broadcast_to(np.asarray(tau, dtype=np.float64), (9,)))
+
+
+def powell_init(Q0: np.ndarray, gamma: float) -> np.ndarray:
+    """Populations f[9, q, *shape] = f_eq(Q0); Q0 has shape [9, (nz,) ny, nx]."""
+    Q0 = _f64(Q0)
+    dim, nx, ny, nz = _dims(Q0.shape[1:])
+    q = 5 if dim == 2 else 7
+    f = np.zeros((9, q) + Q0.shape[1:])
+    _check(lib().orc_powell_init(dim, nx, ny, nz, gamma, _ptr(Q0), _ptr(f)), "powell_init")
+    return f
+
+
+def powell_step(f: np.ndarray, gamma: float, tau, tau_m: float, src=None, nthreads: int = 1) -> np.ndarray:
+    f = _f64(f)
+    dim, nx, ny, nz = _dims(f.shape[2:])
+    out = np.empty_like(f)
+    s = _f64(src) if src is not None else None
+    _check(lib().orc_powell_step(dim, nx, ny, nz, gamma, _ptr(_tau9(tau)), tau_m,
+                                 _ptr(s) if s is not None else None, _ptr(f), _ptr(out), nthreads),
+           "powell_step")
+    return out
+
+
+def powell_moments(f: np.ndarray) -> np.ndarray:
+    f = _f64(f)
+    dim, nx, ny, nz = _dims(f.shape[2:])
+    Q = np.zeros((9,) + f.shape[2:])
+    _check(lib().orc_powell_moments(dim, nx, ny, nz, _ptr(f), _ptr(Q)), "powell_moments")
+    return Q
+
+
+def powell_collide_cell(dim: int, gamma: float, tau, tau_m: float, fin, src=None) -> np.ndarray:
+    """Post-collision populations [9, q] of one cell from its pre-collision ones."""
+    fin = _f64(fin)
+    out = np.zeros_like(fin)
+    s = _f64(src) if src is not None else None
+    _check(lib().orc_powell_collide_cell(dim, gamma, _ptr(_tau9(tau)), tau_m,
+                                         _ptr(s) if s is not None else None, _ptr(fin), _ptr(out)),
+           "powell_collide_cell")
+    return out
+
+
+def powell_run(Q0: np.ndarray, gamma: float, tau, tau_m: float, nsteps: int, src=None,
+               nthreads: int = 1) -> np.ndarray:
+    """Moments [9, ...] after nsteps steps of the Powell form started from f_eq(Q0)."""
+    Q0 = _f64(Q0)
+    dim, nx, ny, nz = _dims(Q0.shape[1:])
+    out = np.zeros_like(Q0)
+    s = _f64(src) if src is not None else None
+    _check(lib().orc_powell_run(dim, nx, ny, nz, gamma, _ptr(_tau9(tau)), tau_m,
+                                _ptr(s) if s is not None else None, _ptr(Q0), nsteps, _ptr(out),
+                                nthreads), "powell_run")
     return out
 
 

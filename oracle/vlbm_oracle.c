@@ -14,6 +14,8 @@
  *   Eq. 5  D = (tau - 1/2) c_s^2 dt                                (sec. 2.2)
  *   Eq. 9  ideal-gas EOS with magnetic energy                      (sec. 2.3)
  *   Eq. 12 ideal MHD state vector and flux                         (sec. 2.3)
+ *   Powell source  S = -(div B)(0, B, u.B, u)          (sec. 2.3, "Powell correction")
+ *   local gradient evolution  dG/dt + div Phi_G = -G/tau_R          (sec. 2.2.1)
  *
  * Readings where the paper is silent (each one is listed in the design notes):
  *   - lattice weights: D2Q5 w0=1/3, w=1/6, cs2=1/3;  D3Q7 w0=1/4, w=1/8,
@@ -337,6 +339,182 @@ int orc_ideal_run(int dim, int nx, int ny, int nz, double gamma, const double *t
         b = t;
     }
     orc_ideal_moments(dim, nx, ny, nz, a, Qout);
+    free(a);
+    free(b);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Ideal MHD with the Powell correction and a local divergence of B     */
+/* ------------------------------------------------------------------ */
+/*
+ * Sec. 2.3 "Powell correction": the source  S = -(div B) (0, B, u.B, u)  is
+ * injected into the lattices of rho, rho u, e_tot and B.  div B comes from
+ * the local moments evolution of sec. 2.2.1: the gradient tensor G of B is
+ * carried with the flux Phi_G = G (x) u - I (x) B and the relaxation source
+ * -G / tau_M (sec. 2.3 "Evolution of the MHD equation system"), so that
+ * G ~ tau_M grad B.  The correction needs only the trace of G; a ninth lattice
+ * carries it: D = tr G, with the trace of that flux, Phi_D = D u - B, and the
+ * source -D / tau_M; then div B = D / tau_M.  (Reading, listed in the design
+ * notes: one trace lattice instead of the full tensor, tau_M in time steps.)
+ * State Q = (rho, rho u_x, rho u_y, rho u_z, e_tot, B_x, B_y, B_z, D).
+ */
+#define ORC_NVAR_POWELL 9
+
+/* Flux of the nine fields along the three axes: Eq. 12 for the first eight,
+ * Phi_D,a = D u_a - B_a for the ninth.  phi[3*k + a]. */
+void orc_powell_flux(double gamma, const double *Q, double *phi)
+{
+    orc_ideal_flux(gamma, Q, phi);
+    double rho = Q[0];
+    for (int a = 0; a < 3; ++a) phi[3 * 8 + a] = Q[8] * (Q[1 + a] / rho) - Q[5 + a];
+}
+
+/* Source of the nine fields at one state: Powell's term with
+ * div B = D / tau_M for the first eight, -D / tau_M for the ninth. */
+void orc_powell_source(double tau_m, const double *Q, double *S)
+{
+    double rho = Q[0];
+    double u[3] = {Q[1] / rho, Q[2] / rho, Q[3] / rho};
+    double B[3] = {Q[5], Q[6], Q[7]};
+    double divB = Q[8] / tau_m;
+    double uB = u[0] * B[0] + u[1] * B[1] + u[2] * B[2];
+    S[0] = 0.0;
+    for (int b = 0; b < 3; ++b) {
+        S[1 + b] = -divB * B[b];
+        S[5 + b] = -divB * u[b];
+    }
+    S[4] = -divB * uB;
+    S[8] = -Q[8] / tau_m;
+}
+
+static void powell_feq(const orc_lattice *L, double gamma, const double *Q,
+                       double feq[ORC_NVAR_POWELL][ORC_QMAX])
+{
+    double phi[3 * ORC_NVAR_POWELL];
+    orc_powell_flux(gamma, Q, phi);
+    for (int k = 0; k < ORC_NVAR_POWELL; ++k)
+        for (int i = 0; i < L->q; ++i) {
+            double cphi = 0.0;
+            for (int a = 0; a < 3; ++a) cphi += L->c[i][a] * phi[3 * k + a];
+            double moving = cphi / L->cs2;
+            feq[k][i] = L->w[i] * (Q[k] + moving); /* Eq. 3 */
+        }
+}
+
+/* Collision of one cell: BGK towards Eq. 3 and direct injection of the
+ * state-dependent source plus an optional uniform source src[9]. */
+static void powell_collide(const orc_lattice *L, double gamma, const double *tau, double tau_m,
+                           const double *src, const double *fin, double *fout)
+{
+    double Q[ORC_NVAR_POWELL];
+    double feq[ORC_NVAR_POWELL][ORC_QMAX];
+    double S[ORC_NVAR_POWELL];
+    for (int k = 0; k < ORC_NVAR_POWELL; ++k) {
+        Q[k] = 0.0;
+        for (int i = 0; i < L->q; ++i) Q[k] += fin[k * L->q + i]; /* Eq. 4 */
+    }
+    powell_feq(L, gamma, Q, feq);
+    orc_powell_source(tau_m, Q, S);
+    for (int k = 0; k < ORC_NVAR_POWELL; ++k)
+        for (int i = 0; i < L->q; ++i) {
+            double f = fin[k * L->q + i];
+            double sk = S[k] + (src ? src[k] : 0.0);
+            fout[k * L->q + i] = f + (feq[k][i] - f) / tau[k] + L->w[i] * sk;
+        }
+}
+
+int orc_powell_collide_cell(int dim, double gamma, const double *tau, double tau_m, const double *src,
+                            const double *fin, double *fout)
+{
+    orc_lattice L;
+    if (dim != 2 && dim != 3) return -1;
+    ideal_lattice(dim, &L);
+    powell_collide(&L, gamma, tau, tau_m, src, fin, fout);
+    return 0;
+}
+
+int orc_powell_init(int dim, int nx, int ny, int nz, double gamma, const double *Q0, double *f)
+{
+    orc_lattice L;
+    if (check_dims(dim, nx, ny, nz)) return -1;
+    ideal_lattice(dim, &L);
+    long N = (long)nx * ny * nz;
+    for (long cell = 0; cell < N; ++cell) {
+        double Q[ORC_NVAR_POWELL];
+        double feq[ORC_NVAR_POWELL][ORC_QMAX];
+        for (int k = 0; k < ORC_NVAR_POWELL; ++k) Q[k] = Q0[k * N + cell];
+        powell_feq(&L, gamma, Q, feq);
+        for (int k = 0; k < ORC_NVAR_POWELL; ++k)
+            for (int i = 0; i < L.q; ++i) f[(long)(k * L.q + i) * N + cell] = feq[k][i];
+    }
+    return 0;
+}
+
+int orc_powell_step(int dim, int nx, int ny, int nz, double gamma, const double *tau, double tau_m,
+                    const double *src, const double *fin, double *fout, int nthreads)
+{
+    orc_lattice L;
+    if (check_dims(dim, nx, ny, nz) || !(tau_m > 0.0)) return -1;
+    ideal_lattice(dim, &L);
+    const long N = (long)nx * ny * nz;
+    const int q = L.q;
+    if (nthreads < 1) nthreads = 1;
+#pragma omp parallel for num_threads(nthreads) schedule(static)
+    for (long cell = 0; cell < N; ++cell) {
+        int x = (int)(cell % nx);
+        int y = (int)((cell / nx) % ny);
+        int z = (int)(cell / ((long)nx * ny));
+        double fc[ORC_NVAR_POWELL * ORC_QMAX];
+        double fs[ORC_NVAR_POWELL * ORC_QMAX];
+        for (int k = 0; k < ORC_NVAR_POWELL; ++k)
+            for (int i = 0; i < q; ++i) fc[k * q + i] = fin[(long)(k * q + i) * N + cell];
+        powell_collide(&L, gamma, tau, tau_m, src, fc, fs);
+        for (int i = 0; i < q; ++i) {
+            long to = neighbour(x, y, z, L.c[i], nx, ny, nz); /* push along c_i */
+            for (int k = 0; k < ORC_NVAR_POWELL; ++k)
+                fout[(long)(k * q + i) * N + to] = fs[k * q + i];
+        }
+    }
+    return 0;
+}
+
+int orc_powell_moments(int dim, int nx, int ny, int nz, const double *f, double *Q)
+{
+    orc_lattice L;
+    if (check_dims(dim, nx, ny, nz)) return -1;
+    ideal_lattice(dim, &L);
+    long N = (long)nx * ny * nz;
+    for (int k = 0; k < ORC_NVAR_POWELL; ++k)
+        for (long cell = 0; cell < N; ++cell) {
+            double s = 0.0;
+            for (int i = 0; i < L.q; ++i) s += f[(long)(k * L.q + i) * N + cell];
+            Q[k * N + cell] = s;
+        }
+    return 0;
+}
+
+int orc_powell_run(int dim, int nx, int ny, int nz, double gamma, const double *tau, double tau_m,
+                   const double *src, const double *Q0, int nsteps, double *Qout, int nthreads)
+{
+    if (check_dims(dim, nx, ny, nz) || nsteps < 0 || !(tau_m > 0.0)) return -1;
+    int q = dim == 2 ? 5 : 7;
+    long N = (long)nx * ny * nz;
+    double *a = (double *)malloc(sizeof(double) * ORC_NVAR_POWELL * q * N);
+    double *b = (double *)malloc(sizeof(double) * ORC_NVAR_POWELL * q * N);
+    if (!a || !b) {
+        free(a);
+        free(b);
+        return -2;
+    }
+    orc_powell_init(dim, nx, ny, nz, gamma, Q0, a);
+    for (int s = 0; s < nsteps; ++s) {
+        orc_powell_step(dim, nx, ny, nz, gamma, tau, tau_m, src, a, b, nthreads);
+        double *t = a;
+        a = b;
+        b = t;
+    }
+    orc_powell_moments(dim, nx, ny, nz, a, Qout);
     free(a);
     free(b);
     return 0;

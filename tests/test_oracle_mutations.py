@@ -9,6 +9,7 @@ import pytest
 
 import oracle
 import test_oracle_pins as P
+import test_oracle_powell as W
 import test_oracle_resistive as R
 
 IDEAL_PINS = [
@@ -30,6 +31,16 @@ RES_PINS = [
     lambda o: R.test_magnetic_diffusion_gives_eta(o),
     lambda o: R.test_poiseuille_profile(o),
     lambda o: R.test_hartmann_profile(o, 5.0),
+]
+
+POWELL_PINS = [
+    lambda o: W.test_trace_flux_is_the_trace_of_the_gradient_tensor_flux(),
+    lambda o: W.test_solenoidal_field_keeps_D_zero_and_matches_the_ideal_scheme((6, 8, 10)),
+    lambda o: W.test_D_relaxes_to_tau_m_times_the_divergence(),
+    lambda o: W.test_powell_source_cancels_the_monopole_force(),
+    lambda o: W.test_mass_is_conserved_exactly(),
+    lambda o: W.test_uniform_state_D_decays_geometrically_and_first_step_momentum(),
+    lambda o: W.test_one_uniform_step_moves_every_field_by_the_divergence_times_its_factor(),
 ]
 
 # (name, original text, planted mistake, which pin family must catch it)
@@ -63,6 +74,23 @@ MUTANTS = [
      "for (int a = 0; a < 3; ++a) phi[a] = u[b] * B[a] - B[b] * u[a];", RES_PINS),
     ("Maxwell stress missing in flow", "(a == b ? 0.5 * B2 : 0.0) - B[a] * B[b];",
      "(a == b ? 0.5 * B2 : 0.0);", RES_PINS),
+    ("trace flux adds B", "phi[3 * 8 + a] = Q[8] * (Q[1 + a] / rho) - Q[5 + a];",
+     "phi[3 * 8 + a] = Q[8] * (Q[1 + a] / rho) + Q[5 + a];", POWELL_PINS),
+    ("trace flux misses D u", "phi[3 * 8 + a] = Q[8] * (Q[1 + a] / rho) - Q[5 + a];",
+     "phi[3 * 8 + a] = -Q[5 + a];", POWELL_PINS),
+    ("divergence scaled by tau_M", "double divB = Q[8] / tau_m;", "double divB = Q[8] * tau_m;",
+     POWELL_PINS),
+    ("momentum source along u", "S[1 + b] = -divB * B[b];", "S[1 + b] = -divB * u[b];", POWELL_PINS),
+    ("induction source along B", "S[5 + b] = -divB * u[b];", "S[5 + b] = -divB * B[b];", POWELL_PINS),
+    ("energy source sign", "S[4] = -divB * uB;", "S[4] = divB * uB;", POWELL_PINS),
+    ("mass source", "S[0] = 0.0;", "S[0] = -divB;", POWELL_PINS),
+    ("trace relaxation sign", "S[8] = -Q[8] / tau_m;", "S[8] = Q[8] / tau_m;", POWELL_PINS),
+    ("Powell step streams against c_i", "long to = neighbour(x, y, z, L.c[i], nx, ny, nz);",
+     "long to = neighbour(x, y, z, L.c[L.opp[i]], nx, ny, nz);", POWELL_PINS),
+    ("Powell equilibrium drops 1/cs^2", "double moving = cphi / L->cs2;", "double moving = cphi;",
+     POWELL_PINS),
+    ("Powell source without weight", "fout[k * L->q + i] = f + (feq[k][i] - f) / tau[k] + L->w[i] * sk;",
+     "fout[k * L->q + i] = f + (feq[k][i] - f) / tau[k] + sk;", POWELL_PINS),
 ]
 
 
