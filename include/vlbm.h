@@ -72,7 +72,13 @@ typedef enum {
     VLBM_ERR_UNSUPPORTED = 8   /* combination of options not built */
 } vlbm_status;
 
-typedef enum { VLBM_IDEAL = 0, VLBM_RESISTIVE = 1 } vlbm_model;
+/* VLBM_IDEAL_POWELL: ideal MHD with Powell's source S = -(div B)(0, B, u.B, u)
+ * (sec. 2.3, "Powell correction"), div B taken locally from a ninth lattice
+ * that carries D, the trace of the gradient tensor of the local moments
+ * evolution (sec. 2.2.1; flux D u - B, relaxation source -D / tau_m), as
+ * div B = D / tau_m.  Nine fields: the eight of VLBM_IDEAL, then D.  Built
+ * for F64 and F32 storage, single domains. */
+typedef enum { VLBM_IDEAL = 0, VLBM_RESISTIVE = 1, VLBM_IDEAL_POWELL = 2 } vlbm_model;
 
 /* Population storage.  F64: double storage and arithmetic.  F32: float
  * storage and arithmetic.  F16_DEV / BF16_DEV: populations stored as
@@ -105,11 +111,15 @@ typedef struct {
     vlbm_alloc_fn alloc;  /* device allocator hook, or NULL for cudaMalloc */
     vlbm_free_fn dealloc; /* matching release hook */
     void *alloc_user;     /* passed back to the hooks */
+    double tau_d;         /* Powell model: BGK relaxation time of the D lattice, > 1/2 */
+    double tau_m;         /* Powell model: relaxation time of D in time steps (source
+                             -D / tau_m; div B = D / tau_m), > 1/2 */
 } vlbm_params;
 
 /* Fill *p with defaults: ideal MHD, dim 3, 64^3 cells, F32 storage,
  * gamma = 5/3, tau = 0.51 on every lattice (the paper's showcase value,
- * sec. 5 table), no source, no walls, check_every = 0, NULL hooks. */
+ * sec. 5 table), no source, no walls, check_every = 0, NULL hooks;
+ * Powell model: tau_d = 0.51, tau_m = 1. */
 void vlbm_default_params(vlbm_params *p);
 
 /* Create a context for one domain: validates p (dims > 0, dim 2 => nz = 1,
@@ -165,7 +175,9 @@ vlbm_status vlbm_gather_populations(vlbm_ctx *ctx, int domain, const int64_t *ce
 /* Domain sums of the conserved fields, sum_x Q_k(x), accumulated in
  * double precision from the stored populations (fixed reduction order:
  * repeated calls on the same state return identical values), into
- * sums[nvar] on the host.  Also refreshes the health status.  Synchronises. */
+ * sums[min(nvar, 8)] on the host (the Powell model: the eight MHD fields;
+ * D is not a conserved field).  Also refreshes the health status.
+ * Synchronises. */
 vlbm_status vlbm_conservation(vlbm_ctx *ctx, int domain, double *sums);
 
 /* Domain sums of the eight ideal-MHD fields, like vlbm_conservation, for a
@@ -297,7 +309,7 @@ int vlbm_tile_shapes(const vlbm_ctx *ctx);
 vlbm_status vlbm_set_tile_shape(vlbm_ctx *ctx, int shape);
 
 /* Small queries. */
-int vlbm_nvar(const vlbm_ctx *ctx);                  /* 8 ideal, 7 resistive */
+int vlbm_nvar(const vlbm_ctx *ctx);                  /* 8 ideal, 7 resistive, 9 Powell */
 int vlbm_slots_per_cell(const vlbm_ctx *ctx);        /* populations per cell: 40, 56 or 40 (D3Q19 + 3 x D3Q7) */
 int vlbm_num_domains(const vlbm_ctx *ctx);
 int64_t vlbm_num_cells(const vlbm_ctx *ctx, int domain);

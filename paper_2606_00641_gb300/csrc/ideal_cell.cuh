@@ -80,4 +80,80 @@ __device__ __forceinline__ void ideal_collide(C (&f)[8][AxisSet<D>::Q], const C 
     }
 }
 
+// Ideal MHD with Powell's source (sec. 2.3, "Powell correction") on nine
+// lattices: the eight of ideal_collide plus D, the trace of the gradient
+// tensor of the local moments evolution (sec. 2.2.1), with flux D u - B.
+// div B = D / tau_M; the source S = -(div B)(0, B, u.B, u) for the eight MHD
+// lattices and -D / tau_M for D is injected directly, f* += w_i S_k, on top
+// of the uniform source src0/src1.  Plain storage only (no deviations).
+template <int D, class C>
+__device__ __forceinline__ void powell_collide(C (&f)[9][AxisSet<D>::Q], const C gm1, const C *omega,
+                                               const C *src0, const C *src1, const C inv_tau_m, unsigned *flags)
+{
+    constexpr int Q = AxisSet<D>::Q;
+    C q[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        C s = f[k][0];
+#pragma unroll
+        for (int i = 1; i < Q; ++i) s += f[k][i];
+        q[k] = s;
+    }
+    const C rho = q[0];
+    const C ir = C(1) / rho;
+    const C m[3] = {q[1], q[2], q[3]};
+    const C u[3] = {m[0] * ir, m[1] * ir, m[2] * ir};
+    const C E = q[4];
+    const C B[3] = {q[5], q[6], q[7]};
+    const C Dv = q[8];
+    const C B2 = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
+    const C mu = m[0] * u[0] + m[1] * u[1] + m[2] * u[2];
+    const C uB = u[0] * B[0] + u[1] * B[1] + u[2] * B[2];
+    const C p = gm1 * (E - C(0.5) * mu - C(0.5) * B2);
+    const C pt = p + C(0.5) * B2;
+    if (!(rho > C(0)) || !(p > C(0))) atomicOr(flags, kFlagNonPhysical);
+    const C Ept = E + pt;
+
+    C phi[9][D];
+#pragma unroll
+    for (int ax = 0; ax < D; ++ax) {
+        phi[0][ax] = m[ax];
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            phi[1 + b][ax] = m[ax] * u[b] - B[ax] * B[b] + (ax == b ? pt : C(0));
+            phi[5 + b][ax] = (ax == b) ? C(0) : u[ax] * B[b] - B[ax] * u[b];
+        }
+        phi[4][ax] = Ept * u[ax] - B[ax] * uB;
+        phi[8][ax] = Dv * u[ax] - B[ax];
+    }
+    // state-dependent source: S_k = -div B * (0, B, u.B, u), S_D = -D / tau_M = -div B
+    const C ndiv = -Dv * inv_tau_m;
+    C S[9];
+    S[0] = C(0);
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        S[1 + b] = ndiv * B[b];
+        S[5 + b] = ndiv * u[b];
+    }
+    S[4] = ndiv * uB;
+    S[8] = ndiv;
+
+    constexpr C w0 = C(AxisSet<D>::w0), w1 = C(AxisSet<D>::w1);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const C om = omega[k];
+        const C omc = C(1) - om;
+        const C A0 = om * w0 * q[k] + src0[k] + w0 * S[k];
+        const C A1 = om * w1 * q[k] + src1[k] + w1 * S[k];
+        const C hom = C(0.5) * om;  // omega * w_moving / cs^2
+        f[k][0] = omc * f[k][0] + A0;
+#pragma unroll
+        for (int ax = 0; ax < D; ++ax) {
+            const C bv = hom * phi[k][ax];
+            f[k][2 * ax + 1] = omc * f[k][2 * ax + 1] + A1 + bv;
+            f[k][2 * ax + 2] = omc * f[k][2 * ax + 2] + A1 - bv;
+        }
+    }
+}
+
 }  // namespace vlbm

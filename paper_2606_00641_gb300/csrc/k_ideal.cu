@@ -33,6 +33,7 @@ template <class C> struct IdealArgs {
     C inv_scale[kMaxLat]; //                    1 / s_k
     unsigned *flags;
     const float *dphi;    // closure: per-cell flux correction [cell][24], or null
+    C inv_tau_m;          // Powell model: 1 / tau_M (div B = D / tau_M)
 };
 
 // Linear indices of the cell's neighbours x + c_i (periodic), i in set order.
@@ -58,7 +59,8 @@ __device__ __forceinline__ void neighbours(int x, int y, int z, int nx, int ny, 
 // The fused collide-and-stream step.  ODD selects the AA parity; CORR adds
 // the learned flux correction dPhi[k][a] to the post-collision populations
 // (f*_{k,+a} += dPhi/2, f*_{k,-a} -= dPhi/2: zero mass, first moment dPhi).
-template <int D, class S, class C, bool ODD, bool CORR = false>
+// NL = 9 is the Powell model (eight MHD lattices and the divergence lattice).
+template <int D, class S, class C, bool ODD, bool CORR = false, int NL = 8>
 __global__ void __launch_bounds__(kBlockX) k_ideal_step(const IdealArgs<C> a)
 {
     constexpr int Q = AxisSet<D>::Q;
@@ -71,9 +73,9 @@ __global__ void __launch_bounds__(kBlockX) k_ideal_step(const IdealArgs<C> a)
     S *pop = static_cast<S *>(a.pop);
 
     // load: even parity reads slot (i, x); odd parity reads slot (opp i, x - c_i)
-    C f[8][Q];
+    C f[NL][Q];
 #pragma unroll
-    for (int k = 0; k < 8; ++k)
+    for (int k = 0; k < NL; ++k)
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const int j = ODD ? opp_axis(i) : i;
@@ -81,9 +83,13 @@ __global__ void __launch_bounds__(kBlockX) k_ideal_step(const IdealArgs<C> a)
             f[k][i] = Codec<S>::load(pop + (int64_t)(k * Q + j) * a.stride + at);
         }
 
-    // deviation storage collides on the stored deviations directly (ideal_cell.cuh)
-    ideal_collide<D, C, Codec<S>::kDev>(f, a.gm1, a.omega, a.src0, a.src1, a.flags, a.ref, a.scale,
-                                        a.inv_scale);
+    if constexpr (NL == 9) {
+        powell_collide<D, C>(f, a.gm1, a.omega, a.src0, a.src1, a.inv_tau_m, a.flags);
+    } else {
+        // deviation storage collides on the stored deviations directly (ideal_cell.cuh)
+        ideal_collide<D, C, Codec<S>::kDev>(f, a.gm1, a.omega, a.src0, a.src1, a.flags, a.ref, a.scale,
+                                            a.inv_scale);
+    }
     if constexpr (CORR) {
         const float *dp = a.dphi + cell * 24;
 #pragma unroll
@@ -99,7 +105,7 @@ __global__ void __launch_bounds__(kBlockX) k_ideal_step(const IdealArgs<C> a)
     // store: even parity sends direction i to slot (opp i, x);
     //        odd parity sends direction i to slot (i, x + c_i)
 #pragma unroll
-    for (int k = 0; k < 8; ++k)
+    for (int k = 0; k < NL; ++k)
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const int j = ODD ? i : opp_axis(i);
@@ -262,7 +268,7 @@ template <int D, class S> struct InitArgs {
     unsigned *flags;
 };
 
-template <int D, class S>
+template <int D, class S, int NL = 8>
 __global__ void k_ideal_init(const InitArgs<D, S> a, const double *__restrict__ Qin)
 {
     using R = typename ComputeOf<S>::T;
@@ -308,6 +314,20 @@ __global__ void k_ideal_init(const InitArgs<D, S> a, const double *__restrict__ 
             R v = feq;
             if (Codec<S>::kDev) v = (feq - w * ref) * inv_scale;
             Codec<S>::store(pop + (int64_t)(k * Q + i) * a.stride + cell, (decltype(Codec<S>::load(pop)))v);
+        }
+    }
+    if constexpr (NL == 9) {  // Powell model: D lattice, flux D u - B (plain storage)
+        const R Dv = (R)Qin[8 * a.qstride + t];
+        R phi[D];
+#pragma unroll
+        for (int ax = 0; ax < D; ++ax) phi[ax] = Dv * u[ax] - B[ax];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const R w = (R)(i == 0 ? AxisSet<D>::w0 : AxisSet<D>::w1);
+            R cphi = R(0);
+            if (i > 0) cphi = ((i & 1) ? R(1) : R(-1)) * phi[(i - 1) / 2];
+            Codec<S>::store(pop + (int64_t)(8 * Q + i) * a.stride + cell,
+                            (decltype(Codec<S>::load(pop)))(w * (Dv + cphi * (R)inv_cs2)));
         }
     }
 }
@@ -372,7 +392,7 @@ __device__ __forceinline__ void cell_xyz(int64_t cell, int nx, int ny, int &x, i
     z = (int)(r / ny);
 }
 
-template <int D, class S>
+template <int D, class S, int NL = 8>
 __global__ void k_ideal_moments(const ReadArgs<D, S> a, int64_t c0, int64_t count, int64_t ostride,
                                 double *__restrict__ out)
 {
@@ -385,7 +405,7 @@ __global__ void k_ideal_moments(const ReadArgs<D, S> a, int64_t c0, int64_t coun
     int64_t nb[Q];
     neighbours<D>(x, y, z, a.nx, a.ny, a.nz, cell, nb);
 #pragma unroll
-    for (int k = 0; k < 8; ++k) out[k * ostride + t] = (double)cell_moment<D, S>(a, cell, nb, k);
+    for (int k = 0; k < NL; ++k) out[k * ostride + t] = (double)cell_moment<D, S>(a, cell, nb, k);
 }
 
 // Closure input features from the populations: the FP32 moments of
@@ -412,7 +432,7 @@ __global__ void k_ideal_features(const ReadArgs<D, S> a, int64_t count, const Fe
     *reinterpret_cast<uint4 *>(x + cell * 8) = *reinterpret_cast<const uint4 *>(v);
 }
 
-template <int D, class S>
+template <int D, class S, int NL = 8>
 __global__ void k_ideal_gather(const ReadArgs<D, S> a, const int64_t *__restrict__ cells, int n,
                                double *__restrict__ out)
 {
@@ -425,9 +445,9 @@ __global__ void k_ideal_gather(const ReadArgs<D, S> a, const int64_t *__restrict
     int64_t nb[Q];
     neighbours<D>(x, y, z, a.nx, a.ny, a.nz, cell, nb);
 #pragma unroll
-    for (int k = 0; k < 8; ++k)
+    for (int k = 0; k < NL; ++k)
 #pragma unroll
-        for (int i = 0; i < Q; ++i) out[(int64_t)t * 8 * Q + k * Q + i] = logical<D, S>(a, cell, nb, k, i);
+        for (int i = 0; i < Q; ++i) out[(int64_t)t * NL * Q + k * Q + i] = logical<D, S>(a, cell, nb, k, i);
 }
 
 // Domain sums of Q_k: each thread accumulates its cells in double, warps and
@@ -512,6 +532,7 @@ template <class C> IdealArgs<C> make_step_args(vlbm_ctx *c)
         a.inv_scale[k] = C(1.0 / s);
     }
     a.flags = c->d_flags;
+    a.inv_tau_m = C(1.0 / d.tau_m);
     return a;
 }
 
@@ -539,6 +560,16 @@ template <int D, class S, class C> vlbm_status step_t(vlbm_ctx *c, int parity)
     const Domain &d = c->dom[0];
     const IdealArgs<C> a = make_step_args<C>(c);
     const dim3 grid((unsigned)((d.nx + kBlockX - 1) / kBlockX), (unsigned)d.ny, (unsigned)d.nz);
+    if constexpr (!Codec<S>::kDev) {
+        if (c->nlat == 9) {  // Powell model
+            if (parity)
+                k_ideal_step<D, S, C, true, false, 9><<<grid, kBlockX, 0, c->stream>>>(a);
+            else
+                k_ideal_step<D, S, C, false, false, 9><<<grid, kBlockX, 0, c->stream>>>(a);
+            c->launches++;
+            return cuda_check(c, cudaGetLastError(), "Powell step launch");
+        }
+    }
     if constexpr (D == 3 && Codec<S>::kDev) {
         if (d.nx % 8 == 0) {  // 16-byte aligned rows: bulk-copy loads, persistent CTAs
             if (c->bulk_ctas == 0) {  // every SM filled to the kernel's occupancy
@@ -583,7 +614,15 @@ template <int D, class S> vlbm_status init_t(vlbm_ctx *c, int di, const double *
     }
     a.flags = c->d_flags;
     const int threads = 256;
-    k_ideal_init<D, S><<<(unsigned)((count + threads - 1) / threads), threads, 0, c->stream>>>(a, Q);
+    const unsigned blocks = (unsigned)((count + threads - 1) / threads);
+    if constexpr (!Codec<S>::kDev) {
+        if (c->nlat == 9) {
+            k_ideal_init<D, S, 9><<<blocks, threads, 0, c->stream>>>(a, Q);
+            c->launches++;
+            return cuda_check(c, cudaGetLastError(), "Powell init launch");
+        }
+    }
+    k_ideal_init<D, S><<<blocks, threads, 0, c->stream>>>(a, Q);
     c->launches++;
     return cuda_check(c, cudaGetLastError(), "ideal init launch");
 }
@@ -592,8 +631,12 @@ template <int D, class S> vlbm_status moments_t(vlbm_ctx *c, int di, double *out
                                                 int64_t ostride)
 {
     const int threads = 256;
-    k_ideal_moments<D, S><<<(unsigned)((count + threads - 1) / threads), threads, 0, c->stream>>>(
-        make_read_args<D, S>(c, di), c0, count, ostride, out);
+    const unsigned blocks = (unsigned)((count + threads - 1) / threads);
+    if (c->nlat == 9)
+        k_ideal_moments<D, S, 9><<<blocks, threads, 0, c->stream>>>(make_read_args<D, S>(c, di), c0, count, ostride,
+                                                                   out);
+    else
+        k_ideal_moments<D, S><<<blocks, threads, 0, c->stream>>>(make_read_args<D, S>(c, di), c0, count, ostride, out);
     c->launches++;
     return cuda_check(c, cudaGetLastError(), "ideal moments launch");
 }
@@ -601,8 +644,11 @@ template <int D, class S> vlbm_status moments_t(vlbm_ctx *c, int di, double *out
 template <int D, class S> vlbm_status gather_t(vlbm_ctx *c, int di, const int64_t *cells, int n, double *out)
 {
     const int threads = 128;
-    k_ideal_gather<D, S><<<(unsigned)((n + threads - 1) / threads), threads, 0, c->stream>>>(
-        make_read_args<D, S>(c, di), cells, n, out);
+    const unsigned blocks = (unsigned)((n + threads - 1) / threads);
+    if (c->nlat == 9)
+        k_ideal_gather<D, S, 9><<<blocks, threads, 0, c->stream>>>(make_read_args<D, S>(c, di), cells, n, out);
+    else
+        k_ideal_gather<D, S><<<blocks, threads, 0, c->stream>>>(make_read_args<D, S>(c, di), cells, n, out);
     c->launches++;
     return cuda_check(c, cudaGetLastError(), "ideal gather launch");
 }

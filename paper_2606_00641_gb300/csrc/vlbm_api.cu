@@ -59,8 +59,8 @@ void dev_free_all(vlbm_ctx *c)
 vlbm_status validate(const vlbm_params *p, bool batch_member)
 {
     if (!p) return VLBM_ERR_ARG;
-    if (p->model != VLBM_IDEAL && p->model != VLBM_RESISTIVE) {
-        g_err = "model must be VLBM_IDEAL or VLBM_RESISTIVE";
+    if (p->model != VLBM_IDEAL && p->model != VLBM_RESISTIVE && p->model != VLBM_IDEAL_POWELL) {
+        g_err = "model must be VLBM_IDEAL, VLBM_RESISTIVE or VLBM_IDEAL_POWELL";
         return VLBM_ERR_ARG;
     }
     if (p->dim != 2 && p->dim != 3) {
@@ -76,13 +76,23 @@ vlbm_status validate(const vlbm_params *p, bool batch_member)
         g_err = "unknown storage";
         return VLBM_ERR_ARG;
     }
-    const int nt = p->model == VLBM_IDEAL ? 8 : 4;
+    const int nt = p->model == VLBM_RESISTIVE ? 4 : 8;
     for (int k = 0; k < nt; ++k)
         if (!(p->tau[k] > 0.5) || !(p->tau[k] < 1e6)) {
             g_err = "tau must be > 1/2 on every lattice";
             return VLBM_ERR_UNSTABLE;
         }
-    if (p->model == VLBM_IDEAL) {
+    if (p->model == VLBM_IDEAL_POWELL) {
+        if (!(p->tau_d > 0.5) || !(p->tau_d < 1e6) || !(p->tau_m > 0.5) || !(p->tau_m < 1e12)) {
+            g_err = "Powell model: tau_d and tau_m must be > 1/2";
+            return VLBM_ERR_UNSTABLE;
+        }
+        if (p->storage != VLBM_F32 && p->storage != VLBM_F64) {
+            g_err = "the Powell model is built for F32 and F64 storage";
+            return VLBM_ERR_UNSUPPORTED;
+        }
+    }
+    if (p->model == VLBM_IDEAL || p->model == VLBM_IDEAL_POWELL) {
         if (!(p->gamma > 1.0)) {
             g_err = "gamma must be > 1";
             return VLBM_ERR_ARG;
@@ -123,12 +133,18 @@ Domain make_domain(const vlbm_params *p)
     d.ncell = (int64_t)p->nx * p->ny * p->nz;
     d.stride = round_up(d.ncell, 64);
     d.gamma = p->gamma;
-    for (int k = 0; k < kMaxLat; ++k) {
+    for (int k = 0; k < 8; ++k) {  // the public arrays hold 8 lattices
         d.tau[k] = p->tau[k] > 0.5 ? p->tau[k] : 1.0;
         d.source[k] = p->source[k];
         d.q_ref[k] = p->q_ref[k];
         d.q_scale[k] = p->q_scale[k] > 0.0 ? p->q_scale[k] : 1.0;
     }
+    // ninth lattice (Powell model): D, no uniform source, no deviation storage
+    d.tau[8] = p->tau_d > 0.5 ? p->tau_d : 1.0;
+    d.source[8] = 0.0;
+    d.q_ref[8] = 0.0;
+    d.q_scale[8] = 1.0;
+    d.tau_m = p->tau_m > 0.5 ? p->tau_m : 1.0;
     for (int a = 0; a < 3; ++a) {
         d.force[a] = p->force[a];
         d.b_wall[a] = p->b_wall[a];
@@ -272,11 +288,11 @@ vlbm_status create_common(const vlbm_params *p, int count, vlbm_ctx **out)
     c->storage = p[0].storage;
     c->elem = elem_size(c->storage);
     c->batched = count > 1;
-    if (c->model == VLBM_IDEAL) {
+    if (c->model == VLBM_IDEAL || c->model == VLBM_IDEAL_POWELL) {
         c->q = c->dim == 2 ? 5 : 7;
-        c->nlat = 8;
-        c->nvar = 8;
-        c->nslot = 8 * c->q;
+        c->nlat = c->model == VLBM_IDEAL_POWELL ? 9 : 8;
+        c->nvar = c->nlat;
+        c->nslot = c->nlat * c->q;
     } else {
         c->q = 19;
         c->nlat = 4;
@@ -359,6 +375,8 @@ void vlbm_default_params(vlbm_params *p)
         p->tau[k] = 0.51;
         p->q_scale[k] = 1.0;
     }
+    p->tau_d = 0.51;
+    p->tau_m = 1.0;
 }
 
 vlbm_status vlbm_create(const vlbm_params *p, vlbm_ctx **out) { return create_common(p, 1, out); }
@@ -560,7 +578,7 @@ vlbm_status vlbm_conservation(vlbm_ctx *c, int domain, double *sums)
     vlbm_status s = c->model == VLBM_RESISTIVE ? resistive_sums(c, domain, c->d_sums)
                                                : ideal_sums(c, domain, c->d_sums);
     if (s == VLBM_OK)
-        s = cuda_check(c, cudaMemcpyAsync(sums, c->d_sums, c->nvar * sizeof(double), cudaMemcpyDeviceToHost,
+        s = cuda_check(c, cudaMemcpyAsync(sums, c->d_sums, std::min(c->nvar, 8) * sizeof(double), cudaMemcpyDeviceToHost,
                                           c->stream),
                        "sums download");
     if (s != VLBM_OK) return s;

@@ -31,7 +31,7 @@
 
 namespace vlbm {
 
-constexpr int kMaxLat = 8;
+constexpr int kMaxLat = 9;  // lattices of one model: ideal 8, Powell 9 (resistive 4)
 constexpr int kBlockX = 128;     // threads per CTA along x for the step kernels
 constexpr int kReduceBlocks = 1216;  // 8 CTAs per SM on 152 SMs
 constexpr int kReduceThreads = 256;
@@ -113,6 +113,7 @@ struct Domain {
     double force[3];
     double b_wall[3];
     int walls_y;
+    double tau_m;          // Powell model: relaxation time of D (steps)
 };
 
 }  // namespace vlbm

@@ -32,6 +32,7 @@ VLBM_ERR_UNSUPPORTED = 8
 
 VLBM_IDEAL = 0
 VLBM_RESISTIVE = 1
+VLBM_IDEAL_POWELL = 2
 
 VLBM_F64 = 0
 VLBM_F32 = 1
@@ -65,6 +66,8 @@ class vlbm_params(ctypes.Structure):
         ("alloc", ALLOC_FN),
         ("dealloc", FREE_FN),
         ("alloc_user", ctypes.c_void_p),
+        ("tau_d", ctypes.c_double),
+        ("tau_m", ctypes.c_double),
     ]
 
 
@@ -181,8 +184,13 @@ def vlbm_default_params() -> vlbm_params:
 def make_params(model: int = VLBM_IDEAL, shape=(64, 64, 64), storage="f32", gamma=5.0 / 3.0,
                 tau=0.51, source=None, force=(0.0, 0.0, 0.0), b_wall=(0.0, 0.0, 0.0),
                 walls_y: bool = False, check_every: int = 0, q_ref=None, q_scale=None,
-                stream: Optional[int] = None, hooks=None) -> vlbm_params:
-    """Parameters for one domain; ``shape`` is (ny, nx) in 2-D, (nz, ny, nx) in 3-D."""
+                stream: Optional[int] = None, hooks=None, tau_d: float = 0.51,
+                tau_m: float = 1.0) -> vlbm_params:
+    """Parameters for one domain; ``shape`` is (ny, nx) in 2-D, (nz, ny, nx) in 3-D.
+
+    ``tau_d`` / ``tau_m`` apply to the Powell model (VLBM_IDEAL_POWELL): the BGK
+    time of the divergence lattice and the relaxation time of D (div B = D / tau_m).
+    """
     p = vlbm_default_params()
     p.model = int(model)
     shape = tuple(int(n) for n in shape)
@@ -204,6 +212,8 @@ def make_params(model: int = VLBM_IDEAL, shape=(64, 64, 64), storage="f32", gamm
         p.b_wall[a] = float(b_wall[a])
     p.walls_y = int(bool(walls_y))
     p.check_every = int(check_every)
+    p.tau_d = float(tau_d)
+    p.tau_m = float(tau_m)
     p.stream = stream if stream else None
     if hooks is not None:
         p.alloc, p.dealloc, p.alloc_user = hooks.alloc, hooks.dealloc, None
@@ -337,7 +347,8 @@ def vlbm_gather_populations(ctx: int, domain: int, cells) -> np.ndarray:
 
 
 def vlbm_conservation(ctx: int, domain: int = 0) -> np.ndarray:
-    out = np.zeros(vlbm_nvar(ctx), dtype=np.float64)
+    """Domain sums of the conserved fields (the eight MHD fields for the Powell model)."""
+    out = np.zeros(min(vlbm_nvar(ctx), 8), dtype=np.float64)
     _check(load().vlbm_conservation(ctx, domain, out.ctypes.data_as(ctypes.c_void_p)), "vlbm_conservation", ctx)
     return out
 
