@@ -76,6 +76,12 @@ def _configure(L):
     L.orc_powell_step.argtypes = [i, i, i, i, d, p, d, p, p, p, i]
     L.orc_powell_moments.argtypes = [i, i, i, i, p, p]
     L.orc_powell_run.argtypes = [i, i, i, i, d, p, d, p, p, i, p, i]
+    L.orc_hlbm_porosity.argtypes = [d, d]
+    L.orc_hlbm_porosity.restype = ctypes.c_double
+    L.orc_hlbm_target.argtypes = [d, p, d, p, p, p]
+    L.orc_hlbm_target.restype = None
+    L.orc_hlbm_step.argtypes = [i, i, i, i, d, p, p, p, p, p, i]
+    L.orc_hlbm_run.argtypes = [i, i, i, i, d, p, p, p, p, i, p, i]
     return L
 
 
@@ -294,6 +300,51 @@ def powell_run(Q0: np.ndarray, gamma: float, tau, tau_m: float, nsteps: int, src
     _check(lib().orc_powell_run(dim, nx, ny, nz, gamma, _ptr(_tau9(tau)), tau_m,
                                 _ptr(s) if s is not None else None, _ptr(Q0), nsteps, _ptr(out),
                                 nthreads), "powell_run")
+    return out
+
+
+# ---- homogenised solids (HLBM, sec. 2.4): porosity d, solid velocity uB and field BB per cell ----
+
+def hlbm_porosity(phi, eps_h: float) -> np.ndarray:
+    """d(phi) for an array of signed distances (positive in the fluid)."""
+    phi = np.asarray(phi, dtype=np.float64)
+    return np.vectorize(lambda v: lib().orc_hlbm_porosity(float(v), float(eps_h)), otypes=[float])(phi)
+
+
+def hlbm_target(gamma: float, Q, d: float, uB, BB) -> np.ndarray:
+    """Blended state Q_hat[8] of one cell."""
+    out = np.zeros(8)
+    lib().orc_hlbm_target(gamma, _ptr(_f64(Q)), float(d), _ptr(_f64(uB)), _ptr(_f64(BB)), _ptr(out))
+    return out
+
+
+def _solid(solid, shape):
+    solid = _f64(solid)
+    assert solid.shape == (7,) + tuple(shape)
+    return solid
+
+
+def hlbm_step(f: np.ndarray, gamma: float, tau, solid, src=None, nthreads: int = 1) -> np.ndarray:
+    """One step with homogenised solids; solid = [d, uB_x, uB_y, uB_z, BB_x, BB_y, BB_z] per cell."""
+    f = _f64(f)
+    dim, nx, ny, nz = _dims(f.shape[2:])
+    out = np.empty_like(f)
+    tau = _f64(np.broadcast_to(np.asarray(tau, dtype=np.float64), (8,)))
+    s = _f64(src) if src is not None else None
+    _check(lib().orc_hlbm_step(dim, nx, ny, nz, gamma, _ptr(tau), _ptr(s) if s is not None else None,
+                               _ptr(_solid(solid, f.shape[2:])), _ptr(f), _ptr(out), nthreads), "hlbm_step")
+    return out
+
+
+def hlbm_run(Q0: np.ndarray, gamma: float, tau, solid, nsteps: int, src=None, nthreads: int = 1) -> np.ndarray:
+    Q0 = _f64(Q0)
+    dim, nx, ny, nz = _dims(Q0.shape[1:])
+    out = np.zeros_like(Q0)
+    tau = _f64(np.broadcast_to(np.asarray(tau, dtype=np.float64), (8,)))
+    s = _f64(src) if src is not None else None
+    _check(lib().orc_hlbm_run(dim, nx, ny, nz, gamma, _ptr(tau), _ptr(s) if s is not None else None,
+                              _ptr(_solid(solid, Q0.shape[1:])), _ptr(Q0), nsteps, _ptr(out), nthreads),
+           "hlbm_run")
     return out
 
 

@@ -183,6 +183,45 @@ def powell_run(Q0: np.ndarray, gamma: float, tau, tau_m: float, nsteps: int) -> 
 
 
 # ----------------------------------------------------------------------------
+# homogenised solids (HLBM, sec. 2.4): u and B blended with the solid's by the
+# porosity d before the equilibrium; rho and the gas pressure kept
+# ----------------------------------------------------------------------------
+
+def hlbm_step(f: np.ndarray, gamma: float, tau, solid: np.ndarray, dim: int, src=None) -> np.ndarray:
+    c, w, _ = vset("D2Q5" if dim == 2 else "D3Q7")
+    Q = f.sum(axis=1)
+    rho, u, e, B, p = primitives(Q, gamma)
+    d = solid[0]
+    uh = d * u + (1.0 - d) * solid[1:4]
+    Bh = d * B + (1.0 - d) * solid[4:7]
+    Qh = np.empty_like(Q)
+    Qh[0] = rho
+    Qh[1:4] = rho * uh
+    Qh[5:8] = Bh
+    Qh[4] = p / (gamma - 1.0) + 0.5 * rho * (uh * uh).sum(0) + 0.5 * (Bh * Bh).sum(0)
+    feq = ideal_feq(Qh, gamma, dim)
+    tau = np.broadcast_to(np.asarray(tau, dtype=float), (8,))
+    shape1 = (8, 1) + (1,) * (f.ndim - 2)
+    post = f + (feq - f) / tau.reshape(shape1)
+    if src is not None:
+        s = np.asarray(src, dtype=float)
+        for i in range(len(w)):
+            post[:, i] += w[i] * s.reshape((8,) + (1,) * (f.ndim - 2))
+    out = np.empty_like(f)
+    for i in range(len(w)):
+        out[:, i] = _shift(post[:, i], c[i], dim)
+    return out
+
+
+def hlbm_run(Q0: np.ndarray, gamma: float, tau, solid: np.ndarray, nsteps: int, src=None) -> np.ndarray:
+    dim = Q0.ndim - 1
+    f = ideal_feq(Q0, gamma, dim)
+    for _ in range(nsteps):
+        f = hlbm_step(f, gamma, tau, solid, dim, src)
+    return f.sum(axis=1)
+
+
+# ----------------------------------------------------------------------------
 # resistive incompressible reading: D3Q19 flow + three D3Q7 B lattices
 # ----------------------------------------------------------------------------
 

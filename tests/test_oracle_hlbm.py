@@ -1,0 +1,119 @@
+"""Pins of the oracle's homogenised solids (HLBM, sec. 2.4 "Homogenization").
+
+The porosity d blends the cell's velocity and field with the solid's,
+u_hat = d u + (1 - d) uB and B_hat = d B + (1 - d) BB, and the equilibrium is
+taken at the blended state (rho and gas pressure kept).  Checked against: the
+porosity's closed form, the pinned ideal scheme (d = 1), closed-form
+relaxation of a uniform solid cell, exact mass conservation, and a
+force-driven channel whose no-slip planes sit at the d = 1/2 level sets.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import numpy_ref as R
+from paper_2606_00641_gb300 import fields
+
+GAMMA = 5.0 / 3.0
+
+
+def test_porosity_of_the_signed_distance():
+    # 0 in the solid, 1 in the fluid, linear across eps_h, 1/2 on the surface
+    eps = 1.5
+    phi = np.array([-3.0, -0.75, -0.5, 0.0, 0.3, 0.75, 3.0])
+    expect = [0.0, 0.0, 1.0 / 6.0, 0.5, 0.7, 1.0, 1.0]
+    np.testing.assert_allclose(oracle.hlbm_porosity(phi, eps), expect, rtol=0, atol=1e-15)
+
+
+def _solid(shape, d, uB=(0.0, 0.0, 0.0), BB=(0.0, 0.0, 0.0)):
+    s = np.zeros((7,) + tuple(shape))
+    s[0] = d
+    for a in range(3):
+        s[1 + a] = uB[a]
+        s[4 + a] = BB[a]
+    return s
+
+
+@pytest.mark.parametrize("shape", [(12, 10), (4, 6, 5)])
+def test_fluid_everywhere_is_the_ideal_scheme(shape):
+    # d = 1: the blend returns the cell's own u and B; the rebuilt energy equals e
+    f0 = fields.ideal_fields(shape, 41, mach=1.0, beta=1.0, cfl=0.2)
+    solid = _solid(shape, 1.0, (0.3, -0.1, 0.2), (0.5, 0.5, -0.5))
+    got = oracle.hlbm_run(f0.Q, f0.gamma, 0.6, solid, 10)
+    ref = oracle.ideal_run(f0.Q, f0.gamma, 0.6, 10)
+    scale = np.abs(f0.Q).reshape(8, -1).max(1)
+    assert (np.abs(got - ref).reshape(8, -1).max(1) / scale).max() < 1e-13
+
+
+def test_uniform_solid_cell_relaxes_to_the_solid_state():
+    # d = 0 on a uniform state: streaming is the identity, so each step is
+    # Q <- Q + omega (Q_hat - Q) with Q_hat carrying uB and BB: the momentum and
+    # field approach rho uB and BB as (1 - omega)^n, the density does not move
+    shape = (3, 4, 5)
+    Q0 = np.array([1.2, 0.12, -0.06, 0.03, 1.0, 0.2, -0.1, 0.05])
+    Q = np.broadcast_to(Q0.reshape(8, 1, 1, 1), (8,) + shape).copy()
+    uB, BB = np.array([0.05, 0.02, -0.04]), np.array([-0.1, 0.15, 0.0])
+    tau = np.array([0.6, 0.8, 0.8, 0.8, 0.7, 0.9, 0.9, 0.9])
+    n = 6
+    out = oracle.hlbm_run(Q, GAMMA, tau, _solid(shape, 0.0, uB, BB), n)[:, 0, 0, 0]
+    om_m, om_b = 1 / tau[1], 1 / tau[5]
+    np.testing.assert_allclose(out[0], Q0[0], rtol=1e-15)
+    np.testing.assert_allclose(out[1:4], Q0[0] * uB + (1 - om_m) ** n * (Q0[1:4] - Q0[0] * uB), rtol=1e-12)
+    np.testing.assert_allclose(out[5:8], BB + (1 - om_b) ** n * (Q0[5:8] - BB), rtol=1e-12, atol=1e-16)
+
+
+def test_mass_is_conserved_exactly():
+    shape = (10, 12)
+    f0 = fields.ideal_fields(shape, 43, mach=1.0, beta=1.0, cfl=0.2)
+    y, x = np.mgrid[0:10, 0:12]
+    phi = np.hypot(x - 6.0, y - 5.0) - 3.0
+    solid = _solid(shape, oracle.hlbm_porosity(phi, 1.0), (0.01, -0.02, 0.0), (0.05, 0.0, 0.02))
+    f = oracle.ideal_init(f0.Q, f0.gamma)
+    m0 = f.sum(axis=1)[0].sum()
+    for _ in range(12):
+        f = oracle.hlbm_step(f, f0.gamma, 0.6, solid)
+    assert abs(f.sum(axis=1)[0].sum() - m0) <= 1e-13 * m0
+
+
+def test_channel_between_homogenised_walls_is_parabolic_with_walls_at_d_half():
+    # a uniform force F along x drives gas at rest between two solid bands (uB = 0);
+    # d comes from the signed distance to the planes y = y_lo, y_hi (eps_h = 1):
+    # the steady x-velocity is the Poiseuille parabola F/(2 nu)(a^2 - (y - y_c)^2)
+    # whose zeros sit on the d = 1/2 level sets (the paper's wall position).  The
+    # momentum diffuses with nu = (tau - 1/2) c_s^2 at low Mach (D2Q5: c_s^2 = 1/3)
+    ny, nx = 40, 4
+    y_lo, y_hi = 6.3, 33.7  # walls between cells: an off-grid surface
+    y = np.arange(ny, dtype=float)[:, None] * np.ones((1, nx))
+    phi = np.minimum(y - y_lo, y_hi - y)
+    d = oracle.hlbm_porosity(phi, 1.0)
+    solid = _solid((ny, nx), d)
+    Q = np.zeros((8, ny, nx))
+    Q[0] = 1.0
+    Q[4] = 0.1 / (GAMMA - 1.0)  # p = 0.1 (sound speed 0.41 < c_s), at rest, no field
+    F = 2e-6
+    src = np.array([0.0, F, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0])
+    tau = 0.9
+    out = oracle.hlbm_run(Q, GAMMA, tau, solid, 4000, src=src)
+    ux = (out[1] / out[0])[:, 0]
+    nu = (tau - 0.5) / 3.0
+    a, yc = 0.5 * (y_hi - y_lo), 0.5 * (y_hi + y_lo)
+    yy = np.arange(ny, dtype=float)
+    inside = np.abs(yy - yc) < a - 2.0
+    expect = F / (2 * nu) * (a * a - (yy - yc) ** 2)
+    err = np.abs(ux[inside] - expect[inside]).max() / expect.max()
+    assert err < 0.05, err
+    # the fitted parabola's zeros are the d = 1/2 planes to within half a cell
+    c2, c1, c0 = np.polyfit(yy[inside], ux[inside], 2)
+    roots = np.sort(np.roots([c2, c1, c0]).real)
+    assert abs(roots[0] - y_lo) < 0.5 and abs(roots[1] - y_hi) < 0.5, roots
+
+
+@pytest.mark.parametrize("shape", [(12, 10), (4, 6, 5)])
+def test_oracle_matches_numpy_restatement(shape):
+    f0 = fields.ideal_fields(shape, 45, mach=1.0, beta=1.0, cfl=0.2)
+    rng = np.random.default_rng(3)
+    solid = np.concatenate([rng.random((1,) + shape), 0.05 * rng.normal(size=(6,) + shape)])
+    tau = [0.6, 0.55, 0.55, 0.55, 0.7, 0.6, 0.6, 0.6]
+    a = oracle.hlbm_run(f0.Q, f0.gamma, tau, solid, 15)
+    b = R.hlbm_run(f0.Q, f0.gamma, tau, solid, 15)
+    assert np.abs(a - b).max() < 1e-13 * np.abs(a).max()

@@ -8,6 +8,7 @@ import numpy as np
 import pytest
 
 import oracle
+import test_oracle_hlbm as H
 import test_oracle_pins as P
 import test_oracle_powell as W
 import test_oracle_resistive as R
@@ -41,6 +42,14 @@ POWELL_PINS = [
     lambda o: W.test_mass_is_conserved_exactly(),
     lambda o: W.test_uniform_state_D_decays_geometrically_and_first_step_momentum(),
     lambda o: W.test_one_uniform_step_moves_every_field_by_the_divergence_times_its_factor(),
+]
+
+HLBM_PINS = [
+    lambda o: H.test_porosity_of_the_signed_distance(),
+    lambda o: H.test_fluid_everywhere_is_the_ideal_scheme((4, 6, 5)),
+    lambda o: H.test_uniform_solid_cell_relaxes_to_the_solid_state(),
+    lambda o: H.test_mass_is_conserved_exactly(),
+    lambda o: H.test_channel_between_homogenised_walls_is_parabolic_with_walls_at_d_half(),
 ]
 
 # (name, original text, planted mistake, which pin family must catch it)
@@ -89,6 +98,14 @@ MUTANTS = [
      "long to = neighbour(x, y, z, L.c[L.opp[i]], nx, ny, nz);", POWELL_PINS),
     ("Powell equilibrium drops 1/cs^2", "double moving = cphi / L->cs2;", "double moving = cphi;",
      POWELL_PINS),
+    ("porosity blend reversed", "uh[a] = d * u[a] + (1.0 - d) * uB[a];",
+     "uh[a] = (1.0 - d) * u[a] + d * uB[a];", HLBM_PINS),
+    ("field blended with the solid velocity", "Bh[a] = d * B[a] + (1.0 - d) * BB[a];",
+     "Bh[a] = d * B[a] + (1.0 - d) * uB[a];", HLBM_PINS),
+    ("porosity without the 1/2 offset", "return phi / eps_h + 0.5;", "return phi / eps_h;", HLBM_PINS),
+    ("blended density", "Qhat[0] = rho;", "Qhat[0] = d * rho + (1.0 - d);", HLBM_PINS),
+    ("HLBM step streams against c_i", "long target = neighbour(x, y, z, L.c[i], nx, ny, nz);",
+     "long target = neighbour(x, y, z, L.c[L.opp[i]], nx, ny, nz);", HLBM_PINS),
     ("Powell source without weight", "fout[k * L->q + i] = f + (feq[k][i] - f) / tau[k] + L->w[i] * sk;",
      "fout[k * L->q + i] = f + (feq[k][i] - f) / tau[k] + sk;", POWELL_PINS),
 ]
