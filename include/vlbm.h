@@ -289,6 +289,32 @@ vlbm_status vlbm_closure_train_step(vlbm_closure *cl, const double *Q0_dev, cons
  * Enqueued on the context's stream; synchronises it. */
 vlbm_status vlbm_closure_train_step_ctx(vlbm_closure *cl, vlbm_ctx *ctx, const double *Qt_dev, double *loss);
 
+/* Homogenised solid objects (sec. 2.4, "Homogenization", HLBM).  Attach
+ * (solid_dev) or detach (NULL) per-cell solid fields to a single-domain
+ * ideal-MHD context (VLBM_IDEAL, F32 or F64 storage, 2-D or 3-D, no closure):
+ * solid_dev points to 7 x N floats on the device, structure of arrays,
+ * solid_dev[v*N + cell] with v = 0 the porosity d in [0, 1] (1 fluid, 0 solid),
+ * v = 1..3 the solid's velocity uB, v = 4..6 its field BB (lattice units),
+ * N = nx*ny*nz, cell = x + nx*(y + ny*z).  Every following vlbm_step blends
+ * u_hat = d u + (1 - d) uB and B_hat = d B + (1 - d) BB in the fused step and
+ * relaxes towards the equilibrium of (rho, rho u_hat, e_hat, B_hat), with
+ * e_hat = p/(gamma-1) + rho|u_hat|^2/2 + |B_hat|^2/2 from the cell's own gas
+ * pressure p.  The caller owns the array: it must stay valid while attached.
+ * A moving object may rewrite it between steps: the rewrite must wait until
+ * the steps already enqueued have completed (they read the array when they
+ * run; vlbm_sync, or an event on the context's stream), and it must be
+ * complete before the next vlbm_step (the stream-ordering convention above).
+ * VLBM_ERR_UNSUPPORTED for other models, storages, batches or with a closure
+ * attached. */
+vlbm_status vlbm_set_solid(vlbm_ctx *ctx, const float *solid_dev);
+
+/* Porosity of the signed distance to a solid surface (sec. 2.4, positive in
+ * the fluid): d = 0 for phi <= -eps_h/2, phi/eps_h + 1/2 inside the
+ * transition, 1 for phi >= eps_h/2; n values, device pointers, enqueued on
+ * `stream` (cudaStream_t or NULL).  eps_h > 0; VLBM_ERR_ARG otherwise. */
+vlbm_status vlbm_porosity_from_distance(const float *phi_dev, int64_t n, double eps_h, float *d_dev,
+                                        void *stream);
+
 /* Attach (cl) or detach (NULL) a closure to a 3-D ideal-MHD context with F32
  * storage and the closure's grid: every following vlbm_step evaluates the
  * network on the current state and applies the correction in the fused

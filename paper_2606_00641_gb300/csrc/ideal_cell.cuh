@@ -80,6 +80,79 @@ __device__ __forceinline__ void ideal_collide(C (&f)[8][AxisSet<D>::Q], const C 
     }
 }
 
+// Homogenised solids (sec. 2.4, "Homogenization"): the equilibrium and the
+// fluxes take the blended velocity and field u_hat = d u + (1 - d) uB,
+// B_hat = d B + (1 - d) BB at the cell's own density and gas pressure, i.e. the
+// state Q_hat = (rho, rho u_hat, p/(gamma-1) + rho|u_hat|^2/2 + |B_hat|^2/2,
+// B_hat); BGK towards f_eq(Q_hat) plus the uniform source.  Plain storage.
+template <int D, class C>
+__device__ __forceinline__ void ideal_collide_hom(C (&f)[8][AxisSet<D>::Q], const C gm1, const C *omega,
+                                                  const C *src0, const C *src1, unsigned *flags, const C d,
+                                                  const C (&uB)[3], const C (&BB)[3])
+{
+    constexpr int Q = AxisSet<D>::Q;
+    C q[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        C s = f[k][0];
+#pragma unroll
+        for (int i = 1; i < Q; ++i) s += f[k][i];
+        q[k] = s;
+    }
+    const C rho = q[0];
+    const C ir = C(1) / rho;
+    const C u[3] = {q[1] * ir, q[2] * ir, q[3] * ir};
+    const C B[3] = {q[5], q[6], q[7]};
+    const C B2 = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
+    const C mu = q[1] * u[0] + q[2] * u[1] + q[3] * u[2];
+    const C p = gm1 * (q[4] - C(0.5) * mu - C(0.5) * B2);
+    if (!(rho > C(0)) || !(p > C(0))) atomicOr(flags, kFlagNonPhysical);
+    // blended state
+    const C dc = C(1) - d;
+    C uh[3], Bh[3], mh[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        uh[a] = d * u[a] + dc * uB[a];
+        Bh[a] = d * B[a] + dc * BB[a];
+        mh[a] = rho * uh[a];
+    }
+    const C Bh2 = Bh[0] * Bh[0] + Bh[1] * Bh[1] + Bh[2] * Bh[2];
+    const C muh = mh[0] * uh[0] + mh[1] * uh[1] + mh[2] * uh[2];
+    const C Eh = p / gm1 + C(0.5) * muh + C(0.5) * Bh2;
+    const C pt = p + C(0.5) * Bh2;
+    const C uBh = uh[0] * Bh[0] + uh[1] * Bh[1] + uh[2] * Bh[2];
+    const C qh[8] = {rho, mh[0], mh[1], mh[2], Eh, Bh[0], Bh[1], Bh[2]};
+
+    C phi[8][D];
+#pragma unroll
+    for (int ax = 0; ax < D; ++ax) {
+        phi[0][ax] = mh[ax];
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            phi[1 + b][ax] = mh[ax] * uh[b] - Bh[ax] * Bh[b] + (ax == b ? pt : C(0));
+            phi[5 + b][ax] = (ax == b) ? C(0) : uh[ax] * Bh[b] - Bh[ax] * uh[b];
+        }
+        phi[4][ax] = (Eh + pt) * uh[ax] - Bh[ax] * uBh;
+    }
+
+    constexpr C w0 = C(AxisSet<D>::w0), w1 = C(AxisSet<D>::w1);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const C om = omega[k];
+        const C omc = C(1) - om;
+        const C A0 = om * w0 * qh[k] + src0[k];
+        const C A1 = om * w1 * qh[k] + src1[k];
+        const C hom = C(0.5) * om;  // omega * w_moving / cs^2
+        f[k][0] = omc * f[k][0] + A0;
+#pragma unroll
+        for (int ax = 0; ax < D; ++ax) {
+            const C bv = hom * phi[k][ax];
+            f[k][2 * ax + 1] = omc * f[k][2 * ax + 1] + A1 + bv;
+            f[k][2 * ax + 2] = omc * f[k][2 * ax + 2] + A1 - bv;
+        }
+    }
+}
+
 // Ideal MHD with Powell's source (sec. 2.3, "Powell correction") on nine
 // lattices: the eight of ideal_collide plus D, the trace of the gradient
 // tensor of the local moments evolution (sec. 2.2.1), with flux D u - B.

@@ -34,6 +34,8 @@ template <class C> struct IdealArgs {
     unsigned *flags;
     const float *dphi;    // closure: per-cell flux correction [cell][24], or null
     C inv_tau_m;          // Powell model: 1 / tau_M (div B = D / tau_M)
+    const float *solid;   // homogenised solids: [7][solid_n] d, uB, BB per cell, or null
+    int64_t solid_n;
 };
 
 // Linear indices of the cell's neighbours x + c_i (periodic), i in set order.
@@ -59,8 +61,9 @@ __device__ __forceinline__ void neighbours(int x, int y, int z, int nx, int ny, 
 // The fused collide-and-stream step.  ODD selects the AA parity; CORR adds
 // the learned flux correction dPhi[k][a] to the post-collision populations
 // (f*_{k,+a} += dPhi/2, f*_{k,-a} -= dPhi/2: zero mass, first moment dPhi).
-// NL = 9 is the Powell model (eight MHD lattices and the divergence lattice).
-template <int D, class S, class C, bool ODD, bool CORR = false, int NL = 8>
+// NL = 9 is the Powell model (eight MHD lattices and the divergence lattice);
+// HOM blends with homogenised solids (a.solid).
+template <int D, class S, class C, bool ODD, bool CORR = false, int NL = 8, bool HOM = false>
 __global__ void __launch_bounds__(kBlockX) k_ideal_step(const IdealArgs<C> a)
 {
     constexpr int Q = AxisSet<D>::Q;
@@ -85,6 +88,12 @@ __global__ void __launch_bounds__(kBlockX) k_ideal_step(const IdealArgs<C> a)
 
     if constexpr (NL == 9) {
         powell_collide<D, C>(f, a.gm1, a.omega, a.src0, a.src1, a.inv_tau_m, a.flags);
+    } else if constexpr (HOM) {
+        const float *sp = a.solid + cell;
+        const C d = C(__ldg(sp));
+        const C uB[3] = {C(__ldg(sp + a.solid_n)), C(__ldg(sp + 2 * a.solid_n)), C(__ldg(sp + 3 * a.solid_n))};
+        const C BB[3] = {C(__ldg(sp + 4 * a.solid_n)), C(__ldg(sp + 5 * a.solid_n)), C(__ldg(sp + 6 * a.solid_n))};
+        ideal_collide_hom<D, C>(f, a.gm1, a.omega, a.src0, a.src1, a.flags, d, uB, BB);
     } else {
         // deviation storage collides on the stored deviations directly (ideal_cell.cuh)
         ideal_collide<D, C, Codec<S>::kDev>(f, a.gm1, a.omega, a.src0, a.src1, a.flags, a.ref, a.scale,
@@ -408,6 +417,16 @@ __global__ void k_ideal_moments(const ReadArgs<D, S> a, int64_t c0, int64_t coun
     for (int k = 0; k < NL; ++k) out[k * ostride + t] = (double)cell_moment<D, S>(a, cell, nb, k);
 }
 
+// HLBM porosity of the signed distance phi (sec. 2.4): 0 in the solid, 1 in the
+// fluid, phi / eps_h + 1/2 across the transition of width eps_h.
+__global__ void k_porosity(const float *__restrict__ phi, int64_t n, float eps_h, float *__restrict__ d)
+{
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const float v = phi[t];
+    d[t] = v <= -0.5f * eps_h ? 0.f : (v >= 0.5f * eps_h ? 1.f : v / eps_h + 0.5f);
+}
+
 // Closure input features from the populations: the FP32 moments of
 // k_ideal_moments, normalised and rounded to BF16, 16 bytes per cell.
 struct FeatureNorm {
@@ -533,6 +552,8 @@ template <class C> IdealArgs<C> make_step_args(vlbm_ctx *c)
     }
     a.flags = c->d_flags;
     a.inv_tau_m = C(1.0 / d.tau_m);
+    a.solid = c->solid;
+    a.solid_n = d.ncell;
     return a;
 }
 
@@ -561,6 +582,14 @@ template <int D, class S, class C> vlbm_status step_t(vlbm_ctx *c, int parity)
     const IdealArgs<C> a = make_step_args<C>(c);
     const dim3 grid((unsigned)((d.nx + kBlockX - 1) / kBlockX), (unsigned)d.ny, (unsigned)d.nz);
     if constexpr (!Codec<S>::kDev) {
+        if (c->solid) {  // homogenised solids
+            if (parity)
+                k_ideal_step<D, S, C, true, false, 8, true><<<grid, kBlockX, 0, c->stream>>>(a);
+            else
+                k_ideal_step<D, S, C, false, false, 8, true><<<grid, kBlockX, 0, c->stream>>>(a);
+            c->launches++;
+            return cuda_check(c, cudaGetLastError(), "homogenised step launch");
+        }
         if (c->nlat == 9) {  // Powell model
             if (parity)
                 k_ideal_step<D, S, C, true, false, 9><<<grid, kBlockX, 0, c->stream>>>(a);
@@ -760,6 +789,13 @@ vlbm_status ideal_gather(vlbm_ctx *c, int d, const int64_t *cells_dev, int n, do
 }
 
 vlbm_status ideal_sums(vlbm_ctx *c, int d, double *sums_dev) { return dispatch<SumsF>(c, d, sums_dev); }
+
+vlbm_status porosity_from_distance(const float *phi, int64_t n, double eps_h, float *d, cudaStream_t s)
+{
+    const int threads = 256;
+    k_porosity<<<(unsigned)((n + threads - 1) / threads), threads, 0, s>>>(phi, n, (float)eps_h, d);
+    return cuda_check(nullptr, cudaGetLastError(), "porosity launch");
+}
 
 vlbm_status ideal_features(vlbm_ctx *c, const float *mu, const float *inv_sigma, __nv_bfloat16 *x)
 {

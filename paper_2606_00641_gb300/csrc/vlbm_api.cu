@@ -693,10 +693,32 @@ vlbm_status vlbm_set_closure(vlbm_ctx *c, vlbm_closure *cl)
             return fail(c, VLBM_ERR_UNSUPPORTED, "the closure applies to single 3-D ideal-MHD F32 contexts");
         if (c->dom[0].nx != nx || c->dom[0].ny != ny || c->dom[0].nz != nz)
             return fail(c, VLBM_ERR_ARG, "closure grid differs from the context grid");
+        if (c->solid) return fail(c, VLBM_ERR_UNSUPPORTED, "a closure and homogenised solids do not combine");
     }
     drop_graphs(c);
     c->closure = cl;
     return VLBM_OK;
+}
+
+vlbm_status vlbm_set_solid(vlbm_ctx *c, const float *solid_dev)
+{
+    if (!c) return VLBM_ERR_ARG;
+    if (solid_dev) {
+        if (c->batched || c->model != VLBM_IDEAL || (c->storage != VLBM_F32 && c->storage != VLBM_F64))
+            return fail(c, VLBM_ERR_UNSUPPORTED,
+                        "homogenised solids apply to single ideal-MHD contexts with F32 or F64 storage");
+        if (c->closure) return fail(c, VLBM_ERR_UNSUPPORTED, "a closure and homogenised solids do not combine");
+    }
+    drop_graphs(c);  // captured steps hold the previous pointer
+    c->solid = solid_dev;
+    return VLBM_OK;
+}
+
+vlbm_status vlbm_porosity_from_distance(const float *phi_dev, int64_t n, double eps_h, float *d_dev, void *stream)
+{
+    if (!phi_dev || !d_dev || n < 0 || !(eps_h > 0.0)) return fail(nullptr, VLBM_ERR_ARG, "porosity: bad arguments");
+    if (n == 0) return VLBM_OK;
+    return porosity_from_distance(phi_dev, n, eps_h, d_dev, static_cast<cudaStream_t>(stream));
 }
 
 int vlbm_tile_shapes(const vlbm_ctx *c) { return (c && c->batched) ? batch_num_choices() : 0; }

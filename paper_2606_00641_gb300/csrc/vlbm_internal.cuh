@@ -163,6 +163,7 @@ struct vlbm_ctx {
 
     // learned flux closure applied in every step (not owned)
     struct vlbm_closure *closure = nullptr;
+    const float *solid = nullptr;       // homogenised solids: [7][N] caller-owned fields, or null
 
     // allocator
     std::vector<std::pair<void *, size_t>> owned;
@@ -199,6 +200,8 @@ int batch_num_choices();
 
 // learned closure (k_closure.cu / k_ideal.cu)
 vlbm_status ideal_step_corrected(vlbm_ctx *c, int parity, const float *dphi);
+// porosity of the signed distance (HLBM), elementwise
+vlbm_status porosity_from_distance(const float *phi, int64_t n, double eps_h, float *d, cudaStream_t s);
 // closure input features of a 3-D FP32 context straight from its populations:
 // x[cell][k] = BF16((Q_k - mu_k) * inv_sigma_k), Q_k summed in FP32 as by ideal_moments
 vlbm_status ideal_features(vlbm_ctx *c, const float *mu, const float *inv_sigma, __nv_bfloat16 *x);

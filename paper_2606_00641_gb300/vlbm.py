@@ -150,6 +150,8 @@ def load(build: bool = True):
         "vlbm_closure_train_step": (i, [P, P, P, ctypes.POINTER(d)]),
         "vlbm_closure_train_step_ctx": (i, [P, P, P, ctypes.POINTER(d)]),
         "vlbm_set_closure": (i, [P, P]),
+        "vlbm_set_solid": (i, [P, P]),
+        "vlbm_porosity_from_distance": (i, [P, ctypes.c_int64, d, P, P]),
         "vlbm_closure_destroy": (None, [P]),
         "vlbm_restrict": (i, [P, i, i, i, i, P, P]),
     }
@@ -409,6 +411,21 @@ def vlbm_restrict(Qf_ptr: int, shape, factor: int, Qc_ptr: int, stream: int = 0)
                                 ctypes.c_void_p(stream) if stream else None), "vlbm_restrict")
 
 
+def vlbm_set_solid(ctx: int, solid_ptr) -> None:
+    """Attach homogenised solid fields ([7][N] float32 on the device: d, uB, BB) or detach (None)."""
+    if solid_ptr:
+        _device_inputs_ready()
+    _check(load().vlbm_set_solid(ctx, solid_ptr if solid_ptr else None), "vlbm_set_solid", ctx)
+
+
+def vlbm_porosity_from_distance(phi_ptr: int, n: int, eps_h: float, d_ptr: int, stream: int = 0) -> None:
+    """d = porosity(phi) on the device (sec. 2.4); float32 arrays of n values."""
+    _device_inputs_ready()
+    _check(load().vlbm_porosity_from_distance(ctypes.c_void_p(phi_ptr), int(n), float(eps_h),
+                                              ctypes.c_void_p(d_ptr), ctypes.c_void_p(stream) if stream else None),
+           "vlbm_porosity_from_distance")
+
+
 def vlbm_set_closure(ctx: int, closure) -> None:
     _check(load().vlbm_set_closure(ctx, closure.ptr if closure is not None else None), "vlbm_set_closure", ctx)
 
@@ -519,6 +536,14 @@ class Context:
 
     def conservation(self, domain: int = 0) -> np.ndarray:
         return vlbm_conservation(self.ptr, domain)
+
+    def set_solid(self, solid_ptr) -> None:
+        """Attach ([7][N] float32 device fields d, uB, BB) or detach (None) homogenised solids.
+
+        A moving object waits for the steps already enqueued (``sync()``: they read
+        the array when they run), rewrites the array, and calls this again so that
+        torch's writes are complete before the next step reads them."""
+        vlbm_set_solid(self.ptr, solid_ptr)
 
     def save(self) -> bytes:
         return vlbm_save(self.ptr)

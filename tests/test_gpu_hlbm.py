@@ -1,0 +1,214 @@
+"""Homogenised solid objects (HLBM, sec. 2.4 "Homogenization") on the GPU
+against the FP64 oracle: a rotating, magnetised sphere (or disc) whose
+porosity comes from the signed distance to its surface.
+
+Tolerances as for the ideal model: FP64 storage 1e-12, FP32 storage 1e-5,
+relative to each field's maximum.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2606_00641_gb300 import fields
+
+pytestmark = pytest.mark.gpu
+
+TAU = [0.6, 0.55, 0.55, 0.55, 0.7, 0.6, 0.6, 0.6]
+
+
+@pytest.fixture(scope="module")
+def V():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2606_00641_gb300 import vlbm
+    vlbm.load()
+    return vlbm
+
+
+def body(shape, omega=0.002, b0=0.02, eps_h=1.0, centre=None):
+    """[7, *shape] float32 fields of a rotating magnetised ball: d, uB = omega e_z x r,
+    BB = b0 times a smooth bump (lattice units), and the signed distance.  The
+    defaults keep |uB| and BB below the flow's speeds and fields (the test
+    states have p ~ 0.006, |u| ~ 0.03, |B| ~ 0.1): a body much faster than the
+    gas would drive the blended cells' gas pressure negative."""
+    dim = len(shape)
+    grids = np.meshgrid(*[np.arange(n, dtype=float) for n in shape], indexing="ij")
+    pos = grids[::-1]  # x, y (, z)
+    c = centre if centre is not None else [0.5 * (n - 1) for n in shape[::-1]]
+    rel = [p - ci for p, ci in zip(pos, c)]
+    r = np.sqrt(sum(v * v for v in rel))
+    radius = 0.3 * min(shape)
+    phi = r - radius
+    d = oracle.hlbm_porosity(phi, eps_h)
+    s = np.zeros((7,) + tuple(shape))
+    s[0] = d
+    s[1] = -omega * rel[1]
+    s[2] = omega * rel[0]
+    bump = np.exp(-(r / radius) ** 2)
+    s[4] = b0 * bump
+    s[6 if dim == 3 else 5] = 0.5 * b0 * bump
+    return s.astype(np.float32), phi.astype(np.float32)
+
+
+def field_errors(got, ref):
+    scale = np.maximum(np.abs(ref).reshape(8, -1).max(1), 1e-300)
+    return np.abs(got - ref).reshape(8, -1).max(1) / scale
+
+
+@pytest.mark.parametrize("shape", [(24, 40), (8, 12, 20)])
+@pytest.mark.parametrize("storage,tol", [("f64", 1e-12), ("f32", 1e-5)])
+@pytest.mark.parametrize("steps", [4, 5])
+def test_hlbm_matches_oracle(V, shape, storage, tol, steps):
+    import torch
+    f0 = fields.ideal_fields(shape, 51, mach=0.5, beta=1.0, cfl=0.2)
+    solid, _ = body(shape)
+    sd = torch.from_numpy(solid).cuda()
+    p = V.make_params(shape=shape, storage=storage, gamma=f0.gamma, tau=TAU)
+    with V.Context(p) as ctx:
+        assert ctx.init_fields(f0.Q) == V.VLBM_OK
+        ctx.set_solid(sd.data_ptr())
+        ctx.step(steps)
+        got = ctx.moments()
+        assert ctx.sync() == V.VLBM_OK
+    ref = oracle.hlbm_run(f0.Q, f0.gamma, TAU, solid.astype(np.float64), steps)
+    err = field_errors(got, ref)
+    assert err.max() < tol, err
+
+
+def test_porosity_kernel_matches_oracle(V):
+    import torch
+    rng = np.random.default_rng(4)
+    phi = rng.uniform(-3, 3, size=5000).astype(np.float32)
+    phi[:7] = [-0.75, -0.5, 0.0, 0.5, 0.75, -1e-7, 1e-7]
+    eps = 1.5
+    pd = torch.from_numpy(phi).cuda()
+    dd = torch.empty_like(pd)
+    V.vlbm_porosity_from_distance(pd.data_ptr(), phi.size, eps, dd.data_ptr())
+    torch.cuda.synchronize()
+    ref = oracle.hlbm_porosity(phi.astype(np.float64), eps)
+    np.testing.assert_allclose(dd.cpu().numpy(), ref, rtol=0, atol=1e-6)
+
+
+def test_moving_object_rewritten_between_steps(V):
+    # the caller rewrites the attached array in place between step batches (the body
+    # moves); captured step graphs must read the current contents
+    import torch
+    shape = (8, 12, 20)
+    f0 = fields.ideal_fields(shape, 52, mach=0.5, beta=1.0, cfl=0.2)
+    s1, _ = body(shape, centre=[8.0, 5.5, 3.5])
+    s2, _ = body(shape, centre=[11.0, 6.0, 4.0], omega=-0.003)
+    sd = torch.from_numpy(s1).cuda()
+    p = V.make_params(shape=shape, storage="f64", gamma=f0.gamma, tau=TAU)
+    with V.Context(p) as ctx:
+        assert ctx.init_fields(f0.Q) == V.VLBM_OK
+        ctx.set_solid(sd.data_ptr())
+        ctx.step(40)
+        assert ctx.sync() == V.VLBM_OK  # the queued steps read the array: wait before rewriting it
+        sd.copy_(torch.from_numpy(s2))
+        ctx.set_solid(sd.data_ptr())
+        ctx.step(41)
+        got = ctx.moments()
+    f = oracle.ideal_init(f0.Q, f0.gamma)
+    for _ in range(40):
+        f = oracle.hlbm_step(f, f0.gamma, TAU, s1.astype(np.float64))
+    for _ in range(41):
+        f = oracle.hlbm_step(f, f0.gamma, TAU, s2.astype(np.float64))
+    ref = oracle.ideal_moments(f)
+    assert field_errors(got, ref).max() < 1e-12
+
+
+def test_detach_returns_to_the_ideal_scheme_and_api_checks(V):
+    import torch
+    shape = (24, 40)
+    f0 = fields.ideal_fields(shape, 53, mach=0.5, beta=1.0, cfl=0.1)
+    solid, _ = body(shape)
+    sd = torch.from_numpy(solid).cuda()
+    p = V.make_params(shape=shape, storage="f64", gamma=f0.gamma, tau=TAU)
+    with V.Context(p) as ctx:
+        assert ctx.init_fields(f0.Q) == V.VLBM_OK
+        ctx.set_solid(sd.data_ptr())
+        ctx.set_solid(None)
+        ctx.step(6)
+        got = ctx.moments()
+    assert field_errors(got, oracle.ideal_run(f0.Q, f0.gamma, TAU, 6)).max() < 1e-12
+    for params in (V.make_params(shape=(4, 8, 16), storage="f16dev"),
+                   V.make_params(model=V.VLBM_IDEAL_POWELL, shape=(4, 8, 16))):
+        with V.Context(params) as ctx:
+            with pytest.raises(V.VlbmError):
+                ctx.set_solid(sd.data_ptr())
+
+
+def _blend_initial_state(Q, solid, gamma):
+    # a body in the gas: u and B start at the blended values at the cell's rho and p
+    rho = Q[0]
+    p = (gamma - 1) * (Q[4] - 0.5 * (Q[1:4] ** 2).sum(0) / rho - 0.5 * (Q[5:8] ** 2).sum(0))
+    d = solid[0].double()
+    for a in range(3):
+        Q[1 + a] = d * Q[1 + a] + (1 - d) * rho * solid[1 + a].double()
+        Q[5 + a] = d * Q[5 + a] + (1 - d) * solid[4 + a].double()
+    Q[4] = p / (gamma - 1) + 0.5 * (Q[1:4] ** 2).sum(0) / rho + 0.5 * (Q[5:8] ** 2).sum(0)
+
+
+def test_full_size_sphere_sampled_against_light_cones(V):
+    # The 512^3 rotating, magnetised sphere run the way the benchmark runs it (its own
+    # stream, so the steps go through captured graphs; 4 + 20 steps).  On D3Q7 a cell's
+    # populations after n steps depend only on the cells within L1 distance n, so the
+    # oracle on the periodic (2n+1)^3 box centred on a sampled cell gives that cell
+    # exactly.
+    import torch
+    n, steps = 512, 24
+    shape = (n, n, n)
+    f0 = fields.ideal_fields(shape, 3003, mach=0.2, beta=10.0, cfl=0.2, k_rho=4, k_u=4, k_b=4,
+                             device=torch.device("cuda"))
+    Q = f0.Q
+    umax = float((Q[1:4] / Q[0]).abs().max())
+    bmax = float(Q[5:8].abs().max())
+    ax = torch.arange(n, device="cuda", dtype=torch.float32) - 0.5 * (n - 1)
+    z, y, x = torch.meshgrid(ax, ax, ax, indexing="ij")
+    r = torch.sqrt(x * x + y * y + z * z)
+    radius = n / 8.0
+    phi = (r - radius).contiguous()
+    solid = torch.zeros((7,) + shape, dtype=torch.float32, device="cuda")
+    V.vlbm_porosity_from_distance(phi.data_ptr(), phi.numel(), 1.0, solid[0].data_ptr())
+    om = 0.25 * umax / radius
+    solid[1] = -om * y
+    solid[2] = om * x
+    bump = torch.exp(-(r / radius) ** 2)
+    solid[4] = 0.25 * bmax * bump
+    solid[6] = 0.125 * bmax * bump
+    del x, y, z, r, phi, bump
+    _blend_initial_state(Q, solid, f0.gamma)
+    scale = Q.abs().reshape(8, -1).amax(1).cpu().numpy()
+
+    c = n // 2
+    # centre; the inner edge of the transition (d ~ 0.004); mid-transition (d ~ 0.46);
+    # just outside (d = 1, |phi| ~ 1); the gas near the body; far gas; the corners
+    samples = [(c, c, c), (c, c, c + 63), (c, c + 40, c + 49), (c, c + 46, c + 45), (c, c, c + 70),
+               (40, 300, 100), (0, 0, 0), (n - 1, n - 1, n - 1)]
+    h = steps
+    boxes = []
+    for (zc, yc, xc) in samples:
+        idx = [torch.arange(v - h, v + h + 1, device="cuda") % n for v in (zc, yc, xc)]
+        Qb = Q[:, idx[0]][:, :, idx[1]][:, :, :, idx[2]].cpu().numpy()
+        Sb = solid[:, idx[0]][:, :, idx[1]][:, :, :, idx[2]].double().cpu().numpy()
+        boxes.append((Qb, Sb))
+
+    stream = torch.cuda.Stream()
+    p = V.make_params(shape=shape, storage="f32", gamma=f0.gamma, tau=0.51, stream=stream.cuda_stream)
+    with V.Context(p) as ctx:
+        assert V.vlbm_init_fields_device(ctx.ptr, 0, Q.data_ptr()) == V.VLBM_OK
+        ctx.set_solid(solid.data_ptr())
+        ctx.step(4)
+        ctx.step(steps - 4)
+        assert ctx.sync() == V.VLBM_OK
+        cells = [xc + n * (yc + n * zc) for (zc, yc, xc) in samples]
+        got = ctx.populations(cells)
+    del Q, solid
+
+    for (Qb, Sb), g in zip(boxes, got):
+        fb = oracle.ideal_init(Qb, f0.gamma)
+        for _ in range(steps):
+            fb = oracle.hlbm_step(fb, f0.gamma, 0.51, Sb, nthreads=8)
+        ref = fb[:, :, h, h, h].reshape(-1)
+        tol = 1e-5 * np.repeat(scale, 7)
+        assert np.all(np.abs(g - ref) <= tol), np.abs(g - ref).reshape(8, 7).max(1) / scale

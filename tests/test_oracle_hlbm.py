@@ -62,6 +62,37 @@ def test_uniform_solid_cell_relaxes_to_the_solid_state():
     np.testing.assert_allclose(out[5:8], BB + (1 - om_b) ** n * (Q0[5:8] - BB), rtol=1e-12, atol=1e-16)
 
 
+def _gas_pressure(Q):
+    return (GAMMA - 1) * (Q[4] - 0.5 * (Q[1:4] ** 2).sum(0) / Q[0] - 0.5 * (Q[5:8] ** 2).sum(0))
+
+
+@pytest.mark.parametrize("tau", [0.6, 1.5])
+def test_uniform_cell_pressure_follows_the_relaxation_of_the_blend(tau):
+    # The blended state keeps rho and p, so with one omega on every lattice a uniform
+    # cell moves to Q + omega (Q_hat - Q).  For weights (1 - omega, omega) the convex
+    # identity a|x|^2 + b|y|^2 - |a x + b y|^2 = a b |x - y|^2 gives the gas pressure
+    # after one step as p + (gamma - 1) omega (1 - omega) (rho |u_hat - u|^2 + |B_hat - B|^2) / 2:
+    # heating for omega < 1, a drain for omega > 1.  With d = 0 the target is fixed, the
+    # contrast decays as (1 - omega)^n, and the n-step sum is geometric.
+    shape = (2, 3, 4)
+    Q0 = np.array([1.2, 0.12, -0.06, 0.03, 1.0, 0.2, -0.1, 0.05])
+    Q = np.broadcast_to(Q0.reshape(8, 1, 1, 1), (8,) + shape).copy()
+    uB, BB = np.array([0.05, 0.02, -0.04]), np.array([-0.1, 0.15, 0.0])
+    om = 1.0 / tau
+    rho, u, B = Q0[0], Q0[1:4] / Q0[0], Q0[5:8]
+    p0 = _gas_pressure(Q0)
+    d = 0.25
+    contrast = rho * (((1 - d) * (uB - u)) ** 2).sum() + (((1 - d) * (BB - B)) ** 2).sum()
+    one = oracle.hlbm_run(Q, GAMMA, tau, _solid(shape, d, uB, BB), 1)[:, 0, 0, 0]
+    np.testing.assert_allclose(_gas_pressure(one), p0 + (GAMMA - 1) * om * (1 - om) * 0.5 * contrast,
+                               rtol=1e-12)
+    n = 9
+    k0 = rho * ((uB - u) ** 2).sum() + ((BB - B) ** 2).sum()
+    many = oracle.hlbm_run(Q, GAMMA, tau, _solid(shape, 0.0, uB, BB), n)[:, 0, 0, 0]
+    expect = p0 - 0.5 * (GAMMA - 1) * (om - 1) / (2 - om) * (1 - (1 - om) ** (2 * n)) * k0
+    np.testing.assert_allclose(_gas_pressure(many), expect, rtol=1e-12)
+
+
 def test_mass_is_conserved_exactly():
     shape = (10, 12)
     f0 = fields.ideal_fields(shape, 43, mach=1.0, beta=1.0, cfl=0.2)

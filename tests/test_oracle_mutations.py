@@ -50,6 +50,7 @@ HLBM_PINS = [
     lambda o: H.test_uniform_solid_cell_relaxes_to_the_solid_state(),
     lambda o: H.test_mass_is_conserved_exactly(),
     lambda o: H.test_channel_between_homogenised_walls_is_parabolic_with_walls_at_d_half(),
+    lambda o: H.test_uniform_cell_pressure_follows_the_relaxation_of_the_blend(0.6),
 ]
 
 # (name, original text, planted mistake, which pin family must catch it)
@@ -106,6 +107,10 @@ MUTANTS = [
     ("blended density", "Qhat[0] = rho;", "Qhat[0] = d * rho + (1.0 - d);", HLBM_PINS),
     ("HLBM step streams against c_i", "long target = neighbour(x, y, z, L.c[i], nx, ny, nz);",
      "long target = neighbour(x, y, z, L.c[L.opp[i]], nx, ny, nz);", HLBM_PINS),
+    ("blended energy keeps the cell's e", "Qhat[4] = p / (gamma - 1.0) + 0.5 * rho * uh2 + 0.5 * Bh2;",
+     "Qhat[4] = Q[4];", HLBM_PINS),
+    ("blended energy misses the field energy", "Qhat[4] = p / (gamma - 1.0) + 0.5 * rho * uh2 + 0.5 * Bh2;",
+     "Qhat[4] = p / (gamma - 1.0) + 0.5 * rho * uh2;", HLBM_PINS),
     ("Powell source without weight", "fout[k * L->q + i] = f + (feq[k][i] - f) / tau[k] + L->w[i] * sk;",
      "fout[k * L->q + i] = f + (feq[k][i] - f) / tau[k] + sk;", POWELL_PINS),
 ]
