@@ -82,6 +82,8 @@ def _configure(L):
     L.orc_hlbm_target.restype = None
     L.orc_hlbm_step.argtypes = [i, i, i, i, d, p, p, p, p, p, i]
     L.orc_hlbm_run.argtypes = [i, i, i, i, d, p, p, p, p, i, p, i]
+    L.orc_open_step.argtypes = [i, i, i, i, d, p, p, p, p, p, p, p, i]
+    L.orc_open_run.argtypes = [i, i, i, i, d, p, p, p, p, p, p, i, p, i]
     return L
 
 
@@ -394,4 +396,57 @@ def resistive_run(Q0, tau_f, tau_m, force, b_wall, walls_y, nsteps, nthreads: in
     _check(lib().orc_resistive_run(nx, ny, nz, tau_f, tau_m, _ptr(_f64(force)),
                                    _ptr(_f64(b_wall)), int(walls_y), _ptr(Q0), nsteps,
                                    _ptr(out), nthreads), "resistive_run")
+    return out
+
+
+# ---- static equilibrium boundaries (sec. 2.4, "Static boundaries") ----
+
+def _faces(faces, dim):
+    """faces: up to six entries for x-, x+, y-, y+, z-, z+, each None (periodic) or
+    (mask, values): bit k of mask set = Q_k Dirichlet at values[k], clear = Neumann."""
+    faces = list(faces) + [None] * (6 - len(faces))
+    open_ = np.zeros(3, dtype=np.int32)
+    mask = np.zeros(6, dtype=np.uint32)
+    vals = np.zeros(48)
+    for a in range(3):
+        lo, hi = faces[2 * a], faces[2 * a + 1]
+        if (lo is None) != (hi is None):
+            raise ValueError("both faces of an axis are open or both periodic")
+        if lo is None:
+            continue
+        if a >= dim:
+            raise ValueError("face beyond the grid's dimension")
+        open_[a] = 1
+        for f, spec in ((2 * a, lo), (2 * a + 1, hi)):
+            m, v = spec
+            mask[f] = int(m)
+            vals[8 * f:8 * f + 8] = np.asarray(v if v is not None else np.zeros(8), dtype=np.float64)
+    return open_, mask, vals
+
+
+def open_step(f: np.ndarray, gamma: float, tau, faces, src=None, nthreads: int = 1) -> np.ndarray:
+    """One step with open faces (equilibrium Dirichlet / Neumann boundaries)."""
+    f = _f64(f)
+    dim, nx, ny, nz = _dims(f.shape[2:])
+    open_, mask, vals = _faces(faces, dim)
+    out = np.zeros_like(f)
+    tau = _f64(np.broadcast_to(np.asarray(tau, dtype=np.float64), (8,)))
+    s = _f64(src) if src is not None else None
+    _check(lib().orc_open_step(dim, nx, ny, nz, gamma, _ptr(tau), _ptr(s) if s is not None else None,
+                               open_.ctypes.data_as(ctypes.c_void_p), mask.ctypes.data_as(ctypes.c_void_p),
+                               _ptr(vals), _ptr(f), _ptr(out), nthreads), "open_step")
+    return out
+
+
+def open_run(Q0: np.ndarray, gamma: float, tau, faces, nsteps: int, src=None, nthreads: int = 1) -> np.ndarray:
+    """Moments [8, ...] after nsteps steps with open faces, started from f_eq(Q0)."""
+    Q0 = _f64(Q0)
+    dim, nx, ny, nz = _dims(Q0.shape[1:])
+    open_, mask, vals = _faces(faces, dim)
+    out = np.zeros_like(Q0)
+    tau = _f64(np.broadcast_to(np.asarray(tau, dtype=np.float64), (8,)))
+    s = _f64(src) if src is not None else None
+    _check(lib().orc_open_run(dim, nx, ny, nz, gamma, _ptr(tau), _ptr(s) if s is not None else None,
+                              open_.ctypes.data_as(ctypes.c_void_p), mask.ctypes.data_as(ctypes.c_void_p),
+                              _ptr(vals), _ptr(Q0), nsteps, _ptr(out), nthreads), "open_run")
     return out

@@ -118,6 +118,52 @@ def ideal_run(Q0: np.ndarray, gamma: float, tau, nsteps: int, src=None) -> np.nd
     return f.sum(axis=1)
 
 
+def open_step(f: np.ndarray, gamma: float, tau, dim: int, faces, src=None) -> np.ndarray:
+    """Static equilibrium boundaries (sec. 2.4): periodic streaming, then on every
+    open face the direction entering across it is overwritten with the equilibrium
+    of the boundary state (Dirichlet values where the mask bit is set, else the
+    streamed moments of the cell one step along the discrete inward normal).
+    faces[2a], faces[2a+1]: None (periodic) or (mask, values) for axis a's low and high face."""
+    c, w, _ = vset("D2Q5" if dim == 2 else "D3Q7")
+    out = ideal_step(f, gamma, tau, dim, src)
+    shape = f.shape[2:]
+    faces = list(faces) + [None] * (6 - len(faces))
+    pos = np.indices(shape)  # pos[j] indexes array axis j, i.e. lattice axis dim - 1 - j
+    size = [shape[dim - 1 - a] for a in range(dim)]
+    coord = [pos[dim - 1 - a] for a in range(dim)]
+    normal = [np.zeros(shape, dtype=int) for _ in range(dim)]
+    for a in range(dim):
+        if faces[2 * a] is not None:
+            normal[a] = np.where(coord[a] == 0, 1, np.where(coord[a] == size[a] - 1, -1, 0))
+    nb_index = tuple(coord[a] + normal[a] for a in range(dim))[::-1]
+    Qs = out.sum(axis=1)
+    Qn = Qs[(slice(None),) + nb_index]
+    for a in range(dim):
+        for side in (0, 1):
+            spec = faces[2 * a + side]
+            if spec is None:
+                continue
+            mask, vals = spec
+            vals = np.zeros(8) if vals is None else np.asarray(vals, dtype=float)
+            on = coord[a] == (0 if side == 0 else size[a] - 1)
+            Qb = np.array([np.full(shape, vals[k]) if (int(mask) >> k) & 1 else Qn[k] for k in range(8)])
+            feq = ideal_feq(Qb, gamma, dim)
+            e = np.zeros(3, dtype=int)
+            e[a] = 1 if side == 0 else -1
+            din = [i for i in range(len(w)) if tuple(c[i]) == tuple(e[:c.shape[1]])][0]
+            for k in range(8):
+                out[k, din][on] = feq[k, din][on]
+    return out
+
+
+def open_run(Q0: np.ndarray, gamma: float, tau, faces, nsteps: int, src=None) -> np.ndarray:
+    dim = Q0.ndim - 1
+    f = ideal_feq(Q0, gamma, dim)
+    for _ in range(nsteps):
+        f = open_step(f, gamma, tau, dim, faces, src)
+    return f.sum(axis=1)
+
+
 # ----------------------------------------------------------------------------
 # ideal MHD with the Powell correction (sec. 2.3): a ninth lattice carries
 # D = tr G (sec. 2.2.1) with flux D u - B and source -D / tau_M; the other

@@ -17,6 +17,7 @@
  *   Powell source  S = -(div B)(0, B, u.B, u)          (sec. 2.3, "Powell correction")
  *   homogenised solids: blended u, B and the porosity of the signed distance
  *                                                      (sec. 2.4, "Homogenization")
+ *   equilibrium Dirichlet / Neumann open boundaries    (sec. 2.4, "Static boundaries")
  *   local gradient evolution  dG/dt + div Phi_G = -G/tau_R          (sec. 2.2.1)
  *
  * Readings where the paper is silent (each one is listed in the design notes):
@@ -644,6 +645,146 @@ int orc_hlbm_run(int dim, int nx, int ny, int nz, double gamma, const double *ta
     free(a);
     free(b);
     return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Static equilibrium boundaries (sec. 2.4, "Static boundaries")         */
+/* ------------------------------------------------------------------ */
+/*
+ * An axis is periodic or open.  On an open face every state variable is
+ * Dirichlet (a set value) or Neumann (the value of the next cell along the
+ * boundary's discrete normal); the equilibrium of that boundary state is
+ * assigned to the lattice direction that enters the domain across the face.
+ *
+ * Faces: 0 x-, 1 x+, 2 y-, 3 y+, 4 z-, 5 z+.  open[a] = 1 makes both faces of
+ * axis a open.  For face F, bit k of mask[F] set means Q_k = vals[8*F + k];
+ * clear means Q_k is copied.  The discrete normal of a cell is the sum of the
+ * inward normals of all open faces it lies on (at an edge or a corner it
+ * points diagonally inwards), so the copied cell is never on an open face
+ * when every open axis has at least three cells.
+ *
+ * One step: every cell collides; each post-collision population moves to
+ * x + c_i, and one whose destination lies beyond an open face leaves the
+ * domain; then every cell on an open face receives, in the direction that
+ * enters across that face, f_eq_i of the face's boundary state, built from
+ * the streamed (next pre-collision) state of its normal neighbour.
+ */
+static int on_face(int face, int x, int y, int z, int nx, int ny, int nz)
+{
+    switch (face) {
+    case 0: return x == 0;
+    case 1: return x == nx - 1;
+    case 2: return y == 0;
+    case 3: return y == ny - 1;
+    case 4: return z == 0;
+    default: return z == nz - 1;
+    }
+}
+
+int orc_open_step(int dim, int nx, int ny, int nz, double gamma, const double *tau, const double *src,
+                  const int *open, const unsigned *mask, const double *vals, const double *fin, double *fout,
+                  int nthreads)
+{
+    orc_lattice L;
+    if (check_dims(dim, nx, ny, nz)) return -1;
+    const int size[3] = {nx, ny, nz};
+    for (int a = 0; a < dim; ++a)
+        if (open[a] && size[a] < 3) return -1;
+    if (dim == 2 && open[2]) return -1;
+    ideal_lattice(dim, &L);
+    const long N = (long)nx * ny * nz;
+    const int q = L.q;
+    if (nthreads < 1) nthreads = 1;
+    /* collide and stream; populations leaving across an open face are dropped */
+#pragma omp parallel for num_threads(nthreads) schedule(static)
+    for (long cell = 0; cell < N; ++cell) {
+        int x = (int)(cell % nx);
+        int y = (int)((cell / nx) % ny);
+        int z = (int)(cell / ((long)nx * ny));
+        int pos[3] = {x, y, z};
+        double fc[ORC_NVAR_IDEAL * ORC_QMAX];
+        double fs[ORC_NVAR_IDEAL * ORC_QMAX];
+        for (int k = 0; k < ORC_NVAR_IDEAL; ++k)
+            for (int i = 0; i < q; ++i) fc[k * q + i] = fin[(long)(k * q + i) * N + cell];
+        ideal_collide(&L, gamma, tau, src, fc, fs);
+        for (int i = 0; i < q; ++i) {
+            int leaves = 0;
+            for (int a = 0; a < 3; ++a) {
+                int to = pos[a] + L.c[i][a];
+                if (open[a] && (to < 0 || to >= size[a])) leaves = 1;
+            }
+            if (leaves) continue;
+            long dst = neighbour(x, y, z, L.c[i], nx, ny, nz);
+            for (int k = 0; k < ORC_NVAR_IDEAL; ++k)
+                fout[(long)(k * q + i) * N + dst] = fs[k * q + i];
+        }
+    }
+    /* the directions entering across open faces get the boundary equilibrium */
+#pragma omp parallel for num_threads(nthreads) schedule(static)
+    for (long cell = 0; cell < N; ++cell) {
+        int x = (int)(cell % nx);
+        int y = (int)((cell / nx) % ny);
+        int z = (int)(cell / ((long)nx * ny));
+        int normal[3] = {0, 0, 0};
+        int any = 0;
+        for (int face = 0; face < 2 * dim; ++face) {
+            int a = face / 2;
+            if (!open[a] || !on_face(face, x, y, z, nx, ny, nz)) continue;
+            normal[a] += (face % 2 == 0) ? 1 : -1; /* inward */
+            any = 1;
+        }
+        if (!any) continue;
+        long nb = (long)(x + normal[0]) + (long)nx * ((long)(y + normal[1]) + (long)ny * (long)(z + normal[2]));
+        double Qn[ORC_NVAR_IDEAL];
+        for (int k = 0; k < ORC_NVAR_IDEAL; ++k) {
+            Qn[k] = 0.0;
+            for (int i = 0; i < q; ++i) Qn[k] += fout[(long)(k * q + i) * N + nb]; /* Eq. 4 */
+        }
+        for (int face = 0; face < 2 * dim; ++face) {
+            int a = face / 2;
+            if (!open[a] || !on_face(face, x, y, z, nx, ny, nz)) continue;
+            int inward[3] = {0, 0, 0};
+            inward[a] = (face % 2 == 0) ? 1 : -1;
+            int din = -1;
+            for (int i = 0; i < q; ++i)
+                if (L.c[i][0] == inward[0] && L.c[i][1] == inward[1] && L.c[i][2] == inward[2]) din = i;
+            double Qb[ORC_NVAR_IDEAL];
+            double feq[ORC_NVAR_IDEAL][ORC_QMAX];
+            for (int k = 0; k < ORC_NVAR_IDEAL; ++k)
+                Qb[k] = ((mask[face] >> k) & 1u) ? vals[ORC_NVAR_IDEAL * face + k] : Qn[k];
+            ideal_feq(&L, gamma, Qb, feq); /* Eq. 3 */
+            for (int k = 0; k < ORC_NVAR_IDEAL; ++k) fout[(long)(k * q + din) * N + cell] = feq[k][din];
+        }
+    }
+    return 0;
+}
+
+int orc_open_run(int dim, int nx, int ny, int nz, double gamma, const double *tau, const double *src,
+                 const int *open, const unsigned *mask, const double *vals, const double *Q0, int nsteps,
+                 double *Qout, int nthreads)
+{
+    if (check_dims(dim, nx, ny, nz) || nsteps < 0) return -1;
+    int q = dim == 2 ? 5 : 7;
+    long N = (long)nx * ny * nz;
+    double *a = (double *)malloc(sizeof(double) * ORC_NVAR_IDEAL * q * N);
+    double *b = (double *)malloc(sizeof(double) * ORC_NVAR_IDEAL * q * N);
+    if (!a || !b) {
+        free(a);
+        free(b);
+        return -2;
+    }
+    orc_ideal_init(dim, nx, ny, nz, gamma, Q0, a);
+    int rc = 0;
+    for (int s = 0; s < nsteps && rc == 0; ++s) {
+        rc = orc_open_step(dim, nx, ny, nz, gamma, tau, src, open, mask, vals, a, b, nthreads);
+        double *t = a;
+        a = b;
+        b = t;
+    }
+    if (rc == 0) orc_ideal_moments(dim, nx, ny, nz, a, Qout);
+    free(a);
+    free(b);
+    return rc;
 }
 
 /* ------------------------------------------------------------------ */

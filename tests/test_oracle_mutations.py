@@ -9,6 +9,7 @@ import pytest
 
 import oracle
 import test_oracle_hlbm as H
+import test_oracle_open as O
 import test_oracle_pins as P
 import test_oracle_powell as W
 import test_oracle_resistive as R
@@ -51,6 +52,16 @@ HLBM_PINS = [
     lambda o: H.test_mass_is_conserved_exactly(),
     lambda o: H.test_channel_between_homogenised_walls_is_parabolic_with_walls_at_d_half(),
     lambda o: H.test_uniform_cell_pressure_follows_the_relaxation_of_the_blend(0.6),
+]
+
+OPEN_PINS = [
+    lambda o: O.test_uniform_state_is_a_fixed_point(
+        (12, 16), [(O.ALL, O.BG), (0, None), (0b10110, O.BG), (0b01001, O.BG)]),
+    lambda o: O.test_open_run_equals_the_periodic_run_inside_the_light_cone(
+        (40, 40), [(O.ALL, O.BG), (0, None), (0b10110, O.BG), (0b01001, O.BG)], 12),
+    lambda o: O.test_supersonic_inflow_flushes_the_domain_to_the_inflow_state(),
+    lambda o: O.test_zero_gradient_faces_let_a_pulse_leave(),
+    lambda o: O.test_oracle_matches_numpy_restatement((5, 6, 7)),
 ]
 
 # (name, original text, planted mistake, which pin family must catch it)
@@ -111,6 +122,19 @@ MUTANTS = [
      "Qhat[4] = Q[4];", HLBM_PINS),
     ("blended energy misses the field energy", "Qhat[4] = p / (gamma - 1.0) + 0.5 * rho * uh2 + 0.5 * Bh2;",
      "Qhat[4] = p / (gamma - 1.0) + 0.5 * rho * uh2;", HLBM_PINS),
+    ("boundary fills the leaving direction", "inward[a] = (face % 2 == 0) ? 1 : -1;",
+     "inward[a] = (face % 2 == 0) ? -1 : 1;", OPEN_PINS),
+    ("Dirichlet and Neumann swapped",
+     "Qb[k] = ((mask[face] >> k) & 1u) ? vals[ORC_NVAR_IDEAL * face + k] : Qn[k];",
+     "Qb[k] = ((mask[face] >> k) & 1u) ? Qn[k] : vals[ORC_NVAR_IDEAL * face + k];", OPEN_PINS),
+    ("Neumann copies the boundary cell itself",
+     "long nb = (long)(x + normal[0]) + (long)nx * ((long)(y + normal[1]) + (long)ny * (long)(z + normal[2]));",
+     "long nb = cell;", OPEN_PINS),
+    ("every face takes face 0's values",
+     "Qb[k] = ((mask[face] >> k) & 1u) ? vals[ORC_NVAR_IDEAL * face + k] : Qn[k];",
+     "Qb[k] = ((mask[face] >> k) & 1u) ? vals[k] : Qn[k];", OPEN_PINS),
+    ("boundary state from the pre-stream state", "Qn[k] += fout[(long)(k * q + i) * N + nb]; /* Eq. 4 */",
+     "Qn[k] += fin[(long)(k * q + i) * N + nb]; /* Eq. 4 */", OPEN_PINS),
     ("Powell source without weight", "fout[k * L->q + i] = f + (feq[k][i] - f) / tau[k] + L->w[i] * sk;",
      "fout[k * L->q + i] = f + (feq[k][i] - f) / tau[k] + sk;", POWELL_PINS),
 ]
