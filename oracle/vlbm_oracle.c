@@ -714,9 +714,9 @@ int orc_open_step(int dim, int nx, int ny, int nz, double gamma, const double *t
                 if (open[a] && (to < 0 || to >= size[a])) leaves = 1;
             }
             if (leaves) continue;
-            long dst = neighbour(x, y, z, L.c[i], nx, ny, nz);
+            long arrive = neighbour(x, y, z, L.c[i], nx, ny, nz);
             for (int k = 0; k < ORC_NVAR_IDEAL; ++k)
-                fout[(long)(k * q + i) * N + dst] = fs[k * q + i];
+                fout[(long)(k * q + i) * N + arrive] = fs[k * q + i];
         }
     }
     /* the directions entering across open faces get the boundary equilibrium */
