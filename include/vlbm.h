@@ -315,6 +315,26 @@ vlbm_status vlbm_set_solid(vlbm_ctx *ctx, const float *solid_dev);
 vlbm_status vlbm_porosity_from_distance(const float *phi_dev, int64_t n, double eps_h, float *d_dev,
                                         void *stream);
 
+/* Static equilibrium boundaries (sec. 2.4, "Static boundaries").  Faces:
+ * 0 x-, 1 x+, 2 y-, 3 y+, 4 z-, 5 z+ (2-D: 0..3).  Every face starts periodic.
+ * kind VLBM_BC_EQUILIBRIUM opens the face: after each step, every cell on it
+ * receives, in the one direction that enters the domain across the face, the
+ * equilibrium f_eq_i (Eq. 3) of the boundary state Q_b, where Q_b,k is
+ * values[k] if bit k of dirichlet_mask is set (Dirichlet) and otherwise the
+ * moment Q_k of the cell one step along the discrete inward normal (Neumann,
+ * "zero gradient"; at an edge or a corner the normal is the sum of the open
+ * faces' normals, so the copied cell is never a boundary cell).  Populations
+ * leaving across an open face are dropped.  values: 8 host doubles
+ * (rho, rho u, e_tot, B), read during the call; NULL when the mask is 0.
+ * Both faces of an axis must be open or both periodic when vlbm_step runs
+ * (VLBM_ERR_ARG there otherwise); an open axis needs at least 3 cells.
+ * Single ideal-MHD contexts with F32 or F64 storage, with or without
+ * homogenised solids; VLBM_ERR_UNSUPPORTED for other models, storages,
+ * batches or with a closure attached.  kind VLBM_BC_PERIODIC closes the face
+ * again.  Each step with an open face launches one more (small) kernel. */
+typedef enum { VLBM_BC_PERIODIC = 0, VLBM_BC_EQUILIBRIUM = 1 } vlbm_bc_kind;
+vlbm_status vlbm_set_boundary(vlbm_ctx *ctx, int face, int kind, unsigned dirichlet_mask, const double *values);
+
 /* Attach (cl) or detach (NULL) a closure to a 3-D ideal-MHD context with F32
  * storage and the closure's grid: every following vlbm_step evaluates the
  * network on the current state and applies the correction in the fused

@@ -82,8 +82,8 @@ def _configure(L):
     L.orc_hlbm_target.restype = None
     L.orc_hlbm_step.argtypes = [i, i, i, i, d, p, p, p, p, p, i]
     L.orc_hlbm_run.argtypes = [i, i, i, i, d, p, p, p, p, i, p, i]
-    L.orc_open_step.argtypes = [i, i, i, i, d, p, p, p, p, p, p, p, i]
-    L.orc_open_run.argtypes = [i, i, i, i, d, p, p, p, p, p, p, i, p, i]
+    L.orc_open_step.argtypes = [i, i, i, i, d, p, p, p, p, p, p, p, p, i]
+    L.orc_open_run.argtypes = [i, i, i, i, d, p, p, p, p, p, p, p, i, p, i]
     return L
 
 
@@ -424,21 +424,25 @@ def _faces(faces, dim):
     return open_, mask, vals
 
 
-def open_step(f: np.ndarray, gamma: float, tau, faces, src=None, nthreads: int = 1) -> np.ndarray:
-    """One step with open faces (equilibrium Dirichlet / Neumann boundaries)."""
+def open_step(f: np.ndarray, gamma: float, tau, faces, src=None, solid=None, nthreads: int = 1) -> np.ndarray:
+    """One step with open faces (equilibrium Dirichlet / Neumann boundaries), optionally
+    with homogenised solids in the domain."""
     f = _f64(f)
     dim, nx, ny, nz = _dims(f.shape[2:])
     open_, mask, vals = _faces(faces, dim)
     out = np.zeros_like(f)
     tau = _f64(np.broadcast_to(np.asarray(tau, dtype=np.float64), (8,)))
     s = _f64(src) if src is not None else None
+    sd = _solid(solid, f.shape[2:]) if solid is not None else None
     _check(lib().orc_open_step(dim, nx, ny, nz, gamma, _ptr(tau), _ptr(s) if s is not None else None,
+                               _ptr(sd) if sd is not None else None,
                                open_.ctypes.data_as(ctypes.c_void_p), mask.ctypes.data_as(ctypes.c_void_p),
                                _ptr(vals), _ptr(f), _ptr(out), nthreads), "open_step")
     return out
 
 
-def open_run(Q0: np.ndarray, gamma: float, tau, faces, nsteps: int, src=None, nthreads: int = 1) -> np.ndarray:
+def open_run(Q0: np.ndarray, gamma: float, tau, faces, nsteps: int, src=None, solid=None,
+             nthreads: int = 1) -> np.ndarray:
     """Moments [8, ...] after nsteps steps with open faces, started from f_eq(Q0)."""
     Q0 = _f64(Q0)
     dim, nx, ny, nz = _dims(Q0.shape[1:])
@@ -446,7 +450,9 @@ def open_run(Q0: np.ndarray, gamma: float, tau, faces, nsteps: int, src=None, nt
     out = np.zeros_like(Q0)
     tau = _f64(np.broadcast_to(np.asarray(tau, dtype=np.float64), (8,)))
     s = _f64(src) if src is not None else None
+    sd = _solid(solid, Q0.shape[1:]) if solid is not None else None
     _check(lib().orc_open_run(dim, nx, ny, nz, gamma, _ptr(tau), _ptr(s) if s is not None else None,
+                              _ptr(sd) if sd is not None else None,
                               open_.ctypes.data_as(ctypes.c_void_p), mask.ctypes.data_as(ctypes.c_void_p),
                               _ptr(vals), _ptr(Q0), nsteps, _ptr(out), nthreads), "open_run")
     return out

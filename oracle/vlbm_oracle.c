@@ -663,6 +663,7 @@ int orc_hlbm_run(int dim, int nx, int ny, int nz, double gamma, const double *ta
  * points diagonally inwards), so the copied cell is never on an open face
  * when every open axis has at least three cells.
  *
+ * solid (or NULL): homogenised solids [7][N] as in orc_hlbm_step.
  * One step: every cell collides; each post-collision population moves to
  * x + c_i, and one whose destination lies beyond an open face leaves the
  * domain; then every cell on an open face receives, in the direction that
@@ -682,8 +683,8 @@ static int on_face(int face, int x, int y, int z, int nx, int ny, int nz)
 }
 
 int orc_open_step(int dim, int nx, int ny, int nz, double gamma, const double *tau, const double *src,
-                  const int *open, const unsigned *mask, const double *vals, const double *fin, double *fout,
-                  int nthreads)
+                  const double *solid, const int *open, const unsigned *mask, const double *vals,
+                  const double *fin, double *fout, int nthreads)
 {
     orc_lattice L;
     if (check_dims(dim, nx, ny, nz)) return -1;
@@ -706,7 +707,16 @@ int orc_open_step(int dim, int nx, int ny, int nz, double gamma, const double *t
         double fs[ORC_NVAR_IDEAL * ORC_QMAX];
         for (int k = 0; k < ORC_NVAR_IDEAL; ++k)
             for (int i = 0; i < q; ++i) fc[k * q + i] = fin[(long)(k * q + i) * N + cell];
-        ideal_collide(&L, gamma, tau, src, fc, fs);
+        if (solid) { /* homogenised solids in the domain (sec. 2.4, "Homogenization") */
+            double uB[3], BB[3];
+            for (int a = 0; a < 3; ++a) {
+                uB[a] = solid[(long)(1 + a) * N + cell];
+                BB[a] = solid[(long)(4 + a) * N + cell];
+            }
+            hlbm_collide(&L, gamma, tau, src, solid[cell], uB, BB, fc, fs);
+        } else {
+            ideal_collide(&L, gamma, tau, src, fc, fs);
+        }
         for (int i = 0; i < q; ++i) {
             int leaves = 0;
             for (int a = 0; a < 3; ++a) {
@@ -760,8 +770,8 @@ int orc_open_step(int dim, int nx, int ny, int nz, double gamma, const double *t
 }
 
 int orc_open_run(int dim, int nx, int ny, int nz, double gamma, const double *tau, const double *src,
-                 const int *open, const unsigned *mask, const double *vals, const double *Q0, int nsteps,
-                 double *Qout, int nthreads)
+                 const double *solid, const int *open, const unsigned *mask, const double *vals,
+                 const double *Q0, int nsteps, double *Qout, int nthreads)
 {
     if (check_dims(dim, nx, ny, nz) || nsteps < 0) return -1;
     int q = dim == 2 ? 5 : 7;
@@ -776,7 +786,7 @@ int orc_open_run(int dim, int nx, int ny, int nz, double gamma, const double *ta
     orc_ideal_init(dim, nx, ny, nz, gamma, Q0, a);
     int rc = 0;
     for (int s = 0; s < nsteps && rc == 0; ++s) {
-        rc = orc_open_step(dim, nx, ny, nz, gamma, tau, src, open, mask, vals, a, b, nthreads);
+        rc = orc_open_step(dim, nx, ny, nz, gamma, tau, src, solid, open, mask, vals, a, b, nthreads);
         double *t = a;
         a = b;
         b = t;

@@ -417,6 +417,90 @@ __global__ void k_ideal_moments(const ReadArgs<D, S> a, int64_t c0, int64_t coun
     for (int k = 0; k < NL; ++k) out[k * ostride + t] = (double)cell_moment<D, S>(a, cell, nb, k);
 }
 
+// Static equilibrium boundaries (sec. 2.4, "Static boundaries").  Faces
+// x-, x+, y-, y+, z-, z+; both faces of an open axis are open.
+struct OpenFaces {
+    int open[3];          // axis open
+    unsigned mask[6];     // bit k set: Q_k Dirichlet at vals[face][k]; clear: Neumann
+    double vals[6][8];
+    int64_t count[6];     // cells on the face (0 for a periodic face)
+    double gm1;
+};
+
+// After a step, every cell on an open face receives, in the direction entering
+// across that face, f_eq_i of the face's boundary state (Eq. 3): Q_k set
+// (Dirichlet) or the moment of the cell one step along the discrete inward
+// normal (Neumann; diagonal at edges and corners, so that cell is never on an
+// open face).  The value goes to the slot this cell reads for that direction in
+// the next step: (i, x) at even parity, (opp i, x - c_i) at odd parity, where
+// periodic addressing puts x - c_i on the opposite face.  Only this cell reads
+// that slot and no thread of the launch reads it, so the pass races neither
+// with itself nor with the step.  One thread per (face, cell); blockIdx.y = face.
+template <int D, class S>
+__global__ void k_open_fill(const ReadArgs<D, S> a, const OpenFaces o, unsigned *flags)
+{
+    using R = typename ComputeOf<S>::T;
+    constexpr int Q = AxisSet<D>::Q;
+    const int face = blockIdx.y;
+    const int ax = face >> 1;
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= o.count[face]) return;
+    const int n[3] = {a.nx, a.ny, a.nz};
+    const int u0 = ax == 0 ? 1 : 0, u1 = ax == 2 ? 1 : 2;  // the in-face axes
+    int pos[3];
+    pos[ax] = (face & 1) ? n[ax] - 1 : 0;
+    pos[u0] = (int)(t % n[u0]);
+    pos[u1] = (int)(t / n[u0]);
+    int nrm[3] = {0, 0, 0};
+#pragma unroll
+    for (int b = 0; b < D; ++b)
+        if (o.open[b]) nrm[b] = pos[b] == 0 ? 1 : (pos[b] == n[b] - 1 ? -1 : 0);
+    const int64_t cell = pos[0] + (int64_t)a.nx * (pos[1] + (int64_t)a.ny * pos[2]);
+    const int xn = pos[0] + nrm[0], yn = pos[1] + nrm[1], zn = pos[2] + nrm[2];
+    const int64_t ncell = xn + (int64_t)a.nx * (yn + (int64_t)a.ny * zn);
+    int64_t nb[Q];
+    neighbours<D>(xn, yn, zn, a.nx, a.ny, a.nz, ncell, nb);
+    R q[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+        q[k] = ((o.mask[face] >> k) & 1u) ? (R)o.vals[face][k] : cell_moment<D, S>(a, ncell, nb, k);
+
+    // the flux of Eq. 12 along the face normal
+    const R rho = q[0];
+    const R ir = R(1) / rho;
+    const R u[3] = {q[1] * ir, q[2] * ir, q[3] * ir};
+    const R B[3] = {q[5], q[6], q[7]};
+    const R B2 = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
+    const R mu = q[1] * u[0] + q[2] * u[1] + q[3] * u[2];
+    const R uB = u[0] * B[0] + u[1] * B[1] + u[2] * B[2];
+    const R p = (R)o.gm1 * (q[4] - R(0.5) * mu - R(0.5) * B2);
+    if (!(rho > R(0)) || !(p > R(0))) atomicOr(flags, kFlagNonPhysical);
+    const R pt = p + R(0.5) * B2;
+    R phi[8];
+    phi[0] = q[1 + ax];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        phi[1 + b] = q[1 + ax] * u[b] - B[ax] * B[b] + (ax == b ? pt : R(0));
+        phi[5 + b] = (ax == b) ? R(0) : u[ax] * B[b] - B[ax] * u[b];
+    }
+    phi[4] = (q[4] + pt) * u[ax] - B[ax] * uB;
+
+    const int din = (face & 1) ? 2 * ax + 2 : 2 * ax + 1;  // +e_ax enters at the low face
+    const R half = (face & 1) ? R(-AxisSet<D>::w1 / AxisSet<D>::cs2) : R(AxisSet<D>::w1 / AxisSet<D>::cs2);
+    int j = din;
+    int64_t at = cell;
+    if (a.parity) {
+        int64_t own[Q];
+        neighbours<D>(pos[0], pos[1], pos[2], a.nx, a.ny, a.nz, cell, own);
+        j = opp_axis(din);
+        at = own[opp_axis(din)];
+    }
+    S *pop = static_cast<S *>(const_cast<void *>(a.pop));
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+        Codec<S>::store(pop + (int64_t)(k * Q + j) * a.stride + at, R(AxisSet<D>::w1) * q[k] + half * phi[k]);
+}
+
 // HLBM porosity of the signed distance phi (sec. 2.4): 0 in the solid, 1 in the
 // fluid, phi / eps_h + 1/2 across the transition of width eps_h.
 __global__ void k_porosity(const float *__restrict__ phi, int64_t n, float eps_h, float *__restrict__ d)
@@ -692,6 +776,32 @@ template <int D, class S> vlbm_status sums_t(vlbm_ctx *c, int di, double *sums)
     return finish_sums(c, 8, sums);
 }
 
+template <int D, class S> vlbm_status open_fill_t(vlbm_ctx *c, int parity)
+{
+    ReadArgs<D, S> a = make_read_args<D, S>(c, 0);
+    a.parity = parity;  // explicit: graph capture does not advance c->step
+    OpenFaces o{};
+    const Domain &d = c->dom[0];
+    const int64_t n[3] = {d.nx, d.ny, d.nz};
+    int64_t most = 0;
+    for (int f = 0; f < 2 * D; ++f) {
+        if (c->face_kind[f] != VLBM_BC_EQUILIBRIUM) continue;
+        const int ax = f >> 1;
+        o.open[ax] = 1;
+        o.mask[f] = c->face_mask[f];
+        for (int k = 0; k < 8; ++k) o.vals[f][k] = c->face_vals[f][k];
+        o.count[f] = n[0] * n[1] * n[2] / n[ax];
+        most = std::max(most, o.count[f]);
+    }
+    o.gm1 = d.gamma - 1.0;
+    if (most == 0) return VLBM_OK;
+    const int threads = 256;
+    const dim3 grid((unsigned)((most + threads - 1) / threads), (unsigned)(2 * D));
+    k_open_fill<D, S><<<grid, threads, 0, c->stream>>>(a, o, c->d_flags);
+    c->launches++;
+    return cuda_check(c, cudaGetLastError(), "boundary fill launch");
+}
+
 // dispatch on (dim, storage)
 template <template <int, class> class F, class... A> vlbm_status dispatch(vlbm_ctx *c, A... args)
 {
@@ -733,6 +843,13 @@ template <int D, class S> struct GatherF {
 };
 template <int D, class S> struct SumsF {
     static vlbm_status run(vlbm_ctx *c, int di, double *sums) { return sums_t<D, S>(c, di, sums); }
+};
+template <int D, class S> struct OpenF {
+    static vlbm_status run(vlbm_ctx *c, int parity)
+    {
+        if constexpr (Codec<S>::kDev) return fail(c, VLBM_ERR_UNSUPPORTED, "open faces need F32 or F64 storage");
+        else return open_fill_t<D, S>(c, parity);
+    }
 };
 
 }  // namespace
@@ -789,6 +906,15 @@ vlbm_status ideal_gather(vlbm_ctx *c, int d, const int64_t *cells_dev, int n, do
 }
 
 vlbm_status ideal_sums(vlbm_ctx *c, int d, double *sums_dev) { return dispatch<SumsF>(c, d, sums_dev); }
+
+bool any_open_face(const vlbm_ctx *c)
+{
+    for (int f = 0; f < 6; ++f)
+        if (c->face_kind[f] == VLBM_BC_EQUILIBRIUM) return true;
+    return false;
+}
+
+vlbm_status open_fill(vlbm_ctx *c, int parity) { return dispatch<OpenF>(c, parity); }
 
 vlbm_status porosity_from_distance(const float *phi, int64_t n, double eps_h, float *d, cudaStream_t s)
 {

@@ -6,6 +6,7 @@
 // bounded chunks, checkpoints.  Every arithmetic step of the method runs in
 // the kernels of k_ideal.cu, k_resistive.cu and k_batch.cu.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 
 #include "vlbm_internal.cuh"
@@ -192,7 +193,9 @@ vlbm_status launch_step(vlbm_ctx *c, int parity)
     if (c->batched) return batch_step(c, parity, c->tune_choice);
     if (c->model == VLBM_RESISTIVE) return resistive_step(c, parity);
     if (c->closure) return closure_step(c, parity);
-    return ideal_step(c, parity);
+    vlbm_status s = ideal_step(c, parity);
+    if (s == VLBM_OK && any_open_face(c)) s = open_fill(c, parity ^ 1);  // for the next step's reads
+    return s;
 }
 
 vlbm_status init_range(vlbm_ctx *c, int d, const double *Q, int64_t c0, int64_t n, int64_t qs)
@@ -240,13 +243,17 @@ void drop_graphs(vlbm_ctx *c)
 {
     for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second);
     c->graphs.clear();
+    c->graph_launches.clear();
 }
 
-cudaGraphExec_t get_graph(vlbm_ctx *c, int parity, int len)
+cudaGraphExec_t get_graph(vlbm_ctx *c, int parity, int len, int64_t *launches)
 {
     const int key = parity * 1024 + len;
     auto it = c->graphs.find(key);
-    if (it != c->graphs.end()) return it->second;
+    if (it != c->graphs.end()) {
+        *launches = c->graph_launches[key];
+        return it->second;
+    }
     if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
         cudaGetLastError();
         return nullptr;
@@ -254,6 +261,7 @@ cudaGraphExec_t get_graph(vlbm_ctx *c, int parity, int len)
     const int64_t before = c->launches;
     bool ok = true;
     for (int s = 0; s < len && ok; ++s) ok = launch_step(c, (parity + s) & 1) == VLBM_OK;
+    const int64_t captured = c->launches - before;
     c->launches = before;
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(c->stream, &g);
@@ -270,6 +278,8 @@ cudaGraphExec_t get_graph(vlbm_ctx *c, int parity, int len)
         return nullptr;
     }
     c->graphs[key] = exec;
+    c->graph_launches[key] = captured;
+    *launches = captured;
     return exec;
 }
 
@@ -464,17 +474,21 @@ vlbm_status vlbm_step(vlbm_ctx *c, int n)
     if (!c || n < 0) return VLBM_ERR_ARG;
     poll_flags(c);
     if (c->sticky != VLBM_OK) return c->sticky;
+    for (int a = 0; a < 3; ++a)
+        if ((c->face_kind[2 * a] == VLBM_BC_EQUILIBRIUM) != (c->face_kind[2 * a + 1] == VLBM_BC_EQUILIBRIUM))
+            return fail(c, VLBM_ERR_ARG, "one face of an axis is open and the other periodic");
     const bool graphs = c->stream != nullptr && c->stream != cudaStreamLegacy &&
                         c->stream != cudaStreamPerThread;
     int left = n;
     while (left > 0) {
         if (graphs && left >= kGraphLen) {
-            cudaGraphExec_t g = get_graph(c, (int)(c->step & 1), kGraphLen);
+            int64_t in_graph = 0;
+            cudaGraphExec_t g = get_graph(c, (int)(c->step & 1), kGraphLen, &in_graph);
             if (g) {
                 vlbm_status s = cuda_check(c, cudaGraphLaunch(g, c->stream), "graph launch");
                 if (s != VLBM_OK) return s;
                 c->step += kGraphLen;
-                c->launches += kGraphLen;
+                c->launches += in_graph;
                 left -= kGraphLen;
                 continue;
             }
@@ -694,6 +708,7 @@ vlbm_status vlbm_set_closure(vlbm_ctx *c, vlbm_closure *cl)
         if (c->dom[0].nx != nx || c->dom[0].ny != ny || c->dom[0].nz != nz)
             return fail(c, VLBM_ERR_ARG, "closure grid differs from the context grid");
         if (c->solid) return fail(c, VLBM_ERR_UNSUPPORTED, "a closure and homogenised solids do not combine");
+        if (any_open_face(c)) return fail(c, VLBM_ERR_UNSUPPORTED, "a closure and open faces do not combine");
     }
     drop_graphs(c);
     c->closure = cl;
@@ -711,6 +726,32 @@ vlbm_status vlbm_set_solid(vlbm_ctx *c, const float *solid_dev)
     }
     drop_graphs(c);  // captured steps hold the previous pointer
     c->solid = solid_dev;
+    return VLBM_OK;
+}
+
+vlbm_status vlbm_set_boundary(vlbm_ctx *c, int face, int kind, unsigned dirichlet_mask, const double *values)
+{
+    if (!c) return VLBM_ERR_ARG;
+    if (face < 0 || face >= 2 * c->dim) return fail(c, VLBM_ERR_ARG, "no such face");
+    if (kind != VLBM_BC_PERIODIC && kind != VLBM_BC_EQUILIBRIUM) return fail(c, VLBM_ERR_ARG, "no such boundary kind");
+    if (kind == VLBM_BC_EQUILIBRIUM) {
+        if (c->batched || c->model != VLBM_IDEAL || (c->storage != VLBM_F32 && c->storage != VLBM_F64))
+            return fail(c, VLBM_ERR_UNSUPPORTED,
+                        "open faces apply to single ideal-MHD contexts with F32 or F64 storage");
+        if (c->closure) return fail(c, VLBM_ERR_UNSUPPORTED, "a closure and open faces do not combine");
+        const int64_t extent[3] = {c->dom[0].nx, c->dom[0].ny, c->dom[0].nz};
+        if (extent[face / 2] < 3) return fail(c, VLBM_ERR_ARG, "an open axis needs at least 3 cells");
+        if ((dirichlet_mask & ~0xFFu) != 0) return fail(c, VLBM_ERR_ARG, "Dirichlet mask has bits beyond the 8 fields");
+        if (dirichlet_mask != 0 && !values) return fail(c, VLBM_ERR_ARG, "Dirichlet values missing");
+        for (int k = 0; k < 8; ++k)
+            if (((dirichlet_mask >> k) & 1u) && !std::isfinite(values[k]))
+                return fail(c, VLBM_ERR_ARG, "Dirichlet value not finite");
+    }
+    drop_graphs(c);  // captured steps hold the previous faces
+    c->face_kind[face] = kind;
+    c->face_mask[face] = kind == VLBM_BC_EQUILIBRIUM ? dirichlet_mask : 0u;
+    for (int k = 0; k < 8; ++k)
+        c->face_vals[face][k] = (kind == VLBM_BC_EQUILIBRIUM && ((dirichlet_mask >> k) & 1u)) ? values[k] : 0.0;
     return VLBM_OK;
 }
 

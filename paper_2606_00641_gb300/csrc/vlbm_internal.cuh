@@ -153,6 +153,7 @@ struct vlbm_ctx {
     std::string err;
 
     std::map<int, cudaGraphExec_t> graphs;  // key: parity*1024 + length
+    std::map<int, int64_t> graph_launches;  // kernels one replay of that graph launches
 
     // batched form
     std::vector<void *> tile_tables;    // per tile shape: device (domain, first cell) pairs
@@ -164,6 +165,10 @@ struct vlbm_ctx {
     // learned flux closure applied in every step (not owned)
     struct vlbm_closure *closure = nullptr;
     const float *solid = nullptr;       // homogenised solids: [7][N] caller-owned fields, or null
+    // static equilibrium boundaries, faces x-, x+, y-, y+, z-, z+
+    int face_kind[6] = {0, 0, 0, 0, 0, 0};  // VLBM_BC_PERIODIC or VLBM_BC_EQUILIBRIUM
+    unsigned face_mask[6] = {0, 0, 0, 0, 0, 0};  // bit k: Q_k Dirichlet (else Neumann)
+    double face_vals[6][8] = {};             // Dirichlet values
 
     // allocator
     std::vector<std::pair<void *, size_t>> owned;
@@ -202,6 +207,8 @@ int batch_num_choices();
 vlbm_status ideal_step_corrected(vlbm_ctx *c, int parity, const float *dphi);
 // porosity of the signed distance (HLBM), elementwise
 vlbm_status porosity_from_distance(const float *phi, int64_t n, double eps_h, float *d, cudaStream_t s);
+bool any_open_face(const vlbm_ctx *c);
+vlbm_status open_fill(vlbm_ctx *c, int parity);
 // closure input features of a 3-D FP32 context straight from its populations:
 // x[cell][k] = BF16((Q_k - mu_k) * inv_sigma_k), Q_k summed in FP32 as by ideal_moments
 vlbm_status ideal_features(vlbm_ctx *c, const float *mu, const float *inv_sigma, __nv_bfloat16 *x);

@@ -33,6 +33,9 @@ VLBM_ERR_UNSUPPORTED = 8
 VLBM_IDEAL = 0
 VLBM_RESISTIVE = 1
 VLBM_IDEAL_POWELL = 2
+VLBM_BC_PERIODIC = 0
+VLBM_BC_EQUILIBRIUM = 1
+FACES = {"x-": 0, "x+": 1, "y-": 2, "y+": 3, "z-": 4, "z+": 5}
 
 VLBM_F64 = 0
 VLBM_F32 = 1
@@ -151,6 +154,7 @@ def load(build: bool = True):
         "vlbm_closure_train_step_ctx": (i, [P, P, P, ctypes.POINTER(d)]),
         "vlbm_set_closure": (i, [P, P]),
         "vlbm_set_solid": (i, [P, P]),
+        "vlbm_set_boundary": (i, [P, i, i, ctypes.c_uint, P]),
         "vlbm_porosity_from_distance": (i, [P, ctypes.c_int64, d, P, P]),
         "vlbm_closure_destroy": (None, [P]),
         "vlbm_restrict": (i, [P, i, i, i, i, P, P]),
@@ -411,6 +415,19 @@ def vlbm_restrict(Qf_ptr: int, shape, factor: int, Qc_ptr: int, stream: int = 0)
                                 ctypes.c_void_p(stream) if stream else None), "vlbm_restrict")
 
 
+def vlbm_set_boundary(ctx: int, face, kind: int, dirichlet_mask: int = 0, values=None) -> None:
+    """Open (VLBM_BC_EQUILIBRIUM) or close (VLBM_BC_PERIODIC) one face (sec. 2.4,
+    "Static boundaries"); face 0..5 or "x-", "x+", ...; bit k of the mask makes Q_k
+    Dirichlet at values[k], the others are copied from the next cell inwards."""
+    f = FACES[face] if isinstance(face, str) else int(face)
+    buf = None
+    if values is not None:
+        buf = np.ascontiguousarray(np.asarray(values, dtype=np.float64).reshape(8))
+    _check(load().vlbm_set_boundary(ctx, f, int(kind), int(dirichlet_mask),
+                                    buf.ctypes.data_as(ctypes.c_void_p) if buf is not None else None),
+           "vlbm_set_boundary", ctx)
+
+
 def vlbm_set_solid(ctx: int, solid_ptr) -> None:
     """Attach homogenised solid fields ([7][N] float32 on the device: d, uB, BB) or detach (None)."""
     if solid_ptr:
@@ -536,6 +553,10 @@ class Context:
 
     def conservation(self, domain: int = 0) -> np.ndarray:
         return vlbm_conservation(self.ptr, domain)
+
+    def set_boundary(self, face, kind: int = VLBM_BC_EQUILIBRIUM, dirichlet_mask: int = 0, values=None) -> None:
+        """Open or close one face; see ``vlbm_set_boundary``."""
+        vlbm_set_boundary(self.ptr, face, kind, dirichlet_mask, values)
 
     def set_solid(self, solid_ptr) -> None:
         """Attach ([7][N] float32 device fields d, uB, BB) or detach (None) homogenised solids.
