@@ -57,7 +57,7 @@ def parse():
     ap.add_argument("--form-steps", type=int, default=20)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the channel, batched and closure forms")
-    ap.add_argument("--extras", default="channel,batch,closure,powell,hlbm",
+    ap.add_argument("--extras", default="channel,batch,closure,powell,hlbm,open",
                     help="which other workloads to run (comma list of channel, batch, closure)")
     ap.add_argument("--closure-fine", type=int, default=512, help="fine grid side of the closure workload")
     ap.add_argument("--no-cpu", action="store_true")
@@ -247,6 +247,40 @@ def powell_form(args, vlbm, fields, torch, stream, hbm_peak):
                         "headline workload, D = 0 at start" % n,
             "init_status": vlbm.status_string(st), "status": status, "glups": gl, "steps": steps,
             "bytes_per_cell": bytes_cell, "roofline_frac": gl * 1e9 * bytes_cell / (hbm_peak * 1e9)}
+
+
+def open_form(args, vlbm, fields, torch, stream, hbm_peak):
+    """Headline workload with open faces (sec. 2.4, "Static boundaries"): x- a
+    Dirichlet reservoir at the mean state, the other five faces zero-gradient."""
+    n = args.size
+    shape = (n, n, n)
+    f0 = fields.ideal_fields(shape, args.seed, gamma=5.0 / 3.0, mach=2.0, beta=1.0, cfl=0.2,
+                             k_rho=4, k_u=4, k_b=4, device=torch.device("cuda"))
+    mean = f0.Q.reshape(8, -1).mean(1).cpu().numpy()
+    p = vlbm.make_params(shape=shape, storage="f32", gamma=f0.gamma, tau=0.51, stream=stream.cuda_stream)
+    ctx = vlbm.Context(p)
+    st = vlbm.vlbm_init_fields_device(ctx.ptr, 0, f0.Q.data_ptr())
+    del f0
+    ctx.set_boundary("x-", vlbm.VLBM_BC_EQUILIBRIUM, 0xFF, mean)
+    for face in ("x+", "y-", "y+", "z-", "z+"):
+        ctx.set_boundary(face, vlbm.VLBM_BC_EQUILIBRIUM)
+    vlbm.vlbm_step(ctx.ptr, 4)
+    steps = args.form_steps
+    l0 = vlbm.vlbm_launch_count(ctx.ptr)
+    ms = _time_steps(vlbm, [ctx.ptr], stream, torch, steps, False)
+    launches = vlbm.vlbm_launch_count(ctx.ptr) - l0
+    status = vlbm.status_string(vlbm.vlbm_sync(ctx.ptr))
+    ctx.close()
+    ncell = n ** 3
+    gl = ncell * steps / (ms * 1e-3) / 1e9
+    # the step's 448 B per cell, plus per face cell the boundary pass: the normal
+    # neighbour's 56 populations read and 8 entering populations written
+    bytes_cell = 2 * 56 * 4 + 6 * n * n * (56 + 8) * 4 / ncell
+    return {"workload": "headline workload (%d^3, 8 x D3Q7, FP32, tau 0.51) with all six faces open: x- a "
+                        "Dirichlet reservoir at the mean state, the other faces zero-gradient" % n,
+            "init_status": vlbm.status_string(st), "status": status, "glups": gl, "steps": steps,
+            "launches_per_step": launches / steps, "bytes_per_cell": bytes_cell,
+            "roofline_frac": gl * 1e9 * bytes_cell / (hbm_peak * 1e9)}
 
 
 def blend_initial_state(Q, solid, gamma):
@@ -546,6 +580,8 @@ def main():
             extra["powell_3d"] = powell_form(args, vlbm, fields, torch, stream, hbm_peak)
         if "hlbm" in which:
             extra["hlbm_sphere_3d"] = hlbm_form(args, vlbm, fields, torch, stream, hbm_peak)
+        if "open" in which:
+            extra["open_faces_3d"] = open_form(args, vlbm, fields, torch, stream, hbm_peak)
 
     cpu = None
     if rank == 0 and not args.no_cpu:

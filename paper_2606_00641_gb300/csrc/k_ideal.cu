@@ -437,33 +437,45 @@ struct OpenFaces {
 // that slot and no thread of the launch reads it, so the pass races neither
 // with itself nor with the step.  One thread per (face, cell); blockIdx.y = face.
 template <int D, class S>
-__global__ void k_open_fill(const ReadArgs<D, S> a, const OpenFaces o, unsigned *flags)
+__global__ void k_open_fill(const ReadArgs<D, S> a, const __grid_constant__ OpenFaces o, unsigned *flags)
 {
     using R = typename ComputeOf<S>::T;
     constexpr int Q = AxisSet<D>::Q;
     const int face = blockIdx.y;
     const int ax = face >> 1;
+    const bool high = face & 1;
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= o.count[face]) return;
-    const int n[3] = {a.nx, a.ny, a.nz};
-    const int u0 = ax == 0 ? 1 : 0, u1 = ax == 2 ? 1 : 2;  // the in-face axes
-    int pos[3];
-    pos[ax] = (face & 1) ? n[ax] - 1 : 0;
-    pos[u0] = (int)(t % n[u0]);
-    pos[u1] = (int)(t / n[u0]);
-    int nrm[3] = {0, 0, 0};
-#pragma unroll
-    for (int b = 0; b < D; ++b)
-        if (o.open[b]) nrm[b] = pos[b] == 0 ? 1 : (pos[b] == n[b] - 1 ? -1 : 0);
-    const int64_t cell = pos[0] + (int64_t)a.nx * (pos[1] + (int64_t)a.ny * pos[2]);
-    const int xn = pos[0] + nrm[0], yn = pos[1] + nrm[1], zn = pos[2] + nrm[2];
+    // the cell: fixed on the face's axis, the other two from t (first in-face axis fastest)
+    int x, y, z;
+    if (ax == 0) {
+        x = high ? a.nx - 1 : 0;
+        y = (int)(t % a.ny);
+        z = (int)(t / a.ny);
+    } else if (ax == 1) {
+        y = high ? a.ny - 1 : 0;
+        x = (int)(t % a.nx);
+        z = (int)(t / a.nx);
+    } else {
+        z = high ? a.nz - 1 : 0;
+        x = (int)(t % a.nx);
+        y = (int)(t / a.nx);
+    }
+    // discrete inward normal: every open face the cell lies on
+    auto inward = [](int v, int nv, int open) { return !open ? 0 : (v == 0 ? 1 : (v == nv - 1 ? -1 : 0)); };
+    const int xn = x + inward(x, a.nx, o.open[0]);
+    const int yn = y + inward(y, a.ny, o.open[1]);
+    const int zn = D == 3 ? z + inward(z, a.nz, o.open[2]) : z;
+    const int64_t cell = x + (int64_t)a.nx * (y + (int64_t)a.ny * z);
     const int64_t ncell = xn + (int64_t)a.nx * (yn + (int64_t)a.ny * zn);
     int64_t nb[Q];
     neighbours<D>(xn, yn, zn, a.nx, a.ny, a.nz, ncell, nb);
+    // a Dirichlet variable reads nothing: on an x face every population load of the
+    // neighbour is a separate strided line, so skipping them is most of the pass's cost
+    const unsigned mask = o.mask[face];
     R q[8];
 #pragma unroll
-    for (int k = 0; k < 8; ++k)
-        q[k] = ((o.mask[face] >> k) & 1u) ? (R)o.vals[face][k] : cell_moment<D, S>(a, ncell, nb, k);
+    for (int k = 0; k < 8; ++k) q[k] = ((mask >> k) & 1u) ? (R)o.vals[face][k] : cell_moment<D, S>(a, ncell, nb, k);
 
     // the flux of Eq. 12 along the face normal
     const R rho = q[0];
@@ -476,24 +488,28 @@ __global__ void k_open_fill(const ReadArgs<D, S> a, const OpenFaces o, unsigned 
     const R p = (R)o.gm1 * (q[4] - R(0.5) * mu - R(0.5) * B2);
     if (!(rho > R(0)) || !(p > R(0))) atomicOr(flags, kFlagNonPhysical);
     const R pt = p + R(0.5) * B2;
+    // components along the face normal, selected without indexing by the runtime axis
+    const R ma = ax == 0 ? q[1] : (ax == 1 ? q[2] : q[3]);
+    const R ua = ax == 0 ? u[0] : (ax == 1 ? u[1] : u[2]);
+    const R Ba = ax == 0 ? B[0] : (ax == 1 ? B[1] : B[2]);
     R phi[8];
-    phi[0] = q[1 + ax];
+    phi[0] = ma;
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
-        phi[1 + b] = q[1 + ax] * u[b] - B[ax] * B[b] + (ax == b ? pt : R(0));
-        phi[5 + b] = (ax == b) ? R(0) : u[ax] * B[b] - B[ax] * u[b];
+        phi[1 + b] = ma * u[b] - Ba * B[b] + (ax == b ? pt : R(0));
+        phi[5 + b] = (ax == b) ? R(0) : ua * B[b] - Ba * u[b];
     }
-    phi[4] = (q[4] + pt) * u[ax] - B[ax] * uB;
+    phi[4] = (q[4] + pt) * ua - Ba * uB;
 
     const int din = (face & 1) ? 2 * ax + 2 : 2 * ax + 1;  // +e_ax enters at the low face
     const R half = (face & 1) ? R(-AxisSet<D>::w1 / AxisSet<D>::cs2) : R(AxisSet<D>::w1 / AxisSet<D>::cs2);
     int j = din;
     int64_t at = cell;
-    if (a.parity) {
-        int64_t own[Q];
-        neighbours<D>(pos[0], pos[1], pos[2], a.nx, a.ny, a.nz, cell, own);
+    if (a.parity) {  // slot (opp i, x - c_i): x - c_i wraps to the opposite face
         j = opp_axis(din);
-        at = own[opp_axis(din)];
+        const int64_t step = ax == 0 ? 1 : (ax == 1 ? (int64_t)a.nx : (int64_t)a.nx * a.ny);
+        const int64_t span = ax == 0 ? (int64_t)a.nx : (ax == 1 ? (int64_t)a.ny : (int64_t)a.nz);
+        at = high ? cell + step - span * step : cell - step + span * step;
     }
     S *pop = static_cast<S *>(const_cast<void *>(a.pop));
 #pragma unroll

@@ -170,3 +170,55 @@ def test_closing_the_faces_returns_to_the_periodic_scheme_and_api_checks(V):
         with V.Context(params) as ctx:
             with pytest.raises(V.VlbmError):
                 ctx.set_boundary("x-", V.VLBM_BC_EQUILIBRIUM)
+
+
+def test_full_size_open_box_sampled_against_light_cones(V):
+    # The 512^3 benchmark run with open faces (x- a Dirichlet reservoir at the mean
+    # state, the other faces zero-gradient), on its own stream (captured graphs),
+    # 4 + 20 steps.  Per step a cell depends on cells within L-inf distance 1 (the
+    # streaming, and the fill's copy along the discrete normal), so the oracle on
+    # the box of half-width n around a sample, clipped to the domain, gives the
+    # sample exactly: a clipped side keeps the domain's face, the opposite side of
+    # that axis is an artificial zero-gradient face n cells away.
+    import torch
+    n, steps = 512, 24
+    shape = (n, n, n)
+    f0 = fields.ideal_fields(shape, 3003, mach=2.0, beta=1.0, cfl=0.2, k_rho=4, k_u=4, k_b=4,
+                             device=torch.device("cuda"))
+    Q = f0.Q
+    mean = Q.reshape(8, -1).mean(1).cpu().numpy()
+    scale = Q.abs().reshape(8, -1).amax(1).cpu().numpy()
+    spec = [(ALL, mean)] + [(0, None)] * 5
+    samples = [(0, 256, 256), (n - 1, 100, 300), (0, 0, 0), (n - 1, n - 1, n - 1), (0, 0, 200),
+               (300, n - 3, 40), (17, 480, 2), (256, 256, 256)]  # (x, y, z)
+    boxes = []
+    for s in samples:
+        lo = [max(0, v - steps) for v in s]
+        hi = [min(n - 1, v + steps) for v in s]
+        faces = []
+        for a in range(3):
+            if lo[a] == 0 or hi[a] == n - 1:
+                faces += [spec[2 * a] if lo[a] == 0 else (0, None), spec[2 * a + 1] if hi[a] == n - 1 else (0, None)]
+            else:
+                faces += [None, None]
+        Qb = Q[:, lo[2]:hi[2] + 1, lo[1]:hi[1] + 1, lo[0]:hi[0] + 1].cpu().numpy()
+        boxes.append((Qb, faces, [s[a] - lo[a] for a in range(3)]))
+
+    stream = torch.cuda.Stream()
+    p = V.make_params(shape=shape, storage="f32", gamma=f0.gamma, tau=0.51, stream=stream.cuda_stream)
+    with V.Context(p) as ctx:
+        assert V.vlbm_init_fields_device(ctx.ptr, 0, Q.data_ptr()) == V.VLBM_OK
+        _apply(ctx, V, spec)
+        ctx.step(4)
+        ctx.step(steps - 4)
+        assert ctx.sync() == V.VLBM_OK
+        got = ctx.populations([x + n * (y + n * z) for (x, y, z) in samples])
+    del Q
+
+    for (Qb, faces, at), g in zip(boxes, got):
+        fb = oracle.ideal_init(Qb, f0.gamma)
+        for _ in range(steps):
+            fb = oracle.open_step(fb, f0.gamma, 0.51, faces, nthreads=8)
+        ref = fb[:, :, at[2], at[1], at[0]].reshape(-1)
+        tol = 1e-5 * np.repeat(scale, 7)
+        assert np.all(np.abs(g - ref) <= tol), np.abs(g - ref).reshape(8, 7).max(1) / scale
