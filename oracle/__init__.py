@@ -82,6 +82,14 @@ def _configure(L):
     L.orc_hlbm_target.restype = None
     L.orc_hlbm_step.argtypes = [i, i, i, i, d, p, p, p, p, p, i]
     L.orc_hlbm_run.argtypes = [i, i, i, i, d, p, p, p, p, i, p, i]
+    L.orc_diss_flux.argtypes = [d, d, d, d, d, p, p]
+    L.orc_diss_flux.restype = None
+    L.orc_diss_source.argtypes = [d, i, p, p]
+    L.orc_diss_source.restype = None
+    L.orc_diss_init.argtypes = [i, i, d, d, d, d, d, p, p]
+    L.orc_diss_step.argtypes = [i, i, d, p, d, d, d, d, i, p, p, i]
+    L.orc_diss_moments.argtypes = [i, i, p, p]
+    L.orc_diss_run.argtypes = [i, i, d, p, d, d, d, d, i, p, i, p, i]
     L.orc_open_step.argtypes = [i, i, i, i, d, p, p, p, p, p, p, p, p, i]
     L.orc_open_run.argtypes = [i, i, i, i, d, p, p, p, p, p, p, p, i, p, i]
     return L
@@ -455,4 +463,80 @@ def open_run(Q0: np.ndarray, gamma: float, tau, faces, nsteps: int, src=None, so
                               _ptr(sd) if sd is not None else None,
                               open_.ctypes.data_as(ctypes.c_void_p), mask.ctypes.data_as(ctypes.c_void_p),
                               _ptr(vals), _ptr(Q0), nsteps, _ptr(out), nthreads), "open_run")
+    return out
+
+
+# ---- dissipative MHD with locally evolved gradients (sec. 2.2.1, 2.3), 2-D D2Q5 ----
+# Q[20]: rho, rho u (3), e, B (3), G_ab = Q[8 + 3a + b] ~ tau_M d_a B_b, W_ab = Q[14 + 3a + b] ~ tau_M d_a u_b
+
+NVAR_DISS = 20
+
+
+class Dissipation:
+    """Physical parameters of the dissipative model: kinematic viscosity nu,
+    resistivity eta0 (1 + |j|^2 / j_c^2) (j_c <= 0: constant), tau_M in steps,
+    Powell source on or off."""
+
+    def __init__(self, nu=0.0, eta0=0.0, j_c=0.0, tau_m=1.0, powell=False):
+        self.nu, self.eta0, self.j_c, self.tau_m, self.powell = float(nu), float(eta0), float(j_c), float(tau_m), bool(powell)
+
+
+def _tau20(tau, tau_g=None):
+    t = np.asarray(tau, dtype=np.float64).reshape(-1)
+    if t.size == 20:
+        return _f64(t)
+    t8 = np.broadcast_to(t, (8,)) if t.size in (1, 8) else None
+    if t8 is None:
+        raise ValueError("tau: 1, 8 or 20 values")
+    g = float(t8[0]) if tau_g is None else float(tau_g)
+    return _f64(np.concatenate([t8, np.full(12, g)]))
+
+
+def diss_flux(gamma: float, dp: Dissipation, Q) -> np.ndarray:
+    """Flux tensor phi[20, 3] of one state."""
+    out = np.zeros(60)
+    lib().orc_diss_flux(gamma, dp.nu, dp.eta0, dp.j_c, dp.tau_m, _ptr(_f64(Q)), _ptr(out))
+    return out.reshape(20, 3)
+
+
+def diss_source(dp: Dissipation, Q) -> np.ndarray:
+    out = np.zeros(20)
+    lib().orc_diss_source(dp.tau_m, int(dp.powell), _ptr(_f64(Q)), _ptr(out))
+    return out
+
+
+def diss_init(Q0: np.ndarray, gamma: float, dp: Dissipation) -> np.ndarray:
+    """Populations f[20, 5, ny, nx] = f_eq(Q0)."""
+    Q0 = _f64(Q0)
+    ny, nx = Q0.shape[1:]
+    f = np.zeros((20, 5, ny, nx))
+    _check(lib().orc_diss_init(nx, ny, gamma, dp.nu, dp.eta0, dp.j_c, dp.tau_m, _ptr(Q0), _ptr(f)), "diss_init")
+    return f
+
+
+def diss_step(f: np.ndarray, gamma: float, tau, dp: Dissipation, tau_g=None, nthreads: int = 1) -> np.ndarray:
+    f = _f64(f)
+    ny, nx = f.shape[2:]
+    out = np.empty_like(f)
+    _check(lib().orc_diss_step(nx, ny, gamma, _ptr(_tau20(tau, tau_g)), dp.nu, dp.eta0, dp.j_c, dp.tau_m,
+                               int(dp.powell), _ptr(f), _ptr(out), nthreads), "diss_step")
+    return out
+
+
+def diss_moments(f: np.ndarray) -> np.ndarray:
+    f = _f64(f)
+    ny, nx = f.shape[2:]
+    Q = np.zeros((20, ny, nx))
+    _check(lib().orc_diss_moments(nx, ny, _ptr(f), _ptr(Q)), "diss_moments")
+    return Q
+
+
+def diss_run(Q0: np.ndarray, gamma: float, tau, dp: Dissipation, nsteps: int, tau_g=None,
+             nthreads: int = 1) -> np.ndarray:
+    """Moments [20, ny, nx] after nsteps steps started from f_eq(Q0)."""
+    Q0 = _f64(Q0)
+    ny, nx = Q0.shape[1:]
+    out = np.zeros_like(Q0)
+    _check(lib().orc_diss_run(nx, ny, gamma, _ptr(_tau20(tau, tau_g)), dp.nu, dp.eta0, dp.j_c, dp.tau_m,
+                              int(dp.powell), _ptr(Q0), nsteps, _ptr(out), nthreads), "diss_run")
     return out

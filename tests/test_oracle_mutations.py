@@ -10,6 +10,7 @@ import pytest
 import oracle
 import test_oracle_hlbm as H
 import test_oracle_open as O
+import test_oracle_diss as DS
 import test_oracle_pins as P
 import test_oracle_powell as W
 import test_oracle_resistive as R
@@ -62,6 +63,18 @@ OPEN_PINS = [
     lambda o: O.test_supersonic_inflow_flushes_the_domain_to_the_inflow_state(),
     lambda o: O.test_zero_gradient_faces_let_a_pulse_leave(),
     lambda o: O.test_oracle_matches_numpy_restatement((5, 6, 7)),
+]
+
+DISS_PINS = [
+    lambda o: DS.test_gradient_lattices_relax_to_tau_m_times_the_gradients(),
+    lambda o: DS.test_shear_wave_decays_at_nu_plus_the_lattice_diffusion(0.01),
+    lambda o: DS.test_magnetic_sheet_diffuses_at_eta_plus_the_lattice_diffusion(0.01),
+    lambda o: DS.test_current_dependent_resistivity_projects_onto_the_mode(),
+    lambda o: DS.test_conserved_fields_are_conserved_exactly(),
+    lambda o: DS.test_heat_appears_where_the_dissipation_is("viscous"),
+    lambda o: DS.test_heat_appears_where_the_dissipation_is("ohmic"),
+    lambda o: DS.test_uniform_step_with_the_powell_source_and_relaxing_gradients(),
+    lambda o: DS.test_oracle_matches_numpy_restatement(True),
 ]
 
 # (name, original text, planted mistake, which pin family must catch it)
@@ -135,6 +148,22 @@ MUTANTS = [
      "Qb[k] = ((mask[face] >> k) & 1u) ? vals[k] : Qn[k];", OPEN_PINS),
     ("boundary state from the pre-stream state", "Qn[k] += fout[(long)(k * q + i) * N + nb]; /* Eq. 4 */",
      "Qn[k] += fin[(long)(k * q + i) * N + nb]; /* Eq. 4 */", OPEN_PINS),
+    ("viscous stress sign", "- B[c] * B[b] - visc[c][b];", "- B[c] * B[b] + visc[c][b];", DISS_PINS),
+    ("viscous stress without the transpose", "rho * nu * (du[a][b] + du[b][a])", "rho * nu * (du[a][b] + du[a][b])",
+     DISS_PINS),
+    ("resistivity linear in j", "j2 / (j_c * j_c)", "sqrt(j2) / j_c", DISS_PINS),
+    ("induction diffusion sign", "- eta * dB[c][b];", "+ eta * dB[c][b];", DISS_PINS),
+    ("induction diffusion transposed", "- eta * dB[c][b];", "- eta * dB[b][c];", DISS_PINS),
+    ("ohmic energy flux sign", "- u_visc + eta * jxB[c];", "- u_visc - eta * jxB[c];", DISS_PINS),
+    ("viscous work sign", "- u_visc + eta * jxB[c];", "+ u_visc + eta * jxB[c];", DISS_PINS),
+    ("gradient flux on the wrong axis", "phi[3 * (8 + 3 * a + b) + c] = Q[8 + 3 * a + b] * u[c] - (a == c ? B[b] : 0.0);",
+     "phi[3 * (8 + 3 * a + b) + c] = Q[8 + 3 * a + b] * u[c] - (b == c ? B[a] : 0.0);", DISS_PINS),
+    ("velocity gradient fed by B", "phi[3 * (14 + 3 * a + b) + c] = Q[14 + 3 * a + b] * u[c] - (a == c ? u[b] : 0.0);",
+     "phi[3 * (14 + 3 * a + b) + c] = Q[14 + 3 * a + b] * u[c] - (a == c ? B[b] : 0.0);", DISS_PINS),
+    ("divergence from G_xy", "-(Q[8 + 0] + Q[8 + 3 + 1]) / tau_m;", "-(Q[8 + 0] + Q[8 + 1]) / tau_m;", DISS_PINS),
+    ("gradient relaxation sign", "for (int k = 8; k < ORC_NVAR_DISS; ++k) S[k] = -Q[k] / tau_m;",
+     "for (int k = 8; k < ORC_NVAR_DISS; ++k) S[k] = Q[k] / tau_m;", DISS_PINS),
+    ("current without the minus of the curl", "dB[0][1] - dB[1][0]", "dB[0][1] + dB[1][0]", DISS_PINS),
     ("Powell source without weight", "fout[k * L->q + i] = f + (feq[k][i] - f) / tau[k] + L->w[i] * sk;",
      "fout[k * L->q + i] = f + (feq[k][i] - f) / tau[k] + sk;", POWELL_PINS),
 ]
