@@ -57,8 +57,9 @@ def parse():
     ap.add_argument("--form-steps", type=int, default=20)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the channel, batched and closure forms")
-    ap.add_argument("--extras", default="channel,batch,closure,powell,hlbm,open",
-                    help="which other workloads to run (comma list of channel, batch, closure)")
+    ap.add_argument("--extras", default="channel,batch,closure,powell,hlbm,open,diss",
+                    help="which other workloads to run (comma list of channel, batch, closure, powell, "
+                         "hlbm, open, diss)")
     ap.add_argument("--closure-fine", type=int, default=512, help="fine grid side of the closure workload")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -245,6 +246,35 @@ def powell_form(args, vlbm, fields, torch, stream, hbm_peak):
     return {"workload": "ideal MHD 3-D with the Powell source, %d^3, 9 x D3Q7 (the 8 fields and the "
                         "divergence lattice D), FP32, tau 0.51, tau_d 0.51, tau_M 1, same fields as the "
                         "headline workload, D = 0 at start" % n,
+            "init_status": vlbm.status_string(st), "status": status, "glups": gl, "steps": steps,
+            "bytes_per_cell": bytes_cell, "roofline_frac": gl * 1e9 * bytes_cell / (hbm_peak * 1e9)}
+
+
+def dissipative_form(args, vlbm, fields, torch, stream, hbm_peak):
+    """Dissipative MHD with evolved gradients (20 D2Q5 lattices, FP32): the
+    low-Mach resistive Orszag-Tang set-up at the paper's finest grid, 2048^2."""
+    n = 2048
+    setup = fields.low_mach_orszag_tang(n)
+    p = vlbm.make_params(model=vlbm.VLBM_DISSIPATIVE, shape=(n, n), storage="f32", gamma=setup.gamma,
+                         tau=setup.tau, tau_g=setup.tau_g, tau_m=setup.tau_m, nu=setup.nu, eta0=setup.eta0,
+                         j_c=setup.j_c, powell=True, stream=stream.cuda_stream)
+    ctx = vlbm.Context(p)
+    Qd = torch.from_numpy(setup.Q).cuda()
+    st = vlbm.vlbm_init_fields_device(ctx.ptr, 0, Qd.data_ptr())
+    del Qd
+    vlbm.vlbm_step(ctx.ptr, 4)
+    steps = args.form_steps
+    ms = _time_steps(vlbm, [ctx.ptr], stream, torch, steps, False)
+    status = vlbm.status_string(vlbm.vlbm_sync(ctx.ptr))
+    ctx.close()
+    ncell = n * n
+    gl = ncell * steps / (ms * 1e-3) / 1e9
+    bytes_cell = 2 * 100 * 4
+    return {"workload": "dissipative MHD 2-D with locally evolved gradients, %d^2, 20 x D2Q5 (8 MHD fields, "
+                        "G ~ tau_M grad B, W ~ tau_M grad u), FP32, low-Mach resistive Orszag-Tang set-up "
+                        "(nu = eta0 = %.3g, j_c = %.3g, tau_M = %.1f steps, tau = %.5f), Powell source on"
+                        % (n, setup.nu, setup.j_c, setup.tau_m, setup.tau),
+            "kernel": "k_diss_step<float> (fused collide+stream, 100 populations per cell)",
             "init_status": vlbm.status_string(st), "status": status, "glups": gl, "steps": steps,
             "bytes_per_cell": bytes_cell, "roofline_frac": gl * 1e9 * bytes_cell / (hbm_peak * 1e9)}
 
@@ -582,6 +612,8 @@ def main():
             extra["hlbm_sphere_3d"] = hlbm_form(args, vlbm, fields, torch, stream, hbm_peak)
         if "open" in which:
             extra["open_faces_3d"] = open_form(args, vlbm, fields, torch, stream, hbm_peak)
+        if "diss" in which:
+            extra["dissipative_2d"] = dissipative_form(args, vlbm, fields, torch, stream, hbm_peak)
 
     cpu = None
     if rank == 0 and not args.no_cpu:

@@ -16,6 +16,9 @@
  *   magnetic lattices with the Eq. 3 equilibrium, Guo body force, halfway
  *   bounce-back walls at y = 0 and ny-1, magnetic walls held at the
  *   equilibrium of the applied field).
+ *   sec. 2.2.1 local moments evolution with sec. 2.3 "Evolution of the MHD
+ *   equation system" for the dissipative model (viscous stress, eta(j)
+ *   resistivity, gradients carried as lattices; VLBM_DISSIPATIVE).
  *
  * Conventions for every call
  *   - Lattice units: dx = dt = 1.  Fields are double precision, structure of
@@ -23,7 +26,8 @@
  *     N = nx * ny * nz.  Ideal MHD has nvar = 8 fields (rho, rho u_x,
  *     rho u_y, rho u_z, e_tot, B_x, B_y, B_z); the resistive model has
  *     nvar = 7 (rho, m_x, m_y, m_z, B_x, B_y, B_z), where m includes the
- *     half-force shift of the Guo scheme.
+ *     half-force shift of the Guo scheme; the Powell model adds D (nvar = 9)
+ *     and the dissipative model G and W (nvar = 20, see vlbm_model).
  *   - Velocity sets and direction order: D2Q5 (w0 = 1/3, w = 1/6,
  *     cs^2 = 1/3), D3Q7 (w0 = 1/4, w = 1/8, cs^2 = 1/4), D3Q19 (1/3, 1/18,
  *     1/36, cs^2 = 1/3).  Direction 0 is rest; 1 +x, 2 -x, 3 +y, 4 -y,
@@ -78,7 +82,20 @@ typedef enum {
  * evolution (sec. 2.2.1; flux D u - B, relaxation source -D / tau_m), as
  * div B = D / tau_m.  Nine fields: the eight of VLBM_IDEAL, then D.  Built
  * for F64 and F32 storage, single domains. */
-typedef enum { VLBM_IDEAL = 0, VLBM_RESISTIVE = 1, VLBM_IDEAL_POWELL = 2 } vlbm_model;
+/* VLBM_DISSIPATIVE: the full dissipative MHD system (sec. 2.3, "Evolution of
+ * the MHD equation system" and "Incompressible resistive MHD") with the
+ * gradients it needs evolved locally (sec. 2.2.1): besides the eight fields of
+ * Eq. 12 the state carries G_ab ~ tau_m d_a B_b (flux G_ab u_c - delta_ac B_b)
+ * and W_ab ~ tau_m d_a u_b (flux W_ab u_c - delta_ac u_b), a in {x, y},
+ * b in {x, y, z}, both relaxed by the source -G / tau_m, -W / tau_m.  Twenty
+ * fields: rho, rho u (3), e_tot, B (3), then G_ab at 8 + 3a + b and W_ab at
+ * 14 + 3a + b.  The MHD fluxes add the viscous stress rho nu (grad u +
+ * grad u^T), -eta grad B in the induction flux and -u . tau_v + eta j x B in
+ * the energy flux (no heat flux), with j = curl B and eta = eta0 (1 + |j|^2 /
+ * j_c^2) (j_c <= 0: eta = eta0); params.powell adds Powell's source with
+ * div B = (G_xx + G_yy) / tau_m.  2-D (D2Q5, 100 populations per cell), F64
+ * and F32 storage, single domains. */
+typedef enum { VLBM_IDEAL = 0, VLBM_RESISTIVE = 1, VLBM_IDEAL_POWELL = 2, VLBM_DISSIPATIVE = 3 } vlbm_model;
 
 /* Population storage.  F64: double storage and arithmetic.  F32: float
  * storage and arithmetic.  F16_DEV / BF16_DEV: populations stored as
@@ -113,13 +130,22 @@ typedef struct {
     void *alloc_user;     /* passed back to the hooks */
     double tau_d;         /* Powell model: BGK relaxation time of the D lattice, > 1/2 */
     double tau_m;         /* Powell model: relaxation time of D in time steps (source
-                             -D / tau_m; div B = D / tau_m), > 1/2 */
+                             -D / tau_m; div B = D / tau_m), > 1/2; dissipative model:
+                             relaxation time of G and W in time steps */
+    double tau_g;         /* dissipative model: BGK relaxation time of the twelve
+                             gradient lattices (G, W), > 1/2; tau[0..7] serve the
+                             eight MHD lattices */
+    double nu;            /* dissipative model: kinematic viscosity (lattice units), >= 0 */
+    double eta0;          /* dissipative model: resistivity at zero current, >= 0 */
+    double j_c;           /* dissipative model: current scale of eta(j); <= 0: constant eta0 */
+    int powell;           /* dissipative model: 1 adds Powell's source */
 } vlbm_params;
 
 /* Fill *p with defaults: ideal MHD, dim 3, 64^3 cells, F32 storage,
  * gamma = 5/3, tau = 0.51 on every lattice (the paper's showcase value,
  * sec. 5 table), no source, no walls, check_every = 0, NULL hooks;
- * Powell model: tau_d = 0.51, tau_m = 1. */
+ * Powell model: tau_d = 0.51, tau_m = 1; dissipative model: tau_g = 0.51,
+ * nu = eta0 = j_c = 0, no Powell source. */
 void vlbm_default_params(vlbm_params *p);
 
 /* Create a context for one domain: validates p (dims > 0, dim 2 => nz = 1,
@@ -175,8 +201,8 @@ vlbm_status vlbm_gather_populations(vlbm_ctx *ctx, int domain, const int64_t *ce
 /* Domain sums of the conserved fields, sum_x Q_k(x), accumulated in
  * double precision from the stored populations (fixed reduction order:
  * repeated calls on the same state return identical values), into
- * sums[min(nvar, 8)] on the host (the Powell model: the eight MHD fields;
- * D is not a conserved field).  Also refreshes the health status.
+ * sums[min(nvar, 8)] on the host (the Powell and dissipative models: the
+ * eight MHD fields; D, G and W are not conserved fields).  Also refreshes the health status.
  * Synchronises. */
 vlbm_status vlbm_conservation(vlbm_ctx *ctx, int domain, double *sums);
 
@@ -355,8 +381,9 @@ int vlbm_tile_shapes(const vlbm_ctx *ctx);
 vlbm_status vlbm_set_tile_shape(vlbm_ctx *ctx, int shape);
 
 /* Small queries. */
-int vlbm_nvar(const vlbm_ctx *ctx);                  /* 8 ideal, 7 resistive, 9 Powell */
-int vlbm_slots_per_cell(const vlbm_ctx *ctx);        /* populations per cell: 40, 56 or 40 (D3Q19 + 3 x D3Q7) */
+int vlbm_nvar(const vlbm_ctx *ctx);                  /* 8 ideal, 7 resistive, 9 Powell, 20 dissipative */
+int vlbm_slots_per_cell(const vlbm_ctx *ctx);        /* populations per cell: 40 or 56 (ideal), 40 (D3Q19 +
+                                                        3 x D3Q7), 45 or 63 (Powell), 100 (dissipative) */
 int vlbm_num_domains(const vlbm_ctx *ctx);
 int64_t vlbm_num_cells(const vlbm_ctx *ctx, int domain);
 int64_t vlbm_step_count(const vlbm_ctx *ctx);

@@ -1,0 +1,383 @@
+// k_diss.cu -- dissipative MHD with locally evolved gradients on D2Q5 (sm_103a).
+//
+// The full MHD system (sec. 2.3, "Evolution of the MHD equation system", with
+// the local moments evolution of sec. 2.2.1) carries, besides the eight fields
+// of Eq. 12, the gradient tensors that the dissipative fluxes need:
+//   G_ab ~ tau_M d_a B_b   flux G_ab u_c - delta_ac B_b,   source -G_ab / tau_M
+//   W_ab ~ tau_M d_a u_b   flux W_ab u_c - delta_ac u_b,   source -W_ab / tau_M
+// with a in {x, y} (the lattice axes) and b in {x, y, z}.  Field order:
+// Q[8 + 3a + b] = G_ab, Q[14 + 3a + b] = W_ab -- 20 lattices of D2Q5,
+// 100 populations per cell.  With d_a B_b = G_ab / tau_M, d_a u_b = W_ab / tau_M
+// and d_z = 0, the fluxes of the MHD fields are those of Eq. 12 plus
+//   momentum   - tau_v,               tau_v = rho nu (grad u + grad u^T)
+//   energy     - u . tau_v + eta j x B            (heat flux zero)
+//   induction  - eta grad B
+// with j = curl B and the current-dependent resistivity
+// eta = eta0 (1 + |j|^2 / j_c^2) (sec. 2.3, "Incompressible resistive MHD";
+// j_c <= 0 keeps eta = eta0).  Optional Powell source
+// S = -(div B)(0, B, u.B, u) with div B = (G_xx + G_yy) / tau_M.
+//
+// One fused kernel per step as for ideal MHD (Eq. 2, AA in-place pattern,
+// one cell per thread, x-contiguous slot planes): load the 100 populations,
+// form the 20 moments, the fluxes and sources above, relax towards the
+// first-order equilibrium of Eq. 3 with direct source injection, store.
+// FP32 keeps the populations in registers between load and store; FP64
+// (400 registers' worth) sums them on the way in and reads them again for the
+// update -- the second read of a slot comes from the cache, and it is safe in
+// place because a thread writes only slots it reads, each after reading it.
+#include "vlbm_internal.cuh"
+
+namespace vlbm {
+namespace {
+
+constexpr int kDissLat = 20;
+constexpr int kDissQ = 5;
+
+template <class C> struct DissArgs {
+    void *pop;
+    int nx, ny;
+    int64_t stride;
+    C gm1;
+    C omega[kDissLat];
+    C nu, eta0, inv_jc2, inv_tau_m;
+    int powell;
+    unsigned *flags;
+};
+
+// Fluxes phi[k][c] along the two lattice axes and sources S[k] of one state.
+template <class C>
+__device__ __forceinline__ void diss_flux_source(const C (&q)[kDissLat], const DissArgs<C> &a, C (&phi)[kDissLat][2],
+                                                 C (&S)[kDissLat], unsigned *flags)
+{
+    const C rho = q[0];
+    const C ir = C(1) / rho;
+    const C m[3] = {q[1], q[2], q[3]};
+    const C u[3] = {m[0] * ir, m[1] * ir, m[2] * ir};
+    const C E = q[4];
+    const C B[3] = {q[5], q[6], q[7]};
+    const C B2 = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
+    const C mu = m[0] * u[0] + m[1] * u[1] + m[2] * u[2];
+    const C uB = u[0] * B[0] + u[1] * B[1] + u[2] * B[2];
+    const C p = a.gm1 * (E - C(0.5) * mu - C(0.5) * B2);  // Eq. 9
+    const C pt = p + C(0.5) * B2;
+    if (!(rho > C(0)) || !(p > C(0))) atomicOr(flags, kFlagNonPhysical);
+
+    // gradients from the evolved tensors (rows a = x, y; the z row is zero in 2-D)
+    C dB[2][3], du[2][3];
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            dB[r][b] = q[8 + 3 * r + b] * a.inv_tau_m;
+            du[r][b] = q[14 + 3 * r + b] * a.inv_tau_m;
+        }
+    // viscous stress rows c = x, y: rho nu (d_c u_b + d_b u_c), d_z = 0
+    const C rn = rho * a.nu;
+    C vs[2][3];
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) vs[c][b] = rn * (du[c][b] + (b < 2 ? du[b][c] : C(0)));
+    // current j = curl B (d_z = 0) and the resistivity eta(j)
+    const C j[3] = {dB[1][2], -dB[0][2], dB[0][1] - dB[1][0]};
+    const C jj = j[0] * j[0] + j[1] * j[1] + j[2] * j[2];
+    const C eta = a.eta0 * (C(1) + jj * a.inv_jc2);
+    const C jxB[2] = {j[1] * B[2] - j[2] * B[1], j[2] * B[0] - j[0] * B[2]};
+    const C Ept = E + pt;
+
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        phi[0][c] = m[c];
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            phi[1 + b][c] = m[c] * u[b] - B[c] * B[b] + (b == c ? pt : C(0)) - vs[c][b];
+            // u_c B_b - B_c u_b vanishes for b = c; written as zero so that no
+            // fused multiply-add leaves a rounding residue there
+            phi[5 + b][c] = (b == c ? C(0) : u[c] * B[b] - B[c] * u[b]) - eta * dB[c][b];
+        }
+        phi[4][c] = Ept * u[c] - B[c] * uB - (u[0] * vs[c][0] + u[1] * vs[c][1] + u[2] * vs[c][2]) + eta * jxB[c];
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                phi[8 + 3 * r + b][c] = q[8 + 3 * r + b] * u[c] - (r == c ? B[b] : C(0));
+                phi[14 + 3 * r + b][c] = q[14 + 3 * r + b] * u[c] - (r == c ? u[b] : C(0));
+            }
+    }
+
+#pragma unroll
+    for (int k = 0; k < 8; ++k) S[k] = C(0);
+#pragma unroll
+    for (int k = 8; k < kDissLat; ++k) S[k] = -q[k] * a.inv_tau_m;
+    if (a.powell) {
+        const C ndiv = -(q[8] + q[12]) * a.inv_tau_m;  // -(G_xx + G_yy) / tau_M
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            S[1 + b] = ndiv * B[b];
+            S[5 + b] = ndiv * u[b];
+        }
+        S[4] = ndiv * uB;
+    }
+}
+
+// Linear indices of x + c_i (periodic), D2Q5 order.
+__device__ __forceinline__ void diss_neighbours(int x, int y, int nx, int ny, int64_t cell, int64_t (&nb)[kDissQ])
+{
+    const int64_t plane = (int64_t)nx * ny;
+    nb[0] = cell;
+    nb[1] = (x + 1 < nx) ? cell + 1 : cell + 1 - nx;
+    nb[2] = (x > 0) ? cell - 1 : cell - 1 + nx;
+    nb[3] = (y + 1 < ny) ? cell + nx : cell + nx - plane;
+    nb[4] = (y > 0) ? cell - nx : cell - nx + plane;
+}
+
+// The fused collide-and-stream step (Eq. 2): even parity reads slot (i, x) and
+// sends direction i to slot (opp i, x); odd parity reads slot (opp i, x - c_i)
+// and sends direction i to slot (i, x + c_i).  HOLD keeps the populations in
+// registers between load and update, otherwise they are read twice.
+template <class C, bool ODD, bool HOLD>
+__global__ void __launch_bounds__(kBlockX) k_diss_step(const DissArgs<C> a)
+{
+    constexpr int Q = kDissQ;
+    const int x = blockIdx.x * kBlockX + threadIdx.x;
+    if (x >= a.nx) return;
+    const int y = blockIdx.y;
+    const int64_t cell = x + (int64_t)a.nx * y;
+    int64_t nb[Q];
+    diss_neighbours(x, y, a.nx, a.ny, cell, nb);
+    C *pop = static_cast<C *>(a.pop);
+    auto src = [&](int k, int i) -> C * {
+        return pop + (int64_t)(k * Q + (ODD ? opp_axis(i) : i)) * a.stride + (ODD ? nb[opp_axis(i)] : cell);
+    };
+    auto dst = [&](int k, int i) -> C * {
+        return pop + (int64_t)(k * Q + (ODD ? i : opp_axis(i))) * a.stride + (ODD ? nb[i] : cell);
+    };
+
+    C q[kDissLat];
+    C f[HOLD ? kDissLat : 1][Q];
+#pragma unroll
+    for (int k = 0; k < kDissLat; ++k) {
+        C s = C(0);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const C v = *src(k, i);
+            if constexpr (HOLD) f[k][i] = v;
+            s += v;
+        }
+        q[k] = s;
+    }
+    C phi[kDissLat][2], S[kDissLat];
+    diss_flux_source<C>(q, a, phi, S, a.flags);
+
+    // Weights that sum to one exactly in the compute precision: w0 = 1 - 4 w1, and
+    // omega w0 = omega - 4 (omega w1) (both differences are exact).  Rounded
+    // products such as omega * w0 would otherwise make every cell gain or lose the
+    // same fraction of Q_k per step, a drift of the FP32 domain sums.
+    constexpr C w1 = C(AxisSet<2>::w1), w0 = C(1) - C(4) * w1;
+#pragma unroll
+    for (int k = 0; k < kDissLat; ++k) {
+        C g[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) g[i] = HOLD ? f[HOLD ? k : 0][i] : *src(k, i);
+        const C om = a.omega[k];
+        const C omc = C(1) - om;
+        const C ow1 = om * w1;
+        const C ow0 = om - C(4) * ow1;
+        const C A0 = ow0 * q[k] + w0 * S[k];
+        const C A1 = ow1 * q[k] + w1 * S[k];
+        const C hom = C(0.5) * om;  // omega * w_moving / cs^2
+        const C bx = hom * phi[k][0], by = hom * phi[k][1];
+        *dst(k, 0) = omc * g[0] + A0;
+        *dst(k, 1) = omc * g[1] + A1 + bx;
+        *dst(k, 2) = omc * g[2] + A1 - bx;
+        *dst(k, 3) = omc * g[3] + A1 + by;
+        *dst(k, 4) = omc * g[4] + A1 - by;
+    }
+}
+
+// f = f_eq(Q) at parity 0 (Eq. 3 with the fluxes above) for cells c0 .. c0 + count;
+// also checks positivity and the sub-characteristic condition
+// max(|u| + c_f) < cs of the ideal part.
+template <class C>
+__global__ void k_diss_init(const DissArgs<C> a, double gamma, int64_t c0, int64_t count, int64_t qstride,
+                            const double *__restrict__ Qin)
+{
+    constexpr int Q = kDissQ;
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= count) return;
+    const int64_t cell = c0 + t;
+    C q[kDissLat];
+#pragma unroll
+    for (int k = 0; k < kDissLat; ++k) q[k] = (C)Qin[k * qstride + t];
+    C phi[kDissLat][2], S[kDissLat];
+    diss_flux_source<C>(q, a, phi, S, a.flags);
+    {
+        const C rho = q[0], ir = C(1) / rho;
+        const C u2 = (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]) * ir * ir;
+        const C B2 = q[5] * q[5] + q[6] * q[6] + q[7] * q[7];
+        const C p = a.gm1 * (q[4] - C(0.5) * rho * u2 - C(0.5) * B2);
+        const C vsig = sqrt(u2) + sqrt(fmax((C(gamma) * p + B2) * ir, C(0)));
+        if (!(vsig < (C)sqrt(AxisSet<2>::cs2))) atomicOr(a.flags, kFlagUnstable);
+    }
+    C *pop = static_cast<C *>(a.pop);
+    constexpr C w1 = C(AxisSet<2>::w1), w0 = C(1) - C(4) * w1;  // as in the step
+    constexpr C h = C(AxisSet<2>::w1 / AxisSet<2>::cs2);
+#pragma unroll
+    for (int k = 0; k < kDissLat; ++k) {
+        C *base = pop + (int64_t)(k * Q) * a.stride + cell;
+        base[0] = w0 * q[k];
+        base[a.stride] = w1 * q[k] + h * phi[k][0];
+        base[2 * a.stride] = w1 * q[k] - h * phi[k][0];
+        base[3 * a.stride] = w1 * q[k] + h * phi[k][1];
+        base[4 * a.stride] = w1 * q[k] - h * phi[k][1];
+    }
+}
+
+struct DissRead {
+    const void *pop;
+    int nx, ny;
+    int64_t stride;
+    int parity;
+};
+
+// Logical (pre-collision) population f_ki of a cell at the current parity.
+template <class C>
+__device__ __forceinline__ C diss_logical(const DissRead &a, int64_t cell, const int64_t (&nb)[kDissQ], int k, int i)
+{
+    const C *pop = static_cast<const C *>(a.pop);
+    const int j = a.parity ? opp_axis(i) : i;
+    const int64_t at = a.parity ? nb[opp_axis(i)] : cell;
+    return pop[(int64_t)(k * kDissQ + j) * a.stride + at];
+}
+
+// Q_k = sum_i f_ki (Eq. 4) for cells c0 .. c0 + count, summed in the storage precision.
+template <class C>
+__global__ void k_diss_moments(const DissRead a, int64_t c0, int64_t count, int64_t ostride, double *__restrict__ out)
+{
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= count) return;
+    const int64_t cell = c0 + t;
+    const int x = (int)(cell % a.nx), y = (int)(cell / a.nx);
+    int64_t nb[kDissQ];
+    diss_neighbours(x, y, a.nx, a.ny, cell, nb);
+#pragma unroll
+    for (int k = 0; k < kDissLat; ++k) {
+        C s = C(0);
+#pragma unroll
+        for (int i = 0; i < kDissQ; ++i) s += diss_logical<C>(a, cell, nb, k, i);
+        out[k * ostride + t] = (double)s;
+    }
+}
+
+template <class C>
+__global__ void k_diss_gather(const DissRead a, const int64_t *__restrict__ cells, int n, double *__restrict__ out)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const int64_t cell = cells[t];
+    const int x = (int)(cell % a.nx), y = (int)(cell / a.nx);
+    int64_t nb[kDissQ];
+    diss_neighbours(x, y, a.nx, a.ny, cell, nb);
+#pragma unroll
+    for (int k = 0; k < kDissLat; ++k)
+#pragma unroll
+        for (int i = 0; i < kDissQ; ++i)
+            out[(int64_t)t * kDissLat * kDissQ + k * kDissQ + i] = (double)diss_logical<C>(a, cell, nb, k, i);
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+
+template <class C> DissArgs<C> make_diss_args(vlbm_ctx *c)
+{
+    const Domain &d = c->dom[0];
+    const vlbm_params &p = c->params;
+    DissArgs<C> a{};
+    a.pop = c->pop;
+    a.nx = d.nx;
+    a.ny = d.ny;
+    a.stride = d.stride;
+    a.gm1 = C(d.gamma - 1.0);
+    for (int k = 0; k < kDissLat; ++k) a.omega[k] = C(1.0 / (k < 8 ? d.tau[k] : p.tau_g));
+    a.nu = C(p.nu);
+    a.eta0 = C(p.eta0);
+    a.inv_jc2 = C(p.j_c > 0.0 ? 1.0 / (p.j_c * p.j_c) : 0.0);
+    a.inv_tau_m = C(1.0 / d.tau_m);
+    a.powell = p.powell ? 1 : 0;
+    a.flags = c->d_flags;
+    return a;
+}
+
+DissRead make_diss_read(vlbm_ctx *c)
+{
+    const Domain &d = c->dom[0];
+    return DissRead{c->pop, d.nx, d.ny, d.stride, (int)(c->step & 1)};
+}
+
+template <class C> vlbm_status step_t(vlbm_ctx *c, int parity)
+{
+    constexpr bool hold = sizeof(C) == 4;
+    const Domain &d = c->dom[0];
+    const DissArgs<C> a = make_diss_args<C>(c);
+    const dim3 grid((unsigned)((d.nx + kBlockX - 1) / kBlockX), (unsigned)d.ny);
+    if (parity)
+        k_diss_step<C, true, hold><<<grid, kBlockX, 0, c->stream>>>(a);
+    else
+        k_diss_step<C, false, hold><<<grid, kBlockX, 0, c->stream>>>(a);
+    c->launches++;
+    return cuda_check(c, cudaGetLastError(), "dissipative step launch");
+}
+
+template <class C> vlbm_status init_t(vlbm_ctx *c, const double *Q, int64_t c0, int64_t n, int64_t qs)
+{
+    const int threads = 128;
+    k_diss_init<C><<<(unsigned)((n + threads - 1) / threads), threads, 0, c->stream>>>(make_diss_args<C>(c),
+                                                                                      c->dom[0].gamma, c0, n, qs, Q);
+    c->launches++;
+    return cuda_check(c, cudaGetLastError(), "dissipative init launch");
+}
+
+template <class C> vlbm_status moments_t(vlbm_ctx *c, double *out, int64_t c0, int64_t n, int64_t os)
+{
+    const int threads = 256;
+    k_diss_moments<C><<<(unsigned)((n + threads - 1) / threads), threads, 0, c->stream>>>(make_diss_read(c), c0, n,
+                                                                                        os, out);
+    c->launches++;
+    return cuda_check(c, cudaGetLastError(), "dissipative moments launch");
+}
+
+template <class C> vlbm_status gather_t(vlbm_ctx *c, const int64_t *cells, int n, double *out)
+{
+    const int threads = 128;
+    k_diss_gather<C><<<(unsigned)((n + threads - 1) / threads), threads, 0, c->stream>>>(make_diss_read(c), cells, n,
+                                                                                       out);
+    c->launches++;
+    return cuda_check(c, cudaGetLastError(), "dissipative gather launch");
+}
+
+bool is_f64(const vlbm_ctx *c) { return c->storage == VLBM_F64; }
+
+}  // namespace
+
+vlbm_status diss_step(vlbm_ctx *c, int parity)
+{
+    return is_f64(c) ? step_t<double>(c, parity) : step_t<float>(c, parity);
+}
+
+vlbm_status diss_init_range(vlbm_ctx *c, const double *Q, int64_t c0, int64_t n, int64_t qstride)
+{
+    return is_f64(c) ? init_t<double>(c, Q, c0, n, qstride) : init_t<float>(c, Q, c0, n, qstride);
+}
+
+vlbm_status diss_moments_range(vlbm_ctx *c, double *out, int64_t c0, int64_t n, int64_t ostride)
+{
+    return is_f64(c) ? moments_t<double>(c, out, c0, n, ostride) : moments_t<float>(c, out, c0, n, ostride);
+}
+
+vlbm_status diss_gather(vlbm_ctx *c, const int64_t *cells_dev, int n, double *out_dev)
+{
+    return is_f64(c) ? gather_t<double>(c, cells_dev, n, out_dev) : gather_t<float>(c, cells_dev, n, out_dev);
+}
+
+}  // namespace vlbm

@@ -4,7 +4,7 @@
 // step loop (kernels captured once into CUDA graphs of kGraphLen steps per
 // AA parity and replayed), health-flag read-back, staging of host fields in
 // bounded chunks, checkpoints.  Every arithmetic step of the method runs in
-// the kernels of k_ideal.cu, k_resistive.cu and k_batch.cu.
+// the kernels of k_ideal.cu, k_resistive.cu, k_diss.cu and k_batch.cu.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -60,8 +60,9 @@ void dev_free_all(vlbm_ctx *c)
 vlbm_status validate(const vlbm_params *p, bool batch_member)
 {
     if (!p) return VLBM_ERR_ARG;
-    if (p->model != VLBM_IDEAL && p->model != VLBM_RESISTIVE && p->model != VLBM_IDEAL_POWELL) {
-        g_err = "model must be VLBM_IDEAL, VLBM_RESISTIVE or VLBM_IDEAL_POWELL";
+    if (p->model != VLBM_IDEAL && p->model != VLBM_RESISTIVE && p->model != VLBM_IDEAL_POWELL &&
+        p->model != VLBM_DISSIPATIVE) {
+        g_err = "model must be VLBM_IDEAL, VLBM_RESISTIVE, VLBM_IDEAL_POWELL or VLBM_DISSIPATIVE";
         return VLBM_ERR_ARG;
     }
     if (p->dim != 2 && p->dim != 3) {
@@ -93,7 +94,26 @@ vlbm_status validate(const vlbm_params *p, bool batch_member)
             return VLBM_ERR_UNSUPPORTED;
         }
     }
-    if (p->model == VLBM_IDEAL || p->model == VLBM_IDEAL_POWELL) {
+    if (p->model == VLBM_DISSIPATIVE) {
+        if (!(p->tau_g > 0.5) || !(p->tau_g < 1e6) || !(p->tau_m > 0.5) || !(p->tau_m < 1e12)) {
+            g_err = "dissipative model: tau_g and tau_m must be > 1/2";
+            return VLBM_ERR_UNSTABLE;
+        }
+        if (!(p->nu >= 0.0) || !(p->eta0 >= 0.0) || !std::isfinite(p->nu) || !std::isfinite(p->eta0) ||
+            !std::isfinite(p->j_c)) {
+            g_err = "dissipative model: nu and eta0 must be finite and >= 0, j_c finite";
+            return VLBM_ERR_ARG;
+        }
+        if (p->dim != 2) {
+            g_err = "the dissipative model is built in 2-D (D2Q5)";
+            return VLBM_ERR_UNSUPPORTED;
+        }
+        if (p->storage != VLBM_F32 && p->storage != VLBM_F64) {
+            g_err = "the dissipative model is built for F32 and F64 storage";
+            return VLBM_ERR_UNSUPPORTED;
+        }
+    }
+    if (p->model == VLBM_IDEAL || p->model == VLBM_IDEAL_POWELL || p->model == VLBM_DISSIPATIVE) {
         if (!(p->gamma > 1.0)) {
             g_err = "gamma must be > 1";
             return VLBM_ERR_ARG;
@@ -192,6 +212,7 @@ vlbm_status launch_step(vlbm_ctx *c, int parity)
 {
     if (c->batched) return batch_step(c, parity, c->tune_choice);
     if (c->model == VLBM_RESISTIVE) return resistive_step(c, parity);
+    if (c->model == VLBM_DISSIPATIVE) return diss_step(c, parity);
     if (c->closure) return closure_step(c, parity);
     vlbm_status s = ideal_step(c, parity);
     if (s == VLBM_OK && any_open_face(c)) s = open_fill(c, parity ^ 1);  // for the next step's reads
@@ -201,12 +222,14 @@ vlbm_status launch_step(vlbm_ctx *c, int parity)
 vlbm_status init_range(vlbm_ctx *c, int d, const double *Q, int64_t c0, int64_t n, int64_t qs)
 {
     if (c->model == VLBM_RESISTIVE) return resistive_init_range(c, d, Q, c0, n, qs);
+    if (c->model == VLBM_DISSIPATIVE) return diss_init_range(c, Q, c0, n, qs);
     return ideal_init_range(c, d, Q, c0, n, qs);
 }
 
 vlbm_status moments_range(vlbm_ctx *c, int d, double *out, int64_t c0, int64_t n, int64_t os)
 {
     if (c->model == VLBM_RESISTIVE) return resistive_moments_range(c, d, out, c0, n, os);
+    if (c->model == VLBM_DISSIPATIVE) return diss_moments_range(c, out, c0, n, os);
     return ideal_moments_range(c, d, out, c0, n, os);
 }
 
@@ -303,6 +326,11 @@ vlbm_status create_common(const vlbm_params *p, int count, vlbm_ctx **out)
         c->nlat = c->model == VLBM_IDEAL_POWELL ? 9 : 8;
         c->nvar = c->nlat;
         c->nslot = c->nlat * c->q;
+    } else if (c->model == VLBM_DISSIPATIVE) {
+        c->q = 5;
+        c->nlat = 20;
+        c->nvar = 20;
+        c->nslot = 100;
     } else {
         c->q = 19;
         c->nlat = 4;
@@ -387,6 +415,7 @@ void vlbm_default_params(vlbm_params *p)
     }
     p->tau_d = 0.51;
     p->tau_m = 1.0;
+    p->tau_g = 0.51;
 }
 
 vlbm_status vlbm_create(const vlbm_params *p, vlbm_ctx **out) { return create_common(p, 1, out); }
@@ -575,8 +604,9 @@ vlbm_status vlbm_gather_populations(vlbm_ctx *c, int domain, const int64_t *cell
     s = cuda_check(c, cudaMemcpyAsync(d_cells, cells, ncells * sizeof(int64_t), cudaMemcpyHostToDevice, c->stream),
                    "cell upload");
     if (s == VLBM_OK)
-        s = c->model == VLBM_RESISTIVE ? resistive_gather(c, domain, d_cells, ncells, d_out)
-                                       : ideal_gather(c, domain, d_cells, ncells, d_out);
+        s = c->model == VLBM_RESISTIVE     ? resistive_gather(c, domain, d_cells, ncells, d_out)
+            : c->model == VLBM_DISSIPATIVE ? diss_gather(c, d_cells, ncells, d_out)
+                                           : ideal_gather(c, domain, d_cells, ncells, d_out);
     if (s == VLBM_OK)
         s = cuda_check(c, cudaMemcpyAsync(f_host, d_out, (size_t)ncells * c->nslot * sizeof(double),
                                           cudaMemcpyDeviceToHost, c->stream),

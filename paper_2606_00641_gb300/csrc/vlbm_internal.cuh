@@ -31,7 +31,8 @@
 
 namespace vlbm {
 
-constexpr int kMaxLat = 9;  // lattices of one model: ideal 8, Powell 9 (resistive 4)
+constexpr int kMaxLat = 9;  // per-lattice tables of Domain: ideal 8, Powell 9 (resistive 4; the
+                            // dissipative model's 12 gradient lattices share params.tau_g)
 constexpr int kBlockX = 128;     // threads per CTA along x for the step kernels
 constexpr int kReduceBlocks = 1216;  // 8 CTAs per SM on 152 SMs
 constexpr int kReduceThreads = 256;
@@ -197,6 +198,12 @@ vlbm_status resistive_step(vlbm_ctx *c, int parity);
 vlbm_status resistive_moments(vlbm_ctx *c, int d, double *Q_dev);
 vlbm_status resistive_gather(vlbm_ctx *c, int d, const int64_t *cells_dev, int n, double *out_dev);
 vlbm_status resistive_sums(vlbm_ctx *c, int d, double *sums_dev);
+
+// launchers (k_diss.cu): dissipative model, 2-D, F32 / F64 storage
+vlbm_status diss_step(vlbm_ctx *c, int parity);
+vlbm_status diss_init_range(vlbm_ctx *c, const double *Q, int64_t c0, int64_t n, int64_t qstride);
+vlbm_status diss_moments_range(vlbm_ctx *c, double *out, int64_t c0, int64_t n, int64_t ostride);
+vlbm_status diss_gather(vlbm_ctx *c, const int64_t *cells_dev, int n, double *out_dev);
 
 // launchers (k_batch.cu)
 vlbm_status batch_prepare(vlbm_ctx *c);

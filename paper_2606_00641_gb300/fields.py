@@ -312,3 +312,70 @@ def batch_specs(count: int = 64, seed: int = 4004, sides=BATCH_SIDES):
         mach = float(rng.uniform(0.5, 3.0))
         specs.append({"side": side, "gamma": gamma, "mach": mach, "seed": seed + d})
     return specs
+
+
+# ----------------------------------------------------------------------------
+# dissipative MHD with evolved gradients (low-Mach Orszag-Tang set-up)
+# ----------------------------------------------------------------------------
+
+DISSIPATIVE_FIELDS = IDEAL_FIELDS + tuple("G%s%s" % (a, b) for a in "xy" for b in "xyz") + \
+    tuple("W%s%s" % (a, b) for a in "xy" for b in "xyz")
+
+
+@dataclass
+class DissipativeSetup:
+    Q: np.ndarray            # [20, ny, nx]: the 8 MHD fields, G_ab at 8 + 3a + b, W_ab at 14 + 3a + b
+    gamma: float
+    tau: float               # BGK time of the eight MHD lattices
+    tau_g: float             # BGK time of the twelve gradient lattices
+    tau_m: float             # relaxation time of G and W, in steps
+    nu: float                # kinematic viscosity, lattice units
+    eta0: float              # resistivity at zero current, lattice units
+    j_c: float               # current scale of eta(j), lattice units
+    dx: float                # physical cell size
+    dt: float                # physical time per step
+
+
+def low_mach_orszag_tang(n: int, *, u_lat: float = 0.02, mach: float = 0.1, gamma: float = 5.0 / 3.0,
+                         nu_phys: float = 1e-3, jc_phys: float = 25.0, tau_m_phys: float = 0.01,
+                         stab: float = 0.05) -> DissipativeSetup:
+    """The low-Mach resistive Orszag-Tang vortex (sec. 3.3, "Low compressible
+    resistive Orszag-Tang vortex") on an n x n grid of
+    the periodic box [0, 2 pi)^2, in lattice units.
+
+    Physical state: rho = 1, u = (2 cos y, -2 sin x, 0), B = (-2 sin 2y, -2 sin x, 0),
+    kinematic viscosity nu_phys, eta0 = nu, j_c = 25, relaxation time of the
+    gradient tensors tau_M = 0.01, lattice diffusion ("stabilisation") stab * nu.
+    Scaling: velocities and fields by s = u_lat / 2 (so the peak speed component
+    is u_lat), dx = 2 pi / n, dt = s dx, uniform pressure from the sound speed
+    u_lat / mach.  G and W start at their relaxed values tau_M grad B,
+    tau_M grad u (analytic gradients of the profiles, scaled to the lattice).
+    """
+    n = int(n)
+    s = 0.5 * u_lat
+    dx = 2.0 * math.pi / n
+    dt = s * dx
+    x = dx * np.arange(n)[None, :]
+    y = dx * np.arange(n)[:, None]
+    one = np.ones((n, n))
+    ux, uy = s * 2.0 * np.cos(y) * one, -s * 2.0 * np.sin(x) * one
+    Bx, By = -s * 2.0 * np.sin(2.0 * y) * one, -s * 2.0 * np.sin(x) * one
+    c = u_lat / mach
+    p = c * c / gamma  # rho = 1
+    nu = nu_phys * s / dx
+    tau_m = tau_m_phys / dt
+    g = tau_m * s * dx  # tau_M times the lattice derivative of a physical derivative
+    Q = np.zeros((20, n, n))
+    Q[0] = 1.0
+    Q[1], Q[2] = ux, uy
+    Q[4] = p / (gamma - 1.0) + 0.5 * (ux * ux + uy * uy) + 0.5 * (Bx * Bx + By * By)
+    Q[5], Q[6] = Bx, By
+    # G_ab = tau_M d_a B_b:  d_x B_y = -2 cos x,  d_y B_x = -4 cos 2y
+    Q[8 + 1] = g * (-2.0 * np.cos(x)) * one
+    Q[8 + 3] = g * (-4.0 * np.cos(2.0 * y)) * one
+    # W_ab = tau_M d_a u_b:  d_x u_y = -2 cos x,  d_y u_x = -2 sin y
+    Q[14 + 1] = g * (-2.0 * np.cos(x)) * one
+    Q[14 + 3] = g * (-2.0 * np.sin(y)) * one
+    tau = 0.5 + 3.0 * stab * nu  # (tau - 1/2) cs^2 = stab * nu on D2Q5
+    return DissipativeSetup(Q=np.ascontiguousarray(Q), gamma=gamma, tau=tau, tau_g=tau, tau_m=tau_m, nu=nu,
+                            eta0=nu, j_c=jc_phys * s * dx, dx=dx, dt=dt)

@@ -33,6 +33,7 @@ VLBM_ERR_UNSUPPORTED = 8
 VLBM_IDEAL = 0
 VLBM_RESISTIVE = 1
 VLBM_IDEAL_POWELL = 2
+VLBM_DISSIPATIVE = 3
 VLBM_BC_PERIODIC = 0
 VLBM_BC_EQUILIBRIUM = 1
 FACES = {"x-": 0, "x+": 1, "y-": 2, "y+": 3, "z-": 4, "z+": 5}
@@ -71,6 +72,11 @@ class vlbm_params(ctypes.Structure):
         ("alloc_user", ctypes.c_void_p),
         ("tau_d", ctypes.c_double),
         ("tau_m", ctypes.c_double),
+        ("tau_g", ctypes.c_double),
+        ("nu", ctypes.c_double),
+        ("eta0", ctypes.c_double),
+        ("j_c", ctypes.c_double),
+        ("powell", ctypes.c_int),
     ]
 
 
@@ -191,11 +197,15 @@ def make_params(model: int = VLBM_IDEAL, shape=(64, 64, 64), storage="f32", gamm
                 tau=0.51, source=None, force=(0.0, 0.0, 0.0), b_wall=(0.0, 0.0, 0.0),
                 walls_y: bool = False, check_every: int = 0, q_ref=None, q_scale=None,
                 stream: Optional[int] = None, hooks=None, tau_d: float = 0.51,
-                tau_m: float = 1.0) -> vlbm_params:
+                tau_m: float = 1.0, tau_g: float = 0.51, nu: float = 0.0, eta0: float = 0.0,
+                j_c: float = 0.0, powell: bool = False) -> vlbm_params:
     """Parameters for one domain; ``shape`` is (ny, nx) in 2-D, (nz, ny, nx) in 3-D.
 
     ``tau_d`` / ``tau_m`` apply to the Powell model (VLBM_IDEAL_POWELL): the BGK
     time of the divergence lattice and the relaxation time of D (div B = D / tau_m).
+    The dissipative model (VLBM_DISSIPATIVE) takes ``tau_m`` as the relaxation time
+    of its gradient tensors G and W, ``tau_g`` as their lattices' BGK time, the
+    viscosity ``nu``, the resistivity eta0 (1 + |j|^2 / j_c^2) and the Powell switch.
     """
     p = vlbm_default_params()
     p.model = int(model)
@@ -220,6 +230,11 @@ def make_params(model: int = VLBM_IDEAL, shape=(64, 64, 64), storage="f32", gamm
     p.check_every = int(check_every)
     p.tau_d = float(tau_d)
     p.tau_m = float(tau_m)
+    p.tau_g = float(tau_g)
+    p.nu = float(nu)
+    p.eta0 = float(eta0)
+    p.j_c = float(j_c)
+    p.powell = int(bool(powell))
     p.stream = stream if stream else None
     if hooks is not None:
         p.alloc, p.dealloc, p.alloc_user = hooks.alloc, hooks.dealloc, None

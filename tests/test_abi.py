@@ -53,6 +53,8 @@ def test_params_struct_layout_matches_c(V):
     assert list(p.source) == [0.0] * 8 and list(p.q_ref) == [0.0] * 8
     assert (p.walls_y, p.check_every) == (0, 0)
     assert p.stream is None and p.alloc_user is None
+    assert (p.tau_d, p.tau_m, p.tau_g) == (0.51, 1.0, 0.51)
+    assert (p.nu, p.eta0, p.j_c, p.powell) == (0.0, 0.0, 0.0, 0)
 
 
 def test_status_strings(V):
@@ -84,6 +86,18 @@ def test_validation_before_any_device_work(V):
     assert _create_status(V, p) == V.VLBM_ERR_ARG
     p = V.make_params(shape=(8, 8, 8))
     p.nz = 0
+    assert _create_status(V, p) == V.VLBM_ERR_ARG
+    # the dissipative model: 2-D, F32 / F64, tau_g > 1/2, nu and eta0 >= 0
+    p = V.make_params(model=V.VLBM_DISSIPATIVE, shape=(8, 8, 8))
+    assert _create_status(V, p) == V.VLBM_ERR_UNSUPPORTED
+    p = V.make_params(model=V.VLBM_DISSIPATIVE, shape=(8, 8), storage="bf16dev")
+    assert _create_status(V, p) == V.VLBM_ERR_UNSUPPORTED
+    p = V.make_params(model=V.VLBM_DISSIPATIVE, shape=(8, 8), tau_g=0.5)
+    assert _create_status(V, p) == V.VLBM_ERR_UNSTABLE
+    p = V.make_params(model=V.VLBM_DISSIPATIVE, shape=(8, 8), eta0=-1e-3)
+    assert _create_status(V, p) == V.VLBM_ERR_ARG
+    p = V.make_params(shape=(8, 8))
+    p.model = 4
     assert _create_status(V, p) == V.VLBM_ERR_ARG
     # NULL contexts and pointers are argument errors, never crashes
     assert L.vlbm_step(None, 1) == V.VLBM_ERR_ARG
