@@ -62,13 +62,14 @@ __device__ __forceinline__ void ideal_collide(C (&f)[8][AxisSet<D>::Q], const C 
         phi[4][ax] = Ept * u[ax] - B[ax] * uB;
     }
 
-    constexpr C w0 = C(AxisSet<D>::w0), w1 = C(AxisSet<D>::w1);
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
         const C om = omega[k];
         const C omc = C(1) - om;
-        const C A0 = om * w0 * G[k] + src0[k];
-        const C A1 = om * w1 * G[k] + src1[k];
+        C ow0, ow1;
+        relax_weights<D, C>(om, ow0, ow1);
+        const C A0 = ow0 * G[k] + src0[k];
+        const C A1 = ow1 * G[k] + src1[k];
         const C hom = DEV ? C(0.5) * om * inv_scale[k] : C(0.5) * om;  // omega * w_moving / cs^2 (/ s_k)
         f[k][0] = omc * f[k][0] + A0;
 #pragma unroll
@@ -135,13 +136,14 @@ __device__ __forceinline__ void ideal_collide_hom(C (&f)[8][AxisSet<D>::Q], cons
         phi[4][ax] = (Eh + pt) * uh[ax] - Bh[ax] * uBh;
     }
 
-    constexpr C w0 = C(AxisSet<D>::w0), w1 = C(AxisSet<D>::w1);
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
         const C om = omega[k];
         const C omc = C(1) - om;
-        const C A0 = om * w0 * qh[k] + src0[k];
-        const C A1 = om * w1 * qh[k] + src1[k];
+        C ow0, ow1;
+        relax_weights<D, C>(om, ow0, ow1);
+        const C A0 = ow0 * qh[k] + src0[k];
+        const C A1 = ow1 * qh[k] + src1[k];
         const C hom = C(0.5) * om;  // omega * w_moving / cs^2
         f[k][0] = omc * f[k][0] + A0;
 #pragma unroll
@@ -211,13 +213,15 @@ __device__ __forceinline__ void powell_collide(C (&f)[9][AxisSet<D>::Q], const C
     S[4] = ndiv * uB;
     S[8] = ndiv;
 
-    constexpr C w0 = C(AxisSet<D>::w0), w1 = C(AxisSet<D>::w1);
+    constexpr C w0 = ExactWeights<D, C>::w0, w1 = ExactWeights<D, C>::w1;
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
         const C om = omega[k];
         const C omc = C(1) - om;
-        const C A0 = om * w0 * q[k] + src0[k] + w0 * S[k];
-        const C A1 = om * w1 * q[k] + src1[k] + w1 * S[k];
+        C ow0, ow1;
+        relax_weights<D, C>(om, ow0, ow1);
+        const C A0 = ow0 * q[k] + src0[k] + w0 * S[k];
+        const C A1 = ow1 * q[k] + src1[k] + w1 * S[k];
         const C hom = C(0.5) * om;  // omega * w_moving / cs^2
         f[k][0] = omc * f[k][0] + A0;
 #pragma unroll

@@ -169,11 +169,8 @@ __global__ void __launch_bounds__(kBlockX) k_diss_step(const DissArgs<C> a)
     C phi[kDissLat][2], S[kDissLat];
     diss_flux_source<C>(q, a, phi, S, a.flags);
 
-    // Weights that sum to one exactly in the compute precision: w0 = 1 - 4 w1, and
-    // omega w0 = omega - 4 (omega w1) (both differences are exact).  Rounded
-    // products such as omega * w0 would otherwise make every cell gain or lose the
-    // same fraction of Q_k per step, a drift of the FP32 domain sums.
-    constexpr C w1 = C(AxisSet<2>::w1), w0 = C(1) - C(4) * w1;
+    // weights and relaxation products that sum to one (omega) exactly (vlbm_internal.cuh)
+    constexpr C w0 = ExactWeights<2, C>::w0, w1 = ExactWeights<2, C>::w1;
 #pragma unroll
     for (int k = 0; k < kDissLat; ++k) {
         C g[Q];
@@ -181,8 +178,8 @@ __global__ void __launch_bounds__(kBlockX) k_diss_step(const DissArgs<C> a)
         for (int i = 0; i < Q; ++i) g[i] = HOLD ? f[HOLD ? k : 0][i] : *src(k, i);
         const C om = a.omega[k];
         const C omc = C(1) - om;
-        const C ow1 = om * w1;
-        const C ow0 = om - C(4) * ow1;
+        C ow0, ow1;
+        relax_weights<2, C>(om, ow0, ow1);
         const C A0 = ow0 * q[k] + w0 * S[k];
         const C A1 = ow1 * q[k] + w1 * S[k];
         const C hom = C(0.5) * om;  // omega * w_moving / cs^2
@@ -220,7 +217,7 @@ __global__ void k_diss_init(const DissArgs<C> a, double gamma, int64_t c0, int64
         if (!(vsig < (C)sqrt(AxisSet<2>::cs2))) atomicOr(a.flags, kFlagUnstable);
     }
     C *pop = static_cast<C *>(a.pop);
-    constexpr C w1 = C(AxisSet<2>::w1), w0 = C(1) - C(4) * w1;  // as in the step
+    constexpr C w0 = ExactWeights<2, C>::w0, w1 = ExactWeights<2, C>::w1;  // as in the step
     constexpr C h = C(AxisSet<2>::w1 / AxisSet<2>::cs2);
 #pragma unroll
     for (int k = 0; k < kDissLat; ++k) {

@@ -316,7 +316,7 @@ __global__ void k_ideal_init(const InitArgs<D, S> a, const double *__restrict__ 
         const R ref = (R)a.ref[k], inv_scale = (R)(1.0 / a.scale[k]);
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            const R w = (R)(i == 0 ? AxisSet<D>::w0 : AxisSet<D>::w1);
+            const R w = i == 0 ? ExactWeights<D, R>::w0 : ExactWeights<D, R>::w1;
             R cphi = R(0);
             if (i > 0) cphi = ((i & 1) ? R(1) : R(-1)) * phi[(i - 1) / 2];
             const R feq = w * (q[k] + cphi * (R)inv_cs2);
@@ -332,7 +332,7 @@ __global__ void k_ideal_init(const InitArgs<D, S> a, const double *__restrict__ 
         for (int ax = 0; ax < D; ++ax) phi[ax] = Dv * u[ax] - B[ax];
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            const R w = (R)(i == 0 ? AxisSet<D>::w0 : AxisSet<D>::w1);
+            const R w = i == 0 ? ExactWeights<D, R>::w0 : ExactWeights<D, R>::w1;
             R cphi = R(0);
             if (i > 0) cphi = ((i & 1) ? R(1) : R(-1)) * phi[(i - 1) / 2];
             Codec<S>::store(pop + (int64_t)(8 * Q + i) * a.stride + cell,

@@ -57,6 +57,22 @@ template <> struct AxisSet<3> {
     static constexpr double w0 = 1.0 / 4.0, w1 = 1.0 / 8.0, cs2 = 1.0 / 4.0;
 };
 
+// Weights in the compute precision C that sum to one exactly.  D3Q7's 1/4 and
+// 1/8 are exact in binary; for D2Q5, w0 = 1 - 4 w1 (exact: Sterbenz), and the
+// relaxation products omega w0 = omega - 4 (omega w1) (also exact).  With
+// rounded products instead, every cell would gain or lose the same fraction of
+// Q_k per step -- a drift of about one or two ulps per step in the FP32 domain
+// sums of the 2-D forms.
+template <int D, class C> struct ExactWeights {
+    static constexpr C w1 = C(AxisSet<D>::w1);
+    static constexpr C w0 = D == 2 ? C(1) - C(4) * w1 : C(AxisSet<D>::w0);
+};
+template <int D, class C> __device__ __forceinline__ void relax_weights(C om, C &ow0, C &ow1)
+{
+    ow1 = om * ExactWeights<D, C>::w1;
+    ow0 = D == 2 ? om - C(4) * ow1 : om * ExactWeights<D, C>::w0;
+}
+
 // An opaque copy of a value: the compiler cannot reuse expressions computed
 // from the original across it, so addresses built from the copy are
 // recomputed where they are used instead of being held in registers.
