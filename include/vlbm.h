@@ -100,7 +100,10 @@ typedef enum { VLBM_IDEAL = 0, VLBM_RESISTIVE = 1, VLBM_IDEAL_POWELL = 2, VLBM_D
 /* Population storage.  F64: double storage and arithmetic.  F32: float
  * storage and arithmetic.  F16_DEV / BF16_DEV: populations stored as
  * half / bfloat16 shifted deviations (f_ki - w_i q_ref_k) / q_scale_k,
- * decoded to float for the arithmetic. */
+ * decoded to float for the arithmetic, except the gas pressure of cells
+ * below params.p_theta and the moments read back (vlbm_moments,
+ * vlbm_conservation), which decode the FP32 sum of a cell's deviations in
+ * FP64. */
 typedef enum { VLBM_F64 = 0, VLBM_F32 = 1, VLBM_F16_DEV = 2, VLBM_BF16_DEV = 3 } vlbm_storage;
 
 typedef void *(*vlbm_alloc_fn)(size_t bytes, void *stream, void *user);
@@ -139,13 +142,18 @@ typedef struct {
     double eta0;          /* dissipative model: resistivity at zero current, >= 0 */
     double j_c;           /* dissipative model: current scale of eta(j); <= 0: constant eta0 */
     int powell;           /* dissipative model: 1 adds Powell's source */
+    double p_theta;       /* deviation storage (F16_DEV, BF16_DEV): a cell whose FP32 gas
+                             pressure is below p_theta * e_tot (near vacuum, high Mach, low
+                             beta: p is a small difference of large terms) recomputes p in
+                             FP64 from the FP64 reference state q_ref + q_scale * (FP32 sum
+                             of its stored deviations); >= 0, 0 disables */
 } vlbm_params;
 
 /* Fill *p with defaults: ideal MHD, dim 3, 64^3 cells, F32 storage,
  * gamma = 5/3, tau = 0.51 on every lattice (the paper's showcase value,
  * sec. 5 table), no source, no walls, check_every = 0, NULL hooks;
  * Powell model: tau_d = 0.51, tau_m = 1; dissipative model: tau_g = 0.51,
- * nu = eta0 = j_c = 0, no Powell source. */
+ * nu = eta0 = j_c = 0, no Powell source; p_theta = 0.01. */
 void vlbm_default_params(vlbm_params *p);
 
 /* Create a context for one domain: validates p (dims > 0, dim 2 => nz = 1,

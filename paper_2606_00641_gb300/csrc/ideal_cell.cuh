@@ -13,6 +13,20 @@
 
 namespace vlbm {
 
+// Gas pressure of Eq. 9 in FP64 from the FP32 sums G_k of a cell's stored
+// deviations: Q_k = r_k + s_k G_k, refscale = r_0..7 then s_0..7 (device).
+static __device__ __noinline__ double pressure_fp64(float G0, float G1, float G2, float G3, float G4, float G5, float G6,
+                                             float G7, const double *__restrict__ refscale, double gm1)
+{
+    const float G[8] = {G0, G1, G2, G3, G4, G5, G6, G7};
+    double q[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) q[k] = fma((double)G[k], __ldg(refscale + 8 + k), __ldg(refscale + k));
+    const double kin = (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]) / q[0];
+    const double mag = q[5] * q[5] + q[6] * q[6] + q[7] * q[7];
+    return gm1 * (q[4] - 0.5 * kin - 0.5 * mag);
+}
+
 //
 // Deviation storage (DEV): the values in f are the stored deviations
 // g_ki = (f_ki - w_i r_k) / s_k.  Because sum_i w_i = 1 the moment is
@@ -20,22 +34,25 @@ namespace vlbm {
 // g directly: g*_ki = (1 - omega) g_ki + omega w_i G_k + w_i S_k / s_k
 // +- omega Phi_k,a / (2 s_k) with G_k = sum_i g_ki -- no per-population decode
 // or encode.  The caller passes src0/src1 already divided by s_k.
-template <int D, class C, bool DEV = false>
-__device__ __forceinline__ void ideal_collide(C (&f)[8][AxisSet<D>::Q], const C gm1, const C *omega,
-                                              const C *src0, const C *src1, unsigned *flags,
-                                              const C *ref = nullptr, const C *scale = nullptr,
-                                              const C *inv_scale = nullptr)
+//
+// Selective FP64 pressure recovery (deviation storage): where the FP32 gas
+// pressure is below p_theta * e_tot -- near vacuum, high Mach or low beta, where
+// p = (gamma - 1)(e_tot - rho|u|^2/2 - |B|^2/2) is a small difference of large
+// terms -- the cell recomputes p in FP64 from the FP64 reference state,
+// Q_k = r_k + s_k G_k (G_k, the FP32 sum of the stored deviations, is exact to
+// its own rounding; refscale holds r_0..7 then s_0..7 in global memory, read
+// only inside the rare branch so that they occupy no registers elsewhere).
+// Everything else stays FP32.
+// Fluxes phi[k][a] of one cell from its moment sums G_k (deviation storage:
+// Q_k = r_k + s_k G_k), with the positivity check.
+template <int D, class C, bool DEV>
+__device__ __forceinline__ void ideal_flux_of_sums(const C (&G)[8], const C gm1, unsigned *flags, const C *ref,
+                                                   const C *scale, const double *refscale, const C p_theta,
+                                                   C (&phi)[8][D])
 {
-    constexpr int Q = AxisSet<D>::Q;
-    C G[8], q[8];
+    C q[8];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        C s = f[k][0];
-#pragma unroll
-        for (int i = 1; i < Q; ++i) s += f[k][i];
-        G[k] = s;
-        q[k] = DEV ? ref[k] + scale[k] * s : s;
-    }
+    for (int k = 0; k < 8; ++k) q[k] = DEV ? ref[k] + scale[k] * G[k] : G[k];
     const C rho = q[0];
     const C ir = C(1) / rho;
     const C m[3] = {q[1], q[2], q[3]};
@@ -45,12 +62,14 @@ __device__ __forceinline__ void ideal_collide(C (&f)[8][AxisSet<D>::Q], const C 
     const C B2 = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
     const C mu = m[0] * u[0] + m[1] * u[1] + m[2] * u[2];
     const C uB = u[0] * B[0] + u[1] * B[1] + u[2] * B[2];
-    const C p = gm1 * (E - C(0.5) * mu - C(0.5) * B2);
+    C p = gm1 * (E - C(0.5) * mu - C(0.5) * B2);
+    if constexpr (DEV) {
+        if (p_theta > C(0) && p < p_theta * E)  // FP64 pressure recovery (a call: no registers held elsewhere)
+            p = (C)pressure_fp64(G[0], G[1], G[2], G[3], G[4], G[5], G[6], G[7], refscale, (double)gm1);
+    }
     const C pt = p + C(0.5) * B2;
     if (!(rho > C(0)) || !(p > C(0))) atomicOr(flags, kFlagNonPhysical);
     const C Ept = E + pt;
-
-    C phi[8][D];
 #pragma unroll
     for (int ax = 0; ax < D; ++ax) {
         phi[0][ax] = m[ax];
@@ -61,24 +80,51 @@ __device__ __forceinline__ void ideal_collide(C (&f)[8][AxisSet<D>::Q], const C 
         }
         phi[4][ax] = Ept * u[ax] - B[ax] * uB;
     }
+}
 
+// BGK relaxation with source of lattice k's populations fk in place, given
+// its sum G_k and flux phi_k.
+template <int D, class C, bool DEV>
+__device__ __forceinline__ void ideal_relax_lattice(C (&fk)[AxisSet<D>::Q], const int k, const C Gk,
+                                                    const C (&phik)[D], const C *omega, const C *src0,
+                                                    const C *src1, const C *inv_scale)
+{
+    const C om = omega[k];
+    const C omc = C(1) - om;
+    C ow0, ow1;
+    relax_weights<D, C>(om, ow0, ow1);
+    const C A0 = ow0 * Gk + src0[k];
+    const C A1 = ow1 * Gk + src1[k];
+    const C hom = DEV ? C(0.5) * om * inv_scale[k] : C(0.5) * om;  // omega * w_moving / cs^2 (/ s_k)
+    fk[0] = omc * fk[0] + A0;
+#pragma unroll
+    for (int ax = 0; ax < D; ++ax) {
+        const C bv = hom * phik[ax];
+        fk[2 * ax + 1] = omc * fk[2 * ax + 1] + A1 + bv;
+        fk[2 * ax + 2] = omc * fk[2 * ax + 2] + A1 - bv;
+    }
+}
+
+template <int D, class C, bool DEV = false>
+__device__ __forceinline__ void ideal_collide(C (&f)[8][AxisSet<D>::Q], const C gm1, const C *omega,
+                                              const C *src0, const C *src1, unsigned *flags,
+                                              const C *ref = nullptr, const C *scale = nullptr,
+                                              const C *inv_scale = nullptr, const double *refscale = nullptr,
+                                              const C p_theta = C(0))
+{
+    constexpr int Q = AxisSet<D>::Q;
+    C G[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-        const C om = omega[k];
-        const C omc = C(1) - om;
-        C ow0, ow1;
-        relax_weights<D, C>(om, ow0, ow1);
-        const C A0 = ow0 * G[k] + src0[k];
-        const C A1 = ow1 * G[k] + src1[k];
-        const C hom = DEV ? C(0.5) * om * inv_scale[k] : C(0.5) * om;  // omega * w_moving / cs^2 (/ s_k)
-        f[k][0] = omc * f[k][0] + A0;
+        C s = f[k][0];
 #pragma unroll
-        for (int ax = 0; ax < D; ++ax) {
-            const C bv = hom * phi[k][ax];
-            f[k][2 * ax + 1] = omc * f[k][2 * ax + 1] + A1 + bv;
-            f[k][2 * ax + 2] = omc * f[k][2 * ax + 2] + A1 - bv;
-        }
+        for (int i = 1; i < Q; ++i) s += f[k][i];
+        G[k] = s;
     }
+    C phi[8][D];
+    ideal_flux_of_sums<D, C, DEV>(G, gm1, flags, ref, scale, refscale, p_theta, phi);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) ideal_relax_lattice<D, C, DEV>(f[k], k, G[k], phi[k], omega, src0, src1, inv_scale);
 }
 
 // Homogenised solids (sec. 2.4, "Homogenization"): the equilibrium and the

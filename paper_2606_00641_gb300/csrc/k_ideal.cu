@@ -36,6 +36,8 @@ template <class C> struct IdealArgs {
     C inv_tau_m;          // Powell model: 1 / tau_M (div B = D / tau_M)
     const float *solid;   // homogenised solids: [7][solid_n] d, uB, BB per cell, or null
     int64_t solid_n;
+    const double *refscale;  // deviation storage: r_0..7, s_0..7 in FP64 (device; pressure recovery)
+    C p_theta;               // deviation storage: FP64 pressure below p_theta * e_tot
 };
 
 // Linear indices of the cell's neighbours x + c_i (periodic), i in set order.
@@ -64,7 +66,7 @@ __device__ __forceinline__ void neighbours(int x, int y, int z, int nx, int ny, 
 // NL = 9 is the Powell model (eight MHD lattices and the divergence lattice);
 // HOM blends with homogenised solids (a.solid).
 template <int D, class S, class C, bool ODD, bool CORR = false, int NL = 8, bool HOM = false>
-__global__ void __launch_bounds__(kBlockX) k_ideal_step(const IdealArgs<C> a)
+__device__ __forceinline__ void ideal_step_body(const IdealArgs<C> &a)
 {
     constexpr int Q = AxisSet<D>::Q;
     const int x = blockIdx.x * kBlockX + threadIdx.x;
@@ -97,7 +99,7 @@ __global__ void __launch_bounds__(kBlockX) k_ideal_step(const IdealArgs<C> a)
     } else {
         // deviation storage collides on the stored deviations directly (ideal_cell.cuh)
         ideal_collide<D, C, Codec<S>::kDev>(f, a.gm1, a.omega, a.src0, a.src1, a.flags, a.ref, a.scale,
-                                            a.inv_scale);
+                                            a.inv_scale, a.refscale, a.p_theta);
     }
     if constexpr (CORR) {
         const float *dp = a.dphi + cell * 24;
@@ -123,6 +125,21 @@ __global__ void __launch_bounds__(kBlockX) k_ideal_step(const IdealArgs<C> a)
         }
 }
 
+template <int D, class S, class C, bool ODD, bool CORR = false, int NL = 8, bool HOM = false>
+__global__ void __launch_bounds__(kBlockX) k_ideal_step(const IdealArgs<C> a)
+{
+    ideal_step_body<D, S, C, ODD, CORR, NL, HOM>(a);
+}
+
+// Deviation storage: the same step bounded to the occupancy of the plain 16-bit
+// step (six CTAs per SM in 2-D, five in 3-D), so that the rare FP64
+// pressure-recovery call does not lower it.
+template <int D, class S, bool ODD>
+__global__ void __launch_bounds__(kBlockX, D == 2 ? 6 : 5) k_ideal_step_dev(const IdealArgs<float> a)
+{
+    ideal_step_body<D, S, float, ODD>(a);
+}
+
 // The same step for 16-bit storage in 3-D with the loads done by the
 // bulk-copy engine.  A tile is an x-row segment of 128 cells; the 56 slot
 // plane rows its cells read (even parity: their own row; odd parity: the row
@@ -133,12 +150,15 @@ __global__ void __launch_bounds__(kBlockX) k_ideal_step(const IdealArgs<C> a)
 // are in flight while the threads collide the current one from shared memory,
 // so the bytes in flight per SM no longer depend on how many warps the
 // registers allow -- the limit of the one-cell-per-thread kernel on 16-bit
-// storage, whose 2-byte loads carry half the bytes of FP32 ones.  Needs
+// storage, whose 2-byte loads carry half the bytes of FP32 ones.  Four CTAs
+// per SM (128 registers).  Reading the staged populations twice instead of
+// holding them (80 registers, six CTAs) was measured slower: 23.5 against
+// 24.1 GLUPS at 512^3.  Needs
 // nx % 8 == 0 (16-byte aligned rows).
 constexpr int kBulkPad = 8;  // elements (16 bytes) before and after each staged row
 
 template <class S, bool ODD>
-__global__ void __launch_bounds__(kBlockX) k_ideal_step_bulk(const IdealArgs<float> a)
+__global__ void __launch_bounds__(kBlockX, 4) k_ideal_step_bulk(const IdealArgs<float> a)
 {
     constexpr int Q = 7;
     constexpr int ROW = kBlockX + 2 * kBulkPad;
@@ -244,7 +264,7 @@ __global__ void __launch_bounds__(kBlockX) k_ideal_step_bulk(const IdealArgs<flo
                     f[k][ii] = Codec<S>::load(&sm[b][k * Q + jj][kBulkPad + tid + sh]);
                 }
             ideal_collide<3, float, true>(f, a.gm1, a.omega, a.src0, a.src1, a.flags, a.ref, a.scale,
-                                          a.inv_scale);
+                                          a.inv_scale, a.refscale, a.p_theta);
             // store: even parity sends direction i to slot (opp i, x);
             //        odd parity sends direction i to slot (i, x + c_i)
             int64_t nb[Q];
@@ -275,6 +295,7 @@ template <int D, class S> struct InitArgs {
     double gamma;
     double ref[kMaxLat], scale[kMaxLat];
     unsigned *flags;
+    double p_theta;  // deviation storage: p below p_theta * e_tot is taken in FP64, as in the step
 };
 
 template <int D, class S, int NL = 8>
@@ -296,7 +317,16 @@ __global__ void k_ideal_init(const InitArgs<D, S> a, const double *__restrict__ 
     const R u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
     const R uB = u[0] * B[0] + u[1] * B[1] + u[2] * B[2];
     const R gamma = (R)a.gamma;
-    const R p = (gamma - R(1)) * (q[4] - R(0.5) * rho * u2 - R(0.5) * B2);
+    R p = (gamma - R(1)) * (q[4] - R(0.5) * rho * u2 - R(0.5) * B2);
+    if constexpr (Codec<S>::kDev) {
+        if (a.p_theta > 0.0 && p < (R)a.p_theta * q[4]) {  // the step's FP64 recovery, from the FP64 fields
+            double v[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) v[k] = Qin[k * a.qstride + t];
+            p = (R)((a.gamma - 1.0) * (v[4] - 0.5 * (v[1] * v[1] + v[2] * v[2] + v[3] * v[3]) / v[0] -
+                                       0.5 * (v[5] * v[5] + v[6] * v[6] + v[7] * v[7])));
+        }
+    }
     const R pt = p + R(0.5) * B2;
     if (!(rho > R(0)) || !(p > R(0))) atomicOr(a.flags, kFlagNonPhysical);
     const R vsig = sqrt(u2) + sqrt(fmax((gamma * p + B2) * inv_rho, R(0)));
@@ -348,7 +378,6 @@ template <int D, class S> struct ReadArgs {
     int64_t stride;
     int parity;
     double ref[kMaxLat], scale[kMaxLat];
-    float ref_f[kMaxLat], scale_f[kMaxLat];  // FP32 copies for the FP32 compute path
 };
 
 
@@ -365,11 +394,11 @@ __device__ __forceinline__ double logical(const ReadArgs<D, S> &a, int64_t cell,
     return v;
 }
 
-// Q_k of one cell in the compute precision: the sum of its populations (Eq. 3);
-// for deviation storage r_k + s_k sum_i g_ki, since the weights sum to one.
+// Q_k of one cell: the sum of its populations (Eq. 3) in the compute precision;
+// for deviation storage r_k + s_k sum_i g_ki (the weights sum to one), with the
+// FP32 sum widened once and decoded in FP64 against the FP64 reference state.
 template <int D, class S>
-__device__ __forceinline__ typename ComputeOf<S>::T cell_moment(const ReadArgs<D, S> &a, int64_t cell,
-                                                                const int64_t *nb, int k)
+__device__ __forceinline__ double cell_moment(const ReadArgs<D, S> &a, int64_t cell, const int64_t *nb, int k)
 {
     using R = typename ComputeOf<S>::T;
     constexpr int Q = AxisSet<D>::Q;
@@ -381,8 +410,8 @@ __device__ __forceinline__ typename ComputeOf<S>::T cell_moment(const ReadArgs<D
         const int64_t at = a.parity ? nb[opp_axis(i)] : cell;
         s += (R)Codec<S>::load(pop + (int64_t)(k * Q + j) * a.stride + at);
     }
-    if (Codec<S>::kDev) s = s * (R)a.scale_f[k] + (R)a.ref_f[k];
-    return s;
+    if (Codec<S>::kDev) return fma((double)s, a.scale[k], a.ref[k]);
+    return (double)s;
 }
 
 template <int D>
@@ -654,6 +683,8 @@ template <class C> IdealArgs<C> make_step_args(vlbm_ctx *c)
     a.inv_tau_m = C(1.0 / d.tau_m);
     a.solid = c->solid;
     a.solid_n = d.ncell;
+    a.refscale = c->d_refscale;
+    a.p_theta = C(dev ? c->params.p_theta : 0.0);
     return a;
 }
 
@@ -670,8 +701,6 @@ template <int D, class S> ReadArgs<D, S> make_read_args(vlbm_ctx *c, int di)
     for (int k = 0; k < kMaxLat; ++k) {
         a.ref[k] = d.q_ref[k];
         a.scale[k] = d.q_scale[k];
-        a.ref_f[k] = (float)d.q_ref[k];
-        a.scale_f[k] = (float)d.q_scale[k];
     }
     return a;
 }
@@ -718,10 +747,17 @@ template <int D, class S, class C> vlbm_status step_t(vlbm_ctx *c, int parity)
             return cuda_check(c, cudaGetLastError(), "ideal step launch");
         }
     }
-    if (parity)
-        k_ideal_step<D, S, C, true><<<grid, kBlockX, 0, c->stream>>>(a);
-    else
-        k_ideal_step<D, S, C, false><<<grid, kBlockX, 0, c->stream>>>(a);
+    if constexpr (Codec<S>::kDev) {
+        if (parity)
+            k_ideal_step_dev<D, S, true><<<grid, kBlockX, 0, c->stream>>>(a);
+        else
+            k_ideal_step_dev<D, S, false><<<grid, kBlockX, 0, c->stream>>>(a);
+    } else {
+        if (parity)
+            k_ideal_step<D, S, C, true><<<grid, kBlockX, 0, c->stream>>>(a);
+        else
+            k_ideal_step<D, S, C, false><<<grid, kBlockX, 0, c->stream>>>(a);
+    }
     c->launches++;
     return cuda_check(c, cudaGetLastError(), "ideal step launch");
 }
@@ -742,6 +778,7 @@ template <int D, class S> vlbm_status init_t(vlbm_ctx *c, int di, const double *
         a.scale[k] = d.q_scale[k];
     }
     a.flags = c->d_flags;
+    a.p_theta = c->params.p_theta;
     const int threads = 256;
     const unsigned blocks = (unsigned)((count + threads - 1) / threads);
     if constexpr (!Codec<S>::kDev) {

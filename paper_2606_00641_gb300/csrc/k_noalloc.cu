@@ -33,15 +33,14 @@ template <class S> struct NaArgs {
     int64_t ncell, stride;
     int parity;
     double ref[8], scale[8];
-    float ref_f[8], scale_f[8];  // FP32 copies for the FP32 compute path
 };
 
 // Q_k of one cell, with the arithmetic of vlbm_conservation: the populations
 // summed in the compute precision of the storage (FP64 only for FP64
-// storage); deviation storage decodes once, r_k + s_k sum_i g_ki.
+// storage); deviation storage widens that sum once and decodes it in FP64,
+// r_k + s_k sum_i g_ki.
 template <int D, class S>
-__device__ __forceinline__ typename ComputeOf<S>::T na_moment(const NaArgs<S> &a, int64_t cell, int x, int y, int z,
-                                                              int k)
+__device__ __forceinline__ double na_moment(const NaArgs<S> &a, int64_t cell, int x, int y, int z, int k)
 {
     using R = typename ComputeOf<S>::T;
     constexpr int Q = AxisSet<D>::Q;
@@ -61,8 +60,8 @@ __device__ __forceinline__ typename ComputeOf<S>::T na_moment(const NaArgs<S> &a
         }
         s += (R)Codec<S>::load(a.pop + (int64_t)(k * Q + j) * a.stride + at);
     }
-    if (Codec<S>::kDev) s = s * (R)a.scale_f[k] + (R)a.ref_f[k];
-    return s;
+    if (Codec<S>::kDev) return fma((double)s, a.scale[k], a.ref[k]);
+    return (double)s;
 }
 
 template <int D, class S>
@@ -153,8 +152,6 @@ vlbm_status na_run(const void *pop, int nx, int ny, int nz, int64_t stride, int 
     for (int k = 0; k < 8; ++k) {
         a.ref[k] = q_ref ? q_ref[k] : 0.0;
         a.scale[k] = (q_scale && q_scale[k] > 0.0) ? q_scale[k] : 1.0;
-        a.ref_f[k] = (float)a.ref[k];
-        a.scale_f[k] = (float)a.scale[k];
     }
     const int nblocks = (int)((a.ncell + kNaCellsPerBlock - 1) / kNaCellsPerBlock);
     k_na_partials<D, S><<<nblocks, kNaThreads, 0, stream>>>(a, scratch);

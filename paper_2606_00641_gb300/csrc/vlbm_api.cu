@@ -118,6 +118,11 @@ vlbm_status validate(const vlbm_params *p, bool batch_member)
             g_err = "gamma must be > 1";
             return VLBM_ERR_ARG;
         }
+        if ((p->storage == VLBM_F16_DEV || p->storage == VLBM_BF16_DEV) &&
+            (!(p->p_theta >= 0.0) || !std::isfinite(p->p_theta))) {
+            g_err = "p_theta must be finite and >= 0";
+            return VLBM_ERR_ARG;
+        }
         if (p->storage == VLBM_F16_DEV || p->storage == VLBM_BF16_DEV)
             for (int k = 0; k < 8; ++k)
                 if (p->q_scale[k] < 0.0 || !(p->q_scale[k] < 1e300)) {
@@ -357,14 +362,24 @@ vlbm_status create_common(const vlbm_params *p, int count, vlbm_ctx **out)
     if (s == VLBM_OK) {
         c->pop_bytes = (size_t)total * c->elem;
         c->pop = dev_alloc(c, c->pop_bytes);
-        void *status = dev_alloc(c, 256 + (size_t)kReduceBlocks * 8 * sizeof(double) + 8 * sizeof(double));
+        const size_t partial_bytes = (size_t)kReduceBlocks * 8 * sizeof(double);
+        void *status = dev_alloc(c, 256 + partial_bytes + 16 * sizeof(double));
         if (!c->pop || !status) {
             s = fail(c, VLBM_ERR_OOM, "device allocation failed");
         } else {
             c->d_flags = static_cast<unsigned *>(status);
             c->d_sums = reinterpret_cast<double *>(static_cast<char *>(status) + 128);
             c->d_partials = reinterpret_cast<double *>(static_cast<char *>(status) + 256);
+            c->d_refscale = reinterpret_cast<double *>(static_cast<char *>(status) + 256 + partial_bytes);
+            for (int k = 0; k < 8; ++k) {
+                c->h_refscale[k] = c->dom[0].q_ref[k];
+                c->h_refscale[8 + k] = c->dom[0].q_scale[k];
+            }
             s = cuda_check(c, cudaMemsetAsync(c->d_flags, 0, 128, c->stream), "flag clear");
+            if (s == VLBM_OK)
+                s = cuda_check(c, cudaMemcpyAsync(c->d_refscale, c->h_refscale, sizeof(c->h_refscale),
+                                                  cudaMemcpyHostToDevice, c->stream),
+                               "reference state upload");
         }
     }
     if (s == VLBM_OK && c->batched) s = batch_prepare(c);
@@ -416,6 +431,7 @@ void vlbm_default_params(vlbm_params *p)
     p->tau_d = 0.51;
     p->tau_m = 1.0;
     p->tau_g = 0.51;
+    p->p_theta = 0.01;
 }
 
 vlbm_status vlbm_create(const vlbm_params *p, vlbm_ctx **out) { return create_common(p, 1, out); }

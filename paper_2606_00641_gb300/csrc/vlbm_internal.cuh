@@ -150,6 +150,8 @@ struct vlbm_ctx {
     unsigned *h_flags = nullptr;        // pinned host mirror
     double *d_partials = nullptr;       // reduction scratch [kReduceBlocks x 8]
     double *d_sums = nullptr;           // reduction result [8]
+    double *d_refscale = nullptr;       // q_ref[8] then q_scale[8] of domain 0 (deviation storage, FP64)
+    double h_refscale[16] = {};         // host copy (the upload's source; kept alive with the context)
     double *d_q = nullptr;              // staging for host fields (lazily sized)
     size_t d_q_bytes = 0;
     double *h_stage = nullptr;          // pinned host staging

@@ -77,6 +77,7 @@ class vlbm_params(ctypes.Structure):
         ("eta0", ctypes.c_double),
         ("j_c", ctypes.c_double),
         ("powell", ctypes.c_int),
+        ("p_theta", ctypes.c_double),
     ]
 
 
@@ -198,7 +199,7 @@ def make_params(model: int = VLBM_IDEAL, shape=(64, 64, 64), storage="f32", gamm
                 walls_y: bool = False, check_every: int = 0, q_ref=None, q_scale=None,
                 stream: Optional[int] = None, hooks=None, tau_d: float = 0.51,
                 tau_m: float = 1.0, tau_g: float = 0.51, nu: float = 0.0, eta0: float = 0.0,
-                j_c: float = 0.0, powell: bool = False) -> vlbm_params:
+                j_c: float = 0.0, powell: bool = False, p_theta: float = 0.01) -> vlbm_params:
     """Parameters for one domain; ``shape`` is (ny, nx) in 2-D, (nz, ny, nx) in 3-D.
 
     ``tau_d`` / ``tau_m`` apply to the Powell model (VLBM_IDEAL_POWELL): the BGK
@@ -206,6 +207,8 @@ def make_params(model: int = VLBM_IDEAL, shape=(64, 64, 64), storage="f32", gamm
     The dissipative model (VLBM_DISSIPATIVE) takes ``tau_m`` as the relaxation time
     of its gradient tensors G and W, ``tau_g`` as their lattices' BGK time, the
     viscosity ``nu``, the resistivity eta0 (1 + |j|^2 / j_c^2) and the Powell switch.
+    ``p_theta``: deviation storage recomputes the gas pressure in FP64 in cells where
+    the FP32 value is below p_theta * e_tot (0 disables).
     """
     p = vlbm_default_params()
     p.model = int(model)
@@ -235,6 +238,7 @@ def make_params(model: int = VLBM_IDEAL, shape=(64, 64, 64), storage="f32", gamm
     p.eta0 = float(eta0)
     p.j_c = float(j_c)
     p.powell = int(bool(powell))
+    p.p_theta = float(p_theta)
     p.stream = stream if stream else None
     if hooks is not None:
         p.alloc, p.dealloc, p.alloc_user = hooks.alloc, hooks.dealloc, None

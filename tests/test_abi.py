@@ -54,7 +54,7 @@ def test_params_struct_layout_matches_c(V):
     assert (p.walls_y, p.check_every) == (0, 0)
     assert p.stream is None and p.alloc_user is None
     assert (p.tau_d, p.tau_m, p.tau_g) == (0.51, 1.0, 0.51)
-    assert (p.nu, p.eta0, p.j_c, p.powell) == (0.0, 0.0, 0.0, 0)
+    assert (p.nu, p.eta0, p.j_c, p.powell, p.p_theta) == (0.0, 0.0, 0.0, 0, 0.01)
 
 
 def test_status_strings(V):

@@ -282,6 +282,36 @@ def test_deviation_storage_error_bound(V, storage, bound, shape):
 # two tiles with a partial edge tile (136), degenerate extents whose y / z
 # neighbours are the cell itself (1, 1, 64) and (2, 1, 16); nx = 44 takes the
 # per-thread loads
+@pytest.mark.parametrize("storage", ["f16dev", "bf16dev"])
+@pytest.mark.parametrize("shape", [(4, 4, 64), (4, 6, 36), (6, 40)])
+def test_fp64_pressure_recovery_in_a_cold_magnetised_plasma(V, storage, shape):
+    # A static plasma at beta = 5e-9: e_tot = p/(gamma - 1) + B^2/2 with p = 1e-10,
+    # B = 0.2.  In FP32, e_tot - B^2/2 = -1.24e-9 (p is below the ulp of e_tot), so
+    # a step that took p in FP32 would flag the state non-physical; cells with
+    # p < p_theta e_tot recompute it in FP64 from the FP64 reference state and the
+    # state stays put.  (4, 4, 64): bulk-copy kernel; the others: one cell per thread.
+    gamma, B0, p0 = 5.0 / 3.0, 0.2, 1e-10
+    Q0 = np.zeros((8,) + shape)
+    Q0[0] = 1.0
+    Q0[4] = p0 / (gamma - 1) + 0.5 * B0 * B0
+    Q0[7] = B0
+    qref = Q0.reshape(8, -1)[:, 0].copy()
+    qscale = [1.0, 0.01, 0.01, 0.01, 1.0, 1.0, 1.0, 1.0]  # momentum populations carry +-p_tot / 2
+    with V.Context(V.make_params(shape=shape, storage=storage, gamma=gamma, tau=0.6, q_ref=qref,
+                                 q_scale=qscale)) as ctx:
+        assert ctx.init_fields(Q0) == V.VLBM_OK
+        ctx.step(7)
+        got = ctx.moments()
+        assert ctx.sync() == V.VLBM_OK
+    np.testing.assert_array_equal(got, Q0)  # moments decoded in FP64: the state exactly
+    p = (gamma - 1) * (got[4] - 0.5 * (got[1:4] ** 2).sum(0) / got[0] - 0.5 * (got[5:8] ** 2).sum(0))
+    assert np.abs(p / p0 - 1).max() < 1e-6
+    # without the recovery the FP32 pressure is negative and the state is refused
+    with V.Context(V.make_params(shape=shape, storage=storage, gamma=gamma, tau=0.6, q_ref=qref,
+                                 q_scale=qscale, p_theta=0.0)) as ctx:
+        assert ctx.init_fields(Q0) == V.VLBM_ERR_NONPHYSICAL
+
+
 @pytest.mark.parametrize("shape", [(5, 6, 128), (4, 6, 136), (1, 1, 64), (2, 1, 16), (3, 5, 44), (9, 192)])
 @pytest.mark.parametrize("storage,ulp", [("f16dev", 2.0 ** -11), ("bf16dev", 2.0 ** -8)])
 @pytest.mark.parametrize("parity", [0, 1])
