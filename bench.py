@@ -539,34 +539,53 @@ def main():
     step_ms = ms_max / args.steps
 
     # ---- end to end through the C ABI with pinned host buffers ----
-    e2e = None
-    if not args.no_e2e:
-        hostQ = torch.empty(Q.shape, dtype=torch.float64, pin_memory=True)
+    def end_to_end(host_dtype):
+        """Host fields in `host_dtype` (pinned) -> init, steps with a health read-back each, moments back."""
+        f32 = host_dtype == torch.float32
+        hostQ = torch.empty(Q.shape, dtype=host_dtype, pin_memory=True)
         hostQ.copy_(Q)
-        hostOut = torch.empty(Q.shape, dtype=torch.float64, pin_memory=True)
+        hostOut = torch.empty(Q.shape, dtype=host_dtype, pin_memory=True)
         hostOut.zero_()  # a reused output buffer: its pages are resident, as after any earlier call
         barrier()
         t0 = time.perf_counter()
-        st = vlbm.vlbm_init_fields_ptr(ctx.ptr, 0, hostQ.data_ptr())  # synchronises
+        if f32:
+            vlbm.vlbm_init_fields_f32_ptr(ctx.ptr, 0, hostQ.data_ptr())  # synchronises
+        else:
+            vlbm.vlbm_init_fields_ptr(ctx.ptr, 0, hostQ.data_ptr())
         t1 = time.perf_counter()
         for _ in range(args.steps):
             vlbm.vlbm_step(ctx.ptr, 1)
             vlbm.vlbm_sync(ctx.ptr)  # 4-byte health word read back every step
         t2 = time.perf_counter()
-        vlbm.vlbm_moments_ptr(ctx.ptr, 0, hostOut.data_ptr())  # synchronises
+        if f32:
+            vlbm.vlbm_moments_f32_ptr(ctx.ptr, 0, hostOut.data_ptr())  # synchronises
+        else:
+            vlbm.vlbm_moments_ptr(ctx.ptr, 0, hostOut.data_ptr())
         t3 = time.perf_counter()
-        dt = t3 - t0
         barrier()
-        e2e = {"value": world * ncell * args.steps / dt / 1e9, "unit": "GLUPS",
-               "h2d_bytes_per_step": int(Q.numel() * 8 / args.steps),
-               "d2h_bytes_per_step": int(Q.numel() * 8 / args.steps + 4),
-               "note": "vlbm_init_fields from pinned host FP64 fields, per step vlbm_step(1) + "
-                       "vlbm_sync (health word read back), final vlbm_moments to pinned host; the "
-                       "host link of a GB300 measured 211 GB/s H2D and 194 GB/s D2H (pinned), so the two "
-                       "field transfers are bound by it",
-               "ms": {"init_from_host": (t1 - t0) * 1e3, "steps": (t2 - t1) * 1e3,
-                      "moments_to_host": (t3 - t2) * 1e3}}
+        nbytes = Q.numel() * hostQ.element_size()
         del hostQ, hostOut
+        return {"value": world * ncell * args.steps / (t3 - t0) / 1e9, "unit": "GLUPS",
+                "h2d_bytes_per_step": int(nbytes / args.steps),
+                "d2h_bytes_per_step": int(nbytes / args.steps + 4),
+                "ms": {"init_from_host": (t1 - t0) * 1e3, "steps": (t2 - t1) * 1e3,
+                       "moments_to_host": (t3 - t2) * 1e3}}
+
+    e2e = None
+    if not args.no_e2e:
+        if args.storage == "f64":
+            e2e = end_to_end(torch.float64)
+            e2e["note"] = "vlbm_init_fields from pinned host FP64 fields, per step vlbm_step(1) + vlbm_sync " \
+                          "(health word read back), final vlbm_moments to pinned host"
+        else:
+            # the step computes in FP32: single-precision host fields carry everything it uses
+            e2e = end_to_end(torch.float32)
+            e2e["note"] = "vlbm_init_fields_f32 from pinned host FP32 fields (the FP32 step rounds its input " \
+                          "to float first: same populations as from FP64 fields), per step vlbm_step(1) + " \
+                          "vlbm_sync (health word read back), final vlbm_moments_f32 to pinned host; the host " \
+                          "link of a GB300 measured 211 GB/s H2D and 194 GB/s D2H (pinned) and bounds the two " \
+                          "field transfers"
+            e2e["f64_fields"] = end_to_end(torch.float64)
     ctx.close()
 
     # ---- other storage forms: GLUPS and per-field error against FP64 ----

@@ -178,6 +178,17 @@ vlbm_status vlbm_create_batch(const vlbm_params *p, int count, vlbm_ctx **out);
  * Synchronises the stream. */
 vlbm_status vlbm_init_fields(vlbm_ctx *ctx, int domain, const double *Q_host);
 
+/* As vlbm_init_fields from single-precision host fields (nvar x N floats):
+ * the host link carries half the bytes (it bounds the host-field calls: about
+ * 200 GB/s each way on a GB300), and the device widens each staged chunk to
+ * double before the same init kernel, so the result equals vlbm_init_fields on
+ * the fields rounded to float -- bit for bit the same populations wherever
+ * the init arithmetic rounds its inputs to float first (ideal, Powell and
+ * dissipative models with F32 storage).  The FP64 pressure check of 16-bit
+ * storage sees the rounded fields.  F64 storage: VLBM_ERR_UNSUPPORTED (use
+ * vlbm_init_fields).  No counterpart in the paper (host interface only). */
+vlbm_status vlbm_init_fields_f32(vlbm_ctx *ctx, int domain, const float *Q_host);
+
 /* As vlbm_init_fields, Q_dev a device pointer (nvar x N doubles). */
 vlbm_status vlbm_init_fields_device(vlbm_ctx *ctx, int domain, const double *Q_dev);
 
@@ -193,6 +204,13 @@ vlbm_status vlbm_sync(vlbm_ctx *ctx);
 /* Zeroth moments Q_k = sum_i f_ki (Eq. 4) of domain `domain` at the
  * current step, nvar x N doubles into host memory (synchronises). */
 vlbm_status vlbm_moments(vlbm_ctx *ctx, int domain, double *Q_host);
+
+/* As vlbm_moments into single-precision host fields (nvar x N floats), half
+ * the bytes over the host link; each staged chunk is narrowed on the device.
+ * Lossless for F32 storage (its moments are FP32 sums); 16-bit storage: its
+ * FP64-decoded moments rounded to float.  F64 storage: VLBM_ERR_UNSUPPORTED.
+ * Synchronises.  No counterpart in the paper (host interface only). */
+vlbm_status vlbm_moments_f32(vlbm_ctx *ctx, int domain, float *Q_host);
 
 /* As vlbm_moments into a device buffer, enqueued on the stream only. */
 vlbm_status vlbm_moments_device(vlbm_ctx *ctx, int domain, double *Q_dev);

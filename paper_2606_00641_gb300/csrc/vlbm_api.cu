@@ -472,35 +472,55 @@ static vlbm_status begin_init(vlbm_ctx *c, int domain)
     return cuda_check(c, cudaMemsetAsync(c->d_flags, 0, sizeof(unsigned), c->stream), "flag clear");
 }
 
-vlbm_status vlbm_init_fields(vlbm_ctx *c, int domain, const double *Q_host)
+// Host fields (double, or float with f32) through the two staging chunks.  The
+// float form copies half the bytes over the host link and widens each chunk to
+// double on the device before the init kernel, whose arithmetic is unchanged.
+static vlbm_status init_from_host(vlbm_ctx *c, int domain, const void *Q_host, bool f32)
 {
-    if (!c || !Q_host) return VLBM_ERR_ARG;
     vlbm_status s = begin_init(c, domain);
     if (s != VLBM_OK) return s;
     const int64_t N = c->dom[domain].ncell;
     const int64_t chunk = std::min<int64_t>(N, kStageCells);
-    const size_t half = (size_t)c->nvar * chunk;  // doubles per staging buffer
-    s = ensure_stage(c, 2 * half * sizeof(double));
+    const size_t half = (size_t)c->nvar * chunk;  // values per staging buffer
+    s = ensure_stage(c, 2 * half * sizeof(double) + (f32 ? 2 * half * sizeof(float) : 0));
     if (s == VLBM_OK) s = ensure_copy_stream(c);
     // both buffers free once the work already queued on the context's stream is done
     for (int b = 0; b < 2 && s == VLBM_OK; ++b) s = cuda_check(c, cudaEventRecord(c->ev_kern[b], c->stream), "event");
+    float *fstage = reinterpret_cast<float *>(c->d_q + 2 * half);
+    const size_t vbytes = f32 ? sizeof(float) : sizeof(double);
     int i = 0;
     for (int64_t c0 = 0; s == VLBM_OK && c0 < N; c0 += chunk, ++i) {
         const int b = i & 1;
         double *buf = c->d_q + b * half;
+        char *land = f32 ? reinterpret_cast<char *>(fstage + b * half) : reinterpret_cast<char *>(buf);
         const int64_t n = std::min<int64_t>(chunk, N - c0);
         s = cuda_check(c, cudaStreamWaitEvent(c->copy_stream, c->ev_kern[b], 0), "stream order");
         for (int v = 0; v < c->nvar && s == VLBM_OK; ++v)
-            s = cuda_check(c, cudaMemcpyAsync(buf + v * chunk, Q_host + v * N + c0, n * sizeof(double),
+            s = cuda_check(c, cudaMemcpyAsync(land + v * chunk * vbytes,
+                                              static_cast<const char *>(Q_host) + (v * N + c0) * vbytes, n * vbytes,
                                               cudaMemcpyHostToDevice, c->copy_stream),
                            "field upload");
         if (s == VLBM_OK) s = cuda_check(c, cudaEventRecord(c->ev_copy[b], c->copy_stream), "event");
         if (s == VLBM_OK) s = cuda_check(c, cudaStreamWaitEvent(c->stream, c->ev_copy[b], 0), "stream order");
+        if (s == VLBM_OK && f32) s = widen_fields(c, fstage + b * half, c->nvar, n, chunk, buf);
         if (s == VLBM_OK) s = init_range(c, domain, buf, c0, n, chunk);
         if (s == VLBM_OK) s = cuda_check(c, cudaEventRecord(c->ev_kern[b], c->stream), "event");
     }
     if (s != VLBM_OK) return s;
     return finish_init(c);
+}
+
+vlbm_status vlbm_init_fields(vlbm_ctx *c, int domain, const double *Q_host)
+{
+    if (!c || !Q_host) return VLBM_ERR_ARG;
+    return init_from_host(c, domain, Q_host, false);
+}
+
+vlbm_status vlbm_init_fields_f32(vlbm_ctx *c, int domain, const float *Q_host)
+{
+    if (!c || !Q_host) return VLBM_ERR_ARG;
+    if (c->storage == VLBM_F64) return fail(c, VLBM_ERR_UNSUPPORTED, "single-precision fields need FP32 or 16-bit storage");
+    return init_from_host(c, domain, Q_host, true);
 }
 
 vlbm_status vlbm_init_fields_device(vlbm_ctx *c, int domain, const double *Q_dev)
@@ -565,29 +585,35 @@ vlbm_status vlbm_sync(vlbm_ctx *c)
     return apply_flags(c, flags);
 }
 
-vlbm_status vlbm_moments(vlbm_ctx *c, int domain, double *Q_host)
+// Moments to host fields (double, or float with f32) through the staging chunks;
+// the float form narrows each chunk on the device and copies half the bytes.
+static vlbm_status moments_to_host(vlbm_ctx *c, int domain, void *Q_host, bool f32)
 {
-    if (!c || !Q_host) return VLBM_ERR_ARG;
     if (domain < 0 || domain >= (int)c->dom.size()) return fail(c, VLBM_ERR_ARG, "bad domain index");
     const int64_t N = c->dom[domain].ncell;
     const int64_t chunk = std::min<int64_t>(N, kStageCells);
-    const size_t half = (size_t)c->nvar * chunk;  // doubles per staging buffer
-    vlbm_status s = ensure_stage(c, 2 * half * sizeof(double));
+    const size_t half = (size_t)c->nvar * chunk;  // values per staging buffer
+    vlbm_status s = ensure_stage(c, 2 * half * sizeof(double) + (f32 ? 2 * half * sizeof(float) : 0));
     if (s == VLBM_OK) s = ensure_copy_stream(c);
     for (int b = 0; b < 2 && s == VLBM_OK; ++b)  // no download pending on either buffer
         s = cuda_check(c, cudaEventRecord(c->ev_copy[b], c->copy_stream), "event");
+    float *fstage = reinterpret_cast<float *>(c->d_q + 2 * half);
+    const size_t vbytes = f32 ? sizeof(float) : sizeof(double);
     int i = 0;
     for (int64_t c0 = 0; s == VLBM_OK && c0 < N; c0 += chunk, ++i) {
         const int b = i & 1;
         double *buf = c->d_q + b * half;
+        char *land = f32 ? reinterpret_cast<char *>(fstage + b * half) : reinterpret_cast<char *>(buf);
         const int64_t n = std::min<int64_t>(chunk, N - c0);
         s = cuda_check(c, cudaStreamWaitEvent(c->stream, c->ev_copy[b], 0), "stream order");
         if (s == VLBM_OK) s = moments_range(c, domain, buf, c0, n, chunk);
+        if (s == VLBM_OK && f32) s = narrow_fields(c, buf, c->nvar, n, chunk, fstage + b * half);
         if (s == VLBM_OK) s = cuda_check(c, cudaEventRecord(c->ev_kern[b], c->stream), "event");
         if (s == VLBM_OK) s = cuda_check(c, cudaStreamWaitEvent(c->copy_stream, c->ev_kern[b], 0), "stream order");
         for (int v = 0; v < c->nvar && s == VLBM_OK; ++v)
-            s = cuda_check(c, cudaMemcpyAsync(Q_host + v * N + c0, buf + v * chunk, n * sizeof(double),
-                                              cudaMemcpyDeviceToHost, c->copy_stream),
+            s = cuda_check(c, cudaMemcpyAsync(static_cast<char *>(Q_host) + (v * N + c0) * vbytes,
+                                              land + v * chunk * vbytes, n * vbytes, cudaMemcpyDeviceToHost,
+                                              c->copy_stream),
                            "field download");
         if (s == VLBM_OK) s = cuda_check(c, cudaEventRecord(c->ev_copy[b], c->copy_stream), "event");
     }
@@ -595,6 +621,19 @@ vlbm_status vlbm_moments(vlbm_ctx *c, int domain, double *Q_host)
     s = cuda_check(c, cudaStreamSynchronize(c->copy_stream), "moments synchronise");
     if (s != VLBM_OK) return s;
     return cuda_check(c, cudaStreamSynchronize(c->stream), "moments synchronise");
+}
+
+vlbm_status vlbm_moments(vlbm_ctx *c, int domain, double *Q_host)
+{
+    if (!c || !Q_host) return VLBM_ERR_ARG;
+    return moments_to_host(c, domain, Q_host, false);
+}
+
+vlbm_status vlbm_moments_f32(vlbm_ctx *c, int domain, float *Q_host)
+{
+    if (!c || !Q_host) return VLBM_ERR_ARG;
+    if (c->storage == VLBM_F64) return fail(c, VLBM_ERR_UNSUPPORTED, "single-precision fields need FP32 or 16-bit storage");
+    return moments_to_host(c, domain, Q_host, true);
 }
 
 vlbm_status vlbm_moments_device(vlbm_ctx *c, int domain, double *Q_dev)

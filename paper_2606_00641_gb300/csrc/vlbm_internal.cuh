@@ -240,6 +240,11 @@ vlbm_status ideal_features(vlbm_ctx *c, const float *mu, const float *inv_sigma,
 vlbm_status closure_step(vlbm_ctx *c, int parity);
 int closure_cells(const vlbm_closure *cl, int *nx, int *ny, int *nz);
 
+// precision of staged host fields (k_convert.cu): nvar fields of n values each,
+// field v at v * stride, enqueued on the context's stream
+vlbm_status widen_fields(vlbm_ctx *c, const float *in, int nvar, int64_t n, int64_t stride, double *out);
+vlbm_status narrow_fields(vlbm_ctx *c, const double *in, int nvar, int64_t n, int64_t stride, float *out);
+
 // reduction of per-block partials into sums (k_ideal.cu)
 vlbm_status finish_sums(vlbm_ctx *c, int nvar, double *sums_dev);
 

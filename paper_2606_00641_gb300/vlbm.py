@@ -129,6 +129,8 @@ def load(build: bool = True):
         "vlbm_create_batch": (i, [pp, i, ctypes.POINTER(P)]),
         "vlbm_init_fields": (i, [P, i, P]),
         "vlbm_init_fields_device": (i, [P, i, P]),
+        "vlbm_init_fields_f32": (i, [P, i, P]),
+        "vlbm_moments_f32": (i, [P, i, P]),
         "vlbm_step": (i, [P, i]),
         "vlbm_sync": (i, [P]),
         "vlbm_moments": (i, [P, i, P]),
@@ -314,6 +316,19 @@ def vlbm_init_fields_ptr(ctx: int, domain: int, host_ptr: int) -> int:
     return load().vlbm_init_fields(ctx, domain, ctypes.c_void_p(host_ptr))
 
 
+def vlbm_init_fields_f32(ctx: int, domain: int, Q: np.ndarray) -> int:
+    """Single-precision host fields Q [nvar, (nz,) ny, nx] (half the host-link bytes)."""
+    Q = np.ascontiguousarray(Q, dtype=np.float32)
+    st = load().vlbm_init_fields_f32(ctx, domain, Q.ctypes.data_as(ctypes.c_void_p))
+    if st not in (VLBM_OK, VLBM_ERR_UNSTABLE, VLBM_ERR_NONPHYSICAL):
+        _check(st, "vlbm_init_fields_f32", ctx)
+    return st
+
+
+def vlbm_init_fields_f32_ptr(ctx: int, domain: int, host_ptr: int) -> int:
+    return load().vlbm_init_fields_f32(ctx, domain, ctypes.c_void_p(host_ptr))
+
+
 def vlbm_init_fields_device(ctx: int, domain: int, dev_ptr: int) -> int:
     _device_inputs_ready()
     st = load().vlbm_init_fields_device(ctx, domain, ctypes.c_void_p(dev_ptr))
@@ -352,6 +367,16 @@ def vlbm_moments(ctx: int, domain: int, shape) -> np.ndarray:
 
 def vlbm_moments_ptr(ctx: int, domain: int, host_ptr: int):
     _check(load().vlbm_moments(ctx, domain, ctypes.c_void_p(host_ptr)), "vlbm_moments", ctx)
+
+
+def vlbm_moments_f32(ctx: int, domain: int, shape) -> np.ndarray:
+    out = np.empty((vlbm_nvar(ctx),) + tuple(shape), dtype=np.float32)
+    _check(load().vlbm_moments_f32(ctx, domain, out.ctypes.data_as(ctypes.c_void_p)), "vlbm_moments_f32", ctx)
+    return out
+
+
+def vlbm_moments_f32_ptr(ctx: int, domain: int, host_ptr: int):
+    _check(load().vlbm_moments_f32(ctx, domain, ctypes.c_void_p(host_ptr)), "vlbm_moments_f32", ctx)
 
 
 def vlbm_moments_device(ctx: int, domain: int, dev_ptr: int):
@@ -566,6 +591,12 @@ class Context:
 
     def moments(self, domain: int = 0) -> np.ndarray:
         return vlbm_moments(self.ptr, domain, self.shape(domain))
+
+    def init_fields_f32(self, Q, domain: int = 0) -> int:
+        return vlbm_init_fields_f32(self.ptr, domain, Q)
+
+    def moments_f32(self, domain: int = 0) -> np.ndarray:
+        return vlbm_moments_f32(self.ptr, domain, self.shape(domain))
 
     def populations(self, cells, domain: int = 0) -> np.ndarray:
         return vlbm_gather_populations(self.ptr, domain, cells)
