@@ -312,7 +312,10 @@ def test_fp64_pressure_recovery_in_a_cold_magnetised_plasma(V, storage, shape):
         assert ctx.init_fields(Q0) == V.VLBM_ERR_NONPHYSICAL
 
 
-@pytest.mark.parametrize("shape", [(5, 6, 128), (4, 6, 136), (1, 1, 64), (2, 1, 16), (3, 5, 44), (9, 192)])
+# (48, 64, 128) and (24, 40, 200): several row tiles per persistent CTA of the
+# bulk-copy kernel (every staging buffer reused), the latter with ragged tiles
+@pytest.mark.parametrize("shape", [(5, 6, 128), (4, 6, 136), (1, 1, 64), (2, 1, 16), (3, 5, 44), (9, 192),
+                                   (48, 64, 128), (24, 40, 200)])
 @pytest.mark.parametrize("storage,ulp", [("f16dev", 2.0 ** -11), ("bf16dev", 2.0 ** -8)])
 @pytest.mark.parametrize("parity", [0, 1])
 def test_deviation_storage_one_step_sampled(V, shape, storage, ulp, parity):
