@@ -153,8 +153,9 @@ __global__ void __launch_bounds__(kBlockX, D == 2 ? 6 : 5) k_ideal_step_dev(cons
 // storage, whose 2-byte loads carry half the bytes of FP32 ones.  Four CTAs
 // per SM (128 registers).  Measured slower at 512^3 and not adopted: reading
 // the staged populations twice instead of holding them (80 registers, six
-// CTAs; 23.5 against 24.1 GLUPS), and three buffers handed over by full/empty
-// mbarriers instead of the CTA barrier per tile (18.8 GLUPS).  Needs
+// CTAs; 23.5 against 24.1 GLUPS), three buffers handed over by full/empty
+// mbarriers instead of the CTA barrier per tile (18.8 GLUPS), and stores walked
+// direction-major with a running pointer (23.53 against 23.67 GLUPS).  Needs
 // nx % 8 == 0 (16-byte aligned rows).
 constexpr int kBulkPad = 8;  // elements (16 bytes) before and after each staged row
 
