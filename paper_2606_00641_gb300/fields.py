@@ -13,9 +13,10 @@ Recipe (the same for every workload, parameters per workload):
 * velocity: each component its own random-phase sum, scaled so that
   ``max |u| = mach * c_s0`` with ``c_s0 = sqrt(gamma p0 / mean(rho))``;
 * magnetic field ``B = delta x A``, the discrete centred curl of a
-  random-phase vector potential (2-D: ``A = A_z``, plus an independent
-  ``B_z``), so that the centred divergence of B vanishes to round-off;
-  scaled so that ``max |B|^2 = 2 p0 / beta``;
+  random-phase vector potential (differences divided by the cell size
+  1/max(n); 2-D: ``A = A_z``, plus an independent ``B_z``), so that the
+  centred divergence of B vanishes to round-off and the field is the same at
+  every resolution up to O(dx^2); scaled so that ``max |B|^2 = 2 p0 / beta``;
 * uniform gas pressure ``p0``; total energy from the ideal-gas relation of
   the paper's EOS (sec. 2.3) solved for e_tot;
 * lattice scaling (sec. 2.2, "Unit conversion"): with the CFL reading
@@ -177,15 +178,21 @@ def ideal_fields(shape, seed: int, *, gamma: float = 5.0 / 3.0, mach: float = 1.
     rho = rho0 * (1.0 + drho * s / be.amax(s))
     del s
     u = [random_phase(rng, shape, k_u, 2, be) for _ in range(3)]
+    # centred differences divided by one cell size for all axes, 1/max(n) (the
+    # lattice is isotropic: one factor keeps the centred divergence exactly zero),
+    # so that the curl approximates the same field at every resolution
+    inv_h = float(max(shape))
+
+    def d(a, axis):
+        return _cdiff(a, axis, be) * inv_h
+
     if dim == 2:
         Az = random_phase(rng, shape, k_b, 3, be)
-        B = [_cdiff(Az, 1, be), -_cdiff(Az, 0, be), random_phase(rng, shape, k_b, 2, be)]
+        B = [d(Az, 1), -d(Az, 0), random_phase(rng, shape, k_b, 2, be)]
         del Az
     else:
         A = [random_phase(rng, shape, k_b, 3, be) for _ in range(3)]
-        B = [_cdiff(A[2], 1, be) - _cdiff(A[1], 2, be),
-             _cdiff(A[0], 2, be) - _cdiff(A[2], 0, be),
-             _cdiff(A[1], 0, be) - _cdiff(A[0], 1, be)]
+        B = [d(A[2], 1) - d(A[1], 2), d(A[0], 2) - d(A[2], 0), d(A[1], 0) - d(A[0], 1)]
         del A
     cs0 = math.sqrt(gamma * p0 / be.mean(rho))
     umag = be.sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2])

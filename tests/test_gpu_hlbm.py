@@ -59,8 +59,11 @@ def field_errors(got, ref):
 @pytest.mark.parametrize("storage,tol", [("f64", 1e-12), ("f32", 1e-5)])
 @pytest.mark.parametrize("steps", [4, 5])
 def test_hlbm_matches_oracle(V, shape, storage, tol, steps):
+    # beta 4: the blend moves the gas pressure of solid cells by about
+    # (gamma - 1)/2 (omega - 1)/(2 - omega) |B_hat - B|^2 (reading of the homogenisation),
+    # which must stay below p = beta |B|^2 / 2 at these tau
     import torch
-    f0 = fields.ideal_fields(shape, 51, mach=0.5, beta=1.0, cfl=0.2)
+    f0 = fields.ideal_fields(shape, 51, mach=0.5, beta=4.0, cfl=0.2)
     solid, _ = body(shape)
     sd = torch.from_numpy(solid).cuda()
     p = V.make_params(shape=shape, storage=storage, gamma=f0.gamma, tau=TAU)

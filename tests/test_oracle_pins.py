@@ -270,6 +270,28 @@ def test_linear_wave_speed_and_decay(orc, case):
         assert abs(D - D_ce) < 0.03 * D_ce, (name, D, D_ce)
 
 
+def test_first_order_self_convergence(orc):
+    # Acoustic scaling (the lattice velocities do not change with N, so a fixed
+    # physical time is N/2 steps) at fixed tau: the scheme's diffusion
+    # (tau - 1/2)(cs^2 - A^2) dx vanishes linearly with dx, so the solution at N
+    # differs from the one at 2N (sampled at the same points) by O(dx), and the
+    # difference halves when N doubles -- for every field, B included.  A wrong
+    # streaming distance, a time step that does not scale with dx or an input
+    # that changes with the resolution breaks the ratio.
+    runs = {}
+    for n in (32, 64, 128, 256):
+        f0 = fields.ideal_fields((n, n), 1001, mach=0.5, cfl=0.1)
+        runs[n] = orc.ideal_run(f0.Q, f0.gamma, 0.6, n // 2, nthreads=4)
+    err = {}
+    for n in (32, 64, 128):
+        coarse, fine = runs[n], runs[2 * n][:, ::2, ::2]
+        err[n] = np.sqrt(((coarse - fine) ** 2).mean(axis=(1, 2)) / (coarse ** 2).mean(axis=(1, 2)))
+    for n in (32, 64):
+        ratio = err[n] / err[2 * n]
+        assert ((ratio > 1.7) & (ratio < 2.6)).all(), (n, ratio)
+    assert err[128].max() < 0.02
+
+
 def test_brio_wu_states_smoke(orc):
     # the paper's Brio-Wu states (sec. 3.1): the run stays finite and
     # positive, conserves mass exactly, and the undisturbed far field ahead
