@@ -29,7 +29,7 @@
  *   - "Strang splitting": every lattice takes its flux from the step-start
  *     state Q of the same cell; the source is injected in the same collision;
  *   - BGK collision and direct source injection  f* += w_i S_k  (sec. 3:
- *     "BGK ... direct injection");
+ *     BGK collisions with the source injected directly);
  *   - the resistive incompressible model (D3Q19 flow lattice with a
  *     second-order equilibrium carrying the Maxwell stress, Guo body force,
  *     three D3Q7 magnetic lattices with the Eq. 3 equilibrium and the
