@@ -406,6 +406,19 @@ vlbm_status vlbm_restrict(const double *Qf_dev, int nx, int ny, int nz, int fact
 int vlbm_tile_shapes(const vlbm_ctx *ctx);
 vlbm_status vlbm_set_tile_shape(vlbm_ctx *ctx, int shape);
 
+/* Failure-detection self-check (no counterpart in the paper).  The persistent
+ * kernels wait on mbarriers with a bounded number of tries (each may suspend
+ * the waiting thread for up to 20 us; 2^16 tries, about 1.3 s, in the step
+ * kernels); when the tries run out a kernel raises the context's timeout flag,
+ * lets its copies in flight land and returns instead of hanging.  This call
+ * enqueues on the context's stream a one-thread kernel whose wait, by the same
+ * bounded primitive, can never succeed (a barrier expecting two arrivals gets
+ * one) and gives up after `tries` (1 .. 65536, VLBM_ERR_ARG otherwise): the next
+ * vlbm_sync returns VLBM_ERR_TIMEOUT and the context stays failed until
+ * vlbm_init_fields or vlbm_load succeeds, as after a real give-up.  Nothing
+ * faults, traps or hangs; the kernel ends within about tries x 20 us. */
+vlbm_status vlbm_check_bounded_wait(vlbm_ctx *ctx, int tries);
+
 /* Small queries. */
 int vlbm_nvar(const vlbm_ctx *ctx);                  /* 8 ideal, 7 resistive, 9 Powell, 20 dissipative */
 int vlbm_slots_per_cell(const vlbm_ctx *ctx);        /* populations per cell: 40 or 56 (ideal), 40 (D3Q19 +

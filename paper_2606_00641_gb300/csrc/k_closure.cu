@@ -374,6 +374,21 @@ __device__ __forceinline__ bool tc_wait(uint32_t mb, uint32_t phase, volatile in
     return false;
 }
 
+// Bounded wait that ignores the abort flag: on the way out of a CTA that gave up,
+// for the bulk copies it started to land before its shared memory is released.
+__device__ __forceinline__ void tc_drain(uint32_t mb, uint32_t phase)
+{
+    for (uint32_t it = 0; it < kTcWaitIters; ++it) {
+        uint32_t done;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}\n"
+                     : "=r"(done)
+                     : "r"(mb), "r"(phase), "r"(kTcSuspendNs)
+                     : "memory");
+        if (done) return;
+    }
+}
+
 __device__ __forceinline__ void tc_arrive(uint32_t mb)
 {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(mb) : "memory");
@@ -523,6 +538,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(const bf16 *__restric
         if (lane == 0) {
             const uint64_t map_addr = reinterpret_cast<uint64_t>(&halo_map);
             bool ok = true;
+            int issued = 0;  // tiles whose halo copies this thread started
             for (int i = 0; i < n_my && ok; ++i) {
                 const int b = i % kTcBufs;
                 if (i >= kTcBufs && !tc_wait(empty(b), (uint32_t)((i / kTcBufs - 1) & 1), abort)) {
@@ -540,8 +556,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(const bf16 *__restric
                                  " [%0], [%1, {%2, %3, %4, %5}], [%6];\n" ::"r"(hb + (uint32_t)(cb * kTcPlane)),
                                  "l"(map_addr), "r"(8 * (x0 - 1)), "r"(y0 - 1), "r"(z0 - 1), "r"(cb), "r"(tma_bar(b))
                                  : "memory");
+                issued = i + 1;
             }
-            if (!ok) atomicOr(err, kFlagTimeout);
+            if (!ok || *abort) {
+                if (!ok) atomicOr(err, kFlagTimeout);
+                // the CTA gives up: the last copies of each buffer land before it exits
+                for (int j = issued > kTcBufs ? issued - kTcBufs : 0; j < issued; ++j)
+                    tc_drain(tma_bar(j % kTcBufs), (uint32_t)((j / kTcBufs) & 1));
+            }
         }
     } else if (warp >= 8 && warp < 13) {
         // ---- patching: once a tile's box has landed, tiles on the boundary get the periodic

@@ -159,6 +159,41 @@ __global__ void __launch_bounds__(kBlockX, D == 2 ? 6 : 5) k_ideal_step_dev(cons
 // nx % 8 == 0 (16-byte aligned rows).
 constexpr int kBulkPad = 8;  // elements (16 bytes) before and after each staged row
 
+// Bounded wait on phase `parity` of an mbarrier: up to `tries` tries, each of
+// which may suspend the thread for up to 20 us (the default 2^16 tries: about
+// 1.3 s); true once the phase has completed, false when the tries ran out.
+constexpr uint32_t kWaitTries = 1u << 16;
+
+__device__ __forceinline__ bool bounded_wait(uint32_t mbar, uint32_t parity, uint32_t tries = kWaitTries)
+{
+    uint32_t done = 0;
+    for (uint32_t it = 0; it < tries && !done; ++it)
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}\n"
+                     : "=r"(done)
+                     : "r"(mbar), "r"(parity), "r"(20000u)
+                     : "memory");
+    return done != 0;
+}
+
+// The same wait, outcome ignored: on the way out of a CTA that gave up, for its
+// copies in flight.
+__device__ __forceinline__ void bulk_drain(uint32_t mbar, uint32_t parity) { (void)bounded_wait(mbar, parity); }
+
+// Failure-detection self-check: one thread waits, with the bounded wait of the
+// persistent step, for a phase that no thread completes (two arrivals expected,
+// one made), gives up after `tries` and raises the timeout flag exactly as a
+// stuck persistent kernel would.
+__global__ void k_wait_check(unsigned *flags, uint32_t tries)
+{
+    __shared__ __align__(8) uint64_t bar;
+    const uint32_t mb = (uint32_t)__cvta_generic_to_shared(&bar);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(mb), "r"(2));
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(mb) : "memory");
+    if (!bounded_wait(mb, 0u, tries)) atomicOr(flags, kFlagTimeout);
+}
+
 template <class S, bool ODD>
 __global__ void __launch_bounds__(kBlockX, 4) k_ideal_step_bulk(const IdealArgs<float> a)
 {
@@ -241,15 +276,15 @@ __global__ void __launch_bounds__(kBlockX, 4) k_ideal_step_bulk(const IdealArgs<
             load_rows(nxt, b ^ 1);
             if (edge_thread) ev = edge_load(nxt);
         }
-        uint32_t done = 0;
-        for (uint32_t it = 0; it < (1u << 16) && !done; ++it)
-            asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
-                         "selp.u32 %0, 1, 0, p;\n\t}\n"
-                         : "=r"(done)
-                         : "r"(bar_s + 8u * (uint32_t)b), "r"((uint32_t)((i >> 1) & 1)), "r"(20000u)
-                         : "memory");
+        const bool done = bounded_wait(bar_s + 8u * (uint32_t)b, (uint32_t)((i >> 1) & 1));
         if (!__syncthreads_and((int)done)) {  // one outcome for the whole CTA
             if (tid == 0) atomicOr(a.flags, kFlagTimeout);
+            // the CTA gives up: the row copies still in flight (this tile's and the
+            // next one's) land before its shared memory is released, within a bound
+            if (tid < 8 * Q) {
+                bulk_drain(bar_s + 8u * (uint32_t)b, (uint32_t)((i >> 1) & 1));
+                if (tn < ntiles) bulk_drain(bar_s + 8u * (uint32_t)(b ^ 1), (uint32_t)(((i + 1) >> 1) & 1));
+            }
             ok = false;
             break;
         }
@@ -970,6 +1005,13 @@ bool any_open_face(const vlbm_ctx *c)
 }
 
 vlbm_status open_fill(vlbm_ctx *c, int parity) { return dispatch<OpenF>(c, parity); }
+
+vlbm_status wait_check(vlbm_ctx *c, uint32_t tries)
+{
+    k_wait_check<<<1, 1, 0, c->stream>>>(c->d_flags, tries);
+    c->launches++;
+    return cuda_check(c, cudaGetLastError(), "bounded-wait check launch");
+}
 
 vlbm_status porosity_from_distance(const float *phi, int64_t n, double eps_h, float *d, cudaStream_t s)
 {

@@ -847,6 +847,13 @@ vlbm_status vlbm_porosity_from_distance(const float *phi_dev, int64_t n, double 
     return porosity_from_distance(phi_dev, n, eps_h, d_dev, static_cast<cudaStream_t>(stream));
 }
 
+vlbm_status vlbm_check_bounded_wait(vlbm_ctx *c, int tries)
+{
+    if (!c) return VLBM_ERR_ARG;
+    if (tries < 1 || tries > 65536) return fail(c, VLBM_ERR_ARG, "tries must be in 1 .. 65536");
+    return wait_check(c, (uint32_t)tries);
+}
+
 int vlbm_tile_shapes(const vlbm_ctx *c) { return (c && c->batched) ? batch_num_choices() : 0; }
 
 vlbm_status vlbm_set_tile_shape(vlbm_ctx *c, int shape)

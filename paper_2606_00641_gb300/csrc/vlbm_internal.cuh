@@ -233,6 +233,8 @@ vlbm_status ideal_step_corrected(vlbm_ctx *c, int parity, const float *dphi);
 // porosity of the signed distance (HLBM), elementwise
 vlbm_status porosity_from_distance(const float *phi, int64_t n, double eps_h, float *d, cudaStream_t s);
 bool any_open_face(const vlbm_ctx *c);
+// failure-detection self-check: a bounded wait that must give up (k_ideal.cu)
+vlbm_status wait_check(vlbm_ctx *c, uint32_t tries);
 vlbm_status open_fill(vlbm_ctx *c, int parity);
 // closure input features of a 3-D FP32 context straight from its populations:
 // x[cell][k] = BF16((Q_k - mu_k) * inv_sigma_k), Q_k summed in FP32 as by ideal_moments

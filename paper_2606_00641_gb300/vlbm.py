@@ -167,6 +167,7 @@ def load(build: bool = True):
         "vlbm_porosity_from_distance": (i, [P, ctypes.c_int64, d, P, P]),
         "vlbm_closure_destroy": (None, [P]),
         "vlbm_restrict": (i, [P, i, i, i, i, P, P]),
+        "vlbm_check_bounded_wait": (i, [P, i]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -449,6 +450,12 @@ def vlbm_stream(ctx: int) -> int:
 def vlbm_destroy(ctx: int):
     if ctx:
         load().vlbm_destroy(ctx)
+
+
+def vlbm_check_bounded_wait(ctx: int, tries: int = 64) -> None:
+    """Enqueue the failure-detection self-check: a bounded wait that gives up and
+    raises the context's timeout flag (the next sync returns VLBM_ERR_TIMEOUT)."""
+    _check(load().vlbm_check_bounded_wait(ctx, int(tries)), "vlbm_check_bounded_wait", ctx)
 
 
 def vlbm_restrict(Qf_ptr: int, shape, factor: int, Qc_ptr: int, stream: int = 0):
