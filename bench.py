@@ -553,6 +553,14 @@ def main():
     per_launch_ms = ms / args.steps
     achieved = ncell * bytes_cell / (per_launch_ms * 1e-3) / 1e9
     step_ms = ms_max / args.steps
+    # spread: five more timed regions of the same length (every rank takes part in
+    # the barriers; rank 0 reports its own; the line's value is the first region,
+    # taken with the clock sampler running)
+    reps = [timed(ctx, args.steps, 0)[0] for _ in range(5)] if args.steps > 0 else []
+    rep_glups = [ncell * args.steps / (r * 1e-3) / 1e9 for r in reps]
+    spread = ({"n": len(rep_glups), "glups_mean": statistics.mean(rep_glups),
+               "glups_std": statistics.stdev(rep_glups) if len(rep_glups) > 1 else 0.0,
+               "glups_min": min(rep_glups), "glups_max": max(rep_glups)} if rep_glups else None)
 
     # ---- end to end through the C ABI with pinned host buffers ----
     def end_to_end(host_dtype):
@@ -683,6 +691,7 @@ def main():
                          "kernel": STEP_KERNEL[args.storage],
                          "algorithmic_bytes_per_launch": ncell * bytes_cell},
             "clocks": clk,
+            "repeats": spread,
             "gpu_launches": launches,
             "e2e": e2e,
             "cpu_baseline": cpu,
