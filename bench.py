@@ -32,16 +32,16 @@ if ROOT not in sys.path:
 BYTES_PER_POP = {"f64": 8, "f32": 4, "f16dev": 2, "bf16dev": 2}
 # DRAM bytes (read + write) per cell update of the step kernel, from one ncu
 # capture of a 256^3 launch of each parity, taken after the last change to the
-# kernels' source (profiles/bench_512cubed_launch_list.md: mean of the two
-# parities); traffic grows in proportion to the cells, so a full launch is this
-# times the cells.  Set an entry to None whenever that kernel changes until it
-# is re-captured.
-MEASURED_DRAM_BYTES_PER_CELL = {"f32": 7457219e3 / 16777216, "f16dev": 3696923e3 / 16777216}
+# kernels' source (f32: profiles/bench_512cubed_launch_list.md; f16dev:
+# profiles/k_ideal_step_f16dev_256cubed.md; mean of the two parities); traffic
+# grows in proportion to the cells, so a full launch is this times the cells.
+# Set an entry to None whenever that kernel changes until it is re-captured.
+MEASURED_DRAM_BYTES_PER_CELL = {"f32": 7457219e3 / 16777216, "f16dev": 3705818e3 / 16777216}
 # the step kernel the roofline describes, per storage (3-D, nx % 8 == 0)
 STEP_KERNEL = {"f32": "k_ideal_step<3,float,float> (fused collide+stream)",
                "f64": "k_ideal_step<3,double,double> (fused collide+stream; FP64-pipe bound on GB300)",
-               "f16dev": "k_ideal_step_bulk<__half> (fused collide+stream, bulk-copy loads)",
-               "bf16dev": "k_ideal_step_bulk<__nv_bfloat16> (fused collide+stream, bulk-copy loads)"}
+               "f16dev": "k_ideal_step_pairs<__half> (fused collide+stream, bulk-copy loads, 2 cells/thread)",
+               "bf16dev": "k_ideal_step_pairs<__nv_bfloat16> (fused collide+stream, bulk-copy loads, 2 cells/thread)"}
 WORKLOAD = "ideal MHD 3-D, 8 x D3Q7, periodic, random-phase k<=4, Mach 2, beta 1, CFL 0.2, tau 0.51"
 
 

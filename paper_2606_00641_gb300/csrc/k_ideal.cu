@@ -150,13 +150,15 @@ __global__ void __launch_bounds__(kBlockX, D == 2 ? 6 : 5) k_ideal_step_dev(cons
 // are in flight while the threads collide the current one from shared memory,
 // so the bytes in flight per SM no longer depend on how many warps the
 // registers allow -- the limit of the one-cell-per-thread kernel on 16-bit
-// storage, whose 2-byte loads carry half the bytes of FP32 ones.  Four CTAs
-// per SM (128 registers).  Measured slower at 512^3 and not adopted: reading
-// the staged populations twice instead of holding them (80 registers, six
-// CTAs; 23.5 against 24.1 GLUPS), three buffers handed over by full/empty
-// mbarriers instead of the CTA barrier per tile (18.8 GLUPS), and stores walked
-// direction-major with a running pointer (23.53 against 23.67 GLUPS).  Needs
-// nx % 8 == 0 (16-byte aligned rows).
+// storage, whose 2-byte loads carry half the bytes of FP32 ones.  Each thread
+// takes two x-adjacent cells (k_ideal_step_pairs below): the instruction issue
+// of ~970 instructions per cell bound the one-cell-per-thread form of this
+// kernel at 0.78 of the HBM roofline.  Measured slower at 512^3 and not
+// adopted (one cell per thread): reading the staged populations twice instead
+// of holding them (80 registers, six CTAs; 23.5 against 24.1 GLUPS), three
+// buffers handed over by full/empty mbarriers instead of the CTA barrier per
+// tile (18.8 GLUPS), and stores walked direction-major with a running pointer
+// (23.53 against 23.67 GLUPS).  Needs nx % 8 == 0 (16-byte aligned rows).
 constexpr int kBulkPad = 8;  // elements (16 bytes) before and after each staged row
 
 // Bounded wait on phase `parity` of an mbarrier: up to `tries` tries, each of
@@ -194,8 +196,39 @@ __global__ void k_wait_check(unsigned *flags, uint32_t tries)
     if (!bounded_wait(mb, 0u, tries)) atomicOr(flags, kFlagTimeout);
 }
 
+// 16-bit pair access: two adjacent cells' values of one slot row as one 32-bit word.
+template <class S> struct Pair;
+template <> struct Pair<__half> {
+    __device__ static __forceinline__ float2 load(const __half *p)
+    {
+        return __half22float2(*reinterpret_cast<const __half2 *>(p));
+    }
+    __device__ static __forceinline__ void store(__half *p, float lo, float hi)
+    {
+        *reinterpret_cast<__half2 *>(p) = __floats2half2_rn(lo, hi);
+    }
+};
+template <> struct Pair<__nv_bfloat16> {
+    __device__ static __forceinline__ float2 load(const __nv_bfloat16 *p)
+    {
+        return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(p));
+    }
+    __device__ static __forceinline__ void store(__nv_bfloat16 *p, float lo, float hi)
+    {
+        *reinterpret_cast<__nv_bfloat162 *>(p) = __floats2bfloat162_rn(lo, hi);
+    }
+};
+
+// The bulk-copy step with two x-adjacent cells per thread (64 threads per 128-cell
+// tile).  A slot row's values of the pair are one 32-bit word in shared memory and
+// in global memory (rows start on 16-byte boundaries and the pair on an even
+// cell), so loads, conversions and stores come in pairs, and one address serves
+// both cells; only the x-moving slots of the odd parity, shifted by one cell,
+// stay 16-bit.  Needs nx % 8 == 0.
+constexpr int kPairThreads = kBlockX / 2;
+
 template <class S, bool ODD>
-__global__ void __launch_bounds__(kBlockX, 4) k_ideal_step_bulk(const IdealArgs<float> a)
+__global__ void __launch_bounds__(kPairThreads, 6) k_ideal_step_pairs(const IdealArgs<float> a)
 {
     constexpr int Q = 7;
     constexpr int ROW = kBlockX + 2 * kBulkPad;
@@ -229,7 +262,7 @@ __global__ void __launch_bounds__(kBlockX, 4) k_ideal_step_bulk(const IdealArgs<
         T.c0 = T.row + T.x0;
         return T;
     };
-    // slot plane j = tid: arm the buffer's barrier with its bytes and copy its row segment
+    // slot plane j = tid (threads 0 .. 55): arm the buffer's barrier and copy its row segment
     auto load_rows = [&](const Tile &T, int b) {
         if (tid >= 8 * Q) return;
         const int j = tid, jj = j % Q;
@@ -249,21 +282,27 @@ __global__ void __launch_bounds__(kBlockX, 4) k_ideal_step_bulk(const IdealArgs<
                      ::"r"(dst), "l"(pop + (int64_t)j * a.stride + src), "r"(bytes), "r"(mb)
                      : "memory");
     };
-    // odd parity: +x reads slot 2 at x - 1, -x reads slot 1 at x + 1, one element beyond each tile edge
-    const bool edge_thread = ODD && tid >= 64 && tid < 80;
-    const int eq = tid - 64, ek = eq & 7;
-    const int ej = eq < 8 ? ek * Q + 2 : ek * Q + 1;
-    auto edge_load = [&](const Tile &T) -> S {
+    // odd parity: +x reads slot 2 at x - 1, -x reads slot 1 at x + 1, one element beyond
+    // each tile edge; threads 56 .. 63 stage two of the sixteen each
+    const bool edge_thread = ODD && tid >= 8 * Q;
+    const int eq0 = 2 * (tid - 8 * Q);
+    auto edge_slot = [&](int eq) { return eq < 8 ? (eq & 7) * Q + 2 : (eq & 7) * Q + 1; };
+    auto edge_load = [&](const Tile &T, int eq) -> S {
         const int xs = eq < 8 ? (T.x0 > 0 ? T.x0 - 1 : a.nx - 1) : (T.x0 + T.tx < a.nx ? T.x0 + T.tx : 0);
-        return pop[(int64_t)ej * a.stride + T.row + xs];
+        return pop[(int64_t)edge_slot(eq) * a.stride + T.row + xs];
     };
-    auto edge_store = [&](const Tile &T, int b, S v) { sm[b][ej][eq < 8 ? kBulkPad - 1 : kBulkPad + T.tx] = v; };
+    auto edge_store = [&](const Tile &T, int b, int eq, S v) {
+        sm[b][edge_slot(eq)][eq < 8 ? kBulkPad - 1 : kBulkPad + T.tx] = v;
+    };
 
     int t = blockIdx.x;
     Tile cur = tile_of(t);
     if (t < ntiles) {
         load_rows(cur, 0);
-        if (edge_thread) edge_store(cur, 0, edge_load(cur));
+        if (edge_thread) {
+            edge_store(cur, 0, eq0, edge_load(cur, eq0));
+            edge_store(cur, 0, eq0 + 1, edge_load(cur, eq0 + 1));
+        }
     }
     __syncthreads();
     bool ok = true;
@@ -271,16 +310,18 @@ __global__ void __launch_bounds__(kBlockX, 4) k_ideal_step_bulk(const IdealArgs<
         const int b = i & 1;
         const int tn = t + gridDim.x;
         const Tile nxt = tile_of(tn);
-        S ev{};
+        S ev0{}, ev1{};
         if (tn < ntiles) {  // the next tile's rows travel while this one is collided
             load_rows(nxt, b ^ 1);
-            if (edge_thread) ev = edge_load(nxt);
+            if (edge_thread) {
+                ev0 = edge_load(nxt, eq0);
+                ev1 = edge_load(nxt, eq0 + 1);
+            }
         }
         const bool done = bounded_wait(bar_s + 8u * (uint32_t)b, (uint32_t)((i >> 1) & 1));
         if (!__syncthreads_and((int)done)) {  // one outcome for the whole CTA
             if (tid == 0) atomicOr(a.flags, kFlagTimeout);
-            // the CTA gives up: the row copies still in flight (this tile's and the
-            // next one's) land before its shared memory is released, within a bound
+            // the CTA gives up: the row copies still in flight land first, within a bound
             if (tid < 8 * Q) {
                 bulk_drain(bar_s + 8u * (uint32_t)b, (uint32_t)((i >> 1) & 1));
                 if (tn < ntiles) bulk_drain(bar_s + 8u * (uint32_t)(b ^ 1), (uint32_t)(((i + 1) >> 1) & 1));
@@ -288,34 +329,64 @@ __global__ void __launch_bounds__(kBlockX, 4) k_ideal_step_bulk(const IdealArgs<
             ok = false;
             break;
         }
-        if (tid < cur.tx) {
-            const int x = cur.x0 + tid;
-            const int64_t cell = cur.c0 + tid;
-            float f[8][Q];
+        const int xl = 2 * tid;  // cells xl and xl + 1 of the tile
+        if (xl < cur.tx) {
+            float fa[8][Q], fb[8][Q];
 #pragma unroll
             for (int k = 0; k < 8; ++k)
 #pragma unroll
                 for (int ii = 0; ii < Q; ++ii) {
                     const int jj = ODD ? opp_axis(ii) : ii;
-                    const int sh = ODD ? (ii == 1 ? -1 : (ii == 2 ? 1 : 0)) : 0;
-                    f[k][ii] = Codec<S>::load(&sm[b][k * Q + jj][kBulkPad + tid + sh]);
+                    const S *r = &sm[b][k * Q + jj][kBulkPad + xl];
+                    if (ODD && (ii == 1 || ii == 2)) {  // shifted by one cell: 16-bit
+                        const int sh = ii == 1 ? -1 : 1;
+                        fa[k][ii] = Codec<S>::load(r + sh);
+                        fb[k][ii] = Codec<S>::load(r + 1 + sh);
+                    } else {
+                        const float2 v = Pair<S>::load(r);
+                        fa[k][ii] = v.x;
+                        fb[k][ii] = v.y;
+                    }
                 }
-            ideal_collide<3, float, true>(f, a.gm1, a.omega, a.src0, a.src1, a.flags, a.ref, a.scale,
+            ideal_collide<3, float, true>(fa, a.gm1, a.omega, a.src0, a.src1, a.flags, a.ref, a.scale,
                                           a.inv_scale, a.refscale, a.p_theta);
-            // store: even parity sends direction i to slot (opp i, x);
-            //        odd parity sends direction i to slot (i, x + c_i)
-            int64_t nb[Q];
-            neighbours<3>(x, cur.y, cur.z, a.nx, a.ny, a.nz, cell, nb);
+            ideal_collide<3, float, true>(fb, a.gm1, a.omega, a.src0, a.src1, a.flags, a.ref, a.scale,
+                                          a.inv_scale, a.refscale, a.p_theta);
+            // store: even parity sends direction i to slot (opp i, x); odd parity to slot
+            // (i, x + c_i), which keeps the pair together except along x
+            const int xa = cur.x0 + xl;
+            const int64_t ca = cur.c0 + xl;
+            int64_t off[Q];  // x + c_i - x for the y and z directions (periodic), pair-aligned
+            off[0] = 0;
+            off[3] = cur.y + 1 < a.ny ? a.nx : -(int64_t)(a.ny - 1) * a.nx;
+            off[4] = cur.y > 0 ? -(int64_t)a.nx : (int64_t)(a.ny - 1) * a.nx;
+            off[5] = cur.z + 1 < a.nz ? plane : -(int64_t)(a.nz - 1) * plane;
+            off[6] = cur.z > 0 ? -plane : (int64_t)(a.nz - 1) * plane;
+            off[1] = off[2] = 0;
+            const int64_t pa_plus = xa + 1 < a.nx ? ca + 1 : ca + 1 - a.nx;       // a + e_x
+            const int64_t pb_plus = xa + 2 < a.nx ? ca + 2 : ca + 2 - a.nx;       // b + e_x
+            const int64_t pa_minus = xa > 0 ? ca - 1 : ca - 1 + a.nx;             // a - e_x
 #pragma unroll
             for (int k = 0; k < 8; ++k)
 #pragma unroll
                 for (int ii = 0; ii < Q; ++ii) {
                     const int j = ODD ? ii : opp_axis(ii);
-                    const int64_t at = ODD ? nb[ii] : cell;
-                    Codec<S>::store(pop + (int64_t)(k * Q + j) * a.stride + at, f[k][ii]);
+                    S *row = pop + (int64_t)(k * Q + j) * a.stride;
+                    if (ODD && ii == 1) {
+                        Codec<S>::store(row + pa_plus, fa[k][ii]);
+                        Codec<S>::store(row + pb_plus, fb[k][ii]);
+                    } else if (ODD && ii == 2) {
+                        Codec<S>::store(row + pa_minus, fa[k][ii]);
+                        Codec<S>::store(row + ca, fb[k][ii]);  // b - e_x = a
+                    } else {
+                        Pair<S>::store(row + ca + (ODD ? off[ii] : 0), fa[k][ii], fb[k][ii]);
+                    }
                 }
         }
-        if (edge_thread && tn < ntiles) edge_store(nxt, b ^ 1, ev);
+        if (edge_thread && tn < ntiles) {
+            edge_store(nxt, b ^ 1, eq0, ev0);
+            edge_store(nxt, b ^ 1, eq0 + 1, ev1);
+        }
         __syncthreads();  // buffer b consumed before it is refilled; edge elements visible
         cur = nxt;
     }
@@ -771,15 +842,15 @@ template <int D, class S, class C> vlbm_status step_t(vlbm_ctx *c, int parity)
                 int dev = 0, sms = 1, per_sm = 1;
                 cudaGetDevice(&dev);
                 cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ideal_step_bulk<S, false>, kBlockX, 0);
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ideal_step_pairs<S, false>, kPairThreads, 0);
                 c->bulk_ctas = std::max(1, sms) * std::max(1, per_sm);
             }
             const int ntiles = (int)grid.x * d.ny * d.nz;
             const unsigned g = (unsigned)std::min(ntiles, c->bulk_ctas);
             if (parity)
-                k_ideal_step_bulk<S, true><<<g, kBlockX, 0, c->stream>>>(a);
+                k_ideal_step_pairs<S, true><<<g, kPairThreads, 0, c->stream>>>(a);
             else
-                k_ideal_step_bulk<S, false><<<g, kBlockX, 0, c->stream>>>(a);
+                k_ideal_step_pairs<S, false><<<g, kPairThreads, 0, c->stream>>>(a);
             c->launches++;
             return cuda_check(c, cudaGetLastError(), "ideal step launch");
         }
