@@ -99,12 +99,18 @@ def test_validation_before_any_device_work(V):
     p = V.make_params(shape=(8, 8))
     p.model = 4
     assert _create_status(V, p) == V.VLBM_ERR_ARG
+    # deviation storage: the FP64 pressure-recovery threshold must be finite and >= 0
+    p = V.make_params(shape=(8, 8, 8), storage="f16dev", p_theta=-0.1)
+    assert _create_status(V, p) == V.VLBM_ERR_ARG
     # NULL contexts and pointers are argument errors, never crashes
     assert L.vlbm_step(None, 1) == V.VLBM_ERR_ARG
     assert L.vlbm_sync(None) == V.VLBM_ERR_ARG
     assert L.vlbm_moments(None, 0, None) == V.VLBM_ERR_ARG
     assert L.vlbm_init_fields(None, 0, None) == V.VLBM_ERR_ARG
     assert L.vlbm_conservation(None, 0, None) == V.VLBM_ERR_ARG
+    assert L.vlbm_init_fields_f32(None, 0, None) == V.VLBM_ERR_ARG
+    assert L.vlbm_moments_f32(None, 0, None) == V.VLBM_ERR_ARG
+    assert L.vlbm_check_bounded_wait(None, 64) == V.VLBM_ERR_ARG
     assert L.vlbm_nvar(None) == 0
     L.vlbm_destroy(None)
 
