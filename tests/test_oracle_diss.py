@@ -176,6 +176,37 @@ def test_uniform_step_with_the_powell_source_and_relaxing_gradients():
     np.testing.assert_allclose(one, expect, rtol=1e-12, atol=1e-16)
 
 
+def test_low_mach_orszag_tang_set_up_carries_the_paper_parameters():
+    # the generator's unit conversion against the numbers the paper prints (golden file):
+    # Re = U L / nu with the peak speed component U and the box side L, eta0 = nu, j_c, the
+    # 5 % stabilisation and tau_M, all recovered from the lattice values
+    import math
+    import os
+    gold = {}
+    with open(os.path.join(os.path.dirname(__file__), "golden", "low_mach_orszag_tang.txt")) as fh:
+        for line in fh:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                k, v = (t.strip() for t in line.split("="))
+                gold[k] = float(v)
+    n = int(gold["finest_n"])
+    s = fields.low_mach_orszag_tang(n)
+    scale = s.dt / s.dx                      # lattice velocity per physical velocity
+    nu_phys = s.nu * s.dx * s.dx / s.dt      # lattice to physical diffusivity
+    assert abs(nu_phys / gold["nu"] - 1) < 1e-12
+    assert abs(gold["u_peak_component"] * 2 * math.pi / nu_phys / gold["reynolds"] - 1) < 1e-12
+    assert s.eta0 == s.nu
+    assert abs(s.j_c / (scale * s.dx) / gold["j_c"] - 1) < 1e-12
+    assert abs((s.tau - 0.5) * CS2 / s.nu / gold["stabilisation"] - 1) < 1e-12
+    assert abs(s.tau_m * s.dt / gold["tau_m"] - 1) < 1e-12
+    u = s.Q[1:3] / s.Q[0]
+    assert abs(np.abs(u).max() / scale / gold["u_peak_component"] - 1) < 1e-6
+    assert abs(np.abs(s.Q[5:7]).max() / scale / gold["B_peak_component"] - 1) < 1e-6
+    # G and W start at tau_M times the field gradients (centred differences agree to O(dx^2))
+    dBy_dx = 0.5 * (np.roll(s.Q[6], -1, 1) - np.roll(s.Q[6], 1, 1))
+    assert np.abs(s.Q[8 + 1] - s.tau_m * dBy_dx).max() < 1e-5 * np.abs(s.Q[8 + 1]).max()
+
+
 @pytest.mark.parametrize("powell", [False, True])
 def test_oracle_matches_numpy_restatement(powell):
     shape = (10, 12)
