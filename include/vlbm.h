@@ -111,13 +111,13 @@ typedef void (*vlbm_free_fn)(void *ptr, size_t bytes, void *stream, void *user);
 
 typedef struct {
     int model;            /* vlbm_model */
-    int dim;              /* 2 (D2Q5 lattices) or 3 (D3Q7); resistive: 3 */
+    int dim;              /* 2 (D2Q5 lattices) or 3 (D3Q7); resistive: 3; dissipative: 2 */
     int nx, ny, nz;       /* cells per axis, nz = 1 when dim = 2 */
     int storage;          /* vlbm_storage */
     double gamma;         /* ideal: adiabatic index of the EOS (Eq. 9) */
     double tau[8];        /* BGK relaxation time per lattice (Eq. 2), > 1/2.
-                             ideal: one per conserved field; resistive:
-                             tau[0] flow lattice, tau[1..3] magnetic lattices */
+                             ideal, Powell, dissipative: one per MHD field;
+                             resistive: tau[0] flow lattice, tau[1..3] magnetic */
     double source[8];     /* ideal: uniform direct-injection source S_k
                              (f* += w_i S_k); zero for the Eq. 12 system */
     double force[3];      /* resistive: body force per cell (Guo scheme) */
