@@ -1,0 +1,92 @@
+"""The seeded input generators (paper_2606_00641_gb300/fields.py) against the
+recipe the design notes state: they hold none of the method's arithmetic, but
+every parity test and benchmark leg starts from them, so their promises are
+checked here -- reproducibility, the amplitude normalisations, the lattice
+scaling from the CFL reading, a discretely solenoidal field, and the same
+fields from the NumPy and the torch builds."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2606_00641_gb300 import fields
+
+
+def primitives(Q, gamma):
+    rho = Q[0]
+    u = Q[1:4] / rho
+    B = Q[5:8]
+    p = (gamma - 1) * (Q[4] - 0.5 * rho * (u * u).sum(0) - 0.5 * (B * B).sum(0))
+    return rho, u, p, B
+
+
+@pytest.mark.parametrize("shape", [(24, 40), (6, 10, 12)])
+def test_recipe_normalisations_and_lattice_scaling(shape):
+    mach, beta, cfl, gamma, p0 = 1.3, 2.0, 0.15, 5.0 / 3.0, 0.6
+    f0 = fields.ideal_fields(shape, 11, gamma=gamma, mach=mach, beta=beta, cfl=cfl, p0=p0)
+    rho, u, p, B = primitives(f0.Q, gamma)
+    lam = f0.lam
+    # density: rho0 (1 + 0.1 s / max|s|)
+    assert abs(np.abs(rho - 1.0).max() - 0.1) < 1e-12
+    # uniform gas pressure p0 / lam^2
+    assert np.abs(p / (p0 / lam ** 2) - 1).max() < 1e-9
+    # peak speed = mach * c_s0 with c_s0 = sqrt(gamma p0 / mean rho) (the ratio is scale free)
+    cs0 = math.sqrt(gamma * p.mean() / rho.mean())
+    assert abs(np.sqrt((u * u).sum(0)).max() / cs0 / mach - 1) < 1e-9
+    # max|B|^2 = 2 p0 / beta
+    assert abs((B * B).sum(0).max() / (2 * p.mean() / beta) - 1) < 1e-9
+    # lattice scaling: max|u| + max c_f = CFL in lattice units
+    cf = np.sqrt((gamma * p + (B * B).sum(0)) / rho)
+    assert abs(np.sqrt((u * u).sum(0)).max() + cf.max() - cfl) < 1e-12
+
+
+@pytest.mark.parametrize("shape", [(16, 12), (6, 8, 10), (5, 7, 9)])
+def test_field_is_discretely_solenoidal(shape):
+    f0 = fields.ideal_fields(shape, 12, beta=0.5)
+    Q = f0.Q
+    div = fields.centred_divergence(Q[5], Q[6], Q[7] if len(shape) == 3 else None)
+    assert np.abs(div).max() < 1e-13 * np.abs(Q[5:8]).max()
+
+
+def test_reproducible_and_seed_dependent():
+    a = fields.ideal_fields((12, 16), 5)
+    b = fields.ideal_fields((12, 16), 5)
+    c = fields.ideal_fields((12, 16), 6)
+    np.testing.assert_array_equal(a.Q, b.Q)
+    assert np.abs(a.Q - c.Q).max() > 1e-3 * np.abs(a.Q).max()
+
+
+@pytest.mark.parametrize("shape", [(16, 20), (6, 8, 10)])
+def test_torch_build_equals_numpy_build(shape):
+    torch = pytest.importorskip("torch")
+    a = fields.ideal_fields(shape, 13, mach=2.0, beta=1.0, cfl=0.2, k_rho=4, k_u=4, k_b=4)
+    b = fields.ideal_fields(shape, 13, mach=2.0, beta=1.0, cfl=0.2, k_rho=4, k_u=4, k_b=4,
+                            device=torch.device("cpu"))
+    got = b.Q.numpy() if hasattr(b.Q, "numpy") else np.asarray(b.Q)
+    assert np.abs(got - a.Q).max() < 1e-12 * np.abs(a.Q).max()
+    assert abs(b.lam / a.lam - 1) < 1e-12
+
+
+def test_hartmann_setup_closed_form_parameters():
+    shape = (4, 34, 8)
+    for Ha in (0.0, 10.0, 30.0):
+        s = fields.hartmann_setup(shape, 2, Ha=Ha, U_c=0.05, Re=100.0, Pm=1.0)
+        a = (34 - 2) / 2.0
+        nu = 0.05 * a / 100.0
+        assert abs(s.nu - nu) < 1e-15 and s.eta == s.nu
+        assert abs(s.tau_f - (0.5 + 3 * nu)) < 1e-15 and abs(s.tau_m - (0.5 + 4 * nu)) < 1e-15
+        assert abs(s.B0 * a / math.sqrt(s.nu * s.eta) - Ha) < 1e-12
+        # the centreline speed of the closed-form profile is U_c
+        u, _ = fields.hartmann_profile(np.array([0.0]), a, s.force[0], 1.0, s.nu, s.eta, s.B0)
+        assert abs(u[0] / 0.05 - 1) < 1e-12
+        # walls at rest, noise of 1 % of U_c elsewhere
+        assert np.abs(s.Q[1:4, :, 0, :]).max() == 0 and np.abs(s.Q[1:4, :, -1, :]).max() == 0
+        assert np.abs(s.Q[1:4]).max() <= 0.01 * 0.05
+
+
+def test_batch_specs_draws():
+    specs = fields.batch_specs(64, 4004)
+    assert specs == fields.batch_specs(64, 4004)
+    assert len(specs) == 64 and len({d["seed"] for d in specs}) == 64
+    assert {d["side"] for d in specs} <= set(fields.BATCH_SIDES)
+    assert all(1.4 <= d["gamma"] <= 5 / 3 and 0.5 <= d["mach"] <= 3.0 for d in specs)
