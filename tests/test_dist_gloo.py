@@ -63,7 +63,7 @@ def test_reference_arm_under_torchrun_prints_one_line():
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
            "--master-addr", "127.0.0.1", "--master-port", str(_free_port()), "bench.py", "--impl", "reference",
-           "--gpus", "2", "--cpu-seconds", "0.3"]
+           "--gpus", "2", "--steps", "2", "--warmup", "1"]
     res = subprocess.run(cmd, cwd=root, capture_output=True, text=True, timeout=300)
     assert res.returncode == 0, res.stderr[-2000:]
     lines = [ln for ln in res.stdout.splitlines() if ln.startswith("{")]
@@ -71,3 +71,64 @@ def test_reference_arm_under_torchrun_prints_one_line():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["cpu_baseline"]["kind"] == "oracle"
     assert d["e2e"]["h2d_bytes_per_step"] == 0
+
+
+# ---------------------------------------------------------------------------
+# Slab decomposition of one domain (the multi-GPU design): each rank advances a
+# z-slab with the oracle's step, wrapping periodically inside the slab, and the
+# one exchange per step swaps what wrapped: the +z populations that left the top
+# layer (they landed in the local bottom layer) go to the upper neighbour, the
+# -z ones that left the bottom layer go to the lower neighbour -- one population
+# per lattice per face cell each way.  The result must equal the single-domain
+# oracle bit for bit.
+# ---------------------------------------------------------------------------
+
+def _slab_main(rank, world, port, out, nz, steps):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import oracle
+    from paper_2606_00641_gb300 import fields
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
+                      LOCAL_RANK=str(rank))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    shape = (nz, 6, 10)
+    f0 = fields.ideal_fields(shape, 91, mach=1.0, cfl=0.2)
+    tau = [0.6, 0.55, 0.55, 0.55, 0.7, 0.6, 0.6, 0.6]
+    full = oracle.ideal_init(f0.Q, f0.gamma)
+    zl = nz // world
+    z0 = rank * zl
+    f = np.ascontiguousarray(full[:, :, z0:z0 + zl])
+    up, down = (rank + 1) % world, (rank - 1) % world
+    sent = 0
+    for _ in range(steps):
+        f = oracle.ideal_step(f, f0.gamma, tau)
+        send_up = torch.from_numpy(np.ascontiguousarray(f[:, 5, 0]))        # +z out of my top layer
+        send_down = torch.from_numpy(np.ascontiguousarray(f[:, 6, zl - 1]))  # -z out of my bottom layer
+        recv_low, recv_high = torch.empty_like(send_up), torch.empty_like(send_down)
+        reqs = [dist.isend(send_up, up, tag=5), dist.isend(send_down, down, tag=6),
+                dist.irecv(recv_low, down, tag=5), dist.irecv(recv_high, up, tag=6)]
+        for r in reqs:
+            r.wait()
+        f[:, 5, 0] = recv_low.numpy()
+        f[:, 6, zl - 1] = recv_high.numpy()
+        sent += send_up.numel() + send_down.numel()
+    ref = full
+    for _ in range(steps):
+        ref = oracle.ideal_step(ref, f0.gamma, tau)
+    out[rank] = (bool(np.array_equal(f, ref[:, :, z0:z0 + zl])), sent)
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world,nz", [(2, 8), (3, 12)])
+def test_slab_halo_exchange_reproduces_the_single_domain_bit_for_bit(world, nz):
+    mgr = mp.get_context("spawn").Manager()
+    out = mgr.dict()
+    steps = 6
+    mp.start_processes(_slab_main, args=(world, _free_port(), out, nz, steps), nprocs=world, join=True,
+                       start_method="spawn")
+    for r in range(world):
+        same, sent = out[r]
+        assert same, r
+        assert sent == steps * 2 * 8 * 6 * 10  # one population per lattice per face cell, each way
