@@ -168,6 +168,7 @@ def load(build: bool = True):
         "vlbm_closure_destroy": (None, [P]),
         "vlbm_restrict": (i, [P, i, i, i, i, P, P]),
         "vlbm_check_bounded_wait": (i, [P, i]),
+        "vlbm_conservation_noalloc": (i, [P, i, i, i, i, i, ctypes.c_int64, i, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -450,6 +451,24 @@ def vlbm_stream(ctx: int) -> int:
 def vlbm_destroy(ctx: int):
     if ctx:
         load().vlbm_destroy(ctx)
+
+
+def vlbm_conservation_noalloc(pop_ptr: int, storage, dim: int, nx: int, ny: int, nz: int, stride: int,
+                              parity: int, sums_ptr: int, q_ref=None, q_scale=None, stream: int = 0) -> None:
+    """Domain sums of the eight ideal-MHD fields from a caller-owned population buffer into 8
+    caller-owned device doubles, allocating nothing (see vlbm.h); enqueued on `stream`."""
+    st_code = STORAGE_NAMES[storage] if isinstance(storage, str) else int(storage)
+    ref = scale = None
+    if q_ref is not None:
+        ref = np.ascontiguousarray(np.asarray(q_ref, dtype=np.float64).reshape(8))
+    if q_scale is not None:
+        scale = np.ascontiguousarray(np.asarray(q_scale, dtype=np.float64).reshape(8))
+    _device_inputs_ready()
+    _check(load().vlbm_conservation_noalloc(
+        ctypes.c_void_p(pop_ptr), st_code, int(dim), int(nx), int(ny), int(nz), int(stride), int(parity),
+        ref.ctypes.data_as(ctypes.c_void_p) if ref is not None else None,
+        scale.ctypes.data_as(ctypes.c_void_p) if scale is not None else None,
+        ctypes.c_void_p(sums_ptr), ctypes.c_void_p(stream) if stream else None), "vlbm_conservation_noalloc")
 
 
 def vlbm_check_bounded_wait(ctx: int, tries: int = 64) -> None:

@@ -44,6 +44,13 @@ def test_library_exports_every_declared_symbol(V):
     assert set(declared_functions()) <= exported
 
 
+def test_binding_declares_a_signature_for_every_entry_point(V):
+    # the thin binding marshals every call of the header (argument types set)
+    lib = V.load()
+    missing = [n for n in declared_functions() if getattr(lib, n).argtypes is None]
+    assert not missing, missing
+
+
 def test_params_struct_layout_matches_c(V):
     p = V.vlbm_default_params()
     assert (p.model, p.dim, p.nx, p.ny, p.nz, p.storage) == (0, 3, 64, 64, 64, V.VLBM_F32)
