@@ -8,7 +8,6 @@ one lattice Boltzmann step of the C oracle (zero change of every domain sum,
 moment change equal to minus the centred divergence of dPhi).
 """
 import numpy as np
-import pytest
 from scipy import ndimage
 
 from oracle import closure_ref as C
