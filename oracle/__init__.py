@@ -90,6 +90,14 @@ def _configure(L):
     L.orc_diss_step.argtypes = [i, i, d, p, d, d, d, d, i, p, p, i]
     L.orc_diss_moments.argtypes = [i, i, p, p]
     L.orc_diss_run.argtypes = [i, i, d, p, d, d, d, d, i, p, i, p, i]
+    L.orc_diss_flux_d.argtypes = [i, d, d, d, d, d, p, p]
+    L.orc_diss_flux_d.restype = None
+    L.orc_diss_source_d.argtypes = [i, d, i, p, p]
+    L.orc_diss_source_d.restype = None
+    L.orc_diss_init_d.argtypes = [i, i, i, i, d, d, d, d, d, p, p]
+    L.orc_diss_step_d.argtypes = [i, i, i, i, d, p, d, d, d, d, i, p, p, i]
+    L.orc_diss_moments_d.argtypes = [i, i, i, i, p, p]
+    L.orc_diss_run_d.argtypes = [i, i, i, i, d, p, d, d, d, d, i, p, i, p, i]
     L.orc_open_step.argtypes = [i, i, i, i, d, p, p, p, p, p, p, p, p, i]
     L.orc_open_run.argtypes = [i, i, i, i, d, p, p, p, p, p, p, p, i, p, i]
     return L
@@ -466,10 +474,16 @@ def open_run(Q0: np.ndarray, gamma: float, tau, faces, nsteps: int, src=None, so
     return out
 
 
-# ---- dissipative MHD with locally evolved gradients (sec. 2.2.1, 2.3), 2-D D2Q5 ----
-# Q[20]: rho, rho u (3), e, B (3), G_ab = Q[8 + 3a + b] ~ tau_M d_a B_b, W_ab = Q[14 + 3a + b] ~ tau_M d_a u_b
+# ---- dissipative MHD with locally evolved gradients (sec. 2.2.1, 2.3), D2Q5 and D3Q7 ----
+# Q[8 + 6 dim]: rho, rho u (3), e, B (3), G_ab = Q[8 + 3a + b] ~ tau_M d_a B_b,
+# W_ab = Q[8 + 3 dim + 3a + b] ~ tau_M d_a u_b, with a over the dim lattice axes and b over x, y, z.
 
-NVAR_DISS = 20
+NVAR_DISS = 20      # 2-D
+NVAR_DISS_3D = 26
+
+
+def diss_nvar(dim: int) -> int:
+    return 8 + 6 * dim
 
 
 class Dissipation:
@@ -481,62 +495,86 @@ class Dissipation:
         self.nu, self.eta0, self.j_c, self.tau_m, self.powell = float(nu), float(eta0), float(j_c), float(tau_m), bool(powell)
 
 
-def _tau20(tau, tau_g=None):
+def _tau_diss(tau, tau_g=None, dim: int = 2):
+    nvar = diss_nvar(dim)
     t = np.asarray(tau, dtype=np.float64).reshape(-1)
-    if t.size == 20:
+    if t.size == nvar:
         return _f64(t)
     t8 = np.broadcast_to(t, (8,)) if t.size in (1, 8) else None
     if t8 is None:
-        raise ValueError("tau: 1, 8 or 20 values")
+        raise ValueError(f"tau: 1, 8 or {nvar} values")
     g = float(t8[0]) if tau_g is None else float(tau_g)
-    return _f64(np.concatenate([t8, np.full(12, g)]))
+    return _f64(np.concatenate([t8, np.full(nvar - 8, g)]))
 
 
-def diss_flux(gamma: float, dp: Dissipation, Q) -> np.ndarray:
-    """Flux tensor phi[20, 3] of one state."""
-    out = np.zeros(60)
-    lib().orc_diss_flux(gamma, dp.nu, dp.eta0, dp.j_c, dp.tau_m, _ptr(_f64(Q)), _ptr(out))
-    return out.reshape(20, 3)
+def _tau20(tau, tau_g=None):
+    return _tau_diss(tau, tau_g, 2)
 
 
-def diss_source(dp: Dissipation, Q) -> np.ndarray:
-    out = np.zeros(20)
-    lib().orc_diss_source(dp.tau_m, int(dp.powell), _ptr(_f64(Q)), _ptr(out))
+def _diss_grid(a: np.ndarray, lead: int):
+    """(dim, nx, ny, nz) of an array [lead..., ny, nx] (2-D) or [lead..., nz, ny, nx] (3-D)."""
+    spatial = a.shape[lead:]
+    if len(spatial) == 2:
+        return 2, spatial[1], spatial[0], 1
+    if len(spatial) == 3:
+        return 3, spatial[2], spatial[1], spatial[0]
+    raise ValueError("dissipative fields: [nvar, ny, nx] or [nvar, nz, ny, nx]")
+
+
+def diss_flux(gamma: float, dp: Dissipation, Q, dim: int = 2) -> np.ndarray:
+    """Flux tensor phi[nvar, 3] of one state (nvar = 20 in 2-D, 26 in 3-D)."""
+    nvar = diss_nvar(dim)
+    Q = _f64(Q)
+    if Q.size != nvar:
+        raise ValueError(f"{dim}-D state: {nvar} values")
+    out = np.zeros(3 * nvar)
+    lib().orc_diss_flux_d(dim, gamma, dp.nu, dp.eta0, dp.j_c, dp.tau_m, _ptr(Q), _ptr(out))
+    return out.reshape(nvar, 3)
+
+
+def diss_source(dp: Dissipation, Q, dim: int = 2) -> np.ndarray:
+    nvar = diss_nvar(dim)
+    Q = _f64(Q)
+    if Q.size != nvar:
+        raise ValueError(f"{dim}-D state: {nvar} values")
+    out = np.zeros(nvar)
+    lib().orc_diss_source_d(dim, dp.tau_m, int(dp.powell), _ptr(Q), _ptr(out))
     return out
 
 
 def diss_init(Q0: np.ndarray, gamma: float, dp: Dissipation) -> np.ndarray:
-    """Populations f[20, 5, ny, nx] = f_eq(Q0)."""
+    """Populations f[nvar, q, (nz,) ny, nx] = f_eq(Q0); Q0 [20, ny, nx] (D2Q5) or [26, nz, ny, nx] (D3Q7)."""
     Q0 = _f64(Q0)
-    ny, nx = Q0.shape[1:]
-    f = np.zeros((20, 5, ny, nx))
-    _check(lib().orc_diss_init(nx, ny, gamma, dp.nu, dp.eta0, dp.j_c, dp.tau_m, _ptr(Q0), _ptr(f)), "diss_init")
+    dim, nx, ny, nz = _diss_grid(Q0, 1)
+    f = np.zeros((diss_nvar(dim), 2 * dim + 1) + Q0.shape[1:])
+    _check(lib().orc_diss_init_d(dim, nx, ny, nz, gamma, dp.nu, dp.eta0, dp.j_c, dp.tau_m, _ptr(Q0), _ptr(f)),
+           "diss_init")
     return f
 
 
 def diss_step(f: np.ndarray, gamma: float, tau, dp: Dissipation, tau_g=None, nthreads: int = 1) -> np.ndarray:
     f = _f64(f)
-    ny, nx = f.shape[2:]
+    dim, nx, ny, nz = _diss_grid(f, 2)
     out = np.empty_like(f)
-    _check(lib().orc_diss_step(nx, ny, gamma, _ptr(_tau20(tau, tau_g)), dp.nu, dp.eta0, dp.j_c, dp.tau_m,
-                               int(dp.powell), _ptr(f), _ptr(out), nthreads), "diss_step")
+    _check(lib().orc_diss_step_d(dim, nx, ny, nz, gamma, _ptr(_tau_diss(tau, tau_g, dim)), dp.nu, dp.eta0, dp.j_c,
+                                 dp.tau_m, int(dp.powell), _ptr(f), _ptr(out), nthreads), "diss_step")
     return out
 
 
 def diss_moments(f: np.ndarray) -> np.ndarray:
     f = _f64(f)
-    ny, nx = f.shape[2:]
-    Q = np.zeros((20, ny, nx))
-    _check(lib().orc_diss_moments(nx, ny, _ptr(f), _ptr(Q)), "diss_moments")
+    dim, nx, ny, nz = _diss_grid(f, 2)
+    Q = np.zeros((diss_nvar(dim),) + f.shape[2:])
+    _check(lib().orc_diss_moments_d(dim, nx, ny, nz, _ptr(f), _ptr(Q)), "diss_moments")
     return Q
 
 
 def diss_run(Q0: np.ndarray, gamma: float, tau, dp: Dissipation, nsteps: int, tau_g=None,
              nthreads: int = 1) -> np.ndarray:
-    """Moments [20, ny, nx] after nsteps steps started from f_eq(Q0)."""
+    """Moments [nvar, (nz,) ny, nx] after nsteps steps started from f_eq(Q0)."""
     Q0 = _f64(Q0)
-    ny, nx = Q0.shape[1:]
+    dim, nx, ny, nz = _diss_grid(Q0, 1)
     out = np.zeros_like(Q0)
-    _check(lib().orc_diss_run(nx, ny, gamma, _ptr(_tau20(tau, tau_g)), dp.nu, dp.eta0, dp.j_c, dp.tau_m,
-                              int(dp.powell), _ptr(Q0), nsteps, _ptr(out), nthreads), "diss_run")
+    _check(lib().orc_diss_run_d(dim, nx, ny, nz, gamma, _ptr(_tau_diss(tau, tau_g, dim)), dp.nu, dp.eta0, dp.j_c,
+                                dp.tau_m, int(dp.powell), _ptr(Q0), nsteps, _ptr(out), nthreads), "diss_run")
     return out

@@ -363,20 +363,23 @@ def resistive_moments(f, g, force, b_wall, walls_y):
 
 
 # ----------------------------------------------------------------------------
-# dissipative MHD with locally evolved gradients (sec. 2.2.1, 2.3), D2Q5:
-# Q[8 + 3a + b] = G_ab ~ tau_M d_a B_b, Q[14 + 3a + b] = W_ab ~ tau_M d_a u_b
+# dissipative MHD with locally evolved gradients (sec. 2.2.1, 2.3), D2Q5 / D3Q7:
+# Q[8 + 3a + b] = G_ab ~ tau_M d_a B_b, Q[8 + 3 dim + 3a + b] = W_ab ~ tau_M d_a u_b,
+# a over the dim lattice axes; dim = Q.ndim - 1
 # ----------------------------------------------------------------------------
 
 def diss_flux(Q: np.ndarray, gamma: float, nu: float, eta0: float, j_c: float, tau_m: float) -> np.ndarray:
-    """phi[20, 3, ...] of the full system: ideal flux plus viscous stress, eta(j) j x B
+    """phi[8 + 6 dim, 3, ...] of the full system: ideal flux plus viscous stress, eta(j) j x B
     and -eta grad B, and the gradient lattices' G u - I B, W u - I u."""
+    dim = Q.ndim - 1
+    nvar, w0 = 8 + 6 * dim, 8 + 3 * dim
     rho, u, e, B, p = primitives(Q[:8], gamma)
     shape = Q.shape[1:]
     pt = p + 0.5 * (B * B).sum(0)
     grad_B = np.zeros((3, 3) + shape)
     grad_u = np.zeros((3, 3) + shape)
-    grad_B[:2] = Q[8:14].reshape((2, 3) + shape) / tau_m
-    grad_u[:2] = Q[14:20].reshape((2, 3) + shape) / tau_m
+    grad_B[:dim] = Q[8:w0].reshape((dim, 3) + shape) / tau_m
+    grad_u[:dim] = Q[w0:nvar].reshape((dim, 3) + shape) / tau_m
     visc = rho * nu * (grad_u + np.swapaxes(grad_u, 0, 1))
     eps = np.zeros((3, 3, 3))
     eps[0, 1, 2] = eps[1, 2, 0] = eps[2, 0, 1] = 1.0
@@ -385,27 +388,28 @@ def diss_flux(Q: np.ndarray, gamma: float, nu: float, eta0: float, j_c: float, t
     eta = eta0 * (1.0 + ((j * j).sum(0) / j_c ** 2 if j_c > 0 else 0.0))
     jxB = np.cross(j, B, axis=0)
     eye = np.eye(3).reshape((3, 3) + (1,) * len(shape))
-    phi = np.zeros((20, 3) + shape)
+    phi = np.zeros((nvar, 3) + shape)
     phi[0] = rho * u
     phi[1:4] = np.einsum("c...,b...->bc...", rho * u, u) + pt * eye - np.einsum("c...,b...->bc...", B, B) \
         - np.swapaxes(visc, 0, 1)
     phi[4] = (e + pt) * u - B * (u * B).sum(0) - np.einsum("b...,bc...->c...", u, visc) + eta * jxB
     phi[5:8] = np.einsum("c...,b...->bc...", u, B) - np.einsum("c...,b...->bc...", B, u) \
         - eta * np.swapaxes(grad_B, 0, 1)
-    for a in range(2):
+    for a in range(dim):
         for b in range(3):
             phi[8 + 3 * a + b] = Q[8 + 3 * a + b] * u - eye[a] * B[b]
-            phi[14 + 3 * a + b] = Q[14 + 3 * a + b] * u - eye[a] * u[b]
+            phi[w0 + 3 * a + b] = Q[w0 + 3 * a + b] * u - eye[a] * u[b]
     return phi
 
 
 def diss_source(Q: np.ndarray, tau_m: float, powell: bool) -> np.ndarray:
+    dim = Q.ndim - 1
     S = np.zeros_like(Q)
     S[8:] = -Q[8:] / tau_m
     if powell:
         rho = Q[0]
         u = Q[1:4] / rho
-        divB = (Q[8] + Q[12]) / tau_m
+        divB = sum(Q[8 + 4 * a] for a in range(dim)) / tau_m   # trace of G over the lattice axes
         S[1:4] = -divB * Q[5:8]
         S[4] = -divB * (u * Q[5:8]).sum(0)
         S[5:8] = -divB * u
@@ -413,24 +417,26 @@ def diss_source(Q: np.ndarray, tau_m: float, powell: bool) -> np.ndarray:
 
 
 def diss_feq(Q: np.ndarray, gamma: float, nu, eta0, j_c, tau_m) -> np.ndarray:
-    c, w, cs2 = vset("D2Q5")
+    dim = Q.ndim - 1
+    c, w, cs2 = vset("D2Q5" if dim == 2 else "D3Q7")
     phi = diss_flux(Q, gamma, nu, eta0, j_c, tau_m)
-    feq = np.zeros((20, 5) + Q.shape[1:])
-    for i in range(5):
-        feq[:, i] = w[i] * (Q + (c[i, 0] * phi[:, 0] + c[i, 1] * phi[:, 1]) / cs2)
+    feq = np.zeros((Q.shape[0], len(w)) + Q.shape[1:])
+    for i in range(len(w)):
+        feq[:, i] = w[i] * (Q + sum(c[i, a] * phi[:, a] for a in range(dim)) / cs2)
     return feq
 
 
 def diss_step(f: np.ndarray, gamma: float, tau20, nu, eta0, j_c, tau_m, powell) -> np.ndarray:
-    c, w, _ = vset("D2Q5")
+    dim = f.ndim - 2
+    c, w, _ = vset("D2Q5" if dim == 2 else "D3Q7")
     Q = f.sum(axis=1)
     feq = diss_feq(Q, gamma, nu, eta0, j_c, tau_m)
     S = diss_source(Q, tau_m, powell)
-    t = np.asarray(tau20, dtype=float).reshape((20, 1, 1, 1))
-    post = f + (feq - f) / t + w.reshape((1, 5, 1, 1)) * S[:, None]
+    t = np.asarray(tau20, dtype=float).reshape((-1, 1) + (1,) * dim)
+    post = f + (feq - f) / t + w.reshape((1, -1) + (1,) * dim) * S[:, None]
     out = np.empty_like(f)
-    for i in range(5):
-        out[:, i] = _shift(post[:, i], c[i], 2)
+    for i in range(len(w)):
+        out[:, i] = _shift(post[:, i], c[i], dim)
     return out
 
 

@@ -19,7 +19,7 @@
  *                                                      (sec. 2.4, "Homogenization")
  *   equilibrium Dirichlet / Neumann open boundaries    (sec. 2.4, "Static boundaries")
  *   dissipative MHD: viscous stress, eta(j) resistivity, gradients evolved
- *   as lattices                                        (sec. 2.2.1, 2.3; 2-D)
+ *   as lattices                                        (sec. 2.2.1, 2.3; 2-D and 3-D)
  *   local gradient evolution  dG/dt + div Phi_G = -G/tau_R          (sec. 2.2.1)
  *
  * Readings where the paper is silent (each one is listed in the design notes):
@@ -658,32 +658,38 @@ int orc_hlbm_run(int dim, int nx, int ny, int nz, double gamma, const double *ta
  * local moments evolution: G_ab ~ tau_M d_a B_b with flux G_ab u_c - delta_ac B_b
  * and source -G_ab / tau_M, and the same construction for the velocity,
  * W_ab ~ tau_M d_a u_b with flux W_ab u_c - delta_ac u_b, from which the
- * viscous stress is built.  On the D2Q5 lattice a runs over x and y and b over
- * x, y, z: Q[8 + 3a + b] = G_ab, Q[14 + 3a + b] = W_ab, 20 lattices.
+ * viscous stress is built.  a runs over the lattice axes (x, y on D2Q5; x, y, z
+ * on D3Q7) and b over x, y, z: Q[8 + 3a + b] = G_ab, Q[8 + 3 dim + 3a + b] = W_ab,
+ * 8 + 6 dim lattices (20 in 2-D, 26 in 3-D).
  *
  * Fluxes (the full system of sec. 2.3), with d_a B_b = G_ab / tau_M,
- * d_a u_b = W_ab / tau_M and d_z = 0:
+ * d_a u_b = W_ab / tau_M and d_z = 0 in 2-D:
  *   momentum  rho u u + p_tot I - B B - tau_v,   tau_v = rho nu (grad u + grad u^T)
  *   energy    (e + p_tot) u - B (u.B) - u.tau_v + eta j x B   (heat flux zero)
  *   induction u B - B u - eta grad B
  * with j = curl B and eta = eta0 (1 + |j|^2 / j_c^2) (j_c <= 0: eta = eta0).
- * Optional Powell source with div B = (G_xx + G_yy) / tau_M.
+ * Optional Powell source with div B = (sum_a G_aa) / tau_M.
  */
-#define ORC_NVAR_DISS 20
+#define ORC_NVAR_DISS 20   /* 2-D */
+#define ORC_NVAR_DISS_MAX 26 /* 3-D */
 
-static void diss_gradients(const double *Q, double tau_m, double dB[3][3], double du[3][3])
+static int diss_nvar(int dim) { return 8 + 6 * dim; }
+
+static void diss_gradients(int dim, const double *Q, double tau_m, double dB[3][3], double du[3][3])
 {
+    const int w0 = 8 + 3 * dim;
     for (int a = 0; a < 3; ++a)
         for (int b = 0; b < 3; ++b) {
-            dB[a][b] = a < 2 ? Q[8 + 3 * a + b] / tau_m : 0.0;
-            du[a][b] = a < 2 ? Q[14 + 3 * a + b] / tau_m : 0.0;
+            dB[a][b] = a < dim ? Q[8 + 3 * a + b] / tau_m : 0.0;
+            du[a][b] = a < dim ? Q[w0 + 3 * a + b] / tau_m : 0.0;
         }
 }
 
 /* phi[3*k + c]: flux of Q_k along axis c (c = 2 unused in 2-D). */
-void orc_diss_flux(double gamma, double nu, double eta0, double j_c, double tau_m, const double *Q,
-                   double *phi)
+void orc_diss_flux_d(int dim, double gamma, double nu, double eta0, double j_c, double tau_m, const double *Q,
+                     double *phi)
 {
+    const int w0 = 8 + 3 * dim;
     double rho = Q[0];
     double u[3] = {Q[1] / rho, Q[2] / rho, Q[3] / rho};
     double e = Q[4];
@@ -694,7 +700,7 @@ void orc_diss_flux(double gamma, double nu, double eta0, double j_c, double tau_
     double p = (gamma - 1.0) * (e - 0.5 * rho * uu - 0.5 * B2); /* Eq. 9 */
     double ptot = 0.5 * B2 + p; /* gas plus magnetic pressure */
     double dB[3][3], du[3][3];
-    diss_gradients(Q, tau_m, dB, du);
+    diss_gradients(dim, Q, tau_m, dB, du);
     double visc[3][3];
     for (int a = 0; a < 3; ++a)
         for (int b = 0; b < 3; ++b) visc[a][b] = rho * nu * (du[a][b] + du[b][a]);
@@ -711,24 +717,32 @@ void orc_diss_flux(double gamma, double nu, double eta0, double j_c, double tau_
             u_visc += u[b] * visc[b][c];
         }
         phi[3 * 4 + c] = (e + ptot) * u[c] - B[c] * uB - u_visc + eta * jxB[c];
-        for (int a = 0; a < 2; ++a)
+        for (int a = 0; a < dim; ++a)
             for (int b = 0; b < 3; ++b) {
                 phi[3 * (8 + 3 * a + b) + c] = Q[8 + 3 * a + b] * u[c] - (a == c ? B[b] : 0.0);
-                phi[3 * (14 + 3 * a + b) + c] = Q[14 + 3 * a + b] * u[c] - (a == c ? u[b] : 0.0);
+                phi[3 * (w0 + 3 * a + b) + c] = Q[w0 + 3 * a + b] * u[c] - (a == c ? u[b] : 0.0);
             }
     }
 }
 
+void orc_diss_flux(double gamma, double nu, double eta0, double j_c, double tau_m, const double *Q, double *phi)
+{
+    orc_diss_flux_d(2, gamma, nu, eta0, j_c, tau_m, Q, phi);
+}
+
 /* Sources: relaxation -G/tau_M and -W/tau_M; with powell != 0 also
  * S = -(div B)(0, B, u.B, u) on the eight MHD lattices (sec. 2.3). */
-void orc_diss_source(double tau_m, int powell, const double *Q, double *S)
+void orc_diss_source_d(int dim, double tau_m, int powell, const double *Q, double *S)
 {
-    for (int k = 0; k < ORC_NVAR_DISS; ++k) S[k] = 0.0;
-    for (int k = 8; k < ORC_NVAR_DISS; ++k) S[k] = -Q[k] / tau_m;
+    const int nvar = diss_nvar(dim);
+    for (int k = 0; k < nvar; ++k) S[k] = 0.0;
+    for (int k = 8; k < nvar; ++k) S[k] = -Q[k] / tau_m;
     if (powell) {
         double rho = Q[0];
         double u[3] = {Q[1] / rho, Q[2] / rho, Q[3] / rho};
-        double minus_div = -(Q[8 + 0] + Q[8 + 3 + 1]) / tau_m; /* -(G_xx + G_yy) / tau_M */
+        double trace = 0.0;
+        for (int a = 0; a < dim; ++a) trace += Q[8 + 4 * a]; /* G_aa */
+        double minus_div = -trace / tau_m;
         double u_dot_B = u[0] * Q[5] + u[1] * Q[6] + u[2] * Q[7];
         for (int b = 0; b < 3; ++b) {
             S[1 + b] = minus_div * Q[5 + b];
@@ -738,12 +752,17 @@ void orc_diss_source(double tau_m, int powell, const double *Q, double *S)
     }
 }
 
-static void diss_feq(const orc_lattice *L, double gamma, double nu, double eta0, double j_c, double tau_m,
-                     const double *Q, double feq[ORC_NVAR_DISS][ORC_QMAX])
+void orc_diss_source(double tau_m, int powell, const double *Q, double *S)
 {
-    double phi[3 * ORC_NVAR_DISS];
-    orc_diss_flux(gamma, nu, eta0, j_c, tau_m, Q, phi);
-    for (int k = 0; k < ORC_NVAR_DISS; ++k)
+    orc_diss_source_d(2, tau_m, powell, Q, S);
+}
+
+static void diss_feq(int dim, const orc_lattice *L, double gamma, double nu, double eta0, double j_c, double tau_m,
+                     const double *Q, double feq[ORC_NVAR_DISS_MAX][ORC_QMAX])
+{
+    double phi[3 * ORC_NVAR_DISS_MAX];
+    orc_diss_flux_d(dim, gamma, nu, eta0, j_c, tau_m, Q, phi);
+    for (int k = 0; k < diss_nvar(dim); ++k)
         for (int i = 0; i < L->q; ++i) {
             double flux_c = 0.0;
             for (int a = 0; a < 3; ++a) flux_c += L->c[i][a] * phi[3 * k + a];
@@ -751,39 +770,76 @@ static void diss_feq(const orc_lattice *L, double gamma, double nu, double eta0,
         }
 }
 
-/* tau[20]: BGK time per lattice.  Collision with direct source injection. */
-static void diss_collide(const orc_lattice *L, double gamma, const double *tau, double nu, double eta0,
+/* tau[nvar]: BGK time per lattice.  Collision with direct source injection. */
+static void diss_collide(int dim, const orc_lattice *L, double gamma, const double *tau, double nu, double eta0,
                          double j_c, double tau_m, int powell, const double *fin, double *fout)
 {
-    double Q[ORC_NVAR_DISS], S[ORC_NVAR_DISS];
-    double feq[ORC_NVAR_DISS][ORC_QMAX];
-    for (int k = 0; k < ORC_NVAR_DISS; ++k) {
+    const int nvar = diss_nvar(dim);
+    double Q[ORC_NVAR_DISS_MAX], S[ORC_NVAR_DISS_MAX];
+    double feq[ORC_NVAR_DISS_MAX][ORC_QMAX];
+    for (int k = 0; k < nvar; ++k) {
         Q[k] = 0.0;
         for (int i = 0; i < L->q; ++i) Q[k] += fin[k * L->q + i]; /* Eq. 4 */
     }
-    diss_feq(L, gamma, nu, eta0, j_c, tau_m, Q, feq);
-    orc_diss_source(tau_m, powell, Q, S);
-    for (int k = 0; k < ORC_NVAR_DISS; ++k)
+    diss_feq(dim, L, gamma, nu, eta0, j_c, tau_m, Q, feq);
+    orc_diss_source_d(dim, tau_m, powell, Q, S);
+    for (int k = 0; k < nvar; ++k)
         for (int i = 0; i < L->q; ++i) {
             double fk = fin[k * L->q + i];
             fout[k * L->q + i] = fk + (feq[k][i] - fk) / tau[k] + L->w[i] * S[k];
         }
 }
 
+int orc_diss_init_d(int dim, int nx, int ny, int nz, double gamma, double nu, double eta0, double j_c,
+                    double tau_m, const double *Q0, double *f)
+{
+    orc_lattice L;
+    if (check_dims(dim, nx, ny, nz)) return -1;
+    build_lattice(dim == 2 ? 5 : 7, &L);
+    const int nvar = diss_nvar(dim);
+    long N = (long)nx * ny * nz;
+    for (long cell = 0; cell < N; ++cell) {
+        double Q[ORC_NVAR_DISS_MAX];
+        double feq[ORC_NVAR_DISS_MAX][ORC_QMAX];
+        for (int k = 0; k < nvar; ++k) Q[k] = Q0[k * N + cell];
+        diss_feq(dim, &L, gamma, nu, eta0, j_c, tau_m, Q, feq);
+        for (int k = 0; k < nvar; ++k)
+            for (int i = 0; i < L.q; ++i) f[(long)(k * L.q + i) * N + cell] = feq[k][i];
+    }
+    return 0;
+}
+
 int orc_diss_init(int nx, int ny, double gamma, double nu, double eta0, double j_c, double tau_m,
                   const double *Q0, double *f)
 {
+    return orc_diss_init_d(2, nx, ny, 1, gamma, nu, eta0, j_c, tau_m, Q0, f);
+}
+
+int orc_diss_step_d(int dim, int nx, int ny, int nz, double gamma, const double *tau, double nu, double eta0,
+                    double j_c, double tau_m, int powell, const double *fin, double *fout, int nthreads)
+{
     orc_lattice L;
-    if (nx < 1 || ny < 1) return -1;
-    build_lattice(5, &L);
-    long N = (long)nx * ny;
+    if (check_dims(dim, nx, ny, nz)) return -1;
+    build_lattice(dim == 2 ? 5 : 7, &L);
+    const int nvar = diss_nvar(dim);
+    const long N = (long)nx * ny * nz;
+    const int q = L.q;
+    if (nthreads < 1) nthreads = 1;
+#pragma omp parallel for num_threads(nthreads) schedule(static)
     for (long cell = 0; cell < N; ++cell) {
-        double Q[ORC_NVAR_DISS];
-        double feq[ORC_NVAR_DISS][ORC_QMAX];
-        for (int k = 0; k < ORC_NVAR_DISS; ++k) Q[k] = Q0[k * N + cell];
-        diss_feq(&L, gamma, nu, eta0, j_c, tau_m, Q, feq);
-        for (int k = 0; k < ORC_NVAR_DISS; ++k)
-            for (int i = 0; i < L.q; ++i) f[(long)(k * L.q + i) * N + cell] = feq[k][i];
+        int x = (int)(cell % nx);
+        int y = (int)((cell / nx) % ny);
+        int z = (int)(cell / ((long)nx * ny));
+        double fc[ORC_NVAR_DISS_MAX * ORC_QMAX];
+        double fs[ORC_NVAR_DISS_MAX * ORC_QMAX];
+        for (int k = 0; k < nvar; ++k)
+            for (int i = 0; i < q; ++i) fc[k * q + i] = fin[(long)(k * q + i) * N + cell];
+        diss_collide(dim, &L, gamma, tau, nu, eta0, j_c, tau_m, powell, fc, fs);
+        for (int i = 0; i < q; ++i) {
+            long moved = neighbour(x, y, z, L.c[i], nx, ny, nz);
+            for (int k = 0; k < nvar; ++k)
+                fout[(long)(k * q + i) * N + moved] = fs[k * q + i];
+        }
     }
     return 0;
 }
@@ -791,66 +847,59 @@ int orc_diss_init(int nx, int ny, double gamma, double nu, double eta0, double j
 int orc_diss_step(int nx, int ny, double gamma, const double *tau, double nu, double eta0, double j_c,
                   double tau_m, int powell, const double *fin, double *fout, int nthreads)
 {
-    orc_lattice L;
-    if (nx < 1 || ny < 1) return -1;
-    build_lattice(5, &L);
-    const long N = (long)nx * ny;
-    const int q = L.q;
-    if (nthreads < 1) nthreads = 1;
-#pragma omp parallel for num_threads(nthreads) schedule(static)
-    for (long cell = 0; cell < N; ++cell) {
-        int x = (int)(cell % nx);
-        int y = (int)(cell / nx);
-        double fc[ORC_NVAR_DISS * ORC_QMAX];
-        double fs[ORC_NVAR_DISS * ORC_QMAX];
-        for (int k = 0; k < ORC_NVAR_DISS; ++k)
-            for (int i = 0; i < q; ++i) fc[k * q + i] = fin[(long)(k * q + i) * N + cell];
-        diss_collide(&L, gamma, tau, nu, eta0, j_c, tau_m, powell, fc, fs);
-        for (int i = 0; i < q; ++i) {
-            long moved = neighbour(x, y, 0, L.c[i], nx, ny, 1);
-            for (int k = 0; k < ORC_NVAR_DISS; ++k)
-                fout[(long)(k * q + i) * N + moved] = fs[k * q + i];
+    return orc_diss_step_d(2, nx, ny, 1, gamma, tau, nu, eta0, j_c, tau_m, powell, fin, fout, nthreads);
+}
+
+int orc_diss_moments_d(int dim, int nx, int ny, int nz, const double *f, double *Q)
+{
+    if (check_dims(dim, nx, ny, nz)) return -1;
+    const int q = dim == 2 ? 5 : 7;
+    long N = (long)nx * ny * nz;
+    for (int k = 0; k < diss_nvar(dim); ++k)
+        for (long cell = 0; cell < N; ++cell) {
+            double s = 0.0;
+            for (int i = 0; i < q; ++i) s += f[(long)(k * q + i) * N + cell];
+            Q[k * N + cell] = s;
         }
-    }
     return 0;
 }
 
 int orc_diss_moments(int nx, int ny, const double *f, double *Q)
 {
-    if (nx < 1 || ny < 1) return -1;
-    long N = (long)nx * ny;
-    for (int k = 0; k < ORC_NVAR_DISS; ++k)
-        for (long cell = 0; cell < N; ++cell) {
-            double s = 0.0;
-            for (int i = 0; i < 5; ++i) s += f[(long)(k * 5 + i) * N + cell];
-            Q[k * N + cell] = s;
-        }
+    return orc_diss_moments_d(2, nx, ny, 1, f, Q);
+}
+
+int orc_diss_run_d(int dim, int nx, int ny, int nz, double gamma, const double *tau, double nu, double eta0,
+                   double j_c, double tau_m, int powell, const double *Q0, int nsteps, double *Qout, int nthreads)
+{
+    if (check_dims(dim, nx, ny, nz) || nsteps < 0) return -1;
+    const int q = dim == 2 ? 5 : 7;
+    long N = (long)nx * ny * nz;
+    size_t len = (size_t)diss_nvar(dim) * q * N;
+    double *a = (double *)malloc(sizeof(double) * len);
+    double *b = (double *)malloc(sizeof(double) * len);
+    if (!a || !b) {
+        free(a);
+        free(b);
+        return -2;
+    }
+    orc_diss_init_d(dim, nx, ny, nz, gamma, nu, eta0, j_c, tau_m, Q0, a);
+    for (int s = 0; s < nsteps; ++s) {
+        orc_diss_step_d(dim, nx, ny, nz, gamma, tau, nu, eta0, j_c, tau_m, powell, a, b, nthreads);
+        double *t = a;
+        a = b;
+        b = t;
+    }
+    orc_diss_moments_d(dim, nx, ny, nz, a, Qout);
+    free(a);
+    free(b);
     return 0;
 }
 
 int orc_diss_run(int nx, int ny, double gamma, const double *tau, double nu, double eta0, double j_c,
                  double tau_m, int powell, const double *Q0, int nsteps, double *Qout, int nthreads)
 {
-    if (nx < 1 || ny < 1 || nsteps < 0) return -1;
-    long N = (long)nx * ny;
-    double *a = (double *)malloc(sizeof(double) * ORC_NVAR_DISS * 5 * N);
-    double *b = (double *)malloc(sizeof(double) * ORC_NVAR_DISS * 5 * N);
-    if (!a || !b) {
-        free(a);
-        free(b);
-        return -2;
-    }
-    orc_diss_init(nx, ny, gamma, nu, eta0, j_c, tau_m, Q0, a);
-    for (int s = 0; s < nsteps; ++s) {
-        orc_diss_step(nx, ny, gamma, tau, nu, eta0, j_c, tau_m, powell, a, b, nthreads);
-        double *t = a;
-        a = b;
-        b = t;
-    }
-    orc_diss_moments(nx, ny, a, Qout);
-    free(a);
-    free(b);
-    return 0;
+    return orc_diss_run_d(2, nx, ny, 1, gamma, tau, nu, eta0, j_c, tau_m, powell, Q0, nsteps, Qout, nthreads);
 }
 
 /* ------------------------------------------------------------------ */

@@ -11,6 +11,7 @@ import oracle
 import test_oracle_hlbm as H
 import test_oracle_open as O
 import test_oracle_diss as DS
+import test_oracle_diss3d as D3
 import test_oracle_pins as P
 import test_oracle_powell as W
 import test_oracle_resistive as R
@@ -75,6 +76,16 @@ DISS_PINS = [
     lambda o: DS.test_heat_appears_where_the_dissipation_is("ohmic"),
     lambda o: DS.test_uniform_step_with_the_powell_source_and_relaxing_gradients(),
     lambda o: DS.test_oracle_matches_numpy_restatement(True),
+]
+
+DISS3_PINS = [
+    lambda o: D3.test_without_dissipation_the_mhd_fields_follow_the_ideal_scheme(),
+    lambda o: D3.test_update_is_covariant_under_the_cyclic_rotation_of_the_axes(True),
+    lambda o: D3.test_shear_wave_along_z_decays_at_nu_plus_the_lattice_diffusion(0.01),
+    lambda o: D3.test_magnetic_sheet_along_z_diffuses_at_eta_plus_the_lattice_diffusion(0.01),
+    lambda o: D3.test_z_gradient_lattices_relax_to_tau_m_times_the_gradients(),
+    lambda o: D3.test_uniform_step_with_the_powell_source_and_relaxing_gradients(),
+    lambda o: D3.test_conserved_fields_are_conserved_exactly(),
 ]
 
 # (name, original text, planted mistake, which pin family must catch it)
@@ -158,12 +169,22 @@ MUTANTS = [
     ("viscous work sign", "- u_visc + eta * jxB[c];", "+ u_visc + eta * jxB[c];", DISS_PINS),
     ("gradient flux on the wrong axis", "phi[3 * (8 + 3 * a + b) + c] = Q[8 + 3 * a + b] * u[c] - (a == c ? B[b] : 0.0);",
      "phi[3 * (8 + 3 * a + b) + c] = Q[8 + 3 * a + b] * u[c] - (b == c ? B[a] : 0.0);", DISS_PINS),
-    ("velocity gradient fed by B", "phi[3 * (14 + 3 * a + b) + c] = Q[14 + 3 * a + b] * u[c] - (a == c ? u[b] : 0.0);",
-     "phi[3 * (14 + 3 * a + b) + c] = Q[14 + 3 * a + b] * u[c] - (a == c ? B[b] : 0.0);", DISS_PINS),
-    ("divergence from G_xy", "-(Q[8 + 0] + Q[8 + 3 + 1]) / tau_m;", "-(Q[8 + 0] + Q[8 + 1]) / tau_m;", DISS_PINS),
-    ("gradient relaxation sign", "for (int k = 8; k < ORC_NVAR_DISS; ++k) S[k] = -Q[k] / tau_m;",
-     "for (int k = 8; k < ORC_NVAR_DISS; ++k) S[k] = Q[k] / tau_m;", DISS_PINS),
+    ("velocity gradient fed by B", "phi[3 * (w0 + 3 * a + b) + c] = Q[w0 + 3 * a + b] * u[c] - (a == c ? u[b] : 0.0);",
+     "phi[3 * (w0 + 3 * a + b) + c] = Q[w0 + 3 * a + b] * u[c] - (a == c ? B[b] : 0.0);", DISS_PINS),
+    ("divergence from G_xy", "trace += Q[8 + 4 * a]; /* G_aa */", "trace += Q[8 + a]; /* G_aa */", DISS_PINS),
+    ("gradient relaxation sign", "for (int k = 8; k < nvar; ++k) S[k] = -Q[k] / tau_m;",
+     "for (int k = 8; k < nvar; ++k) S[k] = Q[k] / tau_m;", DISS_PINS),
     ("current without the minus of the curl", "dB[0][1] - dB[1][0]", "dB[0][1] + dB[1][0]", DISS_PINS),
+    ("3-D gradients read two rows", "dB[a][b] = a < dim ? Q[8 + 3 * a + b] / tau_m : 0.0;",
+     "dB[a][b] = a < 2 ? Q[8 + 3 * a + b] / tau_m : 0.0;", DISS3_PINS),
+    ("3-D velocity gradients read two rows", "du[a][b] = a < dim ? Q[w0 + 3 * a + b] / tau_m : 0.0;",
+     "du[a][b] = a < 2 ? Q[w0 + 3 * a + b] / tau_m : 0.0;", DISS3_PINS),
+    ("3-D Powell divergence misses G_zz", "for (int a = 0; a < dim; ++a) trace += Q[8 + 4 * a];",
+     "for (int a = 0; a < 2; ++a) trace += Q[8 + 4 * a];", DISS3_PINS),
+    ("3-D W fluxes at the 2-D offset", "    const int w0 = 8 + 3 * dim;\n    double rho = Q[0];",
+     "    const int w0 = 14;\n    double rho = Q[0];", DISS3_PINS),
+    ("3-D gradient fluxes stop at the y row", "        for (int a = 0; a < dim; ++a)\n            for (int b = 0; b < 3; ++b) {\n                phi[3 * (8",
+     "        for (int a = 0; a < 2; ++a)\n            for (int b = 0; b < 3; ++b) {\n                phi[3 * (8", DISS3_PINS),
     ("Powell source without weight", "fout[k * L->q + i] = f + (feq[k][i] - f) / tau[k] + L->w[i] * sk;",
      "fout[k * L->q + i] = f + (feq[k][i] - f) / tau[k] + sk;", POWELL_PINS),
 ]
