@@ -1,4 +1,4 @@
-// ideal_cell.cuh -- per-cell arithmetic of the ideal-MHD VLBM step (device).
+// ideal_cell.cuh -- per-cell arithmetic of the ideal-MHD VLBM step (host and device).
 //
 // Given the 8 x q pre-collision populations of one cell, computes
 //   moments          Q_k = sum_i f_ki                                (Eq. 4)
@@ -15,13 +15,13 @@ namespace vlbm {
 
 // Gas pressure of Eq. 9 in FP64 from the FP32 sums G_k of a cell's stored
 // deviations: Q_k = r_k + s_k G_k, refscale = r_0..7 then s_0..7 (device).
-static __device__ __noinline__ double pressure_fp64(float G0, float G1, float G2, float G3, float G4, float G5, float G6,
-                                             float G7, const double *__restrict__ refscale, double gm1)
+static VLBM_HD __noinline__ double pressure_fp64(float G0, float G1, float G2, float G3, float G4, float G5, float G6,
+                                            float G7, const double *__restrict__ refscale, double gm1)
 {
     const float G[8] = {G0, G1, G2, G3, G4, G5, G6, G7};
     double q[8];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) q[k] = fma((double)G[k], __ldg(refscale + 8 + k), __ldg(refscale + k));
+    for (int k = 0; k < 8; ++k) q[k] = fma((double)G[k], ro_load(refscale + 8 + k), ro_load(refscale + k));
     const double kin = (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]) / q[0];
     const double mag = q[5] * q[5] + q[6] * q[6] + q[7] * q[7];
     return gm1 * (q[4] - 0.5 * kin - 0.5 * mag);
@@ -46,9 +46,9 @@ static __device__ __noinline__ double pressure_fp64(float G0, float G1, float G2
 // Fluxes phi[k][a] of one cell from its moment sums G_k (deviation storage:
 // Q_k = r_k + s_k G_k), with the positivity check.
 template <int D, class C, bool DEV>
-__device__ __forceinline__ void ideal_flux_of_sums(const C (&G)[8], const C gm1, unsigned *flags, const C *ref,
-                                                   const C *scale, const double *refscale, const C p_theta,
-                                                   C (&phi)[8][D])
+VLBM_HD __forceinline__ void ideal_flux_of_sums(const C (&G)[8], const C gm1, unsigned *flags, const C *ref,
+                                                const C *scale, const double *refscale, const C p_theta,
+                                                C (&phi)[8][D])
 {
     C q[8];
 #pragma unroll
@@ -68,7 +68,7 @@ __device__ __forceinline__ void ideal_flux_of_sums(const C (&G)[8], const C gm1,
             p = (C)pressure_fp64(G[0], G[1], G[2], G[3], G[4], G[5], G[6], G[7], refscale, (double)gm1);
     }
     const C pt = p + C(0.5) * B2;
-    if (!(rho > C(0)) || !(p > C(0))) atomicOr(flags, kFlagNonPhysical);
+    if (!(rho > C(0)) || !(p > C(0))) raise_flag(flags, kFlagNonPhysical);
     const C Ept = E + pt;
 #pragma unroll
     for (int ax = 0; ax < D; ++ax) {
@@ -85,9 +85,9 @@ __device__ __forceinline__ void ideal_flux_of_sums(const C (&G)[8], const C gm1,
 // BGK relaxation with source of lattice k's populations fk in place, given
 // its sum G_k and flux phi_k.
 template <int D, class C, bool DEV>
-__device__ __forceinline__ void ideal_relax_lattice(C (&fk)[AxisSet<D>::Q], const int k, const C Gk,
-                                                    const C (&phik)[D], const C *omega, const C *src0,
-                                                    const C *src1, const C *inv_scale)
+VLBM_HD __forceinline__ void ideal_relax_lattice(C (&fk)[AxisSet<D>::Q], const int k, const C Gk,
+                                                 const C (&phik)[D], const C *omega, const C *src0,
+                                                 const C *src1, const C *inv_scale)
 {
     const C om = omega[k];
     const C omc = C(1) - om;
@@ -106,11 +106,11 @@ __device__ __forceinline__ void ideal_relax_lattice(C (&fk)[AxisSet<D>::Q], cons
 }
 
 template <int D, class C, bool DEV = false>
-__device__ __forceinline__ void ideal_collide(C (&f)[8][AxisSet<D>::Q], const C gm1, const C *omega,
-                                              const C *src0, const C *src1, unsigned *flags,
-                                              const C *ref = nullptr, const C *scale = nullptr,
-                                              const C *inv_scale = nullptr, const double *refscale = nullptr,
-                                              const C p_theta = C(0))
+VLBM_HD __forceinline__ void ideal_collide(C (&f)[8][AxisSet<D>::Q], const C gm1, const C *omega,
+                                           const C *src0, const C *src1, unsigned *flags,
+                                           const C *ref = nullptr, const C *scale = nullptr,
+                                           const C *inv_scale = nullptr, const double *refscale = nullptr,
+                                           const C p_theta = C(0))
 {
     constexpr int Q = AxisSet<D>::Q;
     C G[8];
@@ -133,9 +133,9 @@ __device__ __forceinline__ void ideal_collide(C (&f)[8][AxisSet<D>::Q], const C 
 // state Q_hat = (rho, rho u_hat, p/(gamma-1) + rho|u_hat|^2/2 + |B_hat|^2/2,
 // B_hat); BGK towards f_eq(Q_hat) plus the uniform source.  Plain storage.
 template <int D, class C>
-__device__ __forceinline__ void ideal_collide_hom(C (&f)[8][AxisSet<D>::Q], const C gm1, const C *omega,
-                                                  const C *src0, const C *src1, unsigned *flags, const C d,
-                                                  const C (&uB)[3], const C (&BB)[3])
+VLBM_HD __forceinline__ void ideal_collide_hom(C (&f)[8][AxisSet<D>::Q], const C gm1, const C *omega,
+                                               const C *src0, const C *src1, unsigned *flags, const C d,
+                                               const C (&uB)[3], const C (&BB)[3])
 {
     constexpr int Q = AxisSet<D>::Q;
     C q[8];
@@ -153,7 +153,7 @@ __device__ __forceinline__ void ideal_collide_hom(C (&f)[8][AxisSet<D>::Q], cons
     const C B2 = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
     const C mu = q[1] * u[0] + q[2] * u[1] + q[3] * u[2];
     const C p = gm1 * (q[4] - C(0.5) * mu - C(0.5) * B2);
-    if (!(rho > C(0)) || !(p > C(0))) atomicOr(flags, kFlagNonPhysical);
+    if (!(rho > C(0)) || !(p > C(0))) raise_flag(flags, kFlagNonPhysical);
     // blended state
     const C dc = C(1) - d;
     C uh[3], Bh[3], mh[3];
@@ -208,8 +208,8 @@ __device__ __forceinline__ void ideal_collide_hom(C (&f)[8][AxisSet<D>::Q], cons
 // lattices and -D / tau_M for D is injected directly, f* += w_i S_k, on top
 // of the uniform source src0/src1.  Plain storage only (no deviations).
 template <int D, class C>
-__device__ __forceinline__ void powell_collide(C (&f)[9][AxisSet<D>::Q], const C gm1, const C *omega,
-                                               const C *src0, const C *src1, const C inv_tau_m, unsigned *flags)
+VLBM_HD __forceinline__ void powell_collide(C (&f)[9][AxisSet<D>::Q], const C gm1, const C *omega,
+                                            const C *src0, const C *src1, const C inv_tau_m, unsigned *flags)
 {
     constexpr int Q = AxisSet<D>::Q;
     C q[9];
@@ -232,7 +232,7 @@ __device__ __forceinline__ void powell_collide(C (&f)[9][AxisSet<D>::Q], const C
     const C uB = u[0] * B[0] + u[1] * B[1] + u[2] * B[2];
     const C p = gm1 * (E - C(0.5) * mu - C(0.5) * B2);
     const C pt = p + C(0.5) * B2;
-    if (!(rho > C(0)) || !(p > C(0))) atomicOr(flags, kFlagNonPhysical);
+    if (!(rho > C(0)) || !(p > C(0))) raise_flag(flags, kFlagNonPhysical);
     const C Ept = E + pt;
 
     C phi[9][D];

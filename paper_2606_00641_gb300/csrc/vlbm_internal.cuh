@@ -45,6 +45,32 @@ constexpr unsigned kFlagTimeout = 4u;      // a bounded device wait gave up
 // Direction i of the axis-aligned sets: 0 rest, 2a+1 = +e_a, 2a+2 = -e_a.
 __host__ __device__ constexpr int opp_axis(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
 
+// The per-cell arithmetic (ideal_cell.cuh) is host-and-device: the step
+// kernels run it on the GPU, and the same source also compiles for the host,
+// where a test checks it cell by cell without a GPU.  The two device-only
+// operations it needs go through these helpers.
+#define VLBM_HD __host__ __device__
+
+// Raise status bits in the flag word (atomically on the device).
+VLBM_HD __forceinline__ void raise_flag(unsigned *flags, unsigned bits)
+{
+#ifdef __CUDA_ARCH__
+    atomicOr(flags, bits);
+#else
+    *flags |= bits;
+#endif
+}
+
+// Load through the read-only data cache on the device.
+template <class T> VLBM_HD __forceinline__ T ro_load(const T *p)
+{
+#ifdef __CUDA_ARCH__
+    return __ldg(p);
+#else
+    return *p;
+#endif
+}
+
 // Weights of the axis sets: D2Q5 (1/3, 1/6; cs^2 = 1/3), D3Q7 (1/4, 1/8;
 // cs^2 = 1/4).  In both, w_moving / cs^2 = 1/2.
 template <int D> struct AxisSet;
@@ -67,7 +93,7 @@ template <int D, class C> struct ExactWeights {
     static constexpr C w1 = C(AxisSet<D>::w1);
     static constexpr C w0 = D == 2 ? C(1) - C(4) * w1 : C(AxisSet<D>::w0);
 };
-template <int D, class C> __device__ __forceinline__ void relax_weights(C om, C &ow0, C &ow1)
+template <int D, class C> VLBM_HD __forceinline__ void relax_weights(C om, C &ow0, C &ow1)
 {
     ow1 = om * ExactWeights<D, C>::w1;
     ow0 = D == 2 ? om - C(4) * ow1 : om * ExactWeights<D, C>::w0;
