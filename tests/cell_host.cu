@@ -1,16 +1,19 @@
 // cell_host.cu -- host build of the step kernels' per-cell arithmetic
 // (ideal_cell.cuh: moments, Eq. 4; pressure, Eq. 9; fluxes, Eq. 12; BGK with
 // direct source injection, Eq. 2 and 3; the Powell, homogenised-solid and
-// deviation-storage forms), so that CPU tests can compare it cell by cell with
-// the oracle.  Test infrastructure only: nothing in the library calls it, and
-// the library has no CPU path.
+// deviation-storage forms; diss_cell.cuh: the fluxes and sources of the
+// dissipative system, sec. 2.2.1 and 2.3), so that CPU tests can compare it
+// cell by cell with the oracle.  Test infrastructure only: nothing in the
+// library calls it, and the library has no CPU path.
 //
-// Every entry takes one cell's populations f[k * q + i] (k lattice, i
-// direction 0 rest, 2a+1 = +e_a, 2a+2 = -e_a; q = 5 in 2-D, 7 in 3-D) and
-// collides them in place with the kernels' own inputs: omega_k = 1 / tau_k,
+// The collision entries take one cell's populations f[k * q + i] (k lattice,
+// i direction 0 rest, 2a+1 = +e_a, 2a+2 = -e_a; q = 5 in 2-D, 7 in 3-D) and
+// collide them in place with the kernels' own inputs: omega_k = 1 / tau_k,
 // src0_k = w_0 S_k, src1_k = w_moving S_k (deviation storage: both divided by
-// the scale s_k).  Status bits the cell raises are OR-ed into *flags.
-// Returns 0, or -1 for a dimension other than 2 or 3.
+// the scale s_k); they return 0, or -1 for a dimension other than 2 or 3.
+// The dissipative entries take one state and return its fluxes and sources.
+// Status bits a cell raises are OR-ed into *flags.
+#include "diss_cell.cuh"
 #include "ideal_cell.cuh"
 
 using namespace vlbm;
@@ -69,6 +72,26 @@ void hom(C gm1, const C *omega, const C *src0, const C *src1, C d, const C *uB, 
     const C b[3] = {BB[0], BB[1], BB[2]};
     ideal_collide_hom<D, C>(c, gm1, omega, src0, src1, flags, d, u, b);
     Cell<D, C>::put(c, f);
+}
+
+template <class C>
+void diss(const C *q, C gm1, C nu, C eta0, C inv_jc2, C inv_tau_m, int powell, C *phi, C *S, unsigned *flags)
+{
+    DissArgs<C> a{};
+    a.gm1 = gm1;
+    a.nu = nu;
+    a.eta0 = eta0;
+    a.inv_jc2 = inv_jc2;
+    a.inv_tau_m = inv_tau_m;
+    a.powell = powell;
+    C qq[kDissLat], ph[kDissLat][2], s[kDissLat];
+    for (int k = 0; k < kDissLat; ++k) qq[k] = q[k];
+    diss_flux_source<C>(qq, a, ph, s, flags);
+    for (int k = 0; k < kDissLat; ++k) {
+        phi[2 * k] = ph[k][0];
+        phi[2 * k + 1] = ph[k][1];
+        S[k] = s[k];
+    }
 }
 
 }  // namespace
@@ -140,6 +163,22 @@ int hc_hom_f32(int dim, float gm1, const float *omega, const float *src0, const 
 {
     HC_DIM(dim, (hom<2, float>(gm1, omega, src0, src1, d, uB, BB, f, flags)),
            (hom<3, float>(gm1, omega, src0, src1, d, uB, BB, f, flags)));
+}
+
+// Dissipative system (2-D): fluxes phi[2 k + c] along x, y and sources S[k] of
+// one state q[20]; inv_jc2 = 1 / j_c^2 (0: constant eta), powell 0 or 1.
+int hc_diss_f64(const double *q, double gm1, double nu, double eta0, double inv_jc2, double inv_tau_m, int powell,
+                double *phi, double *S, unsigned *flags)
+{
+    diss<double>(q, gm1, nu, eta0, inv_jc2, inv_tau_m, powell, phi, S, flags);
+    return 0;
+}
+
+int hc_diss_f32(const float *q, float gm1, float nu, float eta0, float inv_jc2, float inv_tau_m, int powell,
+                float *phi, float *S, unsigned *flags)
+{
+    diss<float>(q, gm1, nu, eta0, inv_jc2, inv_tau_m, powell, phi, S, flags);
+    return 0;
 }
 
 }  // extern "C"

@@ -9,7 +9,9 @@ them; the GPU parity tests check the kernels themselves, streaming included.
 Covered: FP64 and FP32 plain storage, the Powell form (nine lattices), the
 homogenised-solid blend, the FP16/BF16 deviation form (collision on stored
 deviations, sources divided by the scale) with and without the FP64 pressure
-recovery, and the non-physical flag, on D2Q5 and D3Q7 with uniform sources.
+recovery, and the non-physical flag, on D2Q5 and D3Q7 with uniform sources;
+and the dissipative system's fluxes and sources (diss_cell.cuh: viscous
+stress, eta(j), the gradient lattices, the Powell source) state by state.
 """
 import ctypes
 import os
@@ -33,8 +35,8 @@ F32_TOL = 1e-5   # relative to the lattice's largest population: ~80 FP32 ulps
 
 def _deps():
     csrc = os.path.join(ROOT, "paper_2606_00641_gb300", "csrc")
-    return [SRC, os.path.join(csrc, "ideal_cell.cuh"), os.path.join(csrc, "vlbm_internal.cuh"),
-            os.path.join(ROOT, "include", "vlbm.h")]
+    return [SRC, os.path.join(csrc, "ideal_cell.cuh"), os.path.join(csrc, "diss_cell.cuh"),
+            os.path.join(csrc, "vlbm_internal.cuh"), os.path.join(ROOT, "include", "vlbm.h")]
 
 
 @pytest.fixture(scope="module")
@@ -61,6 +63,8 @@ def H():
     L.hc_powell_f32.argtypes = [i, f, p, p, p, f, p, p]
     L.hc_hom_f64.argtypes = [i, d, p, p, p, d, p, p, p, p]
     L.hc_hom_f32.argtypes = [i, f, p, p, p, f, p, p, p, p]
+    L.hc_diss_f64.argtypes = [p, d, d, d, d, d, i, p, p, p]
+    L.hc_diss_f32.argtypes = [p, f, f, f, f, f, i, p, p, p]
     return L
 
 
@@ -241,3 +245,33 @@ def test_non_physical_cell_raises_the_flag(H, dim):
     assert H.hc_ideal_f64(dim, gamma - 1.0, _p(omega), _p(src0), _p(src1), _p(c), _p(flags)) == 0
     assert flags[0] & FLAG_NONPHYSICAL
     assert H.hc_ideal_f64(4, gamma - 1.0, _p(omega), _p(src0), _p(src1), _p(c), _p(flags)) == -1
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("powell", [False, True])
+@pytest.mark.parametrize("j_c", [0.0, 0.08])
+def test_dissipative_fluxes_and_sources_match_the_oracle(H, prec, powell, j_c):
+    shape = (6, 7)
+    f0 = fields.ideal_fields(shape, 61, mach=1.0, beta=1.0, cfl=0.2)
+    rng = np.random.default_rng(62)
+    Q = np.concatenate([f0.Q, 0.05 * rng.normal(size=(12,) + shape)]).reshape(20, -1).T
+    dp = oracle.Dissipation(nu=0.02, eta0=0.03, j_c=j_c, tau_m=1.7, powell=powell)
+    dtype = np.float64 if prec == "f64" else np.float32
+    fn = H.hc_diss_f64 if prec == "f64" else H.hc_diss_f32
+    inv_jc2 = 1.0 / (j_c * j_c) if j_c > 0 else 0.0
+    tol = 1e-13 if prec == "f64" else F32_TOL
+    flags = np.zeros(1, np.uint32)
+    for q in Q:
+        phi = np.zeros(40, dtype)
+        S = np.zeros(20, dtype)
+        assert fn(_p(q.astype(dtype)), f0.gamma - 1.0, dp.nu, dp.eta0, inv_jc2, 1.0 / dp.tau_m, int(powell),
+                  _p(phi), _p(S), _p(flags)) == 0
+        ref_phi = oracle.diss_flux(f0.gamma, dp, q)[:, :2]
+        ref_S = oracle.diss_source(dp, q)
+        # each lattice's fluxes against the largest flux of the state's MHD part (the terms
+        # a flux is made of are of that size), sources against the largest source
+        pscale = np.abs(ref_phi).max()
+        assert np.abs(phi.reshape(20, 2).astype(np.float64) - ref_phi).max() < tol * pscale
+        sscale = np.abs(ref_S).max()
+        assert np.abs(S.astype(np.float64) - ref_S).max() < tol * sscale
+    assert flags[0] == 0
