@@ -34,6 +34,24 @@ def _solid(shape, d, uB=(0.0, 0.0, 0.0), BB=(0.0, 0.0, 0.0)):
     return s
 
 
+@pytest.mark.parametrize("d", [0.0, 0.25, 0.6, 1.0])
+def test_blended_state_of_one_cell(d):
+    # sec. 2.4, "Homogenization": the blend moves u and B affinely from the solid's (d = 0) to
+    # the cell's own (d = 1) and keeps the cell's density and gas pressure; d = 1 is the cell
+    Q = np.array([1.3, 0.13, -0.26, 0.065, 2.0, 0.3, -0.1, 0.2])
+    uB, BB = np.array([0.02, 0.05, -0.01]), np.array([-0.2, 0.1, 0.4])
+    Qh = oracle.hlbm_target(GAMMA, Q, d, uB, BB)
+    u = Q[1:4] / Q[0]
+    assert Qh[0] == Q[0]
+    np.testing.assert_allclose(Qh[1:4] / Qh[0], d * u + (1 - d) * uB, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(Qh[5:8], d * Q[5:8] + (1 - d) * BB, rtol=0, atol=1e-15)
+    assert abs(oracle.ideal_pressure(GAMMA, Qh) / oracle.ideal_pressure(GAMMA, Q) - 1) < 1e-14
+    if d == 1.0:
+        np.testing.assert_allclose(Qh, Q, rtol=1e-15, atol=1e-16)
+    if d == 0.0:
+        np.testing.assert_array_equal(Qh[5:8], BB)
+
+
 @pytest.mark.parametrize("shape", [(12, 10), (4, 6, 5)])
 def test_fluid_everywhere_is_the_ideal_scheme(shape):
     # d = 1: the blend returns the cell's own u and B; the rebuilt energy equals e
