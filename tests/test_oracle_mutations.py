@@ -28,6 +28,8 @@ IDEAL_PINS = [
     lambda o: P.test_linear_wave_speed_and_decay(o, "sound"),
     lambda o: P.test_linear_wave_speed_and_decay(o, "oblique"),
     lambda o: P.test_direct_source_injection_adds_S_per_cell_per_step(o),
+    lambda o: P.test_update_is_covariant_under_the_rotations_of_the_lattice(o, 2),
+    lambda o: P.test_update_is_covariant_under_the_rotations_of_the_lattice(o, 3),
 ]
 RES_PINS = [
     lambda o: R.test_mass_exact_and_force_adds_F_per_cell(o),
@@ -100,6 +102,8 @@ MUTANTS = [
     ("EOS misses magnetic energy", "(e - 0.5 * rho * u2 - 0.5 * B2); /* Eq. 9 */",
      "(e - 0.5 * rho * u2); /* Eq. 9 */", IDEAL_PINS),
     ("Maxwell stress sign", "+ ptot * delta - B[a] * B[b];", "+ ptot * delta + B[a] * B[b];",
+     IDEAL_PINS),
+    ("Maxwell stress from B_x on every axis", "+ ptot * delta - B[a] * B[b];", "+ ptot * delta - B[0] * B[b];",
      IDEAL_PINS),
     ("D2Q5 rest weight", "set_dir(L, 0, 0, 0, 0, 1.0 / 3.0);\n        set_dir(L, 1, 1, 0, 0, 1.0 / 6.0);",
      "set_dir(L, 0, 0, 0, 0, 0.3);\n        set_dir(L, 1, 1, 0, 0, 1.0 / 6.0);", IDEAL_PINS),

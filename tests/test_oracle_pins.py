@@ -327,6 +327,45 @@ def test_brio_wu_states_smoke(orc):
 # brute force: C oracle vs the independent NumPy restatement
 # --------------------------------------------------------------------------
 
+def _rotate_ideal(Q):
+    """The rotation of the whole state that the lattice maps onto itself: in 2-D the
+    quarter turn about z, (x, y) -> (-y, x), on a square grid; in 3-D the cyclic
+    x -> y -> z.  Positions and the vectors rho u and B turn together."""
+    out = np.empty_like(Q)
+    if Q.ndim == 3:  # [8, ny, nx], ny == nx
+        n = Q.shape[-1]
+        Y, X = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+        moved = Q[:, (-X) % n, Y]          # value at (x, y) lands at (-y, x)
+        out[:] = moved
+        for v in (1, 5):                   # (v_x, v_y, v_z) -> (-v_y, v_x, v_z)
+            out[v], out[v + 1] = -moved[v + 1], moved[v]
+        return out
+    moved = np.moveaxis(Q, -3, -1)         # value at (x, y, z) lands at (z, x, y)
+    out = moved.copy()
+    for v in (1, 5):                       # (v_x, v_y, v_z) -> (v_z, v_x, v_y)
+        out[v:v + 3] = np.roll(moved[v:v + 3], 1, axis=0)
+    return out
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_update_is_covariant_under_the_rotations_of_the_lattice(orc, dim):
+    # D2Q5 and D3Q7 are invariant under these rotations and so is ideal MHD: the run of the
+    # rotated state is the rotated run (to rounding; the state itself is far from symmetric)
+    shape = (12, 12) if dim == 2 else (4, 5, 6)
+    f0 = fields.ideal_fields(shape, 333, mach=1.0, beta=1.0, cfl=0.2)
+    tau = [0.6, 0.55, 0.55, 0.55, 0.7, 0.65, 0.65, 0.65]   # equal within each vector
+    a = _rotate_ideal(orc.ideal_run(f0.Q, f0.gamma, tau, 9))
+    b = orc.ideal_run(_rotate_ideal(f0.Q), f0.gamma, tau, 9)
+    assert np.abs(a - b).max() < 1e-13 * np.abs(a).max()
+    R = _rotate_ideal(f0.Q)
+    corner = (slice(None),) + (slice(0, 4),) * dim
+    assert np.abs(R[corner] - f0.Q[corner]).max() > 0.05 * np.abs(f0.Q).max()
+    # four quarter turns (three cyclic rotations) are the identity
+    for _ in range(3 if dim == 2 else 2):
+        R = _rotate_ideal(R)
+    np.testing.assert_array_equal(R, f0.Q)
+
+
 @pytest.mark.parametrize("dim", [2, 3])
 def test_c_oracle_matches_numpy_restatement(orc, dim):
     from oracle import numpy_ref
