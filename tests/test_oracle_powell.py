@@ -164,3 +164,25 @@ def test_oracle_matches_numpy_restatement(shape):
     a = oracle.powell_run(Q, f0.gamma, tau, 2.0, 20)
     b = R.powell_run(Q, f0.gamma, tau, 2.0, 20)
     assert np.abs(a - b).max() < 1e-13 * np.abs(a).max()
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_update_is_covariant_under_the_rotations_of_the_lattice(dim):
+    # as for the ideal scheme: the divergence lattice D is a scalar, so it only moves with
+    # the cells while rho u and B turn (quarter turn about z in 2-D, cyclic x -> y -> z in 3-D)
+    from test_oracle_pins import _rotate_ideal
+
+    def rotate(Q):
+        # D moves like rho, slot 0 of the ideal rotation (a scalar)
+        scalar = _rotate_ideal(np.repeat(Q[8:9], 8, axis=0))[:1]
+        return np.concatenate([_rotate_ideal(Q[:8]), scalar])
+
+    shape = (10, 10) if dim == 2 else (4, 5, 6)
+    f0 = fields.ideal_fields(shape, 444, mach=1.0, beta=1.0, cfl=0.2)
+    rng = np.random.default_rng(444)
+    Q = np.concatenate([f0.Q, 0.05 * rng.normal(size=(1,) + shape)])
+    tau = [0.6, 0.55, 0.55, 0.55, 0.7, 0.65, 0.65, 0.65, 0.8]
+    a = rotate(oracle.powell_run(Q, GAMMA, tau, 2.5, 9))
+    b = oracle.powell_run(rotate(Q), GAMMA, tau, 2.5, 9)
+    assert np.abs(a - b).max() < 1e-13 * np.abs(a).max()
+    assert np.abs(a[8]).max() > 1e-3
