@@ -221,3 +221,43 @@ def test_oracle_matches_numpy_restatement(powell):
     # and the dissipation matters at this size (the comparison is not of two ideal runs)
     c = oracle.diss_run(Q, f0.gamma, tau20, oracle.Dissipation(tau_m=2.0, powell=powell), 12)
     assert np.abs(a - c).max() > 1e-6 * np.abs(a).max()
+
+
+
+@pytest.mark.parametrize("powell", [False, True])
+def test_update_is_covariant_under_the_quarter_turn_of_the_lattice(powell):
+    # D2Q5 and the dissipative system are invariant under the quarter turn about z,
+    # (x, y) -> (-y, x): positions move, rho u and B turn as vectors, G and W as tensors
+    # (T' = R T R^T; their rows x, y map onto each other and the z row stays absent)
+    from test_oracle_pins import _rotate_ideal
+    n = 10
+    Rm = np.array([[0.0, -1.0, 0.0], [1.0, 0.0, 0.0], [0.0, 0.0, 1.0]])
+    Y, Xg = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+
+    def move(A):  # the value at (x, y) lands at (-y, x)
+        return A[..., (-Xg) % n, Y]
+
+    def rotate(Q):
+        out = np.empty_like(Q)
+        out[:8] = _rotate_ideal(Q[:8])
+        for lo in (8, 14):
+            T = np.zeros((3, 3, n, n))
+            T[:2] = Q[lo:lo + 6].reshape(2, 3, n, n)
+            T = np.einsum("ik,jl,kl...->ij...", Rm, Rm, T)
+            assert np.abs(T[2]).max() == 0.0
+            out[lo:lo + 6] = move(T[:2].reshape(6, n, n))
+        return out
+
+    f0 = fields.ideal_fields((n, n), 91, mach=1.0, beta=1.0, cfl=0.2)
+    rng = np.random.default_rng(92)
+    Q = np.concatenate([f0.Q, 0.05 * rng.normal(size=(12, n, n))])
+    dp = oracle.Dissipation(nu=0.02, eta0=0.03, j_c=0.05, tau_m=1.5, powell=powell)
+    tau = [0.6, 0.55, 0.55, 0.55, 0.7, 0.65, 0.65, 0.65]
+    a = rotate(oracle.diss_run(Q, f0.gamma, tau, dp, 8, tau_g=0.7))
+    b = oracle.diss_run(rotate(Q), f0.gamma, tau, dp, 8, tau_g=0.7)
+    assert np.abs(a - b).max() < 1e-13 * np.abs(a).max()
+    # four quarter turns are the identity
+    R = Q
+    for _ in range(4):
+        R = rotate(R)
+    np.testing.assert_array_equal(R, Q)

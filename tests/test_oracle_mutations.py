@@ -79,6 +79,7 @@ DISS_PINS = [
     lambda o: DS.test_heat_appears_where_the_dissipation_is("ohmic"),
     lambda o: DS.test_uniform_step_with_the_powell_source_and_relaxing_gradients(),
     lambda o: DS.test_oracle_matches_numpy_restatement(True),
+    lambda o: DS.test_update_is_covariant_under_the_quarter_turn_of_the_lattice(True),
 ]
 
 DISS3_PINS = [
