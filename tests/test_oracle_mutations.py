@@ -37,6 +37,7 @@ RES_PINS = [
     lambda o: R.test_magnetic_diffusion_gives_eta(o),
     lambda o: R.test_poiseuille_profile(o),
     lambda o: R.test_hartmann_profile(o, 5.0),
+    lambda o: R.test_channel_update_is_symmetric_under_the_mirror_between_its_walls(o),
 ]
 
 POWELL_PINS = [
@@ -119,6 +120,8 @@ MUTANTS = [
      "if (src) out += src[k];", IDEAL_PINS),
     ("bounce-back keeps direction", "fout[(long)L19.opp[i] * N + cell] = fs[i];",
      "fout[(long)i * N + cell] = fs[i];", RES_PINS),
+    ("bounce-back at the bottom wall only", "if (is_wall(dy, ny, walls_y))",
+     "if (is_wall(dy, ny, walls_y) && dy == 0)", RES_PINS),
     ("Guo force half-step factor", "double guo = (1.0 - 0.5 / tau_f) * L19->w[i] *",
      "double guo = L19->w[i] *", RES_PINS),
     ("magnetic flux transposed", "for (int a = 0; a < 3; ++a) phi[a] = u[a] * B[b] - B[a] * u[b];",

@@ -155,3 +155,30 @@ def test_c_oracle_matches_numpy_restatement_resistive(orc):
     Qa = orc.resistive_moments(fa, ga, F, bw, 1)
     Qb = numpy_ref.resistive_moments(fb, gb, F, bw, 1)
     np.testing.assert_allclose(Qa, Qb, rtol=1e-12, atol=1e-15)
+
+
+def test_channel_update_is_symmetric_under_the_mirror_between_its_walls(orc):
+    # y -> ny - 1 - y swaps the two walls; u turns as a vector (u_y flips) and B as a
+    # pseudovector (B_x, B_z flip, B_y stays), which leaves the wall field (0, b, 0) and the
+    # force along x unchanged, so the mirrored run is the run of the mirrored state
+    shape = (3, 8, 5)
+    rng = np.random.default_rng(21)
+    Q = _uniform(shape, B=(0.01, 0.03, -0.02))
+    Q[0] += 0.02 * rng.uniform(-1, 1, size=shape)
+    Q[1:4] = 0.01 * rng.uniform(-1, 1, size=(3,) + shape)
+    Q[4:7] += 0.01 * rng.uniform(-1, 1, size=(3,) + shape)
+    Q[1:4, :, 0, :] = 0
+    Q[1:4, :, -1, :] = 0
+    F, bw = (2e-5, 0.0, 0.0), (0.0, 0.03, 0.0)
+
+    def mirror(S):
+        M = S[:, :, ::-1, :].copy()
+        M[2] *= -1          # u_y
+        M[4] *= -1          # B_x
+        M[6] *= -1          # B_z
+        return M
+
+    a = mirror(orc.resistive_run(Q, 0.62, 0.7, F, bw, True, 9))
+    b = orc.resistive_run(mirror(Q), 0.62, 0.7, F, bw, True, 9)
+    assert np.abs(a - b).max() < 1e-13 * np.abs(a).max()
+    assert np.abs(mirror(Q) - Q).max() > 1e-3   # the state itself is not symmetric
