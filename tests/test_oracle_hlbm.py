@@ -166,3 +166,25 @@ def test_oracle_matches_numpy_restatement(shape):
     a = oracle.hlbm_run(f0.Q, f0.gamma, tau, solid, 15)
     b = R.hlbm_run(f0.Q, f0.gamma, tau, solid, 15)
     assert np.abs(a - b).max() < 1e-13 * np.abs(a).max()
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_update_is_covariant_under_the_rotations_of_the_lattice(dim):
+    # as for the ideal scheme, with the solid turned too: the porosity d moves with the
+    # cells, the solid velocity u^B and field B^B turn as vectors
+    from test_oracle_pins import _rotate_ideal
+
+    def rotate_solid(S):
+        # d and the u^B, B^B vectors in the ideal state's slots 0, 1-3 and 5-7
+        eight = np.concatenate([S[:4], np.zeros((1,) + S.shape[1:]), S[4:7]])
+        return np.delete(_rotate_ideal(eight), 4, axis=0)
+
+    shape = (10, 10) if dim == 2 else (4, 5, 6)
+    f0 = fields.ideal_fields(shape, 555, mach=0.5, beta=2.0, cfl=0.2)
+    rng = np.random.default_rng(555)
+    solid = np.concatenate([rng.uniform(0, 1, size=(1,) + shape),
+                            0.02 * rng.normal(size=(3,) + shape), 0.05 * rng.normal(size=(3,) + shape)])
+    tau = [0.6, 0.55, 0.55, 0.55, 0.7, 0.65, 0.65, 0.65]
+    a = _rotate_ideal(oracle.hlbm_run(f0.Q, GAMMA, tau, solid, 7))
+    b = oracle.hlbm_run(_rotate_ideal(f0.Q), GAMMA, tau, rotate_solid(solid), 7)
+    assert np.abs(a - b).max() < 1e-13 * np.abs(a).max()

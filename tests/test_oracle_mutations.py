@@ -53,6 +53,7 @@ POWELL_PINS = [
 HLBM_PINS = [
     lambda o: H.test_porosity_of_the_signed_distance(),
     lambda o: H.test_blended_state_of_one_cell(0.25),
+    lambda o: H.test_update_is_covariant_under_the_rotations_of_the_lattice(3),
     lambda o: H.test_fluid_everywhere_is_the_ideal_scheme((4, 6, 5)),
     lambda o: H.test_uniform_solid_cell_relaxes_to_the_solid_state(),
     lambda o: H.test_mass_is_conserved_exactly(),
