@@ -69,6 +69,7 @@ OPEN_PINS = [
     lambda o: O.test_supersonic_inflow_flushes_the_domain_to_the_inflow_state(),
     lambda o: O.test_zero_gradient_faces_let_a_pulse_leave(),
     lambda o: O.test_oracle_matches_numpy_restatement((5, 6, 7)),
+    lambda o: O.test_update_is_symmetric_under_the_mirror_that_swaps_the_x_faces(),
 ]
 
 DISS_PINS = [
