@@ -38,6 +38,7 @@ RES_PINS = [
     lambda o: R.test_poiseuille_profile(o),
     lambda o: R.test_hartmann_profile(o, 5.0),
     lambda o: R.test_channel_update_is_symmetric_under_the_mirror_between_its_walls(o),
+    lambda o: R.test_channel_update_is_covariant_under_the_quarter_turn_about_y(o),
 ]
 
 POWELL_PINS = [

@@ -182,3 +182,30 @@ def test_channel_update_is_symmetric_under_the_mirror_between_its_walls(orc):
     b = orc.resistive_run(mirror(Q), 0.62, 0.7, F, bw, True, 9)
     assert np.abs(a - b).max() < 1e-13 * np.abs(a).max()
     assert np.abs(mirror(Q) - Q).max() > 1e-3   # the state itself is not symmetric
+
+
+def test_channel_update_is_covariant_under_the_quarter_turn_about_y(orc):
+    # (x, y, z) -> (z, y, -x) maps D3Q19 and D3Q7 onto themselves and keeps the walls; u, B,
+    # the force and the wall field turn as vectors (v -> (v_z, v_y, -v_x)); square in x, z
+    n, ny = 5, 8
+    rng = np.random.default_rng(22)
+    Q = _uniform((n, ny, n), B=(0.01, 0.03, -0.02))
+    Q[0] += 0.02 * rng.uniform(-1, 1, size=(n, ny, n))
+    Q[1:4] = 0.01 * rng.uniform(-1, 1, size=(3, n, ny, n))
+    Q[4:7] += 0.01 * rng.uniform(-1, 1, size=(3, n, ny, n))
+    Q[1:4, :, 0, :] = 0
+    Q[1:4, :, -1, :] = 0
+    Zi, Yi, Xi = np.meshgrid(np.arange(n), np.arange(ny), np.arange(n), indexing="ij")
+
+    def turn(v):
+        return np.array([v[2], v[1], -v[0]])
+
+    def rotate(S):
+        M = S[:, Xi, Yi, (-Zi) % n]      # the value at (x, y, z) lands at (z, y, -x)
+        return np.concatenate([M[:1], turn(M[1:4]), turn(M[4:7])])
+
+    F, bw = np.array([2e-5, 0.0, 1e-5]), np.array([0.01, 0.03, -0.02])
+    a = rotate(orc.resistive_run(Q, 0.62, 0.7, F, bw, True, 9))
+    b = orc.resistive_run(rotate(Q), 0.62, 0.7, turn(F), turn(bw), True, 9)
+    assert np.abs(a - b).max() < 1e-13 * np.abs(a).max()
+    assert np.abs(rotate(Q) - Q).max() > 1e-3
