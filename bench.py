@@ -31,11 +31,12 @@ if ROOT not in sys.path:
 
 BYTES_PER_POP = {"f64": 8, "f32": 4, "f16dev": 2, "bf16dev": 2}
 # DRAM bytes (read + write) per cell update of the step kernel, from one ncu
-# capture of a 256^3 launch of each parity, taken after the last change to the
-# kernels' source (f32: profiles/bench_512cubed_launch_list.md; f16dev:
-# profiles/k_ideal_step_f16dev_256cubed.md; mean of the two parities); traffic
-# grows in proportion to the cells, so a full launch is this times the cells.
-# Set an entry to None whenever that kernel changes until it is re-captured.
+# capture (dram__bytes_read.sum + dram__bytes_write.sum) of a 256^3 launch of
+# each parity, mean of the two parities, taken after the last change to that
+# kernel's source: f32 7,457,219 kB and f16dev 3,705,818 kB per 16,777,216-cell
+# launch.  Traffic grows in proportion to the cells, so a full launch is this
+# times the cells.  Set an entry to None whenever that kernel changes until it
+# is re-captured.
 MEASURED_DRAM_BYTES_PER_CELL = {"f32": 7457219e3 / 16777216, "f16dev": 3705818e3 / 16777216}
 # the step kernel the roofline describes, per storage (3-D, nx % 8 == 0)
 STEP_KERNEL = {"f32": "k_ideal_step<3,float,float> (fused collide+stream)",

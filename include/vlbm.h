@@ -242,7 +242,9 @@ vlbm_status vlbm_conservation(vlbm_ctx *ctx, int domain, double *sums);
  * Inputs: pop_dev, a device buffer in the library's population layout
  * (slot j = k * q + i of cell x at pop_dev + (j * stride + x) elements of the
  * storage type, q = 5 in 2-D and 7 in 3-D, x = x + nx * (y + ny * z),
- * periodic), holding the state after a number of steps whose parity is
+ * periodic; a context's own buffer has stride = nx * ny * nz rounded up to a
+ * multiple of 64 elements, so that every slot plane starts on a 128-byte
+ * boundary), holding the state after a number of steps whose parity is
  * `parity` (the AA in-place pattern: at parity 0 slot (i, x) is f_i(x), at
  * parity 1 slot (opp i, x - c_i) is); storage as in vlbm_storage, with the
  * per-lattice q_ref and q_scale (8 host doubles each) required for the
@@ -256,7 +258,8 @@ vlbm_status vlbm_conservation(vlbm_ctx *ctx, int domain, double *sums);
  * 268,435,456 cells; larger domains are rejected with VLBM_ERR_ARG before any
  * device work.  The first call on each device looks up the array's device
  * address with that device current, so make that first call before capturing
- * any stream.  All calls share the one array; nothing in it has to start at
+ * any stream; the address is kept for the process, so after a cudaDeviceReset
+ * of that device it is stale and the call must not be used again.  All calls share the one array; nothing in it has to start at
  * zero (every partial is written before it is read), but two calls whose work
  * overlaps on the GPU race on it -- serialise them (one stream, or events).
  * Errors: VLBM_ERR_ARG for NULL buffers, bad sizes or parity, missing
@@ -399,6 +402,72 @@ void vlbm_closure_destroy(vlbm_closure *cl);
  * of device doubles, enqueued on `stream`. */
 vlbm_status vlbm_restrict(const double *Qf_dev, int nx, int ny, int nz, int factor, double *Qc_dev,
                           void *stream);
+
+/* ------------------------------------------------------------------------
+ * Slab decomposition of one periodic domain (sec. 5: the paper ran its
+ * 100-million-cell case on two GPUs; how it split the domain is not given,
+ * this is the library's own decomposition).  A global domain, periodic along
+ * its last axis a (z in 3-D, y in 2-D), is cut into P slabs of whole layers;
+ * slab r (r = 0 .. P-1 in the order of the axis) is an ordinary context of
+ * the slab's size with the global parameters (deviation storage: the same
+ * q_ref and q_scale on every slab), initialised with its part of the global
+ * fields and marked with vlbm_set_slab.  Its kernels wrap axis a inside the
+ * slab; the streaming of Eq. 2 across a slab face is completed by moving, after
+ * every step, the population slot planes that wrapped -- one "lo" message (the
+ * slab's first layer, every slot whose direction has c_a = +1) and one "hi"
+ * message (its last layer, every slot whose direction has c_a = -1).  Slots per
+ * face: one per lattice for D2Q5/D3Q7 models (8 ideal, 9 Powell, 20
+ * dissipative), 5 + 3 for the resistive model (the D3Q19 directions with
+ * c_z = +-1 and the magnetic lattices' +-z slots).  Every element moves
+ * unchanged, so P slabs equal the single domain bit for bit.
+ *
+ * Routing after a step that leaves the slab's step count ODD (an even step
+ * ran): slab r sends hi to slab r+1 and lo to slab r-1 (mod P), and unpacks the
+ * hi it receives from r-1 and the lo from r+1.  After a step that leaves the
+ * count EVEN: hi goes to r-1 and lo to r+1; r unpacks hi from r+1 and lo from
+ * r-1.  Messages are [slot][cell of the face layer] in the storage type,
+ * vlbm_halo_bytes each.  Conservation sums of the decomposed domain are the
+ * sum of the slabs' vlbm_conservation (one all-reduce of 8 doubles across
+ * processes).
+ * ------------------------------------------------------------------------ */
+
+/* Mark (on = 1) or unmark (on = 0) a context as one slab of a decomposed
+ * domain; mark it at an even step count (after vlbm_init_fields).  A slab
+ * steps one step at a time (vlbm_step with n <= 1; n > 1 is VLBM_ERR_STATE)
+ * and after each step its halo exchange must be unpacked before anything
+ * reads its state or steps it again: vlbm_moments*, vlbm_conservation,
+ * vlbm_gather_populations, vlbm_save and vlbm_step return VLBM_ERR_STATE
+ * until vlbm_halo_unpack (or vlbm_slabs_step, or a new init) completes it.
+ * VLBM_ERR_UNSUPPORTED for batched contexts, with a closure attached, or with
+ * an open face on the decomposed axis (faces on the other axes may be open). */
+vlbm_status vlbm_set_slab(vlbm_ctx *ctx, int on);
+
+/* Bytes of one face message (lo or hi) of this context: slots per face x cells
+ * of one layer (nx * ny in 3-D, nx in 2-D) x bytes per stored population;
+ * 0 for NULL or batched contexts. */
+size_t vlbm_halo_bytes(const vlbm_ctx *ctx);
+
+/* Copy the slab's face slot planes into the device buffers lo_dev and hi_dev
+ * (vlbm_halo_bytes each, caller-owned), enqueued on the context's stream.  The
+ * messages are complete when the stream reaches this work (send them from
+ * that stream, or after an event on it).  VLBM_ERR_STATE if not a slab. */
+vlbm_status vlbm_halo_pack(vlbm_ctx *ctx, void *lo_dev, void *hi_dev);
+
+/* Write the received face messages (device buffers, vlbm_halo_bytes each,
+ * complete before the context's stream reaches this work) into the slab's face
+ * slot planes and mark the exchange done.  VLBM_ERR_STATE if not a slab. */
+vlbm_status vlbm_halo_unpack(vlbm_ctx *ctx, const void *lo_dev, const void *hi_dev);
+
+/* Advance P slabs of one decomposed domain that live in this process on one
+ * device and share one stream (slabs[r] is slab r): n steps, each one step of
+ * every slab followed by the exchange above (pack into a per-slab message
+ * buffer the first call allocates through the context's hooks, then unpack
+ * from the neighbours' buffers), 3 launches per slab per step; P = 1 is the
+ * periodic domain itself and exchanges nothing.  All slabs must be slab
+ * contexts of the same model, storage and face layer, at the same step
+ * count, with no exchange pending (VLBM_ERR_ARG / VLBM_ERR_STATE otherwise).
+ * Asynchronous; returns slab 0's sticky health status. */
+vlbm_status vlbm_slabs_step(vlbm_ctx *const *slabs, int nslabs, int n);
 
 /* Batched contexts: number of built tile shapes, and explicit selection of
  * one (0 <= shape < vlbm_tile_shapes; VLBM_ERR_ARG otherwise).  Single-domain

@@ -22,7 +22,7 @@
  *   as lattices                                        (sec. 2.2.1, 2.3; 2-D and 3-D)
  *   local gradient evolution  dG/dt + div Phi_G = -G/tau_R          (sec. 2.2.1)
  *
- * Readings where the paper is silent (each one is listed in the design notes):
+ * Readings where the paper is silent:
  *   - lattice weights: D2Q5 w0=1/3, w=1/6, cs2=1/3;  D3Q7 w0=1/4, w=1/8,
  *     cs2=1/4;  D3Q19 1/3, 1/18, 1/36, cs2=1/3 (the paper's lattice table is
  *     not printed);
@@ -533,8 +533,8 @@ int orc_powell_run(int dim, int nx, int ny, int nz, double gamma, const double *
  * d(x) in [0, 1] (1 fluid, 0 solid), its velocity uB(x) and field BB(x).
  * The equilibrium and the fluxes use the convex blends
  *   u_hat = d u + (1 - d) uB,   B_hat = d B + (1 - d) BB
- * instead of u and B.  Reading (listed in the design notes): rho and the gas
- * pressure p are the cell's own, and the blended state is
+ * instead of u and B.  Reading (the paper does not say which state it keeps):
+ * rho and the gas pressure p are the cell's own, and the blended state is
  *   Q_hat = (rho, rho u_hat, p/(gamma-1) + rho|u_hat|^2/2 + |B_hat|^2/2, B_hat);
  * the BGK collision relaxes towards f_eq(Q_hat) (Eq. 3 with the fluxes of
  * Eq. 12 at Q_hat).  Porosity from the signed distance phi to the surface

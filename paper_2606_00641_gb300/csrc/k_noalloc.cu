@@ -35,29 +35,40 @@ template <class S> struct NaArgs {
     double ref[8], scale[8];
 };
 
+// Linear indices of the upstream cells x - c_i (periodic) that the odd parity
+// reads, i in set order; computed once per cell and shared by the eight fields.
+template <int D>
+__device__ __forceinline__ void na_upstream(int64_t cell, int x, int y, int z, int nx, int ny, int nz,
+                                            int64_t *up)
+{
+    const int64_t row = nx, plane = (int64_t)nx * ny;
+    up[0] = cell;
+    up[1] = x > 0 ? cell - 1 : cell - 1 + nx;             // x - e_x
+    up[2] = x + 1 < nx ? cell + 1 : cell + 1 - nx;        // x + e_x
+    up[3] = y > 0 ? cell - row : cell - row + plane;      // x - e_y
+    up[4] = y + 1 < ny ? cell + row : cell + row - plane;  // x + e_y
+    if (D == 3) {
+        const int64_t vol = plane * nz;
+        up[5] = z > 0 ? cell - plane : cell - plane + vol;
+        up[6] = z + 1 < nz ? cell + plane : cell + plane - vol;
+    }
+}
+
 // Q_k of one cell, with the arithmetic of vlbm_conservation: the populations
 // summed in the compute precision of the storage (FP64 only for FP64
 // storage); deviation storage widens that sum once and decodes it in FP64,
-// r_k + s_k sum_i g_ki.
+// r_k + s_k sum_i g_ki.  At odd parity direction i is in slot opp(i) of the
+// upstream cell up[i].
 template <int D, class S>
-__device__ __forceinline__ double na_moment(const NaArgs<S> &a, int64_t cell, int x, int y, int z, int k)
+__device__ __forceinline__ double na_moment(const NaArgs<S> &a, int64_t cell, const int64_t *up, int k)
 {
     using R = typename ComputeOf<S>::T;
     constexpr int Q = AxisSet<D>::Q;
     R s = R(0);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        int64_t at = cell;
-        int j = i;
-        if (a.parity && i > 0) {
-            // odd parity: direction i is in slot opp(i) of the upstream cell x - c_i
-            j = opp_axis(i);
-            const int ax = (i - 1) >> 1;
-            const int sgn = (i & 1) ? -1 : 1;  // upstream offset along ax
-            if (ax == 0) at = cell + ((x + sgn + a.nx) % a.nx - x);
-            else if (ax == 1) at = cell + (int64_t)a.nx * ((y + sgn + a.ny) % a.ny - y);
-            else at = cell + (int64_t)a.nx * a.ny * ((z + sgn + a.nz) % a.nz - z);
-        }
+        const int j = a.parity ? opp_axis(i) : i;
+        const int64_t at = a.parity ? up[i] : cell;
         s += (R)Codec<S>::load(a.pop + (int64_t)(k * Q + j) * a.stride + at);
     }
     if (Codec<S>::kDev) return fma((double)s, a.scale[k], a.ref[k]);
@@ -67,6 +78,7 @@ __device__ __forceinline__ double na_moment(const NaArgs<S> &a, int64_t cell, in
 template <int D, class S>
 __global__ void __launch_bounds__(kNaThreads) k_na_partials(const NaArgs<S> a, double *__restrict__ partials)
 {
+    constexpr int Q = AxisSet<D>::Q;
     double acc[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) acc[k] = 0.0;
@@ -78,8 +90,10 @@ __global__ void __launch_bounds__(kNaThreads) k_na_partials(const NaArgs<S> a, d
         const int64_t rest = cell / a.nx;
         const int y = (int)(rest % a.ny);
         const int z = (int)(rest / a.ny);
+        int64_t up[Q];
+        na_upstream<D>(cell, x, y, z, a.nx, a.ny, a.nz, up);
 #pragma unroll
-        for (int k = 0; k < 8; ++k) acc[k] += (double)na_moment<D, S>(a, cell, x, y, z, k);
+        for (int k = 0; k < 8; ++k) acc[k] += (double)na_moment<D, S>(a, cell, up, k);
     }
     __shared__ double red[kNaThreads / 32][8];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -118,6 +132,8 @@ __global__ void __launch_bounds__(256) k_na_finish(const double *__restrict__ pa
 
 // Device address of the scratch array on the current device, looked up once
 // per device with that device current (the host-side symbol is only a stand-in).
+// The address belongs to the device's primary context: after cudaDeviceReset
+// the module is loaded again and this cached address is stale.
 vlbm_status na_scratch(double **out)
 {
     int dev = -1;

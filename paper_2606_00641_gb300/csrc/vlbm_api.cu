@@ -469,6 +469,7 @@ static vlbm_status begin_init(vlbm_ctx *c, int domain)
     c->flag_pending = false;
     c->step = 0;
     c->steps_since_check = 0;
+    c->halo_pending = false;  // parity 0: every population is in its own slab
     return cuda_check(c, cudaMemsetAsync(c->d_flags, 0, sizeof(unsigned), c->stream), "flag clear");
 }
 
@@ -534,11 +535,41 @@ vlbm_status vlbm_init_fields_device(vlbm_ctx *c, int domain, const double *Q_dev
     return finish_init(c);
 }
 
+// After n steps were enqueued: read the health flag back asynchronously every
+// params.check_every steps.
+static void schedule_check(vlbm_ctx *c, int n)
+{
+    c->steps_since_check += n;
+    const int every = c->params.check_every;
+    if (every > 0 && c->steps_since_check >= every && !c->flag_pending) {
+        c->steps_since_check = 0;
+        if (cudaMemcpyAsync(c->h_flags, c->d_flags, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream) ==
+                cudaSuccess &&
+            cudaEventRecord(c->flag_event, c->stream) == cudaSuccess)
+            c->flag_pending = true;
+        cudaGetLastError();
+    }
+}
+
+// A slab whose last step has not had its halo exchanged holds populations that
+// belong to its neighbours: nothing may read its state yet.
+static vlbm_status slab_ready(vlbm_ctx *c)
+{
+    if (c->slab && c->halo_pending)
+        return fail(c, VLBM_ERR_STATE, "slab: the last step's halo exchange has not been unpacked");
+    return VLBM_OK;
+}
+
 vlbm_status vlbm_step(vlbm_ctx *c, int n)
 {
     if (!c || n < 0) return VLBM_ERR_ARG;
     poll_flags(c);
     if (c->sticky != VLBM_OK) return c->sticky;
+    if (c->slab) {
+        if (n > 1) return fail(c, VLBM_ERR_STATE, "slab: one step at a time, each followed by its halo exchange");
+        vlbm_status s = slab_ready(c);
+        if (s != VLBM_OK) return s;
+    }
     for (int a = 0; a < 3; ++a)
         if ((c->face_kind[2 * a] == VLBM_BC_EQUILIBRIUM) != (c->face_kind[2 * a + 1] == VLBM_BC_EQUILIBRIUM))
             return fail(c, VLBM_ERR_ARG, "one face of an axis is open and the other periodic");
@@ -562,17 +593,9 @@ vlbm_status vlbm_step(vlbm_ctx *c, int n)
         if (s != VLBM_OK) return s;
         c->step += 1;
         left -= 1;
+        if (c->slab) c->halo_pending = true;
     }
-    c->steps_since_check += n;
-    const int every = c->params.check_every;
-    if (every > 0 && c->steps_since_check >= every && !c->flag_pending) {
-        c->steps_since_check = 0;
-        if (cudaMemcpyAsync(c->h_flags, c->d_flags, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream) ==
-                cudaSuccess &&
-            cudaEventRecord(c->flag_event, c->stream) == cudaSuccess)
-            c->flag_pending = true;
-        cudaGetLastError();
-    }
+    schedule_check(c, n);
     return c->sticky;
 }
 
@@ -590,6 +613,7 @@ vlbm_status vlbm_sync(vlbm_ctx *c)
 static vlbm_status moments_to_host(vlbm_ctx *c, int domain, void *Q_host, bool f32)
 {
     if (domain < 0 || domain >= (int)c->dom.size()) return fail(c, VLBM_ERR_ARG, "bad domain index");
+    if (slab_ready(c) != VLBM_OK) return VLBM_ERR_STATE;
     const int64_t N = c->dom[domain].ncell;
     const int64_t chunk = std::min<int64_t>(N, kStageCells);
     const size_t half = (size_t)c->nvar * chunk;  // values per staging buffer
@@ -640,6 +664,7 @@ vlbm_status vlbm_moments_device(vlbm_ctx *c, int domain, double *Q_dev)
 {
     if (!c || !Q_dev) return VLBM_ERR_ARG;
     if (domain < 0 || domain >= (int)c->dom.size()) return fail(c, VLBM_ERR_ARG, "bad domain index");
+    if (slab_ready(c) != VLBM_OK) return VLBM_ERR_STATE;
     const int64_t N = c->dom[domain].ncell;
     return moments_range(c, domain, Q_dev, 0, N, N);
 }
@@ -648,6 +673,7 @@ vlbm_status vlbm_gather_populations(vlbm_ctx *c, int domain, const int64_t *cell
 {
     if (!c || !cells || !f_host || ncells < 1) return VLBM_ERR_ARG;
     if (domain < 0 || domain >= (int)c->dom.size()) return fail(c, VLBM_ERR_ARG, "bad domain index");
+    if (slab_ready(c) != VLBM_OK) return VLBM_ERR_STATE;
     const int64_t N = c->dom[domain].ncell;
     for (int t = 0; t < ncells; ++t)
         if (cells[t] < 0 || cells[t] >= N) return fail(c, VLBM_ERR_ARG, "cell index out of range");
@@ -674,6 +700,7 @@ vlbm_status vlbm_conservation(vlbm_ctx *c, int domain, double *sums)
 {
     if (!c || !sums) return VLBM_ERR_ARG;
     if (domain < 0 || domain >= (int)c->dom.size()) return fail(c, VLBM_ERR_ARG, "bad domain index");
+    if (slab_ready(c) != VLBM_OK) return VLBM_ERR_STATE;
     vlbm_status s = c->model == VLBM_RESISTIVE ? resistive_sums(c, domain, c->d_sums)
                                                : ideal_sums(c, domain, c->d_sums);
     if (s == VLBM_OK)
@@ -705,6 +732,7 @@ vlbm_status vlbm_save(vlbm_ctx *c, void *buf, size_t *bytes)
         return VLBM_OK;
     }
     if (*bytes < need) return fail(c, VLBM_ERR_ARG, "checkpoint buffer too small");
+    if (slab_ready(c) != VLBM_OK) return VLBM_ERR_STATE;
     SaveHeader h{kMagic, c->model, c->dim, c->storage, (int32_t)c->dom.size(), c->step, c->pop_bytes};
     std::memcpy(buf, &h, sizeof(h));
     vlbm_status s = cuda_check(c, cudaMemcpyAsync(static_cast<char *>(buf) + sizeof(h), c->pop, c->pop_bytes,
@@ -733,6 +761,7 @@ vlbm_status vlbm_load(vlbm_ctx *c, const void *buf, size_t bytes)
     c->step = h.step;
     c->sticky = VLBM_OK;
     c->flag_pending = false;
+    c->halo_pending = false;  // checkpoints are taken with the exchange complete
     return VLBM_OK;
 }
 
@@ -794,6 +823,7 @@ vlbm_status vlbm_set_closure(vlbm_ctx *c, vlbm_closure *cl)
             return fail(c, VLBM_ERR_ARG, "closure grid differs from the context grid");
         if (c->solid) return fail(c, VLBM_ERR_UNSUPPORTED, "a closure and homogenised solids do not combine");
         if (any_open_face(c)) return fail(c, VLBM_ERR_UNSUPPORTED, "a closure and open faces do not combine");
+        if (c->slab) return fail(c, VLBM_ERR_UNSUPPORTED, "a closure and a slab context do not combine");
     }
     drop_graphs(c);
     c->closure = cl;
@@ -824,6 +854,8 @@ vlbm_status vlbm_set_boundary(vlbm_ctx *c, int face, int kind, unsigned dirichle
             return fail(c, VLBM_ERR_UNSUPPORTED,
                         "open faces apply to single ideal-MHD contexts with F32 or F64 storage");
         if (c->closure) return fail(c, VLBM_ERR_UNSUPPORTED, "a closure and open faces do not combine");
+        if (c->slab && face / 2 == c->dim - 1)
+            return fail(c, VLBM_ERR_UNSUPPORTED, "a slab's decomposed axis joins its neighbours: it cannot be open");
         const int64_t extent[3] = {c->dom[0].nx, c->dom[0].ny, c->dom[0].nz};
         if (extent[face / 2] < 3) return fail(c, VLBM_ERR_ARG, "an open axis needs at least 3 cells");
         if ((dirichlet_mask & ~0xFFu) != 0) return fail(c, VLBM_ERR_ARG, "Dirichlet mask has bits beyond the 8 fields");
@@ -852,6 +884,109 @@ vlbm_status vlbm_check_bounded_wait(vlbm_ctx *c, int tries)
     if (!c) return VLBM_ERR_ARG;
     if (tries < 1 || tries > 65536) return fail(c, VLBM_ERR_ARG, "tries must be in 1 .. 65536");
     return wait_check(c, (uint32_t)tries);
+}
+
+vlbm_status vlbm_set_slab(vlbm_ctx *c, int on)
+{
+    if (!c) return VLBM_ERR_ARG;
+    if (!on) {
+        if (c->halo_pending) return fail(c, VLBM_ERR_STATE, "slab: unpack the last exchange first");
+        c->slab = false;
+        return VLBM_OK;
+    }
+    if (c->batched) return fail(c, VLBM_ERR_UNSUPPORTED, "batched contexts are not slabs");
+    if (c->closure) return fail(c, VLBM_ERR_UNSUPPORTED, "a closure and a slab context do not combine");
+    const int a = c->dim - 1;
+    if (c->face_kind[2 * a] == VLBM_BC_EQUILIBRIUM || c->face_kind[2 * a + 1] == VLBM_BC_EQUILIBRIUM)
+        return fail(c, VLBM_ERR_UNSUPPORTED, "a slab's decomposed axis joins its neighbours: it cannot be open");
+    if (c->step & 1) return fail(c, VLBM_ERR_STATE, "slab: mark the context at an even step count");
+    c->halo = halo_slots(c);
+    c->slab = true;
+    c->halo_pending = false;
+    return VLBM_OK;
+}
+
+size_t vlbm_halo_bytes(const vlbm_ctx *c)
+{
+    if (!c || c->batched) return 0;
+    const HaloSlots h = halo_slots(c);
+    const Domain &d = c->dom[0];
+    const int64_t layer = c->dim == 3 ? (int64_t)d.nx * d.ny : (int64_t)d.nx;
+    return (size_t)h.n * (size_t)layer * c->elem;
+}
+
+vlbm_status vlbm_halo_pack(vlbm_ctx *c, void *lo_dev, void *hi_dev)
+{
+    if (!c || !lo_dev || !hi_dev) return VLBM_ERR_ARG;
+    if (!c->slab) return fail(c, VLBM_ERR_STATE, "halo pack: not a slab context (vlbm_set_slab)");
+    return halo_copy(c, lo_dev, hi_dev, true);
+}
+
+vlbm_status vlbm_halo_unpack(vlbm_ctx *c, const void *lo_dev, const void *hi_dev)
+{
+    if (!c || !lo_dev || !hi_dev) return VLBM_ERR_ARG;
+    if (!c->slab) return fail(c, VLBM_ERR_STATE, "halo unpack: not a slab context (vlbm_set_slab)");
+    vlbm_status s = halo_copy(c, const_cast<void *>(lo_dev), const_cast<void *>(hi_dev), false);
+    if (s == VLBM_OK) c->halo_pending = false;
+    return s;
+}
+
+vlbm_status vlbm_slabs_step(vlbm_ctx *const *slabs, int nslabs, int n)
+{
+    if (!slabs || nslabs < 1 || n < 0) return fail(nullptr, VLBM_ERR_ARG, "slabs step: bad arguments");
+    vlbm_ctx *c0 = slabs[0];
+    for (int r = 0; r < nslabs; ++r) {
+        vlbm_ctx *c = slabs[r];
+        if (!c) return fail(nullptr, VLBM_ERR_ARG, "slabs step: NULL context");
+        for (int q = 0; q < r; ++q)
+            if (slabs[q] == c) return fail(nullptr, VLBM_ERR_ARG, "slabs step: a context appears twice");
+        if (!c->slab) return fail(c, VLBM_ERR_STATE, "slabs step: not a slab context (vlbm_set_slab)");
+        if (c->model != c0->model || c->dim != c0->dim || c->storage != c0->storage || c->nlat != c0->nlat ||
+            c->dom[0].nx != c0->dom[0].nx || (c->dim == 3 && c->dom[0].ny != c0->dom[0].ny))
+            return fail(nullptr, VLBM_ERR_ARG, "slabs step: the slabs' models, storage or face layers differ");
+        if (c->stream != c0->stream)
+            return fail(nullptr, VLBM_ERR_ARG, "slabs step: the slabs must share one stream");
+        if (c->step != c0->step) return fail(nullptr, VLBM_ERR_STATE, "slabs step: the slabs' step counts differ");
+        vlbm_status s = slab_ready(c);
+        if (s != VLBM_OK) return s;
+        poll_flags(c);
+        if (c->sticky != VLBM_OK) return c->sticky;
+    }
+    const size_t face = vlbm_halo_bytes(c0);
+    if (nslabs > 1)
+        for (int r = 0; r < nslabs; ++r)
+            if (!slabs[r]->halo_buf) {
+                slabs[r]->halo_buf = dev_alloc(slabs[r], 2 * face);
+                if (!slabs[r]->halo_buf) return fail(slabs[r], VLBM_ERR_OOM, "slabs step: halo buffer allocation");
+            }
+    auto lo_of = [&](int r) { return static_cast<char *>(slabs[r]->halo_buf); };
+    auto hi_of = [&](int r) { return static_cast<char *>(slabs[r]->halo_buf) + face; };
+    for (int t = 0; t < n; ++t) {
+        for (int r = 0; r < nslabs; ++r) {
+            vlbm_ctx *c = slabs[r];
+            vlbm_status s = launch_step(c, (int)(c->step & 1));
+            if (s != VLBM_OK) return s;
+            c->step += 1;
+        }
+        if (nslabs == 1) continue;  // one slab is the whole periodic domain: its wrap is the neighbour
+        for (int r = 0; r < nslabs; ++r) {
+            vlbm_status s = halo_copy(slabs[r], lo_of(r), hi_of(r), true);
+            if (s != VLBM_OK) return s;
+        }
+        // one stream: every pack is complete before the first unpack reads it
+        const bool after_even = (c0->step & 1) != 0;
+        for (int r = 0; r < nslabs; ++r) {
+            const int below = (r + nslabs - 1) % nslabs, above = (r + 1) % nslabs;
+            // after an even step a slab takes its lower neighbour's hi and its upper
+            // neighbour's lo planes; after an odd step the upper's hi and the lower's lo
+            const int hi_src = after_even ? below : above;
+            const int lo_src = after_even ? above : below;
+            vlbm_status s = halo_copy(slabs[r], lo_of(lo_src), hi_of(hi_src), false);
+            if (s != VLBM_OK) return s;
+        }
+    }
+    for (int r = 0; r < nslabs; ++r) schedule_check(slabs[r], n);
+    return c0->sticky;
 }
 
 int vlbm_tile_shapes(const vlbm_ctx *c) { return (c && c->batched) ? batch_num_choices() : 0; }

@@ -159,6 +159,16 @@ struct Domain {
     double tau_m;          // Powell model: relaxation time of D (steps)
 };
 
+// Slab decomposition: the slot planes of a slab's two faces that wrap in the
+// odd step (k_slab.cu).  lo: first layer, directions with c_a = +1; hi: last
+// layer, directions with c_a = -1 (a = z in 3-D, y in 2-D).
+constexpr int kMaxHaloSlots = 32;
+struct HaloSlots {
+    int n;                  // slots per face
+    int lo[kMaxHaloSlots];
+    int hi[kMaxHaloSlots];
+};
+
 }  // namespace vlbm
 
 struct vlbm_ctx {
@@ -214,6 +224,14 @@ struct vlbm_ctx {
     int face_kind[6] = {0, 0, 0, 0, 0, 0};  // VLBM_BC_PERIODIC or VLBM_BC_EQUILIBRIUM
     unsigned face_mask[6] = {0, 0, 0, 0, 0, 0};  // bit k: Q_k Dirichlet (else Neumann)
     double face_vals[6][8] = {};             // Dirichlet values
+
+    // slab of a decomposed domain (k_slab.cu): the face planes move between
+    // slabs after every step; halo_pending: a step ran and its exchange has
+    // not been unpacked yet
+    bool slab = false;
+    bool halo_pending = false;
+    vlbm::HaloSlots halo{};
+    void *halo_buf = nullptr;           // vlbm_slabs_step: this slab's packed lo then hi message
 
     // allocator
     std::vector<std::pair<void *, size_t>> owned;
@@ -272,6 +290,11 @@ int closure_cells(const vlbm_closure *cl, int *nx, int *ny, int *nz);
 // field v at v * stride, enqueued on the context's stream
 vlbm_status widen_fields(vlbm_ctx *c, const float *in, int nvar, int64_t n, int64_t stride, double *out);
 vlbm_status narrow_fields(vlbm_ctx *c, const double *in, int nvar, int64_t n, int64_t stride, float *out);
+
+// slab halo (k_slab.cu): the face slot list of the context's model, and one
+// launch that packs (face planes -> lo, hi messages) or unpacks (the reverse)
+HaloSlots halo_slots(const vlbm_ctx *c);
+vlbm_status halo_copy(vlbm_ctx *c, void *lo, void *hi, bool pack);
 
 // reduction of per-block partials into sums (k_ideal.cu)
 vlbm_status finish_sums(vlbm_ctx *c, int nvar, double *sums_dev);

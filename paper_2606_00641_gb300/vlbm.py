@@ -169,6 +169,11 @@ def load(build: bool = True):
         "vlbm_restrict": (i, [P, i, i, i, i, P, P]),
         "vlbm_check_bounded_wait": (i, [P, i]),
         "vlbm_conservation_noalloc": (i, [P, i, i, i, i, i, ctypes.c_int64, i, P, P, P, P]),
+        "vlbm_set_slab": (i, [P, i]),
+        "vlbm_halo_bytes": (s, [P]),
+        "vlbm_halo_pack": (i, [P, P, P]),
+        "vlbm_halo_unpack": (i, [P, P, P]),
+        "vlbm_slabs_step": (i, [ctypes.POINTER(P), i, i]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -471,6 +476,36 @@ def vlbm_conservation_noalloc(pop_ptr: int, storage, dim: int, nx: int, ny: int,
         ctypes.c_void_p(sums_ptr), ctypes.c_void_p(stream) if stream else None), "vlbm_conservation_noalloc")
 
 
+def vlbm_set_slab(ctx: int, on: bool = True) -> None:
+    """Mark (or unmark) a context as one slab of a domain decomposed along its last axis."""
+    _check(load().vlbm_set_slab(ctx, int(bool(on))), "vlbm_set_slab", ctx)
+
+
+def vlbm_halo_bytes(ctx: int) -> int:
+    """Bytes of one face message (lo or hi) of a slab."""
+    return int(load().vlbm_halo_bytes(ctx))
+
+
+def vlbm_halo_pack(ctx: int, lo_ptr: int, hi_ptr: int) -> None:
+    """Enqueue the copy of the slab's face planes into two device buffers."""
+    _check(load().vlbm_halo_pack(ctx, ctypes.c_void_p(lo_ptr), ctypes.c_void_p(hi_ptr)), "vlbm_halo_pack", ctx)
+
+
+def vlbm_halo_unpack(ctx: int, lo_ptr: int, hi_ptr: int) -> None:
+    """Enqueue the write of two received face messages into the slab's face planes."""
+    _check(load().vlbm_halo_unpack(ctx, ctypes.c_void_p(lo_ptr), ctypes.c_void_p(hi_ptr)), "vlbm_halo_unpack", ctx)
+
+
+def vlbm_slabs_step(ctx_ptrs, n: int) -> int:
+    """n steps of the slabs of one domain in this process (one device, one stream),
+    each step followed by their halo exchange; returns slab 0's health status."""
+    arr = (ctypes.c_void_p * len(ctx_ptrs))(*ctx_ptrs)
+    st = load().vlbm_slabs_step(arr, len(ctx_ptrs), int(n))
+    if st not in (VLBM_OK, VLBM_ERR_NONPHYSICAL, VLBM_ERR_TIMEOUT):
+        _check(st, "vlbm_slabs_step", ctx_ptrs[0] if st == VLBM_ERR_STATE else None)
+    return st
+
+
 def vlbm_check_bounded_wait(ctx: int, tries: int = 64) -> None:
     """Enqueue the failure-detection self-check: a bounded wait that gives up and
     raises the context's timeout flag (the next sync returns VLBM_ERR_TIMEOUT)."""
@@ -641,6 +676,20 @@ class Context:
         the array when they run), rewrites the array, and calls this again so that
         torch's writes are complete before the next step reads them."""
         vlbm_set_solid(self.ptr, solid_ptr)
+
+    def set_slab(self, on: bool = True) -> None:
+        """Mark this context as one slab of a decomposed domain (``vlbm_set_slab``)."""
+        vlbm_set_slab(self.ptr, on)
+
+    @property
+    def halo_bytes(self) -> int:
+        return vlbm_halo_bytes(self.ptr)
+
+    def halo_pack(self, lo_ptr: int, hi_ptr: int) -> None:
+        vlbm_halo_pack(self.ptr, lo_ptr, hi_ptr)
+
+    def halo_unpack(self, lo_ptr: int, hi_ptr: int) -> None:
+        vlbm_halo_unpack(self.ptr, lo_ptr, hi_ptr)
 
     def save(self) -> bytes:
         return vlbm_save(self.ptr)

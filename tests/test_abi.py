@@ -118,6 +118,11 @@ def test_validation_before_any_device_work(V):
     assert L.vlbm_init_fields_f32(None, 0, None) == V.VLBM_ERR_ARG
     assert L.vlbm_moments_f32(None, 0, None) == V.VLBM_ERR_ARG
     assert L.vlbm_check_bounded_wait(None, 64) == V.VLBM_ERR_ARG
+    assert L.vlbm_set_slab(None, 1) == V.VLBM_ERR_ARG
+    assert L.vlbm_halo_pack(None, None, None) == V.VLBM_ERR_ARG
+    assert L.vlbm_halo_unpack(None, None, None) == V.VLBM_ERR_ARG
+    assert L.vlbm_halo_bytes(None) == 0
+    assert L.vlbm_slabs_step(None, 2, 1) == V.VLBM_ERR_ARG
     assert L.vlbm_nvar(None) == 0
     L.vlbm_destroy(None)
 

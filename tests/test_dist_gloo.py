@@ -1,4 +1,5 @@
-"""Multi-rank host logic of the independent-domain runs, on CPU gloo ranks."""
+"""Multi-rank host logic on CPU gloo ranks: the independent-domain runs, and the
+halo exchange of a domain decomposed into slabs."""
 import os
 import socket
 
@@ -132,3 +133,127 @@ def test_slab_halo_exchange_reproduces_the_single_domain_bit_for_bit(world, nz):
         same, sent = out[r]
         assert same, r
         assert sent == steps * 2 * 8 * 6 * 10  # one population per lattice per face cell, each way
+
+
+# ---------------------------------------------------------------------------
+# The library's slab exchange (paper_2606_00641_gb300.slabs.SlabExchange) on
+# gloo ranks: every rank holds its slab in the AA in-place layout of the GPU
+# kernels, steps it with the kernels' addressing (emulated with the oracle's own
+# single-cell collision, periodic inside the slab), and after every step packs
+# the face planes the library packs (lo: first layer, +z slot; hi: last layer,
+# -z slot), routes them with SlabExchange and unpacks what it receives.  Each
+# slab's logical populations, read with the periodic addressing inside the slab
+# as the moments kernels read them, must equal the single-domain oracle bit for
+# bit at both parities.
+# ---------------------------------------------------------------------------
+
+_C7 = [(0, 0, 0), (1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)]  # (x, y, z)
+_OPP7 = [0, 2, 1, 4, 3, 6, 5]
+_TAU = [0.6, 0.55, 0.55, 0.55, 0.7, 0.6, 0.6, 0.6]
+
+
+def _shift(a, c):
+    """result[x] = a[x - c] over the last three axes (z, y, x), periodic."""
+    import numpy as np
+    return np.roll(a, shift=(c[2], c[1], c[0]), axis=(-3, -2, -1))
+
+
+def _aa_step(A, parity, gamma):
+    """One step of the kernels' AA addressing on A[lattice, slot, z, y, x]."""
+    import numpy as np
+
+    import oracle
+
+    def collide(F):
+        out = F.copy()
+        for z in range(F.shape[2]):
+            for y in range(F.shape[3]):
+                for x in range(F.shape[4]):
+                    out[:, :, z, y, x] = oracle.ideal_collide_cell(3, gamma, _TAU, F[:, :, z, y, x])
+        return out
+    if parity == 0:
+        return collide(A)[:, _OPP7]
+    F = np.stack([_shift(A[:, _OPP7[i]], _C7[i]) for i in range(7)], axis=1)
+    P = collide(F)
+    return np.stack([_shift(P[:, i], _C7[i]) for i in range(7)], axis=1)
+
+
+def _logical(A, parity):
+    import numpy as np
+    if parity == 0:
+        return A
+    return np.stack([_shift(A[:, _OPP7[i]], _C7[i]) for i in range(7)], axis=1)
+
+
+def _exchange_main(rank, world, port, out, shape, steps):
+    import numpy as np
+    import torch.distributed as dist
+
+    import oracle
+    from paper_2606_00641_gb300 import fields, slabs
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
+                      LOCAL_RANK=str(rank))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    f0 = fields.ideal_fields(shape, 93, mach=1.0, cfl=0.2)
+    full = oracle.ideal_init(f0.Q, f0.gamma)
+    z0, z1 = slabs.split_layers(shape[0], world)[rank]
+    state = {"A": np.ascontiguousarray(full[:, :, z0:z1])}
+    plane = shape[1] * shape[2]
+
+    def pack(lo, hi):
+        lo.numpy().view(np.float64)[:] = state["A"][:, 5, 0].ravel()
+        hi.numpy().view(np.float64)[:] = state["A"][:, 6, -1].ravel()
+
+    def unpack(lo, hi):
+        state["A"][:, 5, 0] = lo.numpy().view(np.float64).reshape(8, shape[1], shape[2])
+        state["A"][:, 6, -1] = hi.numpy().view(np.float64).reshape(8, shape[1], shape[2])
+
+    ex = slabs.SlabExchange(pack, unpack, 8 * plane * 8)
+    assert (ex.world, ex.rank) == (world, rank)
+    ref = full
+    results = []
+    for s in range(steps):
+        state["A"] = _aa_step(state["A"], s & 1, f0.gamma)
+        ex.exchange(s + 1)
+        ref = oracle.ideal_step(ref, f0.gamma, _TAU)
+        got = _logical(state["A"], (s + 1) & 1)
+        results.append(bool(np.array_equal(got, ref[:, :, z0:z1])))
+    sums = ex.allreduce_sums(oracle.ideal_moments(_logical(state["A"], steps & 1)).reshape(8, -1).sum(1))
+    ref_sums = oracle.ideal_moments(ref).reshape(8, -1).sum(1)
+    out[rank] = (results, ex.bytes_sent, float(np.abs(sums - ref_sums).max() / np.abs(ref_sums).max()))
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world,shape", [(2, (8, 4, 5)), (3, (10, 4, 5)), (2, (2, 3, 4))])
+def test_slab_exchange_routes_the_aa_halo_bit_for_bit(world, shape):
+    mgr = mp.get_context("spawn").Manager()
+    out = mgr.dict()
+    steps = 5
+    mp.start_processes(_exchange_main, args=(world, _free_port(), out, shape, steps), nprocs=world, join=True,
+                       start_method="spawn")
+    for r in range(world):
+        results, sent, sums_err = out[r]
+        assert all(results), (r, results)  # every step, both parities
+        assert sent == steps * 2 * 8 * shape[1] * shape[2] * 8  # two face messages per step
+        assert sums_err < 1e-14
+
+
+def test_route_pairs_every_send_with_the_receiving_slab():
+    from paper_2606_00641_gb300 import slabs
+    for world in (2, 3, 5):
+        for count in (1, 2):
+            for r in range(world):
+                hi_to, lo_to, hi_from, lo_from = slabs.route(r, world, count)
+                # the slab a message goes to expects it from this one
+                assert slabs.route(hi_to, world, count)[2] == r
+                assert slabs.route(lo_to, world, count)[3] == r
+            # after an even step hi goes up; after an odd step it comes back down
+            assert slabs.route(0, world, 1)[0] == 1 % world and slabs.route(0, world, 2)[0] == world - 1
+
+
+def test_split_layers_covers_the_axis():
+    from paper_2606_00641_gb300 import slabs
+    assert slabs.split_layers(10, 3) == [(0, 4), (4, 7), (7, 10)]
+    assert slabs.split_layers(4, 4) == [(0, 1), (1, 2), (2, 3), (3, 4)]
+    with pytest.raises(ValueError):
+        slabs.split_layers(3, 4)

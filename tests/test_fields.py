@@ -1,5 +1,6 @@
-"""The seeded input generators (paper_2606_00641_gb300/fields.py) against the
-recipe the design notes state: they hold none of the method's arithmetic, but
+"""The seeded input generators (paper_2606_00641_gb300/fields.py) against their
+stated recipe (random-phase cosine sums, amplitude normalisations, CFL scaling,
+B as a discrete curl): they hold none of the method's arithmetic, but
 every parity test and benchmark leg starts from them, so their promises are
 checked here -- reproducibility, the amplitude normalisations, the lattice
 scaling from the CFL reading, a discretely solenoidal field, and the same

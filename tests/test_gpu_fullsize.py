@@ -9,6 +9,14 @@
   magnetic wall equilibrium); mass stays conserved.
 * 64 batched 2-D domains: whole-domain moments of a subset against the
   oracle after several steps.
+* Both full-size workloads over many steps, through the launch configuration
+  the benchmark uses (own stream, so 32-step chunks replay a captured graph):
+  the populations of sampled cells after n steps against the oracle run on the
+  cell's light cone.  On D3Q7 a cell after n steps depends only on the cells
+  within L1 distance n, on D3Q19 within L-infinity distance n, so the oracle
+  on the periodic (2n+1) box centred on the cell (for the channel: the full
+  wall-to-wall height, the walls being part of the box) gives that cell
+  exactly.
 """
 import numpy as np
 import pytest
@@ -190,3 +198,91 @@ def test_batched_64_domains_subset(V):
                            + [np.abs(Q0[5:8]).max()] * 3)
             err = np.abs(got - ref).reshape(8, -1).max(1) / scl
             assert err.max() < 1e-5, (side, err)
+
+
+def test_ideal_512cubed_light_cones_after_40_steps(V):
+    # The benchmark's workload and launch configuration: 512^3, 8 x D3Q7, FP32,
+    # Mach 2, beta 1, own stream; 5 single steps then 35 (one captured 32-step
+    # graph and three single launches).  Eight sampled cells (corners, faces,
+    # interior) against the oracle on their periodic 81^3 light-cone boxes.
+    import torch
+    n, warm, steps = 512, 5, 35
+    total = warm + steps
+    shape = (n, n, n)
+    f0 = fields.ideal_fields(shape, 3003, mach=2.0, beta=1.0, cfl=0.2, k_rho=4, k_u=4, k_b=4,
+                             device=torch.device("cuda"))
+    Q, gamma = f0.Q, f0.gamma
+    del f0
+    scale = Q.abs().reshape(8, -1).amax(1).cpu().numpy()
+    samples = [(0, 0, 0), (n - 1, n - 1, n - 1), (n // 2, n // 2, n // 2), (7, 300, 511), (511, 0, 256),
+               (123, 456, 78), (400, 17, 3), (256, 511, 0)]
+    h = total
+    boxes = []
+    for (zc, yc, xc) in samples:
+        idx = [torch.arange(v - h, v + h + 1, device="cuda") % n for v in (zc, yc, xc)]
+        boxes.append(Q[:, idx[0]][:, :, idx[1]][:, :, :, idx[2]].cpu().numpy())
+    stream = torch.cuda.Stream()
+    p = V.make_params(shape=shape, storage="f32", gamma=gamma, tau=0.51, stream=stream.cuda_stream)
+    with V.Context(p) as ctx:
+        assert V.vlbm_init_fields_device(ctx.ptr, 0, Q.data_ptr()) == V.VLBM_OK
+        del Q
+        torch.cuda.empty_cache()
+        ctx.step(warm)
+        l0 = ctx.launches
+        ctx.step(steps)
+        assert ctx.launches - l0 == steps
+        assert ctx.sync() == V.VLBM_OK
+        got = ctx.populations([xc + n * (yc + n * zc) for (zc, yc, xc) in samples])
+    for Qb, g in zip(boxes, got):
+        fb = oracle.ideal_init(Qb, gamma)
+        for _ in range(total):
+            fb = oracle.ideal_step(fb, gamma, 0.51, nthreads=8)
+        expect = fb[:, :, h, h, h].reshape(-1)
+        tol = 1e-5 * np.repeat(scale, 7)
+        assert np.all(np.abs(g - expect) <= tol), np.abs(g - expect).reshape(8, 7).max(1) / scale
+
+
+def test_channel_full_size_light_cones_after_40_steps(V):
+    # 256 x 128 x 128 channel (walls at y = 0, 127), the benchmark's fields and
+    # launch configuration (own stream), 4 + 36 steps; sampled cells on the walls,
+    # next to them and inside, against the oracle on boxes of 81 x 128 x 81 cells
+    # (periodic in x and z, the whole height in y).
+    import torch
+    shape = (128, 128, 256)
+    nz, ny, nx = shape
+    setup = fields.hartmann_setup(shape, 2002, Ha=10.0)
+    warm, steps = 4, 36
+    total = warm + steps
+    h = total
+    stream = torch.cuda.Stream()
+    p = V.make_params(model=V.VLBM_RESISTIVE, shape=shape, storage="f32",
+                      tau=[setup.tau_f, setup.tau_m, setup.tau_m, setup.tau_m], force=setup.force,
+                      b_wall=setup.b_wall, walls_y=True, stream=stream.cuda_stream)
+    samples = [(0, 0, 0), (5, 1, 200), (127, 126, 255), (64, 64, 128), (100, 2, 7), (31, 125, 99),
+               (64, 127, 31), (10, 70, 250)]
+    with V.Context(p) as ctx:
+        Qd = torch.from_numpy(setup.Q).cuda()
+        assert V.vlbm_init_fields_device(ctx.ptr, 0, Qd.data_ptr()) == V.VLBM_OK
+        del Qd
+        ctx.step(warm)
+        ctx.step(steps)
+        assert ctx.sync() == V.VLBM_OK
+        got = ctx.populations([xc + nx * (yc + ny * zc) for (zc, yc, xc) in samples])
+    for (zc, yc, xc), g in zip(samples, got):
+        iz = (np.arange(zc - h, zc + h + 1)) % nz
+        ix = (np.arange(xc - h, xc + h + 1)) % nx
+        Qb = np.ascontiguousarray(setup.Q[:, iz][:, :, :, ix])
+        f, gm = oracle.resistive_init(Qb, setup.force)
+        for _ in range(total):
+            f, gm = oracle.resistive_step(f, gm, setup.tau_f, setup.tau_m, setup.force, setup.b_wall, True,
+                                          nthreads=8)
+        if yc in (0, ny - 1):
+            # a wall cell: its flow slots are never used, its magnetic populations are the wall equilibrium
+            expect_g = gm[:, :, h, yc, h].reshape(-1)
+            err = np.abs(g[19:] - expect_g).max() / np.abs(setup.b_wall).max()
+            assert err < 1e-5, (zc, yc, xc, err)
+            continue
+        expect = np.concatenate([f[:, h, yc, h], gm[:, :, h, yc, h].reshape(-1)])
+        scale = np.array([np.abs(f[:, h]).max()] * 19 + [max(np.abs(gm).max(), 1e-30)] * 21)
+        err = (np.abs(g - expect) / scale).max()
+        assert err < 1e-5, (zc, yc, xc, err)
