@@ -11,8 +11,11 @@ population read once and written once).
 
 Printed: one JSON line on rank 0.  ``--impl reference`` times the CPU oracle
 (plain FP64 C) on the host cores on a bounded sample of the same workload.
-Under torchrun (N > 1) every rank advances its own independent domain (no
-data exchange), so the scaling is weak.
+Under torchrun (N > 1) the ranks hold the z-slabs of one periodic domain of
+512 x 512 x (512 N) cells, one 512^3 slab per rank (the 512^3 fields repeated
+along z, so every slab's result equals the one-GPU run), and after every step
+exchange the population planes that cross the slab faces by NCCL send/recv:
+the work per GPU is fixed, so the scaling is weak.
 """
 from __future__ import annotations
 
@@ -38,6 +41,13 @@ BYTES_PER_POP = {"f64": 8, "f32": 4, "f16dev": 2, "bf16dev": 2}
 # times the cells.  Set an entry to None whenever that kernel changes until it
 # is re-captured.
 MEASURED_DRAM_BYTES_PER_CELL = {"f32": 7457219e3 / 16777216, "f16dev": 3705818e3 / 16777216}
+# FP64 operations per cell update of the FP64 step kernels (k_ideal_step<D,double>),
+# from one ncu capture of each parity: (dadd + dmul + 2 dfma thread instructions,
+# smsp__sass_thread_inst_executed_op_d{add,mul,fma}_pred_on.sum) / cells, mean of
+# the two parities.  3-D (128^3): even 90 + 42 + 2 x 152 = 436, odd 114 + 43 +
+# 2 x 152 = 461; 2-D (128^2): even 91 + 33 + 2 x 122 = 368, odd 79 + 33 + 2 x 122
+# = 356.  Set an entry to None whenever that kernel changes until it is re-captured.
+MEASURED_FP64_FLOP_PER_CELL = {2: 362.0, 3: 448.5}
 # the step kernel the roofline describes, per storage (3-D, nx % 8 == 0)
 STEP_KERNEL = {"f32": "k_ideal_step<3,float,float> (fused collide+stream)",
                "f64": "k_ideal_step<3,double,double> (fused collide+stream; FP64-pipe bound on GB300)",
@@ -57,11 +67,17 @@ def parse():
     ap.add_argument("--forms", default="f64,f16dev,bf16dev",
                     help="other storage forms to time and compare with FP64 ('' to skip)")
     ap.add_argument("--form-steps", type=int, default=20)
+    ap.add_argument("--growth-steps", type=int, default=1000,
+                    help="length of the reduced-precision error run (0 to skip)")
+    ap.add_argument("--growth-size", type=int, default=256, help="cube side of the headline error run")
+    ap.add_argument("--growth-sweep-size", type=int, default=128, help="cube side of the Mach x beta sweep")
+    ap.add_argument("--growth-taus", default="0.51,0.6,0.8",
+                    help="BGK times of the error runs (0.51 is the workload's)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the channel, batched and closure forms")
-    ap.add_argument("--extras", default="channel,batch,closure,powell,hlbm,open,diss",
+    ap.add_argument("--extras", default="channel,batch,closure,powell,hlbm,open,diss,cfg1",
                     help="which other workloads to run (comma list of channel, batch, closure, powell, "
-                         "hlbm, open, diss)")
+                         "hlbm, open, diss, cfg1)")
     ap.add_argument("--closure-fine", type=int, default=512, help="fine grid side of the closure workload")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -445,6 +461,104 @@ def batch_form(args, vlbm, fields, torch, stream, hbm_peak):
             "bytes_per_cell": 320, "roofline_frac_batched": gb * 1e9 * 320 / (hbm_peak * 1e9)}
 
 
+def ideal_2d_f64_form(args, vlbm, fields, torch, stream, fp64_tflops):
+    """2-D ideal MHD, 128^2 periodic, 8 x D2Q5, FP64, 200 steps (seed 1001, Mach 1,
+    beta 10/3, CFL 0.1, tau 0.51): 5.2 MB of populations stay in L2, and the FP64
+    step is bound by the FP64 pipe, so its roof is the measured FP64 FMA rate."""
+    n, steps = 128, 200
+    f0 = fields.ideal_fields((n, n), 1001, device=torch.device("cuda"))
+    p = vlbm.make_params(shape=(n, n), storage="f64", gamma=f0.gamma, tau=0.51, stream=stream.cuda_stream)
+    ctx = vlbm.Context(p)
+    st = vlbm.vlbm_init_fields_device(ctx.ptr, 0, f0.Q.data_ptr())
+    vlbm.vlbm_step(ctx.ptr, 64)
+    ms = min(_time_steps(vlbm, [ctx.ptr], stream, torch, steps, False) for _ in range(3))
+    status = vlbm.status_string(vlbm.vlbm_sync(ctx.ptr))
+    ctx.close()
+    gl = n * n * steps / (ms * 1e-3) / 1e9
+    flop = MEASURED_FP64_FLOP_PER_CELL.get(2)
+    out = {"grid": "128^2", "steps": steps, "init_status": vlbm.status_string(st), "status": status, "glups": gl,
+           "bytes_per_cell": 640, "kernel": "k_ideal_step<2,double,double>"}
+    if flop and fp64_tflops:
+        ach = gl * 1e9 * flop / 1e12
+        out["roofline"] = {"bound": "alu", "achieved": ach, "peak": fp64_tflops, "unit": "TFLOP/s",
+                           "frac": ach / fp64_tflops, "flop_per_cell": flop}
+    return out
+
+
+def error_growth(args, vlbm, fields, torch, stream):
+    """Reduced-precision storage over the configured run: the 3-D ideal workload
+    (k <= 4, CFL 0.2, seed 3003) advanced `growth_steps` steps in FP64, FP32,
+    FP16-deviation and BF16-deviation storage; per-field relative L-inf and L2
+    errors against the FP64 run at a ladder of step counts, and the first check
+    at which a form reports NONPHYSICAL (its health flag: NaN, rho <= 0 or
+    p <= 0).  The headline case (Mach 2, beta 1) on `growth_size`^3 and the
+    Mach {2, 3} x beta {0.1, 1, 10} sweep on `growth_sweep_size`^3, each at the
+    workload's tau 0.51 and at the larger taus of `growth_taus` (more lattice
+    diffusion, (tau - 1/2) cs^2), which keep the shocks these fields develop
+    from driving the scheme non-physical within the run."""
+    last = args.growth_steps
+    checks = [c for c in (10, 20, 50, 100, 200, 500, 1000) if c < last] + [last]
+    taus = [0.51] + [float(t) for t in args.growth_taus.split(",") if t and float(t) != 0.51]
+    cases = [(args.growth_size, 2.0, 1.0, t) for t in taus[:2]]
+    cases += [(args.growth_sweep_size, m, b, t) for t in taus for m in (2.0, 3.0) for b in (0.1, 1.0, 10.0)]
+    out = []
+    for n, mach, beta, tau in cases:
+        shape = (n, n, n)
+        f0 = fields.ideal_fields(shape, args.seed, mach=mach, beta=beta, cfl=0.2, k_rho=4, k_u=4, k_b=4,
+                                 device=torch.device("cuda"))
+        Q = f0.Q
+        flat = Q.reshape(8, -1)
+        scale = flat.abs().amax(1)
+        qref = flat.mean(1).cpu().numpy()
+        qscale = (flat - flat.mean(1, keepdim=True)).abs().amax(1).clamp_min(1e-30).cpu().numpy()
+        ref, case = {}, {"grid": "%d^3" % n, "mach": mach, "beta": beta, "tau": tau,
+                         "nonphysical_at": {}, "linf_worst": {}, "l2_worst": {}}
+        t0 = time.perf_counter()
+        for form in ("f64", "f32", "f16dev", "bf16dev"):
+            p = vlbm.make_params(shape=shape, storage=form, gamma=f0.gamma, tau=tau, q_ref=qref, q_scale=qscale,
+                                 stream=stream.cuda_stream)
+            ctx = vlbm.Context(p)
+            st = vlbm.vlbm_init_fields_device(ctx.ptr, 0, Q.data_ptr())
+            done, bad, linf, l2 = 0, None, {}, {}
+            for chk in checks:
+                if st != vlbm.VLBM_OK:
+                    bad = done
+                    break
+                vlbm.vlbm_step(ctx.ptr, chk - done)
+                done = chk
+                st = vlbm.vlbm_sync(ctx.ptr)
+                if st != vlbm.VLBM_OK:
+                    bad = chk
+                    break
+                M = torch.empty_like(Q)
+                vlbm.vlbm_moments_device(ctx.ptr, 0, M.data_ptr())
+                stream.synchronize()
+                if form == "f64":
+                    ref[chk] = M
+                elif chk in ref:
+                    d = (M - ref[chk]).reshape(8, -1)
+                    linf[chk] = (d.abs().amax(1) / scale).cpu().numpy()
+                    l2[chk] = (d.pow(2).mean(1).sqrt() / scale).cpu().numpy()
+                del M
+            ctx.close()
+            case["nonphysical_at"][form] = bad
+            if form != "f64":
+                case["linf_worst"][form] = {str(c): float(v.max()) for c, v in linf.items()}
+                case["l2_worst"][form] = {str(c): float(v.max()) for c, v in l2.items()}
+                if linf and n == args.growth_size:
+                    at = max(linf)
+                    case.setdefault("linf_per_field", {})[form] = dict(
+                        step=at, **dict(zip(fields.IDEAL_FIELDS, [float(v) for v in linf[at]])))
+        case["seconds"] = time.perf_counter() - t0
+        del ref, Q, f0
+        torch.cuda.empty_cache()
+        out.append(case)
+    return {"note": "relative to each field's max |Q| at t = 0; FP64 storage is the reference; "
+                    "nonphysical_at: the first check at which the form's health flag was raised (None: never); "
+                    "errors are listed for every check the FP64 run and the form both passed",
+            "steps": last, "checks": checks, "cases": out}
+
+
 def closure_form(args, vlbm, torch, stream):
     """Learned flux closure: coarse (fine/4)^3 + closure vs plain coarse and plain fine."""
     from paper_2606_00641_gb300 import closure
@@ -478,6 +592,69 @@ def closure_form(args, vlbm, torch, stream):
             "tensor_frac": (tflops / bf16_peak) if (tflops and bf16_peak) else None}
 
 
+def _r(v, digits=4):
+    """A number rounded to `digits` significant figures (None stays None)."""
+    if v is None:
+        return None
+    return float("%.*g" % (digits, v))
+
+
+def compact_summary(line):
+    """The figures of every form in a few hundred characters, printed as the last
+    key of the JSON line so that a reader of the output's tail sees them all:
+    [GLUPS, fraction of the HBM roof] per path, the storage forms' worst-field
+    relative L-inf against FP64 after the configured run, the closure's times
+    and errors."""
+    out = {"headline": [_r(line["value"]), _r(line["roofline"]["frac"])]}
+    forms = line.get("forms") or {}
+    for k, v in forms.items():
+        worst = max(v["rel_linf_vs_f64"].values()) if "rel_linf_vs_f64" in v else None
+        frac = v.get("roofline_frac", (v.get("roofline") or {}).get("frac"))
+        out["form_" + k] = [_r(v["glups"]), _r(frac), _r(worst, 3)]
+    g = line.get("error_growth")
+    if g:
+        # per case: the FP64 run's first non-physical check (or None), and the
+        # worst-field L-inf of each 16-bit form and FP32 at the last check both passed
+        rows, sweep = {}, {}
+        for c in g["cases"]:
+            last = {f: (max(v, key=int) if v else None) for f, v in c["linf_worst"].items()}
+            row = [c["nonphysical_at"].get("f64")] + [
+                [int(last[f]), _r(c["linf_worst"][f][last[f]], 2)] if last.get(f) else None
+                for f in ("f32", "f16dev", "bf16dev")]
+            if c["grid"] == g["cases"][0]["grid"]:
+                rows["%s M%g b%g t%g" % (c["grid"], c["mach"], c["beta"], c["tau"])] = row
+            else:  # the Mach x beta sweep, per tau: FP64's non-physical checks, worst 16-bit error
+                sw = sweep.setdefault("%s t%g" % (c["grid"], c["tau"]), {"f64bad": [], "bf16_linf_last": 0.0})
+                sw["f64bad"].append(row[0])
+                if row[3]:
+                    sw["bf16_linf_last"] = max(sw["bf16_linf_last"], row[3][1])
+        out["growth_[f64bad,f32,f16,bf16:[step,linf]]"] = rows
+        out["growth_sweep_M2,3xb.1,1,10"] = sweep
+    names = {"resistive_channel": "channel", "powell_3d": "powell", "hlbm_sphere_3d": "hlbm",
+             "open_faces_3d": "open", "dissipative_2d": "diss"}
+    extra = line.get("other_paths") or {}
+    for k, short in names.items():
+        if k in extra:
+            out[short] = [_r(extra[k]["glups"]), _r(extra[k]["roofline_frac"])]
+    if "batched_2d" in extra:
+        b = extra["batched_2d"]
+        out["batched"] = [_r(b["glups_batched"]), _r(b["roofline_frac_batched"]), _r(b["speedup"])]
+    if "ideal_2d_128sq_f64" in extra:
+        c = extra["ideal_2d_128sq_f64"]
+        out["cfg1_f64"] = [_r(c["glups"]), _r((c.get("roofline") or {}).get("frac"))]
+    if "learned_closure" in extra:
+        c = extra["learned_closure"]
+        t = c["time_to_solution_ms"]
+        out["closure_ms_fine_closure_plain"] = [_r(t["fine"]), _r(t["coarse_closure"]), _r(t["coarse_plain"])]
+        te = c["test"]
+        out["closure_relL2_closure_plain"] = [_r(te.get("rel_l2_closure_coarse"), 3),
+                                              _r(te.get("rel_l2_plain_coarse"), 3)]
+        out["closure_tensor_frac"] = _r(c.get("tensor_frac"), 3)
+    if line.get("fp64_tflops"):
+        out["fp64_tflops"] = _r(line["fp64_tflops"])
+    return out
+
+
 def main():
     args = parse()
     world, rank, local = dist_env()
@@ -488,7 +665,7 @@ def main():
     import torch
 
     from paper_2606_00641_gb300 import dist as vdist
-    from paper_2606_00641_gb300 import fields, vlbm
+    from paper_2606_00641_gb300 import fields, slabs, vlbm
 
     assert torch.cuda.is_available(), "bench.py needs a CUDA device"
     torch.cuda.set_device(local)
@@ -508,8 +685,9 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    # seeded fields on the device (rank-specific seed: independent domains)
-    seed = args.seed + rank
+    # seeded fields on the device; every rank holds the same 512^3 fields, so the
+    # decomposed domain is the 512^3 periodic solution repeated along z
+    seed = args.seed
     f0 = fields.ideal_fields(shape, seed, mach=2.0, beta=1.0, cfl=0.2, k_rho=4, k_u=4, k_b=4,
                              device="cuda:%d" % local)
     Q = f0.Q
@@ -529,24 +707,44 @@ def main():
         assert st == vlbm.VLBM_OK, vlbm.status_string(st)
         return ctx
 
-    def timed(ctx, steps, warmup):
-        vlbm.vlbm_step(ctx.ptr, warmup)
-        barrier()
+    exchanges = {}
+
+    def advance(c, n):
+        """n steps of context c; a slab of the decomposed domain exchanges its
+        face planes with the neighbouring ranks after every step, ordered on the
+        context's stream (pack, NCCL send/recv, unpack)."""
+        ex = exchanges.get(c.ptr)
+        if ex is None:
+            vlbm.vlbm_step(c.ptr, n)
+            return
+        with torch.cuda.stream(stream):
+            for _ in range(n):
+                vlbm.vlbm_step(c.ptr, 1)
+                ex.exchange(c.step_count)
+
+    def timed(ctx, steps, warmup, collective=True):
+        """CUDA-event time of `steps` steps on the context's stream; `collective`:
+        every rank takes part (barriers on both sides), else this rank alone."""
+        sync = barrier if collective else torch.cuda.synchronize
+        advance(ctx, warmup)
+        sync()
         stream.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         l0 = ctx.launches
         e0.record(stream)
-        vlbm.vlbm_step(ctx.ptr, steps)
+        advance(ctx, steps)
         e1.record(stream)
         e1.synchronize()
         ms = e0.elapsed_time(e1)
-        barrier()
+        sync()
         return ms, ctx.launches - l0
 
     # ---- main form: timed region with clock sampling ----
     ctx = make_ctx(args.storage)
-    vlbm.vlbm_step(ctx.ptr, args.warmup)
+    if world > 1:
+        exchanges[ctx.ptr] = slabs.SlabExchange.for_context(ctx, device="cuda:%d" % local)
+    advance(ctx, args.warmup)
     stream.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
@@ -569,6 +767,21 @@ def main():
                "glups_std": statistics.stdev(rep_glups) if len(rep_glups) > 1 else 0.0,
                "glups_min": min(rep_glups), "glups_max": max(rep_glups)} if rep_glups else None)
 
+    # the decomposed domain: every slab holds the same 512^3 solution, so every
+    # rank's domain sums must equal rank 0's; the global sums are their all-reduce
+    slab_check = None
+    if world > 1:
+        mine = torch.tensor(ctx.conservation(), dtype=torch.float64, device="cuda")
+        every = [torch.empty_like(mine) for _ in range(world)]
+        dist.all_gather(every, mine)
+        first = every[0].abs().clamp_min(1e-300)
+        spread_rel = max(float(((e - every[0]).abs() / first).max()) for e in every)
+        total = exchanges[ctx.ptr].allreduce_sums(mine.cpu().numpy(), device="cuda")
+        slab_check = {"ranks": world, "max_rel_diff_of_slab_sums_vs_rank0": spread_rel,
+                      "global_mass": float(total[0]),
+                      "halo_bytes_per_face": exchanges[ctx.ptr].nbytes,
+                      "halo_bytes_sent_per_rank": exchanges[ctx.ptr].bytes_sent}
+
     # ---- end to end through the C ABI with pinned host buffers ----
     def end_to_end(host_dtype):
         """Host fields in `host_dtype` (pinned) -> init, steps with a health read-back each, moments back."""
@@ -577,6 +790,14 @@ def main():
         hostQ.copy_(Q)
         hostOut = torch.empty(Q.shape, dtype=host_dtype, pin_memory=True)
         hostOut.zero_()  # a reused output buffer: its pages are resident, as after any earlier call
+        # one untimed round trip: the host-field calls allocate their staging chunks
+        # and copy stream on first use (once per context)
+        if f32:
+            vlbm.vlbm_init_fields_f32_ptr(ctx.ptr, 0, hostQ.data_ptr())
+            vlbm.vlbm_moments_f32_ptr(ctx.ptr, 0, hostOut.data_ptr())
+        else:
+            vlbm.vlbm_init_fields_ptr(ctx.ptr, 0, hostQ.data_ptr())
+            vlbm.vlbm_moments_ptr(ctx.ptr, 0, hostOut.data_ptr())
         barrier()
         t0 = time.perf_counter()
         if f32:
@@ -585,7 +806,7 @@ def main():
             vlbm.vlbm_init_fields_ptr(ctx.ptr, 0, hostQ.data_ptr())
         t1 = time.perf_counter()
         for _ in range(args.steps):
-            vlbm.vlbm_step(ctx.ptr, 1)
+            advance(ctx, 1)
             vlbm.vlbm_sync(ctx.ptr)  # 4-byte health word read back every step
         t2 = time.perf_counter()
         if f32:
@@ -619,6 +840,14 @@ def main():
             e2e["f64_fields"] = end_to_end(torch.float64)
     ctx.close()
 
+    # FP64 FMA rate of this GPU's CUDA cores: the roof of the FP64 forms
+    fp64_tflops = None
+    if rank == 0:
+        try:
+            fp64_tflops = vlbm.vlbm_measure_fp64_rate(4096, stream.cuda_stream)
+        except vlbm.VlbmError:
+            fp64_tflops = None
+
     # ---- other storage forms: GLUPS and per-field error against FP64 ----
     forms = {}
     form_list = [s for s in args.forms.split(",") if s] if rank == 0 else []
@@ -632,15 +861,21 @@ def main():
             return out
 
         ref = make_ctx("f64")
-        ms64, _ = timed(ref, nfs, 0)
+        ms64, _ = timed(ref, nfs, 0, collective=False)
         Q64 = moments_dev(ref)
         ref.close()
         forms["f64"] = {"glups": ncell * nfs / (ms64 * 1e-3) / 1e9, "steps": nfs,
-                        "bytes_per_cell": 2 * 56 * 8}
+                        "bytes_per_cell": 2 * 56 * 8,
+                        "roofline_frac_hbm": ncell * nfs / (ms64 * 1e-3) * 2 * 56 * 8 / (hbm_peak * 1e9)}
+        flop3 = MEASURED_FP64_FLOP_PER_CELL.get(3)
+        if flop3 and fp64_tflops:
+            ach = forms["f64"]["glups"] * 1e9 * flop3 / 1e12
+            forms["f64"]["roofline"] = {"bound": "alu", "achieved": ach, "peak": fp64_tflops, "unit": "TFLOP/s",
+                                        "frac": ach / fp64_tflops, "flop_per_cell": flop3}
         scale = Q.reshape(8, -1).abs().amax(1)
         for form in ["f32"] + [f for f in form_list if f not in ("f64", "f32")]:
             c = make_ctx(form)
-            msf, _ = timed(c, nfs, 0)
+            msf, _ = timed(c, nfs, 0, collective=False)
             Qf = moments_dev(c)
             st = vlbm.vlbm_sync(c.ptr)
             c.close()
@@ -655,6 +890,10 @@ def main():
                            "rel_linf_vs_f64": dict(zip(fields.IDEAL_FIELDS, [float(v) for v in linf])),
                            "rel_l2_vs_f64": dict(zip(fields.IDEAL_FIELDS, [float(v) for v in l2]))}
         del Q64
+
+    growth = None
+    if rank == 0 and args.growth_steps > 0 and form_list:
+        growth = error_growth(args, vlbm, fields, torch, stream)
 
     extra = {}
     if rank == 0 and not args.no_extra:
@@ -673,6 +912,8 @@ def main():
             extra["open_faces_3d"] = open_form(args, vlbm, fields, torch, stream, hbm_peak)
         if "diss" in which:
             extra["dissipative_2d"] = dissipative_form(args, vlbm, fields, torch, stream, hbm_peak)
+        if "cfg1" in which:
+            extra["ideal_2d_128sq_f64"] = ideal_2d_f64_form(args, vlbm, fields, torch, stream, fp64_tflops)
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -685,8 +926,13 @@ def main():
             "metric": "GLUPS", "value": glups, "unit": "GLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
-            "config": {"workload": WORKLOAD, "grid": "%d^3" % n, "cells": ncell, "storage": args.storage,
-                       "populations_per_cell": 56, "parallelism": "independent domain per rank",
+            "config": {"workload": WORKLOAD, "grid": ("%d^3" % n) if world == 1 else
+                       "%d x %d x %d periodic, one %d^3 z-slab per rank" % (n, n, n * world, n),
+                       "cells": ncell * world, "storage": args.storage,
+                       "populations_per_cell": 56,
+                       "parallelism": "single domain" if world == 1 else
+                       "slab decomposition along z, population halo exchanged by NCCL send/recv after "
+                       "every step (one slot plane per lattice per face each way)",
                        "l2": "inputs_larger_than_l2 (%.1f GB of populations per rank)"
                              % (ncell * 56 * BYTES_PER_POP[args.storage] / 1e9)},
             "status": vlbm.status_string(status),
@@ -700,13 +946,17 @@ def main():
             "clocks": clk,
             "repeats": spread,
             "gpu_launches": launches,
+            "slab_check": slab_check,
             "e2e": e2e,
             "cpu_baseline": cpu,
             "forms": forms or None,
+            "error_growth": growth,
             "other_paths": extra or None,
             "paper_context": {"note": "RTX A5000, FP32, 2-D D2Q5 kernel 98.9% and 3-D homogenised D3Q7 "
                                       "kernel 75.8% of a 680 GB/s measured roofline; other hardware"},
+            "fp64_tflops": fp64_tflops,
         }
+        line["summary"] = compact_summary(line)
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -418,7 +418,10 @@ vlbm_status vlbm_restrict(const double *Qf_dev, int nx, int ny, int nz, int fact
  * message (its last layer, every slot whose direction has c_a = -1).  Slots per
  * face: one per lattice for D2Q5/D3Q7 models (8 ideal, 9 Powell, 20
  * dissipative), 5 + 3 for the resistive model (the D3Q19 directions with
- * c_z = +-1 and the magnetic lattices' +-z slots).  Every element moves
+ * c_z = +-1 and the magnetic lattices' +-z slots; with walls, the rows next to
+ * the walls keep their halfway bounce-back entries -- slots 15 and 17 at y = 1,
+ * 16 and 18 at y = ny-2 -- out of the exchange, since they belong to their own
+ * cell, and those message entries are left unwritten).  Every element moves
  * unchanged, so P slabs equal the single domain bit for bit.
  *
  * Routing after a step that leaves the slab's step count ODD (an even step
@@ -487,6 +490,16 @@ vlbm_status vlbm_set_tile_shape(vlbm_ctx *ctx, int shape);
  * vlbm_init_fields or vlbm_load succeeds, as after a real give-up.  Nothing
  * faults, traps or hangs; the kernel ends within about tries x 20 us. */
 vlbm_status vlbm_check_bounded_wait(vlbm_ctx *ctx, int tries);
+
+/* FP64 fused multiply-add rate of the current device's CUDA cores, in TFLOP/s
+ * (2 flops per FMA), for placing the FP64 forms on their arithmetic roofline
+ * (no counterpart in the paper: the FP64 pipe of a GB300 runs far below its
+ * FP32 rate, and the FP64 step is bound by it).  One kernel of independent FMA
+ * chains, `iters` FMAs per chain (1 .. 2^20; 4096 takes a few ms), timed with
+ * CUDA events on `stream` (cudaStream_t or NULL); best of three timed launches
+ * after one warm-up.  Synchronises that stream.  VLBM_ERR_ARG for bad
+ * arguments, VLBM_ERR_CUDA if a launch fails. */
+vlbm_status vlbm_measure_fp64_rate(int iters, void *stream, double *tflops);
 
 /* Small queries. */
 int vlbm_nvar(const vlbm_ctx *ctx);                  /* 8 ideal, 7 resistive, 9 Powell, 20 dissipative */

@@ -65,22 +65,32 @@ def conv3d_bwd_weight(gy, x):
     return gW, gy.reshape(gy.shape[0], -1).sum(1)
 
 
-def net_forward(p, x):
+def _exact(a):
+    return a
+
+
+def net_forward(p, x, store=_exact):
+    """The network on features x.  `store` is applied to each hidden activation
+    as it is kept for the next layer (default: exact FP64).  A network whose
+    activations are held in a narrower type between layers is stated by passing
+    that type's rounding; every sum stays FP64."""
     z1 = conv3d(x, p["W1"], p["b1"])
-    a1 = np.tanh(z1)
+    a1 = store(np.tanh(z1))
     z2 = conv3d(a1, p["W2"], p["b2"])
-    a2 = np.tanh(z2)
+    a2 = store(np.tanh(z2))
     y = conv3d(a2, p["W3"], p["b3"])
     return y, {"x": x, "a1": a1, "a2": a2}
 
 
-def net_backward(p, cache, gy):
-    """Gradients of sum(gy * y) with respect to every weight and bias."""
+def net_backward(p, cache, gy, store=_exact):
+    """Gradients of sum(gy * y) with respect to every weight and bias; `store`
+    is applied to each hidden-layer gradient as it is kept for the next layer
+    down (as in net_forward)."""
     g = {}
     g["W3"], g["b3"] = conv3d_bwd_weight(gy, cache["a2"])
-    gz2 = conv3d_bwd_data(gy, p["W3"]) * (1.0 - cache["a2"] ** 2)
+    gz2 = store(conv3d_bwd_data(gy, p["W3"]) * (1.0 - cache["a2"] ** 2))
     g["W2"], g["b2"] = conv3d_bwd_weight(gz2, cache["a1"])
-    gz1 = conv3d_bwd_data(gz2, p["W2"]) * (1.0 - cache["a1"] ** 2)
+    gz1 = store(conv3d_bwd_data(gz2, p["W2"]) * (1.0 - cache["a1"] ** 2))
     g["W1"], g["b1"] = conv3d_bwd_weight(gz1, cache["x"])
     return g
 

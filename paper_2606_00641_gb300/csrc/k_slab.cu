@@ -29,7 +29,7 @@ namespace vlbm {
 namespace {
 
 template <class E>
-__global__ void k_halo_copy(E *__restrict__ pop, int64_t stride, int64_t layer, int64_t hi_first,
+__global__ void k_halo_copy(E *__restrict__ pop, int64_t stride, int64_t layer, int64_t hi_first, int nx,
                             const __grid_constant__ HaloSlots hs, E *__restrict__ lo, E *__restrict__ hi,
                             int pack)
 {
@@ -37,6 +37,8 @@ __global__ void k_halo_copy(E *__restrict__ pop, int64_t stride, int64_t layer, 
     if (t >= layer) return;
     const int s = blockIdx.y;
     const bool high = blockIdx.z != 0;
+    const int keep = high ? hs.hi_keep[s] : hs.lo_keep[s];
+    if (keep >= 0 && t / nx == keep) return;  // a wall-adjacent row's own bounce-back slot
     const int slot = high ? hs.hi[s] : hs.lo[s];
     E *plane = pop + (int64_t)slot * stride + (high ? hi_first : 0);
     E *msg = (high ? hi : lo) + (int64_t)s * layer;
@@ -52,7 +54,7 @@ template <class E> vlbm_status launch(vlbm_ctx *c, void *lo, void *hi, bool pack
     const int threads = 256;
     const dim3 grid((unsigned)((layer + threads - 1) / threads), (unsigned)c->halo.n, 2u);
     k_halo_copy<E><<<grid, threads, 0, c->stream>>>(static_cast<E *>(c->pop), d.stride, layer,
-                                                    (nlayers - 1) * layer, c->halo, static_cast<E *>(lo),
+                                                    (nlayers - 1) * layer, d.nx, c->halo, static_cast<E *>(lo),
                                                     static_cast<E *>(hi), pack ? 1 : 0);
     c->launches++;
     return cuda_check(c, cudaGetLastError(), pack ? "halo pack launch" : "halo unpack launch");
@@ -63,6 +65,7 @@ template <class E> vlbm_status launch(vlbm_ctx *c, void *lo, void *hi, bool pack
 HaloSlots halo_slots(const vlbm_ctx *c)
 {
     HaloSlots h{};
+    for (int s = 0; s < kMaxHaloSlots; ++s) h.lo_keep[s] = h.hi_keep[s] = -1;
     if (c->model == VLBM_RESISTIVE) {
         // D3Q19 directions with c_z = +1 and -1 (ABI order), then the magnetic
         // lattices' +z / -z slots
@@ -70,6 +73,18 @@ HaloSlots halo_slots(const vlbm_ctx *c)
         for (int s = 0; s < 5; ++s) {
             h.lo[s] = up[s];
             h.hi[s] = dn[s];
+        }
+        if (c->dom[0].walls_y) {
+            // Halfway bounce-back in AA form keeps, in the row next to each wall, the
+            // cell's own populations in the slots of the directions that point into
+            // and out of the wall (y = 1: 15 (0,1,1) and 17 (0,1,-1); y = ny-2: 16
+            // (0,-1,-1) and 18 (0,-1,1)); nothing streams into those entries from
+            // another cell (the source would be the wall row), so they stay put.
+            const int ny = c->dom[0].ny;
+            h.lo_keep[3] = 1;       // lo[3] = 15
+            h.lo_keep[4] = ny - 2;  // lo[4] = 18
+            h.hi_keep[3] = ny - 2;  // hi[3] = 16
+            h.hi_keep[4] = 1;       // hi[4] = 17
         }
         for (int b = 0; b < 3; ++b) {
             h.lo[5 + b] = 19 + 7 * b + 5;

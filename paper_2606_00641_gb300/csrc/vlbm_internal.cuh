@@ -162,11 +162,16 @@ struct Domain {
 // Slab decomposition: the slot planes of a slab's two faces that wrap in the
 // odd step (k_slab.cu).  lo: first layer, directions with c_a = +1; hi: last
 // layer, directions with c_a = -1 (a = z in 3-D, y in 2-D).
+// A slot may keep one row of the face layer out of the exchange (-1: none):
+// with walls, the rows next to a wall hold the halfway bounce-back of their own
+// cell in some c_a != 0 slots, which never stream across a face.
 constexpr int kMaxHaloSlots = 32;
 struct HaloSlots {
     int n;                  // slots per face
     int lo[kMaxHaloSlots];
     int hi[kMaxHaloSlots];
+    int lo_keep[kMaxHaloSlots];  // row y of the face layer that stays (3-D), or -1
+    int hi_keep[kMaxHaloSlots];
 };
 
 }  // namespace vlbm

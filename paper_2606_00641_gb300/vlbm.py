@@ -174,6 +174,7 @@ def load(build: bool = True):
         "vlbm_halo_pack": (i, [P, P, P]),
         "vlbm_halo_unpack": (i, [P, P, P]),
         "vlbm_slabs_step": (i, [ctypes.POINTER(P), i, i]),
+        "vlbm_measure_fp64_rate": (i, [i, P, ctypes.POINTER(d)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -504,6 +505,14 @@ def vlbm_slabs_step(ctx_ptrs, n: int) -> int:
     if st not in (VLBM_OK, VLBM_ERR_NONPHYSICAL, VLBM_ERR_TIMEOUT):
         _check(st, "vlbm_slabs_step", ctx_ptrs[0] if st == VLBM_ERR_STATE else None)
     return st
+
+
+def vlbm_measure_fp64_rate(iters: int = 4096, stream: int = 0) -> float:
+    """FP64 FMA throughput of the current device's CUDA cores, TFLOP/s."""
+    out = ctypes.c_double(0.0)
+    _check(load().vlbm_measure_fp64_rate(int(iters), ctypes.c_void_p(stream) if stream else None,
+                                         ctypes.byref(out)), "vlbm_measure_fp64_rate")
+    return out.value
 
 
 def vlbm_check_bounded_wait(ctx: int, tries: int = 64) -> None:

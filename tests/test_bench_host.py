@@ -34,3 +34,41 @@ def test_clock_summary_reports_thermal_and_hardware_slowdown():
 def test_clock_summary_of_nothing():
     out = bench.summarise_clocks([])
     assert out == {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+
+
+def _fake_line():
+    form = {"glups": 27.0, "roofline_frac": 0.9, "rel_linf_vs_f64": {"rho": 1e-3, "E": 2e-3}}
+    case = lambda grid, tau, bad: {  # noqa: E731
+        "grid": grid, "mach": 2.0, "beta": 1.0, "tau": tau,
+        "nonphysical_at": {"f64": bad, "f32": bad, "f16dev": bad, "bf16dev": bad},
+        "linf_worst": {f: ({"10": 1e-3, "100": 2e-3} if bad != 10 else {}) for f in ("f32", "f16dev", "bf16dev")},
+        "l2_worst": {}}
+    return {
+        "value": 15.2, "roofline": {"frac": 1.01},
+        "forms": {"f64": {"glups": 1.86, "roofline": {"frac": 0.79}}, "f16dev": form},
+        "error_growth": {"steps": 1000, "cases": [case("256^3", 0.51, 1000), case("256^3", 0.6, None),
+                                                  case("128^3", 0.51, 10), case("128^3", 0.6, None)]},
+        "other_paths": {"resistive_channel": {"glups": 20.5, "roofline_frac": 0.98},
+                        "batched_2d": {"glups_batched": 20.4, "roofline_frac_batched": 0.97, "speedup": 1.27},
+                        "ideal_2d_128sq_f64": {"glups": 1.5},
+                        "learned_closure": {"time_to_solution_ms": {"fine": 1128.0, "coarse_closure": 20.6,
+                                                                    "coarse_plain": 5.9},
+                                            "test": {"rel_l2_closure_coarse": 0.00235, "rel_l2_plain_coarse": 0.00254},
+                                            "tensor_frac": 0.26}},
+        "fp64_tflops": 1.057,
+    }
+
+
+def test_compact_summary_keeps_every_path_in_a_short_tail():
+    import json
+    out = bench.compact_summary(_fake_line())
+    text = json.dumps(out)
+    assert len(text) < 1400, len(text)
+    assert out["headline"] == [15.2, 1.01]
+    assert out["form_f64"] == [1.86, 0.79, None] and out["form_f16dev"] == [27.0, 0.9, 0.002]
+    rows = out["growth_[f64bad,f32,f16,bf16:[step,linf]]"]
+    assert rows["256^3 M2 b1 t0.51"] == [1000, [100, 0.002], [100, 0.002], [100, 0.002]]
+    sweep = out["growth_sweep_M2,3xb.1,1,10"]
+    assert sweep["128^3 t0.51"] == {"f64bad": [10], "bf16_linf_last": 0.0}
+    assert out["batched"] == [20.4, 0.97, 1.27] and out["cfg1_f64"] == [1.5, None]
+    assert out["closure_relL2_closure_plain"] == [0.00235, 0.00254]

@@ -1,10 +1,14 @@
 """Learned flux closure on the GPU against the FP64 reference.
 
-Tolerances: BF16 weights and activations with FP32 accumulation -- network
-outputs and parameter gradients within 3e-2 of the largest magnitude of the
-FP64 reference evaluated with the same BF16-rounded weights and inputs; the
-corrected lattice Boltzmann step (FP32 storage) within 1e-5 like every FP32
-step.
+The kernels' type contract, which the reference is evaluated under: BF16
+weights and input features; hidden activations (a1, a2) and hidden-layer
+gradients (gz2, gz1) kept in BF16 between layers; every sum accumulated in
+FP32 (the reference: FP64).  The reference takes the same BF16-rounded
+weights, features and output gradient, and rounds its hidden activations and
+gradients to BF16 where the kernels store them (``store=bf16_round``).
+Tolerances: network outputs and parameter gradients within 1e-2 of the
+largest magnitude of that reference; the corrected lattice Boltzmann step
+(FP32 storage) within 1e-5 like every FP32 step.
 """
 import numpy as np
 import pytest
@@ -79,11 +83,11 @@ def test_closure_forward_matches_reference(V, shape):
     cl.forward(Qd.data_ptr(), dphi.data_ptr())
     got = dphi.cpu().numpy().T.reshape((24,) + shape)
     x = bf16_round(C.features(f0.Q, mu, sigma))
-    y, _ = C.net_forward(pw, x)
+    y, _ = C.net_forward(pw, x, store=bf16_round)
     ref = C.dphi_from_output(y, out_scale).reshape((24,) + shape)
     for k in range(8):
         g, r = got[3 * k:3 * k + 3], ref[3 * k:3 * k + 3]
-        assert np.abs(g - r).max() < 3e-2 * np.abs(r).max(), k
+        assert np.abs(g - r).max() < 1e-2 * np.abs(r).max(), (k, np.abs(g - r).max() / np.abs(r).max())
     cl.close()
 
 
@@ -96,10 +100,11 @@ def test_closure_backward_matches_reference(V, shape):
     gy = rng.normal(size=(N, 24)).astype(np.float32)
     got = unflat(cl.backward(Qd.data_ptr(), torch.from_numpy(gy).cuda().data_ptr()))
     x = bf16_round(C.features(f0.Q, mu, sigma))
-    y, cache = C.net_forward(pw, x)
-    ref = C.net_backward(pw, cache, bf16_round(gy).T.reshape((24,) + shape))
+    y, cache = C.net_forward(pw, x, store=bf16_round)
+    ref = C.net_backward(pw, cache, bf16_round(gy).T.reshape((24,) + shape), store=bf16_round)
     for name in ("W1", "b1", "W2", "b2", "W3", "b3"):
-        assert np.abs(got[name] - ref[name]).max() < 3e-2 * np.abs(ref[name]).max(), name
+        err = np.abs(got[name] - ref[name]).max() / np.abs(ref[name]).max()
+        assert err < 1e-2, (name, err)
     cl.close()
 
 

@@ -120,3 +120,28 @@ def test_loss_gradient_through_the_corrected_step(orc):
         d[k, a, z, y, x] = h
         fd = (loss(dphi + d)[0] - loss(dphi - d)[0]) / (2 * h)
         assert abs(fd - g[k, a, z, y, x]) < 1e-5 * max(abs(fd), 1e-8) + 1e-12
+
+
+def test_storage_rounding_applies_where_the_hidden_values_are_kept():
+    # store = identity is the exact network; a store that keeps nothing (zero)
+    # leaves y = b3 and no gradient below the last layer, so the hook sits on a1,
+    # a2 (forward) and on the hidden-layer gradients (backward); a rounding store
+    # shows up in the cached activations exactly
+    rng = np.random.default_rng(8)
+    p = C.init_params(rng, hidden=4, last_scale=1.0)
+    for k in ("b1", "b2", "b3"):
+        p[k] = rng.normal(size=p[k].shape)
+    x = rng.normal(size=(8, 3, 4, 5))
+    gy = rng.normal(size=(24, 3, 4, 5))
+    y0, c0 = C.net_forward(p, x)
+    y1, c1 = C.net_forward(p, x, store=lambda a: a)
+    assert np.array_equal(y0, y1)
+    yz, cz = C.net_forward(p, x, store=np.zeros_like)
+    assert np.allclose(yz, p["b3"][:, None, None, None] + 0 * yz)
+    g = C.net_backward(p, cz, gy, store=np.zeros_like)
+    for name in ("W1", "b1", "W2", "b2", "W3"):
+        assert not np.any(g[name]), name
+    assert np.allclose(g["b3"], gy.reshape(24, -1).sum(1))
+    yr, cr = C.net_forward(p, x, store=lambda a: np.round(a, 2))
+    assert np.array_equal(cr["a1"], np.round(np.tanh(C.conv3d(x, p["W1"], p["b1"])), 2))
+    assert np.array_equal(cr["a2"], np.round(np.tanh(C.conv3d(cr["a1"], p["W2"], p["b2"])), 2))
