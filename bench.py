@@ -75,10 +75,16 @@ def parse():
                     help="BGK times of the error runs (0.51 is the workload's)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the channel, batched and closure forms")
-    ap.add_argument("--extras", default="channel,batch,closure,powell,hlbm,open,diss,cfg1",
+    ap.add_argument("--extras", default="channel,batch,closure,powell,hlbm,open,diss,diss3,cfg1",
                     help="which other workloads to run (comma list of channel, batch, closure, powell, "
-                         "hlbm, open, diss, cfg1)")
+                         "hlbm, open, diss, diss3, cfg1)")
     ap.add_argument("--closure-fine", type=int, default=512, help="fine grid side of the closure workload")
+    ap.add_argument("--closure-steps", type=int, default=250, help="coarse steps of the closure's test runs")
+    ap.add_argument("--closure-mach", default="1,1.25",
+                    help="range of the seeds' peak Mach (lo,hi); at tau 0.51 some seeds' fields turn "
+                         "non-physical within 1000 fine steps from about Mach 1.4 on")
+    ap.add_argument("--closure-train-seeds", type=int, default=16, help="training seeds from 5000 on")
+    ap.add_argument("--diss3-size", type=int, default=256, help="cube side of the 3-D dissipative leg")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--seed", type=int, default=3003)
@@ -315,6 +321,32 @@ def dissipative_form(args, vlbm, fields, torch, stream, hbm_peak):
                         "(nu = eta0 = %.3g, j_c = %.3g, tau_M = %.1f steps, tau = %.5f), Powell source on"
                         % (n, setup.nu, setup.j_c, setup.tau_m, setup.tau),
             "kernel": "k_diss_step<float> (fused collide+stream, 100 populations per cell)",
+            "init_status": vlbm.status_string(st), "status": status, "glups": gl, "steps": steps,
+            "bytes_per_cell": bytes_cell, "roofline_frac": gl * 1e9 * bytes_cell / (hbm_peak * 1e9)}
+
+
+def dissipative3_form(args, vlbm, fields, torch, stream, hbm_peak):
+    """Dissipative MHD with evolved gradients in 3-D (26 D3Q7 lattices, FP32): the
+    3-D low-Mach resistive vortex at 256^3."""
+    n = args.diss3_size
+    setup = fields.low_mach_vortex_3d(n)
+    p = vlbm.make_params(model=vlbm.VLBM_DISSIPATIVE, shape=(n, n, n), storage="f32", gamma=setup.gamma,
+                         tau=setup.tau, tau_g=setup.tau_g, tau_m=setup.tau_m, nu=setup.nu, eta0=setup.eta0,
+                         j_c=setup.j_c, powell=True, stream=stream.cuda_stream)
+    ctx = vlbm.Context(p)
+    st = vlbm.vlbm_init_fields(ctx.ptr, 0, setup.Q)
+    del setup
+    vlbm.vlbm_step(ctx.ptr, 4)
+    steps = args.form_steps
+    ms = _time_steps(vlbm, [ctx.ptr], stream, torch, steps, False)
+    status = vlbm.status_string(vlbm.vlbm_sync(ctx.ptr))
+    ctx.close()
+    ncell = n ** 3
+    gl = ncell * steps / (ms * 1e-3) / 1e9
+    bytes_cell = 2 * 182 * 4
+    return {"workload": "dissipative MHD 3-D with locally evolved gradients, %d^3, 26 x D3Q7 (8 MHD fields, "
+                        "G, W ~ tau_M grad B, grad u), FP32, 3-D low-Mach resistive vortex, Powell source on" % n,
+            "kernel": "k_diss3_step<float> (fused collide+stream, 182 populations per cell)",
             "init_status": vlbm.status_string(st), "status": status, "glups": gl, "steps": steps,
             "bytes_per_cell": bytes_cell, "roofline_frac": gl * 1e9 * bytes_cell / (hbm_peak * 1e9)}
 
@@ -560,17 +592,22 @@ def error_growth(args, vlbm, fields, torch, stream):
 
 
 def closure_form(args, vlbm, torch, stream):
-    """Learned flux closure: coarse (fine/4)^3 + closure vs plain coarse and plain fine."""
+    """Learned flux closure, the configured protocol: coarse (fine/4)^3 + closure
+    against the plain method's error-vs-time curve and the plain fine run."""
     from paper_2606_00641_gb300 import closure
     nf = args.closure_fine
-    r = closure.run_experiment(fine_shape=(nf, nf, nf), train_seeds=tuple(range(5000, 5008)),
-                               val_seed=5100, test_seeds=(5101,), episodes=120)
-    cl = r["closure"]
-    t = r["tests"][0]
-    # tensor-core cost of the network per coarse step
-    N = (nf // 4) ** 3
-    flop = 2.0 * N * 27 * (8 * 32 + 32 * 32 + 32 * 24)
-    net_ms = (t["coarse_closure_ms"] - t["coarse_plain_ms"]) / r["n_eval"]
+    lo, hi = (float(v) for v in args.closure_mach.split(","))
+    r = closure.run_protocol(fine=nf, n_eval=args.closure_steps, mach_range=(lo, hi),
+                             train_seeds=tuple(range(5000, 5000 + args.closure_train_seeds)))
+    if "closure" not in r:
+        return r
+    cl = r.pop("closure")
+    nc = nf // 4
+    flop = 2.0 * nc ** 3 * 27 * (8 * 32 + 32 * 32 + 32 * 24)
+    tests = r["tests"]
+    ok = [t for t in tests if "coarse_closure" in t]
+    net_ms = (statistics.mean((t["coarse_closure"][0] - t["coarse_plain"][0]) / r["n_eval"] for t in ok)
+              if ok else None)
     cl.close()
     bf16_peak = None
     try:
@@ -578,15 +615,18 @@ def closure_form(args, vlbm, torch, stream):
             bf16_peak = float(json.load(fh)["bf16_tflops"])
     except (OSError, KeyError, ValueError):
         pass
-    tflops = flop / (net_ms * 1e-3) / 1e12 if net_ms > 0 else None
-    return {"workload": "ideal MHD 3-D, fine %d^3 restricted 4x to %d^3, 8 training seeds x 32 coarse "
-                        % (nf, nf // 4) +
-                        "steps, early stopping on seed 5100, test seed 5101, Mach 1.5, tau 0.51; "
-                        "network 3 x conv3x3x3 (8->32->32->24), BF16 tensor cores",
-            "coarse_steps": r["n_eval"], "test": t, "best_validation_rel_l2": r["best_val"],
-            "train_s": r["t_train_s"], "data_s": r["t_data_s"],
-            "time_to_solution_ms": {"fine": t["fine_ms"], "coarse_plain": t["coarse_plain_ms"],
-                                    "coarse_closure": t["coarse_closure_ms"]},
+    tflops = flop / (net_ms * 1e-3) / 1e12 if net_ms and net_ms > 0 else None
+    below = [t["closure_over_curve"] < 1.0 for t in ok if t.get("closure_over_curve")]
+    return {"workload": "ideal MHD 3-D, fine %d^3 restricted 4x to %d^3, %d coarse steps (%d fine), training "
+                        "seeds 5000-%d, early stopping on seed %d, held-out seeds %s, peak Mach U[%g, %g] per "
+                        "seed, tau 0.51; network 3 x conv3x3x3 (8->32->32->24), BF16 tensor cores; plain curve: "
+                        "sides 64, 128, 256 started from the restricted fine initial state, every error on the "
+                        "64^3 restriction"
+                        % (nf, nc, r["n_eval"], 4 * r["n_eval"], 5000 + args.closure_train_seeds - 1,
+                           r["val_seed"], r["test_seeds"], lo, hi),
+            "coarse_steps": r["n_eval"], "tests": tests, "best_validation_rel_l2": r["best_val"],
+            "skipped_train_seeds": r["skipped_train_seeds"], "train_s": r["t_train_s"], "data_s": r["t_data_s"],
+            "below_plain_curve": "%d of %d held-out seeds" % (sum(below), len(below)),
             "network_ms_per_coarse_step": net_ms, "network_gflop_per_step": flop / 1e9,
             "network_tflops": tflops, "bf16_peak_tflops": bf16_peak,
             "tensor_frac": (tflops / bf16_peak) if (tflops and bf16_peak) else None}
@@ -631,7 +671,7 @@ def compact_summary(line):
         out["growth_[f64bad,f32,f16,bf16:[step,linf]]"] = rows
         out["growth_sweep_M2,3xb.1,1,10"] = sweep
     names = {"resistive_channel": "channel", "powell_3d": "powell", "hlbm_sphere_3d": "hlbm",
-             "open_faces_3d": "open", "dissipative_2d": "diss"}
+             "open_faces_3d": "open", "dissipative_2d": "diss", "dissipative_3d": "diss3"}
     extra = line.get("other_paths") or {}
     for k, short in names.items():
         if k in extra:
@@ -642,13 +682,16 @@ def compact_summary(line):
     if "ideal_2d_128sq_f64" in extra:
         c = extra["ideal_2d_128sq_f64"]
         out["cfg1_f64"] = [_r(c["glups"]), _r((c.get("roofline") or {}).get("frac"))]
-    if "learned_closure" in extra:
+    if "learned_closure" in extra and "tests" in extra["learned_closure"]:
         c = extra["learned_closure"]
-        t = c["time_to_solution_ms"]
-        out["closure_ms_fine_closure_plain"] = [_r(t["fine"]), _r(t["coarse_closure"]), _r(t["coarse_plain"])]
-        te = c["test"]
-        out["closure_relL2_closure_plain"] = [_r(te.get("rel_l2_closure_coarse"), 3),
-                                              _r(te.get("rel_l2_plain_coarse"), 3)]
+        # per held-out seed: [fine ms, closure ms, closure err, plain-128 err, closure / plain curve]
+        out["closure_[fine_ms,cl_ms,cl_err,plain_err,cl/curve]"] = [
+            [_r(t["fine_ms"], 3), _r(t["coarse_closure"][0], 3), _r(t["coarse_closure"][1], 3),
+             _r(t["coarse_plain"][1], 3), _r(t.get("closure_over_curve"), 3)]
+            for t in c["tests"] if "coarse_closure" in t]
+        out["closure_curve_ms_err_64,128,256"] = [
+            [[_r(v[0], 3), _r(v[1], 3)] for v in t["plain"].values()]
+            for t in c["tests"] if "plain" in t][:1]
         out["closure_tensor_frac"] = _r(c.get("tensor_frac"), 3)
     if line.get("fp64_tflops"):
         out["fp64_tflops"] = _r(line["fp64_tflops"])
@@ -912,6 +955,8 @@ def main():
             extra["open_faces_3d"] = open_form(args, vlbm, fields, torch, stream, hbm_peak)
         if "diss" in which:
             extra["dissipative_2d"] = dissipative_form(args, vlbm, fields, torch, stream, hbm_peak)
+        if "diss3" in which:
+            extra["dissipative_3d"] = dissipative3_form(args, vlbm, fields, torch, stream, hbm_peak)
         if "cfg1" in which:
             extra["ideal_2d_128sq_f64"] = ideal_2d_f64_form(args, vlbm, fields, torch, stream, fp64_tflops)
 

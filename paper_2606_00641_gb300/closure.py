@@ -251,3 +251,172 @@ def run_experiment(fine_shape=(512, 512, 512), factor=4, train_seeds=tuple(range
                       "coarse_closure_ms": res.coarse_closure_ms, "status": [int(v) for v in st]})
     return {"closure": cl, "best_val": best, "history": hist, "tests": tests, "t_data_s": t_data,
             "t_train_s": t_train, "fine_shape": fine_shape, "coarse_shape": coarse_shape, "n_eval": n_eval}
+
+
+# ---------------------------------------------------------------------------
+# Time to solution against the plain method's error-vs-time curve
+# ---------------------------------------------------------------------------
+
+def _run_plain(Q0, gamma, tau, steps, torch, stream):
+    """A plain FP32 run from device fields Q0: final fields, device ms of the steps, status."""
+    shape = tuple(Q0.shape[1:])
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p = vlbm.make_params(shape=shape, storage="f32", gamma=gamma, tau=tau, stream=stream.cuda_stream)
+    with vlbm.Context(p) as c:
+        st = vlbm.vlbm_init_fields_device(c.ptr, 0, Q0.data_ptr())
+        if st != vlbm.VLBM_OK:
+            return None, 0.0, st
+        stream.synchronize()
+        ev0.record(stream)
+        c.step(steps)
+        ev1.record(stream)
+        ev1.synchronize()
+        out = torch.empty_like(Q0)
+        vlbm.vlbm_moments_device(c.ptr, 0, out.data_ptr())
+        stream.synchronize()
+        return out, ev0.elapsed_time(ev1), c.sync()
+
+
+def _restricted(Q, factor, torch, stream):
+    shape = tuple(Q.shape[1:])
+    out = torch.empty((8,) + tuple(n // factor for n in shape), dtype=torch.float64, device="cuda")
+    vlbm.vlbm_restrict(Q.data_ptr(), shape, factor, out.data_ptr(), stream.cuda_stream)
+    stream.synchronize()
+    return out
+
+
+def _rel_l2(Q, ref):
+    scale = ref.reshape(8, -1).std(1) + 1e-30
+    d = (Q - ref).reshape(8, -1) / scale[:, None]
+    return float(d.pow(2).mean().sqrt())
+
+
+def _curve_error_at(points, t):
+    """Plain error at device time t on the log-log line through the two curve
+    points around t (the last segment beyond the ends); points = [(ms, err)]."""
+    pts = sorted((float(a), float(b)) for a, b in points if a > 0 and b > 0)
+    if len(pts) < 2:
+        return None
+    i = 0
+    while i < len(pts) - 2 and pts[i + 1][0] < t:
+        i += 1
+    (t0, e0), (t1, e1) = pts[i], pts[i + 1]
+    if t1 == t0:
+        return e0
+    w = (np.log(t) - np.log(t0)) / (np.log(t1) - np.log(t0))
+    return float(np.exp(np.log(e0) + w * (np.log(e1) - np.log(e0))))
+
+
+def resolution_curve(closure, seed, mach, n_coarse, tau, torch, stream, fine=512, coarse=128,
+                     sides=(64, 128, 256), measure=64):
+    """One held-out seed: the fine run (fine^3, n_coarse fine / coarse steps in
+    acoustic scaling) and plain runs at every side in `sides`, each started from
+    the conservative restriction of the fine initial state (so every run solves
+    the same physical problem: the seeded recipe normalises its amplitudes and
+    its lattice scale on the grid it is sampled on), for n_coarse side / coarse
+    steps; the coarse run (side `coarse`) with and without `closure`.  Every
+    final state is restricted to `measure`^3 and compared there with the
+    restricted fine state (relative L2, per field over the reference spread).
+    Returns device times, errors and where the closure sits against the plain
+    error-vs-time curve (log-log interpolation between the plain points)."""
+    f0 = fields.ideal_fields((fine,) * 3, seed, device="cuda", **_field_kwargs(mach))
+    gamma = f0.gamma
+    Qf = f0.Q
+    del f0
+    starts = {n: _restricted(Qf, fine // n, torch, stream) for n in sorted(set(sides) | {coarse})}
+    Qf_end, fine_ms, st = _run_plain(Qf, gamma, tau, n_coarse * fine // coarse, torch, stream)
+    del Qf
+    row = {"seed": seed, "mach": mach, "fine_status": int(st), "fine_ms": fine_ms}
+    if st != vlbm.VLBM_OK:
+        return row
+    ref = _restricted(Qf_end, fine // measure, torch, stream)
+    ref_c = _restricted(Qf_end, fine // coarse, torch, stream)
+    del Qf_end
+    torch.cuda.empty_cache()
+
+    def at_measure(Q, n):
+        return Q if n == measure else _restricted(Q, n // measure, torch, stream)
+
+    curve = {}
+    for n in sides:
+        out, ms, stn = _run_plain(starts[n], gamma, tau, n_coarse * n // coarse, torch, stream)
+        curve[str(n)] = [ms, _rel_l2(at_measure(out, n), ref) if stn == vlbm.VLBM_OK else None, int(stn)]
+        del out
+    row["plain"] = curve
+    for name, cl in (("coarse_plain", None), ("coarse_closure", closure)):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p = vlbm.make_params(shape=(coarse,) * 3, storage="f32", gamma=gamma, tau=tau, stream=stream.cuda_stream)
+        with vlbm.Context(p) as c:
+            vlbm.vlbm_init_fields_device(c.ptr, 0, starts[coarse].data_ptr())
+            if cl is not None:
+                vlbm.vlbm_set_closure(c.ptr, cl)
+            stream.synchronize()
+            ev0.record(stream)
+            c.step(n_coarse)
+            ev1.record(stream)
+            ev1.synchronize()
+            out = torch.empty_like(starts[coarse])
+            vlbm.vlbm_moments_device(c.ptr, 0, out.data_ptr())
+            stream.synchronize()
+            vlbm.vlbm_set_closure(c.ptr, None)
+            stc = c.sync()
+        # [device ms, error on the measure grid, error on the coarse grid, status]
+        row[name] = [ev0.elapsed_time(ev1), _rel_l2(at_measure(out, coarse), ref), _rel_l2(out, ref_c), int(stc)]
+    pts = [(v[0], v[1]) for v in curve.values() if v[1] is not None]
+    t_c, e_c = row["coarse_closure"][0], row["coarse_closure"][1]
+    e_curve = _curve_error_at(pts, t_c)
+    row["plain_curve_error_at_closure_time"] = e_curve
+    row["closure_over_curve"] = (e_c / e_curve) if e_curve else None
+    return row
+
+
+def cfg5_mach(seed: int, lo: float = 1.0, hi: float = 3.0) -> float:
+    """Peak Mach of a seed's fields in the learned-closure workload: drawn
+    uniformly in [lo, hi] from the seed (a seeded draw, no arithmetic of the method)."""
+    return float(np.random.default_rng(seed).uniform(lo, hi))
+
+
+def run_protocol(fine=512, factor=4, train_seeds=tuple(range(5000, 5016)), val_seed=5016,
+                 test_seeds=(5100, 5101, 5102, 5103), mach_range=(1.0, 3.0), tau=0.51, n_pairs=16,
+                 warm_steps=(0, 100, 200, 300), n_eval=250, episodes=160, val_every=20, rollout=4, lr=1e-5,
+                 out_scale_rel=0.005, seed=0, sides=(64, 128, 256), measure=64, log=None):
+    """The learned-closure workload end to end: restricted fine trajectories of
+    `train_seeds` (each starting `warm_steps[i % 4]` fine steps into its run, so
+    early and developed states are both seen), in-the-loop training with early
+    stopping on `val_seed` over an `n_eval`-coarse-step run, then on each held-out
+    seed the fine run, the plain error-vs-time curve and the coarse runs with and
+    without the closure (resolution_curve).  Seeds whose fine run turns
+    non-physical are reported and left out of the training data."""
+    import torch
+    stream = torch.cuda.Stream()
+    shape = (fine,) * 3
+    coarse = fine // factor
+    t0 = time.perf_counter()
+    trajs, skipped = [], []
+    for i, s in enumerate(train_seeds):
+        try:
+            trajs.append(fine_trajectory(shape, factor, s, cfg5_mach(s, *mach_range), n_pairs, tau, torch, stream,
+                                         warm=warm_steps[i % len(warm_steps)]))
+        except RuntimeError:
+            skipped.append(s)
+    t_data = time.perf_counter() - t0
+    if not trajs:
+        return {"skipped_train_seeds": skipped, "error": "every training run became non-physical"}
+    mu, sigma = normalisation([q for tr in trajs for q in tr])
+    gamma = 5.0 / 3.0
+    cl = vlbm.Closure((coarse,) * 3, gamma, tau, mu, sigma, out_scale_rel * sigma, lr=lr, stream=stream.cuda_stream)
+    rng = np.random.default_rng(seed)
+    cl.set_weights(init_weights(rng, last_scale=0.0))
+    vref = fine_reference(shape, factor, val_seed, cfg5_mach(val_seed, *mach_range), n_eval, tau, torch, stream)
+    t0 = time.perf_counter()
+    best, hist = train_with_validation(cl, trajs, episodes, gamma, tau, stream, rng,
+                                       lambda: coarse_error(vref, cl, tau, torch, stream)[0],
+                                       val_every=val_every, rollout=rollout, log=log)
+    t_train = time.perf_counter() - t0
+    del trajs, vref
+    torch.cuda.empty_cache()
+    rows = [resolution_curve(cl, s, cfg5_mach(s, *mach_range), n_eval, tau, torch, stream, fine=fine, coarse=coarse,
+                             sides=sides, measure=measure) for s in test_seeds]
+    return {"closure": cl, "best_val": best, "history": hist, "tests": rows, "t_data_s": t_data,
+            "t_train_s": t_train, "skipped_train_seeds": skipped, "n_eval": n_eval, "coarse": coarse,
+            "fine": fine, "train_seeds": list(train_seeds), "val_seed": val_seed, "test_seeds": list(test_seeds)}

@@ -17,14 +17,21 @@
 // j_c <= 0 keeps eta = eta0).  Optional Powell source
 // S = -(div B)(0, B, u.B, u) with div B = (G_xx + G_yy) / tau_M.
 //
+// 3-D (D3Q7): a in {x, y, z}, Q[8 + 3a + b] = G_ab, Q[17 + 3a + b] = W_ab --
+// 26 lattices, 182 populations per cell, div B = (G_xx + G_yy + G_zz) / tau_M.
+//
 // One fused kernel per step as for ideal MHD (Eq. 2, AA in-place pattern,
 // one cell per thread, x-contiguous slot planes): load the 100 populations,
 // form the 20 moments, the fluxes and sources above, relax towards the
 // first-order equilibrium of Eq. 3 with direct source injection, store.
-// FP32 keeps the populations in registers between load and store; FP64
-// (400 registers' worth) sums them on the way in and reads them again for the
-// update -- the second read of a slot comes from the cache, and it is safe in
-// place because a thread writes only slots it reads, each after reading it.
+// 2-D FP32 keeps the populations in registers between load and store; 2-D FP64
+// (400 registers' worth) and every 3-D form (182 populations) sum them on the
+// way in and read them again for the update -- the second read of a slot comes
+// from the cache, and it is safe in place because a thread writes only slots it
+// reads, each after reading it.  The 3-D kernel also forms each lattice's flux
+// where it relaxes that lattice, from a few dozen derived quantities
+// (Diss3State), so that neither the populations nor the 78 flux components are
+// held at once.
 #include "diss_cell.cuh"
 
 namespace vlbm {
@@ -140,9 +147,119 @@ __global__ void k_diss_init(const DissArgs<C> a, double gamma, int64_t c0, int64
     }
 }
 
+// Linear indices of x + c_i (periodic), D3Q7 order.
+__device__ __forceinline__ void diss3_neighbours(int x, int y, int z, int nx, int ny, int nz, int64_t cell,
+                                                 int64_t (&nb)[kDiss3Q])
+{
+    const int64_t plane = (int64_t)nx * ny, vol = plane * nz;
+    nb[0] = cell;
+    nb[1] = (x + 1 < nx) ? cell + 1 : cell + 1 - nx;
+    nb[2] = (x > 0) ? cell - 1 : cell - 1 + nx;
+    nb[3] = (y + 1 < ny) ? cell + nx : cell + nx - plane;
+    nb[4] = (y > 0) ? cell - nx : cell - nx + plane;
+    nb[5] = (z + 1 < nz) ? cell + plane : cell + plane - vol;
+    nb[6] = (z > 0) ? cell - plane : cell - plane + vol;
+}
+
+// The 3-D fused step: the 26 moments from a first read of the 182 populations,
+// the derived state, then per lattice its flux, source and relaxation from a
+// second read of its 7 populations.
+template <class C, bool ODD>
+__global__ void __launch_bounds__(kBlockX) k_diss3_step(const DissArgs<C> a)
+{
+    constexpr int Q = kDiss3Q;
+    const int x = blockIdx.x * kBlockX + threadIdx.x;
+    if (x >= a.nx) return;
+    const int y = blockIdx.y, z = blockIdx.z;
+    const int64_t cell = x + (int64_t)a.nx * (y + (int64_t)a.ny * z);
+    int64_t nb[Q];
+    diss3_neighbours(x, y, z, a.nx, a.ny, a.nz, cell, nb);
+    C *pop = static_cast<C *>(a.pop);
+    auto src = [&](int k, int i) -> C * {
+        return pop + (int64_t)(k * Q + (ODD ? opp_axis(i) : i)) * a.stride + (ODD ? nb[opp_axis(i)] : cell);
+    };
+    auto dst = [&](int k, int i) -> C * {
+        return pop + (int64_t)(k * Q + (ODD ? i : opp_axis(i))) * a.stride + (ODD ? nb[i] : cell);
+    };
+
+    C q[kDiss3Lat];
+#pragma unroll
+    for (int k = 0; k < kDiss3Lat; ++k) {
+        C s = C(0);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) s += *src(k, i);
+        q[k] = s;
+    }
+    const Diss3State<C> st = diss3_state<C>(q, a, a.flags);
+
+    constexpr C w0 = ExactWeights<3, C>::w0, w1 = ExactWeights<3, C>::w1;
+#pragma unroll
+    for (int k = 0; k < kDiss3Lat; ++k) {
+        C phi[3];
+        diss3_flux<C>(k, q, st, phi);
+        const C S = diss3_source<C>(k, q, st, a.inv_tau_m);
+        C g[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) g[i] = *src(k, i);
+        const C om = a.omega[k];
+        const C omc = C(1) - om;
+        C ow0, ow1;
+        relax_weights<3, C>(om, ow0, ow1);
+        const C A0 = ow0 * q[k] + w0 * S;
+        const C A1 = ow1 * q[k] + w1 * S;
+        const C hom = C(0.5) * om;  // omega * w_moving / cs^2
+        const C bx = hom * phi[0], by = hom * phi[1], bz = hom * phi[2];
+        *dst(k, 0) = omc * g[0] + A0;
+        *dst(k, 1) = omc * g[1] + A1 + bx;
+        *dst(k, 2) = omc * g[2] + A1 - bx;
+        *dst(k, 3) = omc * g[3] + A1 + by;
+        *dst(k, 4) = omc * g[4] + A1 - by;
+        *dst(k, 5) = omc * g[5] + A1 + bz;
+        *dst(k, 6) = omc * g[6] + A1 - bz;
+    }
+}
+
+// 3-D f = f_eq(Q) at parity 0, and the positivity and sub-characteristic checks.
+template <class C>
+__global__ void k_diss3_init(const DissArgs<C> a, double gamma, int64_t c0, int64_t count, int64_t qstride,
+                             const double *__restrict__ Qin)
+{
+    constexpr int Q = kDiss3Q;
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= count) return;
+    const int64_t cell = c0 + t;
+    C q[kDiss3Lat];
+#pragma unroll
+    for (int k = 0; k < kDiss3Lat; ++k) q[k] = (C)Qin[k * qstride + t];
+    const Diss3State<C> st = diss3_state<C>(q, a, a.flags);
+    {
+        const C rho = q[0], ir = C(1) / rho;
+        const C u2 = (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]) * ir * ir;
+        const C B2 = q[5] * q[5] + q[6] * q[6] + q[7] * q[7];
+        const C p = a.gm1 * (q[4] - C(0.5) * rho * u2 - C(0.5) * B2);
+        const C vsig = sqrt(u2) + sqrt(fmax((C(gamma) * p + B2) * ir, C(0)));
+        if (!(vsig < (C)sqrt(AxisSet<3>::cs2))) atomicOr(a.flags, kFlagUnstable);
+    }
+    C *pop = static_cast<C *>(a.pop);
+    constexpr C w0 = ExactWeights<3, C>::w0, w1 = ExactWeights<3, C>::w1;
+    constexpr C h = C(AxisSet<3>::w1 / AxisSet<3>::cs2);
+#pragma unroll
+    for (int k = 0; k < kDiss3Lat; ++k) {
+        C phi[3];
+        diss3_flux<C>(k, q, st, phi);
+        C *base = pop + (int64_t)(k * Q) * a.stride + cell;
+        base[0] = w0 * q[k];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            base[(2 * c + 1) * a.stride] = w1 * q[k] + h * phi[c];
+            base[(2 * c + 2) * a.stride] = w1 * q[k] - h * phi[c];
+        }
+    }
+}
+
 struct DissRead {
     const void *pop;
-    int nx, ny;
+    int nx, ny, nz;
     int64_t stride;
     int parity;
 };
@@ -155,6 +272,57 @@ __device__ __forceinline__ C diss_logical(const DissRead &a, int64_t cell, const
     const int j = a.parity ? opp_axis(i) : i;
     const int64_t at = a.parity ? nb[opp_axis(i)] : cell;
     return pop[(int64_t)(k * kDissQ + j) * a.stride + at];
+}
+
+// 3-D: logical population f_ki and the moments and gather over D3Q7.
+template <class C>
+__device__ __forceinline__ C diss3_logical(const DissRead &a, int64_t cell, const int64_t (&nb)[kDiss3Q], int k,
+                                           int i)
+{
+    const C *pop = static_cast<const C *>(a.pop);
+    const int j = a.parity ? opp_axis(i) : i;
+    const int64_t at = a.parity ? nb[opp_axis(i)] : cell;
+    return pop[(int64_t)(k * kDiss3Q + j) * a.stride + at];
+}
+
+__device__ __forceinline__ void diss3_cell_nb(const DissRead &a, int64_t cell, int64_t (&nb)[kDiss3Q])
+{
+    const int x = (int)(cell % a.nx);
+    const int64_t r = cell / a.nx;
+    diss3_neighbours(x, (int)(r % a.ny), (int)(r / a.ny), a.nx, a.ny, a.nz, cell, nb);
+}
+
+template <class C>
+__global__ void k_diss3_moments(const DissRead a, int64_t c0, int64_t count, int64_t ostride,
+                                double *__restrict__ out)
+{
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= count) return;
+    const int64_t cell = c0 + t;
+    int64_t nb[kDiss3Q];
+    diss3_cell_nb(a, cell, nb);
+#pragma unroll
+    for (int k = 0; k < kDiss3Lat; ++k) {
+        C s = C(0);
+#pragma unroll
+        for (int i = 0; i < kDiss3Q; ++i) s += diss3_logical<C>(a, cell, nb, k, i);
+        out[k * ostride + t] = (double)s;
+    }
+}
+
+template <class C>
+__global__ void k_diss3_gather(const DissRead a, const int64_t *__restrict__ cells, int n, double *__restrict__ out)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const int64_t cell = cells[t];
+    int64_t nb[kDiss3Q];
+    diss3_cell_nb(a, cell, nb);
+#pragma unroll
+    for (int k = 0; k < kDiss3Lat; ++k)
+#pragma unroll
+        for (int i = 0; i < kDiss3Q; ++i)
+            out[(int64_t)t * kDiss3Lat * kDiss3Q + k * kDiss3Q + i] = (double)diss3_logical<C>(a, cell, nb, k, i);
 }
 
 // Q_k = sum_i f_ki (Eq. 4) for cells c0 .. c0 + count, summed in the storage precision.
@@ -204,9 +372,10 @@ template <class C> DissArgs<C> make_diss_args(vlbm_ctx *c)
     a.pop = c->pop;
     a.nx = d.nx;
     a.ny = d.ny;
+    a.nz = d.nz;
     a.stride = d.stride;
     a.gm1 = C(d.gamma - 1.0);
-    for (int k = 0; k < kDissLat; ++k) a.omega[k] = C(1.0 / (k < 8 ? d.tau[k] : p.tau_g));
+    for (int k = 0; k < kDiss3Lat; ++k) a.omega[k] = C(1.0 / (k < 8 ? d.tau[k] : p.tau_g));
     a.nu = C(p.nu);
     a.eta0 = C(p.eta0);
     a.inv_jc2 = C(p.j_c > 0.0 ? 1.0 / (p.j_c * p.j_c) : 0.0);
@@ -219,7 +388,7 @@ template <class C> DissArgs<C> make_diss_args(vlbm_ctx *c)
 DissRead make_diss_read(vlbm_ctx *c)
 {
     const Domain &d = c->dom[0];
-    return DissRead{c->pop, d.nx, d.ny, d.stride, (int)(c->step & 1)};
+    return DissRead{c->pop, d.nx, d.ny, d.nz, d.stride, (int)(c->step & 1)};
 }
 
 template <class C> vlbm_status step_t(vlbm_ctx *c, int parity)
@@ -227,11 +396,17 @@ template <class C> vlbm_status step_t(vlbm_ctx *c, int parity)
     constexpr bool hold = sizeof(C) == 4;
     const Domain &d = c->dom[0];
     const DissArgs<C> a = make_diss_args<C>(c);
-    const dim3 grid((unsigned)((d.nx + kBlockX - 1) / kBlockX), (unsigned)d.ny);
-    if (parity)
+    const dim3 grid((unsigned)((d.nx + kBlockX - 1) / kBlockX), (unsigned)d.ny, (unsigned)d.nz);
+    if (c->dim == 3) {
+        if (parity)
+            k_diss3_step<C, true><<<grid, kBlockX, 0, c->stream>>>(a);
+        else
+            k_diss3_step<C, false><<<grid, kBlockX, 0, c->stream>>>(a);
+    } else if (parity) {
         k_diss_step<C, true, hold><<<grid, kBlockX, 0, c->stream>>>(a);
-    else
+    } else {
         k_diss_step<C, false, hold><<<grid, kBlockX, 0, c->stream>>>(a);
+    }
     c->launches++;
     return cuda_check(c, cudaGetLastError(), "dissipative step launch");
 }
@@ -239,8 +414,11 @@ template <class C> vlbm_status step_t(vlbm_ctx *c, int parity)
 template <class C> vlbm_status init_t(vlbm_ctx *c, const double *Q, int64_t c0, int64_t n, int64_t qs)
 {
     const int threads = 128;
-    k_diss_init<C><<<(unsigned)((n + threads - 1) / threads), threads, 0, c->stream>>>(make_diss_args<C>(c),
-                                                                                      c->dom[0].gamma, c0, n, qs, Q);
+    const unsigned blocks = (unsigned)((n + threads - 1) / threads);
+    if (c->dim == 3)
+        k_diss3_init<C><<<blocks, threads, 0, c->stream>>>(make_diss_args<C>(c), c->dom[0].gamma, c0, n, qs, Q);
+    else
+        k_diss_init<C><<<blocks, threads, 0, c->stream>>>(make_diss_args<C>(c), c->dom[0].gamma, c0, n, qs, Q);
     c->launches++;
     return cuda_check(c, cudaGetLastError(), "dissipative init launch");
 }
@@ -248,8 +426,11 @@ template <class C> vlbm_status init_t(vlbm_ctx *c, const double *Q, int64_t c0, 
 template <class C> vlbm_status moments_t(vlbm_ctx *c, double *out, int64_t c0, int64_t n, int64_t os)
 {
     const int threads = 256;
-    k_diss_moments<C><<<(unsigned)((n + threads - 1) / threads), threads, 0, c->stream>>>(make_diss_read(c), c0, n,
-                                                                                        os, out);
+    const unsigned blocks = (unsigned)((n + threads - 1) / threads);
+    if (c->dim == 3)
+        k_diss3_moments<C><<<blocks, threads, 0, c->stream>>>(make_diss_read(c), c0, n, os, out);
+    else
+        k_diss_moments<C><<<blocks, threads, 0, c->stream>>>(make_diss_read(c), c0, n, os, out);
     c->launches++;
     return cuda_check(c, cudaGetLastError(), "dissipative moments launch");
 }
@@ -257,8 +438,11 @@ template <class C> vlbm_status moments_t(vlbm_ctx *c, double *out, int64_t c0, i
 template <class C> vlbm_status gather_t(vlbm_ctx *c, const int64_t *cells, int n, double *out)
 {
     const int threads = 128;
-    k_diss_gather<C><<<(unsigned)((n + threads - 1) / threads), threads, 0, c->stream>>>(make_diss_read(c), cells, n,
-                                                                                       out);
+    const unsigned blocks = (unsigned)((n + threads - 1) / threads);
+    if (c->dim == 3)
+        k_diss3_gather<C><<<blocks, threads, 0, c->stream>>>(make_diss_read(c), cells, n, out);
+    else
+        k_diss_gather<C><<<blocks, threads, 0, c->stream>>>(make_diss_read(c), cells, n, out);
     c->launches++;
     return cuda_check(c, cudaGetLastError(), "dissipative gather launch");
 }

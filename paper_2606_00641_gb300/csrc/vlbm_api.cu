@@ -104,10 +104,6 @@ vlbm_status validate(const vlbm_params *p, bool batch_member)
             g_err = "dissipative model: nu and eta0 must be finite and >= 0, j_c finite";
             return VLBM_ERR_ARG;
         }
-        if (p->dim != 2) {
-            g_err = "the dissipative model is built in 2-D (D2Q5)";
-            return VLBM_ERR_UNSUPPORTED;
-        }
         if (p->storage != VLBM_F32 && p->storage != VLBM_F64) {
             g_err = "the dissipative model is built for F32 and F64 storage";
             return VLBM_ERR_UNSUPPORTED;
@@ -332,10 +328,10 @@ vlbm_status create_common(const vlbm_params *p, int count, vlbm_ctx **out)
         c->nvar = c->nlat;
         c->nslot = c->nlat * c->q;
     } else if (c->model == VLBM_DISSIPATIVE) {
-        c->q = 5;
-        c->nlat = 20;
-        c->nvar = 20;
-        c->nslot = 100;
+        c->q = c->dim == 2 ? 5 : 7;
+        c->nlat = 8 + 6 * c->dim;  // 20 in 2-D, 26 in 3-D
+        c->nvar = c->nlat;
+        c->nslot = c->nlat * c->q;
     } else {
         c->q = 19;
         c->nlat = 4;

@@ -386,3 +386,58 @@ def low_mach_orszag_tang(n: int, *, u_lat: float = 0.02, mach: float = 0.1, gamm
     tau = 0.5 + 3.0 * stab * nu  # (tau - 1/2) cs^2 = stab * nu on D2Q5
     return DissipativeSetup(Q=np.ascontiguousarray(Q), gamma=gamma, tau=tau, tau_g=tau, tau_m=tau_m, nu=nu,
                             eta0=nu, j_c=jc_phys * s * dx, dx=dx, dt=dt)
+
+
+DISSIPATIVE3_FIELDS = IDEAL_FIELDS + tuple("G%s%s" % (a, b) for a in "xyz" for b in "xyz") + \
+    tuple("W%s%s" % (a, b) for a in "xyz" for b in "xyz")
+
+
+def low_mach_vortex_3d(n: int, *, u_lat: float = 0.02, mach: float = 0.1, gamma: float = 5.0 / 3.0,
+                       nu_phys: float = 1e-3, jc_phys: float = 25.0, tau_m_phys: float = 0.01,
+                       stab: float = 0.05) -> DissipativeSetup:
+    """A 3-D companion of the low-Mach resistive Orszag-Tang set-up for the
+    26-lattice D3Q7 form, on an n^3 grid of the periodic box [0, 2 pi)^3, in
+    lattice units (same scalings, viscosity, resistivity and tau_M as
+    low_mach_orszag_tang; a synthetic workload, the paper's dissipative case is
+    2-D).  Physical state: rho = 1,
+        u = (2 cos y + cos z, -2 sin x + sin z, sin x + cos y),
+        B = (-2 sin 2y + sin z, -2 sin x + cos z, cos x + sin 2y),
+    both free of divergence (no component depends on its own coordinate).
+    Scaling by s = u_lat / 3 (the peak of a velocity component), dx = 2 pi / n,
+    dt = s dx, uniform pressure from the sound speed u_lat / mach.  G_ab and W_ab
+    (at 8 + 3a + b and 17 + 3a + b) start at tau_M times the analytic gradients."""
+    n = int(n)
+    s = u_lat / 3.0
+    dx = 2.0 * math.pi / n
+    dt = s * dx
+    ax = dx * np.arange(n)
+    z, y, x = np.meshgrid(ax, ax, ax, indexing="ij")
+    u = [s * (2.0 * np.cos(y) + np.cos(z)), s * (-2.0 * np.sin(x) + np.sin(z)), s * (np.sin(x) + np.cos(y))]
+    B = [s * (-2.0 * np.sin(2.0 * y) + np.sin(z)), s * (-2.0 * np.sin(x) + np.cos(z)),
+         s * (np.cos(x) + np.sin(2.0 * y))]
+    # physical gradients d_a u_b and d_a B_b (rows a = x, y, z)
+    zero = np.zeros_like(x)
+    du = [[zero, -2.0 * np.cos(x), np.cos(x)],
+          [-2.0 * np.sin(y), zero, -np.sin(y)],
+          [-np.sin(z), np.cos(z), zero]]
+    dB = [[zero, -2.0 * np.cos(x), -np.sin(x)],
+          [-4.0 * np.cos(2.0 * y), zero, 2.0 * np.cos(2.0 * y)],
+          [np.cos(z), -np.sin(z), zero]]
+    c = u_lat / mach
+    p = c * c / gamma  # rho = 1
+    nu = nu_phys * s / dx
+    tau_m = tau_m_phys / dt
+    g = tau_m * s * dx  # tau_M times the lattice derivative of a physical derivative
+    Q = np.zeros((26, n, n, n))
+    Q[0] = 1.0
+    for b in range(3):
+        Q[1 + b] = u[b]
+        Q[5 + b] = B[b]
+    Q[4] = p / (gamma - 1.0) + 0.5 * sum(v * v for v in u) + 0.5 * sum(v * v for v in B)
+    for a in range(3):
+        for b in range(3):
+            Q[8 + 3 * a + b] = g * dB[a][b]
+            Q[17 + 3 * a + b] = g * du[a][b]
+    tau = 0.5 + 4.0 * stab * nu  # (tau - 1/2) cs^2 = stab * nu on D3Q7 (cs^2 = 1/4)
+    return DissipativeSetup(Q=np.ascontiguousarray(Q), gamma=gamma, tau=tau, tau_g=tau, tau_m=tau_m, nu=nu,
+                            eta0=nu, j_c=jc_phys * s * dx, dx=dx, dt=dt)

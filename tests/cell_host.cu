@@ -94,6 +94,27 @@ void diss(const C *q, C gm1, C nu, C eta0, C inv_jc2, C inv_tau_m, int powell, C
     }
 }
 
+template <class C>
+void diss3(const C *q, C gm1, C nu, C eta0, C inv_jc2, C inv_tau_m, int powell, C *phi, C *S, unsigned *flags)
+{
+    DissArgs<C> a{};
+    a.gm1 = gm1;
+    a.nu = nu;
+    a.eta0 = eta0;
+    a.inv_jc2 = inv_jc2;
+    a.inv_tau_m = inv_tau_m;
+    a.powell = powell;
+    C qq[kDiss3Lat];
+    for (int k = 0; k < kDiss3Lat; ++k) qq[k] = q[k];
+    const Diss3State<C> st = diss3_state<C>(qq, a, flags);
+    for (int k = 0; k < kDiss3Lat; ++k) {
+        C ph[3];
+        diss3_flux<C>(k, qq, st, ph);
+        for (int c = 0; c < 3; ++c) phi[3 * k + c] = ph[c];
+        S[k] = diss3_source<C>(k, qq, st, inv_tau_m);
+    }
+}
+
 }  // namespace
 
 #define HC_DIM(dim, call2, call3) \
@@ -178,6 +199,22 @@ int hc_diss_f32(const float *q, float gm1, float nu, float eta0, float inv_jc2, 
                 float *phi, float *S, unsigned *flags)
 {
     diss<float>(q, gm1, nu, eta0, inv_jc2, inv_tau_m, powell, phi, S, flags);
+    return 0;
+}
+
+// Dissipative system (3-D): fluxes phi[3 k + c] along x, y, z and sources S[k]
+// of one state q[26].
+int hc_diss3_f64(const double *q, double gm1, double nu, double eta0, double inv_jc2, double inv_tau_m, int powell,
+                 double *phi, double *S, unsigned *flags)
+{
+    diss3<double>(q, gm1, nu, eta0, inv_jc2, inv_tau_m, powell, phi, S, flags);
+    return 0;
+}
+
+int hc_diss3_f32(const float *q, float gm1, float nu, float eta0, float inv_jc2, float inv_tau_m, int powell,
+                 float *phi, float *S, unsigned *flags)
+{
+    diss3<float>(q, gm1, nu, eta0, inv_jc2, inv_tau_m, powell, phi, S, flags);
     return 0;
 }
 

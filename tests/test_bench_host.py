@@ -51,10 +51,13 @@ def _fake_line():
         "other_paths": {"resistive_channel": {"glups": 20.5, "roofline_frac": 0.98},
                         "batched_2d": {"glups_batched": 20.4, "roofline_frac_batched": 0.97, "speedup": 1.27},
                         "ideal_2d_128sq_f64": {"glups": 1.5},
-                        "learned_closure": {"time_to_solution_ms": {"fine": 1128.0, "coarse_closure": 20.6,
-                                                                    "coarse_plain": 5.9},
-                                            "test": {"rel_l2_closure_coarse": 0.00235, "rel_l2_plain_coarse": 0.00254},
-                                            "tensor_frac": 0.26}},
+                        "learned_closure": {"tests": [
+                            {"fine_ms": 8800.0, "coarse_closure": [160.0, 0.02, 0.01, 0], "coarse_plain": [45.0, 0.03,
+                                                                                                0.02, 0],
+                             "plain": {"64": [10.0, 0.06, 0], "128": [45.0, 0.03, 0],
+                                       "256": [550.0, 0.015, 0]},
+                             "closure_over_curve": 1.01}] * 4,
+                            "tensor_frac": 0.26}},
         "fp64_tflops": 1.057,
     }
 
@@ -71,4 +74,5 @@ def test_compact_summary_keeps_every_path_in_a_short_tail():
     sweep = out["growth_sweep_M2,3xb.1,1,10"]
     assert sweep["128^3 t0.51"] == {"f64bad": [10], "bf16_linf_last": 0.0}
     assert out["batched"] == [20.4, 0.97, 1.27] and out["cfg1_f64"] == [1.5, None]
-    assert out["closure_relL2_closure_plain"] == [0.00235, 0.00254]
+    assert out["closure_[fine_ms,cl_ms,cl_err,plain_err,cl/curve]"][0] == [8800.0, 160.0, 0.02, 0.03, 1.01]
+    assert out["closure_curve_ms_err_64,128,256"] == [[[10.0, 0.06], [45.0, 0.03], [550.0, 0.015]]]

@@ -65,6 +65,8 @@ def H():
     L.hc_hom_f32.argtypes = [i, f, p, p, p, f, p, p, p, p]
     L.hc_diss_f64.argtypes = [p, d, d, d, d, d, i, p, p, p]
     L.hc_diss_f32.argtypes = [p, f, f, f, f, f, i, p, p, p]
+    L.hc_diss3_f64.argtypes = [p, d, d, d, d, d, i, p, p, p]
+    L.hc_diss3_f32.argtypes = [p, f, f, f, f, f, i, p, p, p]
     return L
 
 
@@ -272,6 +274,35 @@ def test_dissipative_fluxes_and_sources_match_the_oracle(H, prec, powell, j_c):
         # a flux is made of are of that size), sources against the largest source
         pscale = np.abs(ref_phi).max()
         assert np.abs(phi.reshape(20, 2).astype(np.float64) - ref_phi).max() < tol * pscale
+        sscale = np.abs(ref_S).max()
+        assert np.abs(S.astype(np.float64) - ref_S).max() < tol * sscale
+    assert flags[0] == 0
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("powell", [False, True])
+@pytest.mark.parametrize("j_c", [0.0, 0.08])
+def test_dissipative_3d_fluxes_and_sources_match_the_oracle(H, prec, powell, j_c):
+    # the 26-lattice D3Q7 form: every lattice's flux along x, y, z and its source
+    shape = (3, 4, 5)
+    f0 = fields.ideal_fields(shape, 63, mach=1.0, beta=1.0, cfl=0.2)
+    rng = np.random.default_rng(64)
+    Q = np.concatenate([f0.Q, 0.05 * rng.normal(size=(18,) + shape)]).reshape(26, -1).T
+    dp = oracle.Dissipation(nu=0.02, eta0=0.03, j_c=j_c, tau_m=1.7, powell=powell)
+    dtype = np.float64 if prec == "f64" else np.float32
+    fn = H.hc_diss3_f64 if prec == "f64" else H.hc_diss3_f32
+    inv_jc2 = 1.0 / (j_c * j_c) if j_c > 0 else 0.0
+    tol = 1e-13 if prec == "f64" else F32_TOL
+    flags = np.zeros(1, np.uint32)
+    for q in Q:
+        phi = np.zeros(78, dtype)
+        S = np.zeros(26, dtype)
+        assert fn(_p(q.astype(dtype)), f0.gamma - 1.0, dp.nu, dp.eta0, inv_jc2, 1.0 / dp.tau_m, int(powell),
+                  _p(phi), _p(S), _p(flags)) == 0
+        ref_phi = oracle.diss_flux(f0.gamma, dp, q, dim=3)
+        ref_S = oracle.diss_source(dp, q, dim=3)
+        pscale = np.abs(ref_phi).max()
+        assert np.abs(phi.reshape(26, 3).astype(np.float64) - ref_phi).max() < tol * pscale
         sscale = np.abs(ref_S).max()
         assert np.abs(S.astype(np.float64) - ref_S).max() < tol * sscale
     assert flags[0] == 0

@@ -91,3 +91,29 @@ def test_batch_specs_draws():
     assert len(specs) == 64 and len({d["seed"] for d in specs}) == 64
     assert {d["side"] for d in specs} <= set(fields.BATCH_SIDES)
     assert all(1.4 <= d["gamma"] <= 5 / 3 and 0.5 <= d["mach"] <= 3.0 for d in specs)
+
+
+def test_low_mach_vortex_3d_recipe():
+    # divergence-free u and B, G and W at tau_M times the centred differences of the
+    # fields (second order: the error falls 4x when the grid is refined 2x), the
+    # pressure from the stated sound speed, and the 2-D set-up's scalings
+    errs = []
+    for n in (16, 32):
+        s = fields.low_mach_vortex_3d(n)
+        Q = s.Q
+        assert Q.shape == (26, n, n, n)
+        u = Q[1:4] / Q[0]
+        assert abs(np.abs(u).max() / 0.02 - 1) < 1e-2
+        div = lambda v: sum(0.5 * (np.roll(v[b], -1, 2 - b) - np.roll(v[b], 1, 2 - b)) for b in range(3))  # noqa
+        assert np.abs(div(Q[5:8])).max() < 1e-15 and np.abs(div(u)).max() < 1e-15
+        e = 0.0
+        for a in range(3):
+            for b in range(3):
+                dBab = 0.5 * (np.roll(Q[5 + b], -1, 2 - a) - np.roll(Q[5 + b], 1, 2 - a))
+                duab = 0.5 * (np.roll(u[b], -1, 2 - a) - np.roll(u[b], 1, 2 - a))
+                e = max(e, np.abs(s.tau_m * dBab - Q[8 + 3 * a + b]).max(), np.abs(s.tau_m * duab - Q[17 + 3 * a + b]).max())
+        errs.append(e / np.abs(Q[8:]).max())
+        p = (s.gamma - 1) * (Q[4] - 0.5 * (Q[1:4] ** 2).sum(0) - 0.5 * (Q[5:8] ** 2).sum(0))
+        assert np.allclose(p, (0.02 / 0.1) ** 2 / s.gamma)
+        assert abs((s.tau - 0.5) / 4 - 0.05 * s.nu) < 1e-15 and s.eta0 == s.nu
+    assert errs[1] < errs[0] / 3.5

@@ -1,7 +1,8 @@
 """Dissipative MHD with locally evolved gradients (model VLBM_DISSIPATIVE) on the
 GPU against the FP64 oracle (sec. 2.2.1 local moments evolution; sec. 2.3, the
 full dissipative system: viscous stress, eta(j) resistivity, optional Powell
-source; D2Q5, 20 lattices, 100 populations per cell).
+source; D2Q5, 20 lattices, 100 populations per cell; and the 3-D form on D3Q7,
+26 lattices, 182 populations per cell).
 
 Tolerances as for the ideal model: FP64 storage 1e-12, FP32 storage 1e-5,
 relative L-infinity per field against max(the field's maximum, its reference
@@ -192,7 +193,7 @@ def test_dissipative_checkpoint_and_graphs(V):
 
 def test_dissipative_api_contract(V):
     dp = dissipation(False)
-    for shape, storage in (((4, 6, 16), "f32"), ((8, 16), "f16dev"), ((8, 16), "bf16dev")):
+    for shape, storage in (((4, 6, 16), "f16dev"), ((8, 16), "f16dev"), ((8, 16), "bf16dev")):
         with pytest.raises(V.VlbmError) as e:
             V.Context(make(V, shape, storage, dp))
         assert e.value.status == V.VLBM_ERR_UNSUPPORTED
@@ -260,3 +261,90 @@ def test_low_mach_orszag_tang_full_size_sampled(V):
         ref = oracle.diss_run(box, setup.gamma, setup.tau, dp, steps, tau_g=setup.tau_g)[:, w, w]
         err = np.abs(got[:, y, x] - ref) / scale
         assert err.max() < 1e-5, (y, x, dict(zip(fields.DISSIPATIVE_FIELDS, err)))
+
+
+
+# ---------------------------------------------------------------------------
+# 3-D: 26 lattices of D3Q7 (G_ab at 8 + 3a + b, W_ab at 17 + 3a + b)
+# ---------------------------------------------------------------------------
+
+def diss3_fields(shape, seed, tau_m=TAU_M):
+    # the 3-D ideal recipe, G and W at tau_M times the centred gradients plus noise
+    f0 = fields.ideal_fields(shape, seed, mach=1.0, beta=1.0, cfl=0.2)
+    Q = f0.Q
+    u = Q[1:4] / Q[0]
+    rng = np.random.default_rng(seed)
+    G = np.zeros((18,) + tuple(shape))
+    for a in range(3):
+        ax = 2 - a  # array axis of x, y, z
+        for b in range(3):
+            G[3 * a + b] = tau_m * 0.5 * (np.roll(Q[5 + b], -1, ax) - np.roll(Q[5 + b], 1, ax))
+            G[9 + 3 * a + b] = tau_m * 0.5 * (np.roll(u[b], -1, ax) - np.roll(u[b], 1, ax))
+    G += 0.1 * np.abs(G).max() * rng.normal(size=G.shape)
+    return np.concatenate([Q, G]), f0.gamma
+
+
+def field_scales3(ref, tau_m=TAU_M):
+    n = ref.shape[0]
+    m = np.abs(ref).reshape(n, -1).max(1)
+    scale = m.copy()
+    scale[1:4] = m[1:4].max()
+    scale[5:8] = m[5:8].max()
+    umax = np.abs(ref[1:4] / ref[0]).max()
+    scale[8:17] = max(m[8:17].max(), tau_m * m[5:8].max())
+    scale[17:26] = max(m[17:26].max(), tau_m * umax)
+    return np.maximum(scale, 1e-300)
+
+
+TAU26 = TAU8 + [TAU_G] * 18
+
+
+@pytest.mark.parametrize("shape", [(5, 6, 16), (4, 7, 9), (1, 6, 130), (6, 1, 8)])
+@pytest.mark.parametrize("storage,tol", [("f64", 1e-12), ("f32", 1e-5)])
+@pytest.mark.parametrize("steps", [4, 5])
+@pytest.mark.parametrize("powell", [False, True])
+def test_dissipative_3d_matches_oracle(V, shape, storage, tol, steps, powell):
+    Q0, gamma = diss3_fields(shape, 47)
+    dp = dissipation(powell)
+    with V.Context(make(V, shape, storage, dp, gamma=gamma)) as ctx:
+        assert ctx.nvar == 26 and ctx.nslot == 182
+        assert ctx.init_fields(Q0) == V.VLBM_OK
+        ctx.step(steps)
+        got = ctx.moments()
+        assert ctx.sync() == V.VLBM_OK
+    ref = oracle.diss_run(Q0, gamma, TAU8, dp, steps, tau_g=TAU_G)
+    err = np.abs(got - ref).reshape(26, -1).max(1) / field_scales3(ref)
+    assert err.max() < tol, err
+
+
+@pytest.mark.parametrize("steps", [3, 4])
+def test_dissipative_3d_populations_match_oracle(V, steps):
+    shape = (4, 5, 12)
+    Q0, gamma = diss3_fields(shape, 48)
+    dp = dissipation(True)
+    cells = np.arange(np.prod(shape))
+    with V.Context(make(V, shape, "f64", dp, gamma=gamma)) as ctx:
+        assert ctx.init_fields(Q0) == V.VLBM_OK
+        ctx.step(steps)
+        got = ctx.populations(cells)
+    f = oracle.diss_init(Q0, gamma, dp)
+    for _ in range(steps):
+        f = oracle.diss_step(f, gamma, TAU8, dp, tau_g=TAU_G)
+    ref = f.reshape(26 * 7, -1).T
+    scale = np.abs(ref).max(0) + np.abs(ref).max() * 1e-3
+    assert (np.abs(got - ref) / scale).max() < 1e-12
+
+
+@pytest.mark.parametrize("storage,tol", [("f64", 1e-13), ("f32", 21 * 2.0 ** -24)])
+def test_dissipative_3d_conserves_the_mhd_sums(V, storage, tol):
+    shape = (10, 12, 16)
+    Q0, gamma = diss3_fields(shape, 49)
+    dp = dissipation(False)
+    with V.Context(make(V, shape, storage, dp, gamma=gamma)) as ctx:
+        assert ctx.init_fields(Q0) == V.VLBM_OK
+        s0 = ctx.conservation()
+        ctx.step(21)
+        s1 = ctx.conservation()
+        assert ctx.sync() == V.VLBM_OK
+    scale = np.abs(Q0[:8]).reshape(8, -1).sum(1)
+    assert (np.abs(s1 - s0) / scale).max() < tol

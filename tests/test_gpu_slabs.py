@@ -207,6 +207,22 @@ def test_dissipative_slabs_equal_the_single_domain(V, S):
         assert np.array_equal(got, ref)
 
 
+def test_dissipative_3d_slabs_equal_the_single_domain(V, S):
+    shape = (9, 6, 16)
+    f0 = fields.ideal_fields(shape, 522, mach=1.0, beta=1.0, cfl=0.2)
+    rng = np.random.default_rng(522)
+    Q0 = np.concatenate([f0.Q, 0.01 * rng.normal(size=(18,) + shape)])
+
+    def make(sub):
+        return V.make_params(model=V.VLBM_DISSIPATIVE, shape=sub, storage="f32", gamma=f0.gamma, tau=0.6,
+                             tau_g=0.7, tau_m=3.0, nu=0.02, eta0=0.03, j_c=0.05, powell=True)
+
+    for steps in (4, 5):
+        ref = single_run(V, make(shape), Q0, steps)
+        got, _ = slab_run(V, S, make, shape, 3, Q0, steps)
+        assert np.array_equal(got, ref)
+
+
 # ---------------------------------------------------------------------------
 # the public pack / unpack calls, routed as the one-process-per-GPU driver does
 # ---------------------------------------------------------------------------
