@@ -94,8 +94,8 @@ def test_validation_before_any_device_work(V):
     p = V.make_params(shape=(8, 8, 8))
     p.nz = 0
     assert _create_status(V, p) == V.VLBM_ERR_ARG
-    # the dissipative model: 2-D, F32 / F64, tau_g > 1/2, nu and eta0 >= 0
-    p = V.make_params(model=V.VLBM_DISSIPATIVE, shape=(8, 8, 8))
+    # the dissipative model: 2-D or 3-D, F32 / F64, tau_g > 1/2, nu and eta0 >= 0
+    p = V.make_params(model=V.VLBM_DISSIPATIVE, shape=(8, 8, 8), storage="bf16dev")
     assert _create_status(V, p) == V.VLBM_ERR_UNSUPPORTED
     p = V.make_params(model=V.VLBM_DISSIPATIVE, shape=(8, 8), storage="bf16dev")
     assert _create_status(V, p) == V.VLBM_ERR_UNSUPPORTED
