@@ -27,7 +27,8 @@
  *     rho u_y, rho u_z, e_tot, B_x, B_y, B_z); the resistive model has
  *     nvar = 7 (rho, m_x, m_y, m_z, B_x, B_y, B_z), where m includes the
  *     half-force shift of the Guo scheme; the Powell model adds D (nvar = 9)
- *     and the dissipative model G and W (nvar = 20, see vlbm_model).
+ *     and the dissipative model G and W (nvar = 20 in 2-D, 26 in 3-D, see
+ *     vlbm_model).
  *   - Velocity sets and direction order: D2Q5 (w0 = 1/3, w = 1/6,
  *     cs^2 = 1/3), D3Q7 (w0 = 1/4, w = 1/8, cs^2 = 1/4), D3Q19 (1/3, 1/18,
  *     1/36, cs^2 = 1/3).  Direction 0 is rest; 1 +x, 2 -x, 3 +y, 4 -y,
@@ -86,15 +87,17 @@ typedef enum {
  * the MHD equation system" and "Incompressible resistive MHD") with the
  * gradients it needs evolved locally (sec. 2.2.1): besides the eight fields of
  * Eq. 12 the state carries G_ab ~ tau_m d_a B_b (flux G_ab u_c - delta_ac B_b)
- * and W_ab ~ tau_m d_a u_b (flux W_ab u_c - delta_ac u_b), a in {x, y},
- * b in {x, y, z}, both relaxed by the source -G / tau_m, -W / tau_m.  Twenty
- * fields: rho, rho u (3), e_tot, B (3), then G_ab at 8 + 3a + b and W_ab at
- * 14 + 3a + b.  The MHD fluxes add the viscous stress rho nu (grad u +
- * grad u^T), -eta grad B in the induction flux and -u . tau_v + eta j x B in
- * the energy flux (no heat flux), with j = curl B and eta = eta0 (1 + |j|^2 /
- * j_c^2) (j_c <= 0: eta = eta0); params.powell adds Powell's source with
- * div B = (G_xx + G_yy) / tau_m.  2-D (D2Q5, 100 populations per cell), F64
- * and F32 storage, single domains. */
+ * and W_ab ~ tau_m d_a u_b (flux W_ab u_c - delta_ac u_b), a over the lattice
+ * axes, b in {x, y, z}, both relaxed by the source -G / tau_m, -W / tau_m.
+ * 2-D (D2Q5, 100 populations per cell), twenty fields: rho, rho u (3),
+ * e_tot, B (3), then G_ab at 8 + 3a + b and W_ab at 14 + 3a + b, a in {x, y},
+ * d_z = 0.  3-D (D3Q7, 182 populations per cell), twenty-six fields: G_ab at
+ * 8 + 3a + b and W_ab at 17 + 3a + b, a in {x, y, z}.  The MHD fluxes add the
+ * viscous stress rho nu (grad u + grad u^T), -eta grad B in the induction flux
+ * and -u . tau_v + eta j x B in the energy flux (no heat flux), with
+ * j = curl B and eta = eta0 (1 + |j|^2 / j_c^2) (j_c <= 0: eta = eta0);
+ * params.powell adds Powell's source with div B = trace(G) / tau_m.  F64 and
+ * F32 storage. */
 typedef enum { VLBM_IDEAL = 0, VLBM_RESISTIVE = 1, VLBM_IDEAL_POWELL = 2, VLBM_DISSIPATIVE = 3 } vlbm_model;
 
 /* Population storage.  F64: double storage and arithmetic.  F32: float
@@ -111,7 +114,7 @@ typedef void (*vlbm_free_fn)(void *ptr, size_t bytes, void *stream, void *user);
 
 typedef struct {
     int model;            /* vlbm_model */
-    int dim;              /* 2 (D2Q5 lattices) or 3 (D3Q7); resistive: 3; dissipative: 2 */
+    int dim;              /* 2 (D2Q5 lattices) or 3 (D3Q7); resistive: 3 */
     int nx, ny, nz;       /* cells per axis, nz = 1 when dim = 2 */
     int storage;          /* vlbm_storage */
     double gamma;         /* ideal: adiabatic index of the EOS (Eq. 9) */
@@ -135,9 +138,9 @@ typedef struct {
     double tau_m;         /* Powell model: relaxation time of D in time steps (source
                              -D / tau_m; div B = D / tau_m), > 1/2; dissipative model:
                              relaxation time of G and W in time steps */
-    double tau_g;         /* dissipative model: BGK relaxation time of the twelve
-                             gradient lattices (G, W), > 1/2; tau[0..7] serve the
-                             eight MHD lattices */
+    double tau_g;         /* dissipative model: BGK relaxation time of the gradient
+                             lattices (G, W: 12 in 2-D, 18 in 3-D), > 1/2; tau[0..7]
+                             serve the eight MHD lattices */
     double nu;            /* dissipative model: kinematic viscosity (lattice units), >= 0 */
     double eta0;          /* dissipative model: resistivity at zero current, >= 0 */
     double j_c;           /* dissipative model: current scale of eta(j); <= 0: constant eta0 */
@@ -502,9 +505,9 @@ vlbm_status vlbm_check_bounded_wait(vlbm_ctx *ctx, int tries);
 vlbm_status vlbm_measure_fp64_rate(int iters, void *stream, double *tflops);
 
 /* Small queries. */
-int vlbm_nvar(const vlbm_ctx *ctx);                  /* 8 ideal, 7 resistive, 9 Powell, 20 dissipative */
+int vlbm_nvar(const vlbm_ctx *ctx);                  /* 8 ideal, 7 resistive, 9 Powell, 20 / 26 dissipative (2-D / 3-D) */
 int vlbm_slots_per_cell(const vlbm_ctx *ctx);        /* populations per cell: 40 or 56 (ideal), 40 (D3Q19 +
-                                                        3 x D3Q7), 45 or 63 (Powell), 100 (dissipative) */
+                                                        3 x D3Q7), 45 or 63 (Powell), 100 or 182 (dissipative) */
 int vlbm_num_domains(const vlbm_ctx *ctx);
 int64_t vlbm_num_cells(const vlbm_ctx *ctx, int domain);
 int64_t vlbm_step_count(const vlbm_ctx *ctx);

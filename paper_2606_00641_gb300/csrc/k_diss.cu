@@ -25,13 +25,12 @@
 // form the 20 moments, the fluxes and sources above, relax towards the
 // first-order equilibrium of Eq. 3 with direct source injection, store.
 // 2-D FP32 keeps the populations in registers between load and store; 2-D FP64
-// (400 registers' worth) and every 3-D form (182 populations) sum them on the
-// way in and read them again for the update -- the second read of a slot comes
-// from the cache, and it is safe in place because a thread writes only slots it
-// reads, each after reading it.  The 3-D kernel also forms each lattice's flux
-// where it relaxes that lattice, from a few dozen derived quantities
-// (Diss3State), so that neither the populations nor the 78 flux components are
-// held at once.
+// (400 registers' worth) sums them on the way in and reads them again for the
+// update -- the second read of a slot comes from the cache, and it is safe in
+// place because a thread writes only slots it reads, each after reading it.
+// The 3-D kernel (182 populations) relaxes the gradient lattices as it reads
+// them and holds only the MHD lattices, forming each lattice's flux where it
+// relaxes that lattice (see k_diss3_step).
 #include "diss_cell.cuh"
 
 namespace vlbm {
@@ -161,10 +160,16 @@ __device__ __forceinline__ void diss3_neighbours(int x, int y, int z, int nx, in
     nb[6] = (z > 0) ? cell - plane : cell - plane + vol;
 }
 
-// The 3-D fused step: the 26 moments from a first read of the 182 populations,
-// the derived state, then per lattice its flux, source and relaxation from a
-// second read of its 7 populations.
-template <class C, bool ODD>
+// The 3-D fused step.  The fluxes of the 18 gradient lattices need only their
+// own moment, u and B, so the step reads every population once:
+//   A. the 8 MHD lattices into registers (56 values) and their moments -> u, B;
+//   B. each gradient lattice: read its 7 populations, sum, flux G u_c - I B (or
+//      W u_c - I u), source -G / tau_M, relax and store -- one read per slot;
+//   C. with all 26 moments the derived state (viscous stress, grad B, eta(j),
+//      Powell's div B), then the 8 MHD lattices relaxed from registers and stored.
+// FP64 (HOLD false) keeps nothing in registers and reads the MHD lattices again
+// in C (the FP64 pipe binds that form, not the memory traffic).
+template <class C, bool ODD, bool HOLD>
 __global__ void __launch_bounds__(kBlockX) k_diss3_step(const DissArgs<C> a)
 {
     constexpr int Q = kDiss3Q;
@@ -181,32 +186,15 @@ __global__ void __launch_bounds__(kBlockX) k_diss3_step(const DissArgs<C> a)
     auto dst = [&](int k, int i) -> C * {
         return pop + (int64_t)(k * Q + (ODD ? i : opp_axis(i))) * a.stride + (ODD ? nb[i] : cell);
     };
-
-    C q[kDiss3Lat];
-#pragma unroll
-    for (int k = 0; k < kDiss3Lat; ++k) {
-        C s = C(0);
-#pragma unroll
-        for (int i = 0; i < Q; ++i) s += *src(k, i);
-        q[k] = s;
-    }
-    const Diss3State<C> st = diss3_state<C>(q, a, a.flags);
-
     constexpr C w0 = ExactWeights<3, C>::w0, w1 = ExactWeights<3, C>::w1;
-#pragma unroll
-    for (int k = 0; k < kDiss3Lat; ++k) {
-        C phi[3];
-        diss3_flux<C>(k, q, st, phi);
-        const C S = diss3_source<C>(k, q, st, a.inv_tau_m);
-        C g[Q];
-#pragma unroll
-        for (int i = 0; i < Q; ++i) g[i] = *src(k, i);
+    // BGK with direct source injection for lattice k, populations g, moment qk
+    auto relax = [&](int k, const C (&g)[Q], C qk, const C (&phi)[3], C S) {
         const C om = a.omega[k];
         const C omc = C(1) - om;
         C ow0, ow1;
         relax_weights<3, C>(om, ow0, ow1);
-        const C A0 = ow0 * q[k] + w0 * S;
-        const C A1 = ow1 * q[k] + w1 * S;
+        const C A0 = ow0 * qk + w0 * S;
+        const C A1 = ow1 * qk + w1 * S;
         const C hom = C(0.5) * om;  // omega * w_moving / cs^2
         const C bx = hom * phi[0], by = hom * phi[1], bz = hom * phi[2];
         *dst(k, 0) = omc * g[0] + A0;
@@ -216,6 +204,56 @@ __global__ void __launch_bounds__(kBlockX) k_diss3_step(const DissArgs<C> a)
         *dst(k, 4) = omc * g[4] + A1 - by;
         *dst(k, 5) = omc * g[5] + A1 + bz;
         *dst(k, 6) = omc * g[6] + A1 - bz;
+    };
+
+    // A: the MHD lattices
+    C q[kDiss3Lat];
+    C f8[HOLD ? 8 : 1][Q];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        C s = C(0);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const C v = *src(k, i);
+            if constexpr (HOLD) f8[k][i] = v;
+            s += v;
+        }
+        q[k] = s;
+    }
+    const C ir = C(1) / q[0];
+    const C u[3] = {q[1] * ir, q[2] * ir, q[3] * ir};
+    const C B[3] = {q[5], q[6], q[7]};
+
+    // B: the gradient lattices G (8..16) and W (17..25), one read each
+#pragma unroll
+    for (int k = 8; k < kDiss3Lat; ++k) {
+        C g[Q];
+        C s = C(0);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            g[i] = *src(k, i);
+            s += g[i];
+        }
+        q[k] = s;
+        const bool isG = k < 17;
+        const int r = isG ? (k - 8) / 3 : (k - 17) / 3, b = isG ? (k - 8) % 3 : (k - 17) % 3;
+        C phi[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) phi[c] = s * u[c] - (r == c ? (isG ? B[b] : u[b]) : C(0));
+        relax(k, g, s, phi, -s * a.inv_tau_m);
+    }
+
+    // C: the derived state, then the MHD lattices
+    const Diss3State<C> st = diss3_state<C>(q, a, a.flags);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        C phi[3];
+        diss3_flux<C>(k, q, st, phi);
+        const C S = diss3_source<C>(k, q, st, a.inv_tau_m);
+        C g[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) g[i] = HOLD ? f8[HOLD ? k : 0][i] : *src(k, i);
+        relax(k, g, q[k], phi, S);
     }
 }
 
@@ -399,9 +437,9 @@ template <class C> vlbm_status step_t(vlbm_ctx *c, int parity)
     const dim3 grid((unsigned)((d.nx + kBlockX - 1) / kBlockX), (unsigned)d.ny, (unsigned)d.nz);
     if (c->dim == 3) {
         if (parity)
-            k_diss3_step<C, true><<<grid, kBlockX, 0, c->stream>>>(a);
+            k_diss3_step<C, true, hold><<<grid, kBlockX, 0, c->stream>>>(a);
         else
-            k_diss3_step<C, false><<<grid, kBlockX, 0, c->stream>>>(a);
+            k_diss3_step<C, false, hold><<<grid, kBlockX, 0, c->stream>>>(a);
     } else if (parity) {
         k_diss_step<C, true, hold><<<grid, kBlockX, 0, c->stream>>>(a);
     } else {
