@@ -224,23 +224,32 @@ __global__ void __launch_bounds__(kBlockX) k_diss3_step(const DissArgs<C> a)
     const C u[3] = {q[1] * ir, q[2] * ir, q[3] * ir};
     const C B[3] = {q[5], q[6], q[7]};
 
-    // B: the gradient lattices G (8..16) and W (17..25), one read each
+    // B: the gradient lattices G (8..16) and W (17..25), one read each; two
+    // lattices' loads are issued together, so that more of them are in flight
+    // (measured: 3.63 against 3.29 GLUPS for one at a time, at 166 against 128
+    // registers; three at a time ran the same as two)
+    constexpr int GB = 2;
 #pragma unroll
-    for (int k = 8; k < kDiss3Lat; ++k) {
-        C g[Q];
-        C s = C(0);
+    for (int k0 = 8; k0 < kDiss3Lat; k0 += GB) {
+        C g[GB][Q];
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            g[i] = *src(k, i);
-            s += g[i];
+        for (int kk = 0; kk < GB; ++kk)
+#pragma unroll
+            for (int i = 0; i < Q; ++i) g[kk][i] = *src(k0 + kk, i);
+#pragma unroll
+        for (int kk = 0; kk < GB; ++kk) {
+            const int k = k0 + kk;
+            C s = C(0);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) s += g[kk][i];
+            q[k] = s;
+            const bool isG = k < 17;
+            const int r = isG ? (k - 8) / 3 : (k - 17) / 3, b = isG ? (k - 8) % 3 : (k - 17) % 3;
+            C phi[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) phi[c] = s * u[c] - (r == c ? (isG ? B[b] : u[b]) : C(0));
+            relax(k, g[kk], s, phi, -s * a.inv_tau_m);
         }
-        q[k] = s;
-        const bool isG = k < 17;
-        const int r = isG ? (k - 8) / 3 : (k - 17) / 3, b = isG ? (k - 8) % 3 : (k - 17) % 3;
-        C phi[3];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) phi[c] = s * u[c] - (r == c ? (isG ? B[b] : u[b]) : C(0));
-        relax(k, g, s, phi, -s * a.inv_tau_m);
     }
 
     // C: the derived state, then the MHD lattices
