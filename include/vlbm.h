@@ -461,7 +461,10 @@ vlbm_status vlbm_halo_pack(vlbm_ctx *ctx, void *lo_dev, void *hi_dev);
 
 /* Write the received face messages (device buffers, vlbm_halo_bytes each,
  * complete before the context's stream reaches this work) into the slab's face
- * slot planes and mark the exchange done.  VLBM_ERR_STATE if not a slab. */
+ * slot planes and mark the exchange done.  A slab with open faces (on the axes
+ * the decomposition keeps whole) runs their equilibrium fill here rather than
+ * after its step: the fill's Neumann moments of the first and last layers read
+ * slots the exchange brings.  VLBM_ERR_STATE if not a slab. */
 vlbm_status vlbm_halo_unpack(vlbm_ctx *ctx, const void *lo_dev, const void *hi_dev);
 
 /* Advance P slabs of one decomposed domain that live in this process on one

@@ -216,7 +216,9 @@ vlbm_status launch_step(vlbm_ctx *c, int parity)
     if (c->model == VLBM_DISSIPATIVE) return diss_step(c, parity);
     if (c->closure) return closure_step(c, parity);
     vlbm_status s = ideal_step(c, parity);
-    if (s == VLBM_OK && any_open_face(c)) s = open_fill(c, parity ^ 1);  // for the next step's reads
+    // for the next step's reads; a slab fills after its halo exchange (vlbm_halo_unpack), since
+    // the Neumann moments of its first and last layers read slots the exchange brings
+    if (s == VLBM_OK && any_open_face(c) && !c->slab) s = open_fill(c, parity ^ 1);
     return s;
 }
 
@@ -923,6 +925,9 @@ vlbm_status vlbm_halo_unpack(vlbm_ctx *c, const void *lo_dev, const void *hi_dev
     if (!c || !lo_dev || !hi_dev) return VLBM_ERR_ARG;
     if (!c->slab) return fail(c, VLBM_ERR_STATE, "halo unpack: not a slab context (vlbm_set_slab)");
     vlbm_status s = halo_copy(c, const_cast<void *>(lo_dev), const_cast<void *>(hi_dev), false);
+    // open faces (on the axes the decomposition keeps whole) are filled once the slots their
+    // Neumann moments read have arrived
+    if (s == VLBM_OK && any_open_face(c)) s = open_fill(c, (int)(c->step & 1));
     if (s == VLBM_OK) c->halo_pending = false;
     return s;
 }
@@ -964,7 +969,13 @@ vlbm_status vlbm_slabs_step(vlbm_ctx *const *slabs, int nslabs, int n)
             if (s != VLBM_OK) return s;
             c->step += 1;
         }
-        if (nslabs == 1) continue;  // one slab is the whole periodic domain: its wrap is the neighbour
+        if (nslabs == 1) {  // one slab is the whole periodic domain: its wrap is the neighbour
+            if (any_open_face(c0)) {
+                vlbm_status s = open_fill(c0, (int)(c0->step & 1));
+                if (s != VLBM_OK) return s;
+            }
+            continue;
+        }
         for (int r = 0; r < nslabs; ++r) {
             vlbm_status s = halo_copy(slabs[r], lo_of(r), hi_of(r), true);
             if (s != VLBM_OK) return s;
@@ -978,6 +989,7 @@ vlbm_status vlbm_slabs_step(vlbm_ctx *const *slabs, int nslabs, int n)
             const int hi_src = after_even ? below : above;
             const int lo_src = after_even ? above : below;
             vlbm_status s = halo_copy(slabs[r], lo_of(lo_src), hi_of(hi_src), false);
+            if (s == VLBM_OK && any_open_face(slabs[r])) s = open_fill(slabs[r], (int)(slabs[r]->step & 1));
             if (s != VLBM_OK) return s;
         }
     }
