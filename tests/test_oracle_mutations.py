@@ -30,6 +30,8 @@ IDEAL_PINS = [
     lambda o: P.test_direct_source_injection_adds_S_per_cell_per_step(o),
     lambda o: P.test_update_is_covariant_under_the_rotations_of_the_lattice(o, 2),
     lambda o: P.test_update_is_covariant_under_the_rotations_of_the_lattice(o, 3),
+    lambda o: P.test_linearised_update_operator_predicts_the_run(o),
+    lambda o: P.test_linearised_operator_has_the_mhd_speeds_and_decay(o),
 ]
 RES_PINS = [
     lambda o: R.test_mass_exact_and_force_adds_F_per_cell(o),
@@ -116,6 +118,8 @@ MUTANTS = [
      "feq[k][i] = L->w[i] * (Q[k] + cphi);", IDEAL_PINS),
     ("BGK relaxes the wrong way", "double out = f + (feq[k][i] - f) / tau[k];",
      "double out = f + (f - feq[k][i]) / tau[k];", IDEAL_PINS),
+    ("BGK takes the first lattice's tau", "double out = f + (feq[k][i] - f) / tau[k];",
+     "double out = f + (feq[k][i] - f) / tau[0];", IDEAL_PINS),
     ("streams against c_i", "long dst = neighbour(x, y, z, L.c[i], nx, ny, nz);\n            for (int k = 0;",
      "long dst = neighbour(x, y, z, L.c[L.opp[i]], nx, ny, nz);\n            for (int k = 0;",
      IDEAL_PINS),

@@ -270,6 +270,95 @@ def test_linear_wave_speed_and_decay(orc, case):
         assert abs(D - D_ce) < 0.03 * D_ce, (name, D, D_ce)
 
 
+# --------------------------------------------------------------------------
+# the exact linearised scheme: one Fourier mode of a uniform state evolves by
+# the 40 x 40 D2Q5 update operator M(kappa) = S(kappa) [(1 - W) + W E P]
+# (BGK towards the first-order equilibrium, Eqs. 2-3, then streaming), so
+# after n steps its moments are P M^n E r, to second order in the amplitude.
+# --------------------------------------------------------------------------
+
+def flux_jacobian_4th(orc, gamma, Q, axis, h=1e-3):
+    """d Phi[:, axis] / dQ by the fourth-order central difference (truncation
+    ~h^4, rounding ~1e-16/h: ~1e-12 here)."""
+    J = np.zeros((8, 8))
+    for j in range(8):
+        d = np.zeros(8)
+        d[j] = h
+        fl = lambda s: orc.ideal_flux(gamma, Q + s * d)[:, axis]
+        J[:, j] = (8 * (fl(1) - fl(-1)) - (fl(2) - fl(-2))) / (12 * h)
+    return J
+
+
+def linearised_operator(orc, gamma, base, tau, kappa):
+    """M, E, P of the D2Q5 scheme linearised about the uniform state `base`
+    for the mode exp(i kappa . x): populations ordered (lattice, direction)."""
+    c, w, cs2, _ = orc.lattice(5)
+    J = [flux_jacobian_4th(orc, gamma, base, a) for a in range(2)]
+    E = np.zeros((40, 8))  # d f_eq / d Q
+    P = np.zeros((8, 40))  # moments: sum over the directions of a lattice
+    omega = np.zeros(40)
+    shift = np.zeros(40, complex)
+    for k in range(8):
+        for i in range(5):
+            row = 5 * k + i
+            E[row, k] += w[i]
+            for a in range(2):
+                E[row] += w[i] * c[i, a] * J[a][k] / cs2
+            P[k, row] = 1.0
+            omega[row] = 1.0 / tau[k]
+            # pushed along c_i: the value at x came from x - c_i
+            shift[row] = np.exp(-1j * (kappa[0] * c[i, 0] + kappa[1] * c[i, 1]))
+    M = shift[:, None] * (np.diag(1 - omega) + omega[:, None] * (E @ P))
+    return M, E, P
+
+
+def test_linearised_update_operator_predicts_the_run(orc):
+    gamma = 5 / 3
+    base = state(1.05, [0.03, -0.02, 0.015], 0.05, [0.12, -0.09, 0.06], gamma)
+    tau = np.array([0.62, 0.71, 0.66, 0.93, 0.58, 1.15, 0.77, 0.84])
+    ny, nx, n = 16, 32, 120
+    kappa = (2 * math.pi * 3 / nx, 2 * math.pi * 1 / ny)
+    r = np.random.default_rng(7).normal(size=8)
+    y, x = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    wave = np.exp(1j * (kappa[0] * x + kappa[1] * y))
+    eps = 1e-5
+    runs = []
+    for s in (1, -1):
+        Q0 = base[:, None, None] + s * eps * r[:, None, None] * np.cos(kappa[0] * x + kappa[1] * y)
+        f = orc.ideal_init(Q0, gamma)
+        for _ in range(n):
+            f = orc.ideal_step(f, gamma, tau)
+        runs.append(orc.ideal_moments(f))
+    measured = (runs[0] - runs[1]) / (2 * eps)  # the quadratic term cancels
+    M, E, P = linearised_operator(orc, gamma, base, tau, kappa)
+    amp = P @ np.linalg.matrix_power(M, n) @ E @ r
+    predicted = (amp[:, None, None] * wave[None]).real
+    assert np.abs(predicted).max() > 0.05  # the mode is still there
+    err = np.abs(measured - predicted).max() / np.abs(predicted).max()
+    assert err < 1e-8, err
+
+
+def test_linearised_operator_has_the_mhd_speeds_and_decay(orc):
+    """The 8 slow eigenvalues of M approach exp(-i k lambda - D k^2) with the
+    textbook speeds lambda and the Chapman-Enskog D = (tau - 1/2)(cs^2 - lambda^2)."""
+    gamma = 5 / 3
+    rho, u, p, B = 1.1, [0.02, -0.01, 0.01], 0.05, [0.12, 0.09, -0.05]
+    base = state(rho, u, p, B, gamma)
+    tau = 0.8
+    _, _, cs2, _ = orc.lattice(5)
+    k = 2 * math.pi / 512
+    M, _, _ = linearised_operator(orc, gamma, base, np.full(8, tau), (k, 0.0))
+    mu = np.linalg.eigvals(M)
+    slow = mu[np.argsort(-np.abs(mu))[:8]]
+    assert np.abs(mu[np.argsort(-np.abs(mu))[8:]]).max() < 0.5  # kinetic modes decay fast
+    speed = np.sort(-np.angle(slow) / k)
+    lam = mhd_speeds(rho, np.asarray(u), p, np.asarray(B), gamma, 0)
+    np.testing.assert_allclose(speed, lam, atol=1e-4)
+    order = np.argsort(-np.angle(slow) / k)
+    D = -np.log(np.abs(slow[order])) / k ** 2
+    np.testing.assert_allclose(D, (tau - 0.5) * (cs2 - lam ** 2), rtol=2e-3)
+
+
 def test_first_order_self_convergence(orc):
     # Acoustic scaling (the lattice velocities do not change with N, so a fixed
     # physical time is N/2 steps) at fixed tau: the scheme's diffusion
