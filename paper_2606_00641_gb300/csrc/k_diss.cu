@@ -169,13 +169,45 @@ __device__ __forceinline__ void diss3_neighbours(int x, int y, int z, int nx, in
 //      Powell's div B), then the 8 MHD lattices relaxed from registers and stored.
 // FP64 (HOLD false) keeps nothing in registers and reads the MHD lattices again
 // in C (the FP64 pipe binds that form, not the memory traffic).
-template <class C, bool ODD, bool HOLD>
+template <class C, bool ODD, bool HOLD, bool PF>
 __global__ void __launch_bounds__(kBlockX) k_diss3_step(const DissArgs<C> a)
 {
     constexpr int Q = kDiss3Q;
+    const int y = blockIdx.y, z = blockIdx.z;
+    if constexpr (PF) {
+        // Every slot row this CTA's row segment reads, requested into L2 at once, so that the
+        // 13 rounds of loads below wait on L2 rather than on DRAM.  Slot j of a cell is read at
+        // the cell itself (even step) or at the cell + c_j (odd step); only the 16-byte aligned
+        // part of each row segment inside its row is requested (rows start aligned: nx is a
+        // multiple of 16 / sizeof(C), which the launcher checks).
+        constexpr int A = 16 / (int)sizeof(C);
+        const int x0 = blockIdx.x * kBlockX;
+        const int xe = min(x0 + kBlockX, a.nx);
+        for (int t = threadIdx.x; t < kDiss3Lat * Q; t += kBlockX) {
+            const int j = t % Q;
+            int lo = x0, hi = xe, yy = y, zz = z;
+            if constexpr (ODD) {
+                const int dx = j == 1 ? 1 : (j == 2 ? -1 : 0);
+                const int dy = j == 3 ? 1 : (j == 4 ? -1 : 0);
+                const int dz = j == 5 ? 1 : (j == 6 ? -1 : 0);
+                lo = max(lo + dx, 0);
+                hi = min(hi + dx, a.nx);
+                yy = (yy + dy + a.ny) % a.ny;
+                zz = (zz + dz + a.nz) % a.nz;
+            }
+            lo = (lo + A - 1) / A * A;
+            hi = hi / A * A;
+            if (hi > lo) {
+                const C *row = static_cast<const C *>(a.pop) + (int64_t)t * a.stride +
+                               (int64_t)a.nx * (yy + (int64_t)a.ny * zz);
+                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(row + lo),
+                             "r"((unsigned)((hi - lo) * (int)sizeof(C)))
+                             : "memory");
+            }
+        }
+    }
     const int x = blockIdx.x * kBlockX + threadIdx.x;
     if (x >= a.nx) return;
-    const int y = blockIdx.y, z = blockIdx.z;
     const int64_t cell = x + (int64_t)a.nx * (y + (int64_t)a.ny * z);
     int64_t nb[Q];
     diss3_neighbours(x, y, z, a.nx, a.ny, a.nz, cell, nb);
@@ -445,10 +477,18 @@ template <class C> vlbm_status step_t(vlbm_ctx *c, int parity)
     const DissArgs<C> a = make_diss_args<C>(c);
     const dim3 grid((unsigned)((d.nx + kBlockX - 1) / kBlockX), (unsigned)d.ny, (unsigned)d.nz);
     if (c->dim == 3) {
-        if (parity)
-            k_diss3_step<C, true, hold><<<grid, kBlockX, 0, c->stream>>>(a);
-        else
-            k_diss3_step<C, false, hold><<<grid, kBlockX, 0, c->stream>>>(a);
+        // rows aligned for the L2 row prefetch (measured at 256^3: 3.66 against 3.63 GLUPS)
+        const bool pf = hold && d.nx % (16 / (int)sizeof(C)) == 0;
+        if (pf) {
+            if (parity)
+                k_diss3_step<C, true, hold, hold><<<grid, kBlockX, 0, c->stream>>>(a);
+            else
+                k_diss3_step<C, false, hold, hold><<<grid, kBlockX, 0, c->stream>>>(a);
+        } else if (parity) {
+            k_diss3_step<C, true, hold, false><<<grid, kBlockX, 0, c->stream>>>(a);
+        } else {
+            k_diss3_step<C, false, hold, false><<<grid, kBlockX, 0, c->stream>>>(a);
+        }
     } else if (parity) {
         k_diss_step<C, true, hold><<<grid, kBlockX, 0, c->stream>>>(a);
     } else {
