@@ -167,47 +167,23 @@ __device__ __forceinline__ void diss3_neighbours(int x, int y, int z, int nx, in
 //      W u_c - I u), source -G / tau_M, relax and store -- one read per slot;
 //   C. with all 26 moments the derived state (viscous stress, grad B, eta(j),
 //      Powell's div B), then the 8 MHD lattices relaxed from registers and stored.
-// FP64 (HOLD false) keeps nothing in registers and reads the MHD lattices again
-// in C (the FP64 pipe binds that form, not the memory traffic).
-template <class C, bool ODD, bool HOLD, bool PF>
-__global__ void __launch_bounds__(kBlockX) k_diss3_step(const DissArgs<C> a)
+// The step is bound by the bytes each SM keeps in flight: B's rounds of loads
+// each wait for DRAM.  So FP32 (HOLD) stages them: every thread copies its own
+// populations of the gradient lattices into its own column of shared memory
+// with cp.async, kNs - 1 pairs of lattices ahead of the pair it relaxes (no
+// registers held and no barrier: a thread reads back only what it copied).
+// Measured at 256^3: 3.91 GLUPS against 3.63 with two lattices' loads issued
+// together into registers (and 3.68 with every slot row of the CTA requested
+// into L2 at its start; 3.37 with the MHD lattices staged too, at four CTAs per
+// SM).  FP64 (HOLD false) keeps nothing in registers and reads the MHD lattices
+// again in C (the FP64 pipe binds that form, not the memory traffic).
+template <class C, bool ODD, bool HOLD>
+__device__ __forceinline__ void diss3_step_body(const DissArgs<C> &a)
 {
     constexpr int Q = kDiss3Q;
-    const int y = blockIdx.y, z = blockIdx.z;
-    if constexpr (PF) {
-        // Every slot row this CTA's row segment reads, requested into L2 at once, so that the
-        // 13 rounds of loads below wait on L2 rather than on DRAM.  Slot j of a cell is read at
-        // the cell itself (even step) or at the cell + c_j (odd step); only the 16-byte aligned
-        // part of each row segment inside its row is requested (rows start aligned: nx is a
-        // multiple of 16 / sizeof(C), which the launcher checks).
-        constexpr int A = 16 / (int)sizeof(C);
-        const int x0 = blockIdx.x * kBlockX;
-        const int xe = min(x0 + kBlockX, a.nx);
-        for (int t = threadIdx.x; t < kDiss3Lat * Q; t += kBlockX) {
-            const int j = t % Q;
-            int lo = x0, hi = xe, yy = y, zz = z;
-            if constexpr (ODD) {
-                const int dx = j == 1 ? 1 : (j == 2 ? -1 : 0);
-                const int dy = j == 3 ? 1 : (j == 4 ? -1 : 0);
-                const int dz = j == 5 ? 1 : (j == 6 ? -1 : 0);
-                lo = max(lo + dx, 0);
-                hi = min(hi + dx, a.nx);
-                yy = (yy + dy + a.ny) % a.ny;
-                zz = (zz + dz + a.nz) % a.nz;
-            }
-            lo = (lo + A - 1) / A * A;
-            hi = hi / A * A;
-            if (hi > lo) {
-                const C *row = static_cast<const C *>(a.pop) + (int64_t)t * a.stride +
-                               (int64_t)a.nx * (yy + (int64_t)a.ny * zz);
-                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(row + lo),
-                             "r"((unsigned)((hi - lo) * (int)sizeof(C)))
-                             : "memory");
-            }
-        }
-    }
     const int x = blockIdx.x * kBlockX + threadIdx.x;
     if (x >= a.nx) return;
+    const int y = blockIdx.y, z = blockIdx.z;
     const int64_t cell = x + (int64_t)a.nx * (y + (int64_t)a.ny * z);
     int64_t nb[Q];
     diss3_neighbours(x, y, z, a.nx, a.ny, a.nz, cell, nb);
@@ -238,6 +214,36 @@ __global__ void __launch_bounds__(kBlockX) k_diss3_step(const DissArgs<C> a)
         *dst(k, 6) = omc * g[6] + A1 - bz;
     };
 
+    // B's staging: pairs of gradient lattices, kNs stages of 14 populations per thread
+    constexpr int GB = 2;
+    constexpr int kNp = (kDiss3Lat - 8) / GB;
+    constexpr int kNs = 4;
+    __shared__ C stg[HOLD ? kNs : 1][HOLD ? GB * Q : 1][kBlockX];
+    auto issue = [&](int p) {  // copies of pair p (none past the last), always one commit group
+        if (p < kNp) {
+            // lattice 8 + GB p, direction i: slot (8 + GB p) Q + i' at cell n_i', with i' = i
+            // (even) or opp(i) (odd); one 64-bit base per lattice
+            const C *lat = pop + (int64_t)(8 + GB * p) * Q * a.stride;
+#pragma unroll
+            for (int kk = 0; kk < GB; ++kk)
+#pragma unroll
+                for (int i = 0; i < Q; ++i) {
+                    const int j = ODD ? opp_axis(i) : i;
+                    const C *g = lat + ((int64_t)(kk * Q + j) * a.stride + (ODD ? nb[j] : cell));
+                    const uint32_t d =
+                        (uint32_t)__cvta_generic_to_shared(&stg[p % kNs][kk * Q + i][threadIdx.x]);
+                    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(d), "l"(g),
+                                 "n"((int)sizeof(C))
+                                 : "memory");
+                }
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    };
+    if constexpr (HOLD) {
+#pragma unroll
+        for (int p = 0; p < kNs - 1; ++p) issue(p);
+    }
+
     // A: the MHD lattices
     C q[kDiss3Lat];
     C f8[HOLD ? 8 : 1][Q];
@@ -256,18 +262,25 @@ __global__ void __launch_bounds__(kBlockX) k_diss3_step(const DissArgs<C> a)
     const C u[3] = {q[1] * ir, q[2] * ir, q[3] * ir};
     const C B[3] = {q[5], q[6], q[7]};
 
-    // B: the gradient lattices G (8..16) and W (17..25), one read each; two
-    // lattices' loads are issued together, so that more of them are in flight
-    // (measured: 3.63 against 3.29 GLUPS for one at a time, at 166 against 128
-    // registers; three at a time ran the same as two)
-    constexpr int GB = 2;
+    // B: the gradient lattices G (8..16) and W (17..25), a pair at a time
 #pragma unroll
-    for (int k0 = 8; k0 < kDiss3Lat; k0 += GB) {
+    for (int p = 0; p < kNp; ++p) {
+        const int k0 = 8 + GB * p;
         C g[GB][Q];
+        if constexpr (HOLD) {
+            issue(p + kNs - 1);
+            // every group but the newest kNs - 1 complete: pairs 0..p have landed
+            asm volatile("cp.async.wait_group %0;\n" ::"n"(kNs - 1) : "memory");
 #pragma unroll
-        for (int kk = 0; kk < GB; ++kk)
+            for (int kk = 0; kk < GB; ++kk)
 #pragma unroll
-            for (int i = 0; i < Q; ++i) g[kk][i] = *src(k0 + kk, i);
+                for (int i = 0; i < Q; ++i) g[kk][i] = stg[p % kNs][kk * Q + i][threadIdx.x];
+        } else {
+#pragma unroll
+            for (int kk = 0; kk < GB; ++kk)
+#pragma unroll
+                for (int i = 0; i < Q; ++i) g[kk][i] = *src(k0 + kk, i);
+        }
 #pragma unroll
         for (int kk = 0; kk < GB; ++kk) {
             const int k = k0 + kk;
@@ -296,6 +309,14 @@ __global__ void __launch_bounds__(kBlockX) k_diss3_step(const DissArgs<C> a)
         for (int i = 0; i < Q; ++i) g[i] = HOLD ? f8[HOLD ? k : 0][i] : *src(k, i);
         relax(k, g, q[k], phi, S);
     }
+}
+
+// Three CTAs of the FP32 form fit an SM at 168 registers and 28 KB of staging each
+// (the FP64 form keeps the compiler's own register choice)
+template <class C, bool ODD, bool HOLD>
+__global__ void __launch_bounds__(kBlockX, HOLD ? 3 : 0) k_diss3_step(const DissArgs<C> a)
+{
+    diss3_step_body<C, ODD, HOLD>(a);
 }
 
 // 3-D f = f_eq(Q) at parity 0, and the positivity and sub-characteristic checks.
@@ -477,18 +498,10 @@ template <class C> vlbm_status step_t(vlbm_ctx *c, int parity)
     const DissArgs<C> a = make_diss_args<C>(c);
     const dim3 grid((unsigned)((d.nx + kBlockX - 1) / kBlockX), (unsigned)d.ny, (unsigned)d.nz);
     if (c->dim == 3) {
-        // rows aligned for the L2 row prefetch (measured at 256^3: 3.66 against 3.63 GLUPS)
-        const bool pf = hold && d.nx % (16 / (int)sizeof(C)) == 0;
-        if (pf) {
-            if (parity)
-                k_diss3_step<C, true, hold, hold><<<grid, kBlockX, 0, c->stream>>>(a);
-            else
-                k_diss3_step<C, false, hold, hold><<<grid, kBlockX, 0, c->stream>>>(a);
-        } else if (parity) {
-            k_diss3_step<C, true, hold, false><<<grid, kBlockX, 0, c->stream>>>(a);
-        } else {
-            k_diss3_step<C, false, hold, false><<<grid, kBlockX, 0, c->stream>>>(a);
-        }
+        if (parity)
+            k_diss3_step<C, true, hold><<<grid, kBlockX, 0, c->stream>>>(a);
+        else
+            k_diss3_step<C, false, hold><<<grid, kBlockX, 0, c->stream>>>(a);
     } else if (parity) {
         k_diss_step<C, true, hold><<<grid, kBlockX, 0, c->stream>>>(a);
     } else {
