@@ -48,6 +48,10 @@ MEASURED_DRAM_BYTES_PER_CELL = {"f32": 7457219e3 / 16777216, "f16dev": 3705818e3
 # 2 x 152 = 461; 2-D (128^2): even 91 + 33 + 2 x 122 = 368, odd 79 + 33 + 2 x 122
 # = 356.  Set an entry to None whenever that kernel changes until it is re-captured.
 MEASURED_FP64_FLOP_PER_CELL = {2: 362.0, 3: 448.5}
+# FP64 pipe instructions (dadd + dmul + dfma) per cell update, mean of both parities, from the
+# same ncu capture: each takes one issue of the FP64 pipe, whose instruction rate is half the
+# measured FMA FLOP rate
+MEASURED_FP64_INSTR_PER_CELL = {2: 240.0, 3: 296.5}
 # the step kernel the roofline describes, per storage (3-D, nx % 8 == 0)
 STEP_KERNEL = {"f32": "k_ideal_step<3,float,float> (fused collide+stream)",
                "f64": "k_ideal_step<3,double,double> (fused collide+stream; FP64-pipe bound on GB300)",
@@ -513,7 +517,8 @@ def ideal_2d_f64_form(args, vlbm, fields, torch, stream, fp64_tflops):
     if flop and fp64_tflops:
         ach = gl * 1e9 * flop / 1e12
         out["roofline"] = {"bound": "alu", "achieved": ach, "peak": fp64_tflops, "unit": "TFLOP/s",
-                           "frac": ach / fp64_tflops, "flop_per_cell": flop}
+                           "frac": ach / fp64_tflops, "flop_per_cell": flop,
+                           "fp64_pipe_frac": gl * 1e9 * MEASURED_FP64_INSTR_PER_CELL[2] / (fp64_tflops * 1e12 / 2)}
     return out
 
 
@@ -651,6 +656,8 @@ def compact_summary(line):
         worst = max(v["rel_linf_vs_f64"].values()) if "rel_linf_vs_f64" in v else None
         frac = v.get("roofline_frac", (v.get("roofline") or {}).get("frac"))
         out["form_" + k] = [_r(v["glups"]), _r(frac), _r(worst, 3)]
+        if (v.get("roofline") or {}).get("fp64_pipe_frac"):
+            out["form_" + k + "_fp64_pipe_frac"] = _r(v["roofline"]["fp64_pipe_frac"])
     g = line.get("error_growth")
     if g:
         # per case: the FP64 run's first non-physical check (or None), and the
@@ -681,7 +688,8 @@ def compact_summary(line):
         out["batched"] = [_r(b["glups_batched"]), _r(b["roofline_frac_batched"]), _r(b["speedup"])]
     if "ideal_2d_128sq_f64" in extra:
         c = extra["ideal_2d_128sq_f64"]
-        out["cfg1_f64"] = [_r(c["glups"]), _r((c.get("roofline") or {}).get("frac"))]
+        out["cfg1_f64[glups,flop_frac,pipe_frac]"] = [_r(c["glups"]), _r((c.get("roofline") or {}).get("frac")),
+                                                    _r((c.get("roofline") or {}).get("fp64_pipe_frac"))]
     if "learned_closure" in extra and "tests" in extra["learned_closure"]:
         c = extra["learned_closure"]
         # per held-out seed: [fine ms, closure ms, closure err, plain-128 err, closure / plain curve]
@@ -914,7 +922,9 @@ def main():
         if flop3 and fp64_tflops:
             ach = forms["f64"]["glups"] * 1e9 * flop3 / 1e12
             forms["f64"]["roofline"] = {"bound": "alu", "achieved": ach, "peak": fp64_tflops, "unit": "TFLOP/s",
-                                        "frac": ach / fp64_tflops, "flop_per_cell": flop3}
+                                        "frac": ach / fp64_tflops, "flop_per_cell": flop3,
+                                        "fp64_pipe_frac": forms["f64"]["glups"] * 1e9 *
+                                        MEASURED_FP64_INSTR_PER_CELL[3] / (fp64_tflops * 1e12 / 2)}
         scale = Q.reshape(8, -1).abs().amax(1)
         for form in ["f32"] + [f for f in form_list if f not in ("f64", "f32")]:
             c = make_ctx(form)

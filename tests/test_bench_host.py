@@ -73,6 +73,6 @@ def test_compact_summary_keeps_every_path_in_a_short_tail():
     assert rows["256^3 M2 b1 t0.51"] == [1000, [100, 0.002], [100, 0.002], [100, 0.002]]
     sweep = out["growth_sweep_M2,3xb.1,1,10"]
     assert sweep["128^3 t0.51"] == {"f64bad": [10], "bf16_linf_last": 0.0}
-    assert out["batched"] == [20.4, 0.97, 1.27] and out["cfg1_f64"] == [1.5, None]
+    assert out["batched"] == [20.4, 0.97, 1.27] and out["cfg1_f64[glups,flop_frac,pipe_frac]"] == [1.5, None, None]
     assert out["closure_[fine_ms,cl_ms,cl_err,plain_err,cl/curve]"][0] == [8800.0, 160.0, 0.02, 0.03, 1.01]
     assert out["closure_curve_ms_err_64,128,256"] == [[[10.0, 0.06], [45.0, 0.03], [550.0, 0.015]]]
