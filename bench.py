@@ -480,7 +480,8 @@ def hlbm_form(args, vlbm, fields, torch, stream, hbm_peak):
 
 
 def batch_form(args, vlbm, fields, torch, stream, hbm_peak):
-    """64 independent 2-D domains (sides 64..1024) in one launch per step vs 64 plain launches."""
+    """64 independent 2-D domains (sides 64..1024) in one launch per step vs 64 plain launches,
+    each timed over the workload's 1,000 steps."""
     specs = fields.batch_specs(64, 4004)
     params, Qs = [], []
     for sp in specs:
@@ -491,7 +492,7 @@ def batch_form(args, vlbm, fields, torch, stream, hbm_peak):
         params.append(vlbm.make_params(shape=(n, n), storage="f32", gamma=sp["gamma"], tau=0.51,
                                        stream=stream.cuda_stream))
     ncell = sum(sp["side"] ** 2 for sp in specs)
-    steps = 64
+    steps = 1000
     # batched: one context, one launch per step, graph-captured, autotuned tile shape
     bctx = vlbm.Context(params, batch=True)
     bad = 0
@@ -501,6 +502,18 @@ def batch_form(args, vlbm, fields, torch, stream, hbm_peak):
     vlbm.vlbm_step(bctx.ptr, 64)
     ms_b = _time_steps(vlbm, [bctx.ptr], stream, torch, steps, False)
     st_b = vlbm.status_string(vlbm.vlbm_sync(bctx.ptr))
+    # which domains left the physical states (NaN, rho <= 0 or p <= 0) by the end of the run:
+    # the health flag is one per context; the cost of a step does not depend on the values
+    bad_domains = []
+    for d, sp in enumerate(specs):
+        Qd = torch.empty((8, sp["side"], sp["side"]), dtype=torch.float64, device="cuda")
+        vlbm.vlbm_moments_device(bctx.ptr, d, Qd.data_ptr())
+        stream.synchronize()
+        rho = Qd[0]
+        p = (sp["gamma"] - 1.0) * (Qd[4] - 0.5 * (Qd[1] ** 2 + Qd[2] ** 2 + Qd[3] ** 2) / rho
+                                   - 0.5 * (Qd[5] ** 2 + Qd[6] ** 2 + Qd[7] ** 2))
+        if not bool(torch.isfinite(Qd).all()) or float(rho.min()) <= 0.0 or float(p.min()) <= 0.0:
+            bad_domains.append((d, sp["side"], round(sp["mach"], 3)))
     bctx.close()
     # baseline: 64 contexts, one plain launch per domain per step
     ctxs = [vlbm.Context(p) for p in params]
@@ -516,6 +529,10 @@ def batch_form(args, vlbm, fields, torch, stream, hbm_peak):
     return {"workload": "64 periodic 2-D ideal-MHD domains, sides from {64..1024} (seed 4004), "
                         "gamma U[1.4,5/3], Mach U[0.5,3], 8 x D2Q5, FP32", "cells": ncell,
             "init_failures": int(bad), "status": st_b, "tile_shape": choice,
+            "nonphysical_domains_[index,side,mach]": bad_domains,
+            "lowest_mach_nonphysical": min((m for _, _, m in bad_domains), default=None),
+            "highest_mach_physical": max((sp["mach"] for d, sp in enumerate(specs)
+                                          if d not in {b[0] for b in bad_domains}), default=None),
             "glups_batched": gb, "glups_sequential_launches": gs, "speedup": gb / gs, "steps": steps,
             "bytes_per_cell": 320, "roofline_frac_batched": gb * 1e9 * 320 / (hbm_peak * 1e9)}
 
@@ -713,6 +730,9 @@ def compact_summary(line):
     if "batched_2d" in extra:
         b = extra["batched_2d"]
         out["batched"] = [_r(b["glups_batched"]), _r(b["roofline_frac_batched"]), _r(b["speedup"])]
+        if "nonphysical_domains_[index,side,mach]" in b:
+            out["batched_nonphysical_of_64_[n,lowest_mach]"] = [len(b["nonphysical_domains_[index,side,mach]"]),
+                                                                b["lowest_mach_nonphysical"]]
     if "ideal_2d_128sq_f64" in extra:
         c = extra["ideal_2d_128sq_f64"]
         out["cfg1_f64[glups,flop_frac,pipe_frac]"] = [_r(c["glups"]), _r((c.get("roofline") or {}).get("frac")),
