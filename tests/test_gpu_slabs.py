@@ -357,3 +357,38 @@ def test_slabs_with_open_x_faces_and_solids_equal_the_single_domain(V, S):
         assert g.step(steps) == V.VLBM_OK
         got = g.moments()
     assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("shape", [(24, 20), (10, 12, 16)])
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+@pytest.mark.parametrize("steps", [5, 6])
+def test_slabs_with_open_faces_on_both_kept_axes_equal_the_single_domain(V, S, shape, storage, steps):
+    # open faces with mixed Dirichlet / Neumann masks on both x faces (and both y faces in 3-D,
+    # whose edges with the x faces give diagonal normals), at both parities and both storages:
+    # the slabs fill them after the exchange, the single domain after its step -- bit for bit
+    f0 = fields.ideal_fields(shape, 529, mach=0.5, beta=1.0, cfl=0.2)
+    mean = f0.Q.reshape(8, -1).mean(1)
+    tau = [0.6, 0.55, 0.55, 0.55, 0.7, 0.6, 0.6, 0.6]
+
+    def make(sub):
+        return V.make_params(shape=sub, storage=storage, gamma=f0.gamma, tau=tau)
+
+    def dress(c):
+        c.set_boundary("x-", V.VLBM_BC_EQUILIBRIUM, 0b00010011, mean)
+        c.set_boundary("x+", V.VLBM_BC_EQUILIBRIUM)
+        if len(shape) == 3:  # edges: the x faces' normals turn diagonal there
+            c.set_boundary("y-", V.VLBM_BC_EQUILIBRIUM, 0b11100001, mean)
+            c.set_boundary("y+", V.VLBM_BC_EQUILIBRIUM)
+
+    with V.Context(make(shape)) as ctx:
+        assert ctx.init_fields(f0.Q) == V.VLBM_OK
+        dress(ctx)
+        ctx.step(steps)
+        ref = ctx.moments()
+    with S.LocalSlabs(make, shape, 2) as g:
+        assert g.init_fields(f0.Q) == V.VLBM_OK
+        for c in g.ctxs:
+            dress(c)
+        assert g.step(steps) == V.VLBM_OK
+        got = g.moments()
+    assert np.array_equal(got, ref)
