@@ -347,6 +347,25 @@ vlbm_status vlbm_closure_train_step(vlbm_closure *cl, const double *Q0_dev, cons
  * Enqueued on the context's stream; synchronises it. */
 vlbm_status vlbm_closure_train_step_ctx(vlbm_closure *cl, vlbm_ctx *ctx, const double *Qt_dev, double *loss);
 
+/* The two halves of vlbm_closure_train_step_ctx, for data-parallel training
+ * (one process per GPU, each on its own coarse runs, gradients averaged across
+ * the processes between the halves; no counterpart in the paper, which trains
+ * no network).  grad_step: the network on the context's state, one corrected
+ * step of `ctx`, the loss against Qt_dev (*loss, host) and its gradient with
+ * respect to every parameter into grads_dev (device, vlbm_closure_num_params
+ * floats, flat order above); the weights are not changed.  Synchronises the
+ * context's stream.  apply_grads: one Adam step with the gradient grads_dev
+ * (device, complete before the call), then the weights are re-packed for the
+ * tensor-core kernels; synchronises the closure's stream.  grad_step followed
+ * by apply_grads of the same gradient equals vlbm_closure_train_step_ctx bit
+ * for bit in the weights and the context's state (the gradient is summed in a
+ * fixed order; the reported loss is summed with FP64 atomics, so its last
+ * digits may differ between runs).  VLBM_ERR_ARG for NULL arguments or a context that is not a 3-D F32
+ * ideal context on the closure's grid. */
+vlbm_status vlbm_closure_grad_step_ctx(vlbm_closure *cl, vlbm_ctx *ctx, const double *Qt_dev, double *loss,
+                                       float *grads_dev);
+vlbm_status vlbm_closure_apply_grads(vlbm_closure *cl, const float *grads_dev);
+
 /* Homogenised solid objects (sec. 2.4, "Homogenization", HLBM).  Attach
  * (solid_dev) or detach (NULL) per-cell solid fields to a single-domain
  * ideal-MHD context (VLBM_IDEAL, F32 or F64 storage, 2-D or 3-D, no closure):

@@ -23,6 +23,12 @@ divergence.
 Training loss for one coarse step from state Q0 to target Qt:
     L = sum_{k, x} ((Q1_k(x) - Qt_k(x)) / sigma_k)^2 / N
 with Q1 the moments after the corrected step.
+
+Optimiser: Adam (Kingma and Ba, 2015, "Adam: a method for stochastic
+optimization", their Algorithm 1): first and second moment estimates of the
+gradient, each divided by one minus its decay rate to the power of the step
+count, and the parameter moved by the learning rate times the corrected first
+estimate over (the square root of the corrected second estimate + eps).
 """
 from __future__ import annotations
 
@@ -160,3 +166,13 @@ def init_params(rng, hidden=32, last_scale=0.0):
     return {"W1": w(hidden, 8), "b1": np.zeros(hidden),
             "W2": w(hidden, hidden), "b2": np.zeros(hidden),
             "W3": w(24, hidden, last_scale), "b3": np.zeros(24)}
+
+
+def adam_step(theta, m, v, g, t, lr, beta1, beta2, eps):
+    """Step t (1, 2, ...) of Adam from parameters theta, moment estimates m and v
+    (zero before the first step) and gradient g; returns (theta, m, v)."""
+    m = beta1 * m + (1.0 - beta1) * g
+    v = beta2 * v + (1.0 - beta2) * g * g
+    m_hat = m / (1.0 - beta1 ** t)
+    v_hat = v / (1.0 - beta2 ** t)
+    return theta - lr * m_hat / (np.sqrt(v_hat) + eps), m, v

@@ -85,14 +85,57 @@ def train(closure, trajectories, steps, rng, log_every=0):
     return losses
 
 
-def train_in_the_loop(closure, trajectories, episodes, gamma, tau, stream, rng, rollout=None, log_every=0):
+def _world(group):
+    import torch.distributed as dist
+    return dist.get_world_size(group) if dist.is_available() and dist.is_initialized() else 1
+
+
+def average_gradients(grads, loss, group=None):
+    """Data-parallel training: the mean of every process's gradient (a tensor,
+    changed in place) and loss over `group` (torch.distributed all-reduce; the
+    identity for one process).  Returns the mean loss."""
+    import torch
+    import torch.distributed as dist
+    world = _world(group)
+    if world == 1:
+        return float(loss)
+    lt = torch.tensor([float(loss)], dtype=torch.float64, device=grads.device)
+    dist.all_reduce(grads, group=group)
+    dist.all_reduce(lt, group=group)
+    grads.div_(world)
+    return float(lt.item()) / world
+
+
+def dp_train_step(closure, ctx, Qt, grads, group=None):
+    """One data-parallel training step: this process's loss and gradient for one
+    corrected coarse step of `ctx` against Qt, the gradient averaged over the
+    processes of `group`, one Adam step with the average (the same on every
+    process, so the weights stay equal).  `grads`: a device float tensor of
+    vlbm_closure_num_params entries.  Returns the mean loss."""
+    loss = closure.grad_step_ctx(ctx.ptr, Qt.data_ptr(), grads.data_ptr())
+    loss = average_gradients(grads, loss, group)
+    closure.apply_grads(grads.data_ptr())
+    return loss
+
+
+def train_in_the_loop(closure, trajectories, episodes, gamma, tau, stream, rng, rollout=None, log_every=0,
+                      group=None):
     """Solver-in-the-loop training: each episode restarts a coarse run from the
     restricted fine state at a random time and advances it with the current
     closure, one Adam step per coarse step against the restricted fine state
-    of the same time (gradient through the last step only)."""
+    of the same time (gradient through the last step only).  With a process
+    group of more than one process, every process runs its own episodes (its
+    own trajectories and rng) and the gradients are averaged at every step
+    (`dp_train_step`); each process must run the same number of episodes and
+    roll-out steps."""
+    import torch
     losses = []
     shape = tuple(trajectories[0][0].shape[1:])
     p = vlbm.make_params(shape=shape, storage="f32", gamma=gamma, tau=tau, stream=stream.cuda_stream)
+    dp = _world(group) > 1
+    if dp and not rollout:
+        raise ValueError("data-parallel training needs a fixed roll-out length on every process")
+    grads = torch.empty(closure.nparam, dtype=torch.float32, device="cuda") if dp else None
     with vlbm.Context(p) as ctx:
         for ep in range(episodes):
             tr = trajectories[rng.integers(len(trajectories))]
@@ -102,7 +145,10 @@ def train_in_the_loop(closure, trajectories, episodes, gamma, tau, stream, rng, 
             if st != vlbm.VLBM_OK:
                 raise RuntimeError("coarse init: " + vlbm.status_string(st))
             for n in range(start + 1, start + n_roll + 1):
-                losses.append(closure.train_step_ctx(ctx.ptr, tr[n].data_ptr()))
+                if dp:
+                    losses.append(dp_train_step(closure, ctx, tr[n], grads, group))
+                else:
+                    losses.append(closure.train_step_ctx(ctx.ptr, tr[n].data_ptr()))
             if ctx.sync() != vlbm.VLBM_OK:
                 losses.append(float("nan"))
             if log_every and ep % log_every == 0:
@@ -111,7 +157,7 @@ def train_in_the_loop(closure, trajectories, episodes, gamma, tau, stream, rng, 
 
 
 def train_with_validation(closure, trajectories, episodes, gamma, tau, stream, rng, validate, val_every=10,
-                          rollout=4, log=None):
+                          rollout=4, log=None, group=None):
     """In-the-loop training with early stopping: every `val_every` episodes
     `validate()` returns the held-out error of the corrected coarse run; the
     weights with the lowest validation error (the zero-output start included)
@@ -122,7 +168,7 @@ def train_with_validation(closure, trajectories, episodes, gamma, tau, stream, r
     done = 0
     while done < episodes:
         n = min(val_every, episodes - done)
-        train_in_the_loop(closure, trajectories, n, gamma, tau, stream, rng, rollout=rollout)
+        train_in_the_loop(closure, trajectories, n, gamma, tau, stream, rng, rollout=rollout, group=group)
         done += n
         err = validate()
         history.append((done, err))
@@ -379,18 +425,31 @@ def cfg5_mach(seed: int, lo: float = 1.0, hi: float = 3.0) -> float:
 def run_protocol(fine=512, factor=4, train_seeds=tuple(range(5000, 5016)), val_seed=5016,
                  test_seeds=(5100, 5101, 5102, 5103), mach_range=(1.0, 3.0), tau=0.51, n_pairs=16,
                  warm_steps=(0, 100, 200, 300), n_eval=250, episodes=160, val_every=20, rollout=4, lr=1e-5,
-                 out_scale_rel=0.005, seed=0, sides=(64, 128, 256), measure=64, log=None):
+                 out_scale_rel=0.005, seed=0, sides=(64, 128, 256), measure=64, log=None, group=None):
     """The learned-closure workload end to end: restricted fine trajectories of
     `train_seeds` (each starting `warm_steps[i % 4]` fine steps into its run, so
     early and developed states are both seen), in-the-loop training with early
     stopping on `val_seed` over an `n_eval`-coarse-step run, then on each held-out
     seed the fine run, the plain error-vs-time curve and the coarse runs with and
     without the closure (resolution_curve).  Seeds whose fine run turns
-    non-physical are reported and left out of the training data."""
+    non-physical are reported and left out of the training data.
+
+    With a process group of P > 1 processes (one GPU each), process r takes the
+    training seeds r, r + P, ...; the feature normalisation is the mean of the
+    processes' (they see equal shares), the weights start equal, every process
+    draws its own episodes, gradients are averaged at every step, and every
+    process validates (so that all keep the same weights); the held-out seeds
+    run on process 0 only."""
     import torch
     stream = torch.cuda.Stream()
     shape = (fine,) * 3
     coarse = fine // factor
+    world = _world(group)
+    rank = 0
+    if world > 1:
+        import torch.distributed as dist
+        rank = dist.get_rank(group)
+        train_seeds = tuple(train_seeds)[rank::world]
     t0 = time.perf_counter()
     trajs, skipped = [], []
     for i, s in enumerate(train_seeds):
@@ -403,20 +462,29 @@ def run_protocol(fine=512, factor=4, train_seeds=tuple(range(5000, 5016)), val_s
     if not trajs:
         return {"skipped_train_seeds": skipped, "error": "every training run became non-physical"}
     mu, sigma = normalisation([q for tr in trajs for q in tr])
+    if world > 1:  # the same normalisation on every process: mean of the processes' mean and variance
+        stats = torch.tensor(np.concatenate([mu, sigma ** 2 + mu ** 2]), dtype=torch.float64,
+                             device="cuda" if dist.get_backend(group) == "nccl" else "cpu")
+        dist.all_reduce(stats, group=group)
+        stats = stats.cpu().numpy() / world
+        mu = stats[:8]
+        sigma = np.sqrt(np.maximum(stats[8:] - mu ** 2, 0.0))
     gamma = 5.0 / 3.0
     cl = vlbm.Closure((coarse,) * 3, gamma, tau, mu, sigma, out_scale_rel * sigma, lr=lr, stream=stream.cuda_stream)
     rng = np.random.default_rng(seed)
-    cl.set_weights(init_weights(rng, last_scale=0.0))
+    cl.set_weights(init_weights(rng, last_scale=0.0))  # equal on every process
+    if world > 1:
+        rng = np.random.default_rng([seed, rank])  # each process its own episodes
     vref = fine_reference(shape, factor, val_seed, cfg5_mach(val_seed, *mach_range), n_eval, tau, torch, stream)
     t0 = time.perf_counter()
     best, hist = train_with_validation(cl, trajs, episodes, gamma, tau, stream, rng,
                                        lambda: coarse_error(vref, cl, tau, torch, stream)[0],
-                                       val_every=val_every, rollout=rollout, log=log)
+                                       val_every=val_every, rollout=rollout, log=log, group=group)
     t_train = time.perf_counter() - t0
     del trajs, vref
     torch.cuda.empty_cache()
     rows = [resolution_curve(cl, s, cfg5_mach(s, *mach_range), n_eval, tau, torch, stream, fine=fine, coarse=coarse,
-                             sides=sides, measure=measure) for s in test_seeds]
+                             sides=sides, measure=measure) for s in test_seeds] if rank == 0 else []
     return {"closure": cl, "best_val": best, "history": hist, "tests": rows, "t_data_s": t_data,
             "t_train_s": t_train, "skipped_train_seeds": skipped, "n_eval": n_eval, "coarse": coarse,
             "fine": fine, "train_seeds": list(train_seeds), "val_seed": val_seed, "test_seeds": list(test_seeds)}

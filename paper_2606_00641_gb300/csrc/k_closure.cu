@@ -1755,10 +1755,10 @@ vlbm_status vlbm_closure_backward(vlbm_closure *cl, const double *Q_dev, const f
 namespace vlbm {
 namespace {
 
-// From Q1 (moments after a corrected step) and the target: loss, gradient
-// through the step (Q1 = Q_plain - delta . dPhi), backward pass, Adam step and
-// re-packing of the weights.
-vlbm_status loss_backward_update(vlbm_closure *cl, const double *Qt_dev, double *loss, cudaStream_t s)
+// From Q1 (moments after a corrected step) and the target: loss and the
+// gradient through the step (Q1 = Q_plain - delta . dPhi) and the network,
+// left in cl->grad.
+vlbm_status loss_backward(vlbm_closure *cl, const double *Qt_dev, cudaStream_t s)
 {
     vlbm_status st = cl_check(cudaMemsetAsync(cl->loss, 0, sizeof(double), s), "closure loss clear");
     if (st == VLBM_OK) {
@@ -1770,7 +1770,25 @@ vlbm_status loss_backward_update(vlbm_closure *cl, const double *Qt_dev, double 
         st = cl_check(cudaGetLastError(), "closure loss launch");
     }
     if (st == VLBM_OK) st = backward(cl, s);
-    if (st == VLBM_OK) {
+    return st;
+}
+
+// The loss of the last loss_backward to the host, after the stream has finished.
+vlbm_status loss_to_host(vlbm_closure *cl, double *loss, cudaStream_t s)
+{
+    double h = 0.0;
+    vlbm_status st = cl_check(cudaMemcpyAsync(&h, cl->loss, sizeof(double), cudaMemcpyDeviceToHost, s), "loss");
+    if (st == VLBM_OK) st = cl_check(cudaStreamSynchronize(s), "closure train step");
+    if (st == VLBM_OK) st = cl_flags(cl);
+    if (loss) *loss = h;
+    return st;
+}
+
+// One Adam step from the gradient in cl->grad, and the re-packing of the weights.
+vlbm_status adam_update(vlbm_closure *cl, cudaStream_t s)
+{
+    vlbm_status st = VLBM_OK;
+    {
         cl->adam_t += 1;
         AdamArgs a{};
         a.lr = (float)cl->p.lr;
@@ -1784,11 +1802,31 @@ vlbm_status loss_backward_update(vlbm_closure *cl, const double *Qt_dev, double 
         st = cl_check(cudaGetLastError(), "closure adam launch");
     }
     if (st == VLBM_OK) st = pack_all(cl, s);
-    double h = 0.0;
-    if (st == VLBM_OK) st = cl_check(cudaMemcpyAsync(&h, cl->loss, sizeof(double), cudaMemcpyDeviceToHost, s), "loss");
-    if (st == VLBM_OK) st = cl_check(cudaStreamSynchronize(s), "closure train step");
-    if (st == VLBM_OK) st = cl_flags(cl);
-    if (loss) *loss = h;
+    return st;
+}
+
+// Loss, gradient, Adam step and re-packing (one training step).
+vlbm_status loss_backward_update(vlbm_closure *cl, const double *Qt_dev, double *loss, cudaStream_t s)
+{
+    vlbm_status st = loss_backward(cl, Qt_dev, s);
+    if (st == VLBM_OK) st = adam_update(cl, s);
+    if (st == VLBM_OK) st = loss_to_host(cl, loss, s);
+    return st;
+}
+
+// The forward half of a training step along a coarse run: the network on the
+// context's state, one corrected step, the new moments into cl->q1.
+vlbm_status advance_ctx(vlbm_closure *cl, vlbm_ctx *ctx)
+{
+    if (ctx->batched || ctx->model != VLBM_IDEAL || ctx->dim != 3 || ctx->storage != VLBM_F32 ||
+        ctx->dom[0].nx != cl->nx || ctx->dom[0].ny != cl->ny || ctx->dom[0].nz != cl->nz)
+        return fail(ctx, VLBM_ERR_ARG, "closure training context must be a 3-D F32 ideal context on the closure grid");
+    vlbm_status st = forward_ctx(cl, ctx, cl->dphi);
+    if (st == VLBM_OK) st = ideal_step_corrected(ctx, (int)(ctx->step & 1), cl->dphi);
+    if (st == VLBM_OK) {
+        ctx->step += 1;
+        st = ideal_moments(ctx, 0, cl->q1);
+    }
     return st;
 }
 
@@ -1818,18 +1856,35 @@ vlbm_status vlbm_closure_train_step(vlbm_closure *cl, const double *Q0_dev, cons
 vlbm_status vlbm_closure_train_step_ctx(vlbm_closure *cl, vlbm_ctx *ctx, const double *Qt_dev, double *loss)
 {
     if (!cl || !ctx || !Qt_dev) return VLBM_ERR_ARG;
-    if (ctx->batched || ctx->model != VLBM_IDEAL || ctx->dim != 3 || ctx->storage != VLBM_F32 ||
-        ctx->dom[0].nx != cl->nx || ctx->dom[0].ny != cl->ny || ctx->dom[0].nz != cl->nz)
-        return fail(ctx, VLBM_ERR_ARG, "closure training context must be a 3-D F32 ideal context on the closure grid");
-    cudaStream_t s = ctx->stream;
-    vlbm_status st = forward_ctx(cl, ctx, cl->dphi);
-    if (st == VLBM_OK) st = ideal_step_corrected(ctx, (int)(ctx->step & 1), cl->dphi);
-    if (st == VLBM_OK) {
-        ctx->step += 1;
-        st = ideal_moments(ctx, 0, cl->q1);
-    }
+    vlbm_status st = advance_ctx(cl, ctx);
     if (st != VLBM_OK) return st;
-    return loss_backward_update(cl, Qt_dev, loss, s);
+    return loss_backward_update(cl, Qt_dev, loss, ctx->stream);
+}
+
+vlbm_status vlbm_closure_grad_step_ctx(vlbm_closure *cl, vlbm_ctx *ctx, const double *Qt_dev, double *loss,
+                                       float *grads_dev)
+{
+    if (!cl || !ctx || !Qt_dev || !grads_dev) return VLBM_ERR_ARG;
+    cudaStream_t s = ctx->stream;
+    vlbm_status st = advance_ctx(cl, ctx);
+    if (st == VLBM_OK) st = loss_backward(cl, Qt_dev, s);
+    if (st == VLBM_OK)
+        st = cl_check(cudaMemcpyAsync(grads_dev, cl->grad, cl->nparam * 4, cudaMemcpyDeviceToDevice, s),
+                      "closure gradient copy");
+    if (st == VLBM_OK) st = loss_to_host(cl, loss, s);
+    return st;
+}
+
+vlbm_status vlbm_closure_apply_grads(vlbm_closure *cl, const float *grads_dev)
+{
+    if (!cl || !grads_dev) return VLBM_ERR_ARG;
+    cudaStream_t s = cl->stream;
+    vlbm_status st = cl_check(cudaMemcpyAsync(cl->grad, grads_dev, cl->nparam * 4, cudaMemcpyDeviceToDevice, s),
+                              "closure gradient copy");
+    if (st == VLBM_OK) st = adam_update(cl, s);
+    if (st == VLBM_OK) st = cl_check(cudaStreamSynchronize(s), "closure update");
+    if (st == VLBM_OK) st = cl_flags(cl);
+    return st;
 }
 
 vlbm_status vlbm_restrict(const double *Qf_dev, int nx, int ny, int nz, int factor, double *Qc_dev, void *stream)

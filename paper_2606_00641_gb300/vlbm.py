@@ -161,6 +161,8 @@ def load(build: bool = True):
         "vlbm_closure_backward": (i, [P, P, P, P]),
         "vlbm_closure_train_step": (i, [P, P, P, ctypes.POINTER(d)]),
         "vlbm_closure_train_step_ctx": (i, [P, P, P, ctypes.POINTER(d)]),
+        "vlbm_closure_grad_step_ctx": (i, [P, P, P, ctypes.POINTER(d), P]),
+        "vlbm_closure_apply_grads": (i, [P, P]),
         "vlbm_set_closure": (i, [P, P]),
         "vlbm_set_solid": (i, [P, P]),
         "vlbm_set_boundary": (i, [P, i, i, ctypes.c_uint, P]),
@@ -617,6 +619,19 @@ class Closure:
         _check(load().vlbm_closure_train_step_ctx(self.ptr, ctx_ptr, ctypes.c_void_p(Qt_ptr),
                                                   ctypes.byref(loss)), "vlbm_closure_train_step_ctx", ctx_ptr)
         return loss.value
+
+    def grad_step_ctx(self, ctx_ptr: int, Qt_ptr: int, grads_ptr: int) -> float:
+        """Loss and gradient of one corrected step of ctx into grads (device floats); no update."""
+        _device_inputs_ready()
+        loss = ctypes.c_double(0.0)
+        _check(load().vlbm_closure_grad_step_ctx(self.ptr, ctx_ptr, ctypes.c_void_p(Qt_ptr), ctypes.byref(loss),
+                                                 ctypes.c_void_p(grads_ptr)), "vlbm_closure_grad_step_ctx", ctx_ptr)
+        return loss.value
+
+    def apply_grads(self, grads_ptr: int):
+        """One Adam step with the gradient at grads_ptr (device floats)."""
+        _device_inputs_ready()
+        _check(load().vlbm_closure_apply_grads(self.ptr, ctypes.c_void_p(grads_ptr)), "vlbm_closure_apply_grads")
 
     def close(self):
         if self.ptr:

@@ -257,3 +257,40 @@ def test_split_layers_covers_the_axis():
     assert slabs.split_layers(4, 4) == [(0, 1), (1, 2), (2, 3), (3, 4)]
     with pytest.raises(ValueError):
         slabs.split_layers(3, 4)
+
+
+def _avg_main(rank, world, port, out):
+    import torch
+    import torch.distributed as dist
+    from paper_2606_00641_gb300 import closure
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
+                      LOCAL_RANK=str(rank))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    g = torch.arange(6, dtype=torch.float32) * (rank + 1) + rank
+    loss = closure.average_gradients(g, 0.5 + rank, None)
+    out[rank] = (g.tolist(), loss)
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_data_parallel_gradients_are_averaged_over_the_ranks(world):
+    # every rank ends with the mean gradient and the mean loss (closure.dp_train_step
+    # then applies one and the same Adam step on every rank)
+    mgr = mp.get_context("spawn").Manager()
+    out = mgr.dict()
+    port = _free_port()
+    mp.start_processes(_avg_main, args=(world, port, out), nprocs=world, join=True, start_method="spawn")
+    want = [sum(i * (r + 1) + r for r in range(world)) / world for i in range(6)]
+    want_loss = sum(0.5 + r for r in range(world)) / world
+    for r in range(world):
+        g, loss = out[r]
+        assert max(abs(a - b) for a, b in zip(g, want)) < 1e-6
+        assert abs(loss - want_loss) < 1e-12
+
+
+def test_data_parallel_average_without_a_group_is_the_identity():
+    import torch
+    from paper_2606_00641_gb300 import closure
+    g = torch.tensor([1.0, -2.0, 3.5])
+    assert closure.average_gradients(g, 0.25) == 0.25
+    assert g.tolist() == [1.0, -2.0, 3.5]

@@ -193,3 +193,69 @@ def test_trained_closure_beats_plain_coarse_run(V):
             assert t["rel_l2_closure_coarse"] < 0.95 * t["rel_l2_plain_coarse"], t
     finally:
         r["closure"].close()
+
+
+def _dp_problem(V, seed, lr=1e-3):
+    import torch
+    shape = (4, 16, 16)
+    f0 = fields.ideal_fields(shape, seed, mach=1.0, beta=1.0, cfl=0.2)
+    Q0 = f0.Q
+    mu = Q0.reshape(8, -1).mean(1)
+    sigma = Q0.reshape(8, -1).std(1) + 1e-3 * np.abs(Q0).reshape(8, -1).max(1) + 1e-12
+    out_scale = 1e-2 * sigma
+    rng = np.random.default_rng(seed)
+    Qt = Q0 * (1.0 + 1e-3 * rng.normal(size=Q0.shape))  # any target: the loss has a gradient
+    w0 = flat_params(C.init_params(rng, last_scale=0.1))
+    make_cl = lambda: V.Closure(shape, f0.gamma, 0.55, mu, sigma, out_scale, lr=lr)
+    p = V.make_params(shape=shape, storage="f32", gamma=f0.gamma, tau=0.55)
+    return shape, Q0, torch.from_numpy(Qt).cuda(), w0, make_cl, p
+
+
+def test_gradient_and_update_halves_equal_the_fused_train_step(V):
+    # data-parallel training splits each step into vlbm_closure_grad_step_ctx and
+    # vlbm_closure_apply_grads around the all-reduce; with one process (nothing averaged)
+    # the halves must reproduce the fused step exactly: losses, weights, coarse state
+    import torch
+    shape, Q0, Qtd, w0, make_cl, p = _dp_problem(V, 71)
+    a, b = make_cl(), make_cl()
+    a.set_weights(w0)
+    b.set_weights(w0)
+    grads = torch.empty(b.nparam, dtype=torch.float32, device="cuda")
+    with V.Context(p) as ca, V.Context(p) as cb:
+        assert ca.init_fields(Q0) == V.VLBM_OK and cb.init_fields(Q0) == V.VLBM_OK
+        for _ in range(4):
+            la = a.train_step_ctx(ca.ptr, Qtd.data_ptr())
+            w_before = b.get_weights()
+            lb = b.grad_step_ctx(cb.ptr, Qtd.data_ptr(), grads.data_ptr())
+            assert np.array_equal(b.get_weights(), w_before)  # the gradient half changes no weight
+            b.apply_grads(grads.data_ptr())
+            # the loss is summed with FP64 atomics (order-dependent rounding); the gradient
+            # is summed in a fixed order, so weights and states must agree bit for bit
+            assert abs(la - lb) <= 1e-12 * abs(la)
+        assert np.array_equal(a.get_weights(), b.get_weights())
+        assert np.array_equal(ca.moments(), cb.moments())
+    a.close()
+    b.close()
+
+
+def test_apply_grads_is_adam_on_the_given_gradient(V):
+    # the update half against the reference's Adam (pinned by its closed form), over
+    # three steps with gradients of widely different magnitudes (the bias corrections
+    # of steps 2 and 3 matter); FP32 weights and moment estimates, so within FP32 rounding
+    import torch
+    _, _, _, _, make_cl, _ = _dp_problem(V, 72)
+    cl = make_cl()
+    rng = np.random.default_rng(72)
+    w0 = (0.2 * rng.normal(size=cl.nparam)).astype(np.float32)
+    cl.set_weights(w0)
+    theta, m, v = w0.astype(np.float64), 0.0, 0.0
+    for t in range(1, 4):
+        g = (rng.normal(size=cl.nparam) * 10.0 ** rng.uniform(-4, 0, size=cl.nparam)).astype(np.float32)
+        gd = torch.from_numpy(g).cuda()
+        cl.apply_grads(gd.data_ptr())
+        theta, m, v = C.adam_step(theta, m, v, g.astype(np.float64), t, 1e-3, 0.9, 0.999, 1e-8)
+        got = cl.get_weights().astype(np.float64)
+        assert np.abs(got - theta).max() < 2e-6, (t, np.abs(got - theta).max())
+        # the step taken is the step of the reference (not merely small)
+        assert np.abs((got - w0) - (theta - w0)).max() < 2e-3 * np.abs(theta - w0).max()
+    cl.close()

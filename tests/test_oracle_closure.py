@@ -5,7 +5,9 @@ routine for the single-channel case); both backward passes against the exact
 adjoint identities of a linear map; the network gradient against central
 finite differences; the flux correction against its closed-form effect on
 one lattice Boltzmann step of the C oracle (zero change of every domain sum,
-moment change equal to minus the centred divergence of dPhi).
+moment change equal to minus the centred divergence of dPhi).  Adam against
+its closed form for a constant gradient and its invariance to the gradient's
+scale.
 """
 import numpy as np
 from scipy import ndimage
@@ -145,3 +147,41 @@ def test_storage_rounding_applies_where_the_hidden_values_are_kept():
     yr, cr = C.net_forward(p, x, store=lambda a: np.round(a, 2))
     assert np.array_equal(cr["a1"], np.round(np.tanh(C.conv3d(x, p["W1"], p["b1"])), 2))
     assert np.array_equal(cr["a2"], np.round(np.tanh(C.conv3d(cr["a1"], p["W2"], p["b2"])), 2))
+
+
+def test_adam_under_a_constant_gradient_moves_by_lr_each_step():
+    # with a constant gradient g from zero estimates, the bias corrections make the
+    # corrected estimates exactly g and g^2 at every step t, so each step moves every
+    # parameter by lr g / (|g| + eps), whatever the decay rates
+    rng = np.random.default_rng(3)
+    theta0 = rng.normal(size=50)
+    g = rng.normal(size=50) * 10.0 ** rng.uniform(-3, 1, size=50)
+    lr, b1, b2, eps = 1e-3, 0.9, 0.999, 1e-8
+    theta, m, v = theta0.copy(), np.zeros(50), np.zeros(50)
+    for t in range(1, 8):
+        theta, m, v = C.adam_step(theta, m, v, g, t, lr, b1, b2, eps)
+        np.testing.assert_allclose(theta, theta0 - t * lr * g / (np.abs(g) + eps), rtol=0, atol=1e-12)
+    # other decay rates, the same path
+    theta2, m, v = theta0.copy(), np.zeros(50), np.zeros(50)
+    for t in range(1, 8):
+        theta2, m, v = C.adam_step(theta2, m, v, g, t, lr, 0.5, 0.7, eps)
+    np.testing.assert_allclose(theta2, theta, rtol=0, atol=1e-12)
+
+
+def test_adam_step_is_invariant_to_the_gradient_scale_without_eps():
+    # m_hat / sqrt(v_hat) is homogeneous of degree zero in g: scaling every gradient
+    # of a sequence by c > 0 leaves the path unchanged (eps = 0)
+    rng = np.random.default_rng(4)
+    theta0 = rng.normal(size=40)
+    gs = [rng.normal(size=40) for _ in range(5)]
+    paths = []
+    for c in (1.0, 37.0):
+        theta, m, v = theta0.copy(), np.zeros(40), np.zeros(40)
+        for t, g in enumerate(gs, start=1):
+            theta, m, v = C.adam_step(theta, m, v, c * g, t, 1e-2, 0.9, 0.99, 0.0)
+        paths.append(theta)
+    np.testing.assert_allclose(paths[0], paths[1], rtol=0, atol=1e-13)
+    # and the second step differs from the first: the estimates carry history
+    t1, m, v = C.adam_step(theta0, 0.0, 0.0, gs[0], 1, 1e-2, 0.9, 0.99, 0.0)
+    t2, _, _ = C.adam_step(t1, m, v, gs[1], 2, 1e-2, 0.9, 0.99, 0.0)
+    assert np.abs((t2 - t1) - (-1e-2 * np.sign(gs[1]))).max() > 1e-4
