@@ -348,3 +348,36 @@ def test_dissipative_3d_conserves_the_mhd_sums(V, storage, tol):
         assert ctx.sync() == V.VLBM_OK
     scale = np.abs(Q0[:8]).reshape(8, -1).sum(1)
     assert (np.abs(s1 - s0) / scale).max() < tol
+
+
+def test_vortex_3d_full_size_sampled(V):
+    """The 3-D benchmark workload at its size: 256^3 low-Mach resistive vortex,
+    FP32, the benchmark's stream and first calls (4 + 4 steps), sampled at cells
+    on the domain's corners, faces and interior, each checked against the oracle
+    on the periodic (2n+1)^3 box centred on it (a cell after n D3Q7 steps depends
+    only on cells within L1 distance n; no path of n steps wraps on that box)."""
+    import torch
+    n = 256
+    setup = fields.low_mach_vortex_3d(n)
+    dp = oracle.Dissipation(nu=setup.nu, eta0=setup.eta0, j_c=setup.j_c, tau_m=setup.tau_m, powell=True)
+    stream = torch.cuda.Stream()
+    p = V.make_params(model=V.VLBM_DISSIPATIVE, shape=(n, n, n), storage="f32", gamma=setup.gamma, tau=setup.tau,
+                      tau_g=setup.tau_g, tau_m=setup.tau_m, nu=setup.nu, eta0=setup.eta0, j_c=setup.j_c,
+                      powell=True, stream=stream.cuda_stream)
+    with V.Context(p) as ctx:
+        assert V.vlbm_init_fields(ctx.ptr, 0, setup.Q) == V.VLBM_OK
+        V.vlbm_step(ctx.ptr, 4)
+        V.vlbm_step(ctx.ptr, 4)
+        cells = [(0, 0, 0), (255, 255, 255), (0, 128, 255), (131, 0, 7), (64, 200, 127), (255, 1, 128),
+                 (17, 255, 0), (200, 99, 129)]
+        Qall = ctx.moments()
+        assert ctx.sync() == V.VLBM_OK
+    steps = 8
+    w = steps
+    scale = field_scales3(setup.Q, setup.tau_m)
+    for z, y, x in cells:
+        iz, iy, ix = ((np.arange(c - w, c + w + 1)) % n for c in (z, y, x))
+        box = np.ascontiguousarray(setup.Q[:, iz][:, :, iy][:, :, :, ix])
+        ref = oracle.diss_run(box, setup.gamma, setup.tau, dp, steps, tau_g=setup.tau_g)[:, w, w, w]
+        err = np.abs(Qall[:, z, y, x] - ref) / scale
+        assert err.max() < 1e-5, ((z, y, x), dict(zip(fields.DISSIPATIVE3_FIELDS, err)))
