@@ -3,7 +3,9 @@
 * 512^3 ideal MHD, 8 x D3Q7, FP32 (the benchmark's workload and launch
   configuration): the populations of sampled cells after one step equal the
   oracle's collision of the gathered pre-step populations of their upstream
-  neighbours, at both AA parities; domain sums stay conserved.
+  neighbours, at both AA parities; domain sums stay conserved.  The same
+  one-step check for the FP16 and BF16 deviation forms at 512^3, up to the
+  storage rounding of the deviations.
 * 256 x 128 x 128 resistive channel (D3Q19 + 3 x D3Q7, walls): the same
   one-step check, including cells next to the walls (bounce-back and the
   magnetic wall equilibrium); mass stays conserved.
@@ -94,6 +96,45 @@ def test_ideal_512cubed_sampled_step(V, ideal512, parity):
     scale = np.abs(expect).reshape(len(cells), 8, 7).max(axis=(0, 2))
     err = np.abs(post - expect).reshape(len(cells), 8, 7).max(axis=(0, 2)) / scale
     assert err.max() < 1e-5, err
+
+
+@pytest.mark.parametrize("storage,ulp", [("f16dev", 2.0 ** -11), ("bf16dev", 2.0 ** -8)])
+def test_deviation_storage_512cubed_sampled_step(V, storage, ulp):
+    # the 16-bit forms at the benchmark's size and launch configuration (the persistent
+    # bulk-copy pairs kernel, 912 CTAs walking 2M row tiles): one step of sampled cells
+    # at both parities equals the oracle collision of the gathered upstream populations
+    # up to the storage rounding of the deviations (as at the small sizes)
+    import torch
+    shape = (512, 512, 512)
+    f0 = fields.ideal_fields(shape, 3003, mach=2.0, beta=1.0, cfl=0.2, k_rho=4, k_u=4, k_b=4,
+                             device=torch.device("cuda"))
+    flat = f0.Q.reshape(8, -1)
+    qref = flat.mean(1).cpu().numpy()
+    qscale = (flat - flat.mean(1, keepdim=True)).abs().amax(1).clamp_min(1e-30).cpu().numpy()
+    p = V.make_params(shape=shape, storage=storage, gamma=f0.gamma, tau=0.51, q_ref=qref, q_scale=qscale)
+    w = np.array([1 / 4] + [1 / 8] * 6)
+    with V.Context(p) as ctx:
+        assert V.vlbm_init_fields_device(ctx.ptr, 0, f0.Q.data_ptr()) == V.VLBM_OK
+        del f0, flat
+        torch.cuda.empty_cache()
+        ctx.step(3)
+        for parity in (1, 0):
+            rng = np.random.default_rng(21 + parity)
+            cells = sample_cells(shape, rng, 40)
+            src = {x: [shifted(int(x), c, shape) for c in D3Q7] for x in cells}
+            uniq = np.array(sorted({u for v in src.values() for u in v}), dtype=np.int64)
+            pre = dict(zip(uniq.tolist(), ctx.populations(uniq)))
+            assert (ctx.step_count & 1) == parity
+            ctx.step(1)
+            post = ctx.populations(cells)
+            assert ctx.sync() == V.VLBM_OK
+            coll = {u: oracle.ideal_collide_cell(3, p.gamma, 0.51, pre[u].reshape(8, 7)) for u in uniq.tolist()}
+            for r, x in enumerate(cells.tolist()):
+                exp = np.array([[coll[src[x][i]][k, i] for i in range(7)] for k in range(8)])
+                g_exp = (exp - w[None, :] * qref[:, None]) / qscale[:, None]
+                g_got = (post[r].reshape(8, 7) - w[None, :] * qref[:, None]) / qscale[:, None]
+                tol = ulp * np.abs(g_exp) + 2e-3 * ulp * 64 * np.abs(g_exp).max()
+                assert (np.abs(g_got - g_exp) <= tol).all(), (storage, parity, x, np.abs(g_got - g_exp).max())
 
 
 def test_ideal_512cubed_conservation(V, ideal512):
