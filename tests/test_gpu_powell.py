@@ -120,3 +120,46 @@ def test_powell_api_contract(V):
         bad = V.make_params(model=V.VLBM_IDEAL_POWELL, shape=shape, tau_d=tau_d, tau_m=tau_m)
         with pytest.raises(Exception):
             V.Context(bad)
+
+
+def test_powell_512cubed_light_cones(V):
+    """The benchmark's Powell leg at its size: 512^3, FP32, tau 0.51, tau_M 1, D from
+    rest, the headline fields; after 4 + 4 steps (the leg's first calls) the moments
+    of sampled cells (corners, faces, interior) equal the oracle run on the periodic
+    (2n+1)^3 box centred on each (a cell after n D3Q7 steps depends only on cells
+    within L1 distance n)."""
+    import torch
+    n, steps = 512, 8
+    shape = (n, n, n)
+    f0 = fields.ideal_fields(shape, 3003, gamma=5.0 / 3.0, mach=2.0, beta=1.0, cfl=0.2,
+                             device=torch.device("cuda"))
+    Q = torch.cat([f0.Q, torch.zeros((1,) + shape, dtype=f0.Q.dtype, device=f0.Q.device)])
+    gamma = f0.gamma
+    del f0
+    p = V.make_params(model=V.VLBM_IDEAL_POWELL, shape=shape, storage="f32", gamma=gamma, tau=0.51,
+                      tau_d=0.51, tau_m=1.0, stream=torch.cuda.Stream().cuda_stream)
+    cells = [(0, 0, 0), (511, 511, 511), (0, 256, 511), (300, 0, 17), (128, 400, 255), (511, 1, 128),
+             (63, 511, 0), (200, 99, 129)]
+    w = steps
+    boxes = []
+    for z, y, x in cells:
+        iz, iy, ix = (torch.arange(c - w, c + w + 1, device=Q.device) % n for c in (z, y, x))
+        boxes.append(Q[:, iz][:, :, iy][:, :, :, ix].cpu().numpy())
+    scale = Q.abs().reshape(9, -1).amax(1).cpu().numpy()
+    scale[1:4] = scale[1:4].max()
+    scale[5:8] = scale[5:8].max()
+    scale[8] = 1.0 * scale[5:8].max()  # D ~ tau_M grad B: its round-off scales with B
+    with V.Context(p) as ctx:
+        assert V.vlbm_init_fields_device(ctx.ptr, 0, Q.data_ptr()) == V.VLBM_OK
+        del Q
+        torch.cuda.empty_cache()
+        V.vlbm_step(ctx.ptr, 4)
+        V.vlbm_step(ctx.ptr, 4)
+        idx = np.array([x + n * (y + n * z) for z, y, x in cells], dtype=np.int64)
+        pops = ctx.populations(idx)  # the pre-collision populations: their sums are the moments
+        assert ctx.sync() == V.VLBM_OK
+    got = pops.reshape(len(cells), 9, 7).sum(2)
+    for r, box in enumerate(boxes):
+        ref = oracle.powell_run(box, gamma, [0.51] * 9, 1.0, steps)[:, w, w, w]
+        err = np.abs(got[r] - ref) / scale
+        assert err.max() < 1e-5, (cells[r], err)
