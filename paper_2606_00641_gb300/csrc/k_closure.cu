@@ -1726,6 +1726,7 @@ vlbm_status vlbm_closure_get_weights(vlbm_closure *cl, float *host, size_t count
 
 vlbm_status vlbm_closure_forward(vlbm_closure *cl, const double *Q_dev, float *dphi_dev)
 {
+    vlbm::NvtxRange range("vlbm_closure_forward");
     if (!cl || !Q_dev || !dphi_dev) return VLBM_ERR_ARG;
     vlbm_status st = forward(cl, Q_dev, dphi_dev, cl->stream);
     if (st == VLBM_OK) st = cl_check(cudaStreamSynchronize(cl->stream), "closure forward");
@@ -1735,6 +1736,7 @@ vlbm_status vlbm_closure_forward(vlbm_closure *cl, const double *Q_dev, float *d
 
 vlbm_status vlbm_closure_backward(vlbm_closure *cl, const double *Q_dev, const float *gy_dev, float *grads_host)
 {
+    vlbm::NvtxRange range("vlbm_closure_backward");
     if (!cl || !Q_dev || !gy_dev || !grads_host) return VLBM_ERR_ARG;
     vlbm_status st = forward(cl, Q_dev, cl->dphi, cl->stream);
     if (st == VLBM_OK) {
@@ -1837,6 +1839,7 @@ extern "C" {
 
 vlbm_status vlbm_closure_train_step(vlbm_closure *cl, const double *Q0_dev, const double *Qt_dev, double *loss)
 {
+    vlbm::NvtxRange range("vlbm_closure_train_step");
     if (!cl || !Q0_dev || !Qt_dev) return VLBM_ERR_ARG;
     cudaStream_t s = cl->stream;
     vlbm_ctx *in = cl->inner;
@@ -1855,6 +1858,7 @@ vlbm_status vlbm_closure_train_step(vlbm_closure *cl, const double *Q0_dev, cons
 
 vlbm_status vlbm_closure_train_step_ctx(vlbm_closure *cl, vlbm_ctx *ctx, const double *Qt_dev, double *loss)
 {
+    vlbm::NvtxRange range("vlbm_closure_train_step_ctx");
     if (!cl || !ctx || !Qt_dev) return VLBM_ERR_ARG;
     vlbm_status st = advance_ctx(cl, ctx);
     if (st != VLBM_OK) return st;
@@ -1864,6 +1868,7 @@ vlbm_status vlbm_closure_train_step_ctx(vlbm_closure *cl, vlbm_ctx *ctx, const d
 vlbm_status vlbm_closure_grad_step_ctx(vlbm_closure *cl, vlbm_ctx *ctx, const double *Qt_dev, double *loss,
                                        float *grads_dev)
 {
+    vlbm::NvtxRange range("vlbm_closure_grad_step_ctx");
     if (!cl || !ctx || !Qt_dev || !grads_dev) return VLBM_ERR_ARG;
     cudaStream_t s = ctx->stream;
     vlbm_status st = advance_ctx(cl, ctx);
@@ -1877,6 +1882,7 @@ vlbm_status vlbm_closure_grad_step_ctx(vlbm_closure *cl, vlbm_ctx *ctx, const do
 
 vlbm_status vlbm_closure_apply_grads(vlbm_closure *cl, const float *grads_dev)
 {
+    vlbm::NvtxRange range("vlbm_closure_apply_grads");
     if (!cl || !grads_dev) return VLBM_ERR_ARG;
     cudaStream_t s = cl->stream;
     vlbm_status st = cl_check(cudaMemcpyAsync(cl->grad, grads_dev, cl->nparam * 4, cudaMemcpyDeviceToDevice, s),

@@ -511,12 +511,14 @@ static vlbm_status init_from_host(vlbm_ctx *c, int domain, const void *Q_host, b
 
 vlbm_status vlbm_init_fields(vlbm_ctx *c, int domain, const double *Q_host)
 {
+    vlbm::NvtxRange range("vlbm_init_fields");
     if (!c || !Q_host) return VLBM_ERR_ARG;
     return init_from_host(c, domain, Q_host, false);
 }
 
 vlbm_status vlbm_init_fields_f32(vlbm_ctx *c, int domain, const float *Q_host)
 {
+    vlbm::NvtxRange range("vlbm_init_fields_f32");
     if (!c || !Q_host) return VLBM_ERR_ARG;
     if (c->storage == VLBM_F64) return fail(c, VLBM_ERR_UNSUPPORTED, "single-precision fields need FP32 or 16-bit storage");
     return init_from_host(c, domain, Q_host, true);
@@ -524,6 +526,7 @@ vlbm_status vlbm_init_fields_f32(vlbm_ctx *c, int domain, const float *Q_host)
 
 vlbm_status vlbm_init_fields_device(vlbm_ctx *c, int domain, const double *Q_dev)
 {
+    vlbm::NvtxRange range("vlbm_init_fields_device");
     if (!c || !Q_dev) return VLBM_ERR_ARG;
     vlbm_status s = begin_init(c, domain);
     if (s != VLBM_OK) return s;
@@ -560,6 +563,7 @@ static vlbm_status slab_ready(vlbm_ctx *c)
 
 vlbm_status vlbm_step(vlbm_ctx *c, int n)
 {
+    vlbm::NvtxRange range("vlbm_step");
     if (!c || n < 0) return VLBM_ERR_ARG;
     poll_flags(c);
     if (c->sticky != VLBM_OK) return c->sticky;
@@ -599,6 +603,7 @@ vlbm_status vlbm_step(vlbm_ctx *c, int n)
 
 vlbm_status vlbm_sync(vlbm_ctx *c)
 {
+    vlbm::NvtxRange range("vlbm_sync");
     if (!c) return VLBM_ERR_ARG;
     unsigned flags = 0;
     vlbm_status s = read_flags_sync(c, &flags);
@@ -647,12 +652,14 @@ static vlbm_status moments_to_host(vlbm_ctx *c, int domain, void *Q_host, bool f
 
 vlbm_status vlbm_moments(vlbm_ctx *c, int domain, double *Q_host)
 {
+    vlbm::NvtxRange range("vlbm_moments");
     if (!c || !Q_host) return VLBM_ERR_ARG;
     return moments_to_host(c, domain, Q_host, false);
 }
 
 vlbm_status vlbm_moments_f32(vlbm_ctx *c, int domain, float *Q_host)
 {
+    vlbm::NvtxRange range("vlbm_moments_f32");
     if (!c || !Q_host) return VLBM_ERR_ARG;
     if (c->storage == VLBM_F64) return fail(c, VLBM_ERR_UNSUPPORTED, "single-precision fields need FP32 or 16-bit storage");
     return moments_to_host(c, domain, Q_host, true);
@@ -660,6 +667,7 @@ vlbm_status vlbm_moments_f32(vlbm_ctx *c, int domain, float *Q_host)
 
 vlbm_status vlbm_moments_device(vlbm_ctx *c, int domain, double *Q_dev)
 {
+    vlbm::NvtxRange range("vlbm_moments_device");
     if (!c || !Q_dev) return VLBM_ERR_ARG;
     if (domain < 0 || domain >= (int)c->dom.size()) return fail(c, VLBM_ERR_ARG, "bad domain index");
     if (slab_ready(c) != VLBM_OK) return VLBM_ERR_STATE;
@@ -696,6 +704,7 @@ vlbm_status vlbm_gather_populations(vlbm_ctx *c, int domain, const int64_t *cell
 
 vlbm_status vlbm_conservation(vlbm_ctx *c, int domain, double *sums)
 {
+    vlbm::NvtxRange range("vlbm_conservation");
     if (!c || !sums) return VLBM_ERR_ARG;
     if (domain < 0 || domain >= (int)c->dom.size()) return fail(c, VLBM_ERR_ARG, "bad domain index");
     if (slab_ready(c) != VLBM_OK) return VLBM_ERR_STATE;
@@ -723,6 +732,7 @@ static const uint64_t kMagic = 0x564c424d53415645ull;  // "VLBMSAVE"
 
 vlbm_status vlbm_save(vlbm_ctx *c, void *buf, size_t *bytes)
 {
+    vlbm::NvtxRange range("vlbm_save");
     if (!c || !bytes) return VLBM_ERR_ARG;
     const size_t need = sizeof(SaveHeader) + c->pop_bytes;
     if (!buf) {
@@ -743,6 +753,7 @@ vlbm_status vlbm_save(vlbm_ctx *c, void *buf, size_t *bytes)
 
 vlbm_status vlbm_load(vlbm_ctx *c, const void *buf, size_t bytes)
 {
+    vlbm::NvtxRange range("vlbm_load");
     if (!c || !buf || bytes < sizeof(SaveHeader)) return VLBM_ERR_ARG;
     SaveHeader h;
     std::memcpy(&h, buf, sizeof(h));
@@ -765,6 +776,7 @@ vlbm_status vlbm_load(vlbm_ctx *c, const void *buf, size_t bytes)
 
 vlbm_status vlbm_autotune(vlbm_ctx *c, int steps, int *choice)
 {
+    vlbm::NvtxRange range("vlbm_autotune");
     if (!c || !choice || steps < 0) return VLBM_ERR_ARG;
     *choice = 0;
     if (!c->batched) return VLBM_OK;
@@ -915,6 +927,7 @@ size_t vlbm_halo_bytes(const vlbm_ctx *c)
 
 vlbm_status vlbm_halo_pack(vlbm_ctx *c, void *lo_dev, void *hi_dev)
 {
+    vlbm::NvtxRange range("vlbm_halo_pack");
     if (!c || !lo_dev || !hi_dev) return VLBM_ERR_ARG;
     if (!c->slab) return fail(c, VLBM_ERR_STATE, "halo pack: not a slab context (vlbm_set_slab)");
     return halo_copy(c, lo_dev, hi_dev, true);
@@ -922,6 +935,7 @@ vlbm_status vlbm_halo_pack(vlbm_ctx *c, void *lo_dev, void *hi_dev)
 
 vlbm_status vlbm_halo_unpack(vlbm_ctx *c, const void *lo_dev, const void *hi_dev)
 {
+    vlbm::NvtxRange range("vlbm_halo_unpack");
     if (!c || !lo_dev || !hi_dev) return VLBM_ERR_ARG;
     if (!c->slab) return fail(c, VLBM_ERR_STATE, "halo unpack: not a slab context (vlbm_set_slab)");
     vlbm_status s = halo_copy(c, const_cast<void *>(lo_dev), const_cast<void *>(hi_dev), false);
@@ -934,6 +948,7 @@ vlbm_status vlbm_halo_unpack(vlbm_ctx *c, const void *lo_dev, const void *hi_dev
 
 vlbm_status vlbm_slabs_step(vlbm_ctx *const *slabs, int nslabs, int n)
 {
+    vlbm::NvtxRange range("vlbm_slabs_step");
     if (!slabs || nslabs < 1 || n < 0) return fail(nullptr, VLBM_ERR_ARG, "slabs step: bad arguments");
     vlbm_ctx *c0 = slabs[0];
     for (int r = 0; r < nslabs; ++r) {

@@ -29,6 +29,8 @@
 
 #include "vlbm.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace vlbm {
 
 constexpr int kMaxLat = 9;  // per-lattice tables of Domain: ideal 8, Powell 9 (resistive 4; the
@@ -243,6 +245,15 @@ struct vlbm_ctx {
 };
 
 namespace vlbm {
+
+// A named range on the host timeline of profilers that read NVTX (header-only NVTX3: without
+// an attached tool each push and pop is a test of one pointer).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // host helpers (vlbm_api.cu)
 vlbm_status fail(vlbm_ctx *c, vlbm_status s, const std::string &msg);
