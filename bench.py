@@ -537,7 +537,8 @@ def batch_form(args, vlbm, fields, torch, stream, hbm_peak):
             "note": "the batched run issues its steps in one call; the sequential baseline calls one step per "
                     "domain, and a domain whose health word has turned non-physical stops stepping there "
                     "(a context refuses steps after the flag is seen), so the baseline's rate is an upper "
-                    "bound and the speedup a lower one (the domains named above hold 1.3 % of the cells)",
+                    "bound and the speedup a lower one",
+            "nonphysical_cell_share": sum(side * side for _, side, _ in bad_domains) / ncell,
             "bytes_per_cell": 320, "roofline_frac_batched": gb * 1e9 * 320 / (hbm_peak * 1e9)}
 
 
