@@ -124,6 +124,9 @@ def test_validation_before_any_device_work(V):
     assert L.vlbm_halo_bytes(None) == 0
     assert L.vlbm_slabs_step(None, 2, 1) == V.VLBM_ERR_ARG
     assert L.vlbm_measure_fp64_rate(4096, None, None) == V.VLBM_ERR_ARG
+    assert L.vlbm_closure_grad_step_ctx(None, None, None, None, None) == V.VLBM_ERR_ARG
+    assert L.vlbm_closure_apply_grads(None, None) == V.VLBM_ERR_ARG
+    assert L.vlbm_closure_train_step_ctx(None, None, None, None) == V.VLBM_ERR_ARG
     assert L.vlbm_nvar(None) == 0
     L.vlbm_destroy(None)
 
