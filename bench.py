@@ -15,7 +15,10 @@ Under torchrun (N > 1) the ranks hold the z-slabs of one periodic domain of
 512 x 512 x (512 N) cells, one 512^3 slab per rank (the 512^3 fields repeated
 along z, so every slab's result equals the one-GPU run), and after every step
 exchange the population planes that cross the slab faces by NCCL send/recv:
-the work per GPU is fixed, so the scaling is weak.
+the work per GPU is fixed, so the scaling is weak.  At N > 1 the job runs
+that decomposed headline only (timed region, end to end, slab check); the
+other storage forms, the error sweep, the other paths and the CPU oracle are
+one-GPU measurements of the N = 1 run.
 """
 from __future__ import annotations
 
@@ -953,7 +956,10 @@ def main():
 
     # ---- other storage forms: GLUPS and per-field error against FP64 ----
     forms = {}
-    form_list = [s for s in args.forms.split(",") if s] if rank == 0 else []
+    # the storage forms, the error sweep, the other paths and the CPU oracle are one-GPU
+    # measurements: at N > 1 the job runs the decomposed headline (timed region, e2e, slab check)
+    # only, so that the other GPUs are not held meanwhile
+    form_list = [s for s in args.forms.split(",") if s] if world == 1 else []
     if form_list:
         nfs = args.form_steps
 
@@ -997,11 +1003,11 @@ def main():
         del Q64
 
     growth = None
-    if rank == 0 and args.growth_steps > 0 and form_list:
+    if world == 1 and args.growth_steps > 0 and form_list:
         growth = error_growth(args, vlbm, fields, torch, stream)
 
     extra = {}
-    if rank == 0 and not args.no_extra:
+    if world == 1 and not args.no_extra:
         which = set(x for x in args.extras.split(",") if x)
         if "channel" in which:
             extra["resistive_channel"] = channel_form(args, vlbm, fields, torch, stream, hbm_peak)
@@ -1023,7 +1029,7 @@ def main():
             extra["ideal_2d_128sq_f64"] = ideal_2d_f64_form(args, vlbm, fields, torch, stream, fp64_tflops)
 
     cpu = None
-    if rank == 0 and not args.no_cpu:
+    if world == 1 and not args.no_cpu:
         cpu = cpu_baseline(args, args.cpu_seconds)
         cpu.pop("steps", None)
         cpu.pop("ms_per_step", None)
