@@ -82,9 +82,9 @@ def parse():
                     help="BGK times of the error runs (0.51 is the workload's)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the channel, batched and closure forms")
-    ap.add_argument("--extras", default="channel,batch,closure,powell,hlbm,open,diss,diss3,cfg1",
+    ap.add_argument("--extras", default="channel,batch,closure,powell,hlbm,open,slabs,diss,diss3,cfg1",
                     help="which other workloads to run (comma list of channel, batch, closure, powell, "
-                         "hlbm, open, diss, diss3, cfg1)")
+                         "hlbm, open, slabs, diss, diss3, cfg1)")
     ap.add_argument("--closure-fine", type=int, default=512, help="fine grid side of the closure workload")
     ap.add_argument("--closure-steps", type=int, default=250, help="coarse steps of the closure's test runs")
     ap.add_argument("--closure-mach", default="1,1.25",
@@ -379,6 +379,56 @@ def dissipative3_form(args, vlbm, fields, torch, stream, hbm_peak):
             "kernel": "k_diss3_step<float> (fused collide+stream, 182 populations per cell)",
             "init_status": vlbm.status_string(st), "status": status, "glups": gl, "steps": steps,
             "bytes_per_cell": bytes_cell, "roofline_frac": gl * 1e9 * bytes_cell / (hbm_peak * 1e9)}
+
+
+def slab_form(args, vlbm, fields, torch, stream, hbm_peak, parts_list=(2, 4)):
+    """The headline domain cut into P z-slabs on this one GPU (row f4 without a
+    second device): P contexts on one stream, each step every slab's step kernel,
+    then every slab's face planes packed and unpacked (vlbm_slabs_step).  The
+    rate against the single domain's measures what the halo copies cost per step
+    (on several GPUs NCCL carries the same messages)."""
+    n = args.size
+    shape = (n, n, n)
+    f0 = fields.ideal_fields(shape, args.seed, mach=2.0, beta=1.0, cfl=0.2, k_rho=4, k_u=4, k_b=4,
+                             device=torch.device("cuda"))
+    steps = args.form_steps
+    out = {"workload": "ideal MHD %d^3 (the headline fields), FP32, cut into P z-slabs on one GPU, "
+                       "halo planes exchanged after every step" % n, "steps": steps, "slabs": {}}
+    for parts in parts_list:
+        from paper_2606_00641_gb300 import slabs
+        ctxs = []
+        for z0, z1 in slabs.split_layers(n, parts):
+            p = vlbm.make_params(shape=(z1 - z0, n, n), storage="f32", gamma=f0.gamma, tau=0.51,
+                                 stream=stream.cuda_stream)
+            c = vlbm.Context(p)
+            Qs = f0.Q[:, z0:z1].contiguous()
+            vlbm.vlbm_init_fields_device(c.ptr, 0, Qs.data_ptr())
+            stream.synchronize()
+            del Qs
+            c.set_slab(True)
+            ctxs.append(c)
+        ptrs = [c.ptr for c in ctxs]
+        vlbm.vlbm_slabs_step(ptrs, 4)
+        l0 = sum(c.launches for c in ctxs)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        stream.synchronize()
+        e0.record(stream)
+        st = vlbm.vlbm_slabs_step(ptrs, steps)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        launches = sum(c.launches for c in ctxs) - l0
+        face = vlbm.vlbm_halo_bytes(ptrs[0])
+        statuses = {vlbm.status_string(vlbm.vlbm_sync(c.ptr)) for c in ctxs}
+        for c in ctxs:
+            c.close()
+        gl = n ** 3 * steps / (ms * 1e-3) / 1e9
+        out["slabs"][str(parts)] = {"glups": gl, "roofline_frac": gl * 1e9 * 448 / (hbm_peak * 1e9),
+                                    "launches_per_step": launches / steps, "halo_bytes_per_face": face,
+                                    "halo_message_bytes_per_step": 2 * parts * face,
+                                    "status": "/".join(sorted(statuses))}
+    del f0
+    return out
 
 
 def open_form(args, vlbm, fields, torch, stream, hbm_peak):
@@ -735,6 +785,9 @@ def compact_summary(line):
         # u residual against the closed-form profile after 5,000 steps, Ha 10 / 30 / 50
         out["channel_u_err_5000_Ha10,30,50"] = [
             _r(v["u_rel_linf_vs_closed_form"], 3) for v in extra["resistive_channel"]["hartmann"].values()]
+    if "slabs_one_gpu" in extra:
+        out["slabs_1gpu_[P,glups,frac]"] = [[int(k), _r(v["glups"]), _r(v["roofline_frac"])]
+                                            for k, v in extra["slabs_one_gpu"]["slabs"].items()]
     if "batched_2d" in extra:
         b = extra["batched_2d"]
         out["batched"] = [_r(b["glups_batched"]), _r(b["roofline_frac_batched"]), _r(b["speedup"])]
@@ -1021,6 +1074,8 @@ def main():
             extra["hlbm_sphere_3d"] = hlbm_form(args, vlbm, fields, torch, stream, hbm_peak)
         if "open" in which:
             extra["open_faces_3d"] = open_form(args, vlbm, fields, torch, stream, hbm_peak)
+        if "slabs" in which:
+            extra["slabs_one_gpu"] = slab_form(args, vlbm, fields, torch, stream, hbm_peak)
         if "diss" in which:
             extra["dissipative_2d"] = dissipative_form(args, vlbm, fields, torch, stream, hbm_peak)
         if "diss3" in which:
