@@ -31,6 +31,7 @@ IDEAL_PINS = [
     lambda o: P.test_update_is_covariant_under_the_rotations_of_the_lattice(o, 2),
     lambda o: P.test_update_is_covariant_under_the_rotations_of_the_lattice(o, 3),
     lambda o: P.test_linearised_update_operator_predicts_the_run(o),
+    lambda o: P.test_linearised_d3q7_operator_predicts_the_3d_run(o),
     lambda o: P.test_linearised_operator_has_the_mhd_speeds_and_decay(o),
 ]
 RES_PINS = [
